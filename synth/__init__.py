@@ -1,0 +1,97 @@
+"""Seeded synthetic inputs shared by the oracle tests, the GPU tests and the bench.
+
+This module holds no arithmetic of the method: it only draws the initial
+states, input vectors and problem parameters of the workloads (all from
+``numpy.random.default_rng(seed)``), and lays out grid coordinates.
+Workload recipes:
+
+* advection-diffusion 64x64 (2D periodic, D=1, a=(10,10)),
+  v = exp(-((x-0.6)^2+(y-0.6)^2)/0.01), h = 50 * dx^2/(4D)
+* Gray-Scott 1024x1024 two species (D_u=2e-5, D_v=1e-5, F=0.04, k=0.06),
+  u=1, v=0 plus U(0,0.1) on the central 64x64 cells of both species,
+  h = 100 * dx^2/(4 max D)
+* Burgers 2048x2048, nu=1e-3, u0 = sin(2 pi x) sin(2 pi y) + 0.1 N(0,1)
+  smoothed by 3 Jacobi sweeps, h = 50 * dx^2/(4 nu)
+* batched advection-diffusion problems: side round(exp(U(ln 32, ln 512))),
+  D ~ U(0.1,1), a ~ U(0,50)^2, h = U_log(10,200) * dx^2/(4D), v ~ N(0,1)
+
+Vectors are float64, C-contiguous, planar: species-major, then row (y),
+then column (x); grid nodes x_j = j/n on the periodic unit square.
+"""
+import numpy as np
+
+
+def grid_xy(n):
+    """Node coordinates (X, Y) of shape (n, n), X varying along axis 1."""
+    x = np.arange(n, dtype=np.float64) / n
+    return np.meshgrid(x, x, indexing="xy")
+
+
+def advdiff_gaussian(n=64):
+    X, Y = grid_xy(n)
+    return np.exp(-((X - 0.6) ** 2 + (Y - 0.6) ** 2) / 0.01).reshape(-1)
+
+
+def advdiff_params(n=64, D=1.0, ax=10.0, ay=10.0, mult=50.0):
+    dx = 1.0 / n
+    h = mult * dx * dx / (4.0 * D)
+    return dict(D=D, ax=ax, ay=ay, h=h)
+
+
+def grayscott_state(n=1024, seed=0, patch=64, amp=0.1):
+    """Two planes (u then v) of length n*n each: u=1, v=0 plus a seeded
+    uniform(0, amp) perturbation on the central patch x patch cells of both
+    species (u drawn first, then v)."""
+    rng = np.random.default_rng(seed)
+    u = np.ones((n, n))
+    v = np.zeros((n, n))
+    lo = n // 2 - patch // 2
+    hi = lo + patch
+    if patch > 0:
+        u[lo:hi, lo:hi] += rng.uniform(0.0, amp, size=(patch, patch))
+        v[lo:hi, lo:hi] += rng.uniform(0.0, amp, size=(patch, patch))
+    return np.concatenate([u.reshape(-1), v.reshape(-1)])
+
+
+def grayscott_params(n=1024, Du=2e-5, Dv=1e-5, F=0.04, k=0.06, mult=100.0):
+    dx = 1.0 / n
+    h = mult * dx * dx / (4.0 * max(Du, Dv))
+    return dict(Du=Du, Dv=Dv, F=F, k=k, h=h)
+
+
+def burgers_state(n=2048, seed=0, sweeps=3):
+    """u0 = sin(2 pi x) sin(2 pi y) + 0.1 N(0,1), then `sweeps` periodic
+    Jacobi sweeps u <- (u_E + u_W + u_N + u_S)/4 (a smoothing recipe, not
+    part of the method)."""
+    rng = np.random.default_rng(seed)
+    X, Y = grid_xy(n)
+    u = np.sin(2 * np.pi * X) * np.sin(2 * np.pi * Y) + 0.1 * rng.standard_normal((n, n))
+    for _ in range(sweeps):
+        u = 0.25 * (np.roll(u, 1, 0) + np.roll(u, -1, 0) + np.roll(u, 1, 1) + np.roll(u, -1, 1))
+    return u.reshape(-1)
+
+
+def burgers_params(n=2048, nu=1e-3, mult=50.0):
+    dx = 1.0 / n
+    return dict(nu=nu, h=mult * dx * dx / (4.0 * nu))
+
+
+def random_vector(n, seed=0):
+    return np.random.default_rng(seed).standard_normal(n)
+
+
+def batched_problems(count=4096, seed=0, side_lo=32, side_hi=512, h_lo=10.0, h_hi=200.0):
+    """List of dicts (n, D, ax, ay, h, seed_v) for independent periodic
+    advection-diffusion problems; each v is random_vector(n*n, seed_v)."""
+    rng = np.random.default_rng(seed)
+    sides = np.rint(np.exp(rng.uniform(np.log(side_lo), np.log(side_hi), size=count))).astype(int)
+    D = rng.uniform(0.1, 1.0, size=count)
+    a = rng.uniform(0.0, 50.0, size=(count, 2))
+    mult = np.exp(rng.uniform(np.log(h_lo), np.log(h_hi), size=count))
+    probs = []
+    for i in range(count):
+        n = int(sides[i])
+        dx = 1.0 / n
+        probs.append(dict(n=n, D=float(D[i]), ax=float(a[i, 0]), ay=float(a[i, 1]),
+                          h=float(mult[i] * dx * dx / (4.0 * D[i])), seed_v=seed * 100003 + i))
+    return probs
