@@ -1,0 +1,320 @@
+"""Benchmark: phi_l(hJ)v actions/s of EXPRB43 time steps on 2D Gray-Scott.
+
+Workload (one "step" = one EXPRB43 step = the whole Leja hot path: power
+iteration for the spectral interval, divided differences, the Newton-Leja
+passes phi_1(h/2 J) f h and phi_1(h J) f h (vertical), phi_1(h J) R(a) h,
+phi_3(h J)(16 R(a) - 2 R(b)) h, phi_4(h J)(-48 R(a) + 12 R(b)) h, and the
+stage assembly): Gray-Scott, 1024 x 1024 periodic grid, 2 species
+(N = 2,097,152), D_u = 2e-5, D_v = 1e-5, F = 0.04, k = 0.06, h = 100x the
+explicit limit, tol 1e-8, double-float iteration arithmetic; the state
+evolves over the timed steps.  5 phi-actions per step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl phix|reference]
+
+Under torchrun (N > 1) every rank integrates its own independent problem
+(seed = rank) on its own GPU: weak scaling, no collective on the data path.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+ACTIONS_PER_STEP = 5
+METRIC = "phi_l(hJ)v actions/s"
+UNIT = "phi-actions/s"
+WORKLOAD = "Gray-Scott 1024x1024x2, EXPRB43 steps, h=100x explicit limit, Leja, tol 1e-8"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="phix", choices=["phix", "reference"])
+    ap.add_argument("--prec", default="DF64", choices=["DF64", "FP64", "FP32_JV", "FP32"])
+    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle-reason samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_phix(args, world, rank, local):
+    import torch
+    import synth
+    from paper_2211_08948_gb300 import build, phix
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    phix.load()
+    stream = torch.cuda.current_stream()
+    ctx = phix.phix_create(stream)
+    n = args.n
+    prm = synth.grayscott_params(n)
+    u0 = synth.grayscott_state(n, seed=rank)
+    N = u0.size
+    op = phix.make_jop(phix.PHIX_OP_GRAYSCOTT, n, n, [prm["Du"], prm["Dv"], prm["F"], prm["k"]])
+    prec = getattr(phix, "PHIX_" + args.prec)
+    opts = phix.phix_opts_default(prec=prec, profile=1)
+    tol = 1e-8
+    h = prm["h"]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 135 MB L2
+
+    # ---- device-resident run -------------------------------------------------
+    u = torch.tensor(u0, dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        phix.phix_exprb43_step(ctx, op, u, h, tol, phix.PHIX_LEJA, opts)
+    u.copy_(torch.tensor(u0, dtype=torch.float64, device="cuda"))
+    stats = []
+    sampler = ClockSampler(local)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        flush.fill_(1.0)  # L2 flush between steps
+        stats.append(phix.phix_exprb43_step(ctx, op, u, h, tol, phix.PHIX_LEJA, opts).as_dict())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    u_fast = u.cpu().numpy()
+
+    # ---- accuracy against the plain float64 path (same steps, untimed) -------
+    uref = torch.tensor(u0, dtype=torch.float64, device="cuda")
+    o64 = phix.phix_opts_default(prec=phix.PHIX_FP64)
+    for _ in range(args.steps):
+        phix.phix_exprb43_step(ctx, op, uref, h, tol, phix.PHIX_LEJA, o64)
+    ur = uref.cpu().numpy()
+    rel_err = float(np.linalg.norm(u_fast - ur) / np.linalg.norm(ur))
+    rel_err_incr = float(np.linalg.norm(u_fast - ur) / max(np.linalg.norm(ur - u0), 1e-300))
+
+    # ---- end to end: pinned host buffers, H2D + step + D2H every step ---------
+    e2e = None
+    if not args.no_e2e:
+        hbuf = torch.tensor(u0, dtype=torch.float64).pin_memory()
+        hout = torch.empty_like(hbuf).pin_memory()
+        ud = torch.empty(N, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            ud.copy_(hbuf, non_blocking=True)
+            phix.phix_exprb43_step(ctx, op, ud, h, tol, phix.PHIX_LEJA, opts)
+            hout.copy_(ud, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+            hbuf.copy_(hout)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ems = f0.elapsed_time(f1)
+        if world > 1:
+            t = torch.tensor([ems], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": ACTIONS_PER_STEP * args.steps * world / (ems * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8}
+
+    phix.phix_destroy(ctx)
+
+    iter_ms = sum(s["iter_ms"] for s in stats)
+    iter_bytes = sum(s["iter_bytes"] for s in stats)
+    iter_launches = sum(s["iter_launches"] for s in stats)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = peaks.get("hbm_gbs", 6800.0)
+    achieved = iter_bytes / (iter_ms * 1e-3) / 1e9 if iter_ms > 0 else None
+    result = {
+        "metric": METRIC,
+        "value": ACTIONS_PER_STEP * args.steps * world / (ms * 1e-3),
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32x2 (double-float)" if args.prec == "DF64" else args.prec.lower(),
+        "data": "synthetic (seeded Gray-Scott initial state, seed = rank)",
+        "config": {"workload": WORKLOAD, "grid": [n, n], "species": 2, "unknowns": N, "h": h, "tol": tol,
+                   "method": "leja", "prec": args.prec, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "flushed between steps (256 MB write, inside the timed region)"},
+        "time_steps_per_s": args.steps * world / (ms * 1e-3),
+        "hbm_gbs_iteration_algorithmic": achieved,
+        "rel_err_vs_fp64": rel_err,
+        "rel_err_of_increment_vs_fp64": rel_err_incr,
+        "newton_iters_per_step": statistics.mean(s["iters"] for s in stats),
+        "power_mv_per_step": statistics.mean(s["power_mv"] for s in stats),
+        "gpu_launches": int(sum(s["launches"] for s in stats)),
+        "e2e": e2e,
+        "roofline": {
+            "bound": "hbm", "kernel": "k_iter (Newton-Leja step)",
+            "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": (achieved / peak) if achieved else None,
+            "traffic": None,
+            "launches": iter_launches,
+            "avg_launch_us": 1e3 * iter_ms / max(1, iter_launches),
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback",
+        },
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(n, u0, prm, tol)
+    if world > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+
+
+def cpu_baseline(n, u0, prm, tol):
+    """The oracle as it stands, one full EXPRB43 step of the same workload."""
+    from oracle import integrators, leja
+    from oracle.operators import GrayScott
+    leja.leja_points(501)
+    op = GrayScott(n, prm["Du"], prm["Dv"], prm["F"], prm["k"])
+    t = time.perf_counter()
+    integrators.exprb43_step(op, u0, prm["h"], tol=tol)
+    dt = time.perf_counter() - t
+    return {"value": ACTIONS_PER_STEP / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "one EXPRB43 step (5 phi-actions) of the same 1024^2 Gray-Scott workload, "
+                      "NumPy float64, single thread (%.1f s)" % dt}
+
+
+def run_reference(args, world, rank):
+    """Reference arm: the CPU oracle, each step a bounded sample of the same
+    workload (the vertical Leja pass phi_1(h/2 J) f h, phi_1(h J) f h of one
+    EXPRB43 step: 2 phi-actions)."""
+    if rank != 0:
+        return
+    import synth
+    from oracle import leja, integrators
+    from oracle.operators import GrayScott, with_state
+    n = args.n
+    prm = synth.grayscott_params(n)
+    u0 = synth.grayscott_state(n, seed=0)
+    op = with_state(GrayScott(n, prm["Du"], prm["Dv"], prm["F"], prm["k"]), u0)
+    leja.leja_points(501)
+    spec, _ = integrators.spectrum(op)
+    v = op.f(u0) * prm["h"]
+
+    def sample():
+        leja.leja_phi(op.jv, v, prm["h"], spec[0], spec[1], [(1, 0.5), (1, 1.0)], 1e-8)
+
+    for _ in range(args.warmup):
+        sample()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        sample()
+    dt = time.perf_counter() - t
+    val = 2 * args.steps / dt
+    desc = ("per step: the vertical Leja pass (2 phi-actions) of one EXPRB43 step on the 1024^2 "
+            "Gray-Scott state, NumPy float64 oracle, single thread")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "grid": [n, n]},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_phix(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

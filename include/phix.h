@@ -1,0 +1,201 @@
+/*
+ * phix: actions of the phi-functions of exponential integrators, phi_l(hJ)v,
+ * on GB300 (sm_103a), by real-Leja interpolation and by a KIOPS-style Krylov
+ * method, plus the EXPRB43 and EPIRK4s3 time steps built on them.
+ *
+ * The method is that of Deka & Einkemmer, "A comparison of Leja- and
+ * Krylov-based iterative schemes for Exponential Integrators"
+ * (arXiv:2211.08948):
+ *   phi-functions ........ Sec. 1   (phi_0 = e^z, phi_{l+1} = (phi_l - 1/l!)/z)
+ *   Krylov / augmented ... Sec. 2.1 (Theorem: exp of [[A, B], [0, K]])
+ *   Leja interpolation ... Sec. 2.2 (Newton form at Leja points, stop test)
+ *   vertical form ........ Sec. 4
+ *   EPIRK4s3 ............. Sec. 5.1, Eq. (epirk4s3)
+ *   EXPRB43 .............. Sec. 5.4, Eq. (exprb43)
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Memory.  Every vector argument is a DEVICE pointer to float64 data owned
+ *   by the caller, contiguous, 8-byte aligned (16-byte alignment enables the
+ *   vectorised kernels).  Vectors are planar: species-major, then row y,
+ *   then column x; length N = ncomp * nx * ny.  The library never frees or
+ *   keeps caller memory.  Scalars and small arrays (l[], scale[], b[]) are
+ *   HOST memory.  The context owns a device workspace that grows on demand.
+ * Streams.  All work is enqueued on the stream given to phix_create.  Entry
+ *   points that need a decision from the device (iteration counts,
+ *   convergence) synchronise that stream; on return all outputs are valid.
+ * Grid.  Periodic unit square, dx = 1/nx, dy = 1/ny, second-order centred
+ *   differences (Sec. 3).
+ * Errors.  Every function returns a phix_status; no exception crosses the
+ *   ABI, the GPU never traps.  phix_last_error() gives a message.  On
+ *   PHIX_ENOTCONV outputs hold the last iterate.  Inputs are never written,
+ *   except u_inout of the step functions (on success only).
+ * Threads.  A context is not thread-safe; use one per host thread/stream.
+ */
+#ifndef PHIX_H
+#define PHIX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PHIX_VERSION 100
+
+typedef struct phix_ctx phix_ctx;
+
+typedef enum {
+  PHIX_OK = 0,
+  PHIX_EINVAL = 1,    /* bad argument (sizes, pointers, enum values)        */
+  PHIX_ENOTCONV = 2,  /* Leja: m_max reached; KIOPS: substep limit reached  */
+  PHIX_ENAN = 3,      /* a norm became NaN/Inf                              */
+  PHIX_ETIMEOUT = 4,  /* a bounded device wait expired                      */
+  PHIX_ECUDA = 5,     /* a CUDA runtime call failed                         */
+  PHIX_ENOMEM = 6     /* workspace allocation failed                        */
+} phix_status;
+
+typedef enum { PHIX_LEJA = 0, PHIX_KIOPS = 1 } phix_method;
+
+/* Arithmetic of the iteration (Newton-Leja step / Arnoldi).  Inputs and
+ * outputs are always float64; divided differences, Leja points, the small
+ * Krylov exponential and all scalar control are float64 in every mode.    */
+typedef enum {
+  PHIX_FP64 = 0,    /* native float64 everywhere                            */
+  PHIX_DF64 = 1,    /* double-float: pairs of float32 (hi, lo), ~2^-47
+                       relative per operation, float64-class results          */
+  PHIX_FP32_JV = 2, /* stencil J*y in float32 on hi parts, the Newton update
+                       and accumulation in double-float                      */
+  PHIX_FP32 = 3     /* float32 iteration                                    */
+} phix_prec;
+
+typedef enum {
+  PHIX_OP_ADVDIFF = 0,   /* f(u) = D lap u + ax u_x + ay u_y (linear), 1 species        */
+  PHIX_OP_GRAYSCOTT = 1, /* Sec. 3: f_u = Du lap u - u v^2 + F(1-u),
+                                    f_v = Dv lap v + u v^2 - (F+k) v, 2 species     */
+  PHIX_OP_BURGERS = 2    /* f(u) = nu lap u - u (u_x + u_y), 1 species                  */
+} phix_op_kind;
+
+/* A Jacobian operator J = J(state) of one of the right-hand sides above.  */
+typedef struct {
+  int kind;            /* phix_op_kind                                               */
+  int nx, ny;          /* grid, nx, ny >= 3                                          */
+  double param[8];     /* ADVDIFF: D, ax, ay | GRAYSCOTT: Du, Dv, F, k | BURGERS: nu */
+  const double* state; /* device, linearisation point u^n (GRAYSCOTT, BURGERS); may
+                          be NULL for ADVDIFF.  Ignored by the step functions, which
+                          linearise at u_inout.                                      */
+} phix_jop;
+
+/* Tunables; fill with phix_opts_default() and override fields.            */
+typedef struct {
+  phix_prec prec;      /* iteration arithmetic (default PHIX_DF64)                     */
+  double safety;       /* spectral interval [-safety*rho, 0] from power iteration (1.2) */
+  double rho_re;       /* > 0: |Re lambda|max of J supplied by the caller: the interval
+                          is [-rho_re, rho_hi] and no power iteration runs (default -1) */
+  double rho_hi;       /* upper end of the real interval when rho_re > 0 (default 0)   */
+  double rho_im;       /* >= 0: bound on |Im lambda(J)|, used for substep counts (0)   */
+  double gamma_cap;    /* Leja: max s*h*gamma per substep (default 200)                */
+  double iota_cap;     /* Leja: max s*h*rho_im per substep, 0 = off (default 4)        */
+  int m_max;           /* Leja: max Newton iterations per pass (default 500)           */
+  int m_min;           /* Leja: first iteration where the stop test applies (3)       */
+  int power_max_it;    /* power iteration: max matvecs (50)                           */
+  double power_rel;    /* power iteration: stop at this relative change (1e-2)        */
+  uint64_t power_seed; /* SplitMix64 stream of the power-iteration start vector        */
+  int kiops_m_init;    /* KIOPS: initial Krylov dimension (16)                         */
+  int kiops_m_max;     /* KIOPS: max Krylov dimension (64)                             */
+  int kiops_m_step;    /* KIOPS: basis growth on rejection (8)                         */
+  int kiops_max_substeps; /* KIOPS: substep limit -> PHIX_ENOTCONV (10000)             */
+  int profile;         /* 1: time every iteration launch with CUDA events on the
+                          context's stream and report it in phix_stats (default 0)      */
+} phix_opts;
+
+/* Per-call statistics (host struct, filled on return).                    */
+typedef struct {
+  int status;        /* phix_status of the call                                       */
+  int iters;         /* Leja Newton iterations / KIOPS Arnoldi steps (all passes)      */
+  int jv;            /* Jacobian-vector products in the iteration                      */
+  int substeps;      /* Leja ODE-identity substeps / KIOPS accepted substeps           */
+  int power_mv;      /* power-iteration matvecs                                        */
+  int rejections;    /* KIOPS rejected substep attempts                                */
+  int passes;        /* Leja Newton passes / KIOPS runs                                */
+  int launches;      /* device kernels launched by the call                            */
+  double rho;        /* |lambda|max estimate used for the Leja interval                */
+  double err_est;    /* step functions: ||u4 - u3||_2                                  */
+  /* opts.profile = 1 only: the Newton-Leja / Arnoldi iteration launches that did
+     work, their summed device time (CUDA events) and their algorithmic HBM bytes
+     (each vector read or written once per launch).                                    */
+  int iter_launches;
+  double iter_ms;
+  double iter_bytes;
+} phix_stats;
+
+void phix_opts_default(phix_opts* opts);
+int phix_version(void);
+
+/* Create a context bound to a CUDA stream (cudaStream_t passed as void*,
+ * NULL = legacy default stream) on the current device.  Returns PHIX_EINVAL
+ * if ctx is NULL, PHIX_ECUDA if no device is usable.                       */
+phix_status phix_create(phix_ctx** ctx, void* cuda_stream);
+/* Free the context's workspace (after synchronising its stream).          */
+phix_status phix_destroy(phix_ctx* ctx);
+/* Message of the last failed call on ctx (empty string if none).          */
+const char* phix_last_error(const phix_ctx* ctx);
+
+/* Vertical/individual actions, Sec. 2.2 and Sec. 4:
+ *   out[k] = phi_{l[k]}(scale[k] * h * J) v,   k = 0 .. nout-1,
+ * without any h^l factor.  l[k] in 0..8, scale[k] > 0, 1 <= nout <= 4.
+ * PHIX_LEJA: one Newton basis shared by all outputs when no substeps are
+ * needed (vertical form), else each output by ODE-identity substeps.
+ * PHIX_KIOPS: one Krylov run per distinct l with output times scale[k].
+ * tol: relative 2-norm stop tolerance (Leja: |d_m| ||y_m|| <= tol ||p_m||;
+ * KIOPS: error per unit step relative to the augmented vector norm).
+ * v and out[k] are device vectors of length N; out[k] may not alias v.    */
+phix_status phix_phi_action(phix_ctx* ctx, const phix_jop* op, double h, const double* v,
+                            int nout, const int* l, const double* scale, double* const* out,
+                            double tol, phix_method method, const phix_opts* opts,
+                            phix_stats* stats);
+
+/* Horizontal combination, Theorem of Sec. 2.1:
+ *   out = sum_{j=0}^{p} phi_j(h J) b[j]     (b[j] == NULL means zero),
+ * 0 <= p <= 8.  KIOPS: one augmented Krylov run.  LEJA: one individual
+ * phi_j action per non-NULL b[j] (the paper's Leja evaluates phi_l
+ * individually, App. A), summed.                                          */
+phix_status phix_phi_combination(phix_ctx* ctx, const phix_jop* op, double h,
+                                 const double* const* b, int p, double* out, double tol,
+                                 phix_method method, const phix_opts* opts, phix_stats* stats);
+
+/* Spectrum estimate of J (Sec. 2.2 "power iterations"): *rho = ||J v_k||
+ * for the power iterate v_k from a SplitMix64 start vector.               */
+phix_status phix_spectrum(phix_ctx* ctx, const phix_jop* op, const phix_opts* opts,
+                          double* rho, phix_stats* stats);
+
+/* One EXPRB43 step, Eq. (exprb43): u_inout <- u4 (4th order).  J and f at
+ * u_inout; *err_est = ||u4 - u3||_2 (the embedded 3rd-order estimate).
+ * Leja: phi_1(h/2 J) f h and phi_1(h J) f h vertically, the other three
+ * actions individually.  KIOPS: the first two as output times 1/2, 1 of
+ * one run, the rest individually.                                         */
+phix_status phix_exprb43_step(phix_ctx* ctx, const phix_jop* op, double* u_inout, double h,
+                              double tol, phix_method method, const phix_opts* opts,
+                              double* err_est, phix_stats* stats);
+
+/* One EPIRK4s3 step, Eq. (epirk4s3): phi_1 at scales 1/8, 1/9, 1 on f h
+ * vertically, then phi_3 and phi_4 on the remainder combinations.         */
+phix_status phix_epirk4s3_step(phix_ctx* ctx, const phix_jop* op, double* u_inout, double h,
+                               double tol, phix_method method, const phix_opts* opts,
+                               double* err_est, phix_stats* stats);
+
+/* Host utility: the first m real Leja points on [-2, 2] (xi_0 = 2,
+ * xi_1 = -2, xi_2 = 0, then greedy max-product), Sec. 2.2.  xi is a HOST
+ * array of length m, 1 <= m <= 4096.                                      */
+phix_status phix_leja_points(double* xi, int m);
+
+/* Host utility: Newton divided differences of xi -> phi_l(a + b*xi) on the
+ * first m Leja points (the coefficients d_m of Sec. 2.2).  HOST arrays.   */
+phix_status phix_divided_differences(int l, double a, double b, int m, double* d);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PHIX_H */

@@ -33,7 +33,7 @@ def _phi_actions(opu, v, h, outputs, method, tol, spec, stats, leja_kw, kiops_kw
 
 def spectrum(opu, safety=1.2, seed=0x5EED, max_it=50, rel=1e-2):
     """Leja interval [alpha, beta] = [-safety * rho, 0] from power iteration (Sec. 2.2)."""
-    n = opu.n * opu.n * opu.ncomp
+    n = opu.n * opu.ny * opu.ncomp
     rho, mv = _leja.power_iteration(opu.jv, n, seed=seed, max_it=max_it, rel=rel)
     return (-safety * rho, 0.0), mv
 

@@ -6,6 +6,9 @@ Jacobian action (Sec. 2, "matrix-free implementation ... computation of the
 RHS functions").  Grids are n x n on the periodic unit square, dx = 1/n,
 vectors planar (species, y, x), float64.
 
+Grids may be rectangular: n is the number of columns (x), ny (default n) the
+number of rows, dx = 1/n, dy = 1/ny.
+
 Operators:
 * advection-diffusion  f(u) = D lap(u) + ax u_x + ay u_y    (linear, J = f)
 * Gray-Scott (Sec. 3)  f_u = Du lap(u) - u v^2 + F (1 - u)
@@ -16,8 +19,9 @@ The nonlinear remainder of Sec. 1 is R(a) = F(a) - F(u), F(x) = f(x) - J(u)x.
 import numpy as np
 
 
-def _lap(u, dx):
-    return (np.roll(u, 1, 0) + np.roll(u, -1, 0) + np.roll(u, 1, 1) + np.roll(u, -1, 1) - 4.0 * u) / (dx * dx)
+def _lap(u, dx, dy):
+    return (np.roll(u, 1, 1) + np.roll(u, -1, 1) - 2.0 * u) / (dx * dx) \
+        + (np.roll(u, 1, 0) + np.roll(u, -1, 0) - 2.0 * u) / (dy * dy)
 
 
 def _ddx(u, dx):
@@ -25,21 +29,23 @@ def _ddx(u, dx):
     return (np.roll(u, -1, 1) - np.roll(u, 1, 1)) / (2.0 * dx)
 
 
-def _ddy(u, dx):
-    return (np.roll(u, -1, 0) - np.roll(u, 1, 0)) / (2.0 * dx)
+def _ddy(u, dy):
+    return (np.roll(u, -1, 0) - np.roll(u, 1, 0)) / (2.0 * dy)
 
 
 class AdvDiff:
     """Linear 2D periodic advection-diffusion (Sec. 3 discretisation)."""
     ncomp = 1
 
-    def __init__(self, n, D, ax, ay):
+    def __init__(self, n, D, ax, ay, ny=None):
         self.n, self.D, self.ax, self.ay = n, D, ax, ay
-        self.dx = 1.0 / n
+        self.ny = n if ny is None else ny
+        self.dx, self.dy = 1.0 / n, 1.0 / self.ny
 
     def f(self, u):
-        U = u.reshape(self.n, self.n)
-        return (self.D * _lap(U, self.dx) + self.ax * _ddx(U, self.dx) + self.ay * _ddy(U, self.dx)).reshape(-1)
+        U = u.reshape(self.ny, self.n)
+        return (self.D * _lap(U, self.dx, self.dy) + self.ax * _ddx(U, self.dx)
+                + self.ay * _ddy(U, self.dy)).reshape(-1)
 
     def jv(self, w):
         return self.f(w)
@@ -49,27 +55,28 @@ class GrayScott:
     """Gray-Scott reaction-diffusion, Sec. 3 (a = F feed, b = k kill)."""
     ncomp = 2
 
-    def __init__(self, n, Du, Dv, F, k, state=None):
+    def __init__(self, n, Du, Dv, F, k, state=None, ny=None):
         self.n, self.Du, self.Dv, self.F, self.k = n, Du, Dv, F, k
-        self.dx = 1.0 / n
+        self.ny = n if ny is None else ny
+        self.dx, self.dy = 1.0 / n, 1.0 / self.ny
         self.state = state
 
     def _split(self, x):
-        nn = self.n * self.n
-        return x[:nn].reshape(self.n, self.n), x[nn:].reshape(self.n, self.n)
+        nn = self.n * self.ny
+        return x[:nn].reshape(self.ny, self.n), x[nn:].reshape(self.ny, self.n)
 
     def f(self, x):
         u, v = self._split(x)
         uvv = u * v * v
-        fu = self.Du * _lap(u, self.dx) - uvv + self.F * (1.0 - u)
-        fv = self.Dv * _lap(v, self.dx) + uvv - (self.F + self.k) * v
+        fu = self.Du * _lap(u, self.dx, self.dy) - uvv + self.F * (1.0 - u)
+        fv = self.Dv * _lap(v, self.dx, self.dy) + uvv - (self.F + self.k) * v
         return np.concatenate([fu.reshape(-1), fv.reshape(-1)])
 
     def jv(self, w):
         U, V = self._split(self.state)
         du, dv = self._split(w)
-        ju = self.Du * _lap(du, self.dx) - (V * V + self.F) * du - 2.0 * U * V * dv
-        jvv = self.Dv * _lap(dv, self.dx) + V * V * du + (2.0 * U * V - (self.F + self.k)) * dv
+        ju = self.Du * _lap(du, self.dx, self.dy) - (V * V + self.F) * du - 2.0 * U * V * dv
+        jvv = self.Dv * _lap(dv, self.dx, self.dy) + V * V * du + (2.0 * U * V - (self.F + self.k)) * dv
         return np.concatenate([ju.reshape(-1), jvv.reshape(-1)])
 
 
@@ -77,28 +84,30 @@ class Burgers:
     """2D viscous Burgers u_t = nu lap(u) - u (u_x + u_y)."""
     ncomp = 1
 
-    def __init__(self, n, nu, state=None):
+    def __init__(self, n, nu, state=None, ny=None):
         self.n, self.nu = n, nu
-        self.dx = 1.0 / n
+        self.ny = n if ny is None else ny
+        self.dx, self.dy = 1.0 / n, 1.0 / self.ny
         self.state = state
 
     def f(self, u):
-        U = u.reshape(self.n, self.n)
-        return (self.nu * _lap(U, self.dx) - U * (_ddx(U, self.dx) + _ddy(U, self.dx))).reshape(-1)
+        U = u.reshape(self.ny, self.n)
+        return (self.nu * _lap(U, self.dx, self.dy) - U * (_ddx(U, self.dx) + _ddy(U, self.dy))).reshape(-1)
 
     def jv(self, w):
-        U = self.state.reshape(self.n, self.n)
-        W = w.reshape(self.n, self.n)
-        g = _ddx(U, self.dx) + _ddy(U, self.dx)
-        return (self.nu * _lap(W, self.dx) - W * g - U * (_ddx(W, self.dx) + _ddy(W, self.dx))).reshape(-1)
+        U = self.state.reshape(self.ny, self.n)
+        W = w.reshape(self.ny, self.n)
+        g = _ddx(U, self.dx) + _ddy(U, self.dy)
+        return (self.nu * _lap(W, self.dx, self.dy) - W * g
+                - U * (_ddx(W, self.dx) + _ddy(W, self.dy))).reshape(-1)
 
 
 def with_state(op, state):
     """Copy of a nonlinear operator linearised at `state` (J(u^n), Sec. 1)."""
     if isinstance(op, GrayScott):
-        return GrayScott(op.n, op.Du, op.Dv, op.F, op.k, state)
+        return GrayScott(op.n, op.Du, op.Dv, op.F, op.k, state, ny=op.ny)
     if isinstance(op, Burgers):
-        return Burgers(op.n, op.nu, state)
+        return Burgers(op.n, op.nu, state, ny=op.ny)
     return op
 
 

@@ -1,0 +1,846 @@
+// Iteration kernels of the real-Leja phi-action (Sec. 2.2 of the paper) and
+// of the power iteration that estimates the spectral interval.
+//
+// One launch = one iteration over the whole grid:
+//   MODE_NEWTON: y_m = ((J - c)/gamma - xi_{m-1}) y_{m-1}          (Newton basis)
+//                p_m^(k) = p_{m-1}^(k) + d_k[m] y_m,  k < K          (vertical, Sec. 4)
+//                partial sums of ||y_m||^2 and ||p_m^(k)||^2
+//   MODE_POWER:  y_k = J y_{k-1} / ||y_{k-1}||, partial sums of ||y_k||^2
+// and the last block to finish reduces the partials in block order
+// (deterministic), applies the stop test |d_k[m]| ||y_m|| <= tol ||p_m^(k)||
+// (m >= m_min) or the power-iteration relative-change test, and sets
+// ctl->done.  Every launch first reads ctl->done and returns if set, so a
+// chain of launches stops itself on the device.
+//
+// Layout: planar float64-sized elements (double, or a float2 hi/lo pair),
+// 2D periodic grid, 32 x 8 thread tiles, V = 2 consecutive x points per
+// thread (16-byte loads) when nx is even, grid-stride over tiles.
+#include <cstdio>
+#include <type_traits>
+
+#include "phix_internal.h"
+
+namespace phix {
+
+// ---------------------------------------------------------------------------
+// Precision traits: storage T (one element), vector pair T2, iteration
+// arithmetic C, stencil arithmetic CJ, state storage S, accumulators.
+// ---------------------------------------------------------------------------
+template <int P>
+struct Tr;
+template <>
+struct Tr<P_FP64> {
+  using T = double;
+  using T2 = double2;
+  using C = double;
+  using CJ = double;
+  using S = double;
+  using S2 = double2;
+  using AccN = double;  // Newton norms
+  using AccP = double;  // power-iteration norm (sets the interval: full precision)
+};
+template <>
+struct Tr<P_DF64> {
+  using T = float2;
+  using T2 = float4;
+  using C = df;
+  using CJ = df;
+  using S = float2;
+  using S2 = float4;
+  using AccN = float;
+  using AccP = df;
+};
+template <>
+struct Tr<P_FP32JV> {
+  using T = float2;
+  using T2 = float4;
+  using C = df;
+  using CJ = float;
+  using S = float;
+  using S2 = float2;
+  using AccN = float;
+  using AccP = df;
+};
+template <>
+struct Tr<P_FP32> {
+  using T = float;
+  using T2 = float2;
+  using C = float;
+  using CJ = float;
+  using S = float;
+  using S2 = float2;
+  using AccN = float;
+  using AccP = float;
+};
+
+// ---- element conversions ----------------------------------------------------
+__device__ __forceinline__ double cv(double x) { return x; }
+__device__ __forceinline__ df cv(float2 x) { return df_make(x.x, x.y); }
+__device__ __forceinline__ float cv(float x) { return x; }
+
+__device__ __forceinline__ void st1(double* p, double x) { *p = x; }
+__device__ __forceinline__ void st1(float2* p, df x) { *p = make_float2(x.hi, x.lo); }
+__device__ __forceinline__ void st1(float* p, float x) { *p = x; }
+
+__device__ __forceinline__ void st2(double* p, double a, double b) {
+  *reinterpret_cast<double2*>(p) = make_double2(a, b);
+}
+__device__ __forceinline__ void st2(float2* p, df a, df b) {
+  *reinterpret_cast<float4*>(p) = make_float4(a.hi, a.lo, b.hi, b.lo);
+}
+__device__ __forceinline__ void st2(float* p, float a, float b) {
+  *reinterpret_cast<float2*>(p) = make_float2(a, b);
+}
+
+// read-only loads (y_in, state) through the non-coherent path
+__device__ __forceinline__ double ldr1(const double* p) { return __ldg(p); }
+__device__ __forceinline__ df ldr1(const float2* p) { return cv(__ldg(p)); }
+__device__ __forceinline__ float ldr1(const float* p) { return __ldg(p); }
+__device__ __forceinline__ void ldr2(const double* p, double& a, double& b) {
+  double2 t = __ldg(reinterpret_cast<const double2*>(p));
+  a = t.x;
+  b = t.y;
+}
+__device__ __forceinline__ void ldr2(const float2* p, df& a, df& b) {
+  float4 t = __ldg(reinterpret_cast<const float4*>(p));
+  a = df_make(t.x, t.y);
+  b = df_make(t.z, t.w);
+}
+__device__ __forceinline__ void ldr2(const float* p, float& a, float& b) {
+  float2 t = __ldg(reinterpret_cast<const float2*>(p));
+  a = t.x;
+  b = t.y;
+}
+// read-write loads (accumulators)
+__device__ __forceinline__ double ldw1(const double* p) { return *p; }
+__device__ __forceinline__ df ldw1(const float2* p) { return cv(*p); }
+__device__ __forceinline__ float ldw1(const float* p) { return *p; }
+__device__ __forceinline__ void ldw2(const double* p, double& a, double& b) {
+  double2 t = *reinterpret_cast<const double2*>(p);
+  a = t.x;
+  b = t.y;
+}
+__device__ __forceinline__ void ldw2(const float2* p, df& a, df& b) {
+  float4 t = *reinterpret_cast<const float4*>(p);
+  a = df_make(t.x, t.y);
+  b = df_make(t.z, t.w);
+}
+__device__ __forceinline__ void ldw2(const float* p, float& a, float& b) {
+  float2 t = *reinterpret_cast<const float2*>(p);
+  a = t.x;
+  b = t.y;
+}
+
+// stencil arithmetic from iteration arithmetic and back
+__device__ __forceinline__ double to_cj(double x, double) { return x; }
+__device__ __forceinline__ df to_cj(df x, df) { return x; }
+__device__ __forceinline__ float to_cj(df x, float) { return x.hi; }
+__device__ __forceinline__ float to_cj(float x, float) { return x; }
+__device__ __forceinline__ double from_cj(double x, double) { return x; }
+__device__ __forceinline__ df from_cj(df x, df) { return x; }
+__device__ __forceinline__ df from_cj(float x, df) { return df_make(x, 0.f); }
+__device__ __forceinline__ float from_cj(float x, float) { return x; }
+
+// squares for the norms
+__device__ __forceinline__ void acc_sq(double& a, double x) { a = fma(x, x, a); }
+__device__ __forceinline__ void acc_sq(float& a, df x) { a = fmaf(x.hi, x.hi, a); }
+__device__ __forceinline__ void acc_sq(float& a, float x) { a = fmaf(x, x, a); }
+__device__ __forceinline__ void acc_sq(df& a, df x) { a = df_add(df_mul(x, x), a); }
+
+__device__ __forceinline__ double acc_to_double(double a) { return a; }
+__device__ __forceinline__ double acc_to_double(float a) { return (double)a; }
+__device__ __forceinline__ double acc_to_double(df a) { return (double)a.hi + (double)a.lo; }
+
+__device__ __forceinline__ double shfl_down(double v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ float shfl_down(float v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ df shfl_down(df v, int o) {
+  return df_make(__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o));
+}
+__device__ __forceinline__ double acc_add(double a, double b) { return a + b; }
+__device__ __forceinline__ float acc_add(float a, float b) { return a + b; }
+__device__ __forceinline__ df acc_add(df a, df b) { return df_add(a, b); }
+
+template <typename A>
+__device__ __forceinline__ A acc_zero();
+template <>
+__device__ __forceinline__ double acc_zero<double>() { return 0.0; }
+template <>
+__device__ __forceinline__ float acc_zero<float>() { return 0.f; }
+template <>
+__device__ __forceinline__ df acc_zero<df>() { return df_make(0.f, 0.f); }
+
+// Block reduction of NV accumulators; the block's sums go to partials[blockIdx.x*(KMAX+1) + j]
+// as float64.  Returns true in the block that finished last (all partials visible).
+template <typename A, int NV>
+__device__ bool block_partials_and_last(A (&acc)[NV], double* partials, unsigned int* count) {
+  __shared__ double sred[THREADS / 32][KMAX + 1];
+  __shared__ bool last;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    A v = acc[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = acc_add(v, shfl_down(v, o));
+    if (lane == 0) sred[warp][j] = acc_to_double(v);
+  }
+  __syncthreads();
+  if (tid < NV) {
+    double s = 0.0;
+    for (int w = 0; w < THREADS / 32; ++w) s += sred[w][tid];
+    partials[(size_t)blockIdx.x * (KMAX + 1) + tid] = s;
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    unsigned int t = atomicAdd(count, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  return last;
+}
+
+// Last block: totals[j] = sum over blocks of partials (fixed order).
+template <int NV>
+__device__ void reduce_partials(const double* partials, double (&tot)[NV]) {
+  __shared__ double sfin[THREADS][KMAX + 1];
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  double s[NV];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) s[j] = 0.0;
+  for (int b = tid; b < (int)gridDim.x; b += THREADS) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) s[j] += __ldcg(partials + (size_t)b * (KMAX + 1) + j);
+  }
+#pragma unroll
+  for (int j = 0; j < NV; ++j) sfin[tid][j] = s[j];
+  __syncthreads();
+  for (int w = THREADS / 2; w > 0; w >>= 1) {
+    if (tid < w) {
+#pragma unroll
+      for (int j = 0; j < NV; ++j) sfin[tid][j] += sfin[tid + w][j];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < NV; ++j) tot[j] = sfin[0][j];
+}
+
+// Stop test of the Newton-Leja chain at iteration m (Sec. 2.2).
+__device__ void leja_test(LejaCtl* ctl, int m, int K, int m_min, int m_max, double tol,
+                          const double* dkd, const double* tot) {
+  double ny = sqrt(tot[0]);
+  bool finite = isfinite(ny);
+  bool conv = (m >= m_min);
+  for (int k = 0; k < K; ++k) {
+    double np = sqrt(tot[1 + k]);
+    ctl->pnorm[k] = np;
+    finite = finite && isfinite(np);
+    conv = conv && (fabs(dkd[k]) * ny <= tol * np);
+  }
+  ctl->ynorm = ny;
+  if (!finite) {
+    ctl->status = PHIX_ENAN;
+    ctl->iters = m;
+    ctl->done = 1;
+  } else if (conv) {
+    ctl->status = PHIX_OK;
+    ctl->iters = m;
+    ctl->done = 1;
+  } else if (m >= m_max) {
+    ctl->status = PHIX_ENOTCONV;
+    ctl->iters = m;
+    ctl->done = 1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Stencils.  Each returns J*y at one point in the stencil arithmetic CJ.
+// ---------------------------------------------------------------------------
+template <typename CJ>
+__device__ __forceinline__ CJ stencil_advdiff(const CJ (&k)[8], CJ e, CJ w, CJ n, CJ s, CJ c) {
+  return k[0] * e + k[1] * w + k[2] * n + k[3] * s + k[4] * c;
+}
+
+// GS species u: ku = {x, y, C}; returns J_u, J_v together.
+template <typename CJ>
+__device__ __forceinline__ void stencil_gs(const CJ (&k)[8], CJ ga, CJ ue, CJ uw, CJ un, CJ us, CJ uc,
+                                           CJ ve, CJ vw, CJ vn, CJ vs, CJ vc, CJ g1, CJ g2, CJ& ju,
+                                           CJ& jv) {
+  CJ a1 = ga * g1;
+  CJ a2 = ga * g2;
+  ju = k[0] * (ue + uw) + k[1] * (un + us) + (k[2] - a1) * uc - a2 * vc;
+  jv = k[3] * (ve + vw) + k[4] * (vn + vs) + a1 * uc + (k[5] + a2) * vc;
+}
+
+template <typename CJ>
+__device__ __forceinline__ CJ stencil_burgers(const CJ (&k)[8], CJ ga, CJ e, CJ w, CJ n, CJ s, CJ c,
+                                              CJ Ue, CJ Uw, CJ Un, CJ Us, CJ Uc) {
+  // nu lap y - (U_x + U_y) y - U (y_x + y_y), all centred
+  CJ divU = k[3] * (Ue - Uw) + k[4] * (Un - Us);
+  CJ dy = k[3] * (e - w) + k[4] * (n - s);
+  return k[0] * (e + w) + k[1] * (n + s) + k[2] * c - ga * (divU * c + Uc * dy);
+}
+
+// ---------------------------------------------------------------------------
+// The iteration kernel.
+// ---------------------------------------------------------------------------
+template <int P, int OP, int V, int MODE>
+__global__ void __launch_bounds__(THREADS)
+    k_iter(IterArgs<typename Tr<P>::CJ, typename Tr<P>::C> a) {
+  using T = typename Tr<P>::T;
+  using C = typename Tr<P>::C;
+  using CJ = typename Tr<P>::CJ;
+  using S = typename Tr<P>::S;
+  using Acc = typename std::conditional<MODE == MODE_NEWTON, typename Tr<P>::AccN,
+                                        typename Tr<P>::AccP>::type;
+  constexpr int NC = (OP == PHIX_OP_GRAYSCOTT) ? 2 : 1;
+
+  if (__ldcg(&a.ctl->done)) return;  // the chain already stopped
+
+  C alpha_pw{};
+  if (MODE == MODE_POWER) {
+    if constexpr (P == P_FP64) {
+      alpha_pw = __ldcg(&a.ctl->alpha);
+    } else if constexpr (P == P_FP32) {
+      alpha_pw = __ldcg(&a.ctl->alpha_hi);
+    } else {
+      alpha_pw = df_make(__ldcg(&a.ctl->alpha_hi), __ldcg(&a.ctl->alpha_lo));
+    }
+  }
+
+  Acc acc[KMAX + 1];
+#pragma unroll
+  for (int j = 0; j <= KMAX; ++j) acc[j] = acc_zero<Acc>();
+
+  const T* __restrict__ yin = static_cast<const T*>(a.y_in);
+  T* __restrict__ yout = static_cast<T*>(a.y_out);
+  const S* __restrict__ st = static_cast<const S*>(a.st);
+  const int nx = a.nx, ny = a.ny;
+  const size_t plane = (size_t)nx * ny;
+  CJ kk[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) kk[j] = a.k[j];
+
+  for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+    const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+    const int iy = ty * TILE_Y + threadIdx.y;
+    const int ix = (tx * 32 + threadIdx.x) * V;
+    if (iy >= ny || ix >= nx) continue;
+    const int iym = iy == 0 ? ny - 1 : iy - 1;
+    const int iyp = iy == ny - 1 ? 0 : iy + 1;
+    const int ixm = ix == 0 ? nx - 1 : ix - 1;
+    const int ixp = (ix + V == nx) ? 0 : ix + V;
+    const size_t row = (size_t)iy * nx, rowp = (size_t)iyp * nx, rowm = (size_t)iym * nx;
+
+    // load y (both species for GS): centre pair, north/south pairs, west/east
+    C c[NC][V], nn[NC][V], ss[NC][V], we[NC], ea[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      const T* b = yin + q * plane;
+      if constexpr (V == 2) {
+        ldr2(b + row + ix, c[q][0], c[q][1]);
+        ldr2(b + rowp + ix, nn[q][0], nn[q][1]);
+        ldr2(b + rowm + ix, ss[q][0], ss[q][1]);
+      } else {
+        c[q][0] = ldr1(b + row + ix);
+        nn[q][0] = ldr1(b + rowp + ix);
+        ss[q][0] = ldr1(b + rowm + ix);
+      }
+      we[q] = ldr1(b + row + ixm);
+      ea[q] = ldr1(b + row + ixp);
+    }
+
+    C out[NC][V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      // neighbours of point ix+v
+      CJ J[NC];
+      if constexpr (OP == PHIX_OP_ADVDIFF) {
+        C e = (v == V - 1) ? ea[0] : c[0][v + 1];
+        C w = (v == 0) ? we[0] : c[0][v - 1];
+        J[0] = stencil_advdiff<CJ>(kk, to_cj(e, CJ()), to_cj(w, CJ()), to_cj(nn[0][v], CJ()),
+                                   to_cj(ss[0][v], CJ()), to_cj(c[0][v], CJ()));
+      } else if constexpr (OP == PHIX_OP_GRAYSCOTT) {
+        C eu = (v == V - 1) ? ea[0] : c[0][v + 1];
+        C wu = (v == 0) ? we[0] : c[0][v - 1];
+        C ev = (v == V - 1) ? ea[NC - 1] : c[NC - 1][v + 1];
+        C wv = (v == 0) ? we[NC - 1] : c[NC - 1][v - 1];
+        CJ g1 = to_cj(cv(__ldg(st + row + ix + v)), CJ());
+        CJ g2 = to_cj(cv(__ldg(st + plane + row + ix + v)), CJ());
+        stencil_gs<CJ>(kk, a.ga, to_cj(eu, CJ()), to_cj(wu, CJ()), to_cj(nn[0][v], CJ()),
+                       to_cj(ss[0][v], CJ()), to_cj(c[0][v], CJ()), to_cj(ev, CJ()),
+                       to_cj(wv, CJ()), to_cj(nn[NC - 1][v], CJ()), to_cj(ss[NC - 1][v], CJ()),
+                       to_cj(c[NC - 1][v], CJ()), g1, g2, J[0], J[NC - 1]);
+      } else {
+        C e = (v == V - 1) ? ea[0] : c[0][v + 1];
+        C w = (v == 0) ? we[0] : c[0][v - 1];
+        const int vx = ix + v;
+        const int vxm = (v == 0) ? ixm : vx - 1;
+        const int vxp = (v == V - 1) ? ixp : vx + 1;
+        CJ Uc = to_cj(cv(__ldg(st + row + vx)), CJ());
+        CJ Ue = to_cj(cv(__ldg(st + row + vxp)), CJ());
+        CJ Uw = to_cj(cv(__ldg(st + row + vxm)), CJ());
+        CJ Un = to_cj(cv(__ldg(st + rowp + vx)), CJ());
+        CJ Us = to_cj(cv(__ldg(st + rowm + vx)), CJ());
+        J[0] = stencil_burgers<CJ>(kk, a.ga, to_cj(e, CJ()), to_cj(w, CJ()), to_cj(nn[0][v], CJ()),
+                                   to_cj(ss[0][v], CJ()), to_cj(c[0][v], CJ()), Ue, Uw, Un, Us, Uc);
+      }
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        if (MODE == MODE_NEWTON) {
+          out[q][v] = from_cj(J[q], C()) + a.beta * c[q][v];
+        } else {
+          out[q][v] = alpha_pw * from_cj(J[q], C());
+        }
+      }
+    }
+
+    // store y, accumulate p_k, norms
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      T* yo = yout + q * plane + row + ix;
+      if constexpr (V == 2) {
+        st2(yo, out[q][0], out[q][1]);
+      } else {
+        st1(yo, out[q][0]);
+      }
+#pragma unroll
+      for (int v = 0; v < V; ++v) acc_sq(acc[0], out[q][v]);
+      if (MODE == MODE_NEWTON) {
+#pragma unroll
+        for (int kq = 0; kq < KMAX; ++kq) {
+          if (kq < a.K) {
+            T* pp = static_cast<T*>(a.p[kq]) + q * plane + row + ix;
+            C p0, p1;
+            if constexpr (V == 2) {
+              ldw2(pp, p0, p1);
+              p0 = p0 + a.dk[kq] * out[q][0];
+              p1 = p1 + a.dk[kq] * out[q][1];
+              st2(pp, p0, p1);
+              acc_sq(acc[1 + kq], p0);
+              acc_sq(acc[1 + kq], p1);
+            } else {
+              p0 = ldw1(pp);
+              p0 = p0 + a.dk[kq] * out[q][0];
+              st1(pp, p0);
+              acc_sq(acc[1 + kq], p0);
+            }
+          }
+        }
+      }
+    }
+  }
+
+  if (block_partials_and_last<Acc, KMAX + 1>(acc, a.partials, &a.ctl->count)) {
+    double tot[KMAX + 1];
+    reduce_partials<KMAX + 1>(a.partials, tot);
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    if (tid == 0) {
+      LejaCtl* ctl = a.ctl;
+      if (MODE == MODE_NEWTON) {
+        leja_test(ctl, a.m, a.K, a.m_min, a.m_max, a.tol, a.dkd, tot);
+      } else {
+        // power iteration: y_k = J v_{k-1}, v_{k-1} unit  =>  rho_k = ||y_k||
+        double rho = sqrt(tot[0]);
+        double prev = ctl->rho;
+        ctl->rho_prev = prev;
+        ctl->rho = rho;
+        ctl->iters = a.m;
+        if (!isfinite(rho)) {
+          ctl->status = PHIX_ENAN;
+          ctl->done = 1;
+        } else if (rho == 0.0) {
+          ctl->status = PHIX_OK;
+          ctl->done = 1;
+        } else if ((a.m >= 2 && fabs(rho - prev) <= a.rel * rho) || a.m >= a.m_max) {
+          ctl->status = PHIX_OK;
+          ctl->done = 1;
+        }
+        double al = 1.0 / rho;
+        ctl->alpha = al;
+        float ah = (float)al;
+        ctl->alpha_hi = ah;
+        ctl->alpha_lo = (float)(al - (double)ah);
+      }
+      ctl->count = 0;
+      __threadfence();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// init: y0 = v / sigma, p_k = d_k[0] y0, norms, test at m = 0
+// ---------------------------------------------------------------------------
+template <int P>
+__global__ void __launch_bounds__(THREADS)
+    k_init(const double* __restrict__ v, typename Tr<P>::T* __restrict__ y0, IterArgs<typename Tr<P>::CJ, typename Tr<P>::C> a, size_t n) {
+  using T = typename Tr<P>::T;
+  using C = typename Tr<P>::C;
+  using Acc = typename Tr<P>::AccN;
+  Acc acc[KMAX + 1];
+#pragma unroll
+  for (int j = 0; j <= KMAX; ++j) acc[j] = acc_zero<Acc>();
+  const double is = __ldcg(&a.ctl->inv_sigma);
+  const size_t stride = (size_t)gridDim.x * THREADS;
+  for (size_t i = (size_t)blockIdx.x * THREADS + threadIdx.y * 32 + threadIdx.x; i < n; i += stride) {
+    double x = v[i] * is;
+    C y;
+    if constexpr (P == P_FP64) {
+      y = x;
+      y0[i] = x;
+    } else if constexpr (P == P_FP32) {
+      y = (float)x;
+      y0[i] = y;
+    } else {
+      y = df_from_double(x);
+      y0[i] = make_float2(y.hi, y.lo);
+    }
+    acc_sq(acc[0], y);
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+      if (k < a.K) {
+        C p = a.dk[k] * y;
+        st1(static_cast<T*>(a.p[k]) + i, p);
+        acc_sq(acc[1 + k], p);
+      }
+    }
+  }
+  if (block_partials_and_last<Acc, KMAX + 1>(acc, a.partials, &a.ctl->count)) {
+    double tot[KMAX + 1];
+    reduce_partials<KMAX + 1>(a.partials, tot);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      if (!a.ctl->done) leja_test(a.ctl, 0, a.K, a.m_min, a.m_max, a.tol, a.dkd, tot);
+      a.ctl->count = 0;
+      __threadfence();
+    }
+  }
+}
+
+// sigma = 2^round(log2(rms(v))); ENAN on a non-finite input
+__global__ void __launch_bounds__(THREADS)
+    k_scale(const double* __restrict__ v, size_t n, LejaCtl* ctl, double* partials) {
+  double acc[1] = {0.0};
+  const size_t stride = (size_t)gridDim.x * THREADS;
+  for (size_t i = (size_t)blockIdx.x * THREADS + threadIdx.y * 32 + threadIdx.x; i < n; i += stride) {
+    double x = v[i];
+    acc[0] = fma(x, x, acc[0]);
+  }
+  if (block_partials_and_last<double, 1>(acc, partials, &ctl->count)) {
+    double tot[1];
+    reduce_partials<1>(partials, tot);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      double s = tot[0];
+      double sig = 1.0;
+      if (!isfinite(s)) {
+        ctl->status = PHIX_ENAN;
+        ctl->done = 1;
+      } else if (s > 0.0) {
+        double rms = sqrt(s / (double)n);
+        int e = (int)rint(log2(rms));
+        sig = ldexp(1.0, e);
+      }
+      ctl->sigma = sig;
+      ctl->inv_sigma = 1.0 / sig;
+      ctl->count = 0;
+      __threadfence();
+    }
+  }
+}
+
+template <int P>
+__global__ void __launch_bounds__(THREADS) k_finalize(size_t n, int K, PtrPack pk, const LejaCtl* ctl) {
+  using T = typename Tr<P>::T;
+  const double s = __ldcg(&ctl->sigma);
+  const size_t stride = (size_t)gridDim.x * THREADS;
+  for (int k = 0; k < K; ++k) {
+    const T* p = static_cast<const T*>(pk.p[k]);
+    double* o = pk.o[k];
+    for (size_t i = (size_t)blockIdx.x * THREADS + threadIdx.y * 32 + threadIdx.x; i < n; i += stride) {
+      T x = p[i];
+      double d;
+      if constexpr (P == P_FP64) {
+        d = x;
+      } else if constexpr (P == P_FP32) {
+        d = (double)x;
+      } else {
+        d = (double)x.x + (double)x.y;
+      }
+      o[i] = s * d;
+    }
+  }
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014): x_i = seed + (i+1)*golden; 64-bit finaliser.
+__device__ __forceinline__ double splitmix_uniform(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z = z ^ (z >> 31);
+  return (double)(z >> 11) * 0x1.0p-53 - 0.5;
+}
+
+template <int P>
+__global__ void __launch_bounds__(THREADS)
+    k_power_start(size_t n, uint64_t seed, typename Tr<P>::T* __restrict__ y0, LejaCtl* ctl, double* partials) {
+  using C = typename Tr<P>::C;
+  using Acc = typename Tr<P>::AccP;
+  Acc acc[1] = {acc_zero<Acc>()};
+  const size_t stride = (size_t)gridDim.x * THREADS;
+  for (size_t i = (size_t)blockIdx.x * THREADS + threadIdx.y * 32 + threadIdx.x; i < n; i += stride) {
+    double x = splitmix_uniform(seed, i);
+    C y;
+    if constexpr (P == P_FP64) {
+      y = x;
+      y0[i] = x;
+    } else if constexpr (P == P_FP32) {
+      y = (float)x;
+      y0[i] = y;
+    } else {
+      y = df_from_double(x);
+      y0[i] = make_float2(y.hi, y.lo);
+    }
+    acc_sq(acc[0], y);
+  }
+  if (block_partials_and_last<Acc, 1>(acc, partials, &ctl->count)) {
+    double tot[1];
+    reduce_partials<1>(partials, tot);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      double al = 1.0 / sqrt(tot[0]);
+      ctl->alpha = al;
+      float ah = (float)al;
+      ctl->alpha_hi = ah;
+      ctl->alpha_lo = (float)(al - (double)ah);
+      ctl->rho = 0.0;
+      ctl->count = 0;
+      __threadfence();
+    }
+  }
+}
+
+// GS: st = [V^2, 2UV]; Burgers: st = [U]; computed in float64 then stored in S.
+template <int P>
+__global__ void __launch_bounds__(THREADS)
+    k_prep_state(int op, size_t plane, const double* __restrict__ state, typename Tr<P>::S* __restrict__ st) {
+  using S = typename Tr<P>::S;
+  const size_t stride = (size_t)gridDim.x * THREADS;
+  for (size_t i = (size_t)blockIdx.x * THREADS + threadIdx.y * 32 + threadIdx.x; i < plane; i += stride) {
+    double g[2];
+    int ng = 1;
+    if (op == PHIX_OP_GRAYSCOTT) {
+      double U = state[i], Vv = state[plane + i];
+      g[0] = Vv * Vv;
+      g[1] = 2.0 * U * Vv;
+      ng = 2;
+    } else {
+      g[0] = state[i];
+    }
+    for (int j = 0; j < ng; ++j) {
+      S s;
+      if constexpr (P == P_FP64) {
+        s = g[j];
+      } else if constexpr (P == P_DF64) {
+        df d = df_from_double(g[j]);
+        s = make_float2(d.hi, d.lo);
+      } else {
+        s = (float)g[j];
+      }
+      st[j * plane + i] = s;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------
+static inline double to_c(double x, double) { return x; }
+static inline df to_c(double x, df) { return df_from_double(x); }
+static inline float to_c(double x, float) { return (float)x; }
+
+template <int P>
+static IterArgs<typename Tr<P>::CJ, typename Tr<P>::C> make_args(const IterLaunch& L) {
+  using C = typename Tr<P>::C;
+  using CJ = typename Tr<P>::CJ;
+  IterArgs<CJ, C> a;
+  a.y_in = L.y_in;
+  a.y_out = L.y_out;
+  for (int k = 0; k < KMAX; ++k) {
+    a.p[k] = L.p[k];
+    a.dkd[k] = L.dk[k];
+    a.dk[k] = to_c(L.dk[k], C());
+  }
+  a.st = L.st;
+  a.ctl = L.ctl;
+  a.partials = L.partials;
+  a.nx = L.nx;
+  a.ny = L.ny;
+  a.K = L.K;
+  a.m = L.m;
+  a.m_min = L.m_min;
+  a.m_max = L.m_max;
+  a.tol = L.tol;
+  a.rel = L.rel;
+  for (int j = 0; j < 8; ++j) a.k[j] = to_c(L.k[j], CJ());
+  a.ga = to_c(L.ga, CJ());
+  a.beta = to_c(L.beta, C());
+  return a;
+}
+
+template <int P, int OP, int MODE>
+static cudaError_t launch_iter_t(const IterLaunch& L, cudaStream_t s) {
+  auto a = make_args<P>(L);
+  const bool vec = (L.nx % 2 == 0);
+  const int V = vec ? 2 : 1;
+  a.tiles_x = (L.nx / V + 31) / 32;
+  a.ntiles = a.tiles_x * ((L.ny + TILE_Y - 1) / TILE_Y);
+  int grid = L.grid < a.ntiles ? L.grid : a.ntiles;
+  dim3 blk(32, TILE_Y);
+  if (vec)
+    k_iter<P, OP, 2, MODE><<<grid, blk, 0, s>>>(a);
+  else
+    k_iter<P, OP, 1, MODE><<<grid, blk, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int P, int MODE>
+static cudaError_t launch_iter_op(const IterLaunch& L, cudaStream_t s) {
+  switch (L.op) {
+    case PHIX_OP_ADVDIFF:
+      return launch_iter_t<P, PHIX_OP_ADVDIFF, MODE>(L, s);
+    case PHIX_OP_GRAYSCOTT:
+      return launch_iter_t<P, PHIX_OP_GRAYSCOTT, MODE>(L, s);
+    case PHIX_OP_BURGERS:
+      return launch_iter_t<P, PHIX_OP_BURGERS, MODE>(L, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int P>
+static cudaError_t launch_iter_mode(const IterLaunch& L, cudaStream_t s) {
+  return L.mode == MODE_NEWTON ? launch_iter_op<P, MODE_NEWTON>(L, s)
+                               : launch_iter_op<P, MODE_POWER>(L, s);
+}
+
+cudaError_t launch_iter(const IterLaunch& L, cudaStream_t s) {
+  switch (L.prec) {
+    case P_FP64:
+      return launch_iter_mode<P_FP64>(L, s);
+    case P_DF64:
+      return launch_iter_mode<P_DF64>(L, s);
+    case P_FP32JV:
+      return launch_iter_mode<P_FP32JV>(L, s);
+    case P_FP32:
+      return launch_iter_mode<P_FP32>(L, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int P>
+static cudaError_t launch_init_t(const InitLaunch& L, cudaStream_t s) {
+  IterLaunch IL{};
+  IL.K = L.K;
+  IL.m_min = L.m_min;
+  IL.m_max = L.m_max;
+  IL.ctl = L.ctl;
+  IL.partials = L.partials;
+  IL.tol = L.tol;
+  for (int k = 0; k < KMAX; ++k) {
+    IL.p[k] = L.p[k];
+    IL.dk[k] = L.dk[k];
+  }
+  auto a = make_args<P>(IL);
+  size_t n = (size_t)L.ncomp * L.nx * L.ny;
+  k_init<P><<<L.grid, dim3(32, TILE_Y), 0, s>>>(L.v, static_cast<typename Tr<P>::T*>(L.y0), a, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init(const InitLaunch& L, cudaStream_t s) {
+  switch (L.prec) {
+    case P_FP64:
+      return launch_init_t<P_FP64>(L, s);
+    case P_DF64:
+      return launch_init_t<P_DF64>(L, s);
+    case P_FP32JV:
+      return launch_init_t<P_FP32JV>(L, s);
+    case P_FP32:
+      return launch_init_t<P_FP32>(L, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_scale(const double* v, size_t n, LejaCtl* ctl, double* partials, int grid,
+                         cudaStream_t s) {
+  k_scale<<<grid, dim3(32, TILE_Y), 0, s>>>(v, n, ctl, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(int prec, size_t n, int K, void* const* p, double* const* out,
+                            const LejaCtl* ctl, int grid, cudaStream_t s) {
+  PtrPack pk{};
+  for (int k = 0; k < K && k < KMAX; ++k) {
+    pk.p[k] = p[k];
+    pk.o[k] = out[k];
+  }
+  switch (prec) {
+    case P_FP64:
+      k_finalize<P_FP64><<<grid, dim3(32, TILE_Y), 0, s>>>(n, K, pk, ctl);
+      break;
+    case P_DF64:
+    case P_FP32JV:
+      k_finalize<P_DF64><<<grid, dim3(32, TILE_Y), 0, s>>>(n, K, pk, ctl);
+      break;
+    case P_FP32:
+      k_finalize<P_FP32><<<grid, dim3(32, TILE_Y), 0, s>>>(n, K, pk, ctl);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_power_start(int prec, size_t n, uint64_t seed, void* y0, LejaCtl* ctl,
+                               double* partials, int grid, cudaStream_t s) {
+  dim3 b(32, TILE_Y);
+  switch (prec) {
+    case P_FP64:
+      k_power_start<P_FP64><<<grid, b, 0, s>>>(n, seed, static_cast<double*>(y0), ctl, partials);
+      break;
+    case P_DF64:
+      k_power_start<P_DF64><<<grid, b, 0, s>>>(n, seed, static_cast<float2*>(y0), ctl, partials);
+      break;
+    case P_FP32JV:
+      k_power_start<P_FP32JV><<<grid, b, 0, s>>>(n, seed, static_cast<float2*>(y0), ctl, partials);
+      break;
+    case P_FP32:
+      k_power_start<P_FP32><<<grid, b, 0, s>>>(n, seed, static_cast<float*>(y0), ctl, partials);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prep_state(int prec, int op, int nx, int ny, const double* state, void* st,
+                              int grid, cudaStream_t s) {
+  size_t plane = (size_t)nx * ny;
+  dim3 b(32, TILE_Y);
+  switch (prec) {
+    case P_FP64:
+      k_prep_state<P_FP64><<<grid, b, 0, s>>>(op, plane, state, static_cast<double*>(st));
+      break;
+    case P_DF64:
+      k_prep_state<P_DF64><<<grid, b, 0, s>>>(op, plane, state, static_cast<float2*>(st));
+      break;
+    case P_FP32JV:
+      k_prep_state<P_FP32JV><<<grid, b, 0, s>>>(op, plane, state, static_cast<float*>(st));
+      break;
+    case P_FP32:
+      k_prep_state<P_FP32><<<grid, b, 0, s>>>(op, plane, state, static_cast<float*>(st));
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace phix

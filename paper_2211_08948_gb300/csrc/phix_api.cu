@@ -1,0 +1,782 @@
+// Host driver and C-ABI entry points of libphix (declared in include/phix.h).
+//
+// A phi-action call: validate -> Jacobian state arrays -> spectral interval
+// (caller value or power iteration, Sec. 2.2) -> divided-difference tables
+// (host, float64) -> chains of Newton-Leja launches that stop themselves on
+// the device (the host polls one small control block per chunk) -> outputs
+// scaled back to float64.  EXPRB43 / EPIRK4s3 steps chain these actions with
+// float64 stage kernels.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "phix_internal.h"
+
+using namespace phix;
+
+namespace {
+
+enum Slot {
+  S_Y0 = 0, S_Y1, S_P0, S_P1, S_P2, S_P3, S_ST,                 // Newton pass
+  S_F, S_A, S_B, S_RA, S_RB, S_T0, S_Q, S_T3, S_T4, S_O1, S_O2, S_O3,  // stages
+  S_SUB_U, S_SUB_TMP, S_SUB_W0,                                  // substeps (W0..W0+8)
+  S_NSLOT = S_SUB_W0 + 9
+};
+
+}  // namespace
+
+struct phix_ctx {
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int nsm = 1;
+  int grid_iter = 1;
+  int grid_stream = 1;
+  std::string err;
+  void* buf[S_NSLOT] = {};
+  size_t cap[S_NSLOT] = {};
+  LejaCtl* ctl = nullptr;        // device
+  LejaCtl* ctl_h = nullptr;      // pinned host mirror
+  double* partials = nullptr;    // device, grid_iter * (KMAX+1)
+  double* scal = nullptr;        // device scalars (norms)
+  double* scal_h = nullptr;      // pinned
+  unsigned int* counter = nullptr;
+  long launches = 0;
+  std::vector<cudaEvent_t> ev;   // profiling: event pairs per iteration launch
+};
+
+namespace {
+
+struct Fail {
+  phix_status st;
+};
+
+void set_err(phix_ctx* c, const char* fmt, ...) {
+  char b[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(b, sizeof b, fmt, ap);
+  va_end(ap);
+  c->err = b;
+}
+
+#define CK(call)                                                                  \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess) {                                                      \
+      set_err(ctx, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+      throw Fail{PHIX_ECUDA};                                                     \
+    }                                                                             \
+  } while (0)
+
+#define KL(call)          \
+  do {                    \
+    ctx->launches++;      \
+    CK(call);             \
+  } while (0)
+
+[[noreturn]] void fail(phix_ctx* ctx, phix_status st, const char* fmt, ...) {
+  char b[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(b, sizeof b, fmt, ap);
+  va_end(ap);
+  ctx->err = b;
+  throw Fail{st};
+}
+
+void* ws(phix_ctx* ctx, int slot, size_t bytes) {
+  if (ctx->cap[slot] < bytes) {
+    if (ctx->buf[slot]) {
+      CK(cudaStreamSynchronize(ctx->stream));
+      CK(cudaFree(ctx->buf[slot]));
+      ctx->buf[slot] = nullptr;
+      ctx->cap[slot] = 0;
+    }
+    cudaError_t e = cudaMalloc(&ctx->buf[slot], bytes);
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      fail(ctx, PHIX_ENOMEM, "workspace allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    }
+    ctx->cap[slot] = bytes;
+  }
+  return ctx->buf[slot];
+}
+double* wsd(phix_ctx* ctx, int slot, size_t n) { return static_cast<double*>(ws(ctx, slot, n * sizeof(double))); }
+
+int ncomp_of(int kind) { return kind == PHIX_OP_GRAYSCOTT ? 2 : 1; }
+
+size_t elem_bytes(int prec) { return prec == P_FP32 ? 4 : 8; }
+
+// Validated operator + its per-point state arrays in the iteration precision.
+struct OpState {
+  OpDesc d;
+  int ncomp;
+  size_t plane, N;
+  const double* state;  // float64 state (caller memory)
+  const void* st;       // prepared state arrays (workspace)
+  double kJ[8];         // unscaled uniform J coefficients
+};
+
+void check_op(phix_ctx* ctx, const phix_jop* op, bool need_state) {
+  if (!op) fail(ctx, PHIX_EINVAL, "op is NULL");
+  if (op->kind < 0 || op->kind > 2) fail(ctx, PHIX_EINVAL, "unknown operator kind %d", op->kind);
+  if (op->nx < 3 || op->ny < 3) fail(ctx, PHIX_EINVAL, "grid %dx%d too small (>= 3 required)", op->nx, op->ny);
+  if ((size_t)op->nx * op->ny > ((size_t)1 << 31)) fail(ctx, PHIX_EINVAL, "grid too large");
+  if (need_state && op->kind != PHIX_OP_ADVDIFF && !op->state)
+    fail(ctx, PHIX_EINVAL, "operator kind %d needs a state vector", op->kind);
+}
+
+OpState make_opstate(phix_ctx* ctx, const phix_jop* op, const double* state, int prec) {
+  OpState s{};
+  s.d.kind = op->kind;
+  s.d.nx = op->nx;
+  s.d.ny = op->ny;
+  for (int i = 0; i < 8; ++i) s.d.p[i] = op->param[i];
+  s.ncomp = ncomp_of(op->kind);
+  s.plane = (size_t)op->nx * op->ny;
+  s.N = s.plane * s.ncomp;
+  s.state = state;
+  const double idx2 = (double)op->nx * op->nx, idy2 = (double)op->ny * op->ny;
+  const double* p = op->param;
+  for (double& k : s.kJ) k = 0.0;
+  if (op->kind == PHIX_OP_ADVDIFF) {
+    s.kJ[0] = p[0] * idx2 + 0.5 * p[1] * op->nx;  // E
+    s.kJ[1] = p[0] * idx2 - 0.5 * p[1] * op->nx;  // W
+    s.kJ[2] = p[0] * idy2 + 0.5 * p[2] * op->ny;  // N (y + 1)
+    s.kJ[3] = p[0] * idy2 - 0.5 * p[2] * op->ny;  // S
+    s.kJ[4] = -2.0 * p[0] * (idx2 + idy2);        // C
+  } else if (op->kind == PHIX_OP_GRAYSCOTT) {
+    s.kJ[0] = p[0] * idx2;
+    s.kJ[1] = p[0] * idy2;
+    s.kJ[2] = -2.0 * p[0] * (idx2 + idy2) - p[2];
+    s.kJ[3] = p[1] * idx2;
+    s.kJ[4] = p[1] * idy2;
+    s.kJ[5] = -2.0 * p[1] * (idx2 + idy2) - (p[2] + p[3]);
+  } else {
+    s.kJ[0] = p[0] * idx2;
+    s.kJ[1] = p[0] * idy2;
+    s.kJ[2] = -2.0 * p[0] * (idx2 + idy2);
+    s.kJ[3] = 0.5 * op->nx;
+    s.kJ[4] = 0.5 * op->ny;
+  }
+  s.st = nullptr;
+  if (op->kind != PHIX_OP_ADVDIFF) {
+    size_t nplanes = op->kind == PHIX_OP_GRAYSCOTT ? 2 : 1;
+    size_t sb = prec == P_FP64 || prec == P_DF64 ? 8 : 4;
+    void* st = ws(ctx, S_ST, nplanes * s.plane * sb);
+    KL(launch_prep_state(prec, op->kind, op->nx, op->ny, state, st, ctx->grid_stream, ctx->stream));
+    s.st = st;
+  }
+  return s;
+}
+
+// number of scalar uniform coefficients that alpha scales
+int n_scaled(int kind) { return kind == PHIX_OP_ADVDIFF ? 5 : (kind == PHIX_OP_GRAYSCOTT ? 6 : 3); }
+
+void read_ctl(phix_ctx* ctx) {
+  CK(cudaMemcpyAsync(ctx->ctl_h, ctx->ctl, sizeof(LejaCtl), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+}
+
+struct PassResult {
+  int iters;
+  int status;
+  int launches = 0;   // profiled work launches
+  double ms = 0.0;    // their device time
+  double bytes = 0.0; // their algorithmic bytes
+};
+
+void ensure_events(phix_ctx* ctx, size_t n) {
+  while (ctx->ev.size() < n) {
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    ctx->ev.push_back(e);
+  }
+}
+
+// One Newton-Leja pass (Sec. 2.2): out[k] = sum_m d_k[m] y_m, y_0 = v,
+// y_{m+1} = ((J - c)/gamma - xi_m) y_m, stop at |d_k[m]| ||y_m|| <= tol ||p_k||.
+PassResult leja_pass(phix_ctx* ctx, const OpState& os, int prec, const double* v, int K,
+                     const std::vector<std::vector<double>>& d, double c, double gamma, double tol,
+                     const phix_opts& o, double* const* out) {
+  const int m_max = o.m_max;
+  const double* xi = leja_table(m_max + 1);
+  const size_t eb = elem_bytes(prec);
+  void* y[2] = {ws(ctx, S_Y0, os.N * eb), ws(ctx, S_Y1, os.N * eb)};
+  void* p[KMAX] = {};
+  for (int k = 0; k < K; ++k) p[k] = ws(ctx, S_P0 + k, os.N * eb);
+
+  CK(cudaMemsetAsync(ctx->ctl, 0, sizeof(LejaCtl), ctx->stream));
+  KL(launch_scale(v, os.N, ctx->ctl, ctx->partials, ctx->grid_iter, ctx->stream));
+  InitLaunch IL{};
+  IL.prec = prec;
+  IL.ncomp = os.ncomp;
+  IL.K = K;
+  IL.m_min = o.m_min;
+  IL.m_max = m_max;
+  IL.nx = os.d.nx;
+  IL.ny = os.d.ny;
+  IL.v = v;
+  IL.y0 = y[0];
+  for (int k = 0; k < K; ++k) {
+    IL.p[k] = p[k];
+    IL.dk[k] = d[k][0];
+  }
+  IL.ctl = ctx->ctl;
+  IL.partials = ctx->partials;
+  IL.tol = tol;
+  IL.grid = ctx->grid_iter;
+  KL(launch_init(IL, ctx->stream));
+
+  // predicted length: first m >= m_min where every |d_k[m]| <= tol |d_k[0]| / 2
+  int m_pred = m_max;
+  for (int m = std::max(1, o.m_min); m <= m_max; ++m) {
+    bool ok = true;
+    for (int k = 0; k < K; ++k) ok = ok && std::fabs(d[k][m]) <= 0.5 * tol * std::fabs(d[k][0]);
+    if (ok) {
+      m_pred = m;
+      break;
+    }
+  }
+  const double alpha = 1.0 / gamma;
+  IterLaunch L{};
+  L.prec = prec;
+  L.op = os.d.kind;
+  L.mode = MODE_NEWTON;
+  L.K = K;
+  L.m_min = o.m_min;
+  L.m_max = m_max;
+  L.nx = os.d.nx;
+  L.ny = os.d.ny;
+  for (int k = 0; k < K; ++k) L.p[k] = p[k];
+  L.st = os.st;
+  L.ctl = ctx->ctl;
+  L.partials = ctx->partials;
+  L.tol = tol;
+  L.grid = ctx->grid_iter;
+  const int ns = n_scaled(os.d.kind);
+  for (int j = 0; j < 8; ++j) L.k[j] = j < ns ? alpha * os.kJ[j] : os.kJ[j];
+  L.ga = alpha;
+
+  int launched = 0;  // last m launched
+  int target = std::min(m_max, m_pred + 2);
+  if (o.profile) ensure_events(ctx, 2 * (m_max + 1));
+  for (;;) {
+    for (int m = launched + 1; m <= target; ++m) {
+      L.m = m;
+      L.y_in = y[(m - 1) & 1];
+      L.y_out = y[m & 1];
+      L.beta = -(c / gamma + xi[m - 1]);
+      for (int k = 0; k < K; ++k) L.dk[k] = d[k][m];
+      if (o.profile) CK(cudaEventRecord(ctx->ev[2 * m], ctx->stream));
+      KL(launch_iter(L, ctx->stream));
+      if (o.profile) CK(cudaEventRecord(ctx->ev[2 * m + 1], ctx->stream));
+    }
+    launched = target;
+    read_ctl(ctx);
+    if (ctx->ctl_h->done || launched >= m_max) break;
+    target = std::min(m_max, launched + 8);
+  }
+  KL(launch_finalize(prec, os.N, K, p, out, ctx->ctl, ctx->grid_stream, ctx->stream));
+  PassResult r;
+  r.iters = ctx->ctl_h->iters;
+  r.status = ctx->ctl_h->done ? ctx->ctl_h->status : PHIX_ENOTCONV;
+  r.ms = 0.0;
+  r.bytes = 0.0;
+  if (o.profile) {
+    // launches 1..iters did work (later ones returned at once); all events have
+    // completed: read_ctl synchronised the stream after the last launch
+    const double st_bytes = os.d.kind == PHIX_OP_GRAYSCOTT ? 2.0 * os.plane * (prec == P_FP64 || prec == P_DF64 ? 8 : 4)
+                           : os.d.kind == PHIX_OP_BURGERS ? 1.0 * os.plane * (prec == P_FP64 || prec == P_DF64 ? 8 : 4)
+                                                           : 0.0;
+    const double per = (double)os.N * eb * (2.0 + 2.0 * K) + st_bytes;
+    for (int m = 1; m <= r.iters && m <= launched; ++m) {
+      float t = 0.f;
+      CK(cudaEventElapsedTime(&t, ctx->ev[2 * m], ctx->ev[2 * m + 1]));
+      r.ms += t;
+      r.bytes += per;
+    }
+    r.launches = std::min(r.iters, launched);
+  }
+  return r;
+}
+
+std::vector<double> dd_table(int l, double a, double b, int m) {
+  const double* xi = leja_table(m);
+  std::vector<double> f(m);
+  for (int i = 0; i < m; ++i) f[i] = phi_host(l, a + b * xi[i]);
+  divided_differences_host(xi, f.data(), m);
+  return f;
+}
+
+double power_iteration(phix_ctx* ctx, const OpState& os, int prec, const phix_opts& o, int* mv) {
+  const size_t eb = elem_bytes(prec);
+  void* y[2] = {ws(ctx, S_Y0, os.N * eb), ws(ctx, S_Y1, os.N * eb)};
+  CK(cudaMemsetAsync(ctx->ctl, 0, sizeof(LejaCtl), ctx->stream));
+  KL(launch_power_start(prec, os.N, o.power_seed, y[0], ctx->ctl, ctx->partials, ctx->grid_iter, ctx->stream));
+  IterLaunch L{};
+  L.prec = prec;
+  L.op = os.d.kind;
+  L.mode = MODE_POWER;
+  L.K = 0;
+  L.m_max = o.power_max_it;
+  L.nx = os.d.nx;
+  L.ny = os.d.ny;
+  L.st = os.st;
+  L.ctl = ctx->ctl;
+  L.partials = ctx->partials;
+  L.rel = o.power_rel;
+  L.grid = ctx->grid_iter;
+  for (int j = 0; j < 8; ++j) L.k[j] = os.kJ[j];
+  L.ga = 1.0;
+  int launched = 0, target = std::min(o.power_max_it, 16);
+  for (;;) {
+    for (int m = launched + 1; m <= target; ++m) {
+      L.m = m;
+      L.y_in = y[(m - 1) & 1];
+      L.y_out = y[m & 1];
+      KL(launch_iter(L, ctx->stream));
+    }
+    launched = target;
+    read_ctl(ctx);
+    if (ctx->ctl_h->done || launched >= o.power_max_it) break;
+    target = std::min(o.power_max_it, launched + 8);
+  }
+  if (ctx->ctl_h->status == PHIX_ENAN) fail(ctx, PHIX_ENAN, "power iteration produced a non-finite norm");
+  *mv = ctx->ctl_h->iters;
+  return ctx->ctl_h->rho;
+}
+
+double factorial(int n) {
+  double f = 1.0;
+  for (int i = 2; i <= n; ++i) f *= i;
+  return f;
+}
+
+int substeps_for(double h, double s, double gamma, double rho_im, const phix_opts& o) {
+  int n = 1;
+  if (o.gamma_cap > 0) n = std::max(n, (int)std::ceil(s * h * gamma / o.gamma_cap - 1e-12));
+  if (o.iota_cap > 0 && rho_im > 0) n = std::max(n, (int)std::ceil(s * h * rho_im / o.iota_cap - 1e-12));
+  return n;
+}
+
+void lincomb(phix_ctx* ctx, size_t n, std::vector<double> c, std::vector<const double*> x, double* out) {
+  // chains of at most 6 terms; out may alias x[0]
+  size_t i = 0;
+  bool first = true;
+  while (i < c.size()) {
+    std::vector<double> cc;
+    std::vector<const double*> xx;
+    if (!first) {
+      cc.push_back(1.0);
+      xx.push_back(out);
+    }
+    while (i < c.size() && cc.size() < 6) {
+      cc.push_back(c[i]);
+      xx.push_back(x[i]);
+      ++i;
+    }
+    KL(launch_lincomb(n, (int)cc.size(), cc.data(), xx.data(), out, ctx->grid_stream, ctx->stream));
+    first = false;
+  }
+}
+
+struct Interval {
+  double c, gamma, rho;
+};
+
+// Real Leja actions: out[k] = phi_{l_k}(s_k h J) v (vertical when no substeps).
+void leja_phi(phix_ctx* ctx, const OpState& os, int prec, double h, const double* v, int nout,
+              const int* l, const double* sc, double* const* out, double tol, const phix_opts& o,
+              const Interval& iv, phix_stats& stats) {
+  if (iv.gamma == 0.0) {  // zero spectrum: phi_l(0) v = v / l!
+    for (int k = 0; k < nout; ++k) lincomb(ctx, os.N, {1.0 / factorial(l[k])}, {v}, out[k]);
+    return;
+  }
+  const int M = o.m_max + 1;
+  int smax = 1;
+  std::vector<int> subs(nout);
+  for (int k = 0; k < nout; ++k) {
+    subs[k] = substeps_for(h, sc[k], iv.gamma, o.rho_im, o);
+    smax = std::max(smax, subs[k]);
+  }
+  if (smax == 1) {
+    std::vector<std::vector<double>> d(nout);
+    for (int k = 0; k < nout; ++k) d[k] = dd_table(l[k], sc[k] * h * iv.c, sc[k] * h * iv.gamma, M);
+    PassResult r = leja_pass(ctx, os, prec, v, nout, d, iv.c, iv.gamma, tol, o, out);
+    stats.iter_launches += r.launches;
+    stats.iter_ms += r.ms;
+    stats.iter_bytes += r.bytes;
+    stats.iters += r.iters;
+    stats.jv += r.iters;
+    stats.passes += 1;
+    stats.substeps += 1;
+    if (r.status != PHIX_OK) stats.status = r.status;
+    return;
+  }
+  // ODE-identity substeps, one output at a time:
+  //   u(t+tau) = sum_{j<l} tau^j/j! w_j + tau^l phi_l(tau B) w_l,
+  //   w_0 = u(t), w_j = B w_{j-1} + v t^(l-j)/(l-j)!,  B = s h J
+  double* u = wsd(ctx, S_SUB_U, os.N);
+  double* tmp = wsd(ctx, S_SUB_TMP, os.N);
+  for (int k = 0; k < nout; ++k) {
+    const int L = l[k], ns = subs[k];
+    if (L > 8) fail(ctx, PHIX_EINVAL, "substepped phi_l needs l <= 8");
+    const double tau = 1.0 / ns;
+    std::vector<std::vector<double>> d(1, dd_table(L, tau * sc[k] * h * iv.c, tau * sc[k] * h * iv.gamma, M));
+    if (L == 0)
+      CK(cudaMemcpyAsync(u, v, os.N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    else
+      CK(cudaMemsetAsync(u, 0, os.N * sizeof(double), ctx->stream));
+    std::vector<double*> w(L + 1);
+    w[0] = u;
+    for (int j = 1; j <= L; ++j) w[j] = wsd(ctx, S_SUB_W0 + j, os.N);
+    for (int i = 0; i < ns; ++i) {
+      const double t = i * tau;
+      for (int j = 1; j <= L; ++j) {
+        double coef = std::pow(t, L - j) / factorial(L - j);
+        KL(launch_jv_axpy(os.d, os.state, w[j - 1], sc[k] * h, v, coef, w[j], ctx->grid_stream, ctx->stream));
+        stats.jv += 1;
+      }
+      double* outs[1] = {tmp};
+      PassResult r = leja_pass(ctx, os, prec, w[L], 1, d, iv.c, iv.gamma, tol, o, outs);
+      stats.iter_launches += r.launches;
+      stats.iter_ms += r.ms;
+      stats.iter_bytes += r.bytes;
+      stats.iters += r.iters;
+      stats.jv += r.iters;
+      stats.passes += 1;
+      if (r.status != PHIX_OK) stats.status = r.status;
+      std::vector<double> cc;
+      std::vector<const double*> xx;
+      cc.push_back(std::pow(tau, L));
+      xx.push_back(tmp);
+      for (int j = 0; j < L; ++j) {
+        cc.push_back(std::pow(tau, j) / factorial(j));
+        xx.push_back(w[j]);
+      }
+      // u appears as w[0] on the right: write to tmp first, then swap roles by copying
+      lincomb(ctx, os.N, cc, xx, tmp);
+      CK(cudaMemcpyAsync(u, tmp, os.N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    stats.substeps += ns;
+    CK(cudaMemcpyAsync(out[k], u, os.N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+}
+
+Interval interval_for(phix_ctx* ctx, const OpState& os, int prec, const phix_opts& o, phix_stats& stats) {
+  Interval iv{};
+  double alpha, beta;
+  if (o.rho_re > 0) {
+    alpha = -o.rho_re;
+    beta = o.rho_hi;
+    iv.rho = o.rho_re;
+  } else {
+    int mv = 0;
+    double rho = power_iteration(ctx, os, prec, o, &mv);
+    stats.power_mv += mv;
+    iv.rho = rho;
+    alpha = -o.safety * rho;
+    beta = 0.0;
+  }
+  iv.c = 0.5 * (alpha + beta);
+  iv.gamma = 0.25 * (beta - alpha);
+  stats.rho = iv.rho;
+  return iv;
+}
+
+phix_opts resolve_opts(phix_ctx* ctx, const phix_opts* in) {
+  phix_opts o;
+  phix_opts_default(&o);
+  if (in) o = *in;
+  if (o.prec < PHIX_FP64 || o.prec > PHIX_FP32) fail(ctx, PHIX_EINVAL, "bad precision %d", (int)o.prec);
+  if (o.m_max < 1 || o.m_max > 4000) fail(ctx, PHIX_EINVAL, "m_max must be in 1..4000");
+  if (o.m_min < 0) fail(ctx, PHIX_EINVAL, "m_min must be >= 0");
+  if (!(o.safety > 0)) fail(ctx, PHIX_EINVAL, "safety must be > 0");
+  if (o.power_max_it < 1) fail(ctx, PHIX_EINVAL, "power_max_it must be >= 1");
+  if (o.kiops_m_max < 2 || o.kiops_m_max > 128) fail(ctx, PHIX_EINVAL, "kiops_m_max must be in 2..128");
+  return o;
+}
+
+template <typename F>
+phix_status guarded(phix_ctx* ctx, phix_stats* stats, F&& body) {
+  if (!ctx) return PHIX_EINVAL;
+  ctx->err.clear();
+  phix_stats st{};
+  long l0 = ctx->launches;
+  phix_status rc;
+  try {
+    rc = body(st);
+  } catch (const Fail& f) {
+    rc = f.st;
+  }
+  if (rc == PHIX_OK && st.status != PHIX_OK) {
+    rc = (phix_status)st.status;
+    if (ctx->err.empty())
+      set_err(ctx, "%s", rc == PHIX_ENOTCONV ? "iteration did not converge within m_max" : "non-finite norm");
+  }
+  st.status = rc;
+  st.launches = (int)(ctx->launches - l0);
+  if (stats) *stats = st;
+  return rc;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+int phix_version(void) { return PHIX_VERSION; }
+
+void phix_opts_default(phix_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof *o);
+  o->prec = PHIX_DF64;
+  o->safety = 1.2;
+  o->rho_re = -1.0;
+  o->rho_hi = 0.0;
+  o->rho_im = 0.0;
+  o->gamma_cap = 200.0;
+  o->iota_cap = 4.0;
+  o->m_max = 500;
+  o->m_min = 3;
+  o->power_max_it = 50;
+  o->power_rel = 1e-2;
+  o->power_seed = 0x5EED;
+  o->kiops_m_init = 16;
+  o->kiops_m_max = 64;
+  o->kiops_m_step = 8;
+  o->kiops_max_substeps = 10000;
+}
+
+phix_status phix_create(phix_ctx** out, void* stream) {
+  if (!out) return PHIX_EINVAL;
+  *out = nullptr;
+  phix_ctx* ctx = new phix_ctx();
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  try {
+    CK(cudaGetDevice(&ctx->device));
+    CK(cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, ctx->device));
+    ctx->grid_iter = ctx->nsm * 4;
+    ctx->grid_stream = ctx->nsm * 8;
+    CK(cudaMalloc(&ctx->ctl, sizeof(LejaCtl)));
+    CK(cudaMallocHost(&ctx->ctl_h, sizeof(LejaCtl)));
+    CK(cudaMalloc(&ctx->partials, sizeof(double) * (size_t)std::max(ctx->grid_iter, ctx->grid_stream) * (KMAX + 1)));
+    CK(cudaMalloc(&ctx->scal, sizeof(double) * 16));
+    CK(cudaMallocHost(&ctx->scal_h, sizeof(double) * 16));
+    CK(cudaMalloc(&ctx->counter, sizeof(unsigned int)));
+    CK(cudaMemset(ctx->counter, 0, sizeof(unsigned int)));
+    CK(cudaMemset(ctx->ctl, 0, sizeof(LejaCtl)));
+    CK(cudaDeviceSynchronize());
+  } catch (const Fail& f) {
+    phix_destroy(ctx);
+    return f.st;
+  }
+  *out = ctx;
+  return PHIX_OK;
+}
+
+phix_status phix_destroy(phix_ctx* ctx) {
+  if (!ctx) return PHIX_EINVAL;
+  cudaStreamSynchronize(ctx->stream);
+  for (int i = 0; i < S_NSLOT; ++i)
+    if (ctx->buf[i]) cudaFree(ctx->buf[i]);
+  if (ctx->ctl) cudaFree(ctx->ctl);
+  if (ctx->ctl_h) cudaFreeHost(ctx->ctl_h);
+  if (ctx->partials) cudaFree(ctx->partials);
+  if (ctx->scal) cudaFree(ctx->scal);
+  if (ctx->scal_h) cudaFreeHost(ctx->scal_h);
+  if (ctx->counter) cudaFree(ctx->counter);
+  for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+  delete ctx;
+  return PHIX_OK;
+}
+
+const char* phix_last_error(const phix_ctx* ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }
+
+phix_status phix_leja_points(double* xi, int m) {
+  if (!xi || m < 1 || m > 4096) return PHIX_EINVAL;
+  return leja_points_host(xi, m) == 0 ? PHIX_OK : PHIX_EINVAL;
+}
+
+phix_status phix_divided_differences(int l, double a, double b, int m, double* d) {
+  if (!d || m < 1 || m > 4096 || l < 0 || l > 20) return PHIX_EINVAL;
+  std::vector<double> t = dd_table(l, a, b, m);
+  std::memcpy(d, t.data(), sizeof(double) * m);
+  return PHIX_OK;
+}
+
+phix_status phix_spectrum(phix_ctx* ctx, const phix_jop* op, const phix_opts* opts, double* rho,
+                          phix_stats* stats) {
+  return guarded(ctx, stats, [&](phix_stats& st) -> phix_status {
+    check_op(ctx, op, true);
+    if (!rho) fail(ctx, PHIX_EINVAL, "rho is NULL");
+    phix_opts o = resolve_opts(ctx, opts);
+    OpState os = make_opstate(ctx, op, op->state, o.prec);
+    int mv = 0;
+    *rho = power_iteration(ctx, os, o.prec, o, &mv);
+    st.power_mv = mv;
+    st.rho = *rho;
+    return PHIX_OK;
+  });
+}
+
+phix_status phix_phi_action(phix_ctx* ctx, const phix_jop* op, double h, const double* v, int nout,
+                            const int* l, const double* scale, double* const* out, double tol,
+                            phix_method method, const phix_opts* opts, phix_stats* stats) {
+  return guarded(ctx, stats, [&](phix_stats& st) -> phix_status {
+    check_op(ctx, op, true);
+    if (!v || !out || !l || !scale) fail(ctx, PHIX_EINVAL, "NULL argument");
+    if (nout < 1 || nout > KMAX) fail(ctx, PHIX_EINVAL, "nout must be in 1..%d", KMAX);
+    if (!(h >= 0) || !std::isfinite(h)) fail(ctx, PHIX_EINVAL, "h must be finite and >= 0");
+    if (!(tol > 0)) fail(ctx, PHIX_EINVAL, "tol must be > 0");
+    for (int k = 0; k < nout; ++k) {
+      if (l[k] < 0 || l[k] > 8) fail(ctx, PHIX_EINVAL, "l[%d] = %d out of 0..8", k, l[k]);
+      if (!(scale[k] > 0)) fail(ctx, PHIX_EINVAL, "scale[%d] must be > 0", k);
+      if (!out[k] || out[k] == v) fail(ctx, PHIX_EINVAL, "out[%d] is NULL or aliases v", k);
+    }
+    phix_opts o = resolve_opts(ctx, opts);
+    if (method != PHIX_LEJA) fail(ctx, PHIX_EINVAL, "method %d not available", (int)method);
+    OpState os = make_opstate(ctx, op, op->state, o.prec);
+    if (h == 0.0) {
+      for (int k = 0; k < nout; ++k) lincomb(ctx, os.N, {1.0 / factorial(l[k])}, {v}, out[k]);
+      CK(cudaStreamSynchronize(ctx->stream));
+      return PHIX_OK;
+    }
+    Interval iv = interval_for(ctx, os, o.prec, o, st);
+    leja_phi(ctx, os, o.prec, h, v, nout, l, scale, out, tol, o, iv, st);
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PHIX_OK;
+  });
+}
+
+phix_status phix_phi_combination(phix_ctx* ctx, const phix_jop* op, double h, const double* const* b,
+                                 int p, double* out, double tol, phix_method method,
+                                 const phix_opts* opts, phix_stats* stats) {
+  return guarded(ctx, stats, [&](phix_stats& st) -> phix_status {
+    check_op(ctx, op, true);
+    if (!b || !out) fail(ctx, PHIX_EINVAL, "NULL argument");
+    if (p < 0 || p > 8) fail(ctx, PHIX_EINVAL, "p must be in 0..8");
+    phix_opts o = resolve_opts(ctx, opts);
+    if (method != PHIX_LEJA) fail(ctx, PHIX_EINVAL, "method %d not available", (int)method);
+    OpState os = make_opstate(ctx, op, op->state, o.prec);
+    CK(cudaMemsetAsync(out, 0, os.N * sizeof(double), ctx->stream));
+    Interval iv = interval_for(ctx, os, o.prec, o, st);
+    double* tmp = wsd(ctx, S_O3, os.N);
+    for (int j = 0; j <= p; ++j) {
+      if (!b[j]) continue;
+      if (b[j] == out) fail(ctx, PHIX_EINVAL, "out aliases b[%d]", j);
+      int lj = j;
+      double s1 = 1.0;
+      double* outs[1] = {tmp};
+      leja_phi(ctx, os, o.prec, h, b[j], 1, &lj, &s1, outs, tol, o, iv, st);
+      lincomb(ctx, os.N, {1.0, 1.0}, {out, tmp}, out);
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PHIX_OK;
+  });
+}
+
+// EXPRB43 and EPIRK4s3 share this driver; `scheme` selects the coefficients.
+static phix_status exp_step(phix_ctx* ctx, const phix_jop* op, double* u, double h, double tol,
+                            phix_method method, const phix_opts* opts, double* err_est,
+                            phix_stats* stats, int scheme) {
+  return guarded(ctx, stats, [&](phix_stats& st) -> phix_status {
+    check_op(ctx, op, false);
+    if (!u) fail(ctx, PHIX_EINVAL, "u_inout is NULL");
+    if (!(h > 0) || !std::isfinite(h)) fail(ctx, PHIX_EINVAL, "h must be finite and > 0");
+    if (!(tol > 0)) fail(ctx, PHIX_EINVAL, "tol must be > 0");
+    phix_opts o = resolve_opts(ctx, opts);
+    if (method != PHIX_LEJA) fail(ctx, PHIX_EINVAL, "method %d not available", (int)method);
+    OpState os = make_opstate(ctx, op, u, o.prec);
+    const size_t N = os.N;
+    double* F = wsd(ctx, S_F, N);
+    double* A = wsd(ctx, S_A, N);
+    double* B = wsd(ctx, S_B, N);
+    double* RA = wsd(ctx, S_RA, N);
+    double* RB = wsd(ctx, S_RB, N);
+    double* T0 = wsd(ctx, S_T0, N);
+    double* Q = wsd(ctx, S_Q, N);
+    double* T3 = wsd(ctx, S_T3, N);
+    double* T4 = wsd(ctx, S_T4, N);
+    double* P1 = wsd(ctx, S_O1, N);
+    double* P2 = wsd(ctx, S_O2, N);
+    double* P3 = wsd(ctx, S_O3, N);
+    KL(launch_rhs(os.d, u, F, ctx->grid_stream, ctx->stream));
+    Interval iv = interval_for(ctx, os, o.prec, o, st);
+    lincomb(ctx, N, {h}, {F}, T0);
+    if (scheme == 0) {
+      // EXPRB43, Eq. (exprb43)
+      int l2[2] = {1, 1};
+      double s2[2] = {0.5, 1.0};
+      double* o2[2] = {P1, P2};
+      leja_phi(ctx, os, o.prec, h, T0, 2, l2, s2, o2, tol, o, iv, st);
+      lincomb(ctx, N, {1.0, 0.5}, {u, P1}, A);                 // a = u + 1/2 phi_1(h/2 J) f h
+      KL(launch_remainder(os.d, u, A, F, RA, ctx->grid_stream, ctx->stream));
+      lincomb(ctx, N, {h}, {RA}, T0);
+      int l1 = 1;
+      double s1 = 1.0;
+      double* oq[1] = {Q};
+      leja_phi(ctx, os, o.prec, h, T0, 1, &l1, &s1, oq, tol, o, iv, st);
+      lincomb(ctx, N, {1.0, 1.0, 1.0}, {u, P2, Q}, B);         // b = u + phi_1 f h + phi_1 R(a) h
+      KL(launch_remainder(os.d, u, B, F, RB, ctx->grid_stream, ctx->stream));
+      lincomb(ctx, N, {16.0 * h, -2.0 * h}, {RA, RB}, T0);
+      int l3 = 3;
+      double* o3[1] = {T3};
+      leja_phi(ctx, os, o.prec, h, T0, 1, &l3, &s1, o3, tol, o, iv, st);
+      lincomb(ctx, N, {-48.0 * h, 12.0 * h}, {RA, RB}, T0);
+      int l4 = 4;
+      double* o4[1] = {T4};
+      leja_phi(ctx, os, o.prec, h, T0, 1, &l4, &s1, o4, tol, o, iv, st);
+    } else {
+      // EPIRK4s3, Eq. (epirk4s3)
+      int l3v[3] = {1, 1, 1};
+      double s3[3] = {1.0 / 8.0, 1.0 / 9.0, 1.0};
+      double* o3v[3] = {P1, P3, P2};
+      leja_phi(ctx, os, o.prec, h, T0, 3, l3v, s3, o3v, tol, o, iv, st);
+      lincomb(ctx, N, {1.0, 1.0 / 8.0}, {u, P1}, A);
+      lincomb(ctx, N, {1.0, 1.0 / 9.0}, {u, P3}, B);
+      KL(launch_remainder(os.d, u, A, F, RA, ctx->grid_stream, ctx->stream));
+      KL(launch_remainder(os.d, u, B, F, RB, ctx->grid_stream, ctx->stream));
+      // 1892 Ra + 1458 (Rb - 2 Ra) = -1024 Ra + 1458 Rb
+      lincomb(ctx, N, {(1892.0 - 2.0 * 1458.0) * h, 1458.0 * h}, {RA, RB}, T0);
+      int l3 = 3;
+      double s1 = 1.0;
+      double* o3[1] = {T3};
+      leja_phi(ctx, os, o.prec, h, T0, 1, &l3, &s1, o3, tol, o, iv, st);
+      // -42336 Ra - 34992 (Rb - 2 Ra) = 27648 Ra - 34992 Rb
+      lincomb(ctx, N, {(-42336.0 + 2.0 * 34992.0) * h, -34992.0 * h}, {RA, RB}, T0);
+      int l4 = 4;
+      double* o4[1] = {T4};
+      leja_phi(ctx, os, o.prec, h, T0, 1, &l4, &s1, o4, tol, o, iv, st);
+    }
+    // err = ||u4 - u3|| = ||T4||;  u4 = u + phi_1(hJ) f h + T3 + T4
+    KL(launch_norm2(N, T4, nullptr, ctx->partials, ctx->counter, ctx->scal, ctx->grid_stream, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->scal_h, ctx->scal, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (st.status == PHIX_OK) lincomb(ctx, N, {1.0, 1.0, 1.0, 1.0}, {u, P2, T3, T4}, u);
+    CK(cudaStreamSynchronize(ctx->stream));
+    st.err_est = std::sqrt(ctx->scal_h[0]);
+    if (err_est) *err_est = st.err_est;
+    return PHIX_OK;
+  });
+}
+
+phix_status phix_exprb43_step(phix_ctx* ctx, const phix_jop* op, double* u_inout, double h, double tol,
+                              phix_method method, const phix_opts* opts, double* err_est,
+                              phix_stats* stats) {
+  return exp_step(ctx, op, u_inout, h, tol, method, opts, err_est, stats, 0);
+}
+
+phix_status phix_epirk4s3_step(phix_ctx* ctx, const phix_jop* op, double* u_inout, double h, double tol,
+                               phix_method method, const phix_opts* opts, double* err_est,
+                               phix_stats* stats) {
+  return exp_step(ctx, op, u_inout, h, tol, method, opts, err_est, stats, 1);
+}
+
+}  // extern "C"

@@ -1,0 +1,143 @@
+// Internal declarations shared by the host driver and the kernel files.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "df64.cuh"
+#include "phix.h"
+
+namespace phix {
+
+constexpr int KMAX = 4;       // accumulators of one vertical Newton pass
+constexpr int TILE_Y = 8;     // rows per tile (one warp per row)
+constexpr int THREADS = 256;  // 32 x 8
+
+enum Prec { P_FP64 = 0, P_DF64 = 1, P_FP32JV = 2, P_FP32 = 3 };
+enum Mode { MODE_NEWTON = 0, MODE_POWER = 1 };
+
+// Device-resident control block of one chain of iteration launches.  The
+// last block of each launch reduces the per-block partial sums in a fixed
+// order, takes the stop decision and sets `done`; later launches of the
+// chain read `done` and return at once, so the host may enqueue more
+// launches than needed without reading anything back.
+struct LejaCtl {
+  unsigned int count;  // arrival counter of the last-block reduction (reset by the last block)
+  int done;            // 1: converged or failed
+  int iters;           // iteration index m at which the chain stopped
+  int status;          // phix_status
+  double ynorm;        // ||y_m|| (scaled units) of the last completed launch
+  double pnorm[KMAX];  // ||p_m^(k)||
+  double sigma;        // input scale, a power of two
+  double inv_sigma;
+  double rho;          // power iteration: ||J v_k||
+  double rho_prev;
+  double alpha;        // power iteration: 1/||y_k|| for the next launch
+  float alpha_hi, alpha_lo;
+};
+
+// Coefficient pack of one launch, in the arithmetic of the precision.
+// ADVDIFF:   k = {E, W, N, S, C}
+// GRAYSCOTT: k = {xu, yu, Cu, xv, yv, Cv}, per-point terms g1 = V^2, g2 = 2UV
+// BURGERS:   k = {x, y, C, bx, by},        per-point state U
+// In MODE_NEWTON the host folds alpha = 1/gamma into k and ga, and beta =
+// -(c/gamma + xi_{m-1}) is the shift of the centre value.
+template <typename CJ, typename C>
+struct IterArgs {
+  const void* y_in;
+  void* y_out;
+  void* p[KMAX];
+  const void* st;     // per-point state planes (precision's state type)
+  LejaCtl* ctl;
+  double* partials;   // gridDim.x * (KMAX + 1)
+  int nx, ny, K, m, m_min, m_max, ntiles, tiles_x;
+  double tol, rel;
+  double dkd[KMAX];   // |d_k[m]| test values (float64)
+  C dk[KMAX];         // d_k[m] in the iteration arithmetic
+  CJ k[8];
+  CJ ga;
+  C beta;
+};
+
+// ---- launchers (leja_kernels.cu) -----------------------------------------
+struct IterLaunch {
+  int prec, op, mode, K, m, m_min, m_max;
+  int nx, ny;
+  const void* y_in;
+  void* y_out;
+  void* p[KMAX];
+  const void* st;
+  LejaCtl* ctl;
+  double* partials;
+  double tol, rel;
+  double dk[KMAX];     // d_k[m]
+  double k[8];         // uniform coefficients (alpha-folded for NEWTON)
+  double ga;           // per-point term scale
+  double beta;         // shift
+  int grid;            // blocks
+};
+cudaError_t launch_iter(const IterLaunch& L, cudaStream_t s);
+
+// y0 = v / sigma (stored in the precision's format), p_k = d_k[0] y0, norms.
+struct InitLaunch {
+  int prec, ncomp, K, m_min, m_max, nx, ny;
+  const double* v;
+  void* y0;
+  void* p[KMAX];
+  LejaCtl* ctl;
+  double* partials;
+  double tol;
+  double dk[KMAX];
+  int grid;
+};
+cudaError_t launch_init(const InitLaunch& L, cudaStream_t s);
+
+// ctl->sigma = 2^round(log2(rms(v))), ctl cleared.
+cudaError_t launch_scale(const double* v, size_t n, LejaCtl* ctl, double* partials, int grid,
+                         cudaStream_t s);
+
+struct PtrPack {
+  const void* p[KMAX];
+  double* o[KMAX];
+};
+// out_k = sigma * p_k (float64); p and out are HOST arrays of K device pointers
+cudaError_t launch_finalize(int prec, size_t n, int K, void* const* p, double* const* out,
+                            const LejaCtl* ctl, int grid, cudaStream_t s);
+
+// power iteration start: y0[i] = splitmix64_uniform(seed, i) in the precision's format,
+// ctl->alpha = 1/||y0||.
+cudaError_t launch_power_start(int prec, size_t n, uint64_t seed, void* y0, LejaCtl* ctl,
+                               double* partials, int grid, cudaStream_t s);
+
+// Per-point state arrays of the Jacobian in the precision's format:
+// GRAYSCOTT: st = [V^2 plane, 2UV plane]; BURGERS: st = [U plane].
+cudaError_t launch_prep_state(int prec, int op, int nx, int ny, const double* state, void* st,
+                              int grid, cudaStream_t s);
+
+// ---- float64 stage kernels (stage_kernels.cu) -----------------------------
+struct OpDesc {
+  int kind, nx, ny;
+  double p[8];
+};
+// f = f(u)
+cudaError_t launch_rhs(const OpDesc& op, const double* u, double* f, int grid, cudaStream_t s);
+// R = f(a) - fu - J(u)(a - u)
+cudaError_t launch_remainder(const OpDesc& op, const double* u, const double* a, const double* fu,
+                             double* R, int grid, cudaStream_t s);
+// out = alpha * J(state) x + beta * v   (v may be NULL)
+cudaError_t launch_jv_axpy(const OpDesc& op, const double* state, const double* x, double alpha,
+                           const double* v, double beta, double* out, int grid, cudaStream_t s);
+// out = sum_i c[i] * x[i], i < nterms <= 6 (x[i] may alias out)
+cudaError_t launch_lincomb(size_t n, int nterms, const double* c, const double* const* x,
+                           double* out, int grid, cudaStream_t s);
+// result[0] = ||x - y||_2^2 (y may be NULL) -> device double via last-block reduction
+cudaError_t launch_norm2(size_t n, const double* x, const double* y, double* partials,
+                         unsigned int* counter, double* result, int grid, cudaStream_t s);
+
+// ---- host math (host_math.cpp) --------------------------------------------
+double phi_host(int l, double z);
+int leja_points_host(double* xi, int m);                 // 0 on success
+const double* leja_table(int m);                         // cached, thread-safe
+void divided_differences_host(const double* x, double* f, int n);
+}  // namespace phix

@@ -1,0 +1,244 @@
+// Float64 kernels of the integrator stages: right-hand sides f(u), the
+// nonlinear remainder R(a) = f(a) - f(u) - J(u)(a - u) (Sec. 1), Jacobian
+// actions with an axpy (ODE-identity substeps), linear combinations and
+// norms.  They run a handful of times per time step, against hundreds of
+// Newton-Leja iterations, so they stay in plain float64.
+#include "phix_internal.h"
+
+namespace phix {
+
+namespace {
+
+struct Nbr {
+  double c, e, w, n, s;
+};
+
+__device__ __forceinline__ Nbr load_nbr(const double* __restrict__ x, int nx, int ny, int ix, int iy) {
+  const int ixm = ix == 0 ? nx - 1 : ix - 1, ixp = ix == nx - 1 ? 0 : ix + 1;
+  const int iym = iy == 0 ? ny - 1 : iy - 1, iyp = iy == ny - 1 ? 0 : iy + 1;
+  Nbr r;
+  r.c = x[(size_t)iy * nx + ix];
+  r.e = x[(size_t)iy * nx + ixp];
+  r.w = x[(size_t)iy * nx + ixm];
+  r.n = x[(size_t)iyp * nx + ix];
+  r.s = x[(size_t)iym * nx + ix];
+  return r;
+}
+
+__device__ __forceinline__ double lap(const Nbr& a, double idx2, double idy2) {
+  return (a.e + a.w - 2.0 * a.c) * idx2 + (a.n + a.s - 2.0 * a.c) * idy2;
+}
+__device__ __forceinline__ double ddx(const Nbr& a, double i2dx) { return (a.e - a.w) * i2dx; }
+__device__ __forceinline__ double ddy(const Nbr& a, double i2dy) { return (a.n - a.s) * i2dy; }
+
+struct Geo {
+  int nx, ny;
+  double idx2, idy2, i2dx, i2dy;
+};
+__device__ __forceinline__ Geo geo(const OpDesc& op) {
+  Geo g;
+  g.nx = op.nx;
+  g.ny = op.ny;
+  double dx = 1.0 / op.nx, dy = 1.0 / op.ny;
+  g.idx2 = 1.0 / (dx * dx);
+  g.idy2 = 1.0 / (dy * dy);
+  g.i2dx = 0.5 / dx;
+  g.i2dy = 0.5 / dy;
+  return g;
+}
+
+// f(u) at one grid point; writes 1 or 2 species values
+__device__ __forceinline__ void rhs_point(const OpDesc& op, const Geo& g, const double* u, int ix,
+                                          int iy, double* out) {
+  const size_t plane = (size_t)g.nx * g.ny;
+  if (op.kind == PHIX_OP_ADVDIFF) {
+    Nbr a = load_nbr(u, g.nx, g.ny, ix, iy);
+    out[0] = op.p[0] * lap(a, g.idx2, g.idy2) + op.p[1] * ddx(a, g.i2dx) + op.p[2] * ddy(a, g.i2dy);
+  } else if (op.kind == PHIX_OP_GRAYSCOTT) {
+    Nbr a = load_nbr(u, g.nx, g.ny, ix, iy);
+    Nbr b = load_nbr(u + plane, g.nx, g.ny, ix, iy);
+    double uvv = a.c * b.c * b.c;
+    out[0] = op.p[0] * lap(a, g.idx2, g.idy2) - uvv + op.p[2] * (1.0 - a.c);
+    out[1] = op.p[1] * lap(b, g.idx2, g.idy2) + uvv - (op.p[2] + op.p[3]) * b.c;
+  } else {
+    Nbr a = load_nbr(u, g.nx, g.ny, ix, iy);
+    out[0] = op.p[0] * lap(a, g.idx2, g.idy2) - a.c * (ddx(a, g.i2dx) + ddy(a, g.i2dy));
+  }
+}
+
+// J(state) x at one grid point
+__device__ __forceinline__ void jv_point(const OpDesc& op, const Geo& g, const double* st,
+                                         const double* x, int ix, int iy, double* out) {
+  const size_t plane = (size_t)g.nx * g.ny;
+  const size_t i = (size_t)iy * g.nx + ix;
+  if (op.kind == PHIX_OP_ADVDIFF) {
+    Nbr a = load_nbr(x, g.nx, g.ny, ix, iy);
+    out[0] = op.p[0] * lap(a, g.idx2, g.idy2) + op.p[1] * ddx(a, g.i2dx) + op.p[2] * ddy(a, g.i2dy);
+  } else if (op.kind == PHIX_OP_GRAYSCOTT) {
+    Nbr a = load_nbr(x, g.nx, g.ny, ix, iy);
+    Nbr b = load_nbr(x + plane, g.nx, g.ny, ix, iy);
+    double U = st[i], V = st[plane + i];
+    out[0] = op.p[0] * lap(a, g.idx2, g.idy2) - (V * V + op.p[2]) * a.c - 2.0 * U * V * b.c;
+    out[1] = op.p[1] * lap(b, g.idx2, g.idy2) + V * V * a.c + (2.0 * U * V - (op.p[2] + op.p[3])) * b.c;
+  } else {
+    Nbr a = load_nbr(x, g.nx, g.ny, ix, iy);
+    Nbr U = load_nbr(st, g.nx, g.ny, ix, iy);
+    double divU = ddx(U, g.i2dx) + ddy(U, g.i2dy);
+    out[0] = op.p[0] * lap(a, g.idx2, g.idy2) - divU * a.c - U.c * (ddx(a, g.i2dx) + ddy(a, g.i2dy));
+  }
+}
+
+__global__ void k_rhs(OpDesc op, const double* __restrict__ u, double* __restrict__ f) {
+  Geo g = geo(op);
+  const size_t plane = (size_t)g.nx * g.ny;
+  const int nc = op.kind == PHIX_OP_GRAYSCOTT ? 2 : 1;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < plane; i += (size_t)gridDim.x * blockDim.x) {
+    int ix = (int)(i % g.nx), iy = (int)(i / g.nx);
+    double o[2];
+    rhs_point(op, g, u, ix, iy, o);
+    for (int q = 0; q < nc; ++q) f[q * plane + i] = o[q];
+  }
+}
+
+// R = f(a) - fu - J(u)(a - u); J(u)(a-u) is linear in (a - u), formed from the
+// neighbour differences directly.
+__global__ void k_remainder(OpDesc op, const double* __restrict__ u, const double* __restrict__ a,
+                            const double* __restrict__ fu, double* __restrict__ R) {
+  Geo g = geo(op);
+  const size_t plane = (size_t)g.nx * g.ny;
+  const int nc = op.kind == PHIX_OP_GRAYSCOTT ? 2 : 1;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < plane; i += (size_t)gridDim.x * blockDim.x) {
+    int ix = (int)(i % g.nx), iy = (int)(i / g.nx);
+    double fa[2], jd[2];
+    rhs_point(op, g, a, ix, iy, fa);
+    // J(u)(a - u) without a temporary: difference of neighbour loads
+    if (op.kind == PHIX_OP_ADVDIFF) {
+      Nbr A = load_nbr(a, g.nx, g.ny, ix, iy), U = load_nbr(u, g.nx, g.ny, ix, iy);
+      Nbr d{A.c - U.c, A.e - U.e, A.w - U.w, A.n - U.n, A.s - U.s};
+      jd[0] = op.p[0] * lap(d, g.idx2, g.idy2) + op.p[1] * ddx(d, g.i2dx) + op.p[2] * ddy(d, g.i2dy);
+    } else if (op.kind == PHIX_OP_GRAYSCOTT) {
+      Nbr A = load_nbr(a, g.nx, g.ny, ix, iy), U = load_nbr(u, g.nx, g.ny, ix, iy);
+      Nbr B = load_nbr(a + plane, g.nx, g.ny, ix, iy), Vn = load_nbr(u + plane, g.nx, g.ny, ix, iy);
+      Nbr du{A.c - U.c, A.e - U.e, A.w - U.w, A.n - U.n, A.s - U.s};
+      Nbr dv{B.c - Vn.c, B.e - Vn.e, B.w - Vn.w, B.n - Vn.n, B.s - Vn.s};
+      double Uc = U.c, Vc = Vn.c;
+      jd[0] = op.p[0] * lap(du, g.idx2, g.idy2) - (Vc * Vc + op.p[2]) * du.c - 2.0 * Uc * Vc * dv.c;
+      jd[1] = op.p[1] * lap(dv, g.idx2, g.idy2) + Vc * Vc * du.c + (2.0 * Uc * Vc - (op.p[2] + op.p[3])) * dv.c;
+    } else {
+      Nbr A = load_nbr(a, g.nx, g.ny, ix, iy), U = load_nbr(u, g.nx, g.ny, ix, iy);
+      Nbr d{A.c - U.c, A.e - U.e, A.w - U.w, A.n - U.n, A.s - U.s};
+      double divU = ddx(U, g.i2dx) + ddy(U, g.i2dy);
+      jd[0] = op.p[0] * lap(d, g.idx2, g.idy2) - divU * d.c - U.c * (ddx(d, g.i2dx) + ddy(d, g.i2dy));
+    }
+    for (int q = 0; q < nc; ++q) R[q * plane + i] = fa[q] - fu[q * plane + i] - jd[q];
+  }
+}
+
+__global__ void k_jv_axpy(OpDesc op, const double* __restrict__ st, const double* __restrict__ x,
+                          double alpha, const double* __restrict__ v, double beta,
+                          double* __restrict__ out) {
+  Geo g = geo(op);
+  const size_t plane = (size_t)g.nx * g.ny;
+  const int nc = op.kind == PHIX_OP_GRAYSCOTT ? 2 : 1;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < plane; i += (size_t)gridDim.x * blockDim.x) {
+    int ix = (int)(i % g.nx), iy = (int)(i / g.nx);
+    double o[2];
+    jv_point(op, g, st, x, ix, iy, o);
+    for (int q = 0; q < nc; ++q) {
+      double r = alpha * o[q];
+      if (v) r += beta * v[q * plane + i];
+      out[q * plane + i] = r;
+    }
+  }
+}
+
+struct Comb {
+  double c[6];
+  const double* x[6];
+};
+
+__global__ void k_lincomb(size_t n, int nt, Comb cb, double* out) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    double r = 0.0;
+    for (int t = 0; t < nt; ++t) r += cb.c[t] * cb.x[t][i];
+    out[i] = r;
+  }
+}
+
+__global__ void k_norm2(size_t n, const double* __restrict__ x, const double* __restrict__ y,
+                        double* partials, unsigned int* counter, double* result) {
+  __shared__ double sw[32];
+  __shared__ bool last;
+  double s = 0.0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    double d = y ? x[i] - y[i] : x[i];
+    s = fma(d, d, s);
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += sw[w];
+    partials[blockIdx.x] = b;
+    __threadfence();
+    unsigned int t = atomicAdd(counter, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) tot += __ldcg(partials + b);
+    *result = tot;
+    *counter = 0;
+    __threadfence();
+  }
+}
+
+}  // namespace
+
+static inline int clamp_grid(size_t work, int grid) {
+  size_t need = (work + 255) / 256;
+  if (need < 1) need = 1;
+  return (int)(need < (size_t)grid ? need : (size_t)grid);
+}
+
+cudaError_t launch_rhs(const OpDesc& op, const double* u, double* f, int grid, cudaStream_t s) {
+  size_t plane = (size_t)op.nx * op.ny;
+  k_rhs<<<clamp_grid(plane, grid), 256, 0, s>>>(op, u, f);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_remainder(const OpDesc& op, const double* u, const double* a, const double* fu,
+                             double* R, int grid, cudaStream_t s) {
+  size_t plane = (size_t)op.nx * op.ny;
+  k_remainder<<<clamp_grid(plane, grid), 256, 0, s>>>(op, u, a, fu, R);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_jv_axpy(const OpDesc& op, const double* state, const double* x, double alpha,
+                           const double* v, double beta, double* out, int grid, cudaStream_t s) {
+  size_t plane = (size_t)op.nx * op.ny;
+  k_jv_axpy<<<clamp_grid(plane, grid), 256, 0, s>>>(op, state, x, alpha, v, beta, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lincomb(size_t n, int nterms, const double* c, const double* const* x,
+                           double* out, int grid, cudaStream_t s) {
+  if (nterms < 1 || nterms > 6) return cudaErrorInvalidValue;
+  Comb cb{};
+  for (int t = 0; t < nterms; ++t) {
+    cb.c[t] = c[t];
+    cb.x[t] = x[t];
+  }
+  k_lincomb<<<clamp_grid(n, grid), 256, 0, s>>>(n, nterms, cb, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_norm2(size_t n, const double* x, const double* y, double* partials,
+                         unsigned int* counter, double* result, int grid, cudaStream_t s) {
+  k_norm2<<<clamp_grid(n, grid), 256, 0, s>>>(n, x, y, partials, counter, result);
+  return cudaGetLastError();
+}
+
+}  // namespace phix

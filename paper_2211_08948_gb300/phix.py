@@ -1,0 +1,221 @@
+"""Thin ctypes binding of libphix (include/phix.h), same function names.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Vector arguments are torch CUDA tensors of dtype float64 (their
+device memory is passed by pointer) or raw device addresses (int).  The
+library must exist (``python -m paper_2211_08948_gb300.build``); loading
+fails loudly otherwise.
+"""
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libphix.so")
+
+PHIX_OK, PHIX_EINVAL, PHIX_ENOTCONV, PHIX_ENAN, PHIX_ETIMEOUT, PHIX_ECUDA, PHIX_ENOMEM = range(7)
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOTCONV", 3: "ENAN", 4: "ETIMEOUT", 5: "ECUDA", 6: "ENOMEM"}
+PHIX_LEJA, PHIX_KIOPS = 0, 1
+PHIX_FP64, PHIX_DF64, PHIX_FP32_JV, PHIX_FP32 = 0, 1, 2, 3
+PHIX_OP_ADVDIFF, PHIX_OP_GRAYSCOTT, PHIX_OP_BURGERS = 0, 1, 2
+
+# every symbol include/phix.h declares
+EXPORTS = [
+    "phix_opts_default", "phix_version", "phix_create", "phix_destroy", "phix_last_error",
+    "phix_phi_action", "phix_phi_combination", "phix_spectrum", "phix_exprb43_step",
+    "phix_epirk4s3_step", "phix_leja_points", "phix_divided_differences",
+]
+
+
+class phix_jop(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("param", ctypes.c_double * 8), ("state", ctypes.c_void_p)]
+
+
+class phix_opts(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int), ("safety", ctypes.c_double), ("rho_re", ctypes.c_double),
+                ("rho_hi", ctypes.c_double), ("rho_im", ctypes.c_double),
+                ("gamma_cap", ctypes.c_double), ("iota_cap", ctypes.c_double),
+                ("m_max", ctypes.c_int), ("m_min", ctypes.c_int), ("power_max_it", ctypes.c_int),
+                ("power_rel", ctypes.c_double), ("power_seed", ctypes.c_uint64),
+                ("kiops_m_init", ctypes.c_int), ("kiops_m_max", ctypes.c_int),
+                ("kiops_m_step", ctypes.c_int), ("kiops_max_substeps", ctypes.c_int),
+                ("profile", ctypes.c_int)]
+
+
+class phix_stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("jv", ctypes.c_int),
+                ("substeps", ctypes.c_int), ("power_mv", ctypes.c_int), ("rejections", ctypes.c_int),
+                ("passes", ctypes.c_int), ("launches", ctypes.c_int), ("rho", ctypes.c_double),
+                ("err_est", ctypes.c_double), ("iter_launches", ctypes.c_int), ("iter_ms", ctypes.c_double),
+                ("iter_bytes", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class PhixError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("phix %s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+_lib = None
+
+
+def load(path=None):
+    """Load libphix.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError("libphix.so not built at %s: run python -m paper_2211_08948_gb300.build" % p)
+    lib = ctypes.CDLL(p)
+    P = ctypes.c_void_p
+    D = ctypes.c_double
+    I = ctypes.c_int
+    lib.phix_opts_default.argtypes = [ctypes.POINTER(phix_opts)]
+    lib.phix_opts_default.restype = None
+    lib.phix_version.restype = I
+    lib.phix_create.argtypes = [ctypes.POINTER(P), P]
+    lib.phix_destroy.argtypes = [P]
+    lib.phix_last_error.argtypes = [P]
+    lib.phix_last_error.restype = ctypes.c_char_p
+    lib.phix_phi_action.argtypes = [P, ctypes.POINTER(phix_jop), D, P, I, ctypes.POINTER(I),
+                                    ctypes.POINTER(D), ctypes.POINTER(P), D, I,
+                                    ctypes.POINTER(phix_opts), ctypes.POINTER(phix_stats)]
+    lib.phix_phi_combination.argtypes = [P, ctypes.POINTER(phix_jop), D, ctypes.POINTER(P), I, P, D, I,
+                                         ctypes.POINTER(phix_opts), ctypes.POINTER(phix_stats)]
+    lib.phix_spectrum.argtypes = [P, ctypes.POINTER(phix_jop), ctypes.POINTER(phix_opts),
+                                  ctypes.POINTER(D), ctypes.POINTER(phix_stats)]
+    for f in (lib.phix_exprb43_step, lib.phix_epirk4s3_step):
+        f.argtypes = [P, ctypes.POINTER(phix_jop), P, D, D, I, ctypes.POINTER(phix_opts),
+                      ctypes.POINTER(D), ctypes.POINTER(phix_stats)]
+    lib.phix_leja_points.argtypes = [ctypes.POINTER(D), I]
+    lib.phix_divided_differences.argtypes = [I, D, D, I, ctypes.POINTER(D)]
+    for name in EXPORTS:
+        fn = getattr(lib, name)
+        if name not in ("phix_opts_default", "phix_version", "phix_last_error"):
+            fn.restype = I
+    _lib = lib
+    return lib
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if not (x.is_cuda and x.dtype.is_floating_point and x.element_size() == 8 and x.is_contiguous()):
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return x.data_ptr()
+
+
+def _check(ctx, st):
+    if st != PHIX_OK:
+        msg = load().phix_last_error(ctx).decode() if ctx else ""
+        raise PhixError(st, msg)
+
+
+def phix_opts_default(**overrides):
+    o = phix_opts()
+    load().phix_opts_default(ctypes.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def phix_version():
+    return load().phix_version()
+
+
+def phix_create(stream=None):
+    """Context on the current device bound to `stream` (torch.cuda.Stream, raw handle or None)."""
+    handle = None
+    if stream is not None:
+        handle = stream if isinstance(stream, int) else stream.cuda_stream
+    ctx = ctypes.c_void_p()
+    _check(None, load().phix_create(ctypes.byref(ctx), handle))
+    return ctx
+
+
+def phix_destroy(ctx):
+    load().phix_destroy(ctx)
+
+
+def phix_last_error(ctx):
+    return load().phix_last_error(ctx).decode()
+
+
+def make_jop(kind, nx, ny, params, state=None):
+    op = phix_jop()
+    op.kind, op.nx, op.ny = kind, nx, ny
+    for i, p in enumerate(params):
+        op.param[i] = p
+    op.state = _ptr(state)
+    return op
+
+
+def phix_phi_action(ctx, op, h, v, l, scale, out, tol, method=PHIX_LEJA, opts=None, check=True):
+    """out[k] = phi_{l[k]}(scale[k] h J) v; returns phix_stats."""
+    n = len(l)
+    st = phix_stats()
+    L = (ctypes.c_int * n)(*l)
+    S = (ctypes.c_double * n)(*scale)
+    O = (ctypes.c_void_p * n)(*[_ptr(o) for o in out])
+    rc = load().phix_phi_action(ctx, ctypes.byref(op), h, _ptr(v), n, L, S, O, tol, method,
+                                ctypes.byref(opts) if opts is not None else None, ctypes.byref(st))
+    if check:
+        _check(ctx, rc)
+    return st
+
+
+def phix_phi_combination(ctx, op, h, b, out, tol, method=PHIX_LEJA, opts=None, check=True):
+    """out = sum_j phi_j(h J) b[j] (b[j] None = 0); returns phix_stats."""
+    p = len(b) - 1
+    st = phix_stats()
+    B = (ctypes.c_void_p * (p + 1))(*[_ptr(x) for x in b])
+    rc = load().phix_phi_combination(ctx, ctypes.byref(op), h, B, p, _ptr(out), tol, method,
+                                     ctypes.byref(opts) if opts is not None else None, ctypes.byref(st))
+    if check:
+        _check(ctx, rc)
+    return st
+
+
+def phix_spectrum(ctx, op, opts=None):
+    rho = ctypes.c_double()
+    st = phix_stats()
+    _check(ctx, load().phix_spectrum(ctx, ctypes.byref(op), ctypes.byref(opts) if opts is not None else None,
+                                     ctypes.byref(rho), ctypes.byref(st)))
+    return rho.value, st
+
+
+def _step(fn, ctx, op, u, h, tol, method, opts, check):
+    err = ctypes.c_double()
+    st = phix_stats()
+    rc = fn(ctx, ctypes.byref(op), _ptr(u), h, tol, method,
+            ctypes.byref(opts) if opts is not None else None, ctypes.byref(err), ctypes.byref(st))
+    if check:
+        _check(ctx, rc)
+    return st
+
+
+def phix_exprb43_step(ctx, op, u, h, tol, method=PHIX_LEJA, opts=None, check=True):
+    """u <- EXPRB43 step (in place); returns phix_stats (err_est = ||u4 - u3||)."""
+    return _step(load().phix_exprb43_step, ctx, op, u, h, tol, method, opts, check)
+
+
+def phix_epirk4s3_step(ctx, op, u, h, tol, method=PHIX_LEJA, opts=None, check=True):
+    return _step(load().phix_epirk4s3_step, ctx, op, u, h, tol, method, opts, check)
+
+
+def phix_leja_points(m):
+    a = (ctypes.c_double * m)()
+    _check(None, load().phix_leja_points(a, m))
+    return list(a)
+
+
+def phix_divided_differences(l, a, b, m):
+    d = (ctypes.c_double * m)()
+    _check(None, load().phix_divided_differences(l, a, b, m, d))
+    return list(d)

@@ -116,3 +116,20 @@ def test_dense_phi_taylor_small_matrix():
             ref += t / math.factorial(k + l)
             t = A @ t
         assert np.allclose(exact.dense_phi(A, l, v), ref, rtol=1e-13, atol=1e-15)
+
+
+def test_rectangular_grid_modes():
+    # on an nx x ny grid, sin(2 pi kx x) sin(2 pi ky y) is an eigenvector of the
+    # centred Laplacian with eigenvalue (2cos(2pi kx dx)-2)/dx^2 + (2cos(2pi ky dy)-2)/dy^2
+    nx, ny, kx, ky = 12, 7, 2, 3
+    x = np.arange(nx) / nx
+    y = np.arange(ny) / ny
+    X, Y = np.meshgrid(x, y, indexing="xy")
+    u = (np.sin(2 * np.pi * kx * X) * np.sin(2 * np.pi * ky * Y)).reshape(-1)
+    lam = (2 * np.cos(2 * np.pi * kx / nx) - 2) * nx * nx + (2 * np.cos(2 * np.pi * ky / ny) - 2) * ny * ny
+    op = AdvDiff(nx, 1.0, 0.0, 0.0, ny=ny)
+    assert np.allclose(op.f(u), lam * u, atol=1e-9 * abs(lam))
+    gs = GrayScott(nx, 1.0, 1.0, 0.0, 0.0, ny=ny)
+    z = np.zeros(nx * ny)
+    f = gs.f(np.concatenate([u, z]))
+    assert np.allclose(f[: nx * ny], lam * u, atol=1e-9 * abs(lam))
