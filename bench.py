@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--clock-ms", type=int, default=200, help="nvidia-smi sampling period (0 = off)")
     return ap.parse_args()
 
 
@@ -60,18 +61,27 @@ class ClockSampler:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
+    def __init__(self, index, period_ms=200):
         self.index = index
+        self.period = period_ms
         self.lines = []
         self.proc = None
 
     def start(self):
+        """Start sampling and wait for the first sample, so that nvidia-smi's
+        own start-up does not fall inside the timed region."""
+        if self.period <= 0:
+            return
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.period)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 10.0:
+                time.sleep(0.05)
+            self.n0 = len(self.lines)
         except (OSError, FileNotFoundError):
             self.proc = None
 
@@ -81,7 +91,7 @@ class ClockSampler:
 
     def stop(self):
         if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["not sampled"]}
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -139,11 +149,11 @@ def run_phix(args, world, rank, local):
         phix.phix_exprb43_step(ctx, op, u, h, tol, phix.PHIX_LEJA, opts)
     u.copy_(torch.tensor(u0, dtype=torch.float64, device="cuda"))
     stats = []
-    sampler = ClockSampler(local)
+    sampler = ClockSampler(local, args.clock_ms)
+    sampler.start()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    sampler.start()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)

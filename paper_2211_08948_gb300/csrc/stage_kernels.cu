@@ -186,12 +186,20 @@ __global__ void k_norm2(size_t n, const double* __restrict__ x, const double* __
     last = (t == gridDim.x - 1);
   }
   __syncthreads();
-  if (last && threadIdx.x == 0) {
-    double tot = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) tot += __ldcg(partials + b);
-    *result = tot;
-    *counter = 0;
-    __threadfence();
+  if (last) {
+    // fixed-order parallel sum of the block partials
+    double t = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += __ldcg(partials + b);
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double tot = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += sw[w];
+      *result = tot;
+      *counter = 0;
+      __threadfence();
+    }
   }
 }
 

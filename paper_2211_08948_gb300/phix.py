@@ -148,11 +148,14 @@ def phix_last_error(ctx):
 
 
 def make_jop(kind, nx, ny, params, state=None):
+    """phix_jop for `kind` on an nx x ny grid; `state` (tensor) is kept alive
+    by the returned object so its device memory stays valid."""
     op = phix_jop()
     op.kind, op.nx, op.ny = kind, nx, ny
     for i, p in enumerate(params):
         op.param[i] = p
     op.state = _ptr(state)
+    op._keepalive = state
     return op
 
 

@@ -44,7 +44,8 @@ def _prec(phix, name):
 
 
 def _run_action(phix, ctx, kind, nx, ny, params, state, v, h, outs, tol, prec, **opt):
-    op = phix.make_jop(kind, nx, ny, params, dev(state) if state is not None else None)
+    sd = dev(state) if state is not None else None
+    op = phix.make_jop(kind, nx, ny, params, sd)
     o = phix.phix_opts_default(prec=_prec(phix, prec), **opt)
     vd = dev(v)
     od = [torch.empty_like(vd) for _ in outs]
