@@ -53,7 +53,9 @@ typedef enum {
   PHIX_ENAN = 3,      /* a norm became NaN/Inf                              */
   PHIX_ETIMEOUT = 4,  /* a bounded device wait expired                      */
   PHIX_ECUDA = 5,     /* a CUDA runtime call failed                         */
-  PHIX_ENOMEM = 6     /* workspace allocation failed                        */
+  PHIX_ENOMEM = 6,    /* workspace allocation failed                        */
+  PHIX_ETOOBIG = 7    /* phix_phi_action_noalloc: the problem does not fit its
+                         fixed scratch (PHIX_NOALLOC_SCRATCH_BYTES)           */
 } phix_status;
 
 typedef enum { PHIX_LEJA = 0, PHIX_KIOPS = 1 } phix_method;
@@ -184,6 +186,40 @@ phix_status phix_exprb43_step(phix_ctx* ctx, const phix_jop* op, double* u_inout
 phix_status phix_epirk4s3_step(phix_ctx* ctx, const phix_jop* op, double* u_inout, double h,
                                double tol, phix_method method, const phix_opts* opts,
                                double* err_est, phix_stats* stats);
+
+/* No counterpart in the paper: a library-interface addition.
+ *
+ * phix_phi_action_noalloc: the same vertical Leja computation as
+ * phix_phi_action with PHIX_LEJA, for callers that cannot allocate device
+ * memory: a host application that gives the whole device to its own memory
+ * pool and forbids outside allocations, a code under a hard device-memory
+ * budget, or a latency-critical loop that cannot pay the device-wide
+ * synchronisation an allocation may cause.  It takes no context and calls no
+ * cudaMalloc/cudaFree or other allocating routine.  Its scratch (control
+ * block, reduction partials, Newton basis, accumulators, Jacobian state
+ * arrays) is one fixed array of PHIX_NOALLOC_SCRATCH_BYTES in device memory,
+ * held by every GPU that loads the library until the process exits.
+ *   - Limits: N * e * (2 + nout) + state planes + 80 KiB <= 32 MiB, with
+ *     e = 8 bytes (PHIX_FP64, PHIX_DF64, PHIX_FP32_JV) or 4 (PHIX_FP32); e.g.
+ *     Gray-Scott up to 512 x 512 with nout = 4 in double-float.  Larger
+ *     problems return PHIX_ETOOBIG.  opts->m_max <= PHIX_NOALLOC_MMAX.  Only
+ *     one vertical pass: an action that would need substeps (gamma_cap,
+ *     iota_cap) returns PHIX_EINVAL.
+ *   - The first call on a device sets that device up (looks up the scratch's
+ *     device address); make that first call before any stream capture.
+ *   - Every call, on any stream, shares the one scratch array, which keeps
+ *     the last call's contents (the call clears what must start at zero):
+ *     calls that overlap on the GPU race and give wrong results.  Issue them
+ *     one after another (the call synchronises `cuda_stream` before return).
+ *   - Arguments as phix_phi_action; cuda_stream is a cudaStream_t (NULL =
+ *     legacy default stream); stats may be NULL.  No message string: the
+ *     return value (also stats->status) is the error.                       */
+#define PHIX_NOALLOC_SCRATCH_BYTES (32u << 20)
+#define PHIX_NOALLOC_MMAX 1000
+phix_status phix_phi_action_noalloc(const phix_jop* op, double h, const double* v, int nout,
+                                    const int* l, const double* scale, double* const* out,
+                                    double tol, const phix_opts* opts, void* cuda_stream,
+                                    phix_stats* stats);
 
 /* Host utility: the first m real Leja points on [-2, 2] (xi_0 = 2,
  * xi_1 = -2, xi_2 = 0, then greedy max-product), Sec. 2.2.  xi is a HOST

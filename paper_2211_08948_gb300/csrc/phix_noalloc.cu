@@ -1,0 +1,294 @@
+// phix_phi_action_noalloc: the Leja phi-action for callers that cannot
+// allocate device memory.
+//
+// Some callers may not call cudaMalloc or any allocating routine: a host
+// application that hands the whole device to its own memory pool and forbids
+// outside allocations, a code running under a hard device-memory budget, or a
+// latency-critical loop that cannot afford the device-wide synchronisation an
+// allocation may cause.  This entry point creates no context and allocates
+// nothing: its scratch (control block, reduction partials, the Newton basis
+// pair, the accumulators and the Jacobian state arrays) lives in the fixed
+// file-scope array below, which every GPU that loads the library holds until
+// the process exits.  The caller still provides the input and output vectors.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "phix_internal.h"
+
+using namespace phix;
+
+namespace {
+
+// The scratch itself.  In host code `noalloc_scratch` names a host-side
+// stand-in, not device memory: kernels must be given the device address
+// obtained from cudaGetSymbolAddress (below), never the symbol itself.
+__device__ __align__(256) unsigned char noalloc_scratch[PHIX_NOALLOC_SCRATCH_BYTES];
+
+constexpr int MAX_DEVICES = 64;
+constexpr int MAX_GRID = 2048;
+constexpr size_t CTL_BYTES = 256;
+constexpr size_t PARTIAL_BYTES = sizeof(double) * MAX_GRID * (KMAX + 1);
+
+struct DeviceSetup {
+  bool done = false;
+  unsigned char* scratch = nullptr;  // device address of noalloc_scratch
+  int nsm = 0;
+};
+DeviceSetup g_setup[MAX_DEVICES];
+std::mutex g_mu;
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Once per device, with that device current: the scratch's device address.
+phix_status setup_device(int dev, DeviceSetup** out) {
+  if (dev < 0 || dev >= MAX_DEVICES) return PHIX_EINVAL;
+  std::lock_guard<std::mutex> lk(g_mu);
+  DeviceSetup& s = g_setup[dev];
+  if (!s.done) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, noalloc_scratch) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return PHIX_ECUDA;
+    }
+    int nsm = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return PHIX_ECUDA;
+    }
+    (void)leja_table(PHIX_NOALLOC_MMAX + 1);  // host Leja table built once here
+    s.scratch = static_cast<unsigned char*>(p);
+    s.nsm = nsm;
+    s.done = true;
+  }
+  *out = &s;
+  return PHIX_OK;
+}
+
+struct Ctl {
+  cudaStream_t st;
+  LejaCtl* ctl;
+  LejaCtl h;  // pageable host copy (no pinned allocation)
+};
+
+bool read_ctl(Ctl& c) {
+  if (cudaMemcpyAsync(&c.h, c.ctl, sizeof(LejaCtl), cudaMemcpyDeviceToHost, c.st) != cudaSuccess) return false;
+  return cudaStreamSynchronize(c.st) == cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" phix_status phix_phi_action_noalloc(const phix_jop* op, double h, const double* v, int nout,
+                                               const int* l, const double* scale, double* const* out,
+                                               double tol, const phix_opts* opts, void* cuda_stream,
+                                               phix_stats* stats) {
+  phix_stats st;
+  std::memset(&st, 0, sizeof st);
+  auto finish = [&](phix_status rc) {
+    st.status = rc;
+    if (stats) *stats = st;
+    return rc;
+  };
+  // ---- arguments ---------------------------------------------------------
+  if (!op || !v || !l || !scale || !out || nout < 1 || nout > KMAX) return finish(PHIX_EINVAL);
+  if (op->kind < 0 || op->kind > 2 || op->nx < 3 || op->ny < 3) return finish(PHIX_EINVAL);
+  if (op->kind != PHIX_OP_ADVDIFF && !op->state) return finish(PHIX_EINVAL);
+  if (!(h > 0) || !std::isfinite(h) || !(tol > 0)) return finish(PHIX_EINVAL);
+  phix_opts o;
+  phix_opts_default(&o);
+  if (opts) o = *opts;
+  if (o.prec < PHIX_FP64 || o.prec > PHIX_FP32 || o.m_max < 1 || o.m_max > PHIX_NOALLOC_MMAX || o.m_min < 0 ||
+      !(o.safety > 0) || o.power_max_it < 1)
+    return finish(PHIX_EINVAL);
+  for (int k = 0; k < nout; ++k) {
+    if (l[k] < 0 || l[k] > 8 || !(scale[k] > 0) || !out[k] || out[k] == v) return finish(PHIX_EINVAL);
+  }
+  const int prec = o.prec;
+  const int ncomp = op->kind == PHIX_OP_GRAYSCOTT ? 2 : 1;
+  const size_t plane = (size_t)op->nx * op->ny;
+  const size_t N = plane * ncomp;
+  const size_t eb = prec == P_FP32 ? 4 : 8;
+  const size_t sb = (prec == P_FP64 || prec == P_DF64) ? 8 : 4;
+  const size_t st_planes = op->kind == PHIX_OP_GRAYSCOTT ? 2 : (op->kind == PHIX_OP_BURGERS ? 1 : 0);
+  // scratch layout: control block | partials | y0 | y1 | p_0..p_{K-1} | state planes
+  const size_t vec = align256(N * eb);
+  const size_t need = CTL_BYTES + align256(PARTIAL_BYTES) + (2 + (size_t)nout) * vec + align256(st_planes * plane * sb);
+  if (need > (size_t)PHIX_NOALLOC_SCRATCH_BYTES) return finish(PHIX_ETOOBIG);
+
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return finish(PHIX_ECUDA);
+  DeviceSetup* ds = nullptr;
+  phix_status rc = setup_device(dev, &ds);
+  if (rc != PHIX_OK) return finish(rc);
+
+  unsigned char* base = ds->scratch;
+  Ctl c;
+  c.st = static_cast<cudaStream_t>(cuda_stream);
+  c.ctl = reinterpret_cast<LejaCtl*>(base);
+  double* partials = reinterpret_cast<double*>(base + CTL_BYTES);
+  unsigned char* q = base + CTL_BYTES + align256(PARTIAL_BYTES);
+  void* y[2] = {q, q + vec};
+  void* p[KMAX] = {};
+  for (int k = 0; k < nout; ++k) p[k] = q + (2 + k) * vec;
+  void* stp = st_planes ? (void*)(q + (2 + nout) * vec) : nullptr;
+  const int grid = std::min(MAX_GRID, ds->nsm * 4);
+  const int grid_stream = grid;
+
+  // ---- operator coefficients ---------------------------------------------
+  const double idx2 = (double)op->nx * op->nx, idy2 = (double)op->ny * op->ny;
+  const double* pa = op->param;
+  double kJ[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int nscaled = 5;
+  if (op->kind == PHIX_OP_ADVDIFF) {
+    kJ[0] = pa[0] * idx2 + 0.5 * pa[1] * op->nx;
+    kJ[1] = pa[0] * idx2 - 0.5 * pa[1] * op->nx;
+    kJ[2] = pa[0] * idy2 + 0.5 * pa[2] * op->ny;
+    kJ[3] = pa[0] * idy2 - 0.5 * pa[2] * op->ny;
+    kJ[4] = -2.0 * pa[0] * (idx2 + idy2);
+  } else if (op->kind == PHIX_OP_GRAYSCOTT) {
+    kJ[0] = pa[0] * idx2;
+    kJ[1] = pa[0] * idy2;
+    kJ[2] = -2.0 * pa[0] * (idx2 + idy2) - pa[2];
+    kJ[3] = pa[1] * idx2;
+    kJ[4] = pa[1] * idy2;
+    kJ[5] = -2.0 * pa[1] * (idx2 + idy2) - (pa[2] + pa[3]);
+    nscaled = 6;
+  } else {
+    kJ[0] = pa[0] * idx2;
+    kJ[1] = pa[0] * idy2;
+    kJ[2] = -2.0 * pa[0] * (idx2 + idy2);
+    kJ[3] = 0.5 * op->nx;
+    kJ[4] = 0.5 * op->ny;
+    nscaled = 3;
+  }
+  auto ok = [&](cudaError_t e) {
+    st.launches++;
+    return e == cudaSuccess;
+  };
+  if (st_planes && !ok(launch_prep_state(prec, op->kind, op->nx, op->ny, op->state, stp, grid_stream, c.st)))
+    return finish(PHIX_ECUDA);
+
+  // ---- spectral interval -------------------------------------------------
+  double alpha_i, beta_i;
+  if (o.rho_re > 0) {
+    alpha_i = -o.rho_re;
+    beta_i = o.rho_hi;
+    st.rho = o.rho_re;
+  } else {
+    if (cudaMemsetAsync(c.ctl, 0, sizeof(LejaCtl), c.st) != cudaSuccess) return finish(PHIX_ECUDA);
+    if (!ok(launch_power_start(prec, N, o.power_seed, y[0], c.ctl, partials, grid, c.st))) return finish(PHIX_ECUDA);
+    IterLaunch L{};
+    L.prec = prec;
+    L.op = op->kind;
+    L.mode = MODE_POWER;
+    L.m_max = o.power_max_it;
+    L.nx = op->nx;
+    L.ny = op->ny;
+    L.st = stp;
+    L.ctl = c.ctl;
+    L.partials = partials;
+    L.rel = o.power_rel;
+    L.grid = grid;
+    for (int j = 0; j < 8; ++j) L.k[j] = kJ[j];
+    L.ga = 1.0;
+    int launched = 0, target = std::min(o.power_max_it, 16);
+    for (;;) {
+      for (int m = launched + 1; m <= target; ++m) {
+        L.m = m;
+        L.y_in = y[(m - 1) & 1];
+        L.y_out = y[m & 1];
+        if (!ok(launch_iter(L, c.st))) return finish(PHIX_ECUDA);
+      }
+      launched = target;
+      if (!read_ctl(c)) return finish(PHIX_ECUDA);
+      if (c.h.done || launched >= o.power_max_it) break;
+      target = std::min(o.power_max_it, launched + 8);
+    }
+    if (c.h.status == PHIX_ENAN) return finish(PHIX_ENAN);
+    st.power_mv = c.h.iters;
+    st.rho = c.h.rho;
+    alpha_i = -o.safety * c.h.rho;
+    beta_i = 0.0;
+  }
+  const double cc = 0.5 * (alpha_i + beta_i), gamma = 0.25 * (beta_i - alpha_i);
+  if (gamma == 0.0) return finish(PHIX_EINVAL);
+  // one vertical pass only: a substepped action needs more vectors than the scratch holds
+  for (int k = 0; k < nout; ++k) {
+    double s_re = o.gamma_cap > 0 ? scale[k] * h * gamma / o.gamma_cap : 0.0;
+    double s_im = (o.iota_cap > 0 && o.rho_im > 0) ? scale[k] * h * o.rho_im / o.iota_cap : 0.0;
+    if (s_re > 1.0 + 1e-12 || s_im > 1.0 + 1e-12) return finish(PHIX_EINVAL);
+  }
+
+  // ---- divided differences (host, on the stack) ---------------------------
+  const int M = o.m_max + 1;
+  const double* xi = leja_table(M);
+  double d[KMAX][PHIX_NOALLOC_MMAX + 1];
+  for (int k = 0; k < nout; ++k) {
+    const double a0 = scale[k] * h * cc, b0 = scale[k] * h * gamma;
+    for (int i = 0; i < M; ++i) d[k][i] = phi_host(l[k], a0 + b0 * xi[i]);
+    divided_differences_host(xi, d[k], M);
+  }
+
+  // ---- Newton-Leja pass ----------------------------------------------------
+  if (cudaMemsetAsync(c.ctl, 0, sizeof(LejaCtl), c.st) != cudaSuccess) return finish(PHIX_ECUDA);
+  if (!ok(launch_scale(v, N, c.ctl, partials, grid, c.st))) return finish(PHIX_ECUDA);
+  InitLaunch IL{};
+  IL.prec = prec;
+  IL.ncomp = ncomp;
+  IL.K = nout;
+  IL.m_min = o.m_min;
+  IL.m_max = o.m_max;
+  IL.nx = op->nx;
+  IL.ny = op->ny;
+  IL.v = v;
+  IL.y0 = y[0];
+  for (int k = 0; k < nout; ++k) {
+    IL.p[k] = p[k];
+    IL.dk[k] = d[k][0];
+  }
+  IL.ctl = c.ctl;
+  IL.partials = partials;
+  IL.tol = tol;
+  IL.grid = grid;
+  if (!ok(launch_init(IL, c.st))) return finish(PHIX_ECUDA);
+  IterLaunch L{};
+  L.prec = prec;
+  L.op = op->kind;
+  L.mode = MODE_NEWTON;
+  L.K = nout;
+  L.m_min = o.m_min;
+  L.m_max = o.m_max;
+  L.nx = op->nx;
+  L.ny = op->ny;
+  for (int k = 0; k < nout; ++k) L.p[k] = p[k];
+  L.st = stp;
+  L.ctl = c.ctl;
+  L.partials = partials;
+  L.tol = tol;
+  L.grid = grid;
+  const double al = 1.0 / gamma;
+  for (int j = 0; j < 8; ++j) L.k[j] = j < nscaled ? al * kJ[j] : kJ[j];
+  L.ga = al;
+  int launched = 0, target = std::min(o.m_max, 32);
+  for (;;) {
+    for (int m = launched + 1; m <= target; ++m) {
+      L.m = m;
+      L.y_in = y[(m - 1) & 1];
+      L.y_out = y[m & 1];
+      L.beta = -(cc / gamma + xi[m - 1]);
+      for (int k = 0; k < nout; ++k) L.dk[k] = d[k][m];
+      if (!ok(launch_iter(L, c.st))) return finish(PHIX_ECUDA);
+    }
+    launched = target;
+    if (!read_ctl(c)) return finish(PHIX_ECUDA);
+    if (c.h.done || launched >= o.m_max) break;
+    target = std::min(o.m_max, launched + 8);
+  }
+  if (!ok(launch_finalize(prec, N, nout, p, out, c.ctl, grid_stream, c.st))) return finish(PHIX_ECUDA);
+  if (cudaStreamSynchronize(c.st) != cudaSuccess) return finish(PHIX_ECUDA);
+  st.iters = c.h.iters;
+  st.jv = c.h.iters;
+  st.passes = 1;
+  st.substeps = 1;
+  return finish(c.h.done ? (phix_status)c.h.status : PHIX_ENOTCONV);
+}

@@ -12,8 +12,11 @@ import os
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libphix.so")
 
-PHIX_OK, PHIX_EINVAL, PHIX_ENOTCONV, PHIX_ENAN, PHIX_ETIMEOUT, PHIX_ECUDA, PHIX_ENOMEM = range(7)
-STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOTCONV", 3: "ENAN", 4: "ETIMEOUT", 5: "ECUDA", 6: "ENOMEM"}
+PHIX_OK, PHIX_EINVAL, PHIX_ENOTCONV, PHIX_ENAN, PHIX_ETIMEOUT, PHIX_ECUDA, PHIX_ENOMEM, PHIX_ETOOBIG = range(8)
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOTCONV", 3: "ENAN", 4: "ETIMEOUT", 5: "ECUDA", 6: "ENOMEM",
+                7: "ETOOBIG"}
+PHIX_NOALLOC_SCRATCH_BYTES = 32 << 20
+PHIX_NOALLOC_MMAX = 1000
 PHIX_LEJA, PHIX_KIOPS = 0, 1
 PHIX_FP64, PHIX_DF64, PHIX_FP32_JV, PHIX_FP32 = 0, 1, 2, 3
 PHIX_OP_ADVDIFF, PHIX_OP_GRAYSCOTT, PHIX_OP_BURGERS = 0, 1, 2
@@ -22,7 +25,7 @@ PHIX_OP_ADVDIFF, PHIX_OP_GRAYSCOTT, PHIX_OP_BURGERS = 0, 1, 2
 EXPORTS = [
     "phix_opts_default", "phix_version", "phix_create", "phix_destroy", "phix_last_error",
     "phix_phi_action", "phix_phi_combination", "phix_spectrum", "phix_exprb43_step",
-    "phix_epirk4s3_step", "phix_leja_points", "phix_divided_differences",
+    "phix_epirk4s3_step", "phix_leja_points", "phix_divided_differences", "phix_phi_action_noalloc",
 ]
 
 
@@ -91,6 +94,9 @@ def load(path=None):
     for f in (lib.phix_exprb43_step, lib.phix_epirk4s3_step):
         f.argtypes = [P, ctypes.POINTER(phix_jop), P, D, D, I, ctypes.POINTER(phix_opts),
                       ctypes.POINTER(D), ctypes.POINTER(phix_stats)]
+    lib.phix_phi_action_noalloc.argtypes = [ctypes.POINTER(phix_jop), D, P, I, ctypes.POINTER(I),
+                                            ctypes.POINTER(D), ctypes.POINTER(P), D,
+                                            ctypes.POINTER(phix_opts), P, ctypes.POINTER(phix_stats)]
     lib.phix_leja_points.argtypes = [ctypes.POINTER(D), I]
     lib.phix_divided_differences.argtypes = [I, D, D, I, ctypes.POINTER(D)]
     for name in EXPORTS:
@@ -170,6 +176,26 @@ def phix_phi_action(ctx, op, h, v, l, scale, out, tol, method=PHIX_LEJA, opts=No
                                 ctypes.byref(opts) if opts is not None else None, ctypes.byref(st))
     if check:
         _check(ctx, rc)
+    return st
+
+
+def phix_phi_action_noalloc(op, h, v, l, scale, out, tol, opts=None, stream=None, check=True):
+    """Context-free Leja action whose scratch is the library's fixed device
+    array (no device allocation); returns phix_stats.  Calls must not overlap
+    on the GPU: they share that array."""
+    n = len(l)
+    st = phix_stats()
+    L = (ctypes.c_int * n)(*l)
+    S = (ctypes.c_double * n)(*scale)
+    O = (ctypes.c_void_p * n)(*[_ptr(o) for o in out])
+    handle = None
+    if stream is not None:
+        handle = stream if isinstance(stream, int) else stream.cuda_stream
+    rc = load().phix_phi_action_noalloc(ctypes.byref(op), h, _ptr(v), n, L, S, O, tol,
+                                        ctypes.byref(opts) if opts is not None else None, handle,
+                                        ctypes.byref(st))
+    if check and rc != PHIX_OK:
+        raise PhixError(rc, "phix_phi_action_noalloc failed")
     return st
 
 
