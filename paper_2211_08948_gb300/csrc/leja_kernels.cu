@@ -16,6 +16,7 @@
 // 2D periodic grid, 32 x 8 thread tiles, V = 2 consecutive x points per
 // thread (16-byte loads) when nx is even, grid-stride over tiles.
 #include <cstdio>
+#include <cstring>
 #include <type_traits>
 
 #include "phix_internal.h"
@@ -283,11 +284,65 @@ __device__ __forceinline__ CJ stencil_burgers(const CJ (&k)[8], CJ ga, CJ e, CJ 
 }
 
 // ---------------------------------------------------------------------------
+// Kernel arguments (identical for every launch of a chain) and parameter access
+// ---------------------------------------------------------------------------
+struct IterDev {
+  const void* y[2];
+  void* p[KMAX];
+  const void* st;
+  LejaCtl* ctl;
+  double* partials;
+  const unsigned char* ptab;
+  int nx, ny, ntiles, tiles_x;
+};
+
+__device__ __forceinline__ const PassParams* pp_of(const unsigned char* t) {
+  return reinterpret_cast<const PassParams*>(t);
+}
+__device__ __forceinline__ const double* beta_d_of(const unsigned char* t, int M) {
+  return reinterpret_cast<const double*>(t + sizeof(PassParams));
+}
+__device__ __forceinline__ const float2* beta_f_of(const unsigned char* t, int M) {
+  return reinterpret_cast<const float2*>(t + sizeof(PassParams) + 8 * (size_t)M);
+}
+__device__ __forceinline__ const double* dk_d_of(const unsigned char* t, int M) {
+  return reinterpret_cast<const double*>(t + sizeof(PassParams) + 16 * (size_t)M);
+}
+__device__ __forceinline__ const float2* dk_f_of(const unsigned char* t, int M) {
+  return reinterpret_cast<const float2*>(t + sizeof(PassParams) + 16 * (size_t)M + 8 * (size_t)KMAX * M);
+}
+
+// a coefficient in the arithmetic X, from its float64 / double-float forms
+template <typename X>
+__device__ __forceinline__ X coef(double d, float2 f);
+template <>
+__device__ __forceinline__ double coef<double>(double d, float2) { return d; }
+template <>
+__device__ __forceinline__ df coef<df>(double, float2 f) { return df_make(f.x, f.y); }
+template <>
+__device__ __forceinline__ float coef<float>(double, float2 f) { return f.x; }
+
+// centre-coefficient indices that the Newton shift beta is folded into
+template <int OP>
+struct Centre;
+template <>
+struct Centre<PHIX_OP_ADVDIFF> {
+  static constexpr int a = 4, b = -1;
+};
+template <>
+struct Centre<PHIX_OP_GRAYSCOTT> {
+  static constexpr int a = 2, b = 5;
+};
+template <>
+struct Centre<PHIX_OP_BURGERS> {
+  static constexpr int a = 2, b = -1;
+};
+
+// ---------------------------------------------------------------------------
 // The iteration kernel.
 // ---------------------------------------------------------------------------
 template <int P, int OP, int V, int MODE>
-__global__ void __launch_bounds__(THREADS)
-    k_iter(IterArgs<typename Tr<P>::CJ, typename Tr<P>::C> a) {
+__global__ void __launch_bounds__(THREADS) k_iter(IterDev a) {
   using T = typename Tr<P>::T;
   using C = typename Tr<P>::C;
   using CJ = typename Tr<P>::CJ;
@@ -295,11 +350,32 @@ __global__ void __launch_bounds__(THREADS)
   using Acc = typename std::conditional<MODE == MODE_NEWTON, typename Tr<P>::AccN,
                                         typename Tr<P>::AccP>::type;
   constexpr int NC = (OP == PHIX_OP_GRAYSCOTT) ? 2 : 1;
+  // FP32_JV keeps the stencil in float32 and the shift in double-float: no folding
+  constexpr bool FOLD = (MODE == MODE_NEWTON) && std::is_same<C, CJ>::value;
 
   if (__ldcg(&a.ctl->done)) return;  // the chain already stopped
+  const int m = __ldcg(&a.ctl->m);
+  const PassParams* pp = pp_of(a.ptab);
+  const int M = pp->M;
+  const int K = (MODE == MODE_NEWTON) ? pp->K : 0;
 
+  CJ kk[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) kk[j] = coef<CJ>(pp->kd[j], pp->kf[j]);
+  const CJ ga = coef<CJ>(pp->gad, pp->gaf);
+  C beta{};
+  C dk[KMAX];
   C alpha_pw{};
-  if (MODE == MODE_POWER) {
+  if (MODE == MODE_NEWTON) {
+    beta = coef<C>(beta_d_of(a.ptab, M)[m], beta_f_of(a.ptab, M)[m]);
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k)
+      dk[k] = (k < K) ? coef<C>(dk_d_of(a.ptab, M)[k * M + m], dk_f_of(a.ptab, M)[k * M + m]) : C{};
+    if constexpr (FOLD) {
+      kk[Centre<OP>::a] = kk[Centre<OP>::a] + from_cj(beta, CJ());
+      if constexpr (Centre<OP>::b >= 0) kk[Centre<OP>::b] = kk[Centre<OP>::b] + from_cj(beta, CJ());
+    }
+  } else {
     if constexpr (P == P_FP64) {
       alpha_pw = __ldcg(&a.ctl->alpha);
     } else if constexpr (P == P_FP32) {
@@ -313,14 +389,11 @@ __global__ void __launch_bounds__(THREADS)
 #pragma unroll
   for (int j = 0; j <= KMAX; ++j) acc[j] = acc_zero<Acc>();
 
-  const T* __restrict__ yin = static_cast<const T*>(a.y_in);
-  T* __restrict__ yout = static_cast<T*>(a.y_out);
+  const T* __restrict__ yin = static_cast<const T*>(a.y[(m - 1) & 1]);
+  T* __restrict__ yout = static_cast<T*>(const_cast<void*>(a.y[m & 1]));
   const S* __restrict__ st = static_cast<const S*>(a.st);
   const int nx = a.nx, ny = a.ny;
   const size_t plane = (size_t)nx * ny;
-  CJ kk[8];
-#pragma unroll
-  for (int j = 0; j < 8; ++j) kk[j] = a.k[j];
 
   for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
     const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
@@ -354,7 +427,6 @@ __global__ void __launch_bounds__(THREADS)
     C out[NC][V];
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-      // neighbours of point ix+v
       CJ J[NC];
       if constexpr (OP == PHIX_OP_ADVDIFF) {
         C e = (v == V - 1) ? ea[0] : c[0][v + 1];
@@ -368,7 +440,7 @@ __global__ void __launch_bounds__(THREADS)
         C wv = (v == 0) ? we[NC - 1] : c[NC - 1][v - 1];
         CJ g1 = to_cj(cv(__ldg(st + row + ix + v)), CJ());
         CJ g2 = to_cj(cv(__ldg(st + plane + row + ix + v)), CJ());
-        stencil_gs<CJ>(kk, a.ga, to_cj(eu, CJ()), to_cj(wu, CJ()), to_cj(nn[0][v], CJ()),
+        stencil_gs<CJ>(kk, ga, to_cj(eu, CJ()), to_cj(wu, CJ()), to_cj(nn[0][v], CJ()),
                        to_cj(ss[0][v], CJ()), to_cj(c[0][v], CJ()), to_cj(ev, CJ()),
                        to_cj(wv, CJ()), to_cj(nn[NC - 1][v], CJ()), to_cj(ss[NC - 1][v], CJ()),
                        to_cj(c[NC - 1][v], CJ()), g1, g2, J[0], J[NC - 1]);
@@ -383,13 +455,16 @@ __global__ void __launch_bounds__(THREADS)
         CJ Uw = to_cj(cv(__ldg(st + row + vxm)), CJ());
         CJ Un = to_cj(cv(__ldg(st + rowp + vx)), CJ());
         CJ Us = to_cj(cv(__ldg(st + rowm + vx)), CJ());
-        J[0] = stencil_burgers<CJ>(kk, a.ga, to_cj(e, CJ()), to_cj(w, CJ()), to_cj(nn[0][v], CJ()),
+        J[0] = stencil_burgers<CJ>(kk, ga, to_cj(e, CJ()), to_cj(w, CJ()), to_cj(nn[0][v], CJ()),
                                    to_cj(ss[0][v], CJ()), to_cj(c[0][v], CJ()), Ue, Uw, Un, Us, Uc);
       }
 #pragma unroll
       for (int q = 0; q < NC; ++q) {
-        if (MODE == MODE_NEWTON) {
-          out[q][v] = from_cj(J[q], C()) + a.beta * c[q][v];
+        if constexpr (MODE == MODE_NEWTON) {
+          if constexpr (FOLD)
+            out[q][v] = from_cj(J[q], C());
+          else
+            out[q][v] = from_cj(J[q], C()) + beta * c[q][v];
         } else {
           out[q][v] = alpha_pw * from_cj(J[q], C());
         }
@@ -410,20 +485,20 @@ __global__ void __launch_bounds__(THREADS)
       if (MODE == MODE_NEWTON) {
 #pragma unroll
         for (int kq = 0; kq < KMAX; ++kq) {
-          if (kq < a.K) {
-            T* pp = static_cast<T*>(a.p[kq]) + q * plane + row + ix;
+          if (kq < K) {
+            T* pp2 = static_cast<T*>(a.p[kq]) + q * plane + row + ix;
             C p0, p1;
             if constexpr (V == 2) {
-              ldw2(pp, p0, p1);
-              p0 = p0 + a.dk[kq] * out[q][0];
-              p1 = p1 + a.dk[kq] * out[q][1];
-              st2(pp, p0, p1);
+              ldw2(pp2, p0, p1);
+              p0 = p0 + dk[kq] * out[q][0];
+              p1 = p1 + dk[kq] * out[q][1];
+              st2(pp2, p0, p1);
               acc_sq(acc[1 + kq], p0);
               acc_sq(acc[1 + kq], p1);
             } else {
-              p0 = ldw1(pp);
-              p0 = p0 + a.dk[kq] * out[q][0];
-              st1(pp, p0);
+              p0 = ldw1(pp2);
+              p0 = p0 + dk[kq] * out[q][0];
+              st1(pp2, p0);
               acc_sq(acc[1 + kq], p0);
             }
           }
@@ -439,21 +514,23 @@ __global__ void __launch_bounds__(THREADS)
     if (tid == 0) {
       LejaCtl* ctl = a.ctl;
       if (MODE == MODE_NEWTON) {
-        leja_test(ctl, a.m, a.K, a.m_min, a.m_max, a.tol, a.dkd, tot);
+        double dkd[KMAX];
+        for (int k = 0; k < K; ++k) dkd[k] = dk_d_of(a.ptab, M)[k * M + m];
+        leja_test(ctl, m, K, pp->m_min, pp->m_max, pp->tol, dkd, tot);
       } else {
         // power iteration: y_k = J v_{k-1}, v_{k-1} unit  =>  rho_k = ||y_k||
         double rho = sqrt(tot[0]);
         double prev = ctl->rho;
         ctl->rho_prev = prev;
         ctl->rho = rho;
-        ctl->iters = a.m;
+        ctl->iters = m;
         if (!isfinite(rho)) {
           ctl->status = PHIX_ENAN;
           ctl->done = 1;
         } else if (rho == 0.0) {
           ctl->status = PHIX_OK;
           ctl->done = 1;
-        } else if ((a.m >= 2 && fabs(rho - prev) <= a.rel * rho) || a.m >= a.m_max) {
+        } else if ((m >= 2 && fabs(rho - prev) <= pp->rel * rho) || m >= pp->m_max) {
           ctl->status = PHIX_OK;
           ctl->done = 1;
         }
@@ -463,6 +540,7 @@ __global__ void __launch_bounds__(THREADS)
         ctl->alpha_hi = ah;
         ctl->alpha_lo = (float)(al - (double)ah);
       }
+      ctl->m = m + 1;
       ctl->count = 0;
       __threadfence();
     }
@@ -470,14 +548,20 @@ __global__ void __launch_bounds__(THREADS)
 }
 
 // ---------------------------------------------------------------------------
-// init: y0 = v / sigma, p_k = d_k[0] y0, norms, test at m = 0
+// init: y0 = v / sigma, p_k = d_k[0] y0, norms, test at m = 0, ctl->m = 1
 // ---------------------------------------------------------------------------
 template <int P>
 __global__ void __launch_bounds__(THREADS)
-    k_init(const double* __restrict__ v, typename Tr<P>::T* __restrict__ y0, IterArgs<typename Tr<P>::CJ, typename Tr<P>::C> a, size_t n) {
+    k_init(const double* __restrict__ v, typename Tr<P>::T* __restrict__ y0, IterDev a, size_t n) {
   using T = typename Tr<P>::T;
   using C = typename Tr<P>::C;
   using Acc = typename Tr<P>::AccN;
+  const PassParams* pp = pp_of(a.ptab);
+  const int M = pp->M, K = pp->K;
+  C dk[KMAX];
+#pragma unroll
+  for (int k = 0; k < KMAX; ++k)
+    dk[k] = (k < K) ? coef<C>(dk_d_of(a.ptab, M)[k * M], dk_f_of(a.ptab, M)[k * M]) : C{};
   Acc acc[KMAX + 1];
 #pragma unroll
   for (int j = 0; j <= KMAX; ++j) acc[j] = acc_zero<Acc>();
@@ -499,8 +583,8 @@ __global__ void __launch_bounds__(THREADS)
     acc_sq(acc[0], y);
 #pragma unroll
     for (int k = 0; k < KMAX; ++k) {
-      if (k < a.K) {
-        C p = a.dk[k] * y;
+      if (k < K) {
+        C p = dk[k] * y;
         st1(static_cast<T*>(a.p[k]) + i, p);
         acc_sq(acc[1 + k], p);
       }
@@ -510,7 +594,10 @@ __global__ void __launch_bounds__(THREADS)
     double tot[KMAX + 1];
     reduce_partials<KMAX + 1>(a.partials, tot);
     if (threadIdx.x == 0 && threadIdx.y == 0) {
-      if (!a.ctl->done) leja_test(a.ctl, 0, a.K, a.m_min, a.m_max, a.tol, a.dkd, tot);
+      double dkd[KMAX];
+      for (int k = 0; k < K; ++k) dkd[k] = dk_d_of(a.ptab, M)[k * M];
+      if (!a.ctl->done) leja_test(a.ctl, 0, K, pp->m_min, pp->m_max, pp->tol, dkd, tot);
+      a.ctl->m = 1;
       a.ctl->count = 0;
       __threadfence();
     }
@@ -612,6 +699,7 @@ __global__ void __launch_bounds__(THREADS)
       ctl->alpha_hi = ah;
       ctl->alpha_lo = (float)(al - (double)ah);
       ctl->rho = 0.0;
+      ctl->m = 1;
       ctl->count = 0;
       __threadfence();
     }
@@ -653,102 +741,149 @@ __global__ void __launch_bounds__(THREADS)
 // ---------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------
-static inline double to_c(double x, double) { return x; }
-static inline df to_c(double x, df) { return df_from_double(x); }
-static inline float to_c(double x, float) { return (float)x; }
+size_t ptab_bytes(int M) { return sizeof(PassParams) + 16 * (size_t)M + 16 * (size_t)KMAX * M; }
 
-template <int P>
-static IterArgs<typename Tr<P>::CJ, typename Tr<P>::C> make_args(const IterLaunch& L) {
-  using C = typename Tr<P>::C;
-  using CJ = typename Tr<P>::CJ;
-  IterArgs<CJ, C> a;
-  a.y_in = L.y_in;
-  a.y_out = L.y_out;
-  for (int k = 0; k < KMAX; ++k) {
-    a.p[k] = L.p[k];
-    a.dkd[k] = L.dk[k];
-    a.dk[k] = to_c(L.dk[k], C());
+static float2 split2(double x) {
+  float hi = (float)x;
+  return make_float2(hi, (float)(x - (double)hi));
+}
+
+void ptab_fill(void* host, int K, int m_min, int m_max, double tol, double rel, const double* k8,
+               double ga, const double* beta, const double* const* dk) {
+  const int M = m_max + 1;
+  unsigned char* b = static_cast<unsigned char*>(host);
+  PassParams* pp = reinterpret_cast<PassParams*>(b);
+  std::memset(b, 0, ptab_bytes(M));
+  pp->K = K;
+  pp->m_min = m_min;
+  pp->m_max = m_max;
+  pp->M = M;
+  pp->tol = tol;
+  pp->rel = rel;
+  for (int j = 0; j < 8; ++j) {
+    pp->kd[j] = k8[j];
+    pp->kf[j] = split2(k8[j]);
   }
-  a.st = L.st;
-  a.ctl = L.ctl;
-  a.partials = L.partials;
-  a.nx = L.nx;
-  a.ny = L.ny;
-  a.K = L.K;
-  a.m = L.m;
-  a.m_min = L.m_min;
-  a.m_max = L.m_max;
-  a.tol = L.tol;
-  a.rel = L.rel;
-  for (int j = 0; j < 8; ++j) a.k[j] = to_c(L.k[j], CJ());
-  a.ga = to_c(L.ga, CJ());
-  a.beta = to_c(L.beta, C());
+  pp->gad = ga;
+  pp->gaf = split2(ga);
+  double* bd = reinterpret_cast<double*>(b + sizeof(PassParams));
+  float2* bf = reinterpret_cast<float2*>(b + sizeof(PassParams) + 8 * (size_t)M);
+  double* dd = reinterpret_cast<double*>(b + sizeof(PassParams) + 16 * (size_t)M);
+  float2* df2 = reinterpret_cast<float2*>(b + sizeof(PassParams) + 16 * (size_t)M + 8 * (size_t)KMAX * M);
+  if (beta)
+    for (int m = 0; m < M; ++m) {
+      bd[m] = beta[m];
+      bf[m] = split2(beta[m]);
+    }
+  if (dk)
+    for (int k = 0; k < K; ++k)
+      for (int m = 0; m < M; ++m) {
+        dd[k * M + m] = dk[k][m];
+        df2[k * M + m] = split2(dk[k][m]);
+      }
+}
+
+static IterDev make_dev(const ChainSpec& s, int V) {
+  IterDev a{};
+  a.y[0] = s.y[0];
+  a.y[1] = s.y[1];
+  for (int k = 0; k < KMAX; ++k) a.p[k] = s.p[k];
+  a.st = s.st;
+  a.ctl = s.ctl;
+  a.partials = s.partials;
+  a.ptab = static_cast<const unsigned char*>(s.ptab);
+  a.nx = s.nx;
+  a.ny = s.ny;
+  a.tiles_x = (s.nx / V + 31) / 32;
+  a.ntiles = a.tiles_x * ((s.ny + TILE_Y - 1) / TILE_Y);
   return a;
 }
 
+// the kernel function of a spec
 template <int P, int OP, int MODE>
-static cudaError_t launch_iter_t(const IterLaunch& L, cudaStream_t s) {
-  auto a = make_args<P>(L);
-  const bool vec = (L.nx % 2 == 0);
-  const int V = vec ? 2 : 1;
-  a.tiles_x = (L.nx / V + 31) / 32;
-  a.ntiles = a.tiles_x * ((L.ny + TILE_Y - 1) / TILE_Y);
-  int grid = L.grid < a.ntiles ? L.grid : a.ntiles;
-  dim3 blk(32, TILE_Y);
-  if (vec)
-    k_iter<P, OP, 2, MODE><<<grid, blk, 0, s>>>(a);
-  else
-    k_iter<P, OP, 1, MODE><<<grid, blk, 0, s>>>(a);
-  return cudaGetLastError();
+static void* kfn_t(int V) {
+  return V == 2 ? (void*)k_iter<P, OP, 2, MODE> : (void*)k_iter<P, OP, 1, MODE>;
 }
-
 template <int P, int MODE>
-static cudaError_t launch_iter_op(const IterLaunch& L, cudaStream_t s) {
-  switch (L.op) {
+static void* kfn_op(int op, int V) {
+  switch (op) {
     case PHIX_OP_ADVDIFF:
-      return launch_iter_t<P, PHIX_OP_ADVDIFF, MODE>(L, s);
+      return kfn_t<P, PHIX_OP_ADVDIFF, MODE>(V);
     case PHIX_OP_GRAYSCOTT:
-      return launch_iter_t<P, PHIX_OP_GRAYSCOTT, MODE>(L, s);
+      return kfn_t<P, PHIX_OP_GRAYSCOTT, MODE>(V);
     case PHIX_OP_BURGERS:
-      return launch_iter_t<P, PHIX_OP_BURGERS, MODE>(L, s);
+      return kfn_t<P, PHIX_OP_BURGERS, MODE>(V);
   }
-  return cudaErrorInvalidValue;
+  return nullptr;
 }
-
 template <int P>
-static cudaError_t launch_iter_mode(const IterLaunch& L, cudaStream_t s) {
-  return L.mode == MODE_NEWTON ? launch_iter_op<P, MODE_NEWTON>(L, s)
-                               : launch_iter_op<P, MODE_POWER>(L, s);
+static void* kfn_mode(int op, int mode, int V) {
+  return mode == MODE_NEWTON ? kfn_op<P, MODE_NEWTON>(op, V) : kfn_op<P, MODE_POWER>(op, V);
+}
+static void* kfn(const ChainSpec& s, int V) {
+  switch (s.prec) {
+    case P_FP64:
+      return kfn_mode<P_FP64>(s.op, s.mode, V);
+    case P_DF64:
+      return kfn_mode<P_DF64>(s.op, s.mode, V);
+    case P_FP32JV:
+      return kfn_mode<P_FP32JV>(s.op, s.mode, V);
+    case P_FP32:
+      return kfn_mode<P_FP32>(s.op, s.mode, V);
+  }
+  return nullptr;
 }
 
-cudaError_t launch_iter(const IterLaunch& L, cudaStream_t s) {
-  switch (L.prec) {
-    case P_FP64:
-      return launch_iter_mode<P_FP64>(L, s);
-    case P_DF64:
-      return launch_iter_mode<P_DF64>(L, s);
-    case P_FP32JV:
-      return launch_iter_mode<P_FP32JV>(L, s);
-    case P_FP32:
-      return launch_iter_mode<P_FP32>(L, s);
+cudaError_t iter_node_params(const ChainSpec& s, cudaKernelNodeParams* np, void* arg_storage,
+                             size_t arg_bytes) {
+  if (arg_bytes < sizeof(IterDev)) return cudaErrorInvalidValue;
+  const int V = (s.nx % 2 == 0) ? 2 : 1;
+  IterDev a = make_dev(s, V);
+  std::memcpy(arg_storage, &a, sizeof a);
+  void* fn = kfn(s, V);
+  if (!fn) return cudaErrorInvalidValue;
+  std::memset(np, 0, sizeof *np);
+  np->func = fn;
+  np->gridDim = dim3(s.grid < a.ntiles ? s.grid : a.ntiles);
+  np->blockDim = dim3(32, TILE_Y);
+  np->sharedMemBytes = 0;
+  static thread_local void* argp[1];
+  argp[0] = arg_storage;
+  np->kernelParams = argp;
+  np->extra = nullptr;
+  return cudaSuccess;
+}
+
+cudaError_t launch_iter(const ChainSpec& s, cudaStream_t st) {
+  const int V = (s.nx % 2 == 0) ? 2 : 1;
+  IterDev a = make_dev(s, V);
+  void* fn = kfn(s, V);
+  if (!fn) return cudaErrorInvalidValue;
+  void* args[1] = {&a};
+  dim3 grid(s.grid < a.ntiles ? s.grid : a.ntiles);
+  return cudaLaunchKernel(fn, grid, dim3(32, TILE_Y), args, 0, st);
+}
+
+int iter_blocks_per_sm(const ChainSpec& s) {
+  const int V = (s.nx % 2 == 0) ? 2 : 1;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kfn(s, V), THREADS, 0) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 4;
   }
-  return cudaErrorInvalidValue;
+  return nb < 1 ? 1 : nb;
 }
 
 template <int P>
 static cudaError_t launch_init_t(const InitLaunch& L, cudaStream_t s) {
-  IterLaunch IL{};
-  IL.K = L.K;
-  IL.m_min = L.m_min;
-  IL.m_max = L.m_max;
-  IL.ctl = L.ctl;
-  IL.partials = L.partials;
-  IL.tol = L.tol;
-  for (int k = 0; k < KMAX; ++k) {
-    IL.p[k] = L.p[k];
-    IL.dk[k] = L.dk[k];
-  }
-  auto a = make_args<P>(IL);
+  ChainSpec cs{};
+  cs.nx = L.nx;
+  cs.ny = L.ny;
+  for (int k = 0; k < KMAX; ++k) cs.p[k] = L.p[k];
+  cs.ctl = L.ctl;
+  cs.partials = L.partials;
+  cs.ptab = L.ptab;
+  IterDev a = make_dev(cs, 1);
   size_t n = (size_t)L.ncomp * L.nx * L.ny;
   k_init<P><<<L.grid, dim3(32, TILE_Y), 0, s>>>(L.v, static_cast<typename Tr<P>::T*>(L.y0), a, n);
   return cudaGetLastError();

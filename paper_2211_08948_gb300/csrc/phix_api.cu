@@ -24,7 +24,8 @@ enum Slot {
   S_Y0 = 0, S_Y1, S_P0, S_P1, S_P2, S_P3, S_ST,                 // Newton pass
   S_F, S_A, S_B, S_RA, S_RB, S_T0, S_Q, S_T3, S_T4, S_O1, S_O2, S_O3,  // stages
   S_SUB_U, S_SUB_TMP, S_SUB_W0,                                  // substeps (W0..W0+8)
-  S_NSLOT = S_SUB_W0 + 9
+  S_PTAB = S_SUB_W0 + 9,                                         // chain parameter block
+  S_NSLOT
 };
 
 }  // namespace
@@ -45,8 +46,17 @@ struct phix_ctx {
   double* scal_h = nullptr;      // pinned
   unsigned int* counter = nullptr;
   long launches = 0;
-  std::vector<cudaEvent_t> ev;   // profiling: event pairs per iteration launch
+  std::vector<cudaEvent_t> ev;   // profiling: event pairs per graph launch
+  unsigned char* ptab_h = nullptr;  // pinned staging of the chain parameter block
+  size_t ptab_cap = 0;
+  struct Graph {
+    ChainSpec spec;
+    cudaGraphExec_t exec;
+  };
+  std::vector<Graph> graphs;     // cached chains of GRAPH_NODES iteration launches
 };
+
+static constexpr int GRAPH_NODES = 8;
 
 namespace {
 
@@ -198,37 +208,115 @@ void ensure_events(phix_ctx* ctx, size_t n) {
   }
 }
 
+// Upload a chain parameter block (pinned staging; the previous chain has
+// finished: every chain ends with a synchronising read of the control block).
+const void* upload_ptab(phix_ctx* ctx, int K, int m_min, int m_max, double tol, double rel, const double* k8,
+                        double ga, const double* beta, const double* const* dk) {
+  const size_t bytes = ptab_bytes(m_max + 1);
+  if (ctx->ptab_cap < bytes) {
+    if (ctx->ptab_h) CK(cudaFreeHost(ctx->ptab_h));
+    ctx->ptab_h = nullptr;
+    ctx->ptab_cap = 0;
+    CK(cudaMallocHost(&ctx->ptab_h, bytes));
+    ctx->ptab_cap = bytes;
+  }
+  ptab_fill(ctx->ptab_h, K, m_min, m_max, tol, rel, k8, ga, beta, dk);
+  void* d = ws(ctx, S_PTAB, bytes);
+  CK(cudaMemcpyAsync(d, ctx->ptab_h, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  return d;
+}
+
+// A cached CUDA graph of GRAPH_NODES identical iteration launches of `spec`.
+cudaGraphExec_t chain_graph(phix_ctx* ctx, const ChainSpec& spec) {
+  for (auto& g : ctx->graphs)
+    if (std::memcmp(&g.spec, &spec, sizeof spec) == 0) return g.exec;
+  if (ctx->graphs.size() >= 64) {
+    CK(cudaGraphExecDestroy(ctx->graphs.front().exec));
+    ctx->graphs.erase(ctx->graphs.begin());
+  }
+  cudaGraph_t g;
+  CK(cudaGraphCreate(&g, 0));
+  cudaGraphNode_t prev = nullptr;
+  alignas(16) unsigned char argbuf[512];
+  for (int i = 0; i < GRAPH_NODES; ++i) {
+    cudaKernelNodeParams np;
+    CK(iter_node_params(spec, &np, argbuf, sizeof argbuf));
+    cudaGraphNode_t node;
+    CK(cudaGraphAddKernelNode(&node, g, prev ? &prev : nullptr, prev ? 1 : 0, &np));
+    prev = node;
+  }
+  cudaGraphExec_t exec;
+  cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
+  cudaGraphDestroy(g);
+  CK(e);
+  phix_ctx::Graph gg;
+  gg.spec = spec;
+  gg.exec = exec;
+  ctx->graphs.push_back(gg);
+  return exec;
+}
+
+// Run a chain until the device marks it done or `last` iterations were issued.
+// Returns the number of graph launches; with profiling, event pair i brackets
+// graph launch i (iterations first_m + i*GRAPH_NODES ...).
+int run_chain(phix_ctx* ctx, const ChainSpec& spec, int first_target, int last, bool profile) {
+  cudaGraphExec_t exec = chain_graph(ctx, spec);
+  int issued = 0, ng = 0;
+  int target = std::min(last, first_target);
+  if (profile) ensure_events(ctx, 2 * (size_t)((last + GRAPH_NODES - 1) / GRAPH_NODES + 1));
+  for (;;) {
+    while (issued < target) {
+      if (profile) CK(cudaEventRecord(ctx->ev[2 * ng], ctx->stream));
+      ctx->launches += GRAPH_NODES;
+      CK(cudaGraphLaunch(exec, ctx->stream));
+      if (profile) CK(cudaEventRecord(ctx->ev[2 * ng + 1], ctx->stream));
+      issued += GRAPH_NODES;
+      ++ng;
+    }
+    read_ctl(ctx);
+    if (ctx->ctl_h->done || issued >= last) break;
+    target = std::min(last, issued + GRAPH_NODES);
+  }
+  return ng;
+}
+
 // One Newton-Leja pass (Sec. 2.2): out[k] = sum_m d_k[m] y_m, y_0 = v,
 // y_{m+1} = ((J - c)/gamma - xi_m) y_m, stop at |d_k[m]| ||y_m|| <= tol ||p_k||.
 PassResult leja_pass(phix_ctx* ctx, const OpState& os, int prec, const double* v, int K,
                      const std::vector<std::vector<double>>& d, double c, double gamma, double tol,
                      const phix_opts& o, double* const* out) {
   const int m_max = o.m_max;
-  const double* xi = leja_table(m_max + 1);
+  const int M = m_max + 1;
+  const double* xi = leja_table(M);
   const size_t eb = elem_bytes(prec);
   void* y[2] = {ws(ctx, S_Y0, os.N * eb), ws(ctx, S_Y1, os.N * eb)};
   void* p[KMAX] = {};
   for (int k = 0; k < K; ++k) p[k] = ws(ctx, S_P0 + k, os.N * eb);
+
+  // parameter block: shifts beta_m = -(c/gamma + xi_{m-1}), coefficients d_k[m]
+  std::vector<double> beta(M, 0.0);
+  for (int m = 1; m < M; ++m) beta[m] = -(c / gamma + xi[m - 1]);
+  const double* dk[KMAX] = {};
+  for (int k = 0; k < K; ++k) dk[k] = d[k].data();
+  const double alpha = 1.0 / gamma;
+  const int ns = n_scaled(os.d.kind);
+  double k8[8];
+  for (int j = 0; j < 8; ++j) k8[j] = j < ns ? alpha * os.kJ[j] : os.kJ[j];
+  const void* ptab = upload_ptab(ctx, K, o.m_min, m_max, tol, 0.0, k8, alpha, beta.data(), dk);
 
   CK(cudaMemsetAsync(ctx->ctl, 0, sizeof(LejaCtl), ctx->stream));
   KL(launch_scale(v, os.N, ctx->ctl, ctx->partials, ctx->grid_iter, ctx->stream));
   InitLaunch IL{};
   IL.prec = prec;
   IL.ncomp = os.ncomp;
-  IL.K = K;
-  IL.m_min = o.m_min;
-  IL.m_max = m_max;
   IL.nx = os.d.nx;
   IL.ny = os.d.ny;
   IL.v = v;
   IL.y0 = y[0];
-  for (int k = 0; k < K; ++k) {
-    IL.p[k] = p[k];
-    IL.dk[k] = d[k][0];
-  }
+  for (int k = 0; k < K; ++k) IL.p[k] = p[k];
   IL.ctl = ctx->ctl;
   IL.partials = ctx->partials;
-  IL.tol = tol;
+  IL.ptab = ptab;
   IL.grid = ctx->grid_iter;
   KL(launch_init(IL, ctx->stream));
 
@@ -242,65 +330,40 @@ PassResult leja_pass(phix_ctx* ctx, const OpState& os, int prec, const double* v
       break;
     }
   }
-  const double alpha = 1.0 / gamma;
-  IterLaunch L{};
-  L.prec = prec;
-  L.op = os.d.kind;
-  L.mode = MODE_NEWTON;
-  L.K = K;
-  L.m_min = o.m_min;
-  L.m_max = m_max;
-  L.nx = os.d.nx;
-  L.ny = os.d.ny;
-  for (int k = 0; k < K; ++k) L.p[k] = p[k];
-  L.st = os.st;
-  L.ctl = ctx->ctl;
-  L.partials = ctx->partials;
-  L.tol = tol;
-  L.grid = ctx->grid_iter;
-  const int ns = n_scaled(os.d.kind);
-  for (int j = 0; j < 8; ++j) L.k[j] = j < ns ? alpha * os.kJ[j] : os.kJ[j];
-  L.ga = alpha;
-
-  int launched = 0;  // last m launched
-  int target = std::min(m_max, m_pred + 2);
-  if (o.profile) ensure_events(ctx, 2 * (m_max + 1));
-  for (;;) {
-    for (int m = launched + 1; m <= target; ++m) {
-      L.m = m;
-      L.y_in = y[(m - 1) & 1];
-      L.y_out = y[m & 1];
-      L.beta = -(c / gamma + xi[m - 1]);
-      for (int k = 0; k < K; ++k) L.dk[k] = d[k][m];
-      if (o.profile) CK(cudaEventRecord(ctx->ev[2 * m], ctx->stream));
-      KL(launch_iter(L, ctx->stream));
-      if (o.profile) CK(cudaEventRecord(ctx->ev[2 * m + 1], ctx->stream));
-    }
-    launched = target;
-    read_ctl(ctx);
-    if (ctx->ctl_h->done || launched >= m_max) break;
-    target = std::min(m_max, launched + 8);
-  }
+  ChainSpec cs{};
+  cs.prec = prec;
+  cs.op = os.d.kind;
+  cs.mode = MODE_NEWTON;
+  cs.nx = os.d.nx;
+  cs.ny = os.d.ny;
+  cs.y[0] = y[0];
+  cs.y[1] = y[1];
+  for (int k = 0; k < K; ++k) cs.p[k] = p[k];
+  cs.st = os.st;
+  cs.ctl = ctx->ctl;
+  cs.partials = ctx->partials;
+  cs.ptab = ptab;
+  cs.grid = ctx->nsm * std::min(8, iter_blocks_per_sm(cs));
+  const int ng = run_chain(ctx, cs, m_pred + 2, m_max, o.profile != 0);
   KL(launch_finalize(prec, os.N, K, p, out, ctx->ctl, ctx->grid_stream, ctx->stream));
   PassResult r;
   r.iters = ctx->ctl_h->iters;
   r.status = ctx->ctl_h->done ? ctx->ctl_h->status : PHIX_ENOTCONV;
-  r.ms = 0.0;
-  r.bytes = 0.0;
   if (o.profile) {
-    // launches 1..iters did work (later ones returned at once); all events have
-    // completed: read_ctl synchronised the stream after the last launch
-    const double st_bytes = os.d.kind == PHIX_OP_GRAYSCOTT ? 2.0 * os.plane * (prec == P_FP64 || prec == P_DF64 ? 8 : 4)
-                           : os.d.kind == PHIX_OP_BURGERS ? 1.0 * os.plane * (prec == P_FP64 || prec == P_DF64 ? 8 : 4)
-                                                           : 0.0;
+    // graph launches whose every iteration did work (m <= iters); all events
+    // have completed: run_chain synchronised the stream after the last launch
+    const size_t sb = (prec == P_FP64 || prec == P_DF64) ? 8 : 4;
+    const double st_bytes = os.d.kind == PHIX_OP_GRAYSCOTT ? 2.0 * os.plane * sb
+                           : os.d.kind == PHIX_OP_BURGERS ? 1.0 * os.plane * sb : 0.0;
     const double per = (double)os.N * eb * (2.0 + 2.0 * K) + st_bytes;
-    for (int m = 1; m <= r.iters && m <= launched; ++m) {
+    for (int g = 0; g < ng; ++g) {
+      if ((g + 1) * GRAPH_NODES > r.iters) break;
       float t = 0.f;
-      CK(cudaEventElapsedTime(&t, ctx->ev[2 * m], ctx->ev[2 * m + 1]));
+      CK(cudaEventElapsedTime(&t, ctx->ev[2 * g], ctx->ev[2 * g + 1]));
       r.ms += t;
-      r.bytes += per;
+      r.bytes += per * GRAPH_NODES;
+      r.launches += GRAPH_NODES;
     }
-    r.launches = std::min(r.iters, launched);
   }
   return r;
 }
@@ -316,36 +379,23 @@ std::vector<double> dd_table(int l, double a, double b, int m) {
 double power_iteration(phix_ctx* ctx, const OpState& os, int prec, const phix_opts& o, int* mv) {
   const size_t eb = elem_bytes(prec);
   void* y[2] = {ws(ctx, S_Y0, os.N * eb), ws(ctx, S_Y1, os.N * eb)};
+  const void* ptab = upload_ptab(ctx, 0, 0, o.power_max_it, 0.0, o.power_rel, os.kJ, 1.0, nullptr, nullptr);
   CK(cudaMemsetAsync(ctx->ctl, 0, sizeof(LejaCtl), ctx->stream));
   KL(launch_power_start(prec, os.N, o.power_seed, y[0], ctx->ctl, ctx->partials, ctx->grid_iter, ctx->stream));
-  IterLaunch L{};
-  L.prec = prec;
-  L.op = os.d.kind;
-  L.mode = MODE_POWER;
-  L.K = 0;
-  L.m_max = o.power_max_it;
-  L.nx = os.d.nx;
-  L.ny = os.d.ny;
-  L.st = os.st;
-  L.ctl = ctx->ctl;
-  L.partials = ctx->partials;
-  L.rel = o.power_rel;
-  L.grid = ctx->grid_iter;
-  for (int j = 0; j < 8; ++j) L.k[j] = os.kJ[j];
-  L.ga = 1.0;
-  int launched = 0, target = std::min(o.power_max_it, 16);
-  for (;;) {
-    for (int m = launched + 1; m <= target; ++m) {
-      L.m = m;
-      L.y_in = y[(m - 1) & 1];
-      L.y_out = y[m & 1];
-      KL(launch_iter(L, ctx->stream));
-    }
-    launched = target;
-    read_ctl(ctx);
-    if (ctx->ctl_h->done || launched >= o.power_max_it) break;
-    target = std::min(o.power_max_it, launched + 8);
-  }
+  ChainSpec cs{};
+  cs.prec = prec;
+  cs.op = os.d.kind;
+  cs.mode = MODE_POWER;
+  cs.nx = os.d.nx;
+  cs.ny = os.d.ny;
+  cs.y[0] = y[0];
+  cs.y[1] = y[1];
+  cs.st = os.st;
+  cs.ctl = ctx->ctl;
+  cs.partials = ctx->partials;
+  cs.ptab = ptab;
+  cs.grid = ctx->nsm * std::min(8, iter_blocks_per_sm(cs));
+  run_chain(ctx, cs, 16, o.power_max_it, false);
   if (ctx->ctl_h->status == PHIX_ENAN) fail(ctx, PHIX_ENAN, "power iteration produced a non-finite norm");
   *mv = ctx->ctl_h->iters;
   return ctx->ctl_h->rho;
@@ -563,7 +613,7 @@ phix_status phix_create(phix_ctx** out, void* stream) {
   try {
     CK(cudaGetDevice(&ctx->device));
     CK(cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, ctx->device));
-    ctx->grid_iter = ctx->nsm * 4;
+    ctx->grid_iter = ctx->nsm * 8;   // upper bound; chains use the occupancy of their kernel
     ctx->grid_stream = ctx->nsm * 8;
     CK(cudaMalloc(&ctx->ctl, sizeof(LejaCtl)));
     CK(cudaMallocHost(&ctx->ctl_h, sizeof(LejaCtl)));
@@ -594,6 +644,8 @@ phix_status phix_destroy(phix_ctx* ctx) {
   if (ctx->scal_h) cudaFreeHost(ctx->scal_h);
   if (ctx->counter) cudaFree(ctx->counter);
   for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+  for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.exec);
+  if (ctx->ptab_h) cudaFreeHost(ctx->ptab_h);
   delete ctx;
   return PHIX_OK;
 }

@@ -27,6 +27,8 @@ struct LejaCtl {
   int done;            // 1: converged or failed
   int iters;           // iteration index m at which the chain stopped
   int status;          // phix_status
+  int m;               // index of the next iteration of the chain (advanced by the last block)
+  int pad;
   double ynorm;        // ||y_m|| (scaled units) of the last completed launch
   double pnorm[KMAX];  // ||p_m^(k)||
   double sigma;        // input scale, a power of two
@@ -37,58 +39,58 @@ struct LejaCtl {
   float alpha_hi, alpha_lo;
 };
 
-// Coefficient pack of one launch, in the arithmetic of the precision.
-// ADVDIFF:   k = {E, W, N, S, C}
-// GRAYSCOTT: k = {xu, yu, Cu, xv, yv, Cv}, per-point terms g1 = V^2, g2 = 2UV
-// BURGERS:   k = {x, y, C, bx, by},        per-point state U
-// In MODE_NEWTON the host folds alpha = 1/gamma into k and ga, and beta =
-// -(c/gamma + xi_{m-1}) is the shift of the centre value.
-template <typename CJ, typename C>
-struct IterArgs {
-  const void* y_in;
-  void* y_out;
+// Parameters of one chain of iteration launches, in device memory, written by
+// the host before the chain.  Every launch of a chain then has the same
+// arguments (so a chain can be replayed as a CUDA graph): the kernel reads its
+// iteration index m from the control block and its shift beta_m and
+// coefficients d_k[m] from the tables that follow this header:
+//   PassParams | beta_d[M] | beta_f[M] | dk_d[KMAX][M] | dk_f[KMAX][M]
+// (float64 forms and double-float (hi, lo) forms; float32 kernels use .x).
+// Uniform J coefficients k:
+//   ADVDIFF:   {E, W, N, S, C}
+//   GRAYSCOTT: {xu, yu, Cu, xv, yv, Cv}, per-point terms g1 = V^2, g2 = 2UV
+//   BURGERS:   {x, y, C, bx, by},        per-point state U
+// In MODE_NEWTON the host folds alpha = 1/gamma into k and ga; beta_m =
+// -(c/gamma + xi_{m-1}) shifts the centre value.
+struct PassParams {
+  int K, m_min, m_max, M;
+  double tol, rel;
+  double kd[8], gad;
+  float2 kf[8], gaf;
+};
+size_t ptab_bytes(int M);
+// Fill a host copy of a parameter block.  beta and dk may be NULL (power iteration).
+void ptab_fill(void* host, int K, int m_min, int m_max, double tol, double rel, const double* k8,
+               double ga, const double* beta, const double* const* dk);
+
+// ---- launchers (leja_kernels.cu) -----------------------------------------
+struct ChainSpec {
+  int prec, op, mode, nx, ny;
+  void* y[2];         // Newton basis / power iterate ping-pong: launch m reads y[(m-1)&1]
   void* p[KMAX];
   const void* st;     // per-point state planes (precision's state type)
   LejaCtl* ctl;
-  double* partials;   // gridDim.x * (KMAX + 1)
-  int nx, ny, K, m, m_min, m_max, ntiles, tiles_x;
-  double tol, rel;
-  double dkd[KMAX];   // |d_k[m]| test values (float64)
-  C dk[KMAX];         // d_k[m] in the iteration arithmetic
-  CJ k[8];
-  CJ ga;
-  C beta;
+  double* partials;   // grid * (KMAX + 1)
+  const void* ptab;   // parameter block (device)
+  int grid;           // blocks (<= partials capacity)
 };
+// One iteration launch.
+cudaError_t launch_iter(const ChainSpec& s, cudaStream_t st);
+// Kernel node of one iteration launch, for graph building.
+cudaError_t iter_node_params(const ChainSpec& s, cudaKernelNodeParams* np, void* arg_storage,
+                             size_t arg_bytes);
+// Blocks per SM the iteration kernel of this spec can keep resident.
+int iter_blocks_per_sm(const ChainSpec& s);
 
-// ---- launchers (leja_kernels.cu) -----------------------------------------
-struct IterLaunch {
-  int prec, op, mode, K, m, m_min, m_max;
-  int nx, ny;
-  const void* y_in;
-  void* y_out;
-  void* p[KMAX];
-  const void* st;
-  LejaCtl* ctl;
-  double* partials;
-  double tol, rel;
-  double dk[KMAX];     // d_k[m]
-  double k[8];         // uniform coefficients (alpha-folded for NEWTON)
-  double ga;           // per-point term scale
-  double beta;         // shift
-  int grid;            // blocks
-};
-cudaError_t launch_iter(const IterLaunch& L, cudaStream_t s);
-
-// y0 = v / sigma (stored in the precision's format), p_k = d_k[0] y0, norms.
+// y0 = v / sigma (stored in the precision's format), p_k = d_k[0] y0, norms, ctl->m = 1.
 struct InitLaunch {
-  int prec, ncomp, K, m_min, m_max, nx, ny;
+  int prec, ncomp, nx, ny;
   const double* v;
   void* y0;
   void* p[KMAX];
   LejaCtl* ctl;
   double* partials;
-  double tol;
-  double dk[KMAX];
+  const void* ptab;
   int grid;
 };
 cudaError_t launch_init(const InitLaunch& L, cudaStream_t s);
@@ -106,7 +108,7 @@ cudaError_t launch_finalize(int prec, size_t n, int K, void* const* p, double* c
                             const LejaCtl* ctl, int grid, cudaStream_t s);
 
 // power iteration start: y0[i] = splitmix64_uniform(seed, i) in the precision's format,
-// ctl->alpha = 1/||y0||.
+// ctl->alpha = 1/||y0||, ctl->m = 1.
 cudaError_t launch_power_start(int prec, size_t n, uint64_t seed, void* y0, LejaCtl* ctl,
                                double* partials, int grid, cudaStream_t s);
 

@@ -110,9 +110,11 @@ extern "C" phix_status phix_phi_action_noalloc(const phix_jop* op, double h, con
   const size_t eb = prec == P_FP32 ? 4 : 8;
   const size_t sb = (prec == P_FP64 || prec == P_DF64) ? 8 : 4;
   const size_t st_planes = op->kind == PHIX_OP_GRAYSCOTT ? 2 : (op->kind == PHIX_OP_BURGERS ? 1 : 0);
-  // scratch layout: control block | partials | y0 | y1 | p_0..p_{K-1} | state planes
+  // scratch layout: control block | partials | parameter block | y0 | y1 | p_0..p_{K-1} | state planes
   const size_t vec = align256(N * eb);
-  const size_t need = CTL_BYTES + align256(PARTIAL_BYTES) + (2 + (size_t)nout) * vec + align256(st_planes * plane * sb);
+  const size_t ptb = align256(ptab_bytes(PHIX_NOALLOC_MMAX + 1));
+  const size_t need = CTL_BYTES + align256(PARTIAL_BYTES) + ptb + (2 + (size_t)nout) * vec +
+                      align256(st_planes * plane * sb);
   if (need > (size_t)PHIX_NOALLOC_SCRATCH_BYTES) return finish(PHIX_ETOOBIG);
 
   int dev = 0;
@@ -126,7 +128,8 @@ extern "C" phix_status phix_phi_action_noalloc(const phix_jop* op, double h, con
   c.st = static_cast<cudaStream_t>(cuda_stream);
   c.ctl = reinterpret_cast<LejaCtl*>(base);
   double* partials = reinterpret_cast<double*>(base + CTL_BYTES);
-  unsigned char* q = base + CTL_BYTES + align256(PARTIAL_BYTES);
+  unsigned char* ptab = base + CTL_BYTES + align256(PARTIAL_BYTES);
+  unsigned char* q = ptab + ptb;
   void* y[2] = {q, q + vec};
   void* p[KMAX] = {};
   for (int k = 0; k < nout; ++k) p[k] = q + (2 + k) * vec;
@@ -175,30 +178,32 @@ extern "C" phix_status phix_phi_action_noalloc(const phix_jop* op, double h, con
     beta_i = o.rho_hi;
     st.rho = o.rho_re;
   } else {
+    // parameter block on the host stack, copied synchronously into the scratch
+    static_assert(PHIX_NOALLOC_MMAX <= 1000, "stack parameter block sized for m_max <= 1000");
+    alignas(16) unsigned char hp[sizeof(PassParams) + 16 * 1001 + 16 * KMAX * 1001];
+    if (o.power_max_it > PHIX_NOALLOC_MMAX) return finish(PHIX_EINVAL);
+    ptab_fill(hp, 0, 0, o.power_max_it, 0.0, o.power_rel, kJ, 1.0, nullptr, nullptr);
+    if (cudaMemcpyAsync(ptab, hp, ptab_bytes(o.power_max_it + 1), cudaMemcpyHostToDevice, c.st) != cudaSuccess)
+      return finish(PHIX_ECUDA);
     if (cudaMemsetAsync(c.ctl, 0, sizeof(LejaCtl), c.st) != cudaSuccess) return finish(PHIX_ECUDA);
     if (!ok(launch_power_start(prec, N, o.power_seed, y[0], c.ctl, partials, grid, c.st))) return finish(PHIX_ECUDA);
-    IterLaunch L{};
-    L.prec = prec;
-    L.op = op->kind;
-    L.mode = MODE_POWER;
-    L.m_max = o.power_max_it;
-    L.nx = op->nx;
-    L.ny = op->ny;
-    L.st = stp;
-    L.ctl = c.ctl;
-    L.partials = partials;
-    L.rel = o.power_rel;
-    L.grid = grid;
-    for (int j = 0; j < 8; ++j) L.k[j] = kJ[j];
-    L.ga = 1.0;
+    ChainSpec cs{};
+    cs.prec = prec;
+    cs.op = op->kind;
+    cs.mode = MODE_POWER;
+    cs.nx = op->nx;
+    cs.ny = op->ny;
+    cs.y[0] = y[0];
+    cs.y[1] = y[1];
+    cs.st = stp;
+    cs.ctl = c.ctl;
+    cs.partials = partials;
+    cs.ptab = ptab;
+    cs.grid = grid;
     int launched = 0, target = std::min(o.power_max_it, 16);
     for (;;) {
-      for (int m = launched + 1; m <= target; ++m) {
-        L.m = m;
-        L.y_in = y[(m - 1) & 1];
-        L.y_out = y[m & 1];
-        if (!ok(launch_iter(L, c.st))) return finish(PHIX_ECUDA);
-      }
+      for (int m = launched + 1; m <= target; ++m)
+        if (!ok(launch_iter(cs, c.st))) return finish(PHIX_ECUDA);
       launched = target;
       if (!read_ctl(c)) return finish(PHIX_ECUDA);
       if (c.h.done || launched >= o.power_max_it) break;
@@ -230,55 +235,53 @@ extern "C" phix_status phix_phi_action_noalloc(const phix_jop* op, double h, con
   }
 
   // ---- Newton-Leja pass ----------------------------------------------------
+  {
+    alignas(16) unsigned char hp[sizeof(PassParams) + 16 * 1001 + 16 * KMAX * 1001];
+    double beta[PHIX_NOALLOC_MMAX + 1];
+    beta[0] = 0.0;
+    for (int m = 1; m < M; ++m) beta[m] = -(cc / gamma + xi[m - 1]);
+    const double* dk[KMAX] = {};
+    for (int k = 0; k < nout; ++k) dk[k] = d[k];
+    const double al = 1.0 / gamma;
+    double k8[8];
+    for (int j = 0; j < 8; ++j) k8[j] = j < nscaled ? al * kJ[j] : kJ[j];
+    ptab_fill(hp, nout, o.m_min, o.m_max, tol, 0.0, k8, al, beta, dk);
+    if (cudaMemcpyAsync(ptab, hp, ptab_bytes(M), cudaMemcpyHostToDevice, c.st) != cudaSuccess)
+      return finish(PHIX_ECUDA);
+  }
   if (cudaMemsetAsync(c.ctl, 0, sizeof(LejaCtl), c.st) != cudaSuccess) return finish(PHIX_ECUDA);
   if (!ok(launch_scale(v, N, c.ctl, partials, grid, c.st))) return finish(PHIX_ECUDA);
   InitLaunch IL{};
   IL.prec = prec;
   IL.ncomp = ncomp;
-  IL.K = nout;
-  IL.m_min = o.m_min;
-  IL.m_max = o.m_max;
   IL.nx = op->nx;
   IL.ny = op->ny;
   IL.v = v;
   IL.y0 = y[0];
-  for (int k = 0; k < nout; ++k) {
-    IL.p[k] = p[k];
-    IL.dk[k] = d[k][0];
-  }
+  for (int k = 0; k < nout; ++k) IL.p[k] = p[k];
   IL.ctl = c.ctl;
   IL.partials = partials;
-  IL.tol = tol;
+  IL.ptab = ptab;
   IL.grid = grid;
   if (!ok(launch_init(IL, c.st))) return finish(PHIX_ECUDA);
-  IterLaunch L{};
-  L.prec = prec;
-  L.op = op->kind;
-  L.mode = MODE_NEWTON;
-  L.K = nout;
-  L.m_min = o.m_min;
-  L.m_max = o.m_max;
-  L.nx = op->nx;
-  L.ny = op->ny;
-  for (int k = 0; k < nout; ++k) L.p[k] = p[k];
-  L.st = stp;
-  L.ctl = c.ctl;
-  L.partials = partials;
-  L.tol = tol;
-  L.grid = grid;
-  const double al = 1.0 / gamma;
-  for (int j = 0; j < 8; ++j) L.k[j] = j < nscaled ? al * kJ[j] : kJ[j];
-  L.ga = al;
+  ChainSpec cs{};
+  cs.prec = prec;
+  cs.op = op->kind;
+  cs.mode = MODE_NEWTON;
+  cs.nx = op->nx;
+  cs.ny = op->ny;
+  cs.y[0] = y[0];
+  cs.y[1] = y[1];
+  for (int k = 0; k < nout; ++k) cs.p[k] = p[k];
+  cs.st = stp;
+  cs.ctl = c.ctl;
+  cs.partials = partials;
+  cs.ptab = ptab;
+  cs.grid = grid;
   int launched = 0, target = std::min(o.m_max, 32);
   for (;;) {
-    for (int m = launched + 1; m <= target; ++m) {
-      L.m = m;
-      L.y_in = y[(m - 1) & 1];
-      L.y_out = y[m & 1];
-      L.beta = -(cc / gamma + xi[m - 1]);
-      for (int k = 0; k < nout; ++k) L.dk[k] = d[k][m];
-      if (!ok(launch_iter(L, c.st))) return finish(PHIX_ECUDA);
-    }
+    for (int m = launched + 1; m <= target; ++m)
+      if (!ok(launch_iter(cs, c.st))) return finish(PHIX_ECUDA);
     launched = target;
     if (!read_ctl(c)) return finish(PHIX_ECUDA);
     if (c.h.done || launched >= o.m_max) break;
