@@ -1,0 +1,283 @@
+// Device code shared by the iteration kernels (Newton-Leja, power iteration,
+// Arnoldi): precision traits, element loads/stores in each storage format,
+// the three 5-point stencil Jacobians, and the deterministic last-block
+// reduction of per-block partial sums.
+#pragma once
+#include <type_traits>
+
+#include "phix_internal.h"
+
+namespace phix {
+
+// ---------------------------------------------------------------------------
+// Precision traits: storage T (one element), vector pair T2, iteration
+// arithmetic C, stencil arithmetic CJ, state storage S, accumulators.
+// ---------------------------------------------------------------------------
+template <int P>
+struct Tr;
+template <>
+struct Tr<P_FP64> {
+  using T = double;
+  using T2 = double2;
+  using C = double;
+  using CJ = double;
+  using S = double;
+  using S2 = double2;
+  using AccN = double;  // Newton norms
+  using AccP = double;  // power-iteration norm (sets the interval: full precision)
+};
+template <>
+struct Tr<P_DF64> {
+  using T = float2;
+  using T2 = float4;
+  using C = df;
+  using CJ = df;
+  using S = float2;
+  using S2 = float4;
+  using AccN = float;
+  using AccP = df;
+};
+template <>
+struct Tr<P_FP32JV> {
+  using T = float2;
+  using T2 = float4;
+  using C = df;
+  using CJ = float;
+  using S = float;
+  using S2 = float2;
+  using AccN = float;
+  using AccP = df;
+};
+template <>
+struct Tr<P_FP32> {
+  using T = float;
+  using T2 = float2;
+  using C = float;
+  using CJ = float;
+  using S = float;
+  using S2 = float2;
+  using AccN = float;
+  using AccP = float;
+};
+
+// ---- element conversions ----------------------------------------------------
+__device__ __forceinline__ double cv(double x) { return x; }
+__device__ __forceinline__ df cv(float2 x) { return df_make(x.x, x.y); }
+__device__ __forceinline__ float cv(float x) { return x; }
+
+__device__ __forceinline__ void st1(double* p, double x) { *p = x; }
+__device__ __forceinline__ void st1(float2* p, df x) { *p = make_float2(x.hi, x.lo); }
+__device__ __forceinline__ void st1(float* p, float x) { *p = x; }
+
+__device__ __forceinline__ void st2(double* p, double a, double b) {
+  *reinterpret_cast<double2*>(p) = make_double2(a, b);
+}
+__device__ __forceinline__ void st2(float2* p, df a, df b) {
+  *reinterpret_cast<float4*>(p) = make_float4(a.hi, a.lo, b.hi, b.lo);
+}
+__device__ __forceinline__ void st2(float* p, float a, float b) {
+  *reinterpret_cast<float2*>(p) = make_float2(a, b);
+}
+
+// read-only loads (y_in, state) through the non-coherent path
+__device__ __forceinline__ double ldr1(const double* p) { return __ldg(p); }
+__device__ __forceinline__ df ldr1(const float2* p) { return cv(__ldg(p)); }
+__device__ __forceinline__ float ldr1(const float* p) { return __ldg(p); }
+__device__ __forceinline__ void ldr2(const double* p, double& a, double& b) {
+  double2 t = __ldg(reinterpret_cast<const double2*>(p));
+  a = t.x;
+  b = t.y;
+}
+__device__ __forceinline__ void ldr2(const float2* p, df& a, df& b) {
+  float4 t = __ldg(reinterpret_cast<const float4*>(p));
+  a = df_make(t.x, t.y);
+  b = df_make(t.z, t.w);
+}
+__device__ __forceinline__ void ldr2(const float* p, float& a, float& b) {
+  float2 t = __ldg(reinterpret_cast<const float2*>(p));
+  a = t.x;
+  b = t.y;
+}
+// read-write loads (accumulators)
+__device__ __forceinline__ double ldw1(const double* p) { return *p; }
+__device__ __forceinline__ df ldw1(const float2* p) { return cv(*p); }
+__device__ __forceinline__ float ldw1(const float* p) { return *p; }
+__device__ __forceinline__ void ldw2(const double* p, double& a, double& b) {
+  double2 t = *reinterpret_cast<const double2*>(p);
+  a = t.x;
+  b = t.y;
+}
+__device__ __forceinline__ void ldw2(const float2* p, df& a, df& b) {
+  float4 t = *reinterpret_cast<const float4*>(p);
+  a = df_make(t.x, t.y);
+  b = df_make(t.z, t.w);
+}
+__device__ __forceinline__ void ldw2(const float* p, float& a, float& b) {
+  float2 t = *reinterpret_cast<const float2*>(p);
+  a = t.x;
+  b = t.y;
+}
+
+// stencil arithmetic from iteration arithmetic and back
+__device__ __forceinline__ double to_cj(double x, double) { return x; }
+__device__ __forceinline__ df to_cj(df x, df) { return x; }
+__device__ __forceinline__ float to_cj(df x, float) { return x.hi; }
+__device__ __forceinline__ float to_cj(float x, float) { return x; }
+__device__ __forceinline__ double from_cj(double x, double) { return x; }
+__device__ __forceinline__ df from_cj(df x, df) { return x; }
+__device__ __forceinline__ df from_cj(float x, df) { return df_make(x, 0.f); }
+__device__ __forceinline__ float from_cj(float x, float) { return x; }
+
+// squares for the norms
+__device__ __forceinline__ void acc_sq(double& a, double x) { a = fma(x, x, a); }
+__device__ __forceinline__ void acc_sq(float& a, df x) { a = fmaf(x.hi, x.hi, a); }
+__device__ __forceinline__ void acc_sq(float& a, float x) { a = fmaf(x, x, a); }
+__device__ __forceinline__ void acc_sq(df& a, df x) { a = df_add(df_mul(x, x), a); }
+
+__device__ __forceinline__ double acc_to_double(double a) { return a; }
+__device__ __forceinline__ double acc_to_double(float a) { return (double)a; }
+__device__ __forceinline__ double acc_to_double(df a) { return (double)a.hi + (double)a.lo; }
+
+__device__ __forceinline__ double shfl_down(double v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ float shfl_down(float v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ df shfl_down(df v, int o) {
+  return df_make(__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o));
+}
+__device__ __forceinline__ double acc_add(double a, double b) { return a + b; }
+__device__ __forceinline__ float acc_add(float a, float b) { return a + b; }
+__device__ __forceinline__ df acc_add(df a, df b) { return df_add(a, b); }
+
+template <typename A>
+__device__ __forceinline__ A acc_zero();
+template <>
+__device__ __forceinline__ double acc_zero<double>() { return 0.0; }
+template <>
+__device__ __forceinline__ float acc_zero<float>() { return 0.f; }
+template <>
+__device__ __forceinline__ df acc_zero<df>() { return df_make(0.f, 0.f); }
+
+// Block reduction of NV accumulators; the block's sums go to partials[blockIdx.x*(KMAX+1) + j]
+// as float64.  Returns true in the block that finished last (all partials visible).
+template <typename A, int NV>
+__device__ bool block_partials_and_last(A (&acc)[NV], double* partials, unsigned int* count) {
+  __shared__ double sred[THREADS / 32][KMAX + 1];
+  __shared__ bool last;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    A v = acc[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = acc_add(v, shfl_down(v, o));
+    if (lane == 0) sred[warp][j] = acc_to_double(v);
+  }
+  __syncthreads();
+  if (tid < NV) {
+    double s = 0.0;
+    for (int w = 0; w < THREADS / 32; ++w) s += sred[w][tid];
+    partials[(size_t)blockIdx.x * (KMAX + 1) + tid] = s;
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    unsigned int t = atomicAdd(count, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  return last;
+}
+
+// Last block: totals[j] = sum over blocks of partials (fixed order).
+template <int NV>
+__device__ void reduce_partials(const double* partials, double (&tot)[NV]) {
+  __shared__ double sfin[THREADS][KMAX + 1];
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  double s[NV];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) s[j] = 0.0;
+  for (int b = tid; b < (int)gridDim.x; b += THREADS) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) s[j] += __ldcg(partials + (size_t)b * (KMAX + 1) + j);
+  }
+#pragma unroll
+  for (int j = 0; j < NV; ++j) sfin[tid][j] = s[j];
+  __syncthreads();
+  for (int w = THREADS / 2; w > 0; w >>= 1) {
+    if (tid < w) {
+#pragma unroll
+      for (int j = 0; j < NV; ++j) sfin[tid][j] += sfin[tid + w][j];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < NV; ++j) tot[j] = sfin[0][j];
+}
+
+// Stop test of the Newton-Leja chain at iteration m (Sec. 2.2).
+__device__ inline void leja_test(LejaCtl* ctl, int m, int K, int m_min, int m_max, double tol,
+                          const double* dkd, const double* tot) {
+  double ny = sqrt(tot[0]);
+  bool finite = isfinite(ny);
+  bool conv = (m >= m_min);
+  for (int k = 0; k < K; ++k) {
+    double np = sqrt(tot[1 + k]);
+    ctl->pnorm[k] = np;
+    finite = finite && isfinite(np);
+    conv = conv && (fabs(dkd[k]) * ny <= tol * np);
+  }
+  ctl->ynorm = ny;
+  if (!finite) {
+    ctl->status = PHIX_ENAN;
+    ctl->iters = m;
+    ctl->done = 1;
+  } else if (conv) {
+    ctl->status = PHIX_OK;
+    ctl->iters = m;
+    ctl->done = 1;
+  } else if (m >= m_max) {
+    ctl->status = PHIX_ENOTCONV;
+    ctl->iters = m;
+    ctl->done = 1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Stencils.  Each returns J*y at one point in the stencil arithmetic CJ.
+// ---------------------------------------------------------------------------
+template <typename CJ>
+__device__ __forceinline__ CJ stencil_advdiff(const CJ (&k)[8], CJ e, CJ w, CJ n, CJ s, CJ c) {
+  return k[0] * e + k[1] * w + k[2] * n + k[3] * s + k[4] * c;
+}
+
+// GS species u: ku = {x, y, C}; returns J_u, J_v together.
+template <typename CJ>
+__device__ __forceinline__ void stencil_gs(const CJ (&k)[8], CJ ga, CJ ue, CJ uw, CJ un, CJ us, CJ uc,
+                                           CJ ve, CJ vw, CJ vn, CJ vs, CJ vc, CJ g1, CJ g2, CJ& ju,
+                                           CJ& jv) {
+  CJ a1 = ga * g1;
+  CJ a2 = ga * g2;
+  ju = k[0] * (ue + uw) + k[1] * (un + us) + (k[2] - a1) * uc - a2 * vc;
+  jv = k[3] * (ve + vw) + k[4] * (vn + vs) + a1 * uc + (k[5] + a2) * vc;
+}
+
+template <typename CJ>
+__device__ __forceinline__ CJ stencil_burgers(const CJ (&k)[8], CJ ga, CJ e, CJ w, CJ n, CJ s, CJ c,
+                                              CJ Ue, CJ Uw, CJ Un, CJ Us, CJ Uc) {
+  // nu lap y - (U_x + U_y) y - U (y_x + y_y), all centred
+  CJ divU = k[3] * (Ue - Uw) + k[4] * (Un - Us);
+  CJ dy = k[3] * (e - w) + k[4] * (n - s);
+  return k[0] * (e + w) + k[1] * (n + s) + k[2] * c - ga * (divU * c + Uc * dy);
+}
+
+
+// a coefficient in the arithmetic X, from its float64 / double-float forms
+template <typename X>
+__device__ __forceinline__ X coef(double d, float2 f);
+template <>
+__device__ __forceinline__ double coef<double>(double d, float2) { return d; }
+template <>
+__device__ __forceinline__ df coef<df>(double, float2 f) { return df_make(f.x, f.y); }
+template <>
+__device__ __forceinline__ float coef<float>(double, float2 f) { return f.x; }
+
+}  // namespace phix

@@ -1,0 +1,599 @@
+// KIOPS-style Krylov kernels (Sec. 2.1 of the paper): Arnoldi with window-2
+// incomplete orthogonalisation on the augmented matrix
+//   A~ = [[A, eta B], [0, K]],  A = h J,  B = [b_p, ..., b_1],  K = shift,
+// the small exponential exp(tau Hbar) e_1 of the (tridiagonal) Hessenberg
+// matrix with the corrected-Krylov error estimate, and the combination of the
+// basis into the substep result.
+//
+// The basis is kept unnormalised, V_i = s_i Zhat_i; the N part of Zhat_i is
+// stored in the iteration precision (float64 or double-float), the p tail
+// entries in float64 inside the control block.  Each Arnoldi step is two
+// grid passes:
+//   pass 1: z = A~ V_j (5-point stencil + the eta b columns), partial dots
+//           <Zhat_j, z>, <Zhat_{j-1}, z> and ||z||^2;
+//   pass 2: z <- z - h_jj V_j - h_{j-1,j} V_{j-1} in place, partial ||z||^2;
+// the last block of each pass adds the tail terms, forms h_jj, h_{j-1,j},
+// h_{j+1,j}, s_{j+1} and writes the coefficients of the next launch.
+#include "iter_common.cuh"
+
+namespace phix {
+
+namespace {
+
+// dot products: float64, or double-float accumulation
+__device__ __forceinline__ void acc_dot(double& a, double x, double y) { a = fma(x, y, a); }
+__device__ __forceinline__ void acc_dot(df& a, df x, df y) { a = df_add(df_mul(x, y), a); }
+
+template <int P>
+struct KTr;
+template <>
+struct KTr<P_FP64> {
+  using T = double;
+  using C = double;
+  using S = double;
+  using Acc = double;
+};
+template <>
+struct KTr<P_DF64> {
+  using T = float2;
+  using C = df;
+  using S = float2;
+  using Acc = df;
+};
+
+struct ArnArgs {
+  const void* zj;
+  const void* zjm1;  // NULL for j = 0
+  void* zout;        // slot j + 1
+  const void* bz[KIOPS_PMAX];
+  int bslot[KIOPS_PMAX];
+  int nb;
+  const void* st;
+  KiopsCtl* kc;
+  double* partials;
+  int j, p, nx, ny, ntiles, tiles_x, nscaled;
+  double h;
+  double kJ[8];
+};
+
+// next pass-1 coefficients from s[j] (single thread)
+__device__ void prepare_pass1(KiopsCtl* kc, int j, int p, double h, const double* kJ, int nscaled) {
+  const double sj = kc->s[j];
+  for (int i = 0; i < 8; ++i) {
+    double v = i < nscaled ? kJ[i] * h * sj : kJ[i];
+    kc->kd[i] = v;
+    float hi = (float)v;
+    kc->kf[i] = make_float2(hi, (float)(v - (double)hi));
+  }
+  const double g = h * sj;
+  kc->gad = g;
+  float gh = (float)g;
+  kc->gaf = make_float2(gh, (float)(g - (double)gh));
+  for (int t = 0; t < p; ++t) {
+    double b = kc->eta * sj * kc->tail[j * KIOPS_PMAX + t];
+    kc->bd[t] = b;
+    float bh = (float)b;
+    kc->bf[t] = make_float2(bh, (float)(b - (double)bh));
+  }
+}
+
+__device__ __forceinline__ float2 split2d(double v) {
+  float hi = (float)v;
+  return make_float2(hi, (float)(v - (double)hi));
+}
+
+template <int P, int OP, int V>
+__global__ void __launch_bounds__(THREADS) k_arn1(ArnArgs a) {
+  using T = typename KTr<P>::T;
+  using C = typename KTr<P>::C;
+  using S = typename KTr<P>::S;
+  using Acc = typename KTr<P>::Acc;
+  constexpr int NC = (OP == PHIX_OP_GRAYSCOTT) ? 2 : 1;
+  KiopsCtl* kc = a.kc;
+  if (__ldcg(&kc->stop)) return;
+  C kk[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) kk[i] = coef<C>(__ldcg(&kc->kd[i]), __ldcg(&kc->kf[i]));
+  const C ga = coef<C>(__ldcg(&kc->gad), __ldcg(&kc->gaf));
+  C bw[KIOPS_PMAX];
+#pragma unroll
+  for (int b = 0; b < KIOPS_PMAX; ++b)
+    bw[b] = b < a.nb ? coef<C>(__ldcg(&kc->bd[a.bslot[b]]), __ldcg(&kc->bf[a.bslot[b]])) : C{};
+
+  Acc acc[3] = {acc_zero<Acc>(), acc_zero<Acc>(), acc_zero<Acc>()};
+  const T* __restrict__ zj = static_cast<const T*>(a.zj);
+  const T* __restrict__ zm = static_cast<const T*>(a.zjm1);
+  T* __restrict__ zo = static_cast<T*>(a.zout);
+  const S* __restrict__ st = static_cast<const S*>(a.st);
+  const int nx = a.nx, ny = a.ny;
+  const size_t plane = (size_t)nx * ny;
+
+  for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+    const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+    const int iy = ty * TILE_Y + threadIdx.y;
+    const int ix = (tx * 32 + threadIdx.x) * V;
+    if (iy >= ny || ix >= nx) continue;
+    const int iym = iy == 0 ? ny - 1 : iy - 1;
+    const int iyp = iy == ny - 1 ? 0 : iy + 1;
+    const int ixm = ix == 0 ? nx - 1 : ix - 1;
+    const int ixp = (ix + V == nx) ? 0 : ix + V;
+    const size_t row = (size_t)iy * nx, rowp = (size_t)iyp * nx, rowm = (size_t)iym * nx;
+    C c[NC][V], nn[NC][V], ss[NC][V], we[NC], ea[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      const T* b = zj + q * plane;
+      if constexpr (V == 2) {
+        ldr2(b + row + ix, c[q][0], c[q][1]);
+        ldr2(b + rowp + ix, nn[q][0], nn[q][1]);
+        ldr2(b + rowm + ix, ss[q][0], ss[q][1]);
+      } else {
+        c[q][0] = ldr1(b + row + ix);
+        nn[q][0] = ldr1(b + rowp + ix);
+        ss[q][0] = ldr1(b + rowm + ix);
+      }
+      we[q] = ldr1(b + row + ixm);
+      ea[q] = ldr1(b + row + ixp);
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      C J[NC];
+      if constexpr (OP == PHIX_OP_ADVDIFF) {
+        C e = (v == V - 1) ? ea[0] : c[0][v + 1];
+        C w = (v == 0) ? we[0] : c[0][v - 1];
+        J[0] = stencil_advdiff<C>(kk, e, w, nn[0][v], ss[0][v], c[0][v]);
+      } else if constexpr (OP == PHIX_OP_GRAYSCOTT) {
+        C eu = (v == V - 1) ? ea[0] : c[0][v + 1];
+        C wu = (v == 0) ? we[0] : c[0][v - 1];
+        C ev = (v == V - 1) ? ea[NC - 1] : c[NC - 1][v + 1];
+        C wv = (v == 0) ? we[NC - 1] : c[NC - 1][v - 1];
+        C g1 = cv(__ldg(st + row + ix + v));
+        C g2 = cv(__ldg(st + plane + row + ix + v));
+        stencil_gs<C>(kk, ga, eu, wu, nn[0][v], ss[0][v], c[0][v], ev, wv, nn[NC - 1][v], ss[NC - 1][v],
+                      c[NC - 1][v], g1, g2, J[0], J[NC - 1]);
+      } else {
+        C e = (v == V - 1) ? ea[0] : c[0][v + 1];
+        C w = (v == 0) ? we[0] : c[0][v - 1];
+        const int vx = ix + v;
+        const int vxm = (v == 0) ? ixm : vx - 1;
+        const int vxp = (v == V - 1) ? ixp : vx + 1;
+        C Uc = cv(__ldg(st + row + vx));
+        C Ue = cv(__ldg(st + row + vxp));
+        C Uw = cv(__ldg(st + row + vxm));
+        C Un = cv(__ldg(st + rowp + vx));
+        C Us = cv(__ldg(st + rowm + vx));
+        J[0] = stencil_burgers<C>(kk, ga, e, w, nn[0][v], ss[0][v], c[0][v], Ue, Uw, Un, Us, Uc);
+      }
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        const size_t idx = q * plane + row + ix + v;
+        C z = J[q];
+        for (int b = 0; b < a.nb; ++b) z = z + bw[b] * ldr1(static_cast<const T*>(a.bz[b]) + idx);
+        st1(zo + idx, z);
+        acc_dot(acc[0], c[q][v], z);
+        if (zm) acc_dot(acc[1], ldr1(zm + idx), z);
+        acc_dot(acc[2], z, z);
+      }
+    }
+  }
+
+  if (block_partials_and_last<Acc, 3>(acc, a.partials, &kc->count)) {
+    double tot[3];
+    reduce_partials<3>(a.partials, tot);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      const int j = a.j, p = a.p;
+      const double sj = kc->s[j];
+      const double* tj = kc->tail + j * KIOPS_PMAX;
+      double tz[KIOPS_PMAX];
+      for (int t = 0; t < p; ++t) tz[t] = (t + 1 < p) ? sj * tj[t + 1] : 0.0;
+      double d1 = tot[0], d0 = tot[1], zz = tot[2];
+      for (int t = 0; t < p; ++t) {
+        d1 += tj[t] * tz[t];
+        zz += tz[t] * tz[t];
+        if (j >= 1) d0 += kc->tail[(j - 1) * KIOPS_PMAX + t] * tz[t];
+      }
+      const double hjj = sj * d1;
+      const double hjm = j >= 1 ? kc->s[j - 1] * d0 : 0.0;
+      kc->hd[j] = hjj;
+      kc->hu[j] = hjm;
+      kc->z0[j] = sqrt(zz);
+      for (int t = 0; t < p; ++t) kc->tail[(j + 1) * KIOPS_PMAX + t] = tz[t];
+      const double c1 = hjj * sj, c0 = j >= 1 ? hjm * kc->s[j - 1] : 0.0;
+      kc->c1d = c1;
+      kc->c0d = c0;
+      kc->c1f = split2d(c1);
+      kc->c0f = split2d(c0);
+      if (!isfinite(hjj) || !isfinite(hjm) || !isfinite(zz)) {
+        kc->status = PHIX_ENAN;
+        kc->stop = 1;
+      }
+      kc->count = 0;
+      __threadfence();
+    }
+  }
+}
+
+template <int P>
+__global__ void __launch_bounds__(THREADS) k_arn2(ArnArgs a, size_t n) {
+  using T = typename KTr<P>::T;
+  using C = typename KTr<P>::C;
+  using Acc = typename KTr<P>::Acc;
+  KiopsCtl* kc = a.kc;
+  if (__ldcg(&kc->stop)) return;
+  const C c1 = coef<C>(__ldcg(&kc->c1d), __ldcg(&kc->c1f));
+  const C c0 = coef<C>(__ldcg(&kc->c0d), __ldcg(&kc->c0f));
+  const T* __restrict__ zj = static_cast<const T*>(a.zj);
+  const T* __restrict__ zm = static_cast<const T*>(a.zjm1);
+  T* __restrict__ zo = static_cast<T*>(a.zout);
+  Acc acc[1] = {acc_zero<Acc>()};
+  const size_t stride = (size_t)gridDim.x * THREADS;
+  for (size_t i = (size_t)blockIdx.x * THREADS + threadIdx.y * 32 + threadIdx.x; i < n; i += stride) {
+    C z = ldw1(zo + i) - c1 * ldr1(zj + i);
+    if (zm) z = z - c0 * ldr1(zm + i);
+    st1(zo + i, z);
+    acc_dot(acc[0], z, z);
+  }
+  if (block_partials_and_last<Acc, 1>(acc, a.partials, &kc->count)) {
+    double tot[1];
+    reduce_partials<1>(a.partials, tot);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      const int j = a.j, p = a.p;
+      double* tz = kc->tail + (j + 1) * KIOPS_PMAX;
+      const double c1d = kc->c1d, c0d = kc->c0d;
+      double nz = tot[0];
+      for (int t = 0; t < p; ++t) {
+        double v = tz[t] - c1d * kc->tail[j * KIOPS_PMAX + t];
+        if (j >= 1) v -= c0d * kc->tail[(j - 1) * KIOPS_PMAX + t];
+        tz[t] = v;
+        nz += v * v;
+      }
+      const double hn = sqrt(nz);
+      kc->hl[j] = hn;
+      if (!isfinite(hn)) {
+        kc->status = PHIX_ENAN;
+        kc->stop = 1;
+      } else if (hn <= 1e-12 * kc->z0[j]) {
+        kc->stop = 1;  // happy breakdown: exact invariant subspace of dimension j+1
+        kc->happy_m = j + 1;
+      } else {
+        kc->s[j + 1] = 1.0 / hn;
+        kc->sf[j + 1] = split2d(1.0 / hn);
+        prepare_pass1(kc, j + 1, p, a.h, a.kJ, a.nscaled);
+      }
+      kc->count = 0;
+      __threadfence();
+    }
+  }
+}
+
+// F = exp(tau Hbar) e_1 by Taylor series with scaling (segments of norm <= 1)
+// after a shift by the mean diagonal: exp(tau Hbar) = e^{tau mu} exp(tau (Hbar - mu I)).
+__global__ void __launch_bounds__(128) k_kexp(KiopsCtl* kc, int m, double tau, double tau_end, double tol) {
+  __shared__ double dg[KIOPS_MMAX + 2], up[KIOPS_MMAX + 2], lo[KIOPS_MMAX + 2];
+  __shared__ double x[KIOPS_MMAX + 2], t0[KIOPS_MMAX + 2], t1[KIOPS_MMAX + 2], red[128];
+  __shared__ int n_s, S_s;
+  __shared__ double mu_s;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    const int hm = kc->happy_m;
+    const int mm = hm > 0 ? hm : m;
+    n_s = hm > 0 ? hm : m + 1;
+    const int n = n_s;
+    double tr = 0.0;
+    for (int i = 0; i < n; ++i) {
+      dg[i] = i < mm ? kc->hd[i] : 0.0;          // row m of Hbar has no diagonal
+      up[i] = (i + 1 < mm) ? kc->hu[i + 1] : 0.0;  // (i, i+1); column m is zero
+      lo[i] = (i + 1 < n) ? kc->hl[i] : 0.0;       // (i+1, i)
+      tr += dg[i];
+    }
+    const double mu = tr / n;
+    mu_s = mu;
+    double nrm = 0.0;  // 1-norm of tau (Hbar - mu I)
+    for (int i = 0; i < n; ++i) {
+      double cs = fabs(tau * (dg[i] - mu));
+      if (i >= 1) cs += fabs(tau * up[i - 1]);
+      if (i + 1 < n) cs += fabs(tau * lo[i]);
+      nrm = fmax(nrm, cs);
+    }
+    S_s = nrm > 1.0 ? (int)ceil(nrm) : 1;
+  }
+  __syncthreads();
+  const int n = n_s, S = S_s;
+  const double mu = mu_s;
+  const double sc = tau / S;
+  for (int i = tid; i < n; i += 128) x[i] = (i == 0) ? 1.0 : 0.0;
+  __syncthreads();
+  for (int seg = 0; seg < S; ++seg) {
+    for (int i = tid; i < n; i += 128) t0[i] = x[i];
+    __syncthreads();
+    double* cur = t0;
+    double* nxt = t1;
+    for (int k = 1; k <= 18; ++k) {
+      const double f = sc / k;
+      for (int i = tid; i < n; i += 128) {
+        double v = (dg[i] - mu) * cur[i];
+        if (i + 1 < n) v = fma(up[i], cur[i + 1], v);
+        if (i >= 1) v = fma(lo[i - 1], cur[i - 1], v);
+        v *= f;
+        nxt[i] = v;
+        x[i] += v;
+      }
+      __syncthreads();
+      double* tsw = cur;
+      cur = nxt;
+      nxt = tsw;
+    }
+  }
+  const double e = exp(tau * mu);
+  for (int i = tid; i < n; i += 128) {
+    const double Fi = e * x[i];
+    kc->F[i] = Fi;
+    const double cf = kc->beta * Fi * kc->s[i];
+    kc->coef[i] = cf;
+    kc->coeff[i] = split2d(cf);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double omega = 0.0, err = 0.0;
+    if (kc->happy_m == 0) {
+      err = kc->beta * fabs(e * x[m]);
+      omega = (tau_end / tau) * err / (tol * kc->beta);
+    }
+    kc->err = err;
+    kc->omega = omega;
+    if (!isfinite(omega)) kc->status = PHIX_ENAN;
+    __threadfence();
+  }
+  (void)red;
+}
+
+struct CombArgs {
+  const void* const* Z;  // device array of slot pointers
+  int n;
+  KiopsCtl* kc;
+  double* partials;
+  double* out;
+  double scale;
+  int p, nscaled;
+  double h;
+  double kJ[8];
+};
+
+template <int P>
+__global__ void __launch_bounds__(THREADS) k_kcomb(CombArgs a, size_t N) {
+  using T = typename KTr<P>::T;
+  using C = typename KTr<P>::C;
+  using Acc = typename KTr<P>::Acc;
+  KiopsCtl* kc = a.kc;
+  __shared__ C cf[KIOPS_MMAX + 2];
+  __shared__ const T* zp[KIOPS_MMAX + 2];
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  for (int i = tid; i < a.n; i += THREADS) {
+    cf[i] = coef<C>(__ldcg(&kc->coef[i]), __ldcg(&kc->coeff[i]));
+    zp[i] = static_cast<const T*>(a.Z[i]);
+  }
+  __syncthreads();
+  T* z0 = const_cast<T*>(zp[0]);
+  Acc acc[1] = {acc_zero<Acc>()};
+  const size_t stride = (size_t)gridDim.x * THREADS;
+  for (size_t i = (size_t)blockIdx.x * THREADS + tid; i < N; i += stride) {
+    C w = cf[0] * ldr1(zp[0] + i);
+    for (int k = 1; k < a.n; ++k) w = w + cf[k] * ldr1(zp[k] + i);
+    st1(z0 + i, w);
+    if (a.out) {
+      double d;
+      if constexpr (P == P_FP64)
+        d = w;
+      else
+        d = (double)w.hi + (double)w.lo;
+      a.out[i] = a.scale * d;
+    }
+    acc_dot(acc[0], w, w);
+  }
+  if (block_partials_and_last<Acc, 1>(acc, a.partials, &kc->count)) {
+    double tot[1];
+    reduce_partials<1>(a.partials, tot);
+    if (tid == 0) {
+      double tw[KIOPS_PMAX];
+      double nz = tot[0];
+      for (int t = 0; t < a.p; ++t) {
+        double v = 0.0;
+        for (int k = 0; k < a.n; ++k) v += kc->coef[k] * kc->tail[k * KIOPS_PMAX + t];
+        tw[t] = v;
+        nz += v * v;
+      }
+      for (int t = 0; t < a.p; ++t) kc->tail[t] = tw[t];
+      const double beta = sqrt(nz);
+      kc->beta = beta;
+      kc->s[0] = beta > 0 ? 1.0 / beta : 0.0;
+      kc->sf[0] = split2d(kc->s[0]);
+      kc->stop = 0;
+      kc->happy_m = 0;
+      if (!isfinite(beta)) kc->status = PHIX_ENAN;
+      prepare_pass1(kc, 0, a.p, a.h, a.kJ, a.nscaled);
+      kc->count = 0;
+      __threadfence();
+    }
+  }
+}
+
+template <int P>
+__global__ void __launch_bounds__(THREADS)
+    k_kstart(const double* __restrict__ b0, typename KTr<P>::T* __restrict__ z0, size_t N, CombArgs a, double eta) {
+  using C = typename KTr<P>::C;
+  using Acc = typename KTr<P>::Acc;
+  KiopsCtl* kc = a.kc;
+  Acc acc[1] = {acc_zero<Acc>()};
+  const size_t stride = (size_t)gridDim.x * THREADS;
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  for (size_t i = (size_t)blockIdx.x * THREADS + tid; i < N; i += stride) {
+    double x = b0 ? b0[i] : 0.0;
+    C w;
+    if constexpr (P == P_FP64)
+      w = x;
+    else
+      w = df_from_double(x);
+    st1(z0 + i, w);
+    acc_dot(acc[0], w, w);
+  }
+  if (block_partials_and_last<Acc, 1>(acc, a.partials, &kc->count)) {
+    double tot[1];
+    reduce_partials<1>(a.partials, tot);
+    if (tid == 0) {
+      kc->eta = eta;
+      for (int t = 0; t < KIOPS_PMAX; ++t) kc->tail[t] = 0.0;
+      double nz = tot[0];
+      if (a.p > 0) {
+        kc->tail[a.p - 1] = 1.0 / eta;
+        nz += 1.0 / (eta * eta);
+      }
+      const double beta = sqrt(nz);
+      kc->beta = beta;
+      kc->s[0] = beta > 0 ? 1.0 / beta : 0.0;
+      kc->sf[0] = split2d(kc->s[0]);
+      kc->stop = 0;
+      kc->happy_m = 0;
+      kc->status = isfinite(beta) ? PHIX_OK : PHIX_ENAN;
+      prepare_pass1(kc, 0, a.p, a.h, a.kJ, a.nscaled);
+      kc->count = 0;
+      __threadfence();
+    }
+  }
+}
+
+template <int P>
+__global__ void __launch_bounds__(THREADS)
+    k_kconvert(const double* __restrict__ b, typename KTr<P>::T* __restrict__ out, size_t n, double* partials,
+               unsigned int* counter, double* norm1) {
+  double acc[1] = {0.0};
+  const size_t stride = (size_t)gridDim.x * THREADS;
+  for (size_t i = (size_t)blockIdx.x * THREADS + threadIdx.y * 32 + threadIdx.x; i < n; i += stride) {
+    double x = b[i];
+    acc[0] += fabs(x);
+    if constexpr (P == P_FP64)
+      out[i] = x;
+    else {
+      df w = df_from_double(x);
+      out[i] = make_float2(w.hi, w.lo);
+    }
+  }
+  if (block_partials_and_last<double, 1>(acc, partials, counter)) {
+    double tot[1];
+    reduce_partials<1>(partials, tot);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      *norm1 = tot[0];
+      *counter = 0;
+      __threadfence();
+    }
+  }
+}
+
+ArnArgs make_arn(const KiopsSpec& s, int j, int V) {
+  ArnArgs a{};
+  a.zj = s.Zh[j];
+  a.zjm1 = j >= 1 ? s.Zh[j - 1] : nullptr;
+  a.zout = s.Zh[j + 1];
+  for (int b = 0; b < s.nb; ++b) {
+    a.bz[b] = s.bz[b];
+    a.bslot[b] = s.bslot[b];
+  }
+  a.nb = s.nb;
+  a.st = s.st;
+  a.kc = s.kc;
+  a.partials = s.partials;
+  a.j = j;
+  a.p = s.p;
+  a.nx = s.nx;
+  a.ny = s.ny;
+  a.tiles_x = (s.nx / V + 31) / 32;
+  a.ntiles = a.tiles_x * ((s.ny + TILE_Y - 1) / TILE_Y);
+  a.nscaled = s.nscaled;
+  a.h = s.h;
+  for (int i = 0; i < 8; ++i) a.kJ[i] = s.kJ[i];
+  return a;
+}
+
+CombArgs make_comb(const KiopsSpec& s, int n, double* out, double scale) {
+  CombArgs c{};
+  c.Z = s.Z;
+  c.n = n;
+  c.kc = s.kc;
+  c.partials = s.partials;
+  c.out = out;
+  c.scale = scale;
+  c.p = s.p;
+  c.nscaled = s.nscaled;
+  c.h = s.h;
+  for (int i = 0; i < 8; ++i) c.kJ[i] = s.kJ[i];
+  return c;
+}
+
+template <int P, int OP>
+cudaError_t arn_t(const KiopsSpec& s, int j, cudaStream_t st) {
+  const int V = (s.nx % 2 == 0) ? 2 : 1;
+  ArnArgs a = make_arn(s, j, V);
+  const int g1 = s.grid < a.ntiles ? s.grid : a.ntiles;
+  if (V == 2)
+    k_arn1<P, OP, 2><<<g1, dim3(32, TILE_Y), 0, st>>>(a);
+  else
+    k_arn1<P, OP, 1><<<g1, dim3(32, TILE_Y), 0, st>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t N = (size_t)s.nx * s.ny * (OP == PHIX_OP_GRAYSCOTT ? 2 : 1);
+  k_arn2<P><<<s.grid, dim3(32, TILE_Y), 0, st>>>(a, N);
+  return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t arn_p(const KiopsSpec& s, int j, cudaStream_t st) {
+  switch (s.op) {
+    case PHIX_OP_ADVDIFF:
+      return arn_t<P, PHIX_OP_ADVDIFF>(s, j, st);
+    case PHIX_OP_GRAYSCOTT:
+      return arn_t<P, PHIX_OP_GRAYSCOTT>(s, j, st);
+    case PHIX_OP_BURGERS:
+      return arn_t<P, PHIX_OP_BURGERS>(s, j, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t kiops_arnoldi(const KiopsSpec& s, int j, cudaStream_t st) {
+  return s.prec == P_FP64 ? arn_p<P_FP64>(s, j, st) : arn_p<P_DF64>(s, j, st);
+}
+
+cudaError_t kiops_smallexp(KiopsCtl* kc, int m, double tau, double tau_end, double tol, cudaStream_t st) {
+  k_kexp<<<1, 128, 0, st>>>(kc, m, tau, tau_end, tol);
+  return cudaGetLastError();
+}
+
+cudaError_t kiops_combine(const KiopsSpec& s, int n, double* out, double scale, cudaStream_t st) {
+  const size_t N = (size_t)s.nx * s.ny * (s.op == PHIX_OP_GRAYSCOTT ? 2 : 1);
+  CombArgs c = make_comb(s, n, out, scale);
+  if (s.prec == P_FP64)
+    k_kcomb<P_FP64><<<s.grid, dim3(32, TILE_Y), 0, st>>>(c, N);
+  else
+    k_kcomb<P_DF64><<<s.grid, dim3(32, TILE_Y), 0, st>>>(c, N);
+  return cudaGetLastError();
+}
+
+cudaError_t kiops_start(const KiopsSpec& s, const double* b0, double eta, cudaStream_t st) {
+  const size_t N = (size_t)s.nx * s.ny * (s.op == PHIX_OP_GRAYSCOTT ? 2 : 1);
+  CombArgs c = make_comb(s, 1, nullptr, 0.0);
+  if (s.prec == P_FP64)
+    k_kstart<P_FP64><<<s.grid, dim3(32, TILE_Y), 0, st>>>(b0, static_cast<double*>(s.Zh[0]), N, c, eta);
+  else
+    k_kstart<P_DF64><<<s.grid, dim3(32, TILE_Y), 0, st>>>(b0, static_cast<float2*>(s.Zh[0]), N, c, eta);
+  return cudaGetLastError();
+}
+
+cudaError_t kiops_convert(int prec, size_t n, const double* b, void* out, double* partials,
+                          unsigned int* counter, double* norm1, int grid, cudaStream_t st) {
+  if (prec == P_FP64)
+    k_kconvert<P_FP64><<<grid, dim3(32, TILE_Y), 0, st>>>(b, static_cast<double*>(out), n, partials, counter, norm1);
+  else
+    k_kconvert<P_DF64><<<grid, dim3(32, TILE_Y), 0, st>>>(b, static_cast<float2*>(out), n, partials, counter, norm1);
+  return cudaGetLastError();
+}
+
+}  // namespace phix

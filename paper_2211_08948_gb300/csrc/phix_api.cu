@@ -25,6 +25,7 @@ enum Slot {
   S_F, S_A, S_B, S_RA, S_RB, S_T0, S_Q, S_T3, S_T4, S_O1, S_O2, S_O3,  // stages
   S_SUB_U, S_SUB_TMP, S_SUB_W0,                                  // substeps (W0..W0+8)
   S_PTAB = S_SUB_W0 + 9,                                         // chain parameter block
+  S_KBASIS, S_KB, S_KPTR, S_KCTL,                                // KIOPS basis, b copies, slot table, control
   S_NSLOT
 };
 
@@ -54,6 +55,7 @@ struct phix_ctx {
     cudaGraphExec_t exec;
   };
   std::vector<Graph> graphs;     // cached chains of GRAPH_NODES iteration launches
+  KiopsCtl* kc_h = nullptr;      // pinned mirror of the KIOPS control header
 };
 
 static constexpr int GRAPH_NODES = 8;
@@ -518,6 +520,179 @@ void leja_phi(phix_ctx* ctx, const OpState& os, int prec, double h, const double
   }
 }
 
+struct Interval;
+void leja_phi(phix_ctx* ctx, const OpState& os, int prec, double h, const double* v, int nout,
+              const int* l, const double* sc, double* const* out, double tol, const phix_opts& o,
+              const Interval& iv, phix_stats& stats);
+Interval interval_for(phix_ctx* ctx, const OpState& os, int prec, const phix_opts& o, phix_stats& stats);
+
+// out_k = phi_{l_k}(s_k h J) v by the chosen method (iv: the Leja interval,
+// estimated here when NULL).
+void phi_actions(phix_ctx* ctx, const OpState& os, phix_method method, int prec, double h, const double* v,
+                 int nout, const int* l, const double* sc, double* const* out, double tol, const phix_opts& o,
+                 const Interval* iv, phix_stats& stats);
+
+// ---------------------------------------------------------------------------
+// KIOPS-style run (Sec. 2.1): w(tau) = sum_j tau^j phi_j(tau h J) b_j at the
+// sorted distinct output times; substep and Krylov-dimension control as in
+// the oracle (accept omega <= 1; else grow m by m_step up to m_max, then
+// shrink tau).
+// ---------------------------------------------------------------------------
+struct KOut {
+  double* out;
+  double scale;
+};
+
+int kiops_prec(int prec) { return prec == P_FP64 ? P_FP64 : P_DF64; }
+
+void read_kc(phix_ctx* ctx, KiopsCtl* kc) {
+  CK(cudaMemcpyAsync(ctx->kc_h, kc, KIOPS_HOST_BYTES, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+}
+
+void kiops_run(phix_ctx* ctx, const OpState& os, int prec, double h, const double* const* b, int p,
+               const std::vector<double>& times, const std::vector<std::vector<KOut>>& outs, double tol,
+               const phix_opts& o, phix_stats& stats) {
+  const int kp = kiops_prec(prec);
+  const size_t N = os.N, eb = 8;
+  const int mmax = o.kiops_m_max;
+  if (p > KIOPS_PMAX) fail(ctx, PHIX_EINVAL, "KIOPS supports p <= %d", KIOPS_PMAX);
+  KiopsSpec ks{};
+  ks.prec = kp;
+  ks.op = os.d.kind;
+  ks.nx = os.d.nx;
+  ks.ny = os.d.ny;
+  ks.p = p;
+  unsigned char* base = static_cast<unsigned char*>(ws(ctx, S_KBASIS, (size_t)(mmax + 2) * N * eb));
+  for (int i = 0; i < mmax + 2; ++i) ks.Zh[i] = base + (size_t)i * N * eb;
+  void** Zd = static_cast<void**>(ws(ctx, S_KPTR, sizeof(void*) * (mmax + 2)));
+  CK(cudaMemcpyAsync(Zd, ks.Zh, sizeof(void*) * (mmax + 2), cudaMemcpyHostToDevice, ctx->stream));
+  ks.Z = Zd;
+  ks.st = os.st;
+  KiopsCtl* kc = static_cast<KiopsCtl*>(ws(ctx, S_KCTL, sizeof(KiopsCtl)));
+  CK(cudaMemsetAsync(kc, 0, sizeof(KiopsCtl), ctx->stream));
+  ks.kc = kc;
+  ks.partials = ctx->partials;
+  ks.h = h;
+  for (int i = 0; i < 8; ++i) ks.kJ[i] = os.kJ[i];
+  ks.nscaled = n_scaled(os.d.kind);
+  ks.grid = ctx->grid_iter;
+  // b_j (j >= 1) copies in the iteration precision and their 1-norms -> eta
+  int nb = 0;
+  for (int j = 1; j <= p; ++j)
+    if (b[j]) ++nb;
+  unsigned char* bbase = nb ? static_cast<unsigned char*>(ws(ctx, S_KB, (size_t)nb * N * eb)) : nullptr;
+  double eta = 1.0;
+  if (nb) {
+    int q = 0;
+    for (int j = 1; j <= p; ++j) {
+      if (!b[j]) continue;
+      ks.bz[q] = bbase + (size_t)q * N * eb;
+      ks.bslot[q] = p - j;  // column b_j multiplies tail entry t = p - j
+      KL(kiops_convert(kp, N, b[j], const_cast<void*>(ks.bz[q]), ctx->partials, ctx->counter, ctx->scal + q,
+                       ctx->grid_stream, ctx->stream));
+      ++q;
+    }
+    ks.nb = nb;
+    CK(cudaMemcpyAsync(ctx->scal_h, ctx->scal, sizeof(double) * nb, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    double nmax = 0.0;
+    for (int q2 = 0; q2 < nb; ++q2) nmax = std::max(nmax, ctx->scal_h[q2]);
+    if (!std::isfinite(nmax)) fail(ctx, PHIX_ENAN, "non-finite input vector");
+    if (nmax > 0) eta = std::ldexp(1.0, -(int)std::ceil(std::log2(nmax)));
+  }
+  KL(kiops_start(ks, b[0], eta, ctx->stream));
+  read_kc(ctx, kc);
+  stats.passes += 1;
+  if (ctx->kc_h->status == PHIX_ENAN) fail(ctx, PHIX_ENAN, "non-finite input vector");
+  if (ctx->kc_h->beta == 0.0) {
+    for (size_t ti = 0; ti < times.size(); ++ti)
+      for (const KOut& ko : outs[ti]) CK(cudaMemsetAsync(ko.out, 0, N * sizeof(double), ctx->stream));
+    return;
+  }
+  const double tau_end = times.back();
+  double t = 0.0, tau = tau_end;
+  int m = std::min(o.kiops_m_init, mmax);
+  size_t ti = 0;
+  int substeps = 0;
+  while (ti < times.size()) {
+    if (substeps >= o.kiops_max_substeps) {
+      stats.status = PHIX_ENOTCONV;
+      set_err(ctx, "KIOPS substep limit reached");
+      break;
+    }
+    const double next_out = times[ti];
+    tau = std::min(tau, next_out - t);
+    int built = 0;
+    for (;;) {
+      for (int j = built; j < m; ++j) {
+        ctx->launches += 2;
+        CK(kiops_arnoldi(ks, j, ctx->stream));
+      }
+      KL(kiops_smallexp(kc, m, tau, tau_end, tol, ctx->stream));
+      read_kc(ctx, kc);
+      const KiopsCtl& H = *ctx->kc_h;
+      const int happy = H.happy_m;
+      stats.iters += (happy > 0 ? std::min(happy, m) : m) - built;
+      stats.jv += (happy > 0 ? std::min(happy, m) : m) - built;
+      if (H.status == PHIX_ENAN || !std::isfinite(H.omega)) fail(ctx, PHIX_ENAN, "KIOPS produced a non-finite value");
+      built = m;
+      if (happy > 0) m = happy;
+      const double omega = H.omega;
+      if (happy > 0 || omega <= 1.0) {
+        const bool landed = std::fabs(t + tau - next_out) <= 1e-13 * std::max(1.0, next_out);
+        const KOut* k0 = landed ? &outs[ti][0] : nullptr;
+        KL(kiops_combine(ks, happy > 0 ? m : m + 1, k0 ? k0->out : nullptr, k0 ? k0->scale : 0.0, ctx->stream));
+        if (landed) {
+          for (size_t q = 1; q < outs[ti].size(); ++q)
+            lincomb(ctx, N, {outs[ti][q].scale / k0->scale}, {k0->out}, outs[ti][q].out);
+          t = next_out;
+          ++ti;
+        } else {
+          t = t + tau;
+        }
+        ++substeps;
+        const double g = omega == 0.0 ? 2.0 : std::min(2.0, std::max(1.0, 0.8 * std::pow(omega, -1.0 / m)));
+        tau *= g;
+        break;
+      }
+      stats.rejections += 1;
+      if (m < mmax) {
+        m = std::min(mmax, m + o.kiops_m_step);
+      } else {
+        tau *= std::min(0.9, std::max(0.1, 0.8 * std::pow(omega, -1.0 / m)));
+      }
+    }
+  }
+  stats.substeps += substeps;
+}
+
+// phi_{l_k}(s_k h J) v by KIOPS: one run per distinct l with b_l = v and the
+// output times s_k; out_k = w(s_k) / s_k^l.
+void kiops_phi(phix_ctx* ctx, const OpState& os, int prec, double h, const double* v, int nout,
+               const int* l, const double* sc, double* const* out, double tol, const phix_opts& o,
+               phix_stats& stats) {
+  std::vector<int> ls(l, l + nout);
+  std::sort(ls.begin(), ls.end());
+  ls.erase(std::unique(ls.begin(), ls.end()), ls.end());
+  for (int L : ls) {
+    std::vector<double> times;
+    for (int k = 0; k < nout; ++k)
+      if (l[k] == L) times.push_back(sc[k]);
+    std::sort(times.begin(), times.end());
+    times.erase(std::unique(times.begin(), times.end()), times.end());
+    std::vector<std::vector<KOut>> outs(times.size());
+    for (int k = 0; k < nout; ++k) {
+      if (l[k] != L) continue;
+      size_t ti = std::lower_bound(times.begin(), times.end(), sc[k]) - times.begin();
+      outs[ti].push_back(KOut{out[k], 1.0 / std::pow(sc[k], L)});
+    }
+    std::vector<const double*> b(L + 1, nullptr);
+    b[L] = v;
+    kiops_run(ctx, os, prec, h, b.data(), L, times, outs, tol, o, stats);
+  }
+}
+
 Interval interval_for(phix_ctx* ctx, const OpState& os, int prec, const phix_opts& o, phix_stats& stats) {
   Interval iv{};
   double alpha, beta;
@@ -537,6 +712,21 @@ Interval interval_for(phix_ctx* ctx, const OpState& os, int prec, const phix_opt
   iv.gamma = 0.25 * (beta - alpha);
   stats.rho = iv.rho;
   return iv;
+}
+
+void phi_actions(phix_ctx* ctx, const OpState& os, phix_method method, int prec, double h, const double* v,
+                 int nout, const int* l, const double* sc, double* const* out, double tol, const phix_opts& o,
+                 const Interval* iv, phix_stats& stats) {
+  if (method == PHIX_KIOPS) {
+    kiops_phi(ctx, os, prec, h, v, nout, l, sc, out, tol, o, stats);
+    return;
+  }
+  Interval own;
+  if (!iv) {
+    own = interval_for(ctx, os, prec, o, stats);
+    iv = &own;
+  }
+  leja_phi(ctx, os, prec, h, v, nout, l, sc, out, tol, o, *iv, stats);
 }
 
 phix_opts resolve_opts(phix_ctx* ctx, const phix_opts* in) {
@@ -621,6 +811,7 @@ phix_status phix_create(phix_ctx** out, void* stream) {
     CK(cudaMalloc(&ctx->scal, sizeof(double) * 16));
     CK(cudaMallocHost(&ctx->scal_h, sizeof(double) * 16));
     CK(cudaMalloc(&ctx->counter, sizeof(unsigned int)));
+    CK(cudaMallocHost(&ctx->kc_h, sizeof(KiopsCtl)));
     CK(cudaMemset(ctx->counter, 0, sizeof(unsigned int)));
     CK(cudaMemset(ctx->ctl, 0, sizeof(LejaCtl)));
     CK(cudaDeviceSynchronize());
@@ -646,6 +837,7 @@ phix_status phix_destroy(phix_ctx* ctx) {
   for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
   for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.exec);
   if (ctx->ptab_h) cudaFreeHost(ctx->ptab_h);
+  if (ctx->kc_h) cudaFreeHost(ctx->kc_h);
   delete ctx;
   return PHIX_OK;
 }
@@ -694,15 +886,15 @@ phix_status phix_phi_action(phix_ctx* ctx, const phix_jop* op, double h, const d
       if (!out[k] || out[k] == v) fail(ctx, PHIX_EINVAL, "out[%d] is NULL or aliases v", k);
     }
     phix_opts o = resolve_opts(ctx, opts);
-    if (method != PHIX_LEJA) fail(ctx, PHIX_EINVAL, "method %d not available", (int)method);
-    OpState os = make_opstate(ctx, op, op->state, o.prec);
+    if (method != PHIX_LEJA && method != PHIX_KIOPS) fail(ctx, PHIX_EINVAL, "unknown method %d", (int)method);
+    const int prec = method == PHIX_KIOPS ? kiops_prec(o.prec) : (int)o.prec;
+    OpState os = make_opstate(ctx, op, op->state, prec);
     if (h == 0.0) {
       for (int k = 0; k < nout; ++k) lincomb(ctx, os.N, {1.0 / factorial(l[k])}, {v}, out[k]);
       CK(cudaStreamSynchronize(ctx->stream));
       return PHIX_OK;
     }
-    Interval iv = interval_for(ctx, os, o.prec, o, st);
-    leja_phi(ctx, os, o.prec, h, v, nout, l, scale, out, tol, o, iv, st);
+    phi_actions(ctx, os, method, prec, h, v, nout, l, scale, out, tol, o, nullptr, st);
     CK(cudaStreamSynchronize(ctx->stream));
     return PHIX_OK;
   });
@@ -716,7 +908,17 @@ phix_status phix_phi_combination(phix_ctx* ctx, const phix_jop* op, double h, co
     if (!b || !out) fail(ctx, PHIX_EINVAL, "NULL argument");
     if (p < 0 || p > 8) fail(ctx, PHIX_EINVAL, "p must be in 0..8");
     phix_opts o = resolve_opts(ctx, opts);
-    if (method != PHIX_LEJA) fail(ctx, PHIX_EINVAL, "method %d not available", (int)method);
+    if (method != PHIX_LEJA && method != PHIX_KIOPS) fail(ctx, PHIX_EINVAL, "unknown method %d", (int)method);
+    for (int j = 0; j <= p; ++j)
+      if (b[j] && b[j] == out) fail(ctx, PHIX_EINVAL, "out aliases b[%d]", j);
+    if (method == PHIX_KIOPS) {
+      // one augmented Krylov run (Theorem of Sec. 2.1)
+      OpState os = make_opstate(ctx, op, op->state, kiops_prec(o.prec));
+      std::vector<std::vector<KOut>> outs(1, std::vector<KOut>(1, KOut{out, 1.0}));
+      kiops_run(ctx, os, o.prec, h, b, p, std::vector<double>(1, 1.0), outs, tol, o, st);
+      CK(cudaStreamSynchronize(ctx->stream));
+      return PHIX_OK;
+    }
     OpState os = make_opstate(ctx, op, op->state, o.prec);
     CK(cudaMemsetAsync(out, 0, os.N * sizeof(double), ctx->stream));
     Interval iv = interval_for(ctx, os, o.prec, o, st);
@@ -745,8 +947,9 @@ static phix_status exp_step(phix_ctx* ctx, const phix_jop* op, double* u, double
     if (!(h > 0) || !std::isfinite(h)) fail(ctx, PHIX_EINVAL, "h must be finite and > 0");
     if (!(tol > 0)) fail(ctx, PHIX_EINVAL, "tol must be > 0");
     phix_opts o = resolve_opts(ctx, opts);
-    if (method != PHIX_LEJA) fail(ctx, PHIX_EINVAL, "method %d not available", (int)method);
-    OpState os = make_opstate(ctx, op, u, o.prec);
+    if (method != PHIX_LEJA && method != PHIX_KIOPS) fail(ctx, PHIX_EINVAL, "unknown method %d", (int)method);
+    const int prec = method == PHIX_KIOPS ? kiops_prec(o.prec) : (int)o.prec;
+    OpState os = make_opstate(ctx, op, u, prec);
     const size_t N = os.N;
     double* F = wsd(ctx, S_F, N);
     double* A = wsd(ctx, S_A, N);
@@ -761,37 +964,39 @@ static phix_status exp_step(phix_ctx* ctx, const phix_jop* op, double* u, double
     double* P2 = wsd(ctx, S_O2, N);
     double* P3 = wsd(ctx, S_O3, N);
     KL(launch_rhs(os.d, u, F, ctx->grid_stream, ctx->stream));
-    Interval iv = interval_for(ctx, os, o.prec, o, st);
+    Interval ivv{};
+    if (method == PHIX_LEJA) ivv = interval_for(ctx, os, prec, o, st);
+    const Interval* iv = method == PHIX_LEJA ? &ivv : nullptr;
     lincomb(ctx, N, {h}, {F}, T0);
     if (scheme == 0) {
       // EXPRB43, Eq. (exprb43)
       int l2[2] = {1, 1};
       double s2[2] = {0.5, 1.0};
       double* o2[2] = {P1, P2};
-      leja_phi(ctx, os, o.prec, h, T0, 2, l2, s2, o2, tol, o, iv, st);
+      phi_actions(ctx, os, method, prec, h, T0, 2, l2, s2, o2, tol, o, iv, st);
       lincomb(ctx, N, {1.0, 0.5}, {u, P1}, A);                 // a = u + 1/2 phi_1(h/2 J) f h
       KL(launch_remainder(os.d, u, A, F, RA, ctx->grid_stream, ctx->stream));
       lincomb(ctx, N, {h}, {RA}, T0);
       int l1 = 1;
       double s1 = 1.0;
       double* oq[1] = {Q};
-      leja_phi(ctx, os, o.prec, h, T0, 1, &l1, &s1, oq, tol, o, iv, st);
+      phi_actions(ctx, os, method, prec, h, T0, 1, &l1, &s1, oq, tol, o, iv, st);
       lincomb(ctx, N, {1.0, 1.0, 1.0}, {u, P2, Q}, B);         // b = u + phi_1 f h + phi_1 R(a) h
       KL(launch_remainder(os.d, u, B, F, RB, ctx->grid_stream, ctx->stream));
       lincomb(ctx, N, {16.0 * h, -2.0 * h}, {RA, RB}, T0);
       int l3 = 3;
       double* o3[1] = {T3};
-      leja_phi(ctx, os, o.prec, h, T0, 1, &l3, &s1, o3, tol, o, iv, st);
+      phi_actions(ctx, os, method, prec, h, T0, 1, &l3, &s1, o3, tol, o, iv, st);
       lincomb(ctx, N, {-48.0 * h, 12.0 * h}, {RA, RB}, T0);
       int l4 = 4;
       double* o4[1] = {T4};
-      leja_phi(ctx, os, o.prec, h, T0, 1, &l4, &s1, o4, tol, o, iv, st);
+      phi_actions(ctx, os, method, prec, h, T0, 1, &l4, &s1, o4, tol, o, iv, st);
     } else {
       // EPIRK4s3, Eq. (epirk4s3)
       int l3v[3] = {1, 1, 1};
       double s3[3] = {1.0 / 8.0, 1.0 / 9.0, 1.0};
       double* o3v[3] = {P1, P3, P2};
-      leja_phi(ctx, os, o.prec, h, T0, 3, l3v, s3, o3v, tol, o, iv, st);
+      phi_actions(ctx, os, method, prec, h, T0, 3, l3v, s3, o3v, tol, o, iv, st);
       lincomb(ctx, N, {1.0, 1.0 / 8.0}, {u, P1}, A);
       lincomb(ctx, N, {1.0, 1.0 / 9.0}, {u, P3}, B);
       KL(launch_remainder(os.d, u, A, F, RA, ctx->grid_stream, ctx->stream));
@@ -801,12 +1006,12 @@ static phix_status exp_step(phix_ctx* ctx, const phix_jop* op, double* u, double
       int l3 = 3;
       double s1 = 1.0;
       double* o3[1] = {T3};
-      leja_phi(ctx, os, o.prec, h, T0, 1, &l3, &s1, o3, tol, o, iv, st);
+      phi_actions(ctx, os, method, prec, h, T0, 1, &l3, &s1, o3, tol, o, iv, st);
       // -42336 Ra - 34992 (Rb - 2 Ra) = 27648 Ra - 34992 Rb
       lincomb(ctx, N, {(-42336.0 + 2.0 * 34992.0) * h, -34992.0 * h}, {RA, RB}, T0);
       int l4 = 4;
       double* o4[1] = {T4};
-      leja_phi(ctx, os, o.prec, h, T0, 1, &l4, &s1, o4, tol, o, iv, st);
+      phi_actions(ctx, os, method, prec, h, T0, 1, &l4, &s1, o4, tol, o, iv, st);
     }
     // err = ||u4 - u3|| = ||T4||;  u4 = u + phi_1(hJ) f h + T3 + T4
     KL(launch_norm2(N, T4, nullptr, ctx->partials, ctx->counter, ctx->scal, ctx->grid_stream, ctx->stream));

@@ -117,6 +117,69 @@ cudaError_t launch_power_start(int prec, size_t n, uint64_t seed, void* y0, Leja
 cudaError_t launch_prep_state(int prec, int op, int nx, int ny, const double* state, void* st,
                               int grid, cudaStream_t s);
 
+// ---- KIOPS-style Krylov kernels (kiops_kernels.cu) -----------------------
+constexpr int KIOPS_MMAX = 128;  // largest Krylov dimension
+constexpr int KIOPS_PMAX = 8;    // largest p (augmented tail length)
+
+// Device control block of one KIOPS run.  The basis is kept unnormalised:
+// V_i = s[i] * Zhat_i (N part in the iteration precision, tail in float64).
+// The last block of each Arnoldi pass does the scalar work and prepares the
+// coefficients of the next launch, so the host only reads `omega` & co.
+struct KiopsCtl {
+  // --- read back by the host after each small exponential --------------------
+  int stop;        // happy breakdown or NaN: later Arnoldi launches return at once
+  int happy_m;     // basis size at a happy breakdown (0: none)
+  int status;      // phix_status
+  unsigned int count;
+  double omega, err, beta;
+  // --- device-side state -----------------------------------------------------
+  double eta;
+  double s[KIOPS_MMAX + 2];
+  float2 sf[KIOPS_MMAX + 2];
+  double hd[KIOPS_MMAX + 2];   // h_{j,j}
+  double hu[KIOPS_MMAX + 2];   // h_{j-1,j}
+  double hl[KIOPS_MMAX + 2];   // h_{j+1,j}
+  double z0[KIOPS_MMAX + 2];   // ||A~ V_j|| before orthogonalisation
+  double tail[(KIOPS_MMAX + 2) * KIOPS_PMAX];
+  double F[KIOPS_MMAX + 2];
+  double coef[KIOPS_MMAX + 2];  // beta * F_i * s_i
+  float2 coeff[KIOPS_MMAX + 2];
+  // coefficients of the next pass-1 launch: k (x h s_j), ga, b-column weights
+  double kd[8], gad, bd[KIOPS_PMAX];
+  float2 kf[8], gaf, bf[KIOPS_PMAX];
+  // coefficients of the next pass-2 launch: z' = z - c1 Zhat_j - c0 Zhat_{j-1}
+  double c1d, c0d;
+  float2 c1f, c0f;
+};
+constexpr size_t KIOPS_HOST_BYTES = 40;  // leading fields the host reads back
+
+struct KiopsSpec {
+  int prec, op, nx, ny, p;
+  int nb;                       // nonzero b_j, j >= 1 (converted copies in bz[])
+  int bslot[KIOPS_PMAX];        // tail index t of each nonzero b (b_{p-t})
+  const void* bz[KIOPS_PMAX];   // their copies in the iteration precision
+  void* const* Z;               // device array of basis slot pointers (host copy in Zh)
+  void* Zh[KIOPS_MMAX + 2];
+  const void* st;               // Jacobian state planes
+  KiopsCtl* kc;
+  double* partials;
+  double h;                     // A = h J
+  double kJ[8];                 // unscaled uniform J coefficients
+  int nscaled;
+  int grid;
+};
+// w_0: Zhat_0 = b_0 (or 0), tail_0 = e_p / eta, s_0 = 1/||w||, next pass-1 coefficients.
+cudaError_t kiops_start(const KiopsSpec& s, const double* b0, double eta, cudaStream_t st);
+// Convert b (float64) into the iteration precision; accumulate its 1-norm into *norm1.
+cudaError_t kiops_convert(int prec, size_t n, const double* b, void* out, double* partials,
+                          unsigned int* counter, double* norm1, int grid, cudaStream_t st);
+// Arnoldi step j: pass 1 (z = A~ V_j, dots) and pass 2 (orthogonalise, norm).
+cudaError_t kiops_arnoldi(const KiopsSpec& s, int j, cudaStream_t st);
+// F = exp(tau Hbar) e_1 (n = m+1, or m after a happy breakdown), err, omega.
+cudaError_t kiops_smallexp(KiopsCtl* kc, int m, double tau, double tau_end, double tol, cudaStream_t st);
+// w = sum_{i<n} coef_i Zhat_i into slot 0, s_0 = 1/||w||; out (float64, may be NULL) = scale * w_N.
+cudaError_t kiops_combine(const KiopsSpec& s, int n, double* out, double scale, cudaStream_t st);
+
 // ---- float64 stage kernels (stage_kernels.cu) -----------------------------
 struct OpDesc {
   int kind, nx, ny;
