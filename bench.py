@@ -45,6 +45,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--clock-ms", type=int, default=200, help="nvidia-smi sampling period (0 = off)")
+    ap.add_argument("--method", default="leja", choices=["leja", "kiops"])
+    ap.add_argument("--workload", default="grayscott", choices=["grayscott", "burgers"],
+                    help="grayscott: EXPRB43 steps (headline); burgers: phi_1(hJ) f h actions on the "
+                         "2048^2 Burgers state (mixed-precision workload)")
     return ap.parse_args()
 
 
@@ -139,6 +143,7 @@ def run_phix(args, world, rank, local):
     op = phix.make_jop(phix.PHIX_OP_GRAYSCOTT, n, n, [prm["Du"], prm["Dv"], prm["F"], prm["k"]])
     prec = getattr(phix, "PHIX_" + args.prec)
     opts = phix.phix_opts_default(prec=prec, profile=1)
+    meth = phix.PHIX_KIOPS if args.method == "kiops" else phix.PHIX_LEJA
     tol = 1e-8
     h = prm["h"]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 135 MB L2
@@ -146,7 +151,7 @@ def run_phix(args, world, rank, local):
     # ---- device-resident run -------------------------------------------------
     u = torch.tensor(u0, dtype=torch.float64, device="cuda")
     for _ in range(args.warmup):
-        phix.phix_exprb43_step(ctx, op, u, h, tol, phix.PHIX_LEJA, opts)
+        phix.phix_exprb43_step(ctx, op, u, h, tol, meth, opts)
     u.copy_(torch.tensor(u0, dtype=torch.float64, device="cuda"))
     stats = []
     sampler = ClockSampler(local, args.clock_ms)
@@ -159,7 +164,7 @@ def run_phix(args, world, rank, local):
     e0.record(stream)
     for _ in range(args.steps):
         flush.fill_(1.0)  # L2 flush between steps
-        stats.append(phix.phix_exprb43_step(ctx, op, u, h, tol, phix.PHIX_LEJA, opts).as_dict())
+        stats.append(phix.phix_exprb43_step(ctx, op, u, h, tol, meth, opts).as_dict())
     e1.record(stream)
     torch.cuda.synchronize()
     clocks = sampler.stop()
@@ -175,7 +180,7 @@ def run_phix(args, world, rank, local):
     uref = torch.tensor(u0, dtype=torch.float64, device="cuda")
     o64 = phix.phix_opts_default(prec=phix.PHIX_FP64)
     for _ in range(args.steps):
-        phix.phix_exprb43_step(ctx, op, uref, h, tol, phix.PHIX_LEJA, o64)
+        phix.phix_exprb43_step(ctx, op, uref, h, tol, meth, o64)
     ur = uref.cpu().numpy()
     rel_err = float(np.linalg.norm(u_fast - ur) / np.linalg.norm(ur))
     rel_err_incr = float(np.linalg.norm(u_fast - ur) / max(np.linalg.norm(ur - u0), 1e-300))
@@ -195,7 +200,7 @@ def run_phix(args, world, rank, local):
         for _ in range(args.steps):
             flush.fill_(1.0)
             ud.copy_(hbuf, non_blocking=True)
-            phix.phix_exprb43_step(ctx, op, ud, h, tol, phix.PHIX_LEJA, opts)
+            phix.phix_exprb43_step(ctx, op, ud, h, tol, meth, opts)
             hout.copy_(ud, non_blocking=True)
             torch.cuda.current_stream().synchronize()
             hbuf.copy_(hout)
@@ -234,8 +239,9 @@ def run_phix(args, world, rank, local):
         "vs_baseline": None,
         "dtype": "f32x2 (double-float)" if args.prec == "DF64" else args.prec.lower(),
         "data": "synthetic (seeded Gray-Scott initial state, seed = rank)",
-        "config": {"workload": WORKLOAD, "grid": [n, n], "species": 2, "unknowns": N, "h": h, "tol": tol,
-                   "method": "leja", "prec": args.prec, "parallelism": "replicas" if world > 1 else "single",
+        "config": {"workload": WORKLOAD if args.method == "leja" else WORKLOAD.replace("Leja", "KIOPS"),
+                   "grid": [n, n], "species": 2, "unknowns": N, "h": h, "tol": tol,
+                   "method": args.method, "prec": args.prec, "parallelism": "replicas" if world > 1 else "single",
                    "l2": "flushed between steps (256 MB write, inside the timed region)"},
         "time_steps_per_s": args.steps * world / (ms * 1e-3),
         "hbm_gbs_iteration_algorithmic": achieved,
@@ -262,6 +268,60 @@ def run_phix(args, world, rank, local):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(result), flush=True)
+
+
+def run_burgers(args, world, rank, local):
+    """phi_1(h J) f(u) h on the Burgers 2048^2 state: one action per step, with
+    the interval from power iteration; every precision's result is compared
+    with the float64 path's."""
+    import torch
+    import synth
+    from paper_2211_08948_gb300 import build, phix
+    torch.cuda.set_device(local)
+    build.build()
+    stream = torch.cuda.current_stream()
+    ctx = phix.phix_create(stream)
+    n = 2048 if args.n == 1024 else args.n
+    prm = synth.burgers_params(n)
+    u0 = torch.tensor(synth.burgers_state(n, seed=rank), dtype=torch.float64, device="cuda")
+    op = phix.make_jop(phix.PHIX_OP_BURGERS, n, n, [prm["nu"]], u0)
+    h = prm["h"]
+    # v = f(u0) h (the expensive term of the step), by the library's RHS kernel
+    v = torch.empty_like(u0)
+    phix.phix_rhs(ctx, op, u0, v)
+    v.mul_(h)
+    meth = phix.PHIX_KIOPS if args.method == "kiops" else phix.PHIX_LEJA
+    tol = 1e-8
+    res = {}
+    outs = {}
+    for pr in ["FP64", "DF64", "FP32_JV", "FP32"]:
+        o = phix.phix_opts_default(prec=getattr(phix, "PHIX_" + pr), profile=1)
+        out = torch.empty_like(v)
+        for _ in range(args.warmup):
+            phix.phix_phi_action(ctx, op, h, v, [1], [1.0], [out], tol, meth, o)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        st = []
+        e0.record(stream)
+        for _ in range(args.steps):
+            st.append(phix.phix_phi_action(ctx, op, h, v, [1], [1.0], [out], tol, meth, o).as_dict())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        outs[pr] = out.clone()
+        it_ms = sum(s["iter_ms"] for s in st)
+        it_b = sum(s["iter_bytes"] for s in st)
+        res[pr] = {"actions_per_s": args.steps / (ms * 1e-3), "ms_per_action": ms / args.steps,
+                   "newton_iters": st[-1]["iters"], "power_mv": st[-1]["power_mv"],
+                   "iter_gbs": it_b / (it_ms * 1e-3) / 1e9 if it_ms > 0 else None}
+    ref = outs["FP64"]
+    for pr in res:
+        res[pr]["rel_err_vs_fp64"] = float(torch.linalg.norm(outs[pr] - ref) / torch.linalg.norm(ref))
+    phix.phix_destroy(ctx)
+    print(json.dumps({"metric": METRIC, "workload": "Burgers %dx%d, nu=1e-3, phi_1(hJ) f h, h=50x explicit, "
+                      "tol 1e-8, %s" % (n, n, args.method), "unit": UNIT, "steps": args.steps,
+                      "warmup": args.warmup, "by_precision": res}), flush=True)
 
 
 def cpu_baseline(n, u0, prm, tol):
@@ -322,6 +382,8 @@ def main():
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.workload == "burgers":
+        run_burgers(args, world, rank, local)
     else:
         run_phix(args, world, rank, local)
 

@@ -167,6 +167,11 @@ phix_status phix_phi_combination(phix_ctx* ctx, const phix_jop* op, double h,
                                  const double* const* b, int p, double* out, double tol,
                                  phix_method method, const phix_opts* opts, phix_stats* stats);
 
+/* Right-hand side f(u) of the operator's PDE (Sec. 1 "f(u)", Sec. 3
+ * discretisation), float64: f and u are device vectors of length N
+ * (f may not alias u).  op->state is ignored.                             */
+phix_status phix_rhs(phix_ctx* ctx, const phix_jop* op, const double* u, double* f);
+
 /* Spectrum estimate of J (Sec. 2.2 "power iterations"): *rho = ||J v_k||
  * for the power iterate v_k from a SplitMix64 start vector.               */
 phix_status phix_spectrum(phix_ctx* ctx, const phix_jop* op, const phix_opts* opts,
@@ -186,6 +191,18 @@ phix_status phix_exprb43_step(phix_ctx* ctx, const phix_jop* op, double* u_inout
 phix_status phix_epirk4s3_step(phix_ctx* ctx, const phix_jop* op, double* u_inout, double h,
                                double tol, phix_method method, const phix_opts* opts,
                                double* err_est, phix_stats* stats);
+
+/* The small exponential of the Krylov method (Sec. 2.1: "computing the
+ * exponential of the Hessenberg matrix"): F = exp(tau T) e_1 for an n x n
+ * tridiagonal T (the Hessenberg matrix of window-2 incomplete
+ * orthogonalisation), 1 <= n <= 129.  d[n] diagonal, u[n-1] super- and
+ * l[n-1] sub-diagonal, F[n] output: DEVICE float64 arrays.  One CTA:
+ * Chebyshev expansion on the exact real range of the field of values, or a
+ * shifted Taylor series with scaling when T is strongly non-normal; normwise
+ * accuracy ~1e-15 ||exp(tau T)||.  *method (host, may be NULL) receives 0
+ * (Chebyshev) or 1 (Taylor).  Synchronises the context's stream.          */
+phix_status phix_small_expm(phix_ctx* ctx, int n, const double* d, const double* u, const double* l,
+                            double tau, double* F, int* method);
 
 /* No counterpart in the paper: a library-interface addition.
  *

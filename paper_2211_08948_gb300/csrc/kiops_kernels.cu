@@ -265,67 +265,264 @@ __global__ void __launch_bounds__(THREADS) k_arn2(ArnArgs a, size_t n) {
   }
 }
 
-// F = exp(tau Hbar) e_1 by Taylor series with scaling (segments of norm <= 1)
-// after a shift by the mean diagonal: exp(tau Hbar) = e^{tau mu} exp(tau (Hbar - mu I)).
+// F = exp(tau Hbar) e_1 for the tridiagonal Hbar (one CTA).
+//
+// Main method: Chebyshev expansion on [lo, hi], the exact range of the real
+// parts of the field of values W(X), X = tau Hbar, i.e. the extreme
+// eigenvalues of the symmetric part (X + X^T)/2 (Bendixson):
+//   e^{c + r t} = e^{c + r} (I~_0(r) + 2 sum_k I~_k(r) T_k(t)),  I~_k = e^{-r} I_k,
+// applied with the three-term recurrence to Y = (X - c I)/r.  The extreme
+// eigenvalues come from a 128-way Sturm-sequence multisection (float32
+// counts, then a 1e-5 relative safety margin); the imaginary extent iota is
+// the spectral radius of the skew part (same routine on |skew| entries).
+// The scaled modified Bessel values come from Miller's backward recurrence
+// normalised by I~_0 + 2 sum_k I~_k = 1; the term count makes
+// 2 I~_k rho^k <= 1e-16, rho the Bernstein-ellipse parameter holding the box
+// [lo, hi] x [-iota, iota].  With Crouzeix's bound the error is ~1e-16
+// e^{hi} >= 1e-16 ||exp(X)||, i.e. normwise like a dense expm.
+// Fallback (iota > r/2 or no admissible term count): Taylor series in
+// segments of norm <= 1 after the shift by the interval midpoint.
+constexpr int CHEB_MAX = 600;
+
+__device__ void tridiag_apply(int n, const double* dg, const double* up, const double* lo, double shift, double sc,
+                              const double* in, double* out, int tid) {
+  // out = sc * (T - shift I) in, T = tridiag(lo, dg, up)
+  for (int i = tid; i < n; i += 128) {
+    double v = (dg[i] - shift) * in[i];
+    if (i + 1 < n) v = fma(up[i], in[i + 1], v);
+    if (i >= 1) v = fma(lo[i - 1], in[i - 1], v);
+    out[i] = sc * v;
+  }
+}
+
+// number of eigenvalues < x of the symmetric tridiagonal (diag a, squared off-diagonal b2)
+__device__ int sturm_count(int n, const float* a, const float* b2, float x) {
+  int cnt = 0;
+  float q = a[0] - x;
+  cnt += q < 0.f;
+  for (int i = 1; i < n; ++i) {
+    if (q == 0.f) q = 1e-30f;
+    q = (a[i] - x) - b2[i - 1] / q;
+    cnt += q < 0.f;
+  }
+  return cnt;
+}
+
+// Block-wide multisection: the largest (want_max) or smallest eigenvalue of the
+// symmetric tridiagonal, bracketed in [lo, hi].  Returns an outer bound.
+__device__ double eig_bound(int n, const float* a, const float* b2, double lo, double hi, bool want_max,
+                            int* cnt, double* br, int tid) {
+  for (int round = 0; round < 4; ++round) {
+    const double x = lo + (hi - lo) * (double)(tid + 1) / 129.0;
+    cnt[tid] = sturm_count(n, a, b2, (float)x);
+    __syncthreads();
+    if (tid == 0) {
+      double nlo = lo, nhi = hi;
+      if (want_max) {  // smallest point with all eigenvalues below it
+        int t = 0;
+        while (t < 128 && cnt[t] < n) ++t;
+        nhi = (t < 128) ? lo + (hi - lo) * (t + 1) / 129.0 : hi;
+        nlo = (t > 0) ? lo + (hi - lo) * t / 129.0 : lo;
+      } else {  // largest point with no eigenvalue below it
+        int t = 127;
+        while (t >= 0 && cnt[t] > 0) --t;
+        nlo = (t >= 0) ? lo + (hi - lo) * (t + 1) / 129.0 : lo;
+        nhi = (t < 127) ? lo + (hi - lo) * (t + 2) / 129.0 : hi;
+      }
+      br[0] = nlo;
+      br[1] = nhi;
+    }
+    __syncthreads();
+    lo = br[0];
+    hi = br[1];
+    __syncthreads();
+  }
+  const double margin = 1e-5 * (fabs(lo) + fabs(hi)) + 1e-300;
+  return want_max ? hi + margin : lo - margin;
+}
+
+// x = exp(T) e_1 for the n x n tridiagonal T = tridiag(lo, dg, up) (already
+// scaled by tau); lead: on return x holds exp(T) e_1 / e^{lead}.  Block-wide
+// (128 threads); work arrays in shared memory.
+struct SmallExpWork {
+  double x[KIOPS_MMAX + 2], t0[KIOPS_MMAX + 2], t1[KIOPS_MMAX + 2], t2[KIOPS_MMAX + 2];
+  double bes[CHEB_MAX + 2];
+  float fa[KIOPS_MMAX + 2], fs2[KIOPS_MMAX + 2], fk2[KIOPS_MMAX + 2], fz[KIOPS_MMAX + 2];
+  int cnt[128];
+  double br[2];
+  int mode, S, K;
+  double shift, c, r, lead, glo, ghi, kb, rad;
+};
+
+__device__ void small_exp_e1(int n, const double* dg, const double* up, const double* lo, SmallExpWork& w,
+                             int tid) {
+  if (tid == 0) {
+    double glo = 1e300, ghi = -1e300, kb = 0.0;
+    for (int i = 0; i < n; ++i) {
+      const double s = (i + 1 < n) ? 0.5 * (up[i] + lo[i]) : 0.0;
+      const double k = (i + 1 < n) ? 0.5 * (up[i] - lo[i]) : 0.0;
+      w.fa[i] = (float)dg[i];
+      w.fs2[i] = (float)(s * s);
+      w.fk2[i] = (float)(k * k);
+      w.fz[i] = 0.f;
+      double rs = fabs(s), rk = fabs(k);
+      if (i >= 1) {
+        rs += 0.5 * fabs(up[i - 1] + lo[i - 1]);
+        rk += 0.5 * fabs(up[i - 1] - lo[i - 1]);
+      }
+      glo = fmin(glo, dg[i] - rs);
+      ghi = fmax(ghi, dg[i] + rs);
+      kb = fmax(kb, rk);
+    }
+    w.glo = glo - 1e-6 * (fabs(glo) + 1.0);
+    w.ghi = ghi + 1e-6 * (fabs(ghi) + 1.0);
+    w.kb = kb * (1.0 + 1e-6) + 1e-300;
+  }
+  __syncthreads();
+  const double lam_hi = eig_bound(n, w.fa, w.fs2, w.glo, w.ghi, true, w.cnt, w.br, tid);
+  const double lam_lo = eig_bound(n, w.fa, w.fs2, w.glo, w.ghi, false, w.cnt, w.br, tid);
+  const double iota = (n > 1) ? eig_bound(n, w.fz, w.fk2, 0.0, w.kb, true, w.cnt, w.br, tid) : 0.0;
+  if (tid == 0) {
+    const double r = 0.5 * (lam_hi - lam_lo), c = 0.5 * (lam_hi + lam_lo);
+    int mode = 0;  // 0 Chebyshev, 1 Taylor
+    int K = -1;
+    if (!(r >= 1e-3) || iota > 0.5 * r) mode = 1;
+    if (mode == 0) {
+      const double y0 = iota / r;
+      const double b2 = 0.5 * (y0 * y0 + sqrt(y0 * y0 * y0 * y0 + 4.0 * y0 * y0));
+      const double rho = sqrt(1.0 + b2) + sqrt(b2);
+      int kmax = (int)(r + 12.0 * sqrt(r) + 60.0);
+      if (kmax > CHEB_MAX) kmax = CHEB_MAX;
+      double ip1 = 0.0, ik = 1e-280;
+      const int kstart = kmax + 40 + (int)sqrt(r);
+      const double ir = 1.0 / r;
+      for (int k = kstart; k >= 0; --k) {
+        if (k <= kmax) w.bes[k] = ik;
+        const double im1 = (2.0 * k * ir) * ik + ip1;  // I_{k-1} = (2k/r) I_k + I_{k+1}
+        ip1 = ik;
+        ik = im1;
+        if (fabs(ik) > 1e250) {
+          ik *= 1e-250;
+          ip1 *= 1e-250;
+          for (int q = k; q <= kmax; ++q) w.bes[q] *= 1e-250;
+        }
+      }
+      double sum = w.bes[0];
+      for (int k = 1; k <= kmax; ++k) sum += 2.0 * w.bes[k];
+      const double isum = 1.0 / sum;
+      for (int k = 0; k <= kmax; ++k) w.bes[k] *= isum;
+      // term count, and the amplification max_k 2 I~_k rho^k of rounding errors
+      double rk = 1.0, amp = 0.0;
+      for (int k = 0; k <= kmax; ++k) {
+        amp = fmax(amp, 2.0 * w.bes[k] * rk);
+        if (k > 2 && 2.0 * w.bes[k] * rk <= 1e-16 && 2.0 * w.bes[k - 1] * rk / rho <= 1e-16) {
+          K = k;
+          break;
+        }
+        rk *= rho;
+        if (rk > 1e200) break;
+      }
+      if (K < 0 || amp > 100.0) mode = 1;
+    }
+    if (mode == 1) {
+      // shift to the centre of the field-of-values box; ||T - cI||_2 <= 2 w(T - cI)
+      // <= 2 sqrt(r^2 + iota^2) (numerical radius), or the 1-norm if smaller
+      double nrm1 = 0.0;
+      for (int i = 0; i < n; ++i) {
+        double cs = fabs(dg[i] - c);
+        if (i >= 1) cs += fabs(up[i - 1]);
+        if (i + 1 < n) cs += fabs(lo[i]);
+        nrm1 = fmax(nrm1, cs);
+      }
+      const double nrm = fmin(nrm1, 2.0 * sqrt(r * r + iota * iota));
+      w.shift = c;
+      w.S = nrm > 4.0 ? (int)ceil(nrm / 4.0) : 1;
+      w.lead = c;
+    } else {
+      w.c = c;
+      w.r = r;
+      w.lead = lam_hi;  // e^{c + r}
+    }
+    w.mode = mode;
+    w.K = K;
+  }
+  __syncthreads();
+  double* x = w.x;
+  if (w.mode == 1) {
+    // Taylor, S segments of norm <= 4, 30 terms each (4^31/31! < 6e-16)
+    const int S = w.S;
+    const double mu = w.shift;
+    const double sc = 1.0 / S;
+    for (int i = tid; i < n; i += 128) x[i] = (i == 0) ? 1.0 : 0.0;
+    __syncthreads();
+    for (int seg = 0; seg < S; ++seg) {
+      for (int i = tid; i < n; i += 128) w.t0[i] = x[i];
+      __syncthreads();
+      double* cur = w.t0;
+      double* nxt = w.t1;
+      for (int k = 1; k <= 30; ++k) {
+        tridiag_apply(n, dg, up, lo, mu, sc / k, cur, nxt, tid);
+        for (int i = tid; i < n; i += 128) x[i] += nxt[i];
+        __syncthreads();
+        double* tsw = cur;
+        cur = nxt;
+        nxt = tsw;
+      }
+    }
+  } else {
+    // x = I~_0 e1 + 2 sum_{k>=1} I~_k T_k(Y) e1,  Y = (T - cI)/r
+    const int K = w.K;
+    const double c = w.c, ir = 1.0 / w.r;
+    double* tm = w.t0;
+    double* tc = w.t1;
+    double* tn = w.t2;
+    for (int i = tid; i < n; i += 128) {
+      tm[i] = (i == 0) ? 1.0 : 0.0;
+      x[i] = (i == 0) ? w.bes[0] : 0.0;
+    }
+    __syncthreads();
+    tridiag_apply(n, dg, up, lo, c, ir, tm, tc, tid);
+    for (int i = tid; i < n; i += 128) x[i] += 2.0 * w.bes[1] * tc[i];
+    __syncthreads();
+    for (int k = 2; k < K; ++k) {
+      tridiag_apply(n, dg, up, lo, c, 2.0 * ir, tc, tn, tid);
+      for (int i = tid; i < n; i += 128) {
+        const double v = tn[i] - tm[i];
+        tn[i] = v;
+        x[i] = fma(2.0 * w.bes[k], v, x[i]);
+      }
+      __syncthreads();
+      double* tsw = tm;
+      tm = tc;
+      tc = tn;
+      tn = tsw;
+    }
+  }
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(128) k_kexp(KiopsCtl* kc, int m, double tau, double tau_end, double tol) {
   __shared__ double dg[KIOPS_MMAX + 2], up[KIOPS_MMAX + 2], lo[KIOPS_MMAX + 2];
-  __shared__ double x[KIOPS_MMAX + 2], t0[KIOPS_MMAX + 2], t1[KIOPS_MMAX + 2], red[128];
-  __shared__ int n_s, S_s;
-  __shared__ double mu_s;
+  __shared__ SmallExpWork w;
+  __shared__ int n_s;
   const int tid = threadIdx.x;
   if (tid == 0) {
     const int hm = kc->happy_m;
     const int mm = hm > 0 ? hm : m;
     n_s = hm > 0 ? hm : m + 1;
     const int n = n_s;
-    double tr = 0.0;
     for (int i = 0; i < n; ++i) {
-      dg[i] = i < mm ? kc->hd[i] : 0.0;          // row m of Hbar has no diagonal
-      up[i] = (i + 1 < mm) ? kc->hu[i + 1] : 0.0;  // (i, i+1); column m is zero
-      lo[i] = (i + 1 < n) ? kc->hl[i] : 0.0;       // (i+1, i)
-      tr += dg[i];
+      dg[i] = tau * (i < mm ? kc->hd[i] : 0.0);          // row m of Hbar has no diagonal
+      up[i] = tau * ((i + 1 < mm) ? kc->hu[i + 1] : 0.0);  // (i, i+1); column m is zero
+      lo[i] = tau * ((i + 1 < n) ? kc->hl[i] : 0.0);       // (i+1, i)
     }
-    const double mu = tr / n;
-    mu_s = mu;
-    double nrm = 0.0;  // 1-norm of tau (Hbar - mu I)
-    for (int i = 0; i < n; ++i) {
-      double cs = fabs(tau * (dg[i] - mu));
-      if (i >= 1) cs += fabs(tau * up[i - 1]);
-      if (i + 1 < n) cs += fabs(tau * lo[i]);
-      nrm = fmax(nrm, cs);
-    }
-    S_s = nrm > 1.0 ? (int)ceil(nrm) : 1;
   }
   __syncthreads();
-  const int n = n_s, S = S_s;
-  const double mu = mu_s;
-  const double sc = tau / S;
-  for (int i = tid; i < n; i += 128) x[i] = (i == 0) ? 1.0 : 0.0;
-  __syncthreads();
-  for (int seg = 0; seg < S; ++seg) {
-    for (int i = tid; i < n; i += 128) t0[i] = x[i];
-    __syncthreads();
-    double* cur = t0;
-    double* nxt = t1;
-    for (int k = 1; k <= 18; ++k) {
-      const double f = sc / k;
-      for (int i = tid; i < n; i += 128) {
-        double v = (dg[i] - mu) * cur[i];
-        if (i + 1 < n) v = fma(up[i], cur[i + 1], v);
-        if (i >= 1) v = fma(lo[i - 1], cur[i - 1], v);
-        v *= f;
-        nxt[i] = v;
-        x[i] += v;
-      }
-      __syncthreads();
-      double* tsw = cur;
-      cur = nxt;
-      nxt = tsw;
-    }
-  }
-  const double e = exp(tau * mu);
+  const int n = n_s;
+  small_exp_e1(n, dg, up, lo, w, tid);
+  const double e = exp(w.lead);
   for (int i = tid; i < n; i += 128) {
-    const double Fi = e * x[i];
+    const double Fi = e * w.x[i];
     kc->F[i] = Fi;
     const double cf = kc->beta * Fi * kc->s[i];
     kc->coef[i] = cf;
@@ -335,7 +532,7 @@ __global__ void __launch_bounds__(128) k_kexp(KiopsCtl* kc, int m, double tau, d
   if (tid == 0) {
     double omega = 0.0, err = 0.0;
     if (kc->happy_m == 0) {
-      err = kc->beta * fabs(e * x[m]);
+      err = kc->beta * fabs(e * w.x[m]);
       omega = (tau_end / tau) * err / (tol * kc->beta);
     }
     kc->err = err;
@@ -343,7 +540,24 @@ __global__ void __launch_bounds__(128) k_kexp(KiopsCtl* kc, int m, double tau, d
     if (!isfinite(omega)) kc->status = PHIX_ENAN;
     __threadfence();
   }
-  (void)red;
+}
+
+// exp(tau T) e_1 for a caller's tridiagonal T (device arrays), out[n]
+__global__ void __launch_bounds__(128) k_smallexp(int n, const double* d, const double* u, const double* l,
+                                                  double tau, double* out, int* mode_out) {
+  __shared__ double dg[KIOPS_MMAX + 2], up[KIOPS_MMAX + 2], lo[KIOPS_MMAX + 2];
+  __shared__ SmallExpWork w;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < n; i += 128) {
+    dg[i] = tau * d[i];
+    up[i] = (i + 1 < n) ? tau * u[i] : 0.0;
+    lo[i] = (i + 1 < n) ? tau * l[i] : 0.0;
+  }
+  __syncthreads();
+  small_exp_e1(n, dg, up, lo, w, tid);
+  const double e = exp(w.lead);
+  for (int i = tid; i < n; i += 128) out[i] = e * w.x[i];
+  if (tid == 0 && mode_out) *mode_out = w.mode;
 }
 
 struct CombArgs {
@@ -560,6 +774,13 @@ cudaError_t arn_p(const KiopsSpec& s, int j, cudaStream_t st) {
 
 cudaError_t kiops_arnoldi(const KiopsSpec& s, int j, cudaStream_t st) {
   return s.prec == P_FP64 ? arn_p<P_FP64>(s, j, st) : arn_p<P_DF64>(s, j, st);
+}
+
+cudaError_t small_expm_e1(int n, const double* d, const double* u, const double* l, double tau, double* out,
+                          int* mode, cudaStream_t st) {
+  if (n < 1 || n > KIOPS_MMAX + 1) return cudaErrorInvalidValue;
+  k_smallexp<<<1, 128, 0, st>>>(n, d, u, l, tau, out, mode);
+  return cudaGetLastError();
 }
 
 cudaError_t kiops_smallexp(KiopsCtl* kc, int m, double tau, double tau_end, double tol, cudaStream_t st) {

@@ -25,7 +25,7 @@ enum Slot {
   S_F, S_A, S_B, S_RA, S_RB, S_T0, S_Q, S_T3, S_T4, S_O1, S_O2, S_O3,  // stages
   S_SUB_U, S_SUB_TMP, S_SUB_W0,                                  // substeps (W0..W0+8)
   S_PTAB = S_SUB_W0 + 9,                                         // chain parameter block
-  S_KBASIS, S_KB, S_KPTR, S_KCTL,                                // KIOPS basis, b copies, slot table, control
+  S_KBASIS, S_KB, S_KPTR, S_KCTL, S_KMODE,                       // KIOPS basis, b copies, slot table, control
   S_NSLOT
 };
 
@@ -854,6 +854,36 @@ phix_status phix_divided_differences(int l, double a, double b, int m, double* d
   std::vector<double> t = dd_table(l, a, b, m);
   std::memcpy(d, t.data(), sizeof(double) * m);
   return PHIX_OK;
+}
+
+phix_status phix_small_expm(phix_ctx* ctx, int n, const double* d, const double* u, const double* l,
+                            double tau, double* F, int* method) {
+  return guarded(ctx, nullptr, [&](phix_stats&) -> phix_status {
+    if (n < 1 || n > KIOPS_MMAX + 1 || !d || !F || (n > 1 && (!u || !l)) || !std::isfinite(tau))
+      fail(ctx, PHIX_EINVAL, "bad small_expm arguments");
+    int* md = static_cast<int*>(ws(ctx, S_KMODE, sizeof(int)));
+    KL(small_expm_e1(n, d, u, l, tau, F, md, ctx->stream));
+    int mh = 0;
+    CK(cudaMemcpyAsync(&mh, md, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (method) *method = mh;
+    return PHIX_OK;
+  });
+}
+
+phix_status phix_rhs(phix_ctx* ctx, const phix_jop* op, const double* u, double* f) {
+  return guarded(ctx, nullptr, [&](phix_stats&) -> phix_status {
+    check_op(ctx, op, false);
+    if (!u || !f || u == f) fail(ctx, PHIX_EINVAL, "u/f NULL or aliased");
+    OpDesc d{};
+    d.kind = op->kind;
+    d.nx = op->nx;
+    d.ny = op->ny;
+    for (int i = 0; i < 8; ++i) d.p[i] = op->param[i];
+    KL(launch_rhs(d, u, f, ctx->grid_stream, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PHIX_OK;
+  });
 }
 
 phix_status phix_spectrum(phix_ctx* ctx, const phix_jop* op, const phix_opts* opts, double* rho,

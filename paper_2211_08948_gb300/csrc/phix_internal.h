@@ -177,6 +177,9 @@ cudaError_t kiops_convert(int prec, size_t n, const double* b, void* out, double
 cudaError_t kiops_arnoldi(const KiopsSpec& s, int j, cudaStream_t st);
 // F = exp(tau Hbar) e_1 (n = m+1, or m after a happy breakdown), err, omega.
 cudaError_t kiops_smallexp(KiopsCtl* kc, int m, double tau, double tau_end, double tol, cudaStream_t st);
+// out = exp(tau T) e_1 for a tridiagonal T (device arrays d[n], u[n-1], l[n-1]); mode: 0 Chebyshev, 1 Taylor
+cudaError_t small_expm_e1(int n, const double* d, const double* u, const double* l, double tau, double* out,
+                          int* mode, cudaStream_t st);
 // w = sum_{i<n} coef_i Zhat_i into slot 0, s_0 = 1/||w||; out (float64, may be NULL) = scale * w_N.
 cudaError_t kiops_combine(const KiopsSpec& s, int n, double* out, double scale, cudaStream_t st);
 

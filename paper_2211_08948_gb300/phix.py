@@ -25,7 +25,7 @@ PHIX_OP_ADVDIFF, PHIX_OP_GRAYSCOTT, PHIX_OP_BURGERS = 0, 1, 2
 EXPORTS = [
     "phix_opts_default", "phix_version", "phix_create", "phix_destroy", "phix_last_error",
     "phix_phi_action", "phix_phi_combination", "phix_spectrum", "phix_exprb43_step",
-    "phix_epirk4s3_step", "phix_leja_points", "phix_divided_differences", "phix_phi_action_noalloc",
+    "phix_epirk4s3_step", "phix_rhs", "phix_small_expm", "phix_leja_points", "phix_divided_differences", "phix_phi_action_noalloc",
 ]
 
 
@@ -89,6 +89,8 @@ def load(path=None):
                                     ctypes.POINTER(phix_opts), ctypes.POINTER(phix_stats)]
     lib.phix_phi_combination.argtypes = [P, ctypes.POINTER(phix_jop), D, ctypes.POINTER(P), I, P, D, I,
                                          ctypes.POINTER(phix_opts), ctypes.POINTER(phix_stats)]
+    lib.phix_rhs.argtypes = [P, ctypes.POINTER(phix_jop), P, P]
+    lib.phix_small_expm.argtypes = [P, I, P, P, P, D, P, ctypes.POINTER(I)]
     lib.phix_spectrum.argtypes = [P, ctypes.POINTER(phix_jop), ctypes.POINTER(phix_opts),
                                   ctypes.POINTER(D), ctypes.POINTER(phix_stats)]
     for f in (lib.phix_exprb43_step, lib.phix_epirk4s3_step):
@@ -209,6 +211,18 @@ def phix_phi_combination(ctx, op, h, b, out, tol, method=PHIX_LEJA, opts=None, c
     if check:
         _check(ctx, rc)
     return st
+
+
+def phix_small_expm(ctx, d, u, l, tau, F):
+    """F <- exp(tau T) e_1 for the tridiagonal T = tridiag(l, d, u); returns 0 (Chebyshev) or 1 (Taylor)."""
+    m = ctypes.c_int()
+    _check(ctx, load().phix_small_expm(ctx, d.numel(), _ptr(d), _ptr(u), _ptr(l), tau, _ptr(F), ctypes.byref(m)))
+    return m.value
+
+
+def phix_rhs(ctx, op, u, f):
+    """f <- f(u) (float64)."""
+    _check(ctx, load().phix_rhs(ctx, ctypes.byref(op), _ptr(u), _ptr(f)))
 
 
 def phix_spectrum(ctx, op, opts=None):

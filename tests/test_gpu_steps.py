@@ -90,3 +90,25 @@ def test_step_grayscott_1024_full_size(px):
     assert st.power_mv == ost["power_mv"]
     assert rel(got - u0, u4 - u0) <= 1e-7
     assert rel(got, u4) <= 1e-10
+
+
+@pytest.mark.parametrize("kind", ["advdiff", "grayscott", "burgers"])
+def test_rhs_vs_oracle(px, kind):
+    from oracle.operators import Burgers
+    phix, ctx = px
+    nx, ny = 40, 24
+    rng = np.random.default_rng(11)
+    if kind == "advdiff":
+        prm, ncomp, kd = [0.3, 2.0, -1.0], 1, phix.PHIX_OP_ADVDIFF
+        oop = AdvDiff(nx, *prm, ny=ny)
+    elif kind == "grayscott":
+        prm, ncomp, kd = [2e-3, 1e-3, 0.04, 0.06], 2, phix.PHIX_OP_GRAYSCOTT
+        oop = GrayScott(nx, *prm, ny=ny)
+    else:
+        prm, ncomp, kd = [1e-2], 1, phix.PHIX_OP_BURGERS
+        oop = Burgers(nx, *prm, ny=ny)
+    u = rng.random(ncomp * nx * ny)
+    ud = dev(u)
+    fd = torch.empty_like(ud)
+    phix.phix_rhs(ctx, phix.make_jop(kd, nx, ny, prm), ud, fd)
+    assert rel(host(fd), oop.f(u)) <= 1e-13
