@@ -192,6 +192,35 @@ phix_status phix_epirk4s3_step(phix_ctx* ctx, const phix_jop* op, double* u_inou
                                double tol, phix_method method, const phix_opts* opts,
                                double* err_est, phix_stats* stats);
 
+/* One problem of a batch: a periodic advection-diffusion operator
+ * J = D lap + ax d/dx + ay d/dy on an nx x ny grid, a step h, its spectral
+ * interval and the vectors.                                               */
+typedef struct {
+  int nx, ny;          /* grid, >= 3                                                 */
+  double D, ax, ay;    /* operator coefficients                                      */
+  double h;            /* step: outputs are phi_{l[k]}(h J) v                        */
+  double rho_re;       /* > 0: Leja interval [-rho_re, rho_hi] of the real spectrum  */
+  double rho_hi;
+  double rho_im;       /* >= 0: bound on |Im lambda(J)| (substep count, iota_cap)    */
+  const double* v;     /* device, nx*ny                                              */
+  double* out[3];      /* device, nx*ny each, out[k] for l[k], k < nout             */
+} phix_batch_problem;
+
+/* Batched actions (north_star form "batching"; Sec. 2.2 per problem): for
+ * every problem i < nprob, out[k] = phi_{l[k]}(h_i J_i) v_i, k < nout <= 3,
+ * l[k] in 0..2, all in ONE persistent kernel launch replayed from a CUDA
+ * graph: each CTA takes whole problems from a largest-first queue and runs
+ * the vertical Leja pass (or the ODE-identity substeps) with block-level
+ * reductions.  opts->prec: PHIX_FP64, PHIX_DF64 or PHIX_FP32_JV; opts->m_max
+ * <= 500.  opts->profile = 1 additionally tunes the CTAs per SM on this batch
+ * (first call per batch shape) and reports the launch time in iter_ms.
+ * per_prob (HOST, may be NULL) receives each problem's status; stats->iters
+ * sums the Newton iterations of all problems.  Problems are read from HOST
+ * memory (the array), vectors are device memory.                           */
+phix_status phix_phi_action_batched(phix_ctx* ctx, const phix_batch_problem* probs, int nprob, int nout,
+                                    const int* l, double tol, const phix_opts* opts, int* per_prob,
+                                    phix_stats* stats);
+
 /* The small exponential of the Krylov method (Sec. 2.1: "computing the
  * exponential of the Hessenberg matrix"): F = exp(tau T) e_1 for an n x n
  * tridiagonal T (the Hessenberg matrix of window-2 incomplete

@@ -17,6 +17,12 @@ Readings of the paper (each listed in the design doc):
 * power iteration (Sec. 2.2 "power iterations", Sec. 5.1): start vector
   from the SplitMix64 counter generator, rho_k = ||J v_k|| / ||v_k||,
   stop at relative change <= 1e-2 or 50 matvecs; alpha = -safety*rho.
+* complex spectra: the interval rule above assumes a real spectrum; with an
+  imaginary extent rho_im the half-width is enlarged to
+  gamma = max((beta - alpha)/4, 2 rho_im) and the interval kept anchored at
+  its right end, c = beta - 2 gamma (the scaled imaginary extent stays
+  <= 1/2 and the interpolated function stays bounded on the interval).
+  With rho_im = 0 this is the paper's rule.
 * substepping: the paper substeps only the exponential; for phi_l the
   exact ODE identity below is used, one phi_l Leja pass plus l Jacobian
   actions per substep, when s h gamma exceeds gamma_cap (or s h rho_im
@@ -198,8 +204,8 @@ def leja_phi(jv, v, h, alpha, beta, outputs, tol, m_max=500, rho_im=0.0,
       u(t+tau) = sum_{j<l} tau^j/j! w_j + tau^l phi_l(tau B) w_l,
       w_0 = u(t), w_j = B w_{j-1} + v t^(l-j)/(l-j)!   (B = s_k h J).
     """
-    c = 0.5 * (alpha + beta)
-    gamma = 0.25 * (beta - alpha)
+    gamma = max(0.25 * (beta - alpha), 2.0 * rho_im)
+    c = beta - 2.0 * gamma   # = (alpha + beta)/2 unless enlarged
     xi = leja_points(m_max + 1)
     info = dict(iters=0, jv=0, substeps=0, status=OK)
     subs = [substep_count(h, s, gamma, rho_im, gamma_cap, iota_cap) for (_, s) in outputs]

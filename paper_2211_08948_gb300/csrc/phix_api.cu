@@ -26,6 +26,7 @@ enum Slot {
   S_SUB_U, S_SUB_TMP, S_SUB_W0,                                  // substeps (W0..W0+8)
   S_PTAB = S_SUB_W0 + 9,                                         // chain parameter block
   S_KBASIS, S_KB, S_KPTR, S_KCTL, S_KMODE,                       // KIOPS basis, b copies, slot table, control
+  S_BPROB, S_BORDER, S_BWS, S_BQ, S_XI,                          // batched problems, order, arena, queue, Leja points
   S_NSLOT
 };
 
@@ -56,6 +57,13 @@ struct phix_ctx {
   };
   std::vector<Graph> graphs;     // cached chains of GRAPH_NODES iteration launches
   KiopsCtl* kc_h = nullptr;      // pinned mirror of the KIOPS control header
+  struct BatchGraph {
+    unsigned long long key;
+    int grid;
+    cudaGraphExec_t exec;
+  };
+  std::vector<BatchGraph> bgraphs;  // batched launch graphs
+  std::vector<std::pair<unsigned long long, int>> btune;  // tuned CTAs per SM per batch shape
 };
 
 static constexpr int GRAPH_NODES = 8;
@@ -445,7 +453,12 @@ struct Interval {
 void leja_phi(phix_ctx* ctx, const OpState& os, int prec, double h, const double* v, int nout,
               const int* l, const double* sc, double* const* out, double tol, const phix_opts& o,
               const Interval& iv, phix_stats& stats) {
-  if (iv.gamma == 0.0) {  // zero spectrum: phi_l(0) v = v / l!
+  // complex spectra: the half-width covers twice the imaginary extent (scaled
+  // imaginary extent <= 1/2) and the interval stays anchored at its right end
+  Interval ivc = iv;
+  ivc.gamma = std::max(iv.gamma, 2.0 * std::max(0.0, o.rho_im));
+  ivc.c = (iv.c + 2.0 * iv.gamma) - 2.0 * ivc.gamma;
+  if (ivc.gamma == 0.0) {  // zero spectrum: phi_l(0) v = v / l!
     for (int k = 0; k < nout; ++k) lincomb(ctx, os.N, {1.0 / factorial(l[k])}, {v}, out[k]);
     return;
   }
@@ -453,13 +466,13 @@ void leja_phi(phix_ctx* ctx, const OpState& os, int prec, double h, const double
   int smax = 1;
   std::vector<int> subs(nout);
   for (int k = 0; k < nout; ++k) {
-    subs[k] = substeps_for(h, sc[k], iv.gamma, o.rho_im, o);
+    subs[k] = substeps_for(h, sc[k], ivc.gamma, o.rho_im, o);
     smax = std::max(smax, subs[k]);
   }
   if (smax == 1) {
     std::vector<std::vector<double>> d(nout);
-    for (int k = 0; k < nout; ++k) d[k] = dd_table(l[k], sc[k] * h * iv.c, sc[k] * h * iv.gamma, M);
-    PassResult r = leja_pass(ctx, os, prec, v, nout, d, iv.c, iv.gamma, tol, o, out);
+    for (int k = 0; k < nout; ++k) d[k] = dd_table(l[k], sc[k] * h * ivc.c, sc[k] * h * ivc.gamma, M);
+    PassResult r = leja_pass(ctx, os, prec, v, nout, d, ivc.c, ivc.gamma, tol, o, out);
     stats.iter_launches += r.launches;
     stats.iter_ms += r.ms;
     stats.iter_bytes += r.bytes;
@@ -479,7 +492,7 @@ void leja_phi(phix_ctx* ctx, const OpState& os, int prec, double h, const double
     const int L = l[k], ns = subs[k];
     if (L > 8) fail(ctx, PHIX_EINVAL, "substepped phi_l needs l <= 8");
     const double tau = 1.0 / ns;
-    std::vector<std::vector<double>> d(1, dd_table(L, tau * sc[k] * h * iv.c, tau * sc[k] * h * iv.gamma, M));
+    std::vector<std::vector<double>> d(1, dd_table(L, tau * sc[k] * h * ivc.c, tau * sc[k] * h * ivc.gamma, M));
     if (L == 0)
       CK(cudaMemcpyAsync(u, v, os.N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
     else
@@ -495,7 +508,7 @@ void leja_phi(phix_ctx* ctx, const OpState& os, int prec, double h, const double
         stats.jv += 1;
       }
       double* outs[1] = {tmp};
-      PassResult r = leja_pass(ctx, os, prec, w[L], 1, d, iv.c, iv.gamma, tol, o, outs);
+      PassResult r = leja_pass(ctx, os, prec, w[L], 1, d, ivc.c, ivc.gamma, tol, o, outs);
       stats.iter_launches += r.launches;
       stats.iter_ms += r.ms;
       stats.iter_bytes += r.bytes;
@@ -836,6 +849,7 @@ phix_status phix_destroy(phix_ctx* ctx) {
   if (ctx->counter) cudaFree(ctx->counter);
   for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
   for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.exec);
+  for (auto& g : ctx->bgraphs) cudaGraphExecDestroy(g.exec);
   if (ctx->ptab_h) cudaFreeHost(ctx->ptab_h);
   if (ctx->kc_h) cudaFreeHost(ctx->kc_h);
   delete ctx;
@@ -854,6 +868,142 @@ phix_status phix_divided_differences(int l, double a, double b, int m, double* d
   std::vector<double> t = dd_table(l, a, b, m);
   std::memcpy(d, t.data(), sizeof(double) * m);
   return PHIX_OK;
+}
+
+
+phix_status phix_phi_action_batched(phix_ctx* ctx, const phix_batch_problem* probs, int nprob, int nout,
+                                    const int* l, double tol, const phix_opts* opts, int* per_prob,
+                                    phix_stats* stats) {
+  return guarded(ctx, stats, [&](phix_stats& st) -> phix_status {
+    if (!probs || nprob < 1 || !l || nout < 1 || nout > 3 || !(tol > 0)) fail(ctx, PHIX_EINVAL, "bad batch arguments");
+    phix_opts o = resolve_opts(ctx, opts);
+    if (o.prec != PHIX_FP64 && o.prec != PHIX_DF64 && o.prec != PHIX_FP32_JV)
+      fail(ctx, PHIX_EINVAL, "batched actions support PHIX_FP64, PHIX_DF64, PHIX_FP32_JV");
+    if (o.m_max > 500) fail(ctx, PHIX_EINVAL, "batched actions need m_max <= 500");
+    for (int k = 0; k < nout; ++k)
+      if (l[k] < 0 || l[k] > 2) fail(ctx, PHIX_EINVAL, "batched actions support l in 0..2");
+    const size_t pb = batched_prob_bytes();
+    std::vector<unsigned char> hp(pb * (size_t)nprob);
+    std::vector<std::pair<double, int>> ord(nprob);
+    unsigned long long off = 0, key = 1469598103934665603ull;
+    for (int i = 0; i < nprob; ++i) {
+      const phix_batch_problem& q = probs[i];
+      if (q.nx < 3 || q.ny < 3 || !q.v || !(q.rho_re > 0) || !(q.h > 0) || !std::isfinite(q.h))
+        fail(ctx, PHIX_EINVAL, "problem %d: bad grid, vector, step or interval", i);
+      for (int k = 0; k < nout; ++k)
+        if (!q.out[k]) fail(ctx, PHIX_EINVAL, "problem %d: out[%d] is NULL", i, k);
+      batched_fill_prob(hp.data() + pb * i, q.nx, q.ny, q.D, q.ax, q.ay, q.h, q.rho_re, q.rho_hi, q.rho_im, q.v,
+                        q.out, nout, off);
+      const size_t N = (size_t)q.nx * q.ny;
+      off += 10 * N;
+      ord[i] = std::make_pair(-(double)N * (1.0 + q.h * q.rho_re), i);  // largest work first
+      key = (key ^ (unsigned long long)N) * 1099511628211ull;
+    }
+    std::sort(ord.begin(), ord.end());
+    std::vector<int> order(nprob);
+    for (int i = 0; i < nprob; ++i) order[i] = ord[i].second;
+    const size_t eb = 8;
+    void* dprob = ws(ctx, S_BPROB, pb * nprob);
+    int* dorder = static_cast<int*>(ws(ctx, S_BORDER, sizeof(int) * nprob));
+    void* arena = ws(ctx, S_BWS, off * eb);
+    unsigned int* q = static_cast<unsigned int*>(ws(ctx, S_BQ, sizeof(unsigned int)));
+    const int M = o.m_max + 1;
+    double* xi = static_cast<double*>(ws(ctx, S_XI, sizeof(double) * M));
+    CK(cudaMemcpyAsync(xi, leja_table(M), sizeof(double) * M, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(dprob, hp.data(), pb * nprob, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(dorder, order.data(), sizeof(int) * nprob, cudaMemcpyHostToDevice, ctx->stream));
+    key = (key ^ (unsigned long long)o.prec) * 1099511628211ull;
+    key = (key ^ (unsigned long long)nprob) * 1099511628211ull;
+    // one graph per (arena, problem table, prec, grid): queue reset + persistent launch
+    auto graph_for = [&](int grid) -> cudaGraphExec_t {
+      unsigned long long gk = (key ^ (unsigned long long)(uintptr_t)arena ^ ((unsigned long long)grid << 40)) *
+                              1099511628211ull;
+      for (auto& g : ctx->bgraphs)
+        if (g.key == gk && g.grid == grid) return g.exec;
+      cudaStream_t cs;
+      CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+      cudaGraph_t g;
+      CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e1 = cudaMemsetAsync(q, 0, sizeof(unsigned int), cs);
+      cudaError_t e2 = launch_batched(o.prec, dprob, dorder, nprob, q, arena, xi, o.m_max, o.m_min, tol,
+                                      o.gamma_cap, o.iota_cap, nout, l, grid, cs);
+      cudaError_t e3 = cudaStreamEndCapture(cs, &g);
+      cudaStreamDestroy(cs);
+      CK(e1);
+      CK(e2);
+      CK(e3);
+      cudaGraphExec_t ex;
+      cudaError_t e4 = cudaGraphInstantiate(&ex, g, 0);
+      cudaGraphDestroy(g);
+      CK(e4);
+      if (ctx->bgraphs.size() >= 16) {
+        cudaGraphExecDestroy(ctx->bgraphs.front().exec);
+        ctx->bgraphs.erase(ctx->bgraphs.begin());
+      }
+      ctx->bgraphs.push_back(phix_ctx::BatchGraph{gk, grid, ex});
+      return ex;
+    };
+    int per_sm = 2;
+    bool tuned = false;
+    for (auto& t : ctx->btune)
+      if (t.first == key) {
+        per_sm = t.second;
+        tuned = true;
+      }
+    cudaEvent_t ev0, ev1;
+    CK(cudaEventCreate(&ev0));
+    CK(cudaEventCreate(&ev1));
+    if (o.profile && !tuned) {
+      // autotune: CTAs per SM (each CTA owns whole problems; more CTAs hide
+      // latency, fewer leave more L1 per problem)
+      float best = 1e30f;
+      for (int c = 1; c <= 4; ++c) {
+        cudaGraphExec_t ex = graph_for(ctx->nsm * c);
+        CK(cudaEventRecord(ev0, ctx->stream));
+        CK(cudaGraphLaunch(ex, ctx->stream));
+        CK(cudaEventRecord(ev1, ctx->stream));
+        CK(cudaEventSynchronize(ev1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, ev0, ev1));
+        if (ms < best) {
+          best = ms;
+          per_sm = c;
+        }
+      }
+      ctx->btune.push_back(std::make_pair(key, per_sm));
+    }
+    cudaGraphExec_t ex = graph_for(ctx->nsm * per_sm);
+    CK(cudaEventRecord(ev0, ctx->stream));
+    CK(cudaGraphLaunch(ex, ctx->stream));
+    ctx->launches += 1;
+    CK(cudaEventRecord(ev1, ctx->stream));
+    CK(cudaMemcpyAsync(hp.data(), dprob, pb * nprob, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, ev0, ev1));
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    if (o.profile) {
+      st.iter_ms = ms;
+      st.iter_launches = 1;
+    }
+    st.substeps = per_sm;  // CTAs per SM used (tuned when profile = 1)
+    int worst = PHIX_OK;
+    for (int i = 0; i < nprob; ++i) {
+      int s_, it, sb;
+      batched_read_prob(hp.data() + pb * i, &s_, &it, &sb);
+      if (per_prob) per_prob[i] = s_;
+      st.iters += it;
+      st.jv += it;
+      st.passes += 1;
+      if (s_ != PHIX_OK && worst == PHIX_OK) worst = s_;
+    }
+    if (worst != PHIX_OK) {
+      st.status = worst;
+      set_err(ctx, "a batched problem returned status %d", worst);
+    }
+    return PHIX_OK;
+  });
 }
 
 phix_status phix_small_expm(phix_ctx* ctx, int n, const double* d, const double* u, const double* l,

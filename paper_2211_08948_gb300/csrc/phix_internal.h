@@ -183,6 +183,16 @@ cudaError_t small_expm_e1(int n, const double* d, const double* u, const double*
 // w = sum_{i<n} coef_i Zhat_i into slot 0, s_0 = 1/||w||; out (float64, may be NULL) = scale * w_N.
 cudaError_t kiops_combine(const KiopsSpec& s, int n, double* out, double scale, cudaStream_t st);
 
+// ---- batched persistent kernel (batched_kernels.cu) -------------------------
+size_t batched_prob_bytes();
+void batched_fill_prob(void* dst, int nx, int ny, double D, double ax, double ay, double h, double rho_re,
+                       double rho_hi, double rho_im, const double* v, double* const* out, int nout,
+                       unsigned long long ws_off);
+void batched_read_prob(const void* src, int* status, int* iters, int* substeps);
+cudaError_t launch_batched(int prec, void* probs, const int* order, int nprob, unsigned int* queue, void* ws,
+                           const double* xi, int m_max, int m_min, double tol, double gamma_cap, double iota_cap,
+                           int nout, const int* l, int grid, cudaStream_t st);
+
 // ---- float64 stage kernels (stage_kernels.cu) -----------------------------
 struct OpDesc {
   int kind, nx, ny;

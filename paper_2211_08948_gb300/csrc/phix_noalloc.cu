@@ -215,7 +215,10 @@ extern "C" phix_status phix_phi_action_noalloc(const phix_jop* op, double h, con
     alpha_i = -o.safety * c.h.rho;
     beta_i = 0.0;
   }
-  const double cc = 0.5 * (alpha_i + beta_i), gamma = 0.25 * (beta_i - alpha_i);
+  // half-width covering twice the imaginary extent (complex spectra), the
+  // interval anchored at its right end beta
+  const double gamma = std::max(0.25 * (beta_i - alpha_i), 2.0 * std::max(0.0, o.rho_im));
+  const double cc = beta_i - 2.0 * gamma;
   if (gamma == 0.0) return finish(PHIX_EINVAL);
   // one vertical pass only: a substepped action needs more vectors than the scratch holds
   for (int k = 0; k < nout; ++k) {

@@ -25,7 +25,7 @@ PHIX_OP_ADVDIFF, PHIX_OP_GRAYSCOTT, PHIX_OP_BURGERS = 0, 1, 2
 EXPORTS = [
     "phix_opts_default", "phix_version", "phix_create", "phix_destroy", "phix_last_error",
     "phix_phi_action", "phix_phi_combination", "phix_spectrum", "phix_exprb43_step",
-    "phix_epirk4s3_step", "phix_rhs", "phix_small_expm", "phix_leja_points", "phix_divided_differences", "phix_phi_action_noalloc",
+    "phix_epirk4s3_step", "phix_rhs", "phix_small_expm", "phix_phi_action_batched", "phix_leja_points", "phix_divided_differences", "phix_phi_action_noalloc",
 ]
 
 
@@ -43,6 +43,13 @@ class phix_opts(ctypes.Structure):
                 ("kiops_m_init", ctypes.c_int), ("kiops_m_max", ctypes.c_int),
                 ("kiops_m_step", ctypes.c_int), ("kiops_max_substeps", ctypes.c_int),
                 ("profile", ctypes.c_int)]
+
+
+class phix_batch_problem(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("D", ctypes.c_double), ("ax", ctypes.c_double),
+                ("ay", ctypes.c_double), ("h", ctypes.c_double), ("rho_re", ctypes.c_double),
+                ("rho_hi", ctypes.c_double), ("rho_im", ctypes.c_double), ("v", ctypes.c_void_p),
+                ("out", ctypes.c_void_p * 3)]
 
 
 class phix_stats(ctypes.Structure):
@@ -90,6 +97,8 @@ def load(path=None):
     lib.phix_phi_combination.argtypes = [P, ctypes.POINTER(phix_jop), D, ctypes.POINTER(P), I, P, D, I,
                                          ctypes.POINTER(phix_opts), ctypes.POINTER(phix_stats)]
     lib.phix_rhs.argtypes = [P, ctypes.POINTER(phix_jop), P, P]
+    lib.phix_phi_action_batched.argtypes = [P, ctypes.POINTER(phix_batch_problem), I, I, ctypes.POINTER(I), D,
+                                            ctypes.POINTER(phix_opts), ctypes.POINTER(I), ctypes.POINTER(phix_stats)]
     lib.phix_small_expm.argtypes = [P, I, P, P, P, D, P, ctypes.POINTER(I)]
     lib.phix_spectrum.argtypes = [P, ctypes.POINTER(phix_jop), ctypes.POINTER(phix_opts),
                                   ctypes.POINTER(D), ctypes.POINTER(phix_stats)]
@@ -211,6 +220,29 @@ def phix_phi_combination(ctx, op, h, b, out, tol, method=PHIX_LEJA, opts=None, c
     if check:
         _check(ctx, rc)
     return st
+
+
+def phix_phi_action_batched(ctx, problems, l, tol, opts=None, check=True):
+    """problems: list of dicts nx, ny, D, ax, ay, h, rho_re, rho_hi, rho_im, v (tensor), out (list of
+    tensors, one per l).  Returns (phix_stats, per-problem status list)."""
+    n = len(problems)
+    arr = (phix_batch_problem * n)()
+    for i, q in enumerate(problems):
+        a = arr[i]
+        a.nx, a.ny = q["nx"], q["ny"]
+        a.D, a.ax, a.ay, a.h = q["D"], q["ax"], q["ay"], q["h"]
+        a.rho_re, a.rho_hi, a.rho_im = q["rho_re"], q.get("rho_hi", 0.0), q.get("rho_im", 0.0)
+        a.v = _ptr(q["v"])
+        for k, o in enumerate(q["out"]):
+            a.out[k] = _ptr(o)
+    L = (ctypes.c_int * len(l))(*l)
+    per = (ctypes.c_int * n)()
+    st = phix_stats()
+    rc = load().phix_phi_action_batched(ctx, arr, n, len(l), L, tol,
+                                        ctypes.byref(opts) if opts is not None else None, per, ctypes.byref(st))
+    if check:
+        _check(ctx, rc)
+    return st, list(per)
 
 
 def phix_small_expm(ctx, d, u, l, tau, F):
