@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--clock-ms", type=int, default=200, help="nvidia-smi sampling period (0 = off)")
     ap.add_argument("--method", default="leja", choices=["leja", "kiops"])
-    ap.add_argument("--workload", default="grayscott", choices=["grayscott", "burgers"],
+    ap.add_argument("--workload", default="grayscott", choices=["grayscott", "burgers", "batched"],
                     help="grayscott: EXPRB43 steps (headline); burgers: phi_1(hJ) f h actions on the "
                          "2048^2 Burgers state (mixed-precision workload)")
     return ap.parse_args()
@@ -324,6 +324,59 @@ def run_burgers(args, world, rank, local):
                       "warmup": args.warmup, "by_precision": res}), flush=True)
 
 
+def run_batched(args, world, rank, local):
+    """4096 independent periodic advection-diffusion problems (sides log-uniform
+    32..512, D ~ U(0.1, 1), a ~ U(0, 50)^2, h = 10..200x explicit, Gaussian v),
+    phi_0, phi_1, phi_2 of each, tol 1e-8, in one persistent launch per step."""
+    import torch
+    import synth
+    from paper_2211_08948_gb300 import build, phix
+    torch.cuda.set_device(local)
+    build.build()
+    stream = torch.cuda.current_stream()
+    ctx = phix.phix_create(stream)
+    spec = synth.batched_problems(4096, seed=rank)
+    probs = []
+    unknowns = 0
+    for q in spec:
+        n = q["n"]
+        v = torch.tensor(synth.random_vector(n * n, q["seed_v"]), dtype=torch.float64, device="cuda")
+        probs.append(dict(nx=n, ny=n, D=q["D"], ax=q["ax"], ay=q["ay"], h=q["h"],
+                          rho_re=8.0 * q["D"] * n * n, rho_im=(abs(q["ax"]) + abs(q["ay"])) * n, v=v,
+                          out=[torch.empty_like(v) for _ in range(3)]))
+        unknowns += n * n
+    res = {}
+    outs = {}
+    for pr in ["FP64", "DF64", "FP32_JV"]:
+        o = phix.phix_opts_default(prec=getattr(phix, "PHIX_" + pr), profile=1)
+        for _ in range(args.warmup):
+            st, _ = phix.phix_phi_action_batched(ctx, probs, [0, 1, 2], 1e-8, o)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        launch_ms = 0.0
+        for _ in range(args.steps):
+            st, per = phix.phix_phi_action_batched(ctx, probs, [0, 1, 2], 1e-8, o)
+            launch_ms += st.iter_ms
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        outs[pr] = [[t.clone() for t in q["out"]] for q in probs[:256]]
+        res[pr] = {"actions_per_s": 3 * len(probs) * args.steps / (ms * 1e-3), "ms_per_batch": ms / args.steps,
+                   "launch_ms": launch_ms / args.steps, "ctas_per_sm": st.substeps,
+                   "newton_iters": st.iters, "failed": int(sum(1 for s in per if s != 0))}
+    for pr in res:
+        num = sum(float(torch.linalg.norm(a - b) ** 2) for x, y in zip(outs[pr], outs["FP64"]) for a, b in zip(x, y))
+        den = sum(float(torch.linalg.norm(b) ** 2) for y in outs["FP64"] for b in y)
+        res[pr]["rel_err_vs_fp64_first256"] = (num / den) ** 0.5
+    phix.phix_destroy(ctx)
+    print(json.dumps({"metric": METRIC, "workload": "batched: 4096 periodic advection-diffusion problems, "
+                      "sides 32..512, phi_0..phi_2, tol 1e-8, one persistent launch", "unit": UNIT,
+                      "unknowns": unknowns, "steps": args.steps, "warmup": args.warmup, "by_precision": res}),
+          flush=True)
+
+
 def cpu_baseline(n, u0, prm, tol):
     """The oracle as it stands, one full EXPRB43 step of the same workload."""
     from oracle import integrators, leja
@@ -384,6 +437,8 @@ def main():
         run_reference(args, world, rank)
     elif args.workload == "burgers":
         run_burgers(args, world, rank, local)
+    elif args.workload == "batched":
+        run_batched(args, world, rank, local)
     else:
         run_phix(args, world, rank, local)
 

@@ -221,6 +221,42 @@ phix_status phix_phi_action_batched(phix_ctx* ctx, const phix_batch_problem* pro
                                     const int* l, double tol, const phix_opts* opts, int* per_prob,
                                     phix_stats* stats);
 
+/* Learned spectral interval (north_star form "learned"; replaces the power
+ * iterations of Sec. 2.2 by a prediction, with power iteration as fallback).
+ * MLP 16 -> 64 -> 64 -> 3, GELU, bfloat16 weights / float32 accumulation;
+ * params: PHIX_MLP_NPARAM float32 values W1[64x16] b1[64] W2[64x64] b2[64]
+ * W3[3x64] b3[3] (DEVICE).  Outputs y: rho = rho_diff e^{y0},
+ * rho_im = rho_diff (e^{y1} - 1), substeps e^{y2}, rho_diff = 4 Dmax (nx^2+ny^2).
+ * Features (16 float32, DEVICE): see phix_features.  All arrays DEVICE.    */
+#define PHIX_MLP_NPARAM 5443
+#define PHIX_MLP_NFEAT 16
+/* feats[16] of the operator op at op->state with step h: kind, log sizes,
+ * log D, log h, max/mean |state|, max/mean centred differences, reaction
+ * extrema (Gray-Scott) or divergence and advection bounds (Burgers).      */
+phix_status phix_features(phix_ctx* ctx, const phix_jop* op, double h, float* feats);
+/* Y[n x 3] = MLP(X[n x 16]).                                              */
+phix_status phix_mlp_forward(phix_ctx* ctx, const float* params, const float* X, int n, float* Y);
+/* G[NPARAM] = gradient of the mean loss over (X, T) (n <= 65536 samples);
+ * *loss (HOST) receives the loss.  Loss per sample sum_j w_j (y_j - t_j)^2,
+ * w_0 = 4 when y_0 < t_0, else 1.                                         */
+phix_status phix_mlp_grad(phix_ctx* ctx, const float* params, const float* X, const float* T, int n, float* G,
+                          float* loss);
+/* nsteps Adam steps (lr; beta 0.9 / 0.999, eps 1e-8) on contiguous batches
+ * of `batch` rows of (X, T) (n a multiple of batch; the caller shuffles).
+ * m, v: Adam moments (NPARAM each, zero-initialised by the caller);
+ * *step (HOST) is the Adam step counter, advanced; *loss (HOST, may be NULL)
+ * the last batch's loss.                                                  */
+phix_status phix_mlp_train(phix_ctx* ctx, float* params, float* m, float* v, int* step, const float* X,
+                           const float* T, int n, int batch, int nsteps, float lr, float* loss);
+/* As phix_phi_action (Leja), with the spectral interval [-safety*1.05*rho, 0]
+ * and imaginary bound rho_im from the network instead of power iteration.
+ * If the Leja pass does not converge or produces a non-finite norm, falls
+ * back to power iteration and recomputes (stats->rejections = 1,
+ * stats->power_mv counts the fallback's matvecs).                         */
+phix_status phix_phi_action_learned(phix_ctx* ctx, const phix_jop* op, double h, const double* v, int nout,
+                                    const int* l, const double* scale, double* const* out, double tol,
+                                    const float* params, const phix_opts* opts, phix_stats* stats);
+
 /* The small exponential of the Krylov method (Sec. 2.1: "computing the
  * exponential of the Hessenberg matrix"): F = exp(tau T) e_1 for an n x n
  * tridiagonal T (the Hessenberg matrix of window-2 incomplete

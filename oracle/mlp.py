@@ -108,7 +108,7 @@ def features(kind, nx, ny, params, h, state):
     """16 features of (operator, state, step); kind 1 = Gray-Scott, 2 = Burgers.
     0 kind==GS, 1 log(nx ny)/10, 2 log(Dmax)/10, 3 log(h)/10, 4 log(h rho_diff)/5,
     5 max|s1|, 6 max|s2|, 7 mean|s1|, 8 max g, 9 mean g  (g = (|dE-W| + |dN-S|)/2 of s1),
-    10 GS: max V^2 | Burgers: max|U_x+U_y| / rho_diff, 11 GS: max 2UV | Burgers: 0,
+    10 GS: max V^2 | Burgers: max|U_x+U_y| / rho_diff, 11 GS: max(0, max 2UV) | Burgers: 0,
     12 Burgers: max|U|(nx+ny)/rho_diff | GS: 0, 13 F, 14 k, 15 1.
     rho_diff = 8 Dmax (nx^2 + ny^2)/2 = 4 Dmax (nx^2 + ny^2)."""
     f = np.zeros(NFEAT)
@@ -132,7 +132,7 @@ def features(kind, nx, ny, params, h, state):
     f[9] = np.mean(g)
     if kind == 1:
         f[10] = np.max(s2 * s2)
-        f[11] = np.max(2.0 * s1 * s2)
+        f[11] = max(0.0, np.max(2.0 * s1 * s2))
         f[13] = params[2]
         f[14] = params[3]
     else:

@@ -1,0 +1,278 @@
+// Learned spectral interval: state features and the MLP 16 -> 64 -> 64 -> 3
+// (GELU), bfloat16 weights with float32 accumulation, trained with Adam on
+// float32 master weights.  Hand-written CUDA-core kernels: the network has
+// 5443 parameters and ~5.3k FMAs per sample, far too small for tensor cores.
+//
+// Parameter layout (float32): W1[64x16] b1[64] W2[64x64] b2[64] W3[3x64] b3[3].
+// Loss per sample: sum_j w_j (y_j - t_j)^2, w_0 = 4 when y_0 < t_0 (an
+// under-estimated spectral radius is the dangerous side), batch mean.
+#include <cuda_bf16.h>
+
+#include "iter_common.cuh"
+
+namespace phix {
+
+namespace {
+
+constexpr int H1 = 64, H2 = 64, NI = 16, NO = 3;
+constexpr int OW1 = 0, OB1 = OW1 + H1 * NI, OW2 = OB1 + H1, OB2 = OW2 + H2 * H1, OW3 = OB2 + H2,
+              OB3 = OW3 + NO * H2, NP = OB3 + NO;  // 5443
+
+__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_d(float x) {
+  return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * expf(-0.5f * x * x) * 0.39894228040143268f;
+}
+
+// weights rounded to bfloat16 (kept as bf16 in shared memory, indexed by
+// parameter offset; bias slots unused), biases float32 in b[]
+constexpr int NB = H1 + H2 + NO;
+__host__ __device__ constexpr int bias_slot(int off) {
+  return off < OW2 ? off - OB1 : (off < OW3 ? H1 + off - OB2 : H1 + H2 + off - OB3);
+}
+struct Net {
+  __nv_bfloat16 w[OB3];
+  float b[NB];
+};
+
+__device__ void load_net(const float* __restrict__ p, Net& n, int tid, int nthr) {
+  for (int i = tid; i < NP; i += nthr) {
+    const bool is_b = (i >= OB1 && i < OW2) || (i >= OB2 && i < OW3) || i >= OB3;
+    if (is_b)
+      n.b[bias_slot(i)] = p[i];
+    else
+      n.w[i] = __float2bfloat16_rn(p[i]);
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ float wv(const Net& n, int i) { return __bfloat162float(n.w[i]); }
+
+// one sample: x[16] -> y[3]; activations kept for the backward pass
+__device__ void mlp_sample(const Net& n, const float* x, float* z1, float* a1, float* z2, float* a2, float* y) {
+  for (int j = 0; j < H1; ++j) {
+    float s = n.b[j];
+#pragma unroll
+    for (int i = 0; i < NI; ++i) s = fmaf(wv(n, OW1 + j * NI + i), x[i], s);
+    z1[j] = s;
+    a1[j] = gelu(s);
+  }
+  for (int j = 0; j < H2; ++j) {
+    float s = n.b[H1 + j];
+    for (int i = 0; i < H1; ++i) s = fmaf(wv(n, OW2 + j * H1 + i), a1[i], s);
+    z2[j] = s;
+    a2[j] = gelu(s);
+  }
+  for (int j = 0; j < NO; ++j) {
+    float s = n.b[H1 + H2 + j];
+    for (int i = 0; i < H2; ++i) s = fmaf(wv(n, OW3 + j * H2 + i), a2[i], s);
+    y[j] = s;
+  }
+}
+
+__global__ void __launch_bounds__(128) k_mlp_fwd(const float* __restrict__ p, const float* __restrict__ X, int n,
+                                                 float* __restrict__ Y) {
+  __shared__ Net net;
+  load_net(p, net, threadIdx.x, blockDim.x);
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  float x[NI], z1[H1], a1[H1], z2[H2], a2[H2], y[NO];
+  for (int i = 0; i < NI; ++i) x[i] = X[(size_t)s * NI + i];
+  mlp_sample(net, x, z1, a1, z2, a2, y);
+  for (int j = 0; j < NO; ++j) Y[(size_t)s * NO + j] = y[j];
+}
+
+// Gradient of the batch-mean loss over samples [0, n) of (X, T): one CTA,
+// per-sample backward, shared-memory float atomics for the parameter sums.
+__global__ void __launch_bounds__(256) k_mlp_grad(const float* __restrict__ p, const float* __restrict__ X,
+                                                  const float* __restrict__ T, int n, float* __restrict__ G,
+                                                  float* loss_out) {
+  __shared__ Net net;
+  __shared__ float g[NP];
+  __shared__ float lsum;
+  const int tid = threadIdx.x;
+  load_net(p, net, tid, blockDim.x);
+  for (int i = tid; i < NP; i += blockDim.x) g[i] = 0.f;
+  if (tid == 0) lsum = 0.f;
+  __syncthreads();
+  const float inv_n = 1.f / n;
+  for (int s = tid; s < n; s += blockDim.x) {
+    float x[NI], z1[H1], a1[H1], z2[H2], a2[H2], y[NO];
+    for (int i = 0; i < NI; ++i) x[i] = X[(size_t)s * NI + i];
+    mlp_sample(net, x, z1, a1, z2, a2, y);
+    float dy[NO], l = 0.f;
+    for (int j = 0; j < NO; ++j) {
+      const float t = T[(size_t)s * NO + j];
+      const float d = y[j] - t;
+      const float w = (j == 0 && y[0] < t) ? 4.f : 1.f;
+      l += w * d * d;
+      dy[j] = 2.f * w * d * inv_n;
+    }
+    atomicAdd(&lsum, l * inv_n);
+    // layer 3
+    float da2[H2];
+    for (int i = 0; i < H2; ++i) da2[i] = 0.f;
+    for (int j = 0; j < NO; ++j) {
+      atomicAdd(&g[OB3 + j], dy[j]);
+      for (int i = 0; i < H2; ++i) {
+        atomicAdd(&g[OW3 + j * H2 + i], dy[j] * a2[i]);
+        da2[i] = fmaf(dy[j], wv(net, OW3 + j * H2 + i), da2[i]);
+      }
+    }
+    // layer 2
+    float da1[H1];
+    for (int i = 0; i < H1; ++i) da1[i] = 0.f;
+    for (int j = 0; j < H2; ++j) {
+      const float dz = da2[j] * gelu_d(z2[j]);
+      atomicAdd(&g[OB2 + j], dz);
+      for (int i = 0; i < H1; ++i) {
+        atomicAdd(&g[OW2 + j * H1 + i], dz * a1[i]);
+        da1[i] = fmaf(dz, wv(net, OW2 + j * H1 + i), da1[i]);
+      }
+    }
+    // layer 1
+    for (int j = 0; j < H1; ++j) {
+      const float dz = da1[j] * gelu_d(z1[j]);
+      atomicAdd(&g[OB1 + j], dz);
+      for (int i = 0; i < NI; ++i) atomicAdd(&g[OW1 + j * NI + i], dz * x[i]);
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < NP; i += blockDim.x) G[i] = g[i];
+  if (tid == 0 && loss_out) *loss_out = lsum;
+}
+
+// Adam (Kingma & Ba 2015) on the float32 master weights; step counts from 1
+__global__ void k_adam(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
+                       const float* __restrict__ g, int step, float lr) {
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < NP; i += gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+}
+
+// ---- state features (grid reduction, float64) ----------------------------
+// partial slots: 0 max|s1| 1 max|s2| 2 sum|s1| 3 max g 4 sum g 5 max V^2 6 max 2UV
+//                7 max|div U| (Burgers)
+constexpr int NF = 8;
+__global__ void __launch_bounds__(256) k_features(int kind, int nx, int ny, double p0, double p1, double p2,
+                                                  double p3, double h, const double* __restrict__ st,
+                                                  double* partials, unsigned int* counter, float* feats) {
+  __shared__ double sr[8][NF];
+  __shared__ bool last;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const size_t N = (size_t)nx * ny;
+  double a[NF];
+  for (int j = 0; j < NF; ++j) a[j] = 0.0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + tid; i < N; i += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(i / nx), c = (int)(i % nx);
+    const int cm = c == 0 ? nx - 1 : c - 1, cp = c == nx - 1 ? 0 : c + 1;
+    const int rm = r == 0 ? ny - 1 : r - 1, rp = r == ny - 1 ? 0 : r + 1;
+    const double s1 = st[i];
+    const double dx = st[(size_t)r * nx + cp] - st[(size_t)r * nx + cm];
+    const double dy = st[(size_t)rp * nx + c] - st[(size_t)rm * nx + c];
+    const double g = 0.5 * (fabs(dx) + fabs(dy));
+    a[0] = fmax(a[0], fabs(s1));
+    a[2] += fabs(s1);
+    a[3] = fmax(a[3], g);
+    a[4] += g;
+    if (kind == PHIX_OP_GRAYSCOTT) {
+      const double s2 = st[N + i];
+      a[1] = fmax(a[1], fabs(s2));
+      a[5] = fmax(a[5], s2 * s2);
+      a[6] = fmax(a[6], 2.0 * s1 * s2);
+    } else {
+      a[7] = fmax(a[7], fabs(0.5 * (dx * nx + dy * ny)));
+    }
+  }
+  // max slots: warp max; sum slots: warp sum
+  for (int j = 0; j < NF; ++j) {
+    double x = a[j];
+    const bool is_sum = (j == 2 || j == 4);
+    for (int o = 16; o > 0; o >>= 1) {
+      const double y = __shfl_down_sync(0xffffffffu, x, o);
+      x = is_sum ? x + y : fmax(x, y);
+    }
+    if (lane == 0) sr[warp][j] = x;
+  }
+  __syncthreads();
+  if (tid < NF) {
+    const bool is_sum = (tid == 2 || tid == 4);
+    double x = sr[0][tid];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) x = is_sum ? x + sr[w][tid] : fmax(x, sr[w][tid]);
+    partials[(size_t)blockIdx.x * NF + tid] = x;
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (last && tid == 0) {
+    double t[NF];
+    for (int j = 0; j < NF; ++j) t[j] = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b)
+      for (int j = 0; j < NF; ++j) {
+        const double x = __ldcg(partials + (size_t)b * NF + j);
+        t[j] = (j == 2 || j == 4) ? t[j] + x : fmax(t[j], x);
+      }
+    const double Dmax = kind == PHIX_OP_GRAYSCOTT ? fmax(p0, p1) : p0;
+    const double rho_diff = 4.0 * Dmax * ((double)nx * nx + (double)ny * ny);
+    double f[16];
+    for (int j = 0; j < 16; ++j) f[j] = 0.0;
+    f[0] = kind == PHIX_OP_GRAYSCOTT ? 1.0 : 0.0;
+    f[1] = log((double)N) / 10.0;
+    f[2] = log(Dmax) / 10.0;
+    f[3] = log(h) / 10.0;
+    f[4] = log(h * rho_diff) / 5.0;
+    f[5] = t[0];
+    f[6] = t[1];
+    f[7] = t[2] / (double)N;
+    f[8] = t[3];
+    f[9] = t[4] / (double)N;
+    if (kind == PHIX_OP_GRAYSCOTT) {
+      f[10] = t[5];
+      f[11] = t[6];
+      f[13] = p2;
+      f[14] = p3;
+    } else {
+      f[10] = t[7] / rho_diff;
+      f[12] = t[0] * (nx + ny) / rho_diff;
+    }
+    f[15] = 1.0;
+    for (int j = 0; j < 16; ++j) feats[j] = (float)f[j];
+    *counter = 0;
+    __threadfence();
+  }
+}
+
+}  // namespace
+
+int mlp_nparam() { return NP; }
+
+cudaError_t launch_mlp_forward(const float* p, const float* X, int n, float* Y, cudaStream_t st) {
+  k_mlp_fwd<<<(n + 127) / 128, 128, 0, st>>>(p, X, n, Y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_grad(const float* p, const float* X, const float* T, int n, float* G, float* loss,
+                            cudaStream_t st) {
+  k_mlp_grad<<<1, 256, 0, st>>>(p, X, T, n, G, loss);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float* p, float* m, float* v, const float* g, int step, float lr, cudaStream_t st) {
+  k_adam<<<(NP + 255) / 256, 256, 0, st>>>(p, m, v, g, step, lr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_features(int kind, int nx, int ny, const double* prm, double h, const double* state,
+                            double* partials, unsigned int* counter, float* feats, int grid, cudaStream_t st) {
+  k_features<<<grid, 256, 0, st>>>(kind, nx, ny, prm[0], prm[1], prm[2], prm[3], h, state, partials, counter, feats);
+  return cudaGetLastError();
+}
+
+}  // namespace phix

@@ -27,6 +27,7 @@ enum Slot {
   S_PTAB = S_SUB_W0 + 9,                                         // chain parameter block
   S_KBASIS, S_KB, S_KPTR, S_KCTL, S_KMODE,                       // KIOPS basis, b copies, slot table, control
   S_BPROB, S_BORDER, S_BWS, S_BQ, S_XI,                          // batched problems, order, arena, queue, Leja points
+  S_MFEAT, S_MY, S_MG, S_MCNT,                                   // learned interval: features, outputs, gradient
   S_NSLOT
 };
 
@@ -1002,6 +1003,116 @@ phix_status phix_phi_action_batched(phix_ctx* ctx, const phix_batch_problem* pro
       st.status = worst;
       set_err(ctx, "a batched problem returned status %d", worst);
     }
+    return PHIX_OK;
+  });
+}
+
+phix_status phix_features(phix_ctx* ctx, const phix_jop* op, double h, float* feats) {
+  return guarded(ctx, nullptr, [&](phix_stats&) -> phix_status {
+    check_op(ctx, op, true);
+    if (op->kind == PHIX_OP_ADVDIFF) fail(ctx, PHIX_EINVAL, "features are defined for Gray-Scott and Burgers");
+    if (!feats || !(h > 0)) fail(ctx, PHIX_EINVAL, "bad features arguments");
+    unsigned int* cnt = static_cast<unsigned int*>(ws(ctx, S_MCNT, sizeof(unsigned int)));
+    CK(cudaMemsetAsync(cnt, 0, sizeof(unsigned int), ctx->stream));
+    KL(launch_features(op->kind, op->nx, op->ny, op->param, h, op->state, ctx->partials, cnt, feats,
+                       std::min(ctx->grid_stream, 512), ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PHIX_OK;
+  });
+}
+
+phix_status phix_mlp_forward(phix_ctx* ctx, const float* params, const float* X, int n, float* Y) {
+  return guarded(ctx, nullptr, [&](phix_stats&) -> phix_status {
+    if (!params || !X || !Y || n < 1) fail(ctx, PHIX_EINVAL, "bad mlp_forward arguments");
+    KL(launch_mlp_forward(params, X, n, Y, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PHIX_OK;
+  });
+}
+
+phix_status phix_mlp_grad(phix_ctx* ctx, const float* params, const float* X, const float* T, int n, float* G,
+                          float* loss) {
+  return guarded(ctx, nullptr, [&](phix_stats&) -> phix_status {
+    if (!params || !X || !T || !G || n < 1 || n > 65536) fail(ctx, PHIX_EINVAL, "bad mlp_grad arguments");
+    float* dl = static_cast<float*>(ws(ctx, S_MY, sizeof(float) * 4));
+    KL(launch_mlp_grad(params, X, T, n, G, dl, ctx->stream));
+    float hl = 0.f;
+    CK(cudaMemcpyAsync(&hl, dl, sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (loss) *loss = hl;
+    return PHIX_OK;
+  });
+}
+
+phix_status phix_mlp_train(phix_ctx* ctx, float* params, float* m, float* v, int* step, const float* X,
+                           const float* T, int n, int batch, int nsteps, float lr, float* loss) {
+  return guarded(ctx, nullptr, [&](phix_stats&) -> phix_status {
+    if (!params || !m || !v || !step || !X || !T || batch < 1 || n < batch || n % batch != 0 || nsteps < 0 ||
+        !(lr > 0))
+      fail(ctx, PHIX_EINVAL, "bad mlp_train arguments");
+    float* G = static_cast<float*>(ws(ctx, S_MG, sizeof(float) * mlp_nparam()));
+    float* dl = static_cast<float*>(ws(ctx, S_MY, sizeof(float) * 4));
+    const int nb = n / batch;
+    for (int s = 0; s < nsteps; ++s) {
+      const int b = (*step) % nb;
+      KL(launch_mlp_grad(params, X + (size_t)b * batch * PHIX_MLP_NFEAT, T + (size_t)b * batch * 3, batch, G, dl,
+                         ctx->stream));
+      *step += 1;
+      KL(launch_adam(params, m, v, G, *step, lr, ctx->stream));
+    }
+    float hl = 0.f;
+    CK(cudaMemcpyAsync(&hl, dl, sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (loss) *loss = hl;
+    return PHIX_OK;
+  });
+}
+
+phix_status phix_phi_action_learned(phix_ctx* ctx, const phix_jop* op, double h, const double* v, int nout,
+                                    const int* l, const double* scale, double* const* out, double tol,
+                                    const float* params, const phix_opts* opts, phix_stats* stats) {
+  return guarded(ctx, stats, [&](phix_stats& st) -> phix_status {
+    check_op(ctx, op, true);
+    if (op->kind == PHIX_OP_ADVDIFF) fail(ctx, PHIX_EINVAL, "the learned interval is trained for Gray-Scott and Burgers");
+    if (!v || !out || !l || !scale || !params || nout < 1 || nout > KMAX || !(h > 0) || !(tol > 0))
+      fail(ctx, PHIX_EINVAL, "bad arguments");
+    phix_opts o = resolve_opts(ctx, opts);
+    float* feats = static_cast<float*>(ws(ctx, S_MFEAT, sizeof(float) * PHIX_MLP_NFEAT));
+    float* y = static_cast<float*>(ws(ctx, S_MY, sizeof(float) * 4));
+    unsigned int* cnt = static_cast<unsigned int*>(ws(ctx, S_MCNT, sizeof(unsigned int)));
+    CK(cudaMemsetAsync(cnt, 0, sizeof(unsigned int), ctx->stream));
+    KL(launch_features(op->kind, op->nx, op->ny, op->param, h, op->state, ctx->partials, cnt, feats,
+                       std::min(ctx->grid_stream, 512), ctx->stream));
+    KL(launch_mlp_forward(params, feats, 1, y, ctx->stream));
+    float yh[3];
+    CK(cudaMemcpyAsync(yh, y, sizeof(float) * 3, cudaMemcpyDeviceToHost, ctx->stream));
+    OpState os = make_opstate(ctx, op, op->state, o.prec);  // synchronises nothing; stream-ordered
+    CK(cudaStreamSynchronize(ctx->stream));
+    const double Dmax = op->kind == PHIX_OP_GRAYSCOTT ? std::max(op->param[0], op->param[1]) : op->param[0];
+    const double rho_diff = 4.0 * Dmax * ((double)op->nx * op->nx + (double)op->ny * op->ny);
+    const double rho = rho_diff * std::exp((double)yh[0]);
+    const double rho_im = std::max(0.0, rho_diff * std::expm1((double)yh[1]));
+    if (!std::isfinite(rho) || !(rho > 0)) fail(ctx, PHIX_ENAN, "network produced a non-finite interval");
+    phix_opts ol = o;
+    ol.rho_re = o.safety * 1.05 * rho;
+    ol.rho_hi = 0.0;
+    ol.rho_im = rho_im;
+    Interval iv;
+    iv.c = -0.5 * ol.rho_re;
+    iv.gamma = 0.25 * ol.rho_re;
+    iv.rho = rho;
+    st.rho = rho;
+    leja_phi(ctx, os, o.prec, h, v, nout, l, scale, out, tol, ol, iv, st);
+    if (st.status != PHIX_OK) {
+      // fallback: the method's own power iteration, then recompute
+      st.status = PHIX_OK;
+      st.rejections = 1;
+      phix_opts of = o;
+      of.rho_im = rho_im;
+      Interval ivp = interval_for(ctx, os, o.prec, of, st);
+      leja_phi(ctx, os, o.prec, h, v, nout, l, scale, out, tol, of, ivp, st);
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
     return PHIX_OK;
   });
 }

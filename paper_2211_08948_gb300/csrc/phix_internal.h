@@ -193,6 +193,15 @@ cudaError_t launch_batched(int prec, void* probs, const int* order, int nprob, u
                            const double* xi, int m_max, int m_min, double tol, double gamma_cap, double iota_cap,
                            int nout, const int* l, int grid, cudaStream_t st);
 
+// ---- learned spectral interval (mlp_kernels.cu) ---------------------------
+int mlp_nparam();
+cudaError_t launch_mlp_forward(const float* p, const float* X, int n, float* Y, cudaStream_t st);
+cudaError_t launch_mlp_grad(const float* p, const float* X, const float* T, int n, float* G, float* loss,
+                            cudaStream_t st);
+cudaError_t launch_adam(float* p, float* m, float* v, const float* g, int step, float lr, cudaStream_t st);
+cudaError_t launch_features(int kind, int nx, int ny, const double* prm, double h, const double* state,
+                            double* partials, unsigned int* counter, float* feats, int grid, cudaStream_t st);
+
 // ---- float64 stage kernels (stage_kernels.cu) -----------------------------
 struct OpDesc {
   int kind, nx, ny;

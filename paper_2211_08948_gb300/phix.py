@@ -17,6 +17,8 @@ STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOTCONV", 3: "ENAN", 4: "ETIMEOUT", 5
                 7: "ETOOBIG"}
 PHIX_NOALLOC_SCRATCH_BYTES = 32 << 20
 PHIX_NOALLOC_MMAX = 1000
+PHIX_MLP_NPARAM = 5443
+PHIX_MLP_NFEAT = 16
 PHIX_LEJA, PHIX_KIOPS = 0, 1
 PHIX_FP64, PHIX_DF64, PHIX_FP32_JV, PHIX_FP32 = 0, 1, 2, 3
 PHIX_OP_ADVDIFF, PHIX_OP_GRAYSCOTT, PHIX_OP_BURGERS = 0, 1, 2
@@ -25,7 +27,8 @@ PHIX_OP_ADVDIFF, PHIX_OP_GRAYSCOTT, PHIX_OP_BURGERS = 0, 1, 2
 EXPORTS = [
     "phix_opts_default", "phix_version", "phix_create", "phix_destroy", "phix_last_error",
     "phix_phi_action", "phix_phi_combination", "phix_spectrum", "phix_exprb43_step",
-    "phix_epirk4s3_step", "phix_rhs", "phix_small_expm", "phix_phi_action_batched", "phix_leja_points", "phix_divided_differences", "phix_phi_action_noalloc",
+    "phix_epirk4s3_step", "phix_rhs", "phix_small_expm", "phix_phi_action_batched", "phix_features",
+    "phix_mlp_forward", "phix_mlp_grad", "phix_mlp_train", "phix_phi_action_learned", "phix_leja_points", "phix_divided_differences", "phix_phi_action_noalloc",
 ]
 
 
@@ -97,6 +100,14 @@ def load(path=None):
     lib.phix_phi_combination.argtypes = [P, ctypes.POINTER(phix_jop), D, ctypes.POINTER(P), I, P, D, I,
                                          ctypes.POINTER(phix_opts), ctypes.POINTER(phix_stats)]
     lib.phix_rhs.argtypes = [P, ctypes.POINTER(phix_jop), P, P]
+    F = ctypes.c_float
+    lib.phix_features.argtypes = [P, ctypes.POINTER(phix_jop), D, P]
+    lib.phix_mlp_forward.argtypes = [P, P, P, I, P]
+    lib.phix_mlp_grad.argtypes = [P, P, P, P, I, P, ctypes.POINTER(F)]
+    lib.phix_mlp_train.argtypes = [P, P, P, P, ctypes.POINTER(I), P, P, I, I, I, F, ctypes.POINTER(F)]
+    lib.phix_phi_action_learned.argtypes = [P, ctypes.POINTER(phix_jop), D, P, I, ctypes.POINTER(I),
+                                            ctypes.POINTER(D), ctypes.POINTER(P), D, P,
+                                            ctypes.POINTER(phix_opts), ctypes.POINTER(phix_stats)]
     lib.phix_phi_action_batched.argtypes = [P, ctypes.POINTER(phix_batch_problem), I, I, ctypes.POINTER(I), D,
                                             ctypes.POINTER(phix_opts), ctypes.POINTER(I), ctypes.POINTER(phix_stats)]
     lib.phix_small_expm.argtypes = [P, I, P, P, P, D, P, ctypes.POINTER(I)]
@@ -125,6 +136,14 @@ def _ptr(x):
         return x
     if not (x.is_cuda and x.dtype.is_floating_point and x.element_size() == 8 and x.is_contiguous()):
         raise ValueError("expected a contiguous float64 CUDA tensor")
+    return x.data_ptr()
+
+
+def _fptr(x):
+    if x is None:
+        return None
+    if not (x.is_cuda and x.dtype.is_floating_point and x.element_size() == 4 and x.is_contiguous()):
+        raise ValueError("expected a contiguous float32 CUDA tensor")
     return x.data_ptr()
 
 
@@ -243,6 +262,44 @@ def phix_phi_action_batched(ctx, problems, l, tol, opts=None, check=True):
     if check:
         _check(ctx, rc)
     return st, list(per)
+
+
+def phix_features(ctx, op, h, feats):
+    """feats (float32[16]) <- features of op at op.state with step h."""
+    _check(ctx, load().phix_features(ctx, ctypes.byref(op), h, _fptr(feats)))
+
+
+def phix_mlp_forward(ctx, params, X, Y):
+    _check(ctx, load().phix_mlp_forward(ctx, _fptr(params), _fptr(X), X.shape[0], _fptr(Y)))
+
+
+def phix_mlp_grad(ctx, params, X, T, G):
+    loss = ctypes.c_float()
+    _check(ctx, load().phix_mlp_grad(ctx, _fptr(params), _fptr(X), _fptr(T), X.shape[0], _fptr(G),
+                                     ctypes.byref(loss)))
+    return loss.value
+
+
+def phix_mlp_train(ctx, params, m, v, step, X, T, batch, nsteps, lr):
+    """Returns (new step counter, last batch loss)."""
+    s = ctypes.c_int(step)
+    loss = ctypes.c_float()
+    _check(ctx, load().phix_mlp_train(ctx, _fptr(params), _fptr(m), _fptr(v), ctypes.byref(s), _fptr(X), _fptr(T),
+                                      X.shape[0], batch, nsteps, lr, ctypes.byref(loss)))
+    return s.value, loss.value
+
+
+def phix_phi_action_learned(ctx, op, h, v, l, scale, out, tol, params, opts=None, check=True):
+    n = len(l)
+    st = phix_stats()
+    L = (ctypes.c_int * n)(*l)
+    S = (ctypes.c_double * n)(*scale)
+    O = (ctypes.c_void_p * n)(*[_ptr(o) for o in out])
+    rc = load().phix_phi_action_learned(ctx, ctypes.byref(op), h, _ptr(v), n, L, S, O, tol, _fptr(params),
+                                        ctypes.byref(opts) if opts is not None else None, ctypes.byref(st))
+    if check:
+        _check(ctx, rc)
+    return st
 
 
 def phix_small_expm(ctx, d, u, l, tau, F):

@@ -95,3 +95,34 @@ def batched_problems(count=4096, seed=0, side_lo=32, side_hi=512, h_lo=10.0, h_h
         probs.append(dict(n=n, D=float(D[i]), ax=float(a[i, 0]), ay=float(a[i, 1]),
                           h=float(mult[i] * dx * dx / (4.0 * D[i])), seed_v=seed * 100003 + i))
     return probs
+
+
+def learned_state_specs(count, seed=0, n_lo=32, n_hi=128):
+    """Specs of Gray-Scott and Burgers states for the learned spectral interval:
+    alternating kinds, sides log-uniform in [n_lo, n_hi] (even), diffusion
+    coefficients log-uniform, h = 10..100x the explicit step, random
+    perturbation amplitude and seed."""
+    rng = np.random.default_rng(seed)
+    specs = []
+    for i in range(count):
+        n = int(np.rint(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi))) / 2) * 2)
+        mult = float(np.exp(rng.uniform(np.log(10), np.log(100))))
+        if i % 2 == 0:
+            Du = float(np.exp(rng.uniform(np.log(5e-4), np.log(5e-2))))
+            prm = [Du, 0.5 * Du, 0.04, 0.06]
+            h = mult / (4.0 * Du * n * n)
+            specs.append(dict(kind=1, n=n, params=prm, h=h, amp=float(rng.uniform(0.05, 0.5)),
+                              patch=int(rng.integers(2, max(3, n // 2))), seed=int(rng.integers(1 << 30))))
+        else:
+            nu = float(np.exp(rng.uniform(np.log(1e-3), np.log(5e-2))))
+            h = mult / (4.0 * nu * n * n)
+            specs.append(dict(kind=2, n=n, params=[nu, 0.0, 0.0, 0.0], h=h, amp=float(rng.uniform(0.2, 2.0)),
+                              patch=0, seed=int(rng.integers(1 << 30))))
+    return specs
+
+
+def learned_state(spec):
+    """The state vector of a learned_state_specs entry (float64)."""
+    if spec["kind"] == 1:
+        return grayscott_state(spec["n"], seed=spec["seed"], patch=spec["patch"], amp=spec["amp"])
+    return spec["amp"] * burgers_state(spec["n"], seed=spec["seed"])

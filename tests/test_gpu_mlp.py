@@ -1,0 +1,149 @@
+"""GPU parity of the learned spectral interval (features, MLP forward,
+gradient, Adam) against the oracle, and an end-to-end test: trained on the
+method's own power-iteration estimates, the network replaces the power
+iteration in Leja phi_1 actions (fallback on failure)."""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import mlp
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def px():
+    from paper_2211_08948_gb300 import build, phix
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    ctx = phix.phix_create(torch.cuda.current_stream())
+    yield phix, ctx
+    phix.phix_destroy(ctx)
+
+
+def f32(a):
+    return torch.tensor(np.asarray(a, dtype=np.float32), device="cuda")
+
+
+def f64(a):
+    return torch.tensor(np.asarray(a, dtype=np.float64), device="cuda")
+
+
+def init_params(seed=0):
+    """Scaled Gaussian initial weights (1/sqrt(fan_in)), zero biases."""
+    rng = np.random.default_rng(seed)
+    p = np.zeros(mlp.NPARAM)
+    o = 0
+    for (r, c) in mlp.SIZES:
+        p[o:o + r * c] = rng.standard_normal(r * c) / math.sqrt(c)
+        o += r * c + r
+    return p.astype(np.float32).astype(np.float64)
+
+
+def _op(phix, spec, state_dev):
+    kind = phix.PHIX_OP_GRAYSCOTT if spec["kind"] == 1 else phix.PHIX_OP_BURGERS
+    return phix.make_jop(kind, spec["n"], spec["n"], spec["params"], state_dev)
+
+
+def test_features_vs_oracle(px):
+    phix, ctx = px
+    for spec in synth.learned_state_specs(8, seed=3):
+        s = synth.learned_state(spec)
+        sd = f64(s)
+        feats = torch.empty(16, dtype=torch.float32, device="cuda")
+        phix.phix_features(ctx, _op(phix, spec, sd), spec["h"], feats)
+        ref = mlp.features(spec["kind"], spec["n"], spec["n"], spec["params"], spec["h"], s)
+        assert np.allclose(feats.cpu().numpy(), ref, rtol=1e-6, atol=1e-6), (spec["kind"], feats, ref)
+
+
+def test_forward_and_grad_vs_oracle(px):
+    phix, ctx = px
+    rng = np.random.default_rng(1)
+    p = init_params(1)
+    X = rng.standard_normal((300, 16))
+    T = rng.standard_normal((300, 3))
+    Y = torch.empty((300, 3), dtype=torch.float32, device="cuda")
+    phix.phix_mlp_forward(ctx, f32(p), f32(X), Y)
+    Xq = X.astype(np.float32).astype(np.float64)
+    yref, _ = mlp.forward(p, Xq)
+    assert np.allclose(Y.cpu().numpy(), yref, rtol=1e-4, atol=1e-5)
+    G = torch.empty(mlp.NPARAM, dtype=torch.float32, device="cuda")
+    loss = phix.phix_mlp_grad(ctx, f32(p), f32(X), f32(T), G)
+    lref, gref = mlp.loss_and_grad(p, Xq, T.astype(np.float32).astype(np.float64))
+    assert loss == pytest.approx(lref, rel=1e-4)
+    g = G.cpu().numpy()
+    assert np.linalg.norm(g - gref) <= 1e-4 * np.linalg.norm(gref)
+
+
+def test_adam_steps_vs_oracle(px):
+    phix, ctx = px
+    rng = np.random.default_rng(2)
+    p = init_params(2)
+    X = rng.standard_normal((256, 16))
+    T = rng.standard_normal((256, 3))
+    pd, md, vd = f32(p), torch.zeros(mlp.NPARAM, device="cuda"), torch.zeros(mlp.NPARAM, device="cuda")
+    step, _ = phix.phix_mlp_train(ctx, pd, md, vd, 0, f32(X), f32(T), 128, 6, 1e-3)
+    assert step == 6
+    po, mo, vo = p.copy(), np.zeros(mlp.NPARAM), np.zeros(mlp.NPARAM)
+    Xq = X.astype(np.float32).astype(np.float64)
+    Tq = T.astype(np.float32).astype(np.float64)
+    for s in range(6):
+        b = s % 2
+        _, g = mlp.loss_and_grad(po, Xq[b * 128:(b + 1) * 128], Tq[b * 128:(b + 1) * 128])
+        po, mo, vo = mlp.adam_step(po, mo, vo, g, s + 1, 1e-3)
+    assert np.max(np.abs(pd.cpu().numpy() - po)) <= 5e-5
+
+
+def test_learned_interval_end_to_end(px):
+    phix, ctx = px
+    specs = synth.learned_state_specs(1280, seed=0)
+    X, T, states, rhos = [], [], [], []
+    for spec in specs:
+        s = synth.learned_state(spec)
+        sd = f64(s)
+        op = _op(phix, spec, sd)
+        feats = torch.empty(16, dtype=torch.float32, device="cuda")
+        phix.phix_features(ctx, op, spec["h"], feats)
+        rho, st = phix.phix_spectrum(ctx, op, phix.phix_opts_default())
+        X.append(feats.cpu().numpy())
+        T.append(mlp.labels(spec["kind"], spec["n"], spec["n"], spec["params"], spec["h"], s, rho))
+        states.append(s)
+        rhos.append((rho, st.power_mv))
+    X = np.array(X)
+    T = np.array(T)
+    ntr = 1024
+    params = f32(init_params(0))
+    m = torch.zeros(mlp.NPARAM, device="cuda")
+    v = torch.zeros(mlp.NPARAM, device="cuda")
+    step = 0
+    for lr, nsteps in [(3e-3, 2000), (1e-3, 2000), (3e-4, 1000)]:
+        step, loss = phix.phix_mlp_train(ctx, params, m, v, step, f32(X[:ntr]), f32(T[:ntr]), 256, nsteps, lr)
+    Y = torch.empty((len(X) - ntr, 3), dtype=torch.float32, device="cuda")
+    phix.phix_mlp_forward(ctx, params, f32(X[ntr:]), Y)
+    yh = Y.cpu().numpy()
+    err0 = np.abs(yh[:, 0] - T[ntr:, 0])
+    print("train loss", loss, "median |log rho err|", np.median(err0), "max", np.max(err0))
+    # phi_1 actions on held-out states: learned interval vs power iteration
+    saved, fallbacks, worst = 0, 0, 0.0
+    for i in range(ntr, ntr + 64):
+        spec = specs[i]
+        sd = f64(states[i])
+        op = _op(phix, spec, sd)
+        vvec = f64(np.random.default_rng(i).standard_normal(states[i].size))
+        out_l = torch.empty_like(vvec)
+        out_p = torch.empty_like(vvec)
+        rho_im = 0.0 if spec["kind"] == 1 else float(np.max(np.abs(states[i]))) * 2 * spec["n"]
+        o = phix.phix_opts_default(rho_im=rho_im)
+        sl = phix.phix_phi_action_learned(ctx, op, spec["h"], vvec, [1], [1.0], [out_l], 1e-8, params, o)
+        sp = phix.phix_phi_action(ctx, op, spec["h"], vvec, [1], [1.0], [out_p], 1e-8, phix.PHIX_LEJA, o)
+        fallbacks += sl.rejections
+        saved += sp.power_mv - sl.power_mv
+        worst = max(worst, float(torch.linalg.norm(out_l - out_p) / torch.linalg.norm(out_p)))
+    print("matvecs saved", saved, "fallbacks", fallbacks, "worst rel diff", worst)
+    assert np.median(err0) < 0.1
+    assert fallbacks <= 6
+    assert saved > 0.8 * sum(r[1] for r in rhos[ntr:ntr + 64])
+    assert worst <= 1e-6
