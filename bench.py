@@ -46,10 +46,26 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--clock-ms", type=int, default=200, help="nvidia-smi sampling period (0 = off)")
     ap.add_argument("--method", default="leja", choices=["leja", "kiops"])
-    ap.add_argument("--workload", default="grayscott", choices=["grayscott", "burgers", "batched"],
+    ap.add_argument("--workload", default="grayscott", choices=["grayscott", "burgers", "batched", "learned"],
                     help="grayscott: EXPRB43 steps (headline); burgers: phi_1(hJ) f h actions on the "
                          "2048^2 Burgers state (mixed-precision workload)")
     return ap.parse_args()
+
+
+def max_over_ranks(x, world, device="cpu"):
+    """The largest value of x over all ranks (x itself when world == 1)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, ms_max, world):
+    """Throughput of the whole job: every rank's units over the slowest rank's time."""
+    return units_per_rank * world / (ms_max * 1e-3)
 
 
 def dist_setup():
@@ -168,11 +184,8 @@ def run_phix(args, world, rank, local):
     e1.record(stream)
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
     if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     u_fast = u.cpu().numpy()
 
@@ -206,12 +219,8 @@ def run_phix(args, world, rank, local):
             hbuf.copy_(hout)
         f1.record(stream)
         torch.cuda.synchronize()
-        ems = f0.elapsed_time(f1)
-        if world > 1:
-            t = torch.tensor([ems], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
-        e2e = {"value": ACTIONS_PER_STEP * args.steps * world / (ems * 1e-3), "unit": UNIT,
+        ems = max_over_ranks(f0.elapsed_time(f1), world, "cuda")
+        e2e = {"value": whole_job_rate(ACTIONS_PER_STEP * args.steps, ems, world), "unit": UNIT,
                "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8}
 
     phix.phix_destroy(ctx)
@@ -228,7 +237,7 @@ def run_phix(args, world, rank, local):
     achieved = iter_bytes / (iter_ms * 1e-3) / 1e9 if iter_ms > 0 else None
     result = {
         "metric": METRIC,
-        "value": ACTIONS_PER_STEP * args.steps * world / (ms * 1e-3),
+        "value": whole_job_rate(ACTIONS_PER_STEP * args.steps, ms, world),
         "unit": UNIT,
         "n_gpus": world,
         "steps": args.steps,
@@ -377,6 +386,70 @@ def run_batched(args, world, rank, local):
           flush=True)
 
 
+def run_learned(args, world, rank, local):
+    """Learned spectral interval: label 1024 Gray-Scott / Burgers states (sides
+    32..128) with the method's power iteration, train the MLP on the GPU, then
+    run phi_1 actions on 256 held-out states (cycled, fresh v each time) with
+    the learned interval and with power iteration; report actions/s, matvecs
+    saved, fallbacks and the largest difference between the two results."""
+    import torch
+    import synth
+    from paper_2211_08948_gb300 import build, phix, learned
+    torch.cuda.set_device(local)
+    build.build()
+    stream = torch.cuda.current_stream()
+    ctx = phix.phix_create(stream)
+    specs = synth.learned_state_specs(1280, seed=rank)
+    probs = []
+    for sp in specs:
+        st = torch.tensor(synth.learned_state(sp), dtype=torch.float64, device="cuda")
+        kind = phix.PHIX_OP_GRAYSCOTT if sp["kind"] == 1 else phix.PHIX_OP_BURGERS
+        probs.append((phix.make_jop(kind, sp["n"], sp["n"], sp["params"], st), sp["h"], st))
+    t0 = time.perf_counter()
+    X, T, mv_labels = learned.make_dataset(ctx, probs[:1024], torch)
+    t1 = time.perf_counter()
+    params, loss = learned.train(ctx, X, T, torch)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    nact = max(1, args.steps)
+    evalp = probs[1024:]
+    res = {}
+    outs = {}
+    for mode in ["learned", "power"]:
+        mv, fb, worst = 0, 0, 0.0
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for a in range(nact):
+            op, h, st = evalp[a % len(evalp)]
+            gen = torch.Generator(device="cuda").manual_seed(a)
+            v = torch.randn(st.numel(), dtype=torch.float64, device="cuda", generator=gen)
+            out = torch.empty_like(v)
+            rho_im = 0.0 if op.kind == phix.PHIX_OP_GRAYSCOTT else float(torch.max(torch.abs(st))) * 2 * op.nx
+            o = phix.phix_opts_default(rho_im=rho_im)
+            if mode == "learned":
+                s = phix.phix_phi_action_learned(ctx, op, h, v, [1], [1.0], [out], 1e-8, params, o)
+                fb += s.rejections
+            else:
+                s = phix.phix_phi_action(ctx, op, h, v, [1], [1.0], [out], 1e-8, phix.PHIX_LEJA, o)
+            mv += s.power_mv
+            if a < 256:
+                outs.setdefault(mode, []).append(out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        res[mode] = {"actions_per_s": nact / (ms * 1e-3), "power_matvecs": mv, "fallbacks": fb}
+    worst = max(float(torch.linalg.norm(a - b) / torch.linalg.norm(b)) for a, b in zip(outs["learned"], outs["power"]))
+    phix.phix_destroy(ctx)
+    print(json.dumps({"metric": METRIC, "workload": "learned spectral interval: phi_1(hJ)v on 256 held-out Gray-Scott/"
+                      "Burgers states (sides 32..128), tol 1e-8", "unit": UNIT, "actions": nact,
+                      "label_states": 1024, "label_power_matvecs": mv_labels, "label_s": t1 - t0, "train_s": t2 - t1,
+                      "train_loss": loss, "by_interval": res,
+                      "matvecs_saved": res["power"]["power_matvecs"] - res["learned"]["power_matvecs"],
+                      "max_rel_diff_learned_vs_power": worst}), flush=True)
+
+
 def cpu_baseline(n, u0, prm, tol):
     """The oracle as it stands, one full EXPRB43 step of the same workload."""
     from oracle import integrators, leja
@@ -439,6 +512,8 @@ def main():
         run_burgers(args, world, rank, local)
     elif args.workload == "batched":
         run_batched(args, world, rank, local)
+    elif args.workload == "learned":
+        run_learned(args, world, rank, local)
     else:
         run_phix(args, world, rank, local)
 
