@@ -37,14 +37,14 @@ WORKLOAD = "Gray-Scott 1024x1024x2, EXPRB43 steps, h=100x explicit limit, Leja, 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="phix", choices=["phix", "reference"])
     ap.add_argument("--prec", default="DF64", choices=["DF64", "FP64", "FP32_JV", "FP32"])
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--clock-ms", type=int, default=200, help="nvidia-smi sampling period (0 = off)")
+    ap.add_argument("--clock-ms", type=int, default=100, help="nvidia-smi sampling period (0 = off)")
     ap.add_argument("--method", default="leja", choices=["leja", "kiops"])
     ap.add_argument("--workload", default="grayscott", choices=["grayscott", "burgers", "batched", "learned"],
                     help="grayscott: EXPRB43 steps (headline); burgers: phi_1(hJ) f h actions on the "
@@ -415,6 +415,23 @@ def run_learned(args, world, rank, local):
     evalp = probs[1024:]
     res = {}
     outs = {}
+    def act(mode, a):
+        op, h, st = evalp[a % len(evalp)]
+        gen = torch.Generator(device="cuda").manual_seed(a)
+        v = torch.randn(st.numel(), dtype=torch.float64, device="cuda", generator=gen)
+        out = torch.empty_like(v)
+        rho_im = 0.0 if op.kind == phix.PHIX_OP_GRAYSCOTT else float(torch.max(torch.abs(st))) * 2 * op.nx
+        o = phix.phix_opts_default(rho_im=rho_im)
+        if mode == "learned":
+            s = phix.phix_phi_action_learned(ctx, op, h, v, [1], [1.0], [out], 1e-8, params, o)
+        else:
+            s = phix.phix_phi_action(ctx, op, h, v, [1], [1.0], [out], 1e-8, phix.PHIX_LEJA, o)
+        return out, s
+
+    # warm-up: both arms see every timed problem once (tables, graphs, workspace)
+    for mode in ["learned", "power"]:
+        for a in range(min(nact, len(evalp))):
+            act(mode, a)
     for mode in ["learned", "power"]:
         mv, fb, worst = 0, 0, 0.0
         e0 = torch.cuda.Event(enable_timing=True)
@@ -422,17 +439,9 @@ def run_learned(args, world, rank, local):
         torch.cuda.synchronize()
         e0.record(stream)
         for a in range(nact):
-            op, h, st = evalp[a % len(evalp)]
-            gen = torch.Generator(device="cuda").manual_seed(a)
-            v = torch.randn(st.numel(), dtype=torch.float64, device="cuda", generator=gen)
-            out = torch.empty_like(v)
-            rho_im = 0.0 if op.kind == phix.PHIX_OP_GRAYSCOTT else float(torch.max(torch.abs(st))) * 2 * op.nx
-            o = phix.phix_opts_default(rho_im=rho_im)
+            out, s = act(mode, a)
             if mode == "learned":
-                s = phix.phix_phi_action_learned(ctx, op, h, v, [1], [1.0], [out], 1e-8, params, o)
                 fb += s.rejections
-            else:
-                s = phix.phix_phi_action(ctx, op, h, v, [1], [1.0], [out], 1e-8, phix.PHIX_LEJA, o)
             mv += s.power_mv
             if a < 256:
                 outs.setdefault(mode, []).append(out)

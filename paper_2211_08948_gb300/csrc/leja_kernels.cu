@@ -154,6 +154,25 @@ __global__ void __launch_bounds__(THREADS) k_iter(IterDev a) {
       ea[q] = ldr1(b + row + ixp);
     }
 
+    // accumulators p_k, loaded before any store of this tile so that all
+    // loads are in flight together (p and y may alias as far as the compiler
+    // knows, so it would not move these loads above the stores by itself)
+    C pv[NC][KMAX][V];
+    if constexpr (MODE == MODE_NEWTON) {
+#pragma unroll
+      for (int q = 0; q < NC; ++q)
+#pragma unroll
+        for (int kq = 0; kq < KMAX; ++kq) {
+          if (kq < K) {
+            const T* pp2 = static_cast<const T*>(a.p[kq]) + q * plane + row + ix;
+            if constexpr (V == 2)
+              ldw2(pp2, pv[q][kq][0], pv[q][kq][1]);
+            else
+              pv[q][kq][0] = ldw1(pp2);
+          }
+        }
+    }
+
     C out[NC][V];
 #pragma unroll
     for (int v = 0; v < V; ++v) {
@@ -217,17 +236,14 @@ __global__ void __launch_bounds__(THREADS) k_iter(IterDev a) {
         for (int kq = 0; kq < KMAX; ++kq) {
           if (kq < K) {
             T* pp2 = static_cast<T*>(a.p[kq]) + q * plane + row + ix;
-            C p0, p1;
             if constexpr (V == 2) {
-              ldw2(pp2, p0, p1);
-              p0 = p0 + dk[kq] * out[q][0];
-              p1 = p1 + dk[kq] * out[q][1];
+              const C p0 = pv[q][kq][0] + dk[kq] * out[q][0];
+              const C p1 = pv[q][kq][1] + dk[kq] * out[q][1];
               st2(pp2, p0, p1);
               acc_sq(acc[1 + kq], p0);
               acc_sq(acc[1 + kq], p1);
             } else {
-              p0 = ldw1(pp2);
-              p0 = p0 + dk[kq] * out[q][0];
+              const C p0 = pv[q][kq][0] + dk[kq] * out[q][0];
               st1(pp2, p0);
               acc_sq(acc[1 + kq], p0);
             }

@@ -160,12 +160,35 @@ __global__ void k_adam(float* __restrict__ p, float* __restrict__ m, float* __re
 // partial slots: 0 max|s1| 1 max|s2| 2 sum|s1| 3 max g 4 sum g 5 max V^2 6 max 2UV
 //                7 max|div U| (Burgers)
 constexpr int NF = 8;
+// Reduce a[NF] over the block (slots 2 and 4 summed, the rest by max); the
+// result is left in sr[0][0..NF).
+__device__ void feat_block_reduce(const double* a, double (*sr)[NF]) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int j = 0; j < NF; ++j) {
+    double x = a[j];
+    const bool is_sum = (j == 2 || j == 4);
+    for (int o = 16; o > 0; o >>= 1) {
+      const double y = __shfl_down_sync(0xffffffffu, x, o);
+      x = is_sum ? x + y : fmax(x, y);
+    }
+    if (lane == 0) sr[warp][j] = x;
+  }
+  __syncthreads();
+  if (tid < NF) {
+    const bool is_sum = (tid == 2 || tid == 4);
+    double x = sr[0][tid];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) x = is_sum ? x + sr[w][tid] : fmax(x, sr[w][tid]);
+    sr[0][tid] = x;
+  }
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(256) k_features(int kind, int nx, int ny, double p0, double p1, double p2,
                                                   double p3, double h, const double* __restrict__ st,
                                                   double* partials, unsigned int* counter, float* feats) {
   __shared__ double sr[8][NF];
   __shared__ bool last;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x;
   const size_t N = (size_t)nx * ny;
   double a[NF];
   for (int j = 0; j < NF; ++j) a[j] = 0.0;
@@ -190,35 +213,26 @@ __global__ void __launch_bounds__(256) k_features(int kind, int nx, int ny, doub
       a[7] = fmax(a[7], fabs(0.5 * (dx * nx + dy * ny)));
     }
   }
-  // max slots: warp max; sum slots: warp sum
-  for (int j = 0; j < NF; ++j) {
-    double x = a[j];
-    const bool is_sum = (j == 2 || j == 4);
-    for (int o = 16; o > 0; o >>= 1) {
-      const double y = __shfl_down_sync(0xffffffffu, x, o);
-      x = is_sum ? x + y : fmax(x, y);
-    }
-    if (lane == 0) sr[warp][j] = x;
-  }
-  __syncthreads();
-  if (tid < NF) {
-    const bool is_sum = (tid == 2 || tid == 4);
-    double x = sr[0][tid];
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) x = is_sum ? x + sr[w][tid] : fmax(x, sr[w][tid]);
-    partials[(size_t)blockIdx.x * NF + tid] = x;
-  }
+  // block reduction: max slots by max, slots 2 and 4 by sum
+  feat_block_reduce(a, sr);
+  if (tid < NF) partials[(size_t)blockIdx.x * NF + tid] = sr[0][tid];
   __threadfence();
   __syncthreads();
   if (tid == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
   __syncthreads();
-  if (last && tid == 0) {
+  if (!last) return;
+  // the last block folds the per-block partials, all its threads at once
+  for (int j = 0; j < NF; ++j) a[j] = 0.0;
+  for (int b = tid; b < (int)gridDim.x; b += blockDim.x)
+    for (int j = 0; j < NF; ++j) {
+      const double x = __ldcg(partials + (size_t)b * NF + j);
+      a[j] = (j == 2 || j == 4) ? a[j] + x : fmax(a[j], x);
+    }
+  __syncthreads();
+  feat_block_reduce(a, sr);
+  if (tid == 0) {
     double t[NF];
-    for (int j = 0; j < NF; ++j) t[j] = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b)
-      for (int j = 0; j < NF; ++j) {
-        const double x = __ldcg(partials + (size_t)b * NF + j);
-        t[j] = (j == 2 || j == 4) ? t[j] + x : fmax(t[j], x);
-      }
+    for (int j = 0; j < NF; ++j) t[j] = sr[0][j];
     const double Dmax = kind == PHIX_OP_GRAYSCOTT ? fmax(p0, p1) : p0;
     const double rho_diff = 4.0 * Dmax * ((double)nx * nx + (double)ny * ny);
     double f[16];

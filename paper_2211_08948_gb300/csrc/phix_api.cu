@@ -241,7 +241,7 @@ const void* upload_ptab(phix_ctx* ctx, int K, int m_min, int m_max, double tol, 
 cudaGraphExec_t chain_graph(phix_ctx* ctx, const ChainSpec& spec) {
   for (auto& g : ctx->graphs)
     if (std::memcmp(&g.spec, &spec, sizeof spec) == 0) return g.exec;
-  if (ctx->graphs.size() >= 64) {
+  if (ctx->graphs.size() >= 256) {
     CK(cudaGraphExecDestroy(ctx->graphs.front().exec));
     ctx->graphs.erase(ctx->graphs.begin());
   }
@@ -267,35 +267,49 @@ cudaGraphExec_t chain_graph(phix_ctx* ctx, const ChainSpec& spec) {
   return exec;
 }
 
-// Run a chain until the device marks it done or `last` iterations were issued.
-// Returns the number of graph launches; with profiling, event pair i brackets
-// graph launch i (iterations first_m + i*GRAPH_NODES ...).
-int run_chain(phix_ctx* ctx, const ChainSpec& spec, int first_target, int last, bool profile) {
+// Run a chain until the device marks it done or iteration `last` was issued.
+// `m_next` is the device's next iteration index (advanced here by the graph
+// size per launch); with profiling, event pair i brackets graph launch i and
+// m0[i] records its first iteration.
+void run_chain(phix_ctx* ctx, const ChainSpec& spec, int& m_next, int first_target, int last, bool profile,
+               std::vector<int>* m0) {
   cudaGraphExec_t exec = chain_graph(ctx, spec);
-  int issued = 0, ng = 0;
   int target = std::min(last, first_target);
-  if (profile) ensure_events(ctx, 2 * (size_t)((last + GRAPH_NODES - 1) / GRAPH_NODES + 1));
+  if (profile) ensure_events(ctx, 2 * (size_t)((last + GRAPH_NODES - 1) / GRAPH_NODES + 2 + (m0 ? m0->size() : 0)));
   for (;;) {
-    while (issued < target) {
-      if (profile) CK(cudaEventRecord(ctx->ev[2 * ng], ctx->stream));
+    while (m_next <= target) {
+      const int g = m0 ? (int)m0->size() : 0;
+      if (profile) CK(cudaEventRecord(ctx->ev[2 * g], ctx->stream));
       ctx->launches += GRAPH_NODES;
       CK(cudaGraphLaunch(exec, ctx->stream));
-      if (profile) CK(cudaEventRecord(ctx->ev[2 * ng + 1], ctx->stream));
-      issued += GRAPH_NODES;
-      ++ng;
+      if (profile) {
+        CK(cudaEventRecord(ctx->ev[2 * g + 1], ctx->stream));
+        m0->push_back(m_next);
+      }
+      m_next += GRAPH_NODES;
     }
     read_ctl(ctx);
-    if (ctx->ctl_h->done || issued >= last) break;
-    target = std::min(last, issued + GRAPH_NODES);
+    if (ctx->ctl_h->done || m_next > last) break;
+    target = std::min(last, m_next - 1 + GRAPH_NODES);
   }
-  return ng;
 }
+
+// Divided-difference tables of one pass, computed on the first M1 Leja
+// points and extended to all m_max + 1 on demand (Newton divided differences
+// of a prefix of the points are the prefix of the full table, bit for bit).
+struct DDSpec {
+  int K;
+  int l[KMAX];
+  double a[KMAX], b[KMAX];  // tables of xi -> phi_l(a + b xi)
+};
+
+std::vector<double> dd_table(int l, double a, double b, int m);
 
 // One Newton-Leja pass (Sec. 2.2): out[k] = sum_m d_k[m] y_m, y_0 = v,
 // y_{m+1} = ((J - c)/gamma - xi_m) y_m, stop at |d_k[m]| ||y_m|| <= tol ||p_k||.
-PassResult leja_pass(phix_ctx* ctx, const OpState& os, int prec, const double* v, int K,
-                     const std::vector<std::vector<double>>& d, double c, double gamma, double tol,
-                     const phix_opts& o, double* const* out) {
+PassResult leja_pass(phix_ctx* ctx, const OpState& os, int prec, const double* v, const DDSpec& dds, double c,
+                     double gamma, double tol, const phix_opts& o, double* const* out) {
+  const int K = dds.K;
   const int m_max = o.m_max;
   const int M = m_max + 1;
   const double* xi = leja_table(M);
@@ -304,16 +318,26 @@ PassResult leja_pass(phix_ctx* ctx, const OpState& os, int prec, const double* v
   void* p[KMAX] = {};
   for (int k = 0; k < K; ++k) p[k] = ws(ctx, S_P0 + k, os.N * eb);
 
-  // parameter block: shifts beta_m = -(c/gamma + xi_{m-1}), coefficients d_k[m]
-  std::vector<double> beta(M, 0.0);
-  for (int m = 1; m < M; ++m) beta[m] = -(c / gamma + xi[m - 1]);
-  const double* dk[KMAX] = {};
-  for (int k = 0; k < K; ++k) dk[k] = d[k].data();
+  // first phase: tables on M1 points, enough for most passes
+  double bmax = 0.0;
+  for (int k = 0; k < K; ++k) bmax = std::max(bmax, std::fabs(dds.b[k]));
+  int M1 = std::min(M, (int)(60.0 + 1.6 * bmax));
+  std::vector<std::vector<double>> d(K);
+  for (int k = 0; k < K; ++k) d[k] = dd_table(dds.l[k], dds.a[k], dds.b[k], M1);
+
   const double alpha = 1.0 / gamma;
   const int ns = n_scaled(os.d.kind);
   double k8[8];
   for (int j = 0; j < 8; ++j) k8[j] = j < ns ? alpha * os.kJ[j] : os.kJ[j];
-  const void* ptab = upload_ptab(ctx, K, o.m_min, m_max, tol, 0.0, k8, alpha, beta.data(), dk);
+  auto upload = [&](int Mp) {
+    std::vector<double> beta(Mp, 0.0);
+    for (int m = 1; m < Mp; ++m) beta[m] = -(c / gamma + xi[m - 1]);
+    const double* dk[KMAX] = {};
+    for (int k = 0; k < K; ++k) dk[k] = d[k].data();
+    return upload_ptab(ctx, K, o.m_min, Mp - 1, tol, 0.0, k8, alpha, beta.data(), dk);
+  };
+  ws(ctx, S_PTAB, ptab_bytes(M));  // room for the extended table: the block stays put
+  const void* ptab = upload(M1);
 
   CK(cudaMemsetAsync(ctx->ctl, 0, sizeof(LejaCtl), ctx->stream));
   KL(launch_scale(v, os.N, ctx->ctl, ctx->partials, ctx->grid_iter, ctx->stream));
@@ -332,8 +356,8 @@ PassResult leja_pass(phix_ctx* ctx, const OpState& os, int prec, const double* v
   KL(launch_init(IL, ctx->stream));
 
   // predicted length: first m >= m_min where every |d_k[m]| <= tol |d_k[0]| / 2
-  int m_pred = m_max;
-  for (int m = std::max(1, o.m_min); m <= m_max; ++m) {
+  int m_pred = M1 - 1;
+  for (int m = std::max(1, o.m_min); m < M1; ++m) {
     bool ok = true;
     for (int k = 0; k < K; ++k) ok = ok && std::fabs(d[k][m]) <= 0.5 * tol * std::fabs(d[k][0]);
     if (ok) {
@@ -354,8 +378,27 @@ PassResult leja_pass(phix_ctx* ctx, const OpState& os, int prec, const double* v
   cs.ctl = ctx->ctl;
   cs.partials = ctx->partials;
   cs.ptab = ptab;
-  cs.grid = ctx->nsm * std::min(8, iter_blocks_per_sm(cs));
-  const int ng = run_chain(ctx, cs, m_pred + 2, m_max, o.profile != 0);
+  {
+    const int gmax = ctx->nsm * std::min(8, iter_blocks_per_sm(cs));
+    const int V = (os.d.nx % 2 == 0) ? 2 : 1;
+    const int ntiles = ((os.d.nx / V + 31) / 32) * ((os.d.ny + TILE_Y - 1) / TILE_Y);
+    const int per = (ntiles + gmax - 1) / gmax;  // tiles per block, balanced
+    cs.grid = (ntiles + per - 1) / per;
+  }
+  std::vector<int> m0;
+  int m_next = 1;
+  run_chain(ctx, cs, m_next, m_pred + 2, M1 - 1, o.profile != 0, &m0);
+  if (ctx->ctl_h->status == PHIX_ENOTCONV && ctx->ctl_h->iters == M1 - 1 && M1 < M) {
+    // extend the tables to all points and resume from the same iterate
+    for (int k = 0; k < K; ++k) d[k] = dd_table(dds.l[k], dds.a[k], dds.b[k], M);
+    const void* pt2 = upload(M);
+    if (pt2 != ptab) fail(ctx, PHIX_ECUDA, "parameter block moved");
+    const int zero[2] = {0, 0};
+    CK(cudaMemcpyAsync(&ctx->ctl->done, zero, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(&ctx->ctl->status, zero, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    m_next = M1;
+    run_chain(ctx, cs, m_next, M1 + GRAPH_NODES, m_max, o.profile != 0, &m0);
+  }
   KL(launch_finalize(prec, os.N, K, p, out, ctx->ctl, ctx->grid_stream, ctx->stream));
   PassResult r;
   r.iters = ctx->ctl_h->iters;
@@ -367,8 +410,8 @@ PassResult leja_pass(phix_ctx* ctx, const OpState& os, int prec, const double* v
     const double st_bytes = os.d.kind == PHIX_OP_GRAYSCOTT ? 2.0 * os.plane * sb
                            : os.d.kind == PHIX_OP_BURGERS ? 1.0 * os.plane * sb : 0.0;
     const double per = (double)os.N * eb * (2.0 + 2.0 * K) + st_bytes;
-    for (int g = 0; g < ng; ++g) {
-      if ((g + 1) * GRAPH_NODES > r.iters) break;
+    for (size_t g = 0; g < m0.size(); ++g) {
+      if (m0[g] + GRAPH_NODES - 1 > r.iters) continue;
       float t = 0.f;
       CK(cudaEventElapsedTime(&t, ctx->ev[2 * g], ctx->ev[2 * g + 1]));
       r.ms += t;
@@ -406,7 +449,8 @@ double power_iteration(phix_ctx* ctx, const OpState& os, int prec, const phix_op
   cs.partials = ctx->partials;
   cs.ptab = ptab;
   cs.grid = ctx->nsm * std::min(8, iter_blocks_per_sm(cs));
-  run_chain(ctx, cs, 16, o.power_max_it, false);
+  int m_next = 1;
+  run_chain(ctx, cs, m_next, 16, o.power_max_it, false, nullptr);
   if (ctx->ctl_h->status == PHIX_ENAN) fail(ctx, PHIX_ENAN, "power iteration produced a non-finite norm");
   *mv = ctx->ctl_h->iters;
   return ctx->ctl_h->rho;
@@ -463,7 +507,6 @@ void leja_phi(phix_ctx* ctx, const OpState& os, int prec, double h, const double
     for (int k = 0; k < nout; ++k) lincomb(ctx, os.N, {1.0 / factorial(l[k])}, {v}, out[k]);
     return;
   }
-  const int M = o.m_max + 1;
   int smax = 1;
   std::vector<int> subs(nout);
   for (int k = 0; k < nout; ++k) {
@@ -471,9 +514,14 @@ void leja_phi(phix_ctx* ctx, const OpState& os, int prec, double h, const double
     smax = std::max(smax, subs[k]);
   }
   if (smax == 1) {
-    std::vector<std::vector<double>> d(nout);
-    for (int k = 0; k < nout; ++k) d[k] = dd_table(l[k], sc[k] * h * ivc.c, sc[k] * h * ivc.gamma, M);
-    PassResult r = leja_pass(ctx, os, prec, v, nout, d, ivc.c, ivc.gamma, tol, o, out);
+    DDSpec dds{};
+    dds.K = nout;
+    for (int k = 0; k < nout; ++k) {
+      dds.l[k] = l[k];
+      dds.a[k] = sc[k] * h * ivc.c;
+      dds.b[k] = sc[k] * h * ivc.gamma;
+    }
+    PassResult r = leja_pass(ctx, os, prec, v, dds, ivc.c, ivc.gamma, tol, o, out);
     stats.iter_launches += r.launches;
     stats.iter_ms += r.ms;
     stats.iter_bytes += r.bytes;
@@ -493,7 +541,11 @@ void leja_phi(phix_ctx* ctx, const OpState& os, int prec, double h, const double
     const int L = l[k], ns = subs[k];
     if (L > 8) fail(ctx, PHIX_EINVAL, "substepped phi_l needs l <= 8");
     const double tau = 1.0 / ns;
-    std::vector<std::vector<double>> d(1, dd_table(L, tau * sc[k] * h * ivc.c, tau * sc[k] * h * ivc.gamma, M));
+    DDSpec dds{};
+    dds.K = 1;
+    dds.l[0] = L;
+    dds.a[0] = tau * sc[k] * h * ivc.c;
+    dds.b[0] = tau * sc[k] * h * ivc.gamma;
     if (L == 0)
       CK(cudaMemcpyAsync(u, v, os.N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
     else
@@ -509,7 +561,7 @@ void leja_phi(phix_ctx* ctx, const OpState& os, int prec, double h, const double
         stats.jv += 1;
       }
       double* outs[1] = {tmp};
-      PassResult r = leja_pass(ctx, os, prec, w[L], 1, d, ivc.c, ivc.gamma, tol, o, outs);
+      PassResult r = leja_pass(ctx, os, prec, w[L], dds, ivc.c, ivc.gamma, tol, o, outs);
       stats.iter_launches += r.launches;
       stats.iter_ms += r.ms;
       stats.iter_bytes += r.bytes;
@@ -1007,6 +1059,12 @@ phix_status phix_phi_action_batched(phix_ctx* ctx, const phix_batch_problem* pro
   });
 }
 
+// blocks of the features reduction: about four points per thread, at most 512
+int features_grid(const phix_ctx* ctx, const phix_jop* op) {
+  const long long n = (long long)op->nx * op->ny;
+  return (int)std::max(1LL, std::min<long long>({(long long)ctx->grid_stream, 512LL, (n + 1023) / 1024}));
+}
+
 phix_status phix_features(phix_ctx* ctx, const phix_jop* op, double h, float* feats) {
   return guarded(ctx, nullptr, [&](phix_stats&) -> phix_status {
     check_op(ctx, op, true);
@@ -1015,7 +1073,7 @@ phix_status phix_features(phix_ctx* ctx, const phix_jop* op, double h, float* fe
     unsigned int* cnt = static_cast<unsigned int*>(ws(ctx, S_MCNT, sizeof(unsigned int)));
     CK(cudaMemsetAsync(cnt, 0, sizeof(unsigned int), ctx->stream));
     KL(launch_features(op->kind, op->nx, op->ny, op->param, h, op->state, ctx->partials, cnt, feats,
-                       std::min(ctx->grid_stream, 512), ctx->stream));
+                       features_grid(ctx, op), ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return PHIX_OK;
   });
@@ -1082,7 +1140,7 @@ phix_status phix_phi_action_learned(phix_ctx* ctx, const phix_jop* op, double h,
     unsigned int* cnt = static_cast<unsigned int*>(ws(ctx, S_MCNT, sizeof(unsigned int)));
     CK(cudaMemsetAsync(cnt, 0, sizeof(unsigned int), ctx->stream));
     KL(launch_features(op->kind, op->nx, op->ny, op->param, h, op->state, ctx->partials, cnt, feats,
-                       std::min(ctx->grid_stream, 512), ctx->stream));
+                       features_grid(ctx, op), ctx->stream));
     KL(launch_mlp_forward(params, feats, 1, y, ctx->stream));
     float yh[3];
     CK(cudaMemcpyAsync(yh, y, sizeof(float) * 3, cudaMemcpyDeviceToHost, ctx->stream));
