@@ -101,7 +101,7 @@ typedef struct {
   double iota_cap;     /* Leja: max s*h*rho_im per substep, 0 = off (default 4)        */
   int m_max;           /* Leja: max Newton iterations per pass (default 500)           */
   int m_min;           /* Leja: first iteration where the stop test applies (3)       */
-  int power_max_it;    /* power iteration: max matvecs (50)                           */
+  int power_max_it;    /* power iteration: max matvecs (50), at most 4000             */
   double power_rel;    /* power iteration: stop at this relative change (1e-2)        */
   uint64_t power_seed; /* SplitMix64 stream of the power-iteration start vector        */
   int kiops_m_init;    /* KIOPS: initial Krylov dimension (16)                         */
@@ -124,9 +124,11 @@ typedef struct {
   int launches;      /* device kernels launched by the call                            */
   double rho;        /* |lambda|max estimate used for the Leja interval                */
   double err_est;    /* step functions: ||u4 - u3||_2                                  */
-  /* opts.profile = 1 only: the Newton-Leja / Arnoldi iteration launches that did
-     work, their summed device time (CUDA events) and their algorithmic HBM bytes
-     (each vector read or written once per launch).                                    */
+  /* opts.profile = 1 only: the Newton-Leja iterations / KIOPS Arnoldi steps that
+     did work, the device time of the loops that ran them (CUDA events around each
+     Newton loop, which includes the few no-op launches that end it, and around
+     each run of Arnoldi steps) and their algorithmic HBM bytes (each vector read
+     or written once per iteration or step).                                           */
   int iter_launches;
   double iter_ms;
   double iter_bytes;

@@ -34,7 +34,14 @@ struct IterDev {
   double* partials;
   const unsigned char* ptab;
   int nx, ny, ntiles, tiles_x;
+  int use_cond;
+  cudaGraphConditionalHandle cond;
 };
+
+// Inside a conditional WHILE node: stop the loop (one thread per launch).
+__device__ __forceinline__ void stop_loop(const IterDev& a) {
+  if (a.use_cond) cudaGraphSetConditional(a.cond, 0);
+}
 
 __device__ __forceinline__ const PassParams* pp_of(const unsigned char* t) {
   return reinterpret_cast<const PassParams*>(t);
@@ -83,7 +90,10 @@ __global__ void __launch_bounds__(THREADS) k_iter(IterDev a) {
   // FP32_JV keeps the stencil in float32 and the shift in double-float: no folding
   constexpr bool FOLD = (MODE == MODE_NEWTON) && std::is_same<C, CJ>::value;
 
-  if (__ldcg(&a.ctl->done)) return;  // the chain already stopped
+  if (__ldcg(&a.ctl->done)) {  // the chain already stopped
+    if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) stop_loop(a);
+    return;
+  }
   const int m = __ldcg(&a.ctl->m);
   const PassParams* pp = pp_of(a.ptab);
   const int M = pp->M;
@@ -288,6 +298,7 @@ __global__ void __launch_bounds__(THREADS) k_iter(IterDev a) {
       }
       ctl->m = m + 1;
       ctl->count = 0;
+      if (ctl->done) stop_loop(a);
       __threadfence();
     }
   }
@@ -542,6 +553,8 @@ static IterDev make_dev(const ChainSpec& s, int V) {
   a.ny = s.ny;
   a.tiles_x = (s.nx / V + 31) / 32;
   a.ntiles = a.tiles_x * ((s.ny + TILE_Y - 1) / TILE_Y);
+  a.use_cond = s.use_cond;
+  a.cond = s.cond;
   return a;
 }
 
@@ -608,6 +621,11 @@ cudaError_t launch_iter(const ChainSpec& s, cudaStream_t st) {
   void* args[1] = {&a};
   dim3 grid(s.grid < a.ntiles ? s.grid : a.ntiles);
   return cudaLaunchKernel(fn, grid, dim3(32, TILE_Y), args, 0, st);
+}
+
+int iter_tiles(const ChainSpec& s) {
+  const int V = (s.nx % 2 == 0) ? 2 : 1;
+  return make_dev(s, V).ntiles;
 }
 
 int iter_blocks_per_sm(const ChainSpec& s) {

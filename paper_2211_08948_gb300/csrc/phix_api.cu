@@ -3,8 +3,8 @@
 // A phi-action call: validate -> Jacobian state arrays -> spectral interval
 // (caller value or power iteration, Sec. 2.2) -> divided-difference tables
 // (host, float64) -> chains of Newton-Leja launches that stop themselves on
-// the device (the host polls one small control block per chunk) -> outputs
-// scaled back to float64.  EXPRB43 / EPIRK4s3 steps chain these actions with
+// the device (a conditional WHILE graph node per chain; the host reads the
+// chains' control blocks once per call) -> outputs scaled back to float64.  EXPRB43 / EPIRK4s3 steps chain these actions with
 // float64 stage kernels.
 #include <algorithm>
 #include <cmath>
@@ -24,14 +24,15 @@ enum Slot {
   S_Y0 = 0, S_Y1, S_P0, S_P1, S_P2, S_P3, S_ST,                 // Newton pass
   S_F, S_A, S_B, S_RA, S_RB, S_T0, S_Q, S_T3, S_T4, S_O1, S_O2, S_O3,  // stages
   S_SUB_U, S_SUB_TMP, S_SUB_W0,                                  // substeps (W0..W0+8)
-  S_PTAB = S_SUB_W0 + 9,                                         // chain parameter block
-  S_KBASIS, S_KB, S_KPTR, S_KCTL, S_KMODE,                       // KIOPS basis, b copies, slot table, control
+  S_KBASIS = S_SUB_W0 + 9, S_KB, S_KPTR, S_KCTL, S_KMODE,                       // KIOPS basis, b copies, slot table, control
   S_BPROB, S_BORDER, S_BWS, S_BQ, S_XI,                          // batched problems, order, arena, queue, Leja points
   S_MFEAT, S_MY, S_MG, S_MCNT,                                   // learned interval: features, outputs, gradient
   S_NSLOT
 };
 
 }  // namespace
+
+static constexpr int NSLOT = 16;  // passes queued between synchronisations
 
 struct phix_ctx {
   cudaStream_t stream = nullptr;
@@ -42,21 +43,30 @@ struct phix_ctx {
   std::string err;
   void* buf[S_NSLOT] = {};
   size_t cap[S_NSLOT] = {};
-  LejaCtl* ctl = nullptr;        // device
+  LejaCtl* ctl = nullptr;        // device, one control block per slot
   LejaCtl* ctl_h = nullptr;      // pinned host mirror
   double* partials = nullptr;    // device, grid_iter * (KMAX+1)
   double* scal = nullptr;        // device scalars (norms)
   double* scal_h = nullptr;      // pinned
   unsigned int* counter = nullptr;
   long launches = 0;
-  std::vector<cudaEvent_t> ev;   // profiling: event pairs per graph launch
-  unsigned char* ptab_h = nullptr;  // pinned staging of the chain parameter block
-  size_t ptab_cap = 0;
+  std::vector<cudaEvent_t> ev;   // profiling: one event pair per slot
+  unsigned char* ptab_d = nullptr;  // chain parameter blocks, one per slot (device)
+  unsigned char* ptab_h = nullptr;  // their pinned staging
+  size_t ptab_slot = 0;             // bytes per slot
+  struct Pending {
+    int slot;
+    phix_stats* stats;    // where the outcome goes (null: read by the caller)
+    bool profile;
+    double bytes_per_launch;
+  };
+  std::vector<Pending> pend;     // queued passes since the last flush
+  int nslot = 0;                 // slots in use
   struct Graph {
     ChainSpec spec;
     cudaGraphExec_t exec;
   };
-  std::vector<Graph> graphs;     // cached chains of GRAPH_NODES iteration launches
+  std::vector<Graph> graphs;     // cached chain graphs (WHILE loops of iteration launches)
   KiopsCtl* kc_h = nullptr;      // pinned mirror of the KIOPS control header
   struct BatchGraph {
     unsigned long long key;
@@ -67,7 +77,7 @@ struct phix_ctx {
   std::vector<std::pair<unsigned long long, int>> btune;  // tuned CTAs per SM per batch shape
 };
 
-static constexpr int GRAPH_NODES = 8;
+static constexpr int GRAPH_ITERS = 8;  // iteration launches per body of a chain's WHILE loop
 
 namespace {
 
@@ -198,118 +208,144 @@ OpState make_opstate(phix_ctx* ctx, const phix_jop* op, const double* state, int
 // number of scalar uniform coefficients that alpha scales
 int n_scaled(int kind) { return kind == PHIX_OP_ADVDIFF ? 5 : (kind == PHIX_OP_GRAYSCOTT ? 6 : 3); }
 
-void read_ctl(phix_ctx* ctx) {
-  CK(cudaMemcpyAsync(ctx->ctl_h, ctx->ctl, sizeof(LejaCtl), cudaMemcpyDeviceToHost, ctx->stream));
+// ---------------------------------------------------------------------------
+// Deferred chains.  Each pass (a Newton-Leja chain or a power iteration) gets
+// a slot: its own control block, parameter block (device + pinned staging)
+// and event pair.  The chain is one CUDA graph whose conditional WHILE node
+// repeats GRAPH_ITERS iterations until the kernel clears the
+// condition (the chain converged, hit m_max, or met a non-finite norm; m_max
+// bounds the loop).  The host does not wait for a chain: it reads every
+// pending slot at the next flush (one copy, one synchronisation), at the end
+// of each API call or where it needs a value (the power-iteration estimate).
+// ---------------------------------------------------------------------------
+void flush(phix_ctx* ctx) {
+  if (ctx->nslot == 0) return;
+  CK(cudaMemcpyAsync(ctx->ctl_h, ctx->ctl, sizeof(LejaCtl) * ctx->nslot, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
-}
-
-struct PassResult {
-  int iters;
-  int status;
-  int launches = 0;   // profiled work launches
-  double ms = 0.0;    // their device time
-  double bytes = 0.0; // their algorithmic bytes
-};
-
-void ensure_events(phix_ctx* ctx, size_t n) {
-  while (ctx->ev.size() < n) {
-    cudaEvent_t e;
-    CK(cudaEventCreate(&e));
-    ctx->ev.push_back(e);
+  for (const phix_ctx::Pending& q : ctx->pend) {
+    const LejaCtl& c = ctx->ctl_h[q.slot];
+    // the WHILE loop ran until the body holding iteration `iters` (one body
+    // when the chain stopped before its first iteration)
+    ctx->launches += (long)GRAPH_ITERS * std::max(1, (c.iters + GRAPH_ITERS - 1) / GRAPH_ITERS);
+    if (!q.stats) continue;
+    phix_stats& s = *q.stats;
+    s.iters += c.iters;
+    s.jv += c.iters;
+    const int status = c.done ? c.status : PHIX_ENOTCONV;
+    if (status != PHIX_OK) s.status = status;
+    if (q.profile) {
+      float t = 0.f;
+      CK(cudaEventElapsedTime(&t, ctx->ev[2 * q.slot], ctx->ev[2 * q.slot + 1]));
+      s.iter_ms += t;
+      s.iter_bytes += q.bytes_per_launch * c.iters;
+      s.iter_launches += c.iters;
+    }
   }
+  ctx->pend.clear();
+  ctx->nslot = 0;
 }
 
-// Upload a chain parameter block (pinned staging; the previous chain has
-// finished: every chain ends with a synchronising read of the control block).
-const void* upload_ptab(phix_ctx* ctx, int K, int m_min, int m_max, double tol, double rel, const double* k8,
+// A free slot whose parameter block holds `ptab_need` bytes (flushes when
+// every slot is taken or the blocks must grow).
+int acquire_slot(phix_ctx* ctx, size_t ptab_need) {
+  if (ctx->nslot == NSLOT || ptab_need > ctx->ptab_slot) flush(ctx);
+  if (ptab_need > ctx->ptab_slot) {
+    const size_t sz = (std::max(ptab_need, (size_t)(64 << 10)) + 255) & ~(size_t)255;
+    if (ctx->ptab_d) CK(cudaFree(ctx->ptab_d));
+    if (ctx->ptab_h) CK(cudaFreeHost(ctx->ptab_h));
+    ctx->ptab_d = nullptr;
+    ctx->ptab_h = nullptr;
+    ctx->ptab_slot = 0;
+    cudaError_t e = cudaMalloc(&ctx->ptab_d, sz * NSLOT);
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      fail(ctx, PHIX_ENOMEM, "parameter blocks of %zu bytes: %s", sz * NSLOT, cudaGetErrorString(e));
+    }
+    CK(cudaMallocHost(&ctx->ptab_h, sz * NSLOT));
+    ctx->ptab_slot = sz;
+  }
+  const int s = ctx->nslot++;
+  CK(cudaMemsetAsync(ctx->ctl + s, 0, sizeof(LejaCtl), ctx->stream));
+  return s;
+}
+
+// Fill slot s's parameter block and queue its upload.
+const void* upload_ptab(phix_ctx* ctx, int s, int K, int m_min, int m_max, double tol, double rel, const double* k8,
                         double ga, const double* beta, const double* const* dk) {
   const size_t bytes = ptab_bytes(m_max + 1);
-  if (ctx->ptab_cap < bytes) {
-    if (ctx->ptab_h) CK(cudaFreeHost(ctx->ptab_h));
-    ctx->ptab_h = nullptr;
-    ctx->ptab_cap = 0;
-    CK(cudaMallocHost(&ctx->ptab_h, bytes));
-    ctx->ptab_cap = bytes;
-  }
-  ptab_fill(ctx->ptab_h, K, m_min, m_max, tol, rel, k8, ga, beta, dk);
-  void* d = ws(ctx, S_PTAB, bytes);
-  CK(cudaMemcpyAsync(d, ctx->ptab_h, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  unsigned char* h = ctx->ptab_h + (size_t)s * ctx->ptab_slot;
+  unsigned char* d = ctx->ptab_d + (size_t)s * ctx->ptab_slot;
+  ptab_fill(h, K, m_min, m_max, tol, rel, k8, ga, beta, dk);
+  CK(cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, ctx->stream));
   return d;
 }
 
-// A cached CUDA graph of GRAPH_NODES identical iteration launches of `spec`.
-cudaGraphExec_t chain_graph(phix_ctx* ctx, const ChainSpec& spec) {
+// A cached CUDA graph: one conditional WHILE node whose body is GRAPH_ITERS
+// iteration launches of `spec`; the key is the spec without the handle.
+cudaGraphExec_t chain_graph(phix_ctx* ctx, const ChainSpec& key) {
   for (auto& g : ctx->graphs)
-    if (std::memcmp(&g.spec, &spec, sizeof spec) == 0) return g.exec;
+    if (std::memcmp(&g.spec, &key, sizeof key) == 0) return g.exec;
   if (ctx->graphs.size() >= 256) {
     CK(cudaGraphExecDestroy(ctx->graphs.front().exec));
     ctx->graphs.erase(ctx->graphs.begin());
   }
   cudaGraph_t g;
   CK(cudaGraphCreate(&g, 0));
-  cudaGraphNode_t prev = nullptr;
-  alignas(16) unsigned char argbuf[512];
-  for (int i = 0; i < GRAPH_NODES; ++i) {
-    cudaKernelNodeParams np;
-    CK(iter_node_params(spec, &np, argbuf, sizeof argbuf));
-    cudaGraphNode_t node;
-    CK(cudaGraphAddKernelNode(&node, g, prev ? &prev : nullptr, prev ? 1 : 0, &np));
-    prev = node;
-  }
-  cudaGraphExec_t exec;
-  cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
+  cudaGraphExec_t exec = nullptr;
+  cudaError_t e = cudaSuccess;
+  do {
+    cudaGraphConditionalHandle h;
+    e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) break;
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};  // the rest zero
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cn;
+    e = cudaGraphAddNode(&cn, g, nullptr, nullptr, 0, &cp);
+    if (e != cudaSuccess) break;
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    ChainSpec spec = key;
+    spec.use_cond = 1;
+    spec.cond = h;
+    alignas(16) unsigned char argbuf[512];
+    cudaGraphNode_t prev = nullptr;
+    for (int i = 0; i < GRAPH_ITERS && e == cudaSuccess; ++i) {
+      cudaKernelNodeParams np;
+      e = iter_node_params(spec, &np, argbuf, sizeof argbuf);
+      if (e != cudaSuccess) break;
+      cudaGraphNode_t node;
+      e = cudaGraphAddKernelNode(&node, body, prev ? &prev : nullptr, prev ? 1 : 0, &np);
+      prev = node;
+    }
+    if (e != cudaSuccess) break;
+    e = cudaGraphInstantiate(&exec, g, 0);
+  } while (false);
   cudaGraphDestroy(g);
   CK(e);
   phix_ctx::Graph gg;
-  gg.spec = spec;
+  gg.spec = key;
   gg.exec = exec;
   ctx->graphs.push_back(gg);
   return exec;
 }
 
-// Run a chain until the device marks it done or iteration `last` was issued.
-// `m_next` is the device's next iteration index (advanced here by the graph
-// size per launch); with profiling, event pair i brackets graph launch i and
-// m0[i] records its first iteration.
-void run_chain(phix_ctx* ctx, const ChainSpec& spec, int& m_next, int first_target, int last, bool profile,
-               std::vector<int>* m0) {
-  cudaGraphExec_t exec = chain_graph(ctx, spec);
-  int target = std::min(last, first_target);
-  if (profile) ensure_events(ctx, 2 * (size_t)((last + GRAPH_NODES - 1) / GRAPH_NODES + 2 + (m0 ? m0->size() : 0)));
-  for (;;) {
-    while (m_next <= target) {
-      const int g = m0 ? (int)m0->size() : 0;
-      if (profile) CK(cudaEventRecord(ctx->ev[2 * g], ctx->stream));
-      ctx->launches += GRAPH_NODES;
-      CK(cudaGraphLaunch(exec, ctx->stream));
-      if (profile) {
-        CK(cudaEventRecord(ctx->ev[2 * g + 1], ctx->stream));
-        m0->push_back(m_next);
-      }
-      m_next += GRAPH_NODES;
-    }
-    read_ctl(ctx);
-    if (ctx->ctl_h->done || m_next > last) break;
-    target = std::min(last, m_next - 1 + GRAPH_NODES);
-  }
+// Queue a chain in slot s (bracketed by the slot's events when profiling).
+void queue_chain(phix_ctx* ctx, int s, const ChainSpec& spec, bool profile) {
+  ChainSpec key = spec;
+  key.use_cond = 0;
+  key.cond = 0;
+  cudaGraphExec_t exec = chain_graph(ctx, key);
+  if (profile) CK(cudaEventRecord(ctx->ev[2 * s], ctx->stream));
+  CK(cudaGraphLaunch(exec, ctx->stream));  // its kernel launches are counted at the flush
+  if (profile) CK(cudaEventRecord(ctx->ev[2 * s + 1], ctx->stream));
 }
 
-// Divided-difference tables of one pass, computed on the first M1 Leja
-// points and extended to all m_max + 1 on demand (Newton divided differences
-// of a prefix of the points are the prefix of the full table, bit for bit).
-struct DDSpec {
-  int K;
-  int l[KMAX];
-  double a[KMAX], b[KMAX];  // tables of xi -> phi_l(a + b xi)
-};
-
-std::vector<double> dd_table(int l, double a, double b, int m);
-
-// One Newton-Leja pass (Sec. 2.2): out[k] = sum_m d_k[m] y_m, y_0 = v,
-// y_{m+1} = ((J - c)/gamma - xi_m) y_m, stop at |d_k[m]| ||y_m|| <= tol ||p_k||.
-PassResult leja_pass(phix_ctx* ctx, const OpState& os, int prec, const double* v, const DDSpec& dds, double c,
-                     double gamma, double tol, const phix_opts& o, double* const* out) {
-  const int K = dds.K;
+// One Newton-Leja pass (Sec. 2.2): queued; its outcome reaches `stats` at the
+// next flush.
+void leja_pass(phix_ctx* ctx, const OpState& os, int prec, const double* v, int K,
+               const std::vector<std::vector<double>>& d, double c, double gamma, double tol, const phix_opts& o,
+               double* const* out, phix_stats& stats) {
   const int m_max = o.m_max;
   const int M = m_max + 1;
   const double* xi = leja_table(M);
@@ -318,29 +354,19 @@ PassResult leja_pass(phix_ctx* ctx, const OpState& os, int prec, const double* v
   void* p[KMAX] = {};
   for (int k = 0; k < K; ++k) p[k] = ws(ctx, S_P0 + k, os.N * eb);
 
-  // first phase: tables on M1 points, enough for most passes
-  double bmax = 0.0;
-  for (int k = 0; k < K; ++k) bmax = std::max(bmax, std::fabs(dds.b[k]));
-  int M1 = std::min(M, (int)(60.0 + 1.6 * bmax));
-  std::vector<std::vector<double>> d(K);
-  for (int k = 0; k < K; ++k) d[k] = dd_table(dds.l[k], dds.a[k], dds.b[k], M1);
-
+  const int s = acquire_slot(ctx, ptab_bytes(M));
+  LejaCtl* ctl = ctx->ctl + s;
   const double alpha = 1.0 / gamma;
   const int ns = n_scaled(os.d.kind);
   double k8[8];
   for (int j = 0; j < 8; ++j) k8[j] = j < ns ? alpha * os.kJ[j] : os.kJ[j];
-  auto upload = [&](int Mp) {
-    std::vector<double> beta(Mp, 0.0);
-    for (int m = 1; m < Mp; ++m) beta[m] = -(c / gamma + xi[m - 1]);
-    const double* dk[KMAX] = {};
-    for (int k = 0; k < K; ++k) dk[k] = d[k].data();
-    return upload_ptab(ctx, K, o.m_min, Mp - 1, tol, 0.0, k8, alpha, beta.data(), dk);
-  };
-  ws(ctx, S_PTAB, ptab_bytes(M));  // room for the extended table: the block stays put
-  const void* ptab = upload(M1);
+  std::vector<double> beta(M, 0.0);
+  for (int m = 1; m < M; ++m) beta[m] = -(c / gamma + xi[m - 1]);
+  const double* dk[KMAX] = {};
+  for (int k = 0; k < K; ++k) dk[k] = d[k].data();
+  const void* ptab = upload_ptab(ctx, s, K, o.m_min, m_max, tol, 0.0, k8, alpha, beta.data(), dk);
 
-  CK(cudaMemsetAsync(ctx->ctl, 0, sizeof(LejaCtl), ctx->stream));
-  KL(launch_scale(v, os.N, ctx->ctl, ctx->partials, ctx->grid_iter, ctx->stream));
+  KL(launch_scale(v, os.N, ctl, ctx->partials, ctx->grid_iter, ctx->stream));
   InitLaunch IL{};
   IL.prec = prec;
   IL.ncomp = os.ncomp;
@@ -349,22 +375,12 @@ PassResult leja_pass(phix_ctx* ctx, const OpState& os, int prec, const double* v
   IL.v = v;
   IL.y0 = y[0];
   for (int k = 0; k < K; ++k) IL.p[k] = p[k];
-  IL.ctl = ctx->ctl;
+  IL.ctl = ctl;
   IL.partials = ctx->partials;
   IL.ptab = ptab;
   IL.grid = ctx->grid_iter;
   KL(launch_init(IL, ctx->stream));
 
-  // predicted length: first m >= m_min where every |d_k[m]| <= tol |d_k[0]| / 2
-  int m_pred = M1 - 1;
-  for (int m = std::max(1, o.m_min); m < M1; ++m) {
-    bool ok = true;
-    for (int k = 0; k < K; ++k) ok = ok && std::fabs(d[k][m]) <= 0.5 * tol * std::fabs(d[k][0]);
-    if (ok) {
-      m_pred = m;
-      break;
-    }
-  }
   ChainSpec cs{};
   cs.prec = prec;
   cs.op = os.d.kind;
@@ -375,51 +391,31 @@ PassResult leja_pass(phix_ctx* ctx, const OpState& os, int prec, const double* v
   cs.y[1] = y[1];
   for (int k = 0; k < K; ++k) cs.p[k] = p[k];
   cs.st = os.st;
-  cs.ctl = ctx->ctl;
+  cs.ctl = ctl;
   cs.partials = ctx->partials;
   cs.ptab = ptab;
   {
     const int gmax = ctx->nsm * std::min(8, iter_blocks_per_sm(cs));
-    const int V = (os.d.nx % 2 == 0) ? 2 : 1;
-    const int ntiles = ((os.d.nx / V + 31) / 32) * ((os.d.ny + TILE_Y - 1) / TILE_Y);
+    const int ntiles = iter_tiles(cs);
     const int per = (ntiles + gmax - 1) / gmax;  // tiles per block, balanced
     cs.grid = (ntiles + per - 1) / per;
   }
-  std::vector<int> m0;
-  int m_next = 1;
-  run_chain(ctx, cs, m_next, m_pred + 2, M1 - 1, o.profile != 0, &m0);
-  if (ctx->ctl_h->status == PHIX_ENOTCONV && ctx->ctl_h->iters == M1 - 1 && M1 < M) {
-    // extend the tables to all points and resume from the same iterate
-    for (int k = 0; k < K; ++k) d[k] = dd_table(dds.l[k], dds.a[k], dds.b[k], M);
-    const void* pt2 = upload(M);
-    if (pt2 != ptab) fail(ctx, PHIX_ECUDA, "parameter block moved");
-    const int zero[2] = {0, 0};
-    CK(cudaMemcpyAsync(&ctx->ctl->done, zero, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(&ctx->ctl->status, zero, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
-    m_next = M1;
-    run_chain(ctx, cs, m_next, M1 + GRAPH_NODES, m_max, o.profile != 0, &m0);
-  }
-  KL(launch_finalize(prec, os.N, K, p, out, ctx->ctl, ctx->grid_stream, ctx->stream));
-  PassResult r;
-  r.iters = ctx->ctl_h->iters;
-  r.status = ctx->ctl_h->done ? ctx->ctl_h->status : PHIX_ENOTCONV;
-  if (o.profile) {
-    // graph launches whose every iteration did work (m <= iters); all events
-    // have completed: run_chain synchronised the stream after the last launch
+  const bool profile = o.profile != 0;
+  queue_chain(ctx, s, cs, profile);
+  KL(launch_finalize(prec, os.N, K, p, out, ctl, ctx->grid_stream, ctx->stream));
+  phix_ctx::Pending q{};
+  q.slot = s;
+  q.stats = &stats;
+  q.profile = profile;
+  if (profile) {
+    // algorithmic bytes of one iteration launch: read y, write the new
+    // iterate, read and write each p_k, read the state planes
     const size_t sb = (prec == P_FP64 || prec == P_DF64) ? 8 : 4;
     const double st_bytes = os.d.kind == PHIX_OP_GRAYSCOTT ? 2.0 * os.plane * sb
                            : os.d.kind == PHIX_OP_BURGERS ? 1.0 * os.plane * sb : 0.0;
-    const double per = (double)os.N * eb * (2.0 + 2.0 * K) + st_bytes;
-    for (size_t g = 0; g < m0.size(); ++g) {
-      if (m0[g] + GRAPH_NODES - 1 > r.iters) continue;
-      float t = 0.f;
-      CK(cudaEventElapsedTime(&t, ctx->ev[2 * g], ctx->ev[2 * g + 1]));
-      r.ms += t;
-      r.bytes += per * GRAPH_NODES;
-      r.launches += GRAPH_NODES;
-    }
+    q.bytes_per_launch = (double)os.N * eb * (2.0 + 2.0 * K) + st_bytes;
   }
-  return r;
+  ctx->pend.push_back(q);
 }
 
 std::vector<double> dd_table(int l, double a, double b, int m) {
@@ -430,12 +426,14 @@ std::vector<double> dd_table(int l, double a, double b, int m) {
   return f;
 }
 
+// Power iteration (Sec. 2.2) on the device; flushes to read the estimate.
 double power_iteration(phix_ctx* ctx, const OpState& os, int prec, const phix_opts& o, int* mv) {
   const size_t eb = elem_bytes(prec);
   void* y[2] = {ws(ctx, S_Y0, os.N * eb), ws(ctx, S_Y1, os.N * eb)};
-  const void* ptab = upload_ptab(ctx, 0, 0, o.power_max_it, 0.0, o.power_rel, os.kJ, 1.0, nullptr, nullptr);
-  CK(cudaMemsetAsync(ctx->ctl, 0, sizeof(LejaCtl), ctx->stream));
-  KL(launch_power_start(prec, os.N, o.power_seed, y[0], ctx->ctl, ctx->partials, ctx->grid_iter, ctx->stream));
+  const int s = acquire_slot(ctx, ptab_bytes(o.power_max_it + 1));
+  LejaCtl* ctl = ctx->ctl + s;
+  const void* ptab = upload_ptab(ctx, s, 0, 0, o.power_max_it, 0.0, o.power_rel, os.kJ, 1.0, nullptr, nullptr);
+  KL(launch_power_start(prec, os.N, o.power_seed, y[0], ctl, ctx->partials, ctx->grid_iter, ctx->stream));
   ChainSpec cs{};
   cs.prec = prec;
   cs.op = os.d.kind;
@@ -445,15 +443,19 @@ double power_iteration(phix_ctx* ctx, const OpState& os, int prec, const phix_op
   cs.y[0] = y[0];
   cs.y[1] = y[1];
   cs.st = os.st;
-  cs.ctl = ctx->ctl;
+  cs.ctl = ctl;
   cs.partials = ctx->partials;
   cs.ptab = ptab;
   cs.grid = ctx->nsm * std::min(8, iter_blocks_per_sm(cs));
-  int m_next = 1;
-  run_chain(ctx, cs, m_next, 16, o.power_max_it, false, nullptr);
-  if (ctx->ctl_h->status == PHIX_ENAN) fail(ctx, PHIX_ENAN, "power iteration produced a non-finite norm");
-  *mv = ctx->ctl_h->iters;
-  return ctx->ctl_h->rho;
+  queue_chain(ctx, s, cs, false);
+  phix_ctx::Pending q{};
+  q.slot = s;
+  ctx->pend.push_back(q);
+  flush(ctx);
+  const LejaCtl& c = ctx->ctl_h[s];
+  if (c.status == PHIX_ENAN) fail(ctx, PHIX_ENAN, "power iteration produced a non-finite norm");
+  *mv = c.iters;
+  return c.rho;
 }
 
 double factorial(int n) {
@@ -513,23 +515,13 @@ void leja_phi(phix_ctx* ctx, const OpState& os, int prec, double h, const double
     subs[k] = substeps_for(h, sc[k], ivc.gamma, o.rho_im, o);
     smax = std::max(smax, subs[k]);
   }
+  const int M = o.m_max + 1;
   if (smax == 1) {
-    DDSpec dds{};
-    dds.K = nout;
-    for (int k = 0; k < nout; ++k) {
-      dds.l[k] = l[k];
-      dds.a[k] = sc[k] * h * ivc.c;
-      dds.b[k] = sc[k] * h * ivc.gamma;
-    }
-    PassResult r = leja_pass(ctx, os, prec, v, dds, ivc.c, ivc.gamma, tol, o, out);
-    stats.iter_launches += r.launches;
-    stats.iter_ms += r.ms;
-    stats.iter_bytes += r.bytes;
-    stats.iters += r.iters;
-    stats.jv += r.iters;
+    std::vector<std::vector<double>> d(nout);
+    for (int k = 0; k < nout; ++k) d[k] = dd_table(l[k], sc[k] * h * ivc.c, sc[k] * h * ivc.gamma, M);
+    leja_pass(ctx, os, prec, v, nout, d, ivc.c, ivc.gamma, tol, o, out, stats);
     stats.passes += 1;
     stats.substeps += 1;
-    if (r.status != PHIX_OK) stats.status = r.status;
     return;
   }
   // ODE-identity substeps, one output at a time:
@@ -541,11 +533,7 @@ void leja_phi(phix_ctx* ctx, const OpState& os, int prec, double h, const double
     const int L = l[k], ns = subs[k];
     if (L > 8) fail(ctx, PHIX_EINVAL, "substepped phi_l needs l <= 8");
     const double tau = 1.0 / ns;
-    DDSpec dds{};
-    dds.K = 1;
-    dds.l[0] = L;
-    dds.a[0] = tau * sc[k] * h * ivc.c;
-    dds.b[0] = tau * sc[k] * h * ivc.gamma;
+    const std::vector<std::vector<double>> d(1, dd_table(L, tau * sc[k] * h * ivc.c, tau * sc[k] * h * ivc.gamma, M));
     if (L == 0)
       CK(cudaMemcpyAsync(u, v, os.N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
     else
@@ -561,14 +549,8 @@ void leja_phi(phix_ctx* ctx, const OpState& os, int prec, double h, const double
         stats.jv += 1;
       }
       double* outs[1] = {tmp};
-      PassResult r = leja_pass(ctx, os, prec, w[L], dds, ivc.c, ivc.gamma, tol, o, outs);
-      stats.iter_launches += r.launches;
-      stats.iter_ms += r.ms;
-      stats.iter_bytes += r.bytes;
-      stats.iters += r.iters;
-      stats.jv += r.iters;
+      leja_pass(ctx, os, prec, w[L], 1, d, ivc.c, ivc.gamma, tol, o, outs, stats);
       stats.passes += 1;
-      if (r.status != PHIX_OK) stats.status = r.status;
       std::vector<double> cc;
       std::vector<const double*> xx;
       cc.push_back(std::pow(tau, L));
@@ -667,6 +649,12 @@ void kiops_run(phix_ctx* ctx, const OpState& os, int prec, double h, const doubl
     if (!std::isfinite(nmax)) fail(ctx, PHIX_ENAN, "non-finite input vector");
     if (nmax > 0) eta = std::ldexp(1.0, -(int)std::ceil(std::log2(nmax)));
   }
+  // algorithmic bytes of one Arnoldi step: the Jacobian product reads z_j, the
+  // state planes and the b copies and writes w, with <w, z_{j-1}> on the way;
+  // the orthogonalisation reads w, z_j, z_{j-1} and writes w back
+  const size_t sbytes = os.d.kind == PHIX_OP_GRAYSCOTT ? 2 * os.plane * eb
+                       : os.d.kind == PHIX_OP_BURGERS ? os.plane * eb : 0;
+  const double step_bytes = (double)N * eb * (7.0 + nb) + (double)sbytes;
   KL(kiops_start(ks, b[0], eta, ctx->stream));
   read_kc(ctx, kc);
   stats.passes += 1;
@@ -691,16 +679,27 @@ void kiops_run(phix_ctx* ctx, const OpState& os, int prec, double h, const doubl
     tau = std::min(tau, next_out - t);
     int built = 0;
     for (;;) {
+      const bool prof = o.profile != 0 && m > built;
+      if (prof) CK(cudaEventRecord(ctx->ev[2 * NSLOT], ctx->stream));
       for (int j = built; j < m; ++j) {
         ctx->launches += 2;
         CK(kiops_arnoldi(ks, j, ctx->stream));
       }
+      if (prof) CK(cudaEventRecord(ctx->ev[2 * NSLOT + 1], ctx->stream));
       KL(kiops_smallexp(kc, m, tau, tau_end, tol, ctx->stream));
       read_kc(ctx, kc);
       const KiopsCtl& H = *ctx->kc_h;
       const int happy = H.happy_m;
-      stats.iters += (happy > 0 ? std::min(happy, m) : m) - built;
-      stats.jv += (happy > 0 ? std::min(happy, m) : m) - built;
+      const int steps = (happy > 0 ? std::min(happy, m) : m) - built;
+      stats.iters += steps;
+      stats.jv += steps;
+      if (prof) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, ctx->ev[2 * NSLOT], ctx->ev[2 * NSLOT + 1]));
+        stats.iter_ms += ms;
+        stats.iter_launches += 2 * steps;
+        stats.iter_bytes += steps * step_bytes;
+      }
       if (H.status == PHIX_ENAN || !std::isfinite(H.omega)) fail(ctx, PHIX_ENAN, "KIOPS produced a non-finite value");
       built = m;
       if (happy > 0) m = happy;
@@ -803,7 +802,7 @@ phix_opts resolve_opts(phix_ctx* ctx, const phix_opts* in) {
   if (o.m_max < 1 || o.m_max > 4000) fail(ctx, PHIX_EINVAL, "m_max must be in 1..4000");
   if (o.m_min < 0) fail(ctx, PHIX_EINVAL, "m_min must be >= 0");
   if (!(o.safety > 0)) fail(ctx, PHIX_EINVAL, "safety must be > 0");
-  if (o.power_max_it < 1) fail(ctx, PHIX_EINVAL, "power_max_it must be >= 1");
+  if (o.power_max_it < 1 || o.power_max_it > 4000) fail(ctx, PHIX_EINVAL, "power_max_it must be in 1..4000");
   if (o.kiops_m_max < 2 || o.kiops_m_max > 128) fail(ctx, PHIX_EINVAL, "kiops_m_max must be in 2..128");
   return o;
 }
@@ -817,8 +816,13 @@ phix_status guarded(phix_ctx* ctx, phix_stats* stats, F&& body) {
   phix_status rc;
   try {
     rc = body(st);
+    flush(ctx);  // outcomes of the passes still queued
   } catch (const Fail& f) {
     rc = f.st;
+    // drop queued passes: their stats target is this call's local record
+    (void)cudaStreamSynchronize(ctx->stream);
+    ctx->pend.clear();
+    ctx->nslot = 0;
   }
   if (rc == PHIX_OK && st.status != PHIX_OK) {
     rc = (phix_status)st.status;
@@ -871,15 +875,20 @@ phix_status phix_create(phix_ctx** out, void* stream) {
     CK(cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, ctx->device));
     ctx->grid_iter = ctx->nsm * 8;   // upper bound; chains use the occupancy of their kernel
     ctx->grid_stream = ctx->nsm * 8;
-    CK(cudaMalloc(&ctx->ctl, sizeof(LejaCtl)));
-    CK(cudaMallocHost(&ctx->ctl_h, sizeof(LejaCtl)));
+    CK(cudaMalloc(&ctx->ctl, sizeof(LejaCtl) * NSLOT));
+    CK(cudaMallocHost(&ctx->ctl_h, sizeof(LejaCtl) * NSLOT));
+    for (int i = 0; i < 2 * NSLOT + 2; ++i) {  // + one pair for KIOPS
+      cudaEvent_t e;
+      CK(cudaEventCreate(&e));
+      ctx->ev.push_back(e);
+    }
     CK(cudaMalloc(&ctx->partials, sizeof(double) * (size_t)std::max(ctx->grid_iter, ctx->grid_stream) * (KMAX + 1)));
     CK(cudaMalloc(&ctx->scal, sizeof(double) * 16));
     CK(cudaMallocHost(&ctx->scal_h, sizeof(double) * 16));
     CK(cudaMalloc(&ctx->counter, sizeof(unsigned int)));
     CK(cudaMallocHost(&ctx->kc_h, sizeof(KiopsCtl)));
     CK(cudaMemset(ctx->counter, 0, sizeof(unsigned int)));
-    CK(cudaMemset(ctx->ctl, 0, sizeof(LejaCtl)));
+    CK(cudaMemset(ctx->ctl, 0, sizeof(LejaCtl) * NSLOT));
     CK(cudaDeviceSynchronize());
   } catch (const Fail& f) {
     phix_destroy(ctx);
@@ -904,6 +913,7 @@ phix_status phix_destroy(phix_ctx* ctx) {
   for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.exec);
   for (auto& g : ctx->bgraphs) cudaGraphExecDestroy(g.exec);
   if (ctx->ptab_h) cudaFreeHost(ctx->ptab_h);
+  if (ctx->ptab_d) cudaFree(ctx->ptab_d);
   if (ctx->kc_h) cudaFreeHost(ctx->kc_h);
   delete ctx;
   return PHIX_OK;
@@ -1161,6 +1171,7 @@ phix_status phix_phi_action_learned(phix_ctx* ctx, const phix_jop* op, double h,
     iv.rho = rho;
     st.rho = rho;
     leja_phi(ctx, os, o.prec, h, v, nout, l, scale, out, tol, ol, iv, st);
+    flush(ctx);  // the fallback decision needs the passes' outcome
     if (st.status != PHIX_OK) {
       // fallback: the method's own power iteration, then recompute
       st.status = PHIX_OK;
@@ -1324,14 +1335,14 @@ static phix_status exp_step(phix_ctx* ctx, const phix_jop* op, double* u, double
       double* o2[2] = {P1, P2};
       phi_actions(ctx, os, method, prec, h, T0, 2, l2, s2, o2, tol, o, iv, st);
       lincomb(ctx, N, {1.0, 0.5}, {u, P1}, A);                 // a = u + 1/2 phi_1(h/2 J) f h
-      KL(launch_remainder(os.d, u, A, F, RA, ctx->grid_stream, ctx->stream));
+      KL(launch_remainder(os.d, u, A, RA, ctx->grid_stream, ctx->stream));
       lincomb(ctx, N, {h}, {RA}, T0);
       int l1 = 1;
       double s1 = 1.0;
       double* oq[1] = {Q};
       phi_actions(ctx, os, method, prec, h, T0, 1, &l1, &s1, oq, tol, o, iv, st);
       lincomb(ctx, N, {1.0, 1.0, 1.0}, {u, P2, Q}, B);         // b = u + phi_1 f h + phi_1 R(a) h
-      KL(launch_remainder(os.d, u, B, F, RB, ctx->grid_stream, ctx->stream));
+      KL(launch_remainder(os.d, u, B, RB, ctx->grid_stream, ctx->stream));
       lincomb(ctx, N, {16.0 * h, -2.0 * h}, {RA, RB}, T0);
       int l3 = 3;
       double* o3[1] = {T3};
@@ -1348,8 +1359,8 @@ static phix_status exp_step(phix_ctx* ctx, const phix_jop* op, double* u, double
       phi_actions(ctx, os, method, prec, h, T0, 3, l3v, s3, o3v, tol, o, iv, st);
       lincomb(ctx, N, {1.0, 1.0 / 8.0}, {u, P1}, A);
       lincomb(ctx, N, {1.0, 1.0 / 9.0}, {u, P3}, B);
-      KL(launch_remainder(os.d, u, A, F, RA, ctx->grid_stream, ctx->stream));
-      KL(launch_remainder(os.d, u, B, F, RB, ctx->grid_stream, ctx->stream));
+      KL(launch_remainder(os.d, u, A, RA, ctx->grid_stream, ctx->stream));
+      KL(launch_remainder(os.d, u, B, RB, ctx->grid_stream, ctx->stream));
       // 1892 Ra + 1458 (Rb - 2 Ra) = -1024 Ra + 1458 Rb
       lincomb(ctx, N, {(1892.0 - 2.0 * 1458.0) * h, 1458.0 * h}, {RA, RB}, T0);
       int l3 = 3;
@@ -1365,6 +1376,7 @@ static phix_status exp_step(phix_ctx* ctx, const phix_jop* op, double* u, double
     // err = ||u4 - u3|| = ||T4||;  u4 = u + phi_1(hJ) f h + T3 + T4
     KL(launch_norm2(N, T4, nullptr, ctx->partials, ctx->counter, ctx->scal, ctx->grid_stream, ctx->stream));
     CK(cudaMemcpyAsync(ctx->scal_h, ctx->scal, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    flush(ctx);  // u changes only when every pass succeeded
     if (st.status == PHIX_OK) lincomb(ctx, N, {1.0, 1.0, 1.0, 1.0}, {u, P2, T3, T4}, u);
     CK(cudaStreamSynchronize(ctx->stream));
     st.err_est = std::sqrt(ctx->scal_h[0]);

@@ -73,6 +73,8 @@ struct ChainSpec {
   double* partials;   // grid * (KMAX + 1)
   const void* ptab;   // parameter block (device)
   int grid;           // blocks (<= partials capacity)
+  int use_cond;       // launched as the body of a conditional WHILE graph node:
+  unsigned long long cond;  // its handle; the kernel clears it once the chain stopped
 };
 // One iteration launch.
 cudaError_t launch_iter(const ChainSpec& s, cudaStream_t st);
@@ -81,6 +83,7 @@ cudaError_t iter_node_params(const ChainSpec& s, cudaKernelNodeParams* np, void*
                              size_t arg_bytes);
 // Blocks per SM the iteration kernel of this spec can keep resident.
 int iter_blocks_per_sm(const ChainSpec& s);
+int iter_tiles(const ChainSpec& s);  // tiles of one launch (work units of the grid loop)
 
 // y0 = v / sigma (stored in the precision's format), p_k = d_k[0] y0, norms, ctl->m = 1.
 struct InitLaunch {
@@ -210,8 +213,8 @@ struct OpDesc {
 // f = f(u)
 cudaError_t launch_rhs(const OpDesc& op, const double* u, double* f, int grid, cudaStream_t s);
 // R = f(a) - fu - J(u)(a - u)
-cudaError_t launch_remainder(const OpDesc& op, const double* u, const double* a, const double* fu,
-                             double* R, int grid, cudaStream_t s);
+cudaError_t launch_remainder(const OpDesc& op, const double* u, const double* a, double* R, int grid,
+                             cudaStream_t s);
 // out = alpha * J(state) x + beta * v   (v may be NULL)
 cudaError_t launch_jv_axpy(const OpDesc& op, const double* state, const double* x, double alpha,
                            const double* v, double beta, double* out, int grid, cudaStream_t s);

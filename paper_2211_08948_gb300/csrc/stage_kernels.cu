@@ -93,44 +93,42 @@ __global__ void k_rhs(OpDesc op, const double* __restrict__ u, double* __restric
   const size_t plane = (size_t)g.nx * g.ny;
   const int nc = op.kind == PHIX_OP_GRAYSCOTT ? 2 : 1;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < plane; i += (size_t)gridDim.x * blockDim.x) {
-    int ix = (int)(i % g.nx), iy = (int)(i / g.nx);
+    const int ix = (int)((unsigned)i % (unsigned)g.nx), iy = (int)((unsigned)i / (unsigned)g.nx);  // i < 2^31
     double o[2];
     rhs_point(op, g, u, ix, iy, o);
     for (int q = 0; q < nc; ++q) f[q * plane + i] = o[q];
   }
 }
 
-// R = f(a) - fu - J(u)(a - u); J(u)(a-u) is linear in (a - u), formed from the
-// neighbour differences directly.
-__global__ void k_remainder(OpDesc op, const double* __restrict__ u, const double* __restrict__ a,
-                            const double* __restrict__ fu, double* __restrict__ R) {
-  Geo g = geo(op);
-  const size_t plane = (size_t)g.nx * g.ny;
-  const int nc = op.kind == PHIX_OP_GRAYSCOTT ? 2 : 1;
+// R(a) = f(a) - f(u) - J(u)(a - u) (Sec. 1).  The linear parts of f cancel
+// exactly, so R is the remainder of the nonlinear term alone, with d = a - u:
+//   Gray-Scott  n(u, v) = u v^2:   n(a) - n(u) - n'(u) d = dv (a_u dv + 2 v du),
+//               R_u = -that, R_v = +that (pointwise, no stencil);
+//   Burgers     n(u) = -u (D_x u + D_y u):  R = -d (D_x d + D_y d);
+//   advection-diffusion is linear: R = 0.
+// This is the same quantity as the definition, without its cancellation
+// (f(a) and f(u) carry the O(n^2) Laplacian terms; R is O(|d|^2)).
+__global__ void k_remainder_gs(size_t plane, const double* __restrict__ u, const double* __restrict__ a,
+                               double* __restrict__ R) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < plane; i += (size_t)gridDim.x * blockDim.x) {
-    int ix = (int)(i % g.nx), iy = (int)(i / g.nx);
-    double fa[2], jd[2];
-    rhs_point(op, g, a, ix, iy, fa);
-    // J(u)(a - u) without a temporary: difference of neighbour loads
-    if (op.kind == PHIX_OP_ADVDIFF) {
-      Nbr A = load_nbr(a, g.nx, g.ny, ix, iy), U = load_nbr(u, g.nx, g.ny, ix, iy);
-      Nbr d{A.c - U.c, A.e - U.e, A.w - U.w, A.n - U.n, A.s - U.s};
-      jd[0] = op.p[0] * lap(d, g.idx2, g.idy2) + op.p[1] * ddx(d, g.i2dx) + op.p[2] * ddy(d, g.i2dy);
-    } else if (op.kind == PHIX_OP_GRAYSCOTT) {
-      Nbr A = load_nbr(a, g.nx, g.ny, ix, iy), U = load_nbr(u, g.nx, g.ny, ix, iy);
-      Nbr B = load_nbr(a + plane, g.nx, g.ny, ix, iy), Vn = load_nbr(u + plane, g.nx, g.ny, ix, iy);
-      Nbr du{A.c - U.c, A.e - U.e, A.w - U.w, A.n - U.n, A.s - U.s};
-      Nbr dv{B.c - Vn.c, B.e - Vn.e, B.w - Vn.w, B.n - Vn.n, B.s - Vn.s};
-      double Uc = U.c, Vc = Vn.c;
-      jd[0] = op.p[0] * lap(du, g.idx2, g.idy2) - (Vc * Vc + op.p[2]) * du.c - 2.0 * Uc * Vc * dv.c;
-      jd[1] = op.p[1] * lap(dv, g.idx2, g.idy2) + Vc * Vc * du.c + (2.0 * Uc * Vc - (op.p[2] + op.p[3])) * dv.c;
-    } else {
-      Nbr A = load_nbr(a, g.nx, g.ny, ix, iy), U = load_nbr(u, g.nx, g.ny, ix, iy);
-      Nbr d{A.c - U.c, A.e - U.e, A.w - U.w, A.n - U.n, A.s - U.s};
-      double divU = ddx(U, g.i2dx) + ddy(U, g.i2dy);
-      jd[0] = op.p[0] * lap(d, g.idx2, g.idy2) - divU * d.c - U.c * (ddx(d, g.i2dx) + ddy(d, g.i2dy));
-    }
-    for (int q = 0; q < nc; ++q) R[q * plane + i] = fa[q] - fu[q * plane + i] - jd[q];
+    const double v = u[plane + i];
+    const double au = a[i], av = a[plane + i];
+    const double du = au - u[i], dv = av - v;
+    const double r = dv * (au * dv + 2.0 * v * du);
+    R[i] = -r;
+    R[plane + i] = r;
+  }
+}
+
+__global__ void k_remainder_burgers(OpDesc op, const double* __restrict__ u, const double* __restrict__ a,
+                                    double* __restrict__ R) {
+  Geo g = geo(op);
+  const unsigned plane = (unsigned)g.nx * (unsigned)g.ny;  // <= 2^31 points
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < plane; i += gridDim.x * blockDim.x) {
+    const int ix = (int)(i % (unsigned)g.nx), iy = (int)(i / (unsigned)g.nx);
+    Nbr A = load_nbr(a, g.nx, g.ny, ix, iy), U = load_nbr(u, g.nx, g.ny, ix, iy);
+    Nbr d{A.c - U.c, A.e - U.e, A.w - U.w, A.n - U.n, A.s - U.s};
+    R[i] = -d.c * (ddx(d, g.i2dx) + ddy(d, g.i2dy));
   }
 }
 
@@ -141,7 +139,7 @@ __global__ void k_jv_axpy(OpDesc op, const double* __restrict__ st, const double
   const size_t plane = (size_t)g.nx * g.ny;
   const int nc = op.kind == PHIX_OP_GRAYSCOTT ? 2 : 1;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < plane; i += (size_t)gridDim.x * blockDim.x) {
-    int ix = (int)(i % g.nx), iy = (int)(i / g.nx);
+    const int ix = (int)((unsigned)i % (unsigned)g.nx), iy = (int)((unsigned)i / (unsigned)g.nx);  // i < 2^31
     double o[2];
     jv_point(op, g, st, x, ix, iy, o);
     for (int q = 0; q < nc; ++q) {
@@ -217,10 +215,16 @@ cudaError_t launch_rhs(const OpDesc& op, const double* u, double* f, int grid, c
   return cudaGetLastError();
 }
 
-cudaError_t launch_remainder(const OpDesc& op, const double* u, const double* a, const double* fu,
-                             double* R, int grid, cudaStream_t s) {
-  size_t plane = (size_t)op.nx * op.ny;
-  k_remainder<<<clamp_grid(plane, grid), 256, 0, s>>>(op, u, a, fu, R);
+cudaError_t launch_remainder(const OpDesc& op, const double* u, const double* a, double* R, int grid,
+                             cudaStream_t s) {
+  const size_t plane = (size_t)op.nx * op.ny;
+  if (op.kind == PHIX_OP_GRAYSCOTT) {
+    k_remainder_gs<<<clamp_grid(plane, grid), 256, 0, s>>>(plane, u, a, R);
+  } else if (op.kind == PHIX_OP_BURGERS) {
+    k_remainder_burgers<<<clamp_grid(plane, grid), 256, 0, s>>>(op, u, a, R);
+  } else {
+    return cudaMemsetAsync(R, 0, plane * sizeof(double), s);
+  }
   return cudaGetLastError();
 }
 

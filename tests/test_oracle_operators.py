@@ -133,3 +133,38 @@ def test_rectangular_grid_modes():
     z = np.zeros(nx * ny)
     f = gs.f(np.concatenate([u, z]))
     assert np.allclose(f[: nx * ny], lam * u, atol=1e-9 * abs(lam))
+
+
+def test_remainder_is_the_nonlinear_remainder():
+    """The linear terms of f cancel in R(a) = f(a) - f(u) - J(u)(a - u) (Sec. 1):
+    Gray-Scott keeps dv (a_u dv + 2 v du) with sign -/+ per species, Burgers
+    keeps -d (D_x d + D_y d) with the central differences of f, advection-
+    diffusion keeps 0.  The GPU stage kernel evaluates these forms; here they
+    are compared with the definition, on a rectangular grid."""
+    rng = np.random.default_rng(11)
+    nx, ny = 24, 17
+    N = nx * ny
+    gs = GrayScott(nx, 2e-5, 1e-5, 0.04, 0.06, ny=ny)
+    u = np.concatenate([1.0 - 0.3 * rng.random(N), 0.3 * rng.random(N)])
+    a = u + 0.05 * rng.standard_normal(2 * N)
+    R = remainder(GrayScott(nx, 2e-5, 1e-5, 0.04, 0.06, u, ny=ny), u, a)
+    du, dv = a[:N] - u[:N], a[N:] - u[N:]
+    r = dv * (a[:N] * dv + 2.0 * u[N:] * du)
+    scale = np.linalg.norm(gs.f(a))
+    assert np.max(np.abs(R - np.concatenate([-r, r]))) <= 1e-13 * scale
+    assert np.linalg.norm(r) > 1e-4  # the remainder itself is not negligible here
+
+    bu = Burgers(nx, 1e-3, ny=ny)
+    ub = rng.standard_normal(N)
+    ab = ub + 0.05 * rng.standard_normal(N)
+    Rb = remainder(Burgers(nx, 1e-3, ub, ny=ny), ub, ab)
+    d = (ab - ub).reshape(ny, nx)
+    ddx = (np.roll(d, -1, 1) - np.roll(d, 1, 1)) * (0.5 * nx)
+    ddy = (np.roll(d, -1, 0) - np.roll(d, 1, 0)) * (0.5 * ny)
+    rb = (-d * (ddx + ddy)).reshape(-1)
+    assert np.max(np.abs(Rb - rb)) <= 1e-13 * np.linalg.norm(bu.f(ab))
+    assert np.linalg.norm(rb) > 1e-3
+
+    ad = AdvDiff(nx, 1e-3, 0.3, -0.2, ny=ny)
+    ua = rng.standard_normal(N)
+    assert np.max(np.abs(remainder(ad, ua, ua + rng.standard_normal(N)))) <= 1e-12 * np.linalg.norm(ad.f(ua))
