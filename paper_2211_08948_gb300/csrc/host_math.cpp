@@ -95,6 +95,7 @@ const double* leja_table(int m) {
   std::lock_guard<std::mutex> lk(mu);
   if ((int)table.size() < m) {
     if (table.empty()) {
+      table.reserve(4096);  // returned pointers stay valid as the table grows
       table.push_back(2.0);
       if (m > 1) table.push_back(-2.0);
       if (m > 2) table.push_back(0.0);
@@ -108,6 +109,34 @@ const double* leja_table(int m) {
 void divided_differences_host(const double* x, double* f, int n) {
   for (int j = 1; j < n; ++j)
     for (int i = n - 1; i >= j; --i) f[i] = (f[i] - f[i - 1]) / (x[i] - x[i - j]);
+}
+
+void DDTable::grow(int n) {
+  if ((int)d.size() >= n) return;
+  const double* x = leja_table(n);
+  d.reserve(n);
+  diag.reserve(n);
+  for (int i = (int)d.size(); i < n; ++i) {
+    // new diagonal: nd[0] = f(x_i), nd[k] = (nd[k-1] - diag[k-1]) / (x_i - x_{i-k})
+    double nv = phi_host(l, a + b * x[i]);
+    if (i == 0) {
+      diag.push_back(nv);
+      d.push_back(nv);
+      continue;
+    }
+    double ov = diag[0];
+    diag[0] = nv;
+    for (int k = 1; k <= i; ++k) {
+      const double next_ov = k < i ? diag[k] : 0.0;
+      nv = (nv - ov) / (x[i] - x[i - k]);
+      ov = next_ov;
+      if (k < i)
+        diag[k] = nv;
+      else
+        diag.push_back(nv);
+    }
+    d.push_back(nv);
+  }
 }
 
 }  // namespace phix

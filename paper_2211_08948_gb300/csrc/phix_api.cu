@@ -11,6 +11,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <list>
 #include <string>
 #include <vector>
 
@@ -59,9 +60,17 @@ struct phix_ctx {
     phix_stats* stats;    // where the outcome goes (null: read by the caller)
     bool profile;
     double bytes_per_launch;
+    int m_table;          // last iteration the pass's table covers
+    int m_limit;          // the caller's m_max
   };
   std::vector<Pending> pend;     // queued passes since the last flush
   int nslot = 0;                 // slots in use
+  // divided-difference tables: truncated to about twice the predicted chain
+  // length; a chain that reaches the end of its table without converging
+  // sets ran_out, and the call is run again once with full tables
+  bool full_tables = false;
+  bool ran_out = false;
+  std::list<DDTable> dd_cache;   // recent tables (pure functions of l, a, b); references stay valid
   struct Graph {
     ChainSpec spec;
     cudaGraphExec_t exec;
@@ -84,6 +93,7 @@ namespace {
 struct Fail {
   phix_status st;
 };
+struct Rerun {};  // a pass ran past its truncated table: repeat the call with full tables
 
 void set_err(phix_ctx* c, const char* fmt, ...) {
   char b[512];
@@ -228,10 +238,14 @@ void flush(phix_ctx* ctx) {
     // when the chain stopped before its first iteration)
     ctx->launches += (long)GRAPH_ITERS * std::max(1, (c.iters + GRAPH_ITERS - 1) / GRAPH_ITERS);
     if (!q.stats) continue;
+    const int status = c.done ? c.status : PHIX_ENOTCONV;
+    if (status == PHIX_ENOTCONV && c.iters == q.m_table && q.m_table < q.m_limit) {
+      ctx->ran_out = true;  // the table was too short: the call runs again with full tables
+      continue;
+    }
     phix_stats& s = *q.stats;
     s.iters += c.iters;
     s.jv += c.iters;
-    const int status = c.done ? c.status : PHIX_ENOTCONV;
     if (status != PHIX_OK) s.status = status;
     if (q.profile) {
       float t = 0.f;
@@ -344,10 +358,10 @@ void queue_chain(phix_ctx* ctx, int s, const ChainSpec& spec, bool profile) {
 // One Newton-Leja pass (Sec. 2.2): queued; its outcome reaches `stats` at the
 // next flush.
 void leja_pass(phix_ctx* ctx, const OpState& os, int prec, const double* v, int K,
-               const std::vector<std::vector<double>>& d, double c, double gamma, double tol, const phix_opts& o,
-               double* const* out, phix_stats& stats) {
-  const int m_max = o.m_max;
-  const int M = m_max + 1;
+               const std::vector<const std::vector<double>*>& d, double c, double gamma, double tol,
+               const phix_opts& o, double* const* out, phix_stats& stats) {
+  const int M = (int)d[0]->size();  // table length: at most o.m_max + 1
+  const int m_max = M - 1;
   const double* xi = leja_table(M);
   const size_t eb = elem_bytes(prec);
   void* y[2] = {ws(ctx, S_Y0, os.N * eb), ws(ctx, S_Y1, os.N * eb)};
@@ -363,7 +377,7 @@ void leja_pass(phix_ctx* ctx, const OpState& os, int prec, const double* v, int 
   std::vector<double> beta(M, 0.0);
   for (int m = 1; m < M; ++m) beta[m] = -(c / gamma + xi[m - 1]);
   const double* dk[KMAX] = {};
-  for (int k = 0; k < K; ++k) dk[k] = d[k].data();
+  for (int k = 0; k < K; ++k) dk[k] = d[k]->data();
   const void* ptab = upload_ptab(ctx, s, K, o.m_min, m_max, tol, 0.0, k8, alpha, beta.data(), dk);
 
   KL(launch_scale(v, os.N, ctl, ctx->partials, ctx->grid_iter, ctx->stream));
@@ -407,6 +421,8 @@ void leja_pass(phix_ctx* ctx, const OpState& os, int prec, const double* v, int 
   q.slot = s;
   q.stats = &stats;
   q.profile = profile;
+  q.m_table = m_max;
+  q.m_limit = o.m_max;
   if (profile) {
     // algorithmic bytes of one iteration launch: read y, write the new
     // iterate, read and write each p_k, read the state planes
@@ -418,12 +434,56 @@ void leja_pass(phix_ctx* ctx, const OpState& os, int prec, const double* v, int 
   ctx->pend.push_back(q);
 }
 
-std::vector<double> dd_table(int l, double a, double b, int m) {
-  const double* xi = leja_table(m);
-  std::vector<double> f(m);
-  for (int i = 0; i < m; ++i) f[i] = phi_host(l, a + b * xi[i]);
-  divided_differences_host(xi, f.data(), m);
-  return f;
+// The cached table of phi_l(a + b x), grown as needed.  At most 16 are kept,
+// least recently used first; one pass looks up at most KMAX < 16 tables, so
+// none of them is evicted while the pass holds references.
+DDTable& dd_lookup(phix_ctx* ctx, int l, double a, double b) {
+  auto& c = ctx->dd_cache;
+  for (auto it = c.begin(); it != c.end(); ++it)
+    if (it->l == l && it->a == a && it->b == b) {
+      c.splice(c.end(), c, it);  // most recent last
+      return c.back();
+    }
+  if (c.size() >= 16) c.pop_front();
+  c.emplace_back();
+  DDTable& t = c.back();
+  t.l = l;
+  t.a = a;
+  t.b = b;
+  return t;
+}
+
+// Coefficient tables of one pass (outputs l_k of phi_{l_k}(a_k + b_k x)),
+// truncated to twice the predicted chain length plus 24 points: the chain is
+// predicted to stop by the first m >= m_min with |d_k[m]| <= tol |d_k[0]| / 2
+// for every k (the Newton terms decay like the divided differences).  Full
+// length (m_max + 1) when ctx->full_tables is set.
+std::vector<std::vector<double>> pass_tables(phix_ctx* ctx, int K, const int* l, const double* a, const double* b,
+                                             double tol, const phix_opts& o) {
+  const int M = o.m_max + 1;
+  std::vector<DDTable*> t(K);
+  for (int k = 0; k < K; ++k) t[k] = &dd_lookup(ctx, l[k], a[k], b[k]);
+  int M1 = M;
+  if (!ctx->full_tables) {
+    int m_pred = -1, n = 0;
+    while (m_pred < 0 && n < M) {
+      const int n0 = n;
+      n = std::min(M, n + 32);
+      for (int k = 0; k < K; ++k) t[k]->grow(n);
+      for (int m = std::max({1, o.m_min, n0}); m < n && m_pred < 0; ++m) {
+        bool ok = true;
+        for (int k = 0; k < K && ok; ++k) ok = std::fabs(t[k]->d[m]) <= 0.5 * tol * std::fabs(t[k]->d[0]);
+        if (ok) m_pred = m;
+      }
+    }
+    if (m_pred >= 0) M1 = std::min(M, 2 * m_pred + 24);
+  }
+  std::vector<std::vector<double>> d(K);
+  for (int k = 0; k < K; ++k) {
+    t[k]->grow(M1);
+    d[k].assign(t[k]->d.begin(), t[k]->d.begin() + M1);
+  }
+  return d;
 }
 
 // Power iteration (Sec. 2.2) on the device; flushes to read the estimate.
@@ -515,11 +575,16 @@ void leja_phi(phix_ctx* ctx, const OpState& os, int prec, double h, const double
     subs[k] = substeps_for(h, sc[k], ivc.gamma, o.rho_im, o);
     smax = std::max(smax, subs[k]);
   }
-  const int M = o.m_max + 1;
   if (smax == 1) {
-    std::vector<std::vector<double>> d(nout);
-    for (int k = 0; k < nout; ++k) d[k] = dd_table(l[k], sc[k] * h * ivc.c, sc[k] * h * ivc.gamma, M);
-    leja_pass(ctx, os, prec, v, nout, d, ivc.c, ivc.gamma, tol, o, out, stats);
+    double ta[KMAX], tb[KMAX];
+    for (int k = 0; k < nout; ++k) {
+      ta[k] = sc[k] * h * ivc.c;
+      tb[k] = sc[k] * h * ivc.gamma;
+    }
+    const std::vector<std::vector<double>> d = pass_tables(ctx, nout, l, ta, tb, tol, o);
+    std::vector<const std::vector<double>*> dp(nout);
+    for (int k = 0; k < nout; ++k) dp[k] = &d[k];
+    leja_pass(ctx, os, prec, v, nout, dp, ivc.c, ivc.gamma, tol, o, out, stats);
     stats.passes += 1;
     stats.substeps += 1;
     return;
@@ -533,7 +598,9 @@ void leja_phi(phix_ctx* ctx, const OpState& os, int prec, double h, const double
     const int L = l[k], ns = subs[k];
     if (L > 8) fail(ctx, PHIX_EINVAL, "substepped phi_l needs l <= 8");
     const double tau = 1.0 / ns;
-    const std::vector<std::vector<double>> d(1, dd_table(L, tau * sc[k] * h * ivc.c, tau * sc[k] * h * ivc.gamma, M));
+    const double ta = tau * sc[k] * h * ivc.c, tb = tau * sc[k] * h * ivc.gamma;
+    const std::vector<std::vector<double>> d = pass_tables(ctx, 1, &L, &ta, &tb, tol, o);
+    const std::vector<const std::vector<double>*> dp(1, &d[0]);
     if (L == 0)
       CK(cudaMemcpyAsync(u, v, os.N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
     else
@@ -549,7 +616,7 @@ void leja_phi(phix_ctx* ctx, const OpState& os, int prec, double h, const double
         stats.jv += 1;
       }
       double* outs[1] = {tmp};
-      leja_pass(ctx, os, prec, w[L], 1, d, ivc.c, ivc.gamma, tol, o, outs, stats);
+      leja_pass(ctx, os, prec, w[L], 1, dp, ivc.c, ivc.gamma, tol, o, outs, stats);
       stats.passes += 1;
       std::vector<double> cc;
       std::vector<const double*> xx;
@@ -813,17 +880,32 @@ phix_status guarded(phix_ctx* ctx, phix_stats* stats, F&& body) {
   ctx->err.clear();
   phix_stats st{};
   long l0 = ctx->launches;
-  phix_status rc;
-  try {
-    rc = body(st);
-    flush(ctx);  // outcomes of the passes still queued
-  } catch (const Fail& f) {
-    rc = f.st;
-    // drop queued passes: their stats target is this call's local record
-    (void)cudaStreamSynchronize(ctx->stream);
-    ctx->pend.clear();
-    ctx->nslot = 0;
+  phix_status rc = PHIX_OK;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    // a second attempt runs with full-length tables; the body changes none
+    // of its inputs before its last flush, so it can run again
+    st = phix_stats{};
+    ctx->ran_out = false;
+    ctx->full_tables = attempt > 0;
+    bool rerun = false;
+    try {
+      rc = body(st);
+      flush(ctx);  // outcomes of the passes still queued
+      rerun = ctx->ran_out;
+    } catch (const Rerun&) {
+      rerun = true;
+    } catch (const Fail& f) {
+      rc = f.st;
+      // drop queued passes: their stats target is this call's local record
+      (void)cudaStreamSynchronize(ctx->stream);
+      ctx->pend.clear();
+      ctx->nslot = 0;
+    }
+    if (!rerun) break;
+    rc = PHIX_OK;
   }
+  ctx->full_tables = false;
+  ctx->ran_out = false;
   if (rc == PHIX_OK && st.status != PHIX_OK) {
     rc = (phix_status)st.status;
     if (ctx->err.empty())
@@ -928,8 +1010,12 @@ phix_status phix_leja_points(double* xi, int m) {
 
 phix_status phix_divided_differences(int l, double a, double b, int m, double* d) {
   if (!d || m < 1 || m > 4096 || l < 0 || l > 20) return PHIX_EINVAL;
-  std::vector<double> t = dd_table(l, a, b, m);
-  std::memcpy(d, t.data(), sizeof(double) * m);
+  DDTable t;
+  t.l = l;
+  t.a = a;
+  t.b = b;
+  t.grow(m);
+  std::memcpy(d, t.d.data(), sizeof(double) * m);
   return PHIX_OK;
 }
 
@@ -1172,6 +1258,7 @@ phix_status phix_phi_action_learned(phix_ctx* ctx, const phix_jop* op, double h,
     st.rho = rho;
     leja_phi(ctx, os, o.prec, h, v, nout, l, scale, out, tol, ol, iv, st);
     flush(ctx);  // the fallback decision needs the passes' outcome
+    if (ctx->ran_out) throw Rerun{};
     if (st.status != PHIX_OK) {
       // fallback: the method's own power iteration, then recompute
       st.status = PHIX_OK;
@@ -1377,6 +1464,7 @@ static phix_status exp_step(phix_ctx* ctx, const phix_jop* op, double* u, double
     KL(launch_norm2(N, T4, nullptr, ctx->partials, ctx->counter, ctx->scal, ctx->grid_stream, ctx->stream));
     CK(cudaMemcpyAsync(ctx->scal_h, ctx->scal, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     flush(ctx);  // u changes only when every pass succeeded
+    if (ctx->ran_out) throw Rerun{};
     if (st.status == PHIX_OK) lincomb(ctx, N, {1.0, 1.0, 1.0, 1.0}, {u, P2, T3, T4}, u);
     CK(cudaStreamSynchronize(ctx->stream));
     st.err_est = std::sqrt(ctx->scal_h[0]);

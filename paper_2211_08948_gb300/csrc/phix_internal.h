@@ -8,6 +8,8 @@
 #include "df64.cuh"
 #include "phix.h"
 
+#include <vector>
+
 namespace phix {
 
 constexpr int KMAX = 4;       // accumulators of one vertical Newton pass
@@ -230,4 +232,18 @@ double phi_host(int l, double z);
 int leja_points_host(double* xi, int m);                 // 0 on success
 const double* leja_table(int m);                         // cached, thread-safe
 void divided_differences_host(const double* x, double* f, int n);
+
+// Newton divided differences d_i = f[x_0, ..., x_i] of f(x) = phi_l(a + b x)
+// on the Leja points, built one point at a time (O(n) per point): appending
+// x_n forms f[x_{n-k}, ..., x_n] for k = 1..n from the previous point's
+// diagonal.  Every entry comes from the same two operands and the same
+// formula as in the column-by-column recursion, so a table grown to n points
+// equals, bit for bit, the first n entries of any longer table.
+struct DDTable {
+  int l = 0;
+  double a = 0.0, b = 0.0;
+  std::vector<double> d;     // d[i] = f[x_0, ..., x_i]
+  std::vector<double> diag;  // diag[k] = f[x_{n-1-k}, ..., x_{n-1}], n = d.size()
+  void grow(int n);          // extend to n points (n <= 4096)
+};
 }  // namespace phix

@@ -74,3 +74,14 @@ def test_host_divided_differences_match_oracle(l, a, b):
     for m in range(150):
         assert abs(d[m] - do[m]) * np.max(np.abs(w)) <= 1e-13 * max(1.0, abs(do[0]))
         w = w * (t - x[m])
+
+
+@pytest.mark.parametrize("l,a,b", [(1, -50.0, 25.0), (4, -400.0, 200.0)])
+def test_host_divided_differences_prefix_is_exact(l, a, b):
+    """Tables are built one Leja point at a time; a short table is the prefix
+    of a long one bit for bit, so a chain may start on a truncated table and
+    continue on the full one with the same coefficients."""
+    phix, _ = _lib()
+    short = phix.phix_divided_differences(l, a, b, 40)
+    full = phix.phix_divided_differences(l, a, b, 300)
+    assert short == full[:40]

@@ -227,3 +227,28 @@ def test_invalid_arguments_and_nonconvergence(px):
     # the context stays usable
     st = phix.phix_phi_action(ctx, op, 1e-2, w, [1], [1.0], [out], 1e-10, phix.PHIX_LEJA, o)
     assert st.status == 0
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_chain_past_its_truncated_table_reruns_with_full_table(px, prec):
+    """Coefficient tables are sized to about twice the predicted chain length.
+    With m_min far above that prediction the chain reaches the end of its
+    table unconverged; the call then repeats itself once with full tables and
+    must agree with the oracle run under the same m_min."""
+    phix, ctx = px
+    n = 48
+    p = synth.advdiff_params(n)
+    v = synth.advdiff_gaussian(n)
+    rho = 8.0 * p["D"] * n * n
+    h = 10.0 / rho  # h * gamma = 3: the prediction is a few dozen iterations
+    outs = [(1, 1.0), (2, 1.0)]
+    tol = 1e-10
+    m_min = 150
+    res, st = _run_action(phix, ctx, phix.PHIX_OP_ADVDIFF, n, n, [p["D"], p["ax"], p["ay"]], None, v, h, outs,
+                          tol, prec, rho_re=rho, m_min=m_min)
+    op = AdvDiff(n, p["D"], p["ax"], p["ay"])
+    ref, info = leja.leja_phi(op.jv, v, h, -rho, 0.0, outs, tol, m_min=m_min)
+    assert st.status == 0 and info["status"] == 0
+    assert st.iters == info["iters"] == m_min
+    for r, o in zip(res, ref):
+        assert rel(r, o) <= 1e-10
