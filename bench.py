@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--clock-ms", type=int, default=100, help="nvidia-smi sampling period (0 = off)")
     ap.add_argument("--method", default="leja", choices=["leja", "kiops"])
+    ap.add_argument("--direct-launch", action="store_true",
+                    help="launch every iteration kernel on its own (for ncu, which does not see into "
+                         "conditional graphs); not a bench measurement")
     ap.add_argument("--workload", default="grayscott", choices=["grayscott", "burgers", "batched", "learned"],
                     help="grayscott: EXPRB43 steps (headline); burgers: phi_1(hJ) f h actions on the "
                          "2048^2 Burgers state (mixed-precision workload)")
@@ -158,7 +161,7 @@ def run_phix(args, world, rank, local):
     N = u0.size
     op = phix.make_jop(phix.PHIX_OP_GRAYSCOTT, n, n, [prm["Du"], prm["Dv"], prm["F"], prm["k"]])
     prec = getattr(phix, "PHIX_" + args.prec)
-    opts = phix.phix_opts_default(prec=prec, profile=1)
+    opts = phix.phix_opts_default(prec=prec, profile=2 if args.direct_launch else 1)
     meth = phix.PHIX_KIOPS if args.method == "kiops" else phix.PHIX_LEJA
     tol = 1e-8
     h = prm["h"]

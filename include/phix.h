@@ -108,9 +108,20 @@ typedef struct {
   int kiops_m_max;     /* KIOPS: max Krylov dimension (64)                             */
   int kiops_m_step;    /* KIOPS: basis growth on rejection (8)                         */
   int kiops_max_substeps; /* KIOPS: substep limit -> PHIX_ENOTCONV (10000)             */
-  int profile;         /* 1: time every iteration launch with CUDA events on the
-                          context's stream and report it in phix_stats (default 0)      */
+  int profile;         /* 1: time the iteration loops with CUDA events on the
+                          context's stream and report them in phix_stats; 2: as 1, and
+                          launch every iteration kernel on its own instead of in a
+                          conditional CUDA graph, for per-kernel profilers (slower:
+                          the host polls the chain) (default 0)                         */
+  int kernel;          /* Leja Newton-step kernel: PHIX_KERNEL_AUTO (default) takes the
+                          TMA-staged kernel when one iteration's operands exceed the L2
+                          cache and the single-step kernel otherwise; PHIX_KERNEL_SINGLE
+                          and PHIX_KERNEL_TMA force one (TMA needs rows of a multiple of
+                          16 bytes, i.e. nx even, nx % 4 == 0 for 4-byte state, and
+                          falls back to the single-step kernel otherwise)             */
 } phix_opts;
+
+typedef enum { PHIX_KERNEL_AUTO = 0, PHIX_KERNEL_SINGLE = 1, PHIX_KERNEL_TMA = 2 } phix_kernel;
 
 /* Per-call statistics (host struct, filled on return).                    */
 typedef struct {
@@ -132,6 +143,7 @@ typedef struct {
   int iter_launches;
   double iter_ms;
   double iter_bytes;
+  int tma_passes;    /* Leja Newton passes that ran the TMA-staged kernel              */
 } phix_stats;
 
 void phix_opts_default(phix_opts* opts);

@@ -270,6 +270,41 @@ __device__ __forceinline__ CJ stencil_burgers(const CJ (&k)[8], CJ ga, CJ e, CJ 
 }
 
 
+// ---------------------------------------------------------------------------
+// Chain parameter block: PassParams | beta_d[M] | beta_f[M] | dk_d[KMAX][M] | dk_f[KMAX][M]
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ const PassParams* pp_of(const unsigned char* t) {
+  return reinterpret_cast<const PassParams*>(t);
+}
+__device__ __forceinline__ const double* beta_d_of(const unsigned char* t, int M) {
+  return reinterpret_cast<const double*>(t + sizeof(PassParams));
+}
+__device__ __forceinline__ const float2* beta_f_of(const unsigned char* t, int M) {
+  return reinterpret_cast<const float2*>(t + sizeof(PassParams) + 8 * (size_t)M);
+}
+__device__ __forceinline__ const double* dk_d_of(const unsigned char* t, int M) {
+  return reinterpret_cast<const double*>(t + sizeof(PassParams) + 16 * (size_t)M);
+}
+__device__ __forceinline__ const float2* dk_f_of(const unsigned char* t, int M) {
+  return reinterpret_cast<const float2*>(t + sizeof(PassParams) + 16 * (size_t)M + 8 * (size_t)KMAX * M);
+}
+
+// centre-coefficient indices that the Newton shift beta is folded into
+template <int OP>
+struct Centre;
+template <>
+struct Centre<PHIX_OP_ADVDIFF> {
+  static constexpr int a = 4, b = -1;
+};
+template <>
+struct Centre<PHIX_OP_GRAYSCOTT> {
+  static constexpr int a = 2, b = 5;
+};
+template <>
+struct Centre<PHIX_OP_BURGERS> {
+  static constexpr int a = 2, b = -1;
+};
+
 // a coefficient in the arithmetic X, from its float64 / double-float forms
 template <typename X>
 __device__ __forceinline__ X coef(double d, float2 f);

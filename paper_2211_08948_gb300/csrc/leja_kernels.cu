@@ -43,37 +43,6 @@ __device__ __forceinline__ void stop_loop(const IterDev& a) {
   if (a.use_cond) cudaGraphSetConditional(a.cond, 0);
 }
 
-__device__ __forceinline__ const PassParams* pp_of(const unsigned char* t) {
-  return reinterpret_cast<const PassParams*>(t);
-}
-__device__ __forceinline__ const double* beta_d_of(const unsigned char* t, int M) {
-  return reinterpret_cast<const double*>(t + sizeof(PassParams));
-}
-__device__ __forceinline__ const float2* beta_f_of(const unsigned char* t, int M) {
-  return reinterpret_cast<const float2*>(t + sizeof(PassParams) + 8 * (size_t)M);
-}
-__device__ __forceinline__ const double* dk_d_of(const unsigned char* t, int M) {
-  return reinterpret_cast<const double*>(t + sizeof(PassParams) + 16 * (size_t)M);
-}
-__device__ __forceinline__ const float2* dk_f_of(const unsigned char* t, int M) {
-  return reinterpret_cast<const float2*>(t + sizeof(PassParams) + 16 * (size_t)M + 8 * (size_t)KMAX * M);
-}
-
-// centre-coefficient indices that the Newton shift beta is folded into
-template <int OP>
-struct Centre;
-template <>
-struct Centre<PHIX_OP_ADVDIFF> {
-  static constexpr int a = 4, b = -1;
-};
-template <>
-struct Centre<PHIX_OP_GRAYSCOTT> {
-  static constexpr int a = 2, b = 5;
-};
-template <>
-struct Centre<PHIX_OP_BURGERS> {
-  static constexpr int a = 2, b = -1;
-};
 
 // ---------------------------------------------------------------------------
 // The iteration kernel.
@@ -595,6 +564,7 @@ static void* kfn(const ChainSpec& s, int V) {
 
 cudaError_t iter_node_params(const ChainSpec& s, cudaKernelNodeParams* np, void* arg_storage,
                              size_t arg_bytes) {
+  if (s.tma) return tma_node_params(s, np, arg_storage, arg_bytes);
   if (arg_bytes < sizeof(IterDev)) return cudaErrorInvalidValue;
   const int V = (s.nx % 2 == 0) ? 2 : 1;
   IterDev a = make_dev(s, V);

@@ -41,6 +41,7 @@ struct phix_ctx {
   int nsm = 1;
   int grid_iter = 1;
   int grid_stream = 1;
+  double l2_bytes = 0.0;
   std::string err;
   void* buf[S_NSLOT] = {};
   size_t cap[S_NSLOT] = {};
@@ -322,7 +323,7 @@ cudaGraphExec_t chain_graph(phix_ctx* ctx, const ChainSpec& key) {
     ChainSpec spec = key;
     spec.use_cond = 1;
     spec.cond = h;
-    alignas(16) unsigned char argbuf[512];
+    alignas(64) unsigned char argbuf[2048];  // kernel arguments (tensor maps are 64-byte aligned)
     cudaGraphNode_t prev = nullptr;
     for (int i = 0; i < GRAPH_ITERS && e == cudaSuccess; ++i) {
       cudaKernelNodeParams np;
@@ -345,13 +346,33 @@ cudaGraphExec_t chain_graph(phix_ctx* ctx, const ChainSpec& key) {
 }
 
 // Queue a chain in slot s (bracketed by the slot's events when profiling).
-void queue_chain(phix_ctx* ctx, int s, const ChainSpec& spec, bool profile) {
+// direct: launch the iteration kernels one by one, GRAPH_ITERS at a time,
+// reading the slot's control block in between (for per-kernel profilers,
+// which do not see into conditional graphs); the device stops the chain by
+// m_max, so at most m_max + GRAPH_ITERS launches are made.
+void queue_chain(phix_ctx* ctx, int s, const ChainSpec& spec, bool profile, bool direct, int m_max) {
   ChainSpec key = spec;
   key.use_cond = 0;
   key.cond = 0;
-  cudaGraphExec_t exec = chain_graph(ctx, key);
   if (profile) CK(cudaEventRecord(ctx->ev[2 * s], ctx->stream));
-  CK(cudaGraphLaunch(exec, ctx->stream));  // its kernel launches are counted at the flush
+  if (direct) {
+    alignas(64) unsigned char argbuf[2048];
+    cudaKernelNodeParams np;
+    CK(iter_node_params(key, &np, argbuf, sizeof argbuf));
+    LejaCtl c{};
+    for (int launched = 0; launched <= m_max;) {
+      for (int i = 0; i < GRAPH_ITERS; ++i, ++launched) {
+        CK(cudaLaunchKernel(np.func, np.gridDim, np.blockDim, np.kernelParams, np.sharedMemBytes, ctx->stream));
+        ctx->launches += 1;
+      }
+      CK(cudaMemcpyAsync(&c, ctx->ctl + s, sizeof c, cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      if (c.done) break;
+    }
+    ctx->launches -= (long)GRAPH_ITERS * std::max(1, (c.iters + GRAPH_ITERS - 1) / GRAPH_ITERS);  // counted at the flush
+  } else {
+    CK(cudaGraphLaunch(chain_graph(ctx, key), ctx->stream));  // its kernel launches are counted at the flush
+  }
   if (profile) CK(cudaEventRecord(ctx->ev[2 * s + 1], ctx->stream));
 }
 
@@ -408,14 +429,27 @@ void leja_pass(phix_ctx* ctx, const OpState& os, int prec, const double* v, int 
   cs.ctl = ctl;
   cs.partials = ctx->partials;
   cs.ptab = ptab;
+  cs.K = K;
   {
+    // TMA staging pays once an iteration's operands no longer stay in L2
+    // (read y, write y', read and write each p_k, read the state)
+    const double st_b = os.d.kind == PHIX_OP_GRAYSCOTT ? 2.0 * os.plane * eb
+                       : os.d.kind == PHIX_OP_BURGERS ? 1.0 * os.plane * eb : 0.0;
+    const double work = (double)os.N * eb * (2.0 + 2.0 * K) + st_b;
+    const bool want = o.kernel == PHIX_KERNEL_TMA || (o.kernel == PHIX_KERNEL_AUTO && work > ctx->l2_bytes);
+    cs.tma = want && tma_eligible(cs) ? 1 : 0;
+  }
+  if (cs.tma) {
+    cs.grid = tma_grid(cs, ctx->nsm);
+  } else {
     const int gmax = ctx->nsm * std::min(8, iter_blocks_per_sm(cs));
     const int ntiles = iter_tiles(cs);
     const int per = (ntiles + gmax - 1) / gmax;  // tiles per block, balanced
     cs.grid = (ntiles + per - 1) / per;
   }
   const bool profile = o.profile != 0;
-  queue_chain(ctx, s, cs, profile);
+  queue_chain(ctx, s, cs, profile, o.profile == 2, m_max);
+  stats.tma_passes += cs.tma;
   KL(launch_finalize(prec, os.N, K, p, out, ctl, ctx->grid_stream, ctx->stream));
   phix_ctx::Pending q{};
   q.slot = s;
@@ -507,7 +541,7 @@ double power_iteration(phix_ctx* ctx, const OpState& os, int prec, const phix_op
   cs.partials = ctx->partials;
   cs.ptab = ptab;
   cs.grid = ctx->nsm * std::min(8, iter_blocks_per_sm(cs));
-  queue_chain(ctx, s, cs, false);
+  queue_chain(ctx, s, cs, false, o.profile == 2, o.power_max_it);
   phix_ctx::Pending q{};
   q.slot = s;
   ctx->pend.push_back(q);
@@ -870,6 +904,8 @@ phix_opts resolve_opts(phix_ctx* ctx, const phix_opts* in) {
   if (o.m_min < 0) fail(ctx, PHIX_EINVAL, "m_min must be >= 0");
   if (!(o.safety > 0)) fail(ctx, PHIX_EINVAL, "safety must be > 0");
   if (o.power_max_it < 1 || o.power_max_it > 4000) fail(ctx, PHIX_EINVAL, "power_max_it must be in 1..4000");
+  if (o.kernel < PHIX_KERNEL_AUTO || o.kernel > PHIX_KERNEL_TMA) fail(ctx, PHIX_EINVAL, "unknown kernel %d", o.kernel);
+  if (o.profile < 0 || o.profile > 2) fail(ctx, PHIX_EINVAL, "profile must be 0, 1 or 2");
   if (o.kiops_m_max < 2 || o.kiops_m_max > 128) fail(ctx, PHIX_EINVAL, "kiops_m_max must be in 2..128");
   return o;
 }
@@ -955,6 +991,9 @@ phix_status phix_create(phix_ctx** out, void* stream) {
   try {
     CK(cudaGetDevice(&ctx->device));
     CK(cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, ctx->device));
+    int l2 = 0;
+    CK(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, ctx->device));
+    ctx->l2_bytes = l2;
     ctx->grid_iter = ctx->nsm * 8;   // upper bound; chains use the occupancy of their kernel
     ctx->grid_stream = ctx->nsm * 8;
     CK(cudaMalloc(&ctx->ctl, sizeof(LejaCtl) * NSLOT));

@@ -75,6 +75,8 @@ struct ChainSpec {
   double* partials;   // grid * (KMAX + 1)
   const void* ptab;   // parameter block (device)
   int grid;           // blocks (<= partials capacity)
+  int K;              // MODE_NEWTON: accumulators
+  int tma;            // MODE_NEWTON: 1 = the TMA-staged kernel (leja_tma.cu)
   int use_cond;       // launched as the body of a conditional WHILE graph node:
   unsigned long long cond;  // its handle; the kernel clears it once the chain stopped
 };
@@ -85,6 +87,12 @@ cudaError_t iter_node_params(const ChainSpec& s, cudaKernelNodeParams* np, void*
                              size_t arg_bytes);
 // Blocks per SM the iteration kernel of this spec can keep resident.
 int iter_blocks_per_sm(const ChainSpec& s);
+// TMA-staged Newton step (leja_tma.cu): applicable when the rows are 16-byte
+// multiples and the staging fits; persistent CTAs, four per SM
+bool tma_eligible(const ChainSpec& s);
+int tma_grid(const ChainSpec& s, int nsm);
+cudaError_t tma_node_params(const ChainSpec& s, cudaKernelNodeParams* np, void* arg_storage, size_t arg_bytes);
+size_t tma_arg_bytes();
 int iter_tiles(const ChainSpec& s);  // tiles of one launch (work units of the grid loop)
 
 // y0 = v / sigma (stored in the precision's format), p_k = d_k[0] y0, norms, ctl->m = 1.

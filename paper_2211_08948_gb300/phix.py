@@ -20,6 +20,7 @@ PHIX_NOALLOC_MMAX = 1000
 PHIX_MLP_NPARAM = 5443
 PHIX_MLP_NFEAT = 16
 PHIX_LEJA, PHIX_KIOPS = 0, 1
+PHIX_KERNEL_AUTO, PHIX_KERNEL_SINGLE, PHIX_KERNEL_TMA = 0, 1, 2
 PHIX_FP64, PHIX_DF64, PHIX_FP32_JV, PHIX_FP32 = 0, 1, 2, 3
 PHIX_OP_ADVDIFF, PHIX_OP_GRAYSCOTT, PHIX_OP_BURGERS = 0, 1, 2
 
@@ -45,7 +46,7 @@ class phix_opts(ctypes.Structure):
                 ("power_rel", ctypes.c_double), ("power_seed", ctypes.c_uint64),
                 ("kiops_m_init", ctypes.c_int), ("kiops_m_max", ctypes.c_int),
                 ("kiops_m_step", ctypes.c_int), ("kiops_max_substeps", ctypes.c_int),
-                ("profile", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("kernel", ctypes.c_int)]
 
 
 class phix_batch_problem(ctypes.Structure):
@@ -60,7 +61,7 @@ class phix_stats(ctypes.Structure):
                 ("substeps", ctypes.c_int), ("power_mv", ctypes.c_int), ("rejections", ctypes.c_int),
                 ("passes", ctypes.c_int), ("launches", ctypes.c_int), ("rho", ctypes.c_double),
                 ("err_est", ctypes.c_double), ("iter_launches", ctypes.c_int), ("iter_ms", ctypes.c_double),
-                ("iter_bytes", ctypes.c_double)]
+                ("iter_bytes", ctypes.c_double), ("tma_passes", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
