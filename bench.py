@@ -34,6 +34,12 @@ UNIT = "phi-actions/s"
 WORKLOAD = "Gray-Scott 1024x1024x2, EXPRB43 steps, h=100x explicit limit, Leja, tol 1e-8"
 
 
+# DRAM bytes (read + write) of one launch of the dominant kernel, from an ncu --set full capture
+# of this configuration (k_iter, a K = 2 launch, cold caches); null for configurations without a
+# capture of the current kernel.
+TRAFFIC = {("leja", 1024, "DF64"): 67.16e6 + 9.05e6}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -270,7 +276,7 @@ def run_phix(args, world, rank, local):
                        else "k_arn1 + k_arn2 (Arnoldi step; CUDA events around each run of steps)"),
             "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None,
-            "traffic": None,
+            "traffic": TRAFFIC.get((args.method, n, args.prec)),
             "launches": iter_launches,
             "avg_launch_us": 1e3 * iter_ms / max(1, iter_launches),
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback",
