@@ -632,7 +632,8 @@ __global__ void __launch_bounds__(THREADS) k_kcomb(CombArgs a, size_t N) {
 
 template <int P>
 __global__ void __launch_bounds__(THREADS)
-    k_kstart(const double* __restrict__ b0, typename KTr<P>::T* __restrict__ z0, size_t N, CombArgs a, double eta) {
+    k_kstart(const double* __restrict__ b0, typename KTr<P>::T* __restrict__ z0, size_t N, CombArgs a, double eta,
+             double c) {
   using C = typename KTr<P>::C;
   using Acc = typename KTr<P>::Acc;
   KiopsCtl* kc = a.kc;
@@ -640,7 +641,7 @@ __global__ void __launch_bounds__(THREADS)
   const size_t stride = (size_t)gridDim.x * THREADS;
   const int tid = threadIdx.y * 32 + threadIdx.x;
   for (size_t i = (size_t)blockIdx.x * THREADS + tid; i < N; i += stride) {
-    double x = b0 ? b0[i] : 0.0;
+    double x = b0 ? c * b0[i] : 0.0;  // c: a power of two, exact
     C w;
     if constexpr (P == P_FP64)
       w = x;
@@ -657,8 +658,8 @@ __global__ void __launch_bounds__(THREADS)
       for (int t = 0; t < KIOPS_PMAX; ++t) kc->tail[t] = 0.0;
       double nz = tot[0];
       if (a.p > 0) {
-        kc->tail[a.p - 1] = 1.0 / eta;
-        nz += 1.0 / (eta * eta);
+        kc->tail[a.p - 1] = c / eta;
+        nz += (c / eta) * (c / eta);
       }
       const double beta = sqrt(nz);
       kc->beta = beta;
@@ -683,6 +684,7 @@ __global__ void __launch_bounds__(THREADS)
   for (size_t i = (size_t)blockIdx.x * THREADS + threadIdx.y * 32 + threadIdx.x; i < n; i += stride) {
     double x = b[i];
     acc[0] += fabs(x);
+    if (!out) continue;  // norm only
     if constexpr (P == P_FP64)
       out[i] = x;
     else {
@@ -798,13 +800,13 @@ cudaError_t kiops_combine(const KiopsSpec& s, int n, double* out, double scale, 
   return cudaGetLastError();
 }
 
-cudaError_t kiops_start(const KiopsSpec& s, const double* b0, double eta, cudaStream_t st) {
+cudaError_t kiops_start(const KiopsSpec& s, const double* b0, double eta, double cscale, cudaStream_t st) {
   const size_t N = (size_t)s.nx * s.ny * (s.op == PHIX_OP_GRAYSCOTT ? 2 : 1);
   CombArgs c = make_comb(s, 1, nullptr, 0.0);
   if (s.prec == P_FP64)
-    k_kstart<P_FP64><<<s.grid, dim3(32, TILE_Y), 0, st>>>(b0, static_cast<double*>(s.Zh[0]), N, c, eta);
+    k_kstart<P_FP64><<<s.grid, dim3(32, TILE_Y), 0, st>>>(b0, static_cast<double*>(s.Zh[0]), N, c, eta, cscale);
   else
-    k_kstart<P_DF64><<<s.grid, dim3(32, TILE_Y), 0, st>>>(b0, static_cast<float2*>(s.Zh[0]), N, c, eta);
+    k_kstart<P_DF64><<<s.grid, dim3(32, TILE_Y), 0, st>>>(b0, static_cast<float2*>(s.Zh[0]), N, c, eta, cscale);
   return cudaGetLastError();
 }
 

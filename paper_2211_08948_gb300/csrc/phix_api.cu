@@ -731,8 +731,11 @@ void kiops_run(phix_ctx* ctx, const OpState& os, int prec, double h, const doubl
   for (int j = 1; j <= p; ++j)
     if (b[j]) ++nb;
   unsigned char* bbase = nb ? static_cast<unsigned char*>(ws(ctx, S_KB, (size_t)nb * N * eb)) : nullptr;
-  double eta = 1.0;
-  if (nb) {
+  // 1-norms (float64 sums) of b_1..b_p, with their copies, and of b_0 -> eta and
+  // a power-of-two scale c of the whole augmented start vector [c b_0; c e_p / eta]
+  // (the action is linear; c keeps the double-float squares of the basis in range)
+  double eta = 1.0, cscale = 1.0;
+  {
     int q = 0;
     for (int j = 1; j <= p; ++j) {
       if (!b[j]) continue;
@@ -743,12 +746,18 @@ void kiops_run(phix_ctx* ctx, const OpState& os, int prec, double h, const doubl
       ++q;
     }
     ks.nb = nb;
-    CK(cudaMemcpyAsync(ctx->scal_h, ctx->scal, sizeof(double) * nb, cudaMemcpyDeviceToHost, ctx->stream));
+    if (b[0])
+      KL(kiops_convert(kp, N, b[0], nullptr, ctx->partials, ctx->counter, ctx->scal + nb, ctx->grid_stream,
+                       ctx->stream));
+    CK(cudaMemcpyAsync(ctx->scal_h, ctx->scal, sizeof(double) * (nb + 1), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     double nmax = 0.0;
     for (int q2 = 0; q2 < nb; ++q2) nmax = std::max(nmax, ctx->scal_h[q2]);
-    if (!std::isfinite(nmax)) fail(ctx, PHIX_ENAN, "non-finite input vector");
+    const double n0 = b[0] ? ctx->scal_h[nb] : 0.0;
+    if (!std::isfinite(nmax) || !std::isfinite(n0)) fail(ctx, PHIX_ENAN, "non-finite input vector");
     if (nmax > 0) eta = std::ldexp(1.0, -(int)std::ceil(std::log2(nmax)));
+    const double ref = std::max(n0, nb ? 1.0 / eta : 0.0);
+    if (ref > 0) cscale = std::ldexp(1.0, -(int)std::ceil(std::log2(ref)));
   }
   // algorithmic bytes of one Arnoldi step: the Jacobian product reads z_j, the
   // state planes and the b copies and writes w, with <w, z_{j-1}> on the way;
@@ -756,7 +765,7 @@ void kiops_run(phix_ctx* ctx, const OpState& os, int prec, double h, const doubl
   const size_t sbytes = os.d.kind == PHIX_OP_GRAYSCOTT ? 2 * os.plane * eb
                        : os.d.kind == PHIX_OP_BURGERS ? os.plane * eb : 0;
   const double step_bytes = (double)N * eb * (7.0 + nb) + (double)sbytes;
-  KL(kiops_start(ks, b[0], eta, ctx->stream));
+  KL(kiops_start(ks, b[0], eta, cscale, ctx->stream));
   read_kc(ctx, kc);
   stats.passes += 1;
   if (ctx->kc_h->status == PHIX_ENAN) fail(ctx, PHIX_ENAN, "non-finite input vector");
@@ -808,7 +817,8 @@ void kiops_run(phix_ctx* ctx, const OpState& os, int prec, double h, const doubl
       if (happy > 0 || omega <= 1.0) {
         const bool landed = std::fabs(t + tau - next_out) <= 1e-13 * std::max(1.0, next_out);
         const KOut* k0 = landed ? &outs[ti][0] : nullptr;
-        KL(kiops_combine(ks, happy > 0 ? m : m + 1, k0 ? k0->out : nullptr, k0 ? k0->scale : 0.0, ctx->stream));
+        KL(kiops_combine(ks, happy > 0 ? m : m + 1, k0 ? k0->out : nullptr, k0 ? k0->scale / cscale : 0.0,
+                         ctx->stream));
         if (landed) {
           for (size_t q = 1; q < outs[ti].size(); ++q)
             lincomb(ctx, N, {outs[ti][q].scale / k0->scale}, {k0->out}, outs[ti][q].out);

@@ -181,9 +181,10 @@ struct KiopsSpec {
   int nscaled;
   int grid;
 };
-// w_0: Zhat_0 = b_0 (or 0), tail_0 = e_p / eta, s_0 = 1/||w||, next pass-1 coefficients.
-cudaError_t kiops_start(const KiopsSpec& s, const double* b0, double eta, cudaStream_t st);
-// Convert b (float64) into the iteration precision; accumulate its 1-norm into *norm1.
+// w_0 = c [b_0; e_p / eta] (c a power of two): Zhat_0 = c b_0 (or 0), tail_0 = c e_p / eta,
+// s_0 = 1/||w_0||, next pass-1 coefficients.
+cudaError_t kiops_start(const KiopsSpec& s, const double* b0, double eta, double cscale, cudaStream_t st);
+// Convert b (float64) into the iteration precision (out may be NULL: norm only); its 1-norm -> *norm1.
 cudaError_t kiops_convert(int prec, size_t n, const double* b, void* out, double* partials,
                           unsigned int* counter, double* norm1, int grid, cudaStream_t st);
 // Arnoldi step j: pass 1 (z = A~ V_j, dots) and pass 2 (orthogonalise, norm).

@@ -185,3 +185,30 @@ def test_kiops_vs_leja_grayscott_1024_step(px):
     print("kiops", sk.as_dict(), "leja", sl.as_dict())
     a, b = host(uk), host(ul)
     assert rel(a - u0, b - u0) <= 1e-6
+
+
+@pytest.mark.parametrize("prec", ["FP64", "DF64"])
+@pytest.mark.parametrize("c", [2.0 ** -90, 2.0 ** 90])
+def test_kiops_scales_with_its_input(px, prec, c):
+    """phi_l(A)(c v) = c phi_l(A) v.  With c a power of two every rounding of
+    the method scales with it, so the results agree to rounding; the Krylov
+    basis must stay inside the double-float range however small or large the
+    input is (tiny inputs arise in practice: the nonlinear remainders that
+    feed phi_3 and phi_4 near a steady state)."""
+    phix, ctx = px
+    n = 64
+    p = synth.advdiff_params(n)
+    v = synth.advdiff_gaussian(n)
+    op = phix.make_jop(phix.PHIX_OP_ADVDIFF, n, n, [p["D"], p["ax"], p["ay"]])
+    outs = [(0, 1.0), (1, 1.0)]
+    res = {}
+    for scale in (1.0, c):
+        vd = dev(scale * v)
+        od = [torch.empty_like(vd) for _ in outs]
+        st = phix.phix_phi_action(ctx, op, p["h"], vd, [l for l, _ in outs], [s for _, s in outs], od, 1e-10,
+                                  phix.PHIX_KIOPS, _opts(phix, prec, **KW))
+        assert st.status == 0
+        res[scale] = [host(t) / scale for t in od]
+    for a, b in zip(res[c], res[1.0]):
+        assert np.all(np.isfinite(a))
+        assert np.linalg.norm(a - b) <= 1e-12 * np.linalg.norm(b)
