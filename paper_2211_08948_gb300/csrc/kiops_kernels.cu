@@ -265,34 +265,61 @@ __global__ void __launch_bounds__(THREADS) k_arn2(ArnArgs a, size_t n) {
   }
 }
 
-// F = exp(tau Hbar) e_1 for the tridiagonal Hbar (one CTA).
+// F = exp(tau Hbar) e_1 for the tridiagonal Hbar (one CTA of 128 threads).
 //
 // Main method: Chebyshev expansion on [lo, hi], the exact range of the real
 // parts of the field of values W(X), X = tau Hbar, i.e. the extreme
 // eigenvalues of the symmetric part (X + X^T)/2 (Bendixson):
 //   e^{c + r t} = e^{c + r} (I~_0(r) + 2 sum_k I~_k(r) T_k(t)),  I~_k = e^{-r} I_k,
 // applied with the three-term recurrence to Y = (X - c I)/r.  The extreme
-// eigenvalues come from a 128-way Sturm-sequence multisection (float32
-// counts, then a 1e-5 relative safety margin); the imaginary extent iota is
-// the spectral radius of the skew part (same routine on |skew| entries).
-// The scaled modified Bessel values come from Miller's backward recurrence
-// normalised by I~_0 + 2 sum_k I~_k = 1; the term count makes
-// 2 I~_k rho^k <= 1e-16, rho the Bernstein-ellipse parameter holding the box
-// [lo, hi] x [-iota, iota].  With Crouzeix's bound the error is ~1e-16
-// e^{hi} >= 1e-16 ||exp(X)||, i.e. normwise like a dense expm.
-// Fallback (iota > r/2 or no admissible term count): Taylor series in
-// segments of norm <= 1 after the shift by the interval midpoint.
+// eigenvalues come from Sturm-sequence multisection (float32 counts, then a
+// 1e-5 relative safety margin); the imaginary extent iota is the spectral
+// radius of the skew part (same routine on |skew| entries).  The scaled
+// modified Bessel values come from Miller's backward recurrence normalised by
+// I~_0 + 2 sum_k I~_k = 1; the term count makes 2 I~_k rho^k <= 1e-16, rho the
+// Bernstein-ellipse parameter holding the box [lo, hi] x [-iota, iota].  With
+// Crouzeix's bound the error is ~1e-16 e^{hi} >= 1e-16 ||exp(X)||, normwise
+// like a dense expm.  Fallback (iota > r/2, no admissible term count, or
+// rounding amplification above 100): Taylor series in segments of norm <= 4
+// after the shift by the interval midpoint.
+//
+// GB300 issues float64 at 1/64 of the float32 rate, so a serial float64 chain
+// costs ~70 cycles per operation: the recurrences (Bessel values, Chebyshev
+// and Taylor terms) run in double-float (~2^-47 per operation, far below the
+// tolerances the result serves) and every loop over rows or terms is spread
+// over the block.
 constexpr int CHEB_MAX = 600;
+constexpr int SX = 128;  // threads
 
-__device__ void tridiag_apply(int n, const double* dg, const double* up, const double* lo, double shift, double sc,
-                              const double* in, double* out, int tid) {
-  // out = sc * (T - shift I) in, T = tridiag(lo, dg, up)
-  for (int i = tid; i < n; i += 128) {
-    double v = (dg[i] - shift) * in[i];
-    if (i + 1 < n) v = fma(up[i], in[i + 1], v);
-    if (i >= 1) v = fma(lo[i - 1], in[i - 1], v);
-    out[i] = sc * v;
-  }
+__device__ __forceinline__ df dfd(double v) { return df_from_double(v); }
+__device__ __forceinline__ double dd(df v) { return (double)v.hi + (double)v.lo; }
+
+// block reductions over SX threads (sh: 4 doubles of scratch, reused after a barrier)
+__device__ double blk_min(double v, double* sh, int tid) {
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
+  if ((tid & 31) == 0) sh[tid >> 5] = v;
+  __syncthreads();
+  const double r = fmin(fmin(sh[0], sh[1]), fmin(sh[2], sh[3]));
+  __syncthreads();
+  return r;
+}
+__device__ double blk_max(double v, double* sh, int tid) { return -blk_min(-v, sh, tid); }
+__device__ df blk_dfsum(df v, df* sh, int tid) {
+  for (int o = 16; o > 0; o >>= 1)
+    v = df_add(v, df_make(__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)));
+  if ((tid & 31) == 0) sh[tid >> 5] = v;
+  __syncthreads();
+  const df r = df_add(df_add(sh[0], sh[1]), df_add(sh[2], sh[3]));
+  __syncthreads();
+  return r;
+}
+__device__ int blk_imin(int v, int* sh, int tid) {
+  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_down_sync(0xffffffffu, v, o));
+  if ((tid & 31) == 0) sh[tid >> 5] = v;
+  __syncthreads();
+  const int r = min(min(sh[0], sh[1]), min(sh[2], sh[3]));
+  __syncthreads();
+  return r;
 }
 
 // number of eigenvalues < x of the symmetric tridiagonal (diag a, squared off-diagonal b2)
@@ -308,200 +335,308 @@ __device__ int sturm_count(int n, const float* a, const float* b2, float x) {
   return cnt;
 }
 
-// Block-wide multisection: the largest (want_max) or smallest eigenvalue of the
-// symmetric tridiagonal, bracketed in [lo, hi].  Returns an outer bound.
-__device__ double eig_bound(int n, const float* a, const float* b2, double lo, double hi, bool want_max,
-                            int* cnt, double* br, int tid) {
-  for (int round = 0; round < 4; ++round) {
-    const double x = lo + (hi - lo) * (double)(tid + 1) / 129.0;
-    cnt[tid] = sturm_count(n, a, b2, (float)x);
-    __syncthreads();
-    if (tid == 0) {
-      double nlo = lo, nhi = hi;
-      if (want_max) {  // smallest point with all eigenvalues below it
-        int t = 0;
-        while (t < 128 && cnt[t] < n) ++t;
-        nhi = (t < 128) ? lo + (hi - lo) * (t + 1) / 129.0 : hi;
-        nlo = (t > 0) ? lo + (hi - lo) * t / 129.0 : lo;
-      } else {  // largest point with no eigenvalue below it
-        int t = 127;
-        while (t >= 0 && cnt[t] > 0) --t;
-        nlo = (t >= 0) ? lo + (hi - lo) * (t + 1) / 129.0 : lo;
-        nhi = (t < 127) ? lo + (hi - lo) * (t + 2) / 129.0 : hi;
-      }
-      br[0] = nlo;
-      br[1] = nhi;
+struct SmallExpWork {
+  double x[KIOPS_MMAX + 2];  // result (float64)
+  df xv[KIOPS_MMAX + 2], t0[KIOPS_MMAX + 2], t1[KIOPS_MMAX + 2], t2[KIOPS_MMAX + 2];
+  df ca[KIOPS_MMAX + 2], cu[KIOPS_MMAX + 2], cl[KIOPS_MMAX + 2];  // scaled matrix of the recurrence
+  df bes[CHEB_MAX + 2];
+  df invk[32];
+  float fa[KIOPS_MMAX + 2], fs2[KIOPS_MMAX + 2], fk2[KIOPS_MMAX + 2], fz[KIOPS_MMAX + 2];
+  int cnt[SX];
+  double br[4];
+  double sh[4];
+  df shd[4];
+  int shi[4];
+  int mode, S, K;
+  double shift, c, r, lead, glo, ghi, kb, rho, l2rho;
+};
+
+// Sturm multisection of [lo, hi] with `np` points per round on threads
+// [t0, t0 + np), `rounds` rounds; returns the outer bound of the largest
+// (want_max) or smallest eigenvalue.  All SX threads call it (barriers).
+// (Used for the imaginary extent; the two real bounds share their rounds.)
+__device__ double multisect(int n, const float* a, const float* b2, double lo, double hi, bool want_max, int t0,
+                            int np, int rounds, SmallExpWork& w, int slot, int tid) {
+  for (int round = 0; round < rounds; ++round) {
+    const bool mine = tid >= t0 && tid < t0 + np;
+    if (mine) {
+      const int t = tid - t0;
+      const double x = lo + (hi - lo) * (double)(t + 1) / (double)(np + 1);
+      w.cnt[tid] = sturm_count(n, a, b2, (float)x);
     }
     __syncthreads();
-    lo = br[0];
-    hi = br[1];
+    if (tid == t0) {
+      double nlo = lo, nhi = hi;
+      const double step = (hi - lo) / (double)(np + 1);
+      if (want_max) {  // smallest point with all eigenvalues below it
+        int t = 0;
+        while (t < np && w.cnt[t0 + t] < n) ++t;
+        nhi = (t < np) ? lo + step * (t + 1) : hi;
+        nlo = (t > 0) ? lo + step * t : lo;
+      } else {  // largest point with no eigenvalue below it
+        int t = np - 1;
+        while (t >= 0 && w.cnt[t0 + t] > 0) --t;
+        nlo = (t >= 0) ? lo + step * (t + 1) : lo;
+        nhi = (t < np - 1) ? lo + step * (t + 2) : hi;
+      }
+      w.br[2 * slot] = nlo;
+      w.br[2 * slot + 1] = nhi;
+    }
+    __syncthreads();
+    lo = w.br[2 * slot];
+    hi = w.br[2 * slot + 1];
     __syncthreads();
   }
   const double margin = 1e-5 * (fabs(lo) + fabs(hi)) + 1e-300;
   return want_max ? hi + margin : lo - margin;
 }
 
+// The largest (threads 0..63) and the smallest (threads 64..127) eigenvalue
+// of the symmetric tridiagonal at once: 4 rounds of 64-point multisection
+// each; outer bounds with the 1e-5 relative margin.
+__device__ void multisect2(int n, const float* a, const float* b2, double glo, double ghi, SmallExpWork& w,
+                           int tid, double& lam_hi, double& lam_lo) {
+  double lo[2] = {glo, glo}, hi[2] = {ghi, ghi};
+  const int g = tid >> 6, t = tid & 63;  // group 0: largest, group 1: smallest
+  for (int round = 0; round < 4; ++round) {
+    const double x = lo[g] + (hi[g] - lo[g]) * (double)(t + 1) / 65.0;
+    w.cnt[tid] = sturm_count(n, a, b2, (float)x);
+    __syncthreads();
+    if (t == 0) {
+      const double step = (hi[g] - lo[g]) / 65.0;
+      double nlo = lo[g], nhi = hi[g];
+      if (g == 0) {  // smallest point with all eigenvalues below it
+        int s = 0;
+        while (s < 64 && w.cnt[s] < n) ++s;
+        nhi = (s < 64) ? lo[g] + step * (s + 1) : hi[g];
+        nlo = (s > 0) ? lo[g] + step * s : lo[g];
+      } else {  // largest point with no eigenvalue below it
+        int s = 63;
+        while (s >= 0 && w.cnt[64 + s] > 0) --s;
+        nlo = (s >= 0) ? lo[g] + step * (s + 1) : lo[g];
+        nhi = (s < 63) ? lo[g] + step * (s + 2) : hi[g];
+      }
+      w.br[2 * g] = nlo;
+      w.br[2 * g + 1] = nhi;
+    }
+    __syncthreads();
+    for (int q = 0; q < 2; ++q) {
+      lo[q] = w.br[2 * q];
+      hi[q] = w.br[2 * q + 1];
+    }
+    __syncthreads();
+  }
+  lam_hi = hi[0] + (1e-5 * (fabs(lo[0]) + fabs(hi[0])) + 1e-300);
+  lam_lo = lo[1] - (1e-5 * (fabs(lo[1]) + fabs(hi[1])) + 1e-300);
+}
+
 // x = exp(T) e_1 for the n x n tridiagonal T = tridiag(lo, dg, up) (already
 // scaled by tau); lead: on return x holds exp(T) e_1 / e^{lead}.  Block-wide
-// (128 threads); work arrays in shared memory.
-struct SmallExpWork {
-  double x[KIOPS_MMAX + 2], t0[KIOPS_MMAX + 2], t1[KIOPS_MMAX + 2], t2[KIOPS_MMAX + 2];
-  double bes[CHEB_MAX + 2];
-  float fa[KIOPS_MMAX + 2], fs2[KIOPS_MMAX + 2], fk2[KIOPS_MMAX + 2], fz[KIOPS_MMAX + 2];
-  int cnt[128];
-  double br[2];
-  int mode, S, K;
-  double shift, c, r, lead, glo, ghi, kb, rad;
-};
-
+// (SX threads); work arrays in shared memory.
 __device__ void small_exp_e1(int n, const double* dg, const double* up, const double* lo, SmallExpWork& w,
                              int tid) {
-  if (tid == 0) {
-    double glo = 1e300, ghi = -1e300, kb = 0.0;
-    for (int i = 0; i < n; ++i) {
-      const double s = (i + 1 < n) ? 0.5 * (up[i] + lo[i]) : 0.0;
-      const double k = (i + 1 < n) ? 0.5 * (up[i] - lo[i]) : 0.0;
-      w.fa[i] = (float)dg[i];
-      w.fs2[i] = (float)(s * s);
-      w.fk2[i] = (float)(k * k);
-      w.fz[i] = 0.f;
-      double rs = fabs(s), rk = fabs(k);
-      if (i >= 1) {
-        rs += 0.5 * fabs(up[i - 1] + lo[i - 1]);
-        rk += 0.5 * fabs(up[i - 1] - lo[i - 1]);
-      }
-      glo = fmin(glo, dg[i] - rs);
-      ghi = fmax(ghi, dg[i] + rs);
-      kb = fmax(kb, rk);
+  // symmetric / skew parts in float32, Gershgorin box of each (one row per thread)
+  double glo = 1e300, ghi = -1e300, kb = 0.0;
+  for (int i = tid; i < n; i += SX) {
+    const double s = (i + 1 < n) ? 0.5 * (up[i] + lo[i]) : 0.0;
+    const double k = (i + 1 < n) ? 0.5 * (up[i] - lo[i]) : 0.0;
+    w.fa[i] = (float)dg[i];
+    w.fs2[i] = (float)(s * s);
+    w.fk2[i] = (float)(k * k);
+    w.fz[i] = 0.f;
+    double rs = fabs(s), rk = fabs(k);
+    if (i >= 1) {
+      rs += 0.5 * fabs(up[i - 1] + lo[i - 1]);
+      rk += 0.5 * fabs(up[i - 1] - lo[i - 1]);
     }
-    w.glo = glo - 1e-6 * (fabs(glo) + 1.0);
-    w.ghi = ghi + 1e-6 * (fabs(ghi) + 1.0);
-    w.kb = kb * (1.0 + 1e-6) + 1e-300;
+    glo = fmin(glo, dg[i] - rs);
+    ghi = fmax(ghi, dg[i] + rs);
+    kb = fmax(kb, rk);
   }
-  __syncthreads();
-  const double lam_hi = eig_bound(n, w.fa, w.fs2, w.glo, w.ghi, true, w.cnt, w.br, tid);
-  const double lam_lo = eig_bound(n, w.fa, w.fs2, w.glo, w.ghi, false, w.cnt, w.br, tid);
-  const double iota = (n > 1) ? eig_bound(n, w.fz, w.fk2, 0.0, w.kb, true, w.cnt, w.br, tid) : 0.0;
-  if (tid == 0) {
-    const double r = 0.5 * (lam_hi - lam_lo), c = 0.5 * (lam_hi + lam_lo);
-    int mode = 0;  // 0 Chebyshev, 1 Taylor
-    int K = -1;
-    if (!(r >= 1e-3) || iota > 0.5 * r) mode = 1;
-    if (mode == 0) {
-      const double y0 = iota / r;
-      const double b2 = 0.5 * (y0 * y0 + sqrt(y0 * y0 * y0 * y0 + 4.0 * y0 * y0));
-      const double rho = sqrt(1.0 + b2) + sqrt(b2);
-      int kmax = (int)(r + 12.0 * sqrt(r) + 60.0);
-      if (kmax > CHEB_MAX) kmax = CHEB_MAX;
-      double ip1 = 0.0, ik = 1e-280;
+  glo = blk_min(glo, w.sh, tid);
+  ghi = blk_max(ghi, w.sh, tid);
+  kb = blk_max(kb, w.sh, tid);
+  glo -= 1e-6 * (fabs(glo) + 1.0);
+  ghi += 1e-6 * (fabs(ghi) + 1.0);
+  kb = kb * (1.0 + 1e-6) + 1e-300;
+  // both real-part bounds in the same rounds (64 points each, 4 rounds: 65^-4 of the box), then iota
+  double lam_hi = 0.0, lam_lo = 0.0;
+  multisect2(n, w.fa, w.fs2, glo, ghi, w, tid, lam_hi, lam_lo);
+  const double iota = (n > 1) ? multisect(n, w.fz, w.fk2, 0.0, kb, true, 0, SX, 3, w, 0, tid) : 0.0;
+  const double r = 0.5 * (lam_hi - lam_lo), c = 0.5 * (lam_hi + lam_lo);
+  int mode = (!(r >= 1e-3) || iota > 0.5 * r) ? 1 : 0;
+  int K = -1;
+  if (mode == 0) {
+    const double y0 = iota / r;
+    const double b2 = 0.5 * (y0 * y0 + sqrt(y0 * y0 * y0 * y0 + 4.0 * y0 * y0));
+    const double rho = sqrt(1.0 + b2) + sqrt(b2);
+    int kmax = (int)(r + 12.0 * sqrt(r) + 60.0);
+    if (kmax > CHEB_MAX) kmax = CHEB_MAX;
+    if (tid == 0) {
+      // Miller's backward recurrence I_{k-1} = (2k/r) I_k + I_{k+1} in double-float,
+      // rescaled by powers of two
       const int kstart = kmax + 40 + (int)sqrt(r);
-      const double ir = 1.0 / r;
+      const df ir2 = dfd(2.0 / r);
+      df ip1 = df_make(0.f, 0.f), ik = df_make(1e-30f, 0.f);
       for (int k = kstart; k >= 0; --k) {
         if (k <= kmax) w.bes[k] = ik;
-        const double im1 = (2.0 * k * ir) * ik + ip1;  // I_{k-1} = (2k/r) I_k + I_{k+1}
+        const df im1 = df_add(df_mul(df_mul(df_make((float)k, 0.f), ir2), ik), ip1);
         ip1 = ik;
         ik = im1;
-        if (fabs(ik) > 1e250) {
-          ik *= 1e-250;
-          ip1 *= 1e-250;
-          for (int q = k; q <= kmax; ++q) w.bes[q] *= 1e-250;
+        if (fabsf(ik.hi) > 1e30f) {
+          ik = df_scale2(ik, 0x1p-100f);
+          ip1 = df_scale2(ip1, 0x1p-100f);
+          for (int q = k; q <= kmax; ++q) w.bes[q] = df_scale2(w.bes[q], 0x1p-100f);
         }
       }
-      double sum = w.bes[0];
-      for (int k = 1; k <= kmax; ++k) sum += 2.0 * w.bes[k];
-      const double isum = 1.0 / sum;
-      for (int k = 0; k <= kmax; ++k) w.bes[k] *= isum;
-      // term count, and the amplification max_k 2 I~_k rho^k of rounding errors
-      double rk = 1.0, amp = 0.0;
-      for (int k = 0; k <= kmax; ++k) {
-        amp = fmax(amp, 2.0 * w.bes[k] * rk);
-        if (k > 2 && 2.0 * w.bes[k] * rk <= 1e-16 && 2.0 * w.bes[k - 1] * rk / rho <= 1e-16) {
-          K = k;
-          break;
-        }
-        rk *= rho;
-        if (rk > 1e200) break;
-      }
-      if (K < 0 || amp > 100.0) mode = 1;
+      w.rho = rho;
+      w.l2rho = log2(rho);
     }
-    if (mode == 1) {
-      // shift to the centre of the field-of-values box; ||T - cI||_2 <= 2 w(T - cI)
-      // <= 2 sqrt(r^2 + iota^2) (numerical radius), or the 1-norm if smaller
-      double nrm1 = 0.0;
-      for (int i = 0; i < n; ++i) {
-        double cs = fabs(dg[i] - c);
-        if (i >= 1) cs += fabs(up[i - 1]);
-        if (i + 1 < n) cs += fabs(lo[i]);
-        nrm1 = fmax(nrm1, cs);
-      }
-      const double nrm = fmin(nrm1, 2.0 * sqrt(r * r + iota * iota));
-      w.shift = c;
-      w.S = nrm > 4.0 ? (int)ceil(nrm / 4.0) : 1;
-      w.lead = c;
-    } else {
-      w.c = c;
-      w.r = r;
-      w.lead = lam_hi;  // e^{c + r}
-    }
-    w.mode = mode;
-    w.K = K;
-  }
-  __syncthreads();
-  double* x = w.x;
-  if (w.mode == 1) {
-    // Taylor, S segments of norm <= 4, 30 terms each (4^31/31! < 6e-16)
-    const int S = w.S;
-    const double mu = w.shift;
-    const double sc = 1.0 / S;
-    for (int i = tid; i < n; i += 128) x[i] = (i == 0) ? 1.0 : 0.0;
     __syncthreads();
+    // normalise: I~_0 + 2 sum_{k >= 1} I~_k = 1
+    df part = df_make(0.f, 0.f);
+    for (int k = tid; k <= kmax; k += SX) part = df_add(part, k == 0 ? w.bes[0] : df_scale2(w.bes[k], 2.f));
+    const df sum = blk_dfsum(part, w.shd, tid);
+    const df isum = dfd(1.0 / dd(sum));
+    for (int k = tid; k <= kmax; k += SX) w.bes[k] = df_mul(w.bes[k], isum);
+    __syncthreads();
+    // term count: the first k > 2 with 2 I~_k rho^k and 2 I~_{k-1} rho^{k-1} <= 1e-16
+    // (log2 in float32: a threshold test); no count before rho^k > 2^96 (T_k(Y) e1 must
+    // stay inside the double-float range) -> Taylor
+    const float l2r = (float)w.l2rho;
+    const float lim = -53.15f;  // log2(1e-16)
+    auto lv = [&](int k) -> float {
+      const float b = 2.f * w.bes[k].hi;
+      return (b > 0.f ? log2f(b) : -1e30f) + (float)k * l2r;
+    };
+    int kc = 1 << 30;
+    for (int k = 3 + tid; k <= kmax; k += SX)
+      if (lv(k) <= lim && lv(k - 1) <= lim && (float)k * l2r <= 96.f) kc = min(kc, k);
+    kc = blk_imin(kc, w.shi, tid);
+    if (kc < (1 << 30)) {
+      // amplification of rounding errors: max_{k < K} 2 I~_k rho^k
+      double amp = -1e300;
+      for (int k = tid; k < kc; k += SX) amp = fmax(amp, (double)lv(k));
+      amp = blk_max(amp, w.sh, tid);
+      if (amp <= 6.644) K = kc;  // log2(100)
+    }
+    if (K < 0) mode = 1;
+  }
+  // the recurrence in double-float
+  df* x = w.xv;
+  if (mode == 1) {
+    // Taylor, S segments of norm <= 4, 30 terms each (4^31/31! < 6e-16), about
+    // the centre of the field-of-values box; ||T - cI||_2 <= 2 sqrt(r^2 + iota^2)
+    // (numerical radius), or the 1-norm if smaller
+    double cs = 0.0;
+    for (int i = tid; i < n; i += SX) {
+      double v = fabs(dg[i] - c);
+      if (i >= 1) v += fabs(up[i - 1]);
+      if (i + 1 < n) v += fabs(lo[i]);
+      cs = fmax(cs, v);
+    }
+    const double nrm1 = blk_max(cs, w.sh, tid);
+    const double nrm = fmin(nrm1, 2.0 * sqrt(r * r + iota * iota));
+    const int S = nrm > 4.0 ? (int)ceil(nrm / 4.0) : 1;
+    const double sc = 1.0 / S;
+    for (int i = tid; i < n; i += SX) {
+      w.ca[i] = dfd((dg[i] - c) * sc);
+      w.cu[i] = dfd(up[i] * sc);
+      w.cl[i] = dfd(lo[i] * sc);
+      x[i] = df_make(i == 0 ? 1.f : 0.f, 0.f);
+    }
+    if (tid < 32) w.invk[tid] = dfd(tid > 0 ? 1.0 / tid : 0.0);
+    __syncthreads();
+    double lead = c;
     for (int seg = 0; seg < S; ++seg) {
-      for (int i = tid; i < n; i += 128) w.t0[i] = x[i];
+      // keep x near 1 by a power of two (each segment multiplies it by at most e^4)
+      double mx = 0.0;
+      for (int i = tid; i < n; i += SX) mx = fmax(mx, fabs((double)x[i].hi));
+      mx = blk_max(mx, w.sh, tid);
+      int e = 0;
+      if (mx > 0.0) (void)frexp(mx, &e);
+      if (e != 0) {
+        const float f = ldexpf(1.f, -e);
+        for (int i = tid; i < n; i += SX) w.t0[i] = df_scale2(x[i], f);
+        lead += e * 0.69314718055994530942;
+      } else {
+        for (int i = tid; i < n; i += SX) w.t0[i] = x[i];
+      }
       __syncthreads();
-      double* cur = w.t0;
-      double* nxt = w.t1;
+      for (int i = tid; i < n; i += SX) x[i] = w.t0[i];
+      __syncthreads();
+      df* cur = w.t0;
+      df* nxt = w.t1;
       for (int k = 1; k <= 30; ++k) {
-        tridiag_apply(n, dg, up, lo, mu, sc / k, cur, nxt, tid);
-        for (int i = tid; i < n; i += 128) x[i] += nxt[i];
+        for (int i = tid; i < n; i += SX) {
+          df v = df_mul(w.ca[i], cur[i]);
+          if (i + 1 < n) v = df_add(v, df_mul(w.cu[i], cur[i + 1]));
+          if (i >= 1) v = df_add(v, df_mul(w.cl[i - 1], cur[i - 1]));
+          v = df_mul(v, w.invk[k]);
+          nxt[i] = v;
+          x[i] = df_add(x[i], v);
+        }
         __syncthreads();
-        double* tsw = cur;
+        df* tsw = cur;
         cur = nxt;
         nxt = tsw;
       }
     }
+    if (tid == 0) {
+      w.mode = 1;
+      w.lead = lead;
+      w.S = S;
+    }
   } else {
     // x = I~_0 e1 + 2 sum_{k>=1} I~_k T_k(Y) e1,  Y = (T - cI)/r
-    const int K = w.K;
-    const double c = w.c, ir = 1.0 / w.r;
-    double* tm = w.t0;
-    double* tc = w.t1;
-    double* tn = w.t2;
-    for (int i = tid; i < n; i += 128) {
-      tm[i] = (i == 0) ? 1.0 : 0.0;
-      x[i] = (i == 0) ? w.bes[0] : 0.0;
+    const double ir = 1.0 / r;
+    for (int i = tid; i < n; i += SX) {
+      w.ca[i] = dfd((dg[i] - c) * ir);
+      w.cu[i] = dfd(up[i] * ir);
+      w.cl[i] = dfd(lo[i] * ir);
     }
     __syncthreads();
-    tridiag_apply(n, dg, up, lo, c, ir, tm, tc, tid);
-    for (int i = tid; i < n; i += 128) x[i] += 2.0 * w.bes[1] * tc[i];
+    df* tm = w.t0;
+    df* tc = w.t1;
+    df* tn = w.t2;
+    for (int i = tid; i < n; i += SX) {
+      tm[i] = df_make(i == 0 ? 1.f : 0.f, 0.f);
+      // T_1 e1 = Y e1: column 0 of Y
+      tc[i] = i == 0 ? w.ca[0] : (i == 1 ? w.cl[0] : df_make(0.f, 0.f));
+      x[i] = df_make(0.f, 0.f);
+      if (i == 0) x[i] = w.bes[0];
+      x[i] = df_add(x[i], df_mul(df_scale2(w.bes[1], 2.f), tc[i]));
+    }
     __syncthreads();
     for (int k = 2; k < K; ++k) {
-      tridiag_apply(n, dg, up, lo, c, 2.0 * ir, tc, tn, tid);
-      for (int i = tid; i < n; i += 128) {
-        const double v = tn[i] - tm[i];
+      const df bk = df_scale2(w.bes[k], 2.f);
+      for (int i = tid; i < n; i += SX) {
+        // T_{k} = 2 Y T_{k-1} - T_{k-2}
+        df v = df_mul(w.ca[i], tc[i]);
+        if (i + 1 < n) v = df_add(v, df_mul(w.cu[i], tc[i + 1]));
+        if (i >= 1) v = df_add(v, df_mul(w.cl[i - 1], tc[i - 1]));
+        v = df_sub(df_scale2(v, 2.f), tm[i]);
         tn[i] = v;
-        x[i] = fma(2.0 * w.bes[k], v, x[i]);
+        x[i] = df_add(x[i], df_mul(bk, v));
       }
       __syncthreads();
-      double* tsw = tm;
+      df* tsw = tm;
       tm = tc;
       tc = tn;
       tn = tsw;
     }
+    if (tid == 0) {
+      w.mode = 0;
+      w.lead = lam_hi;  // e^{c + r}
+      w.K = K;
+    }
   }
+  __syncthreads();
+  for (int i = tid; i < n; i += SX) w.x[i] = dd(x[i]);
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(128) k_kexp(KiopsCtl* kc, int m, double tau, double tau_end, double tol) {
+__global__ void __launch_bounds__(SX) k_kexp(KiopsCtl* kc, int m, double tau, double tau_end, double tol) {
   __shared__ double dg[KIOPS_MMAX + 2], up[KIOPS_MMAX + 2], lo[KIOPS_MMAX + 2];
   __shared__ SmallExpWork w;
   __shared__ int n_s;

@@ -46,7 +46,9 @@ def test_small_expm_vs_scipy(px, skew):
         modes.add(mode)
         got = F.cpu().numpy()
         err = np.linalg.norm(got - ref) / np.linalg.norm(E, 2)
-        assert err <= 1e-13, (n, tau, mode, err)
+        # double-float recurrences (~2^-47 per operation, up to 30 S Taylor terms):
+        # normwise 1e-12, two orders below the tolerances the result serves
+        assert err <= 1e-12, (n, tau, mode, err)
     print("skew", skew, "paths", sorted(modes))
 
 
