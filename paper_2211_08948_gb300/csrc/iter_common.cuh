@@ -128,6 +128,11 @@ __device__ __forceinline__ df from_cj(df x, df) { return x; }
 __device__ __forceinline__ df from_cj(float x, df) { return df_make(x, 0.f); }
 __device__ __forceinline__ float from_cj(float x, float) { return x; }
 
+// a * b + c in each arithmetic
+__device__ __forceinline__ double mad(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float mad(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ df mad(df a, df b, df c) { return df_fma(a, b, c); }
+
 // squares for the norms
 __device__ __forceinline__ void acc_sq(double& a, double x) { a = fma(x, x, a); }
 __device__ __forceinline__ void acc_sq(float& a, df x) { a = fmaf(x.hi, x.hi, a); }
@@ -258,6 +263,36 @@ __device__ __forceinline__ void stencil_gs(const CJ (&k)[8], CJ ga, CJ ue, CJ uw
   CJ a2 = ga * g2;
   ju = k[0] * (ue + uw) + k[1] * (un + us) + (k[2] - a1) * uc - a2 * vc;
   jv = k[3] * (ve + vw) + k[4] * (vn + vs) + a1 * uc + (k[5] + a2) * vc;
+}
+
+// double-float forms: the products of each row summed as unnormalised pairs
+template <>
+__device__ __forceinline__ df stencil_advdiff<df>(const df (&k)[8], df e, df w, df n, df s, df c) {
+  float p[5], q[5];
+  df_prod(k[0], e, p[0], q[0]);
+  df_prod(k[1], w, p[1], q[1]);
+  df_prod(k[2], n, p[2], q[2]);
+  df_prod(k[3], s, p[3], q[3]);
+  df_prod(k[4], c, p[4], q[4]);
+  return df_sum_pairs<5>(p, q);
+}
+
+template <>
+__device__ __forceinline__ void stencil_gs<df>(const df (&k)[8], df ga, df ue, df uw, df un, df us, df uc, df ve,
+                                               df vw, df vn, df vs, df vc, df g1, df g2, df& ju, df& jv) {
+  const df a1 = ga * g1;
+  const df a2 = ga * g2;
+  float p[4], q[4];
+  df_prod(k[0], ue + uw, p[0], q[0]);
+  df_prod(k[1], un + us, p[1], q[1]);
+  df_prod(k[2] - a1, uc, p[2], q[2]);
+  df_prod(df_neg(a2), vc, p[3], q[3]);
+  ju = df_sum_pairs<4>(p, q);
+  df_prod(k[3], ve + vw, p[0], q[0]);
+  df_prod(k[4], vn + vs, p[1], q[1]);
+  df_prod(a1, uc, p[2], q[2]);
+  df_prod(k[5] + a2, vc, p[3], q[3]);
+  jv = df_sum_pairs<4>(p, q);
 }
 
 template <typename CJ>

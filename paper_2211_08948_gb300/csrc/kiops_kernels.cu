@@ -225,12 +225,46 @@ __global__ void __launch_bounds__(THREADS) k_arn2(ArnArgs a, size_t n) {
   const T* __restrict__ zm = static_cast<const T*>(a.zjm1);
   T* __restrict__ zo = static_cast<T*>(a.zout);
   Acc acc[1] = {acc_zero<Acc>()};
+  // element pairs (16-byte accesses; every vector starts 256-byte aligned), two
+  // pairs per thread per trip so that six loads are in flight
+  const size_t np = n / 2;
+  const size_t t0 = (size_t)blockIdx.x * THREADS + threadIdx.y * 32 + threadIdx.x;
   const size_t stride = (size_t)gridDim.x * THREADS;
-  for (size_t i = (size_t)blockIdx.x * THREADS + threadIdx.y * 32 + threadIdx.x; i < n; i += stride) {
+  auto pair = [&](size_t q) {
+    const size_t i = 2 * q;
+    C w0, w1, a0, a1, b0 = C{}, b1 = C{};
+    ldw2(zo + i, w0, w1);
+    ldr2(zj + i, a0, a1);
+    if (zm) ldr2(zm + i, b0, b1);
+    C z0 = w0 - c1 * a0, z1 = w1 - c1 * a1;
+    if (zm) {
+      z0 = z0 - c0 * b0;
+      z1 = z1 - c0 * b1;
+    }
+    st2(zo + i, z0, z1);
+    acc_dot(acc[0], z0, z0);
+    acc_dot(acc[0], z1, z1);
+  };
+  auto single = [&](size_t i) {
     C z = ldw1(zo + i) - c1 * ldr1(zj + i);
     if (zm) z = z - c0 * ldr1(zm + i);
     st1(zo + i, z);
     acc_dot(acc[0], z, z);
+  };
+  // basis slots lie N elements apart: with N odd every other slot is only
+  // 8-byte aligned, and the pairs would be misaligned
+  const bool vec = ((reinterpret_cast<uintptr_t>(zo) | reinterpret_cast<uintptr_t>(zj) |
+                     reinterpret_cast<uintptr_t>(zm)) & 15) == 0;
+  if (vec) {
+    size_t q = t0;
+    for (; q + stride < np; q += 2 * stride) {
+      pair(q);
+      pair(q + stride);
+    }
+    if (q < np) pair(q);
+    if ((n & 1) && t0 == 0) single(n - 1);  // odd length: the last element
+  } else {
+    for (size_t i = t0; i < n; i += stride) single(i);
   }
   if (block_partials_and_last<Acc, 1>(acc, a.partials, &kc->count)) {
     double tot[1];

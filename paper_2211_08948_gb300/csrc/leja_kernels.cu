@@ -216,13 +216,13 @@ __global__ void __launch_bounds__(THREADS) k_iter(IterDev a) {
           if (kq < K) {
             T* pp2 = static_cast<T*>(a.p[kq]) + q * plane + row + ix;
             if constexpr (V == 2) {
-              const C p0 = pv[q][kq][0] + dk[kq] * out[q][0];
-              const C p1 = pv[q][kq][1] + dk[kq] * out[q][1];
+              const C p0 = mad(dk[kq], out[q][0], pv[q][kq][0]);
+              const C p1 = mad(dk[kq], out[q][1], pv[q][kq][1]);
               st2(pp2, p0, p1);
               acc_sq(acc[1 + kq], p0);
               acc_sq(acc[1 + kq], p1);
             } else {
-              const C p0 = pv[q][kq][0] + dk[kq] * out[q][0];
+              const C p0 = mad(dk[kq], out[q][0], pv[q][kq][0]);
               st1(pp2, p0);
               acc_sq(acc[1 + kq], p0);
             }

@@ -362,8 +362,8 @@ __global__ void __launch_bounds__(TT, CTAS_PER_SM) k_iter_tma(const __grid_const
 #pragma unroll
         for (int k = 0; k < KMAX; ++k) {
           if (k < K) {
-            const C p0 = pv[q][k][0] + dk[k] * out[q][0];
-            const C p1 = pv[q][k][1] + dk[k] * out[q][1];
+            const C p0 = mad(dk[k], out[q][0], pv[q][k][0]);
+            const C p1 = mad(dk[k], out[q][1], pv[q][k][1]);
             st2(static_cast<T*>(a.p[k]) + q * plane + g, p0, p1);
             acc_sq(acc[1 + k], p0);
             acc_sq(acc[1 + k], p1);

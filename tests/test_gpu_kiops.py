@@ -141,7 +141,9 @@ def test_kiops_happy_breakdown(px):
     st = phix.phix_phi_action(ctx, op, 0.01, vd, [0], [1.0], [out], 1e-10, phix.PHIX_KIOPS,
                               phix.phix_opts_default())
     assert st.iters == 1 and st.substeps == 1
-    assert torch.allclose(out, vd, rtol=1e-14, atol=0)
+    # J v = 0 is a cancellation of stencil products of size ~200: double-float
+    # leaves ~2^-47 of that, so exp(hJ) v = v holds to rounding, not exactly
+    assert torch.allclose(out, vd, rtol=1e-12, atol=0)
     ref, info = kiops.kiops(lambda x: 0.01 * AdvDiff(n, 1.0, 2.0, 3.0).jv(x), [np.full(n * n, 0.75)], [1.0], 1e-10)
     assert info["matvecs"] == 1
 
