@@ -137,7 +137,7 @@ __device__ __forceinline__ df mad(df a, df b, df c) { return df_fma(a, b, c); }
 __device__ __forceinline__ void acc_sq(double& a, double x) { a = fma(x, x, a); }
 __device__ __forceinline__ void acc_sq(float& a, df x) { a = fmaf(x.hi, x.hi, a); }
 __device__ __forceinline__ void acc_sq(float& a, float x) { a = fmaf(x, x, a); }
-__device__ __forceinline__ void acc_sq(df& a, df x) { a = df_add(df_mul(x, x), a); }
+__device__ __forceinline__ void acc_sq(df& a, df x) { a = df_fma(x, x, a); }
 
 __device__ __forceinline__ double acc_to_double(double a) { return a; }
 __device__ __forceinline__ double acc_to_double(float a) { return (double)a; }

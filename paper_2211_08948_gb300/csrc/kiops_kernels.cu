@@ -22,7 +22,7 @@ namespace {
 
 // dot products: float64, or double-float accumulation
 __device__ __forceinline__ void acc_dot(double& a, double x, double y) { a = fma(x, y, a); }
-__device__ __forceinline__ void acc_dot(df& a, df x, df y) { a = df_add(df_mul(x, y), a); }
+__device__ __forceinline__ void acc_dot(df& a, df x, df y) { a = df_fma(x, y, a); }
 
 template <int P>
 struct KTr;
