@@ -254,15 +254,19 @@ __device__ __forceinline__ CJ stencil_advdiff(const CJ (&k)[8], CJ e, CJ w, CJ n
   return k[0] * e + k[1] * w + k[2] * n + k[3] * s + k[4] * c;
 }
 
-// GS species u: ku = {x, y, C}; returns J_u, J_v together.
+// GS species u: ku = {x, y, C}; returns J_u, J_v together, given the state
+// terms a1 = ga V^2, a2 = ga 2UV at the point.
+template <typename CJ>
+__device__ __forceinline__ void stencil_gs_a(const CJ (&k)[8], CJ ue, CJ uw, CJ un, CJ us, CJ uc, CJ ve, CJ vw,
+                                             CJ vn, CJ vs, CJ vc, CJ a1, CJ a2, CJ& ju, CJ& jv) {
+  ju = k[0] * (ue + uw) + k[1] * (un + us) + (k[2] - a1) * uc - a2 * vc;
+  jv = k[3] * (ve + vw) + k[4] * (vn + vs) + a1 * uc + (k[5] + a2) * vc;
+}
 template <typename CJ>
 __device__ __forceinline__ void stencil_gs(const CJ (&k)[8], CJ ga, CJ ue, CJ uw, CJ un, CJ us, CJ uc,
                                            CJ ve, CJ vw, CJ vn, CJ vs, CJ vc, CJ g1, CJ g2, CJ& ju,
                                            CJ& jv) {
-  CJ a1 = ga * g1;
-  CJ a2 = ga * g2;
-  ju = k[0] * (ue + uw) + k[1] * (un + us) + (k[2] - a1) * uc - a2 * vc;
-  jv = k[3] * (ve + vw) + k[4] * (vn + vs) + a1 * uc + (k[5] + a2) * vc;
+  stencil_gs_a<CJ>(k, ue, uw, un, us, uc, ve, vw, vn, vs, vc, ga * g1, ga * g2, ju, jv);
 }
 
 // double-float forms: the products of each row summed as unnormalised pairs
@@ -278,10 +282,8 @@ __device__ __forceinline__ df stencil_advdiff<df>(const df (&k)[8], df e, df w, 
 }
 
 template <>
-__device__ __forceinline__ void stencil_gs<df>(const df (&k)[8], df ga, df ue, df uw, df un, df us, df uc, df ve,
-                                               df vw, df vn, df vs, df vc, df g1, df g2, df& ju, df& jv) {
-  const df a1 = ga * g1;
-  const df a2 = ga * g2;
+__device__ __forceinline__ void stencil_gs_a<df>(const df (&k)[8], df ue, df uw, df un, df us, df uc, df ve, df vw,
+                                                 df vn, df vs, df vc, df a1, df a2, df& ju, df& jv) {
   float p[4], q[4];
   df_prod(k[0], ue + uw, p[0], q[0]);
   df_prod(k[1], un + us, p[1], q[1]);

@@ -72,6 +72,7 @@ __global__ void __launch_bounds__(THREADS) k_iter(IterDev a) {
 #pragma unroll
   for (int j = 0; j < 8; ++j) kk[j] = coef<CJ>(pp->kd[j], pp->kf[j]);
   const CJ ga = coef<CJ>(pp->gad, pp->gaf);
+  const bool prescaled = MODE == MODE_NEWTON && pp->prescaled;
   C beta{};
   C dk[KMAX];
   C alpha_pw{};
@@ -168,10 +169,13 @@ __global__ void __launch_bounds__(THREADS) k_iter(IterDev a) {
         C wv = (v == 0) ? we[NC - 1] : c[NC - 1][v - 1];
         CJ g1 = to_cj(cv(__ldg(st + row + ix + v)), CJ());
         CJ g2 = to_cj(cv(__ldg(st + plane + row + ix + v)), CJ());
-        stencil_gs<CJ>(kk, ga, to_cj(eu, CJ()), to_cj(wu, CJ()), to_cj(nn[0][v], CJ()),
-                       to_cj(ss[0][v], CJ()), to_cj(c[0][v], CJ()), to_cj(ev, CJ()),
-                       to_cj(wv, CJ()), to_cj(nn[NC - 1][v], CJ()), to_cj(ss[NC - 1][v], CJ()),
-                       to_cj(c[NC - 1][v], CJ()), g1, g2, J[0], J[NC - 1]);
+        if (!prescaled) {
+          g1 = ga * g1;
+          g2 = ga * g2;
+        }
+        stencil_gs_a<CJ>(kk, to_cj(eu, CJ()), to_cj(wu, CJ()), to_cj(nn[0][v], CJ()), to_cj(ss[0][v], CJ()),
+                         to_cj(c[0][v], CJ()), to_cj(ev, CJ()), to_cj(wv, CJ()), to_cj(nn[NC - 1][v], CJ()),
+                         to_cj(ss[NC - 1][v], CJ()), to_cj(c[NC - 1][v], CJ()), g1, g2, J[0], J[NC - 1]);
       } else {
         C e = (v == V - 1) ? ea[0] : c[0][v + 1];
         C w = (v == 0) ? we[0] : c[0][v - 1];
@@ -435,7 +439,8 @@ __global__ void __launch_bounds__(THREADS)
 // GS: st = [V^2, 2UV]; Burgers: st = [U]; computed in float64 then stored in S.
 template <int P>
 __global__ void __launch_bounds__(THREADS)
-    k_prep_state(int op, size_t plane, const double* __restrict__ state, typename Tr<P>::S* __restrict__ st) {
+    k_prep_state(int op, size_t plane, const double* __restrict__ state, typename Tr<P>::S* __restrict__ st,
+                 double scale) {
   using S = typename Tr<P>::S;
   const size_t stride = (size_t)gridDim.x * THREADS;
   for (size_t i = (size_t)blockIdx.x * THREADS + threadIdx.y * 32 + threadIdx.x; i < plane; i += stride) {
@@ -443,11 +448,11 @@ __global__ void __launch_bounds__(THREADS)
     int ng = 1;
     if (op == PHIX_OP_GRAYSCOTT) {
       double U = state[i], Vv = state[plane + i];
-      g[0] = Vv * Vv;
-      g[1] = 2.0 * U * Vv;
+      g[0] = scale * (Vv * Vv);
+      g[1] = scale * (2.0 * U * Vv);
       ng = 2;
     } else {
-      g[0] = state[i];
+      g[0] = scale * state[i];
     }
     for (int j = 0; j < ng; ++j) {
       S s;
@@ -475,7 +480,7 @@ static float2 split2(double x) {
 }
 
 void ptab_fill(void* host, int K, int m_min, int m_max, double tol, double rel, const double* k8,
-               double ga, const double* beta, const double* const* dk) {
+               double ga, const double* beta, const double* const* dk, int prescaled) {
   const int M = m_max + 1;
   unsigned char* b = static_cast<unsigned char*>(host);
   PassParams* pp = reinterpret_cast<PassParams*>(b);
@@ -492,6 +497,7 @@ void ptab_fill(void* host, int K, int m_min, int m_max, double tol, double rel, 
   }
   pp->gad = ga;
   pp->gaf = split2(ga);
+  pp->prescaled = prescaled;
   double* bd = reinterpret_cast<double*>(b + sizeof(PassParams));
   float2* bf = reinterpret_cast<float2*>(b + sizeof(PassParams) + 8 * (size_t)M);
   double* dd = reinterpret_cast<double*>(b + sizeof(PassParams) + 16 * (size_t)M);
@@ -690,21 +696,21 @@ cudaError_t launch_power_start(int prec, size_t n, uint64_t seed, void* y0, Leja
 }
 
 cudaError_t launch_prep_state(int prec, int op, int nx, int ny, const double* state, void* st,
-                              int grid, cudaStream_t s) {
+                              int grid, cudaStream_t s, double scale) {
   size_t plane = (size_t)nx * ny;
   dim3 b(32, TILE_Y);
   switch (prec) {
     case P_FP64:
-      k_prep_state<P_FP64><<<grid, b, 0, s>>>(op, plane, state, static_cast<double*>(st));
+      k_prep_state<P_FP64><<<grid, b, 0, s>>>(op, plane, state, static_cast<double*>(st), scale);
       break;
     case P_DF64:
-      k_prep_state<P_DF64><<<grid, b, 0, s>>>(op, plane, state, static_cast<float2*>(st));
+      k_prep_state<P_DF64><<<grid, b, 0, s>>>(op, plane, state, static_cast<float2*>(st), scale);
       break;
     case P_FP32JV:
-      k_prep_state<P_FP32JV><<<grid, b, 0, s>>>(op, plane, state, static_cast<float*>(st));
+      k_prep_state<P_FP32JV><<<grid, b, 0, s>>>(op, plane, state, static_cast<float*>(st), scale);
       break;
     case P_FP32:
-      k_prep_state<P_FP32><<<grid, b, 0, s>>>(op, plane, state, static_cast<float*>(st));
+      k_prep_state<P_FP32><<<grid, b, 0, s>>>(op, plane, state, static_cast<float*>(st), scale);
       break;
     default:
       return cudaErrorInvalidValue;

@@ -190,6 +190,7 @@ __global__ void __launch_bounds__(TT, CTAS_PER_SM) k_iter_tma(const __grid_const
 #pragma unroll
   for (int j = 0; j < 8; ++j) kk[j] = coef<CJ>(pp->kd[j], pp->kf[j]);
   const CJ ga = coef<CJ>(pp->gad, pp->gaf);
+  const bool prescaled = pp->prescaled != 0;
   const C beta = coef<C>(beta_d_of(a.ptab, M)[m], beta_f_of(a.ptab, M)[m]);
   C dk[KMAX];
 #pragma unroll
@@ -332,10 +333,14 @@ __global__ void __launch_bounds__(TT, CTAS_PER_SM) k_iter_tma(const __grid_const
         } else if constexpr (OP == PHIX_OP_GRAYSCOTT) {
           CJ g1 = to_cj(g1v[v], CJ());
           CJ g2 = to_cj(g2v[v], CJ());
-          stencil_gs<CJ>(kk, ga, to_cj(ee[0][v], CJ()), to_cj(ww[0][v], CJ()), to_cj(nn[0][v], CJ()),
-                         to_cj(so[0][v], CJ()), to_cj(cc[0][v], CJ()), to_cj(ee[NC - 1][v], CJ()),
-                         to_cj(ww[NC - 1][v], CJ()), to_cj(nn[NC - 1][v], CJ()), to_cj(so[NC - 1][v], CJ()),
-                         to_cj(cc[NC - 1][v], CJ()), g1, g2, J[0], J[NC - 1]);
+          if (!prescaled) {
+            g1 = ga * g1;
+            g2 = ga * g2;
+          }
+          stencil_gs_a<CJ>(kk, to_cj(ee[0][v], CJ()), to_cj(ww[0][v], CJ()), to_cj(nn[0][v], CJ()),
+                           to_cj(so[0][v], CJ()), to_cj(cc[0][v], CJ()), to_cj(ee[NC - 1][v], CJ()),
+                           to_cj(ww[NC - 1][v], CJ()), to_cj(nn[NC - 1][v], CJ()), to_cj(so[NC - 1][v], CJ()),
+                           to_cj(cc[NC - 1][v], CJ()), g1, g2, J[0], J[NC - 1]);
         } else {
           const S* srow = ss + (r + 1) * BWS + HXS + c2 + v;
           CJ Uc = to_cj(cv(srow[0]), CJ());

@@ -26,6 +26,7 @@ enum Slot {
   S_F, S_A, S_B, S_RA, S_RB, S_T0, S_Q, S_T3, S_T4, S_O1, S_O2, S_O3,  // stages
   S_SUB_U, S_SUB_TMP, S_SUB_W0,                                  // substeps (W0..W0+8)
   S_KBASIS = S_SUB_W0 + 9, S_KB, S_KPTR, S_KCTL, S_KMODE,                       // KIOPS basis, b copies, slot table, control
+  S_ST2,                                                         // Gray-Scott state planes scaled for Newton passes
   S_BPROB, S_BORDER, S_BWS, S_BQ, S_XI,                          // batched problems, order, arena, queue, Leja points
   S_MFEAT, S_MY, S_MG, S_MCNT,                                   // learned interval: features, outputs, gradient
   S_NSLOT
@@ -71,6 +72,10 @@ struct phix_ctx {
   // sets ran_out, and the call is run again once with full tables
   bool full_tables = false;
   bool ran_out = false;
+  // state planes scaled by the Newton factor: valid for one preparation of the
+  // planes (prep_gen) and one factor
+  unsigned long prep_gen = 0, st2_gen = ~0ul;
+  double st2_alpha = 0.0;
   std::list<DDTable> dd_cache;   // recent tables (pure functions of l, a, b); references stay valid
   struct Graph {
     ChainSpec spec;
@@ -212,6 +217,7 @@ OpState make_opstate(phix_ctx* ctx, const phix_jop* op, const double* state, int
     void* st = ws(ctx, S_ST, nplanes * s.plane * sb);
     KL(launch_prep_state(prec, op->kind, op->nx, op->ny, state, st, ctx->grid_stream, ctx->stream));
     s.st = st;
+    ++ctx->prep_gen;
   }
   return s;
 }
@@ -286,11 +292,11 @@ int acquire_slot(phix_ctx* ctx, size_t ptab_need) {
 
 // Fill slot s's parameter block and queue its upload.
 const void* upload_ptab(phix_ctx* ctx, int s, int K, int m_min, int m_max, double tol, double rel, const double* k8,
-                        double ga, const double* beta, const double* const* dk) {
+                        double ga, const double* beta, const double* const* dk, int prescaled = 0) {
   const size_t bytes = ptab_bytes(m_max + 1);
   unsigned char* h = ctx->ptab_h + (size_t)s * ctx->ptab_slot;
   unsigned char* d = ctx->ptab_d + (size_t)s * ctx->ptab_slot;
-  ptab_fill(h, K, m_min, m_max, tol, rel, k8, ga, beta, dk);
+  ptab_fill(h, K, m_min, m_max, tol, rel, k8, ga, beta, dk, prescaled);
   CK(cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, ctx->stream));
   return d;
 }
@@ -380,7 +386,8 @@ void queue_chain(phix_ctx* ctx, int s, const ChainSpec& spec, bool profile, bool
 // next flush.
 void leja_pass(phix_ctx* ctx, const OpState& os, int prec, const double* v, int K,
                const std::vector<const std::vector<double>*>& d, double c, double gamma, double tol,
-               const phix_opts& o, double* const* out, phix_stats& stats) {
+               const phix_opts& o, double* const* out, phix_stats& stats, const void* st_newton,
+               int prescaled) {
   const int M = (int)d[0]->size();  // table length: at most o.m_max + 1
   const int m_max = M - 1;
   const double* xi = leja_table(M);
@@ -399,7 +406,7 @@ void leja_pass(phix_ctx* ctx, const OpState& os, int prec, const double* v, int 
   for (int m = 1; m < M; ++m) beta[m] = -(c / gamma + xi[m - 1]);
   const double* dk[KMAX] = {};
   for (int k = 0; k < K; ++k) dk[k] = d[k]->data();
-  const void* ptab = upload_ptab(ctx, s, K, o.m_min, m_max, tol, 0.0, k8, alpha, beta.data(), dk);
+  const void* ptab = upload_ptab(ctx, s, K, o.m_min, m_max, tol, 0.0, k8, alpha, beta.data(), dk, prescaled);
 
   KL(launch_scale(v, os.N, ctl, ctx->partials, ctx->grid_iter, ctx->stream));
   InitLaunch IL{};
@@ -425,7 +432,7 @@ void leja_pass(phix_ctx* ctx, const OpState& os, int prec, const double* v, int 
   cs.y[0] = y[0];
   cs.y[1] = y[1];
   for (int k = 0; k < K; ++k) cs.p[k] = p[k];
-  cs.st = os.st;
+  cs.st = st_newton;
   cs.ctl = ctl;
   cs.partials = ctx->partials;
   cs.ptab = ptab;
@@ -603,6 +610,23 @@ void leja_phi(phix_ctx* ctx, const OpState& os, int prec, double h, const double
     for (int k = 0; k < nout; ++k) lincomb(ctx, os.N, {1.0 / factorial(l[k])}, {v}, out[k]);
     return;
   }
+  // Gray-Scott: the Newton passes read the state terms V^2, 2UV already
+  // multiplied by the factor 1/gamma their stencil applies (one preparation
+  // per state and factor, shared by every pass of the call)
+  const void* st_n = os.st;
+  int pre = 0;
+  if (os.d.kind == PHIX_OP_GRAYSCOTT) {
+    const double alpha = 1.0 / ivc.gamma;
+    const size_t sb = prec == P_FP64 || prec == P_DF64 ? 8 : 4;
+    void* st2 = ws(ctx, S_ST2, 2 * os.plane * sb);
+    if (ctx->st2_gen != ctx->prep_gen || ctx->st2_alpha != alpha) {
+      KL(launch_prep_state(prec, os.d.kind, os.d.nx, os.d.ny, os.state, st2, ctx->grid_stream, ctx->stream, alpha));
+      ctx->st2_gen = ctx->prep_gen;
+      ctx->st2_alpha = alpha;
+    }
+    st_n = st2;
+    pre = 1;
+  }
   int smax = 1;
   std::vector<int> subs(nout);
   for (int k = 0; k < nout; ++k) {
@@ -618,7 +642,7 @@ void leja_phi(phix_ctx* ctx, const OpState& os, int prec, double h, const double
     const std::vector<std::vector<double>> d = pass_tables(ctx, nout, l, ta, tb, tol, o);
     std::vector<const std::vector<double>*> dp(nout);
     for (int k = 0; k < nout; ++k) dp[k] = &d[k];
-    leja_pass(ctx, os, prec, v, nout, dp, ivc.c, ivc.gamma, tol, o, out, stats);
+    leja_pass(ctx, os, prec, v, nout, dp, ivc.c, ivc.gamma, tol, o, out, stats, st_n, pre);
     stats.passes += 1;
     stats.substeps += 1;
     return;
@@ -650,7 +674,7 @@ void leja_phi(phix_ctx* ctx, const OpState& os, int prec, double h, const double
         stats.jv += 1;
       }
       double* outs[1] = {tmp};
-      leja_pass(ctx, os, prec, w[L], 1, dp, ivc.c, ivc.gamma, tol, o, outs, stats);
+      leja_pass(ctx, os, prec, w[L], 1, dp, ivc.c, ivc.gamma, tol, o, outs, stats, st_n, pre);
       stats.passes += 1;
       std::vector<double> cc;
       std::vector<const double*> xx;

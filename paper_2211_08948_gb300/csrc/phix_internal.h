@@ -56,6 +56,7 @@ struct LejaCtl {
 // -(c/gamma + xi_{m-1}) shifts the centre value.
 struct PassParams {
   int K, m_min, m_max, M;
+  int prescaled, pad;  // 1: the state planes already carry the factor ga (Gray-Scott Newton passes)
   double tol, rel;
   double kd[8], gad;
   float2 kf[8], gaf;
@@ -63,7 +64,7 @@ struct PassParams {
 size_t ptab_bytes(int M);
 // Fill a host copy of a parameter block.  beta and dk may be NULL (power iteration).
 void ptab_fill(void* host, int K, int m_min, int m_max, double tol, double rel, const double* k8,
-               double ga, const double* beta, const double* const* dk);
+               double ga, const double* beta, const double* const* dk, int prescaled = 0);
 
 // ---- launchers (leja_kernels.cu) -----------------------------------------
 struct ChainSpec {
@@ -128,7 +129,7 @@ cudaError_t launch_power_start(int prec, size_t n, uint64_t seed, void* y0, Leja
 // Per-point state arrays of the Jacobian in the precision's format:
 // GRAYSCOTT: st = [V^2 plane, 2UV plane]; BURGERS: st = [U plane].
 cudaError_t launch_prep_state(int prec, int op, int nx, int ny, const double* state, void* st,
-                              int grid, cudaStream_t s);
+                              int grid, cudaStream_t s, double scale = 1.0);
 
 // ---- KIOPS-style Krylov kernels (kiops_kernels.cu) -----------------------
 constexpr int KIOPS_MMAX = 128;  // largest Krylov dimension
