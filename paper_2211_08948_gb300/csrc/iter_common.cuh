@@ -161,8 +161,21 @@ __device__ __forceinline__ float acc_zero<float>() { return 0.f; }
 template <>
 __device__ __forceinline__ df acc_zero<df>() { return df_make(0.f, 0.f); }
 
-// Block reduction of NV accumulators; the block's sums go to partials[blockIdx.x*(KMAX+1) + j]
-// as float64.  Returns true in the block that finished last (all partials visible).
+// Deterministic two-level reduction of NV accumulators: each block reduces its
+// values (warp shuffles, warps in order) into partials[blockIdx.x * (KMAX+1) + j];
+// the block that finishes last sums the partials in a fixed order.  GB300
+// issues float64 at 1/64 of the float32 rate (a warp-wide float64 add holds the
+// pipe ~64 cycles), so float and double-float accumulators keep their partials
+// and the final tree in double-float (float2 bits in the double slots); float64
+// accumulators keep float64 throughout.
+template <typename A>
+struct PartialsDF {
+  static constexpr bool value = !std::is_same<A, double>::value;
+};
+__device__ __forceinline__ df acc_to_df(float a) { return df_make(a, 0.f); }
+__device__ __forceinline__ df acc_to_df(df a) { return a; }
+
+// true in the block that arrived last (all partials visible)
 template <typename A, int NV>
 __device__ bool block_partials_and_last(A (&acc)[NV], double* partials, unsigned int* count) {
   __shared__ double sred[THREADS / 32][KMAX + 1];
@@ -174,13 +187,26 @@ __device__ bool block_partials_and_last(A (&acc)[NV], double* partials, unsigned
     A v = acc[j];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = acc_add(v, shfl_down(v, o));
-    if (lane == 0) sred[warp][j] = acc_to_double(v);
+    if (lane == 0) {
+      if constexpr (PartialsDF<A>::value) {
+        const df d = acc_to_df(v);
+        reinterpret_cast<float2*>(&sred[warp][j])[0] = make_float2(d.hi, d.lo);
+      } else {
+        sred[warp][j] = v;
+      }
+    }
   }
   __syncthreads();
   if (tid < NV) {
-    double s = 0.0;
-    for (int w = 0; w < THREADS / 32; ++w) s += sred[w][tid];
-    partials[(size_t)blockIdx.x * (KMAX + 1) + tid] = s;
+    if constexpr (PartialsDF<A>::value) {
+      df s = df_make(0.f, 0.f);
+      for (int w = 0; w < THREADS / 32; ++w) s = df_add(s, cv(reinterpret_cast<const float2*>(&sred[w][tid])[0]));
+      reinterpret_cast<float2*>(partials + (size_t)blockIdx.x * (KMAX + 1) + tid)[0] = make_float2(s.hi, s.lo);
+    } else {
+      double s = 0.0;
+      for (int w = 0; w < THREADS / 32; ++w) s += sred[w][tid];
+      partials[(size_t)blockIdx.x * (KMAX + 1) + tid] = s;
+    }
   }
   __threadfence();
   __syncthreads();
@@ -192,45 +218,77 @@ __device__ bool block_partials_and_last(A (&acc)[NV], double* partials, unsigned
   return last;
 }
 
-// Last block: totals[j] = sum over blocks of partials (fixed order).
-template <int NV>
+// Last block: totals[j] = sum over blocks of the partials (fixed order: strided
+// per thread, then a halving tree).  The totals are valid in thread 0 only.
+template <typename A, int NV>
 __device__ void reduce_partials(const double* partials, double (&tot)[NV]) {
-  __shared__ double sfin[THREADS][KMAX + 1];
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-  double s[NV];
+  if constexpr (PartialsDF<A>::value) {
+    __shared__ float2 sfin[THREADS][KMAX + 1];
+    df s[NV];
 #pragma unroll
-  for (int j = 0; j < NV; ++j) s[j] = 0.0;
-  for (int b = tid; b < (int)gridDim.x; b += THREADS) {
+    for (int j = 0; j < NV; ++j) s[j] = df_make(0.f, 0.f);
+    for (int b = tid; b < (int)gridDim.x; b += THREADS) {
 #pragma unroll
-    for (int j = 0; j < NV; ++j) s[j] += __ldcg(partials + (size_t)b * (KMAX + 1) + j);
-  }
-#pragma unroll
-  for (int j = 0; j < NV; ++j) sfin[tid][j] = s[j];
-  __syncthreads();
-  for (int w = THREADS / 2; w > 0; w >>= 1) {
-    if (tid < w) {
-#pragma unroll
-      for (int j = 0; j < NV; ++j) sfin[tid][j] += sfin[tid + w][j];
+      for (int j = 0; j < NV; ++j)
+        s[j] = df_add(s[j], cv(__ldcg(reinterpret_cast<const float2*>(partials + (size_t)b * (KMAX + 1) + j))));
     }
-    __syncthreads();
-  }
 #pragma unroll
-  for (int j = 0; j < NV; ++j) tot[j] = sfin[0][j];
+    for (int j = 0; j < NV; ++j) sfin[tid][j] = make_float2(s[j].hi, s[j].lo);
+    __syncthreads();
+    for (int w = THREADS / 2; w > 0; w >>= 1) {
+      if (tid < w) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+          const df t = df_add(cv(sfin[tid][j]), cv(sfin[tid + w][j]));
+          sfin[tid][j] = make_float2(t.hi, t.lo);
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < NV; ++j) tot[j] = tid == 0 ? (double)sfin[0][j].x + (double)sfin[0][j].y : 0.0;
+  } else {
+    __shared__ double sfin[THREADS][KMAX + 1];
+    double s[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) s[j] = 0.0;
+    for (int b = tid; b < (int)gridDim.x; b += THREADS) {
+#pragma unroll
+      for (int j = 0; j < NV; ++j) s[j] += __ldcg(partials + (size_t)b * (KMAX + 1) + j);
+    }
+#pragma unroll
+    for (int j = 0; j < NV; ++j) sfin[tid][j] = s[j];
+    __syncthreads();
+    for (int w = THREADS / 2; w > 0; w >>= 1) {
+      if (tid < w) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) sfin[tid][j] += sfin[tid + w][j];
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < NV; ++j) tot[j] = sfin[0][j];
+  }
 }
 
-// Stop test of the Newton-Leja chain at iteration m (Sec. 2.2).
+// Stop test of the Newton-Leja chain at iteration m (Sec. 2.2):
+// |d_k[m]| ||y_m|| <= tol ||p_m^(k)|| for every k, compared as squares (no
+// square root on the critical path between launches); tot holds the squared
+// norms.
 __device__ inline void leja_test(LejaCtl* ctl, int m, int K, int m_min, int m_max, double tol,
                           const double* dkd, const double* tot) {
-  double ny = sqrt(tot[0]);
-  bool finite = isfinite(ny);
+  const double ny2 = tot[0];
+  bool finite = isfinite(ny2);
   bool conv = (m >= m_min);
+  const double tol2 = tol * tol;
   for (int k = 0; k < K; ++k) {
-    double np = sqrt(tot[1 + k]);
-    ctl->pnorm[k] = np;
-    finite = finite && isfinite(np);
-    conv = conv && (fabs(dkd[k]) * ny <= tol * np);
+    const double np2 = tot[1 + k];
+    ctl->psq[k] = np2;
+    finite = finite && isfinite(np2);
+    conv = conv && (dkd[k] * dkd[k] * ny2 <= tol2 * np2);
   }
-  ctl->ynorm = ny;
+  ctl->ysq = ny2;
   if (!finite) {
     ctl->status = PHIX_ENAN;
     ctl->iters = m;

@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(THREADS) k_arn1(ArnArgs a) {
 
   if (block_partials_and_last<Acc, 3>(acc, a.partials, &kc->count)) {
     double tot[3];
-    reduce_partials<3>(a.partials, tot);
+    reduce_partials<Acc, 3>(a.partials, tot);
     if (threadIdx.x == 0 && threadIdx.y == 0) {
       const int j = a.j, p = a.p;
       const double sj = kc->s[j];
@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(THREADS) k_arn2(ArnArgs a, size_t n) {
   }
   if (block_partials_and_last<Acc, 1>(acc, a.partials, &kc->count)) {
     double tot[1];
-    reduce_partials<1>(a.partials, tot);
+    reduce_partials<Acc, 1>(a.partials, tot);
     if (threadIdx.x == 0 && threadIdx.y == 0) {
       const int j = a.j, p = a.p;
       double* tz = kc->tail + (j + 1) * KIOPS_PMAX;
@@ -774,7 +774,7 @@ __global__ void __launch_bounds__(THREADS) k_kcomb(CombArgs a, size_t N) {
   }
   if (block_partials_and_last<Acc, 1>(acc, a.partials, &kc->count)) {
     double tot[1];
-    reduce_partials<1>(a.partials, tot);
+    reduce_partials<Acc, 1>(a.partials, tot);
     if (tid == 0) {
       double tw[KIOPS_PMAX];
       double nz = tot[0];
@@ -821,7 +821,7 @@ __global__ void __launch_bounds__(THREADS)
   }
   if (block_partials_and_last<Acc, 1>(acc, a.partials, &kc->count)) {
     double tot[1];
-    reduce_partials<1>(a.partials, tot);
+    reduce_partials<Acc, 1>(a.partials, tot);
     if (tid == 0) {
       kc->eta = eta;
       for (int t = 0; t < KIOPS_PMAX; ++t) kc->tail[t] = 0.0;
@@ -863,7 +863,7 @@ __global__ void __launch_bounds__(THREADS)
   }
   if (block_partials_and_last<double, 1>(acc, partials, counter)) {
     double tot[1];
-    reduce_partials<1>(partials, tot);
+    reduce_partials<double, 1>(partials, tot);
     if (threadIdx.x == 0 && threadIdx.y == 0) {
       *norm1 = tot[0];
       *counter = 0;

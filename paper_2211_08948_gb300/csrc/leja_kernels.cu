@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(THREADS) k_iter(IterDev a) {
 
   if (block_partials_and_last<Acc, KMAX + 1>(acc, a.partials, &a.ctl->count)) {
     double tot[KMAX + 1];
-    reduce_partials<KMAX + 1>(a.partials, tot);
+    reduce_partials<Acc, KMAX + 1>(a.partials, tot);
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     if (tid == 0) {
       LejaCtl* ctl = a.ctl;
@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(THREADS)
   }
   if (block_partials_and_last<Acc, KMAX + 1>(acc, a.partials, &a.ctl->count)) {
     double tot[KMAX + 1];
-    reduce_partials<KMAX + 1>(a.partials, tot);
+    reduce_partials<Acc, KMAX + 1>(a.partials, tot);
     if (threadIdx.x == 0 && threadIdx.y == 0) {
       double dkd[KMAX];
       for (int k = 0; k < K; ++k) dkd[k] = dk_d_of(a.ptab, M)[k * M];
@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(THREADS)
   }
   if (block_partials_and_last<double, 1>(acc, partials, &ctl->count)) {
     double tot[1];
-    reduce_partials<1>(partials, tot);
+    reduce_partials<double, 1>(partials, tot);
     if (threadIdx.x == 0 && threadIdx.y == 0) {
       double s = tot[0];
       double sig = 1.0;
@@ -421,7 +421,7 @@ __global__ void __launch_bounds__(THREADS)
   }
   if (block_partials_and_last<Acc, 1>(acc, partials, &ctl->count)) {
     double tot[1];
-    reduce_partials<1>(partials, tot);
+    reduce_partials<Acc, 1>(partials, tot);
     if (threadIdx.x == 0 && threadIdx.y == 0) {
       double al = 1.0 / sqrt(tot[0]);
       ctl->alpha = al;

@@ -31,8 +31,8 @@ struct LejaCtl {
   int status;          // phix_status
   int m;               // index of the next iteration of the chain (advanced by the last block)
   int pad;
-  double ynorm;        // ||y_m|| (scaled units) of the last completed launch
-  double pnorm[KMAX];  // ||p_m^(k)||
+  double ysq;          // ||y_m||^2 (scaled units) of the last completed launch
+  double psq[KMAX];    // ||p_m^(k)||^2
   double sigma;        // input scale, a power of two
   double inv_sigma;
   double rho;          // power iteration: ||J v_k||
