@@ -112,3 +112,10 @@ def test_rhs_vs_oracle(px, kind):
     fd = torch.empty_like(ud)
     phix.phix_rhs(ctx, phix.make_jop(kd, nx, ny, prm), ud, fd)
     assert rel(host(fd), oop.f(u)) <= 1e-13
+
+
+def test_entry_smoke_runs(px):
+    """The package's smoke entry (one phi-action and one EXPRB43 step, each
+    against the oracle) completes on cuda:0."""
+    import __graft_entry__
+    __graft_entry__.smoke()
