@@ -305,17 +305,22 @@ __global__ void __launch_bounds__(THREADS) k_arn2(ArnArgs a, size_t n) {
 // parts of the field of values W(X), X = tau Hbar, i.e. the extreme
 // eigenvalues of the symmetric part (X + X^T)/2 (Bendixson):
 //   e^{c + r t} = e^{c + r} (I~_0(r) + 2 sum_k I~_k(r) T_k(t)),  I~_k = e^{-r} I_k,
-// applied with the three-term recurrence to Y = (X - c I)/r.  The extreme
+// applied with the three-term recurrence to Y = (X - c I)/r, in S segments
+// exp(X) e_1 = exp(X/S)^S e_1 (the expansion at r/S, applied S times): one
+// segment at r ~ 100 needs terms whose size 2 I~_k rho^k reaches 2^16 and
+// amplifies rounding as much; S segments of r/S keep it below 100 at about
+// 1.5x the terms of one, against ~15 r terms for the Taylor series.  The extreme
 // eigenvalues come from Sturm-sequence multisection (float32 counts, then a
 // 1e-5 relative safety margin); the imaginary extent iota is the spectral
 // radius of the skew part (same routine on |skew| entries).  The scaled
 // modified Bessel values come from Miller's backward recurrence normalised by
 // I~_0 + 2 sum_k I~_k = 1; the term count makes 2 I~_k rho^k <= 1e-16, rho the
 // Bernstein-ellipse parameter holding the box [lo, hi] x [-iota, iota].  With
-// Crouzeix's bound the error is ~1e-16 e^{hi} >= 1e-16 ||exp(X)||, normwise
-// like a dense expm.  Fallback (iota > r/2, no admissible term count, or
-// rounding amplification above 100): Taylor series in segments of norm <= 4
-// after the shift by the interval midpoint.
+// Crouzeix's bound the error of a segment is ~1e-16 of its input times
+// e^{hi/S} >= ||exp(X/S)||, so ~S 1e-16 e^{hi} >= S 1e-16 ||exp(X)|| in all,
+// normwise like a dense expm.  Fallback (iota > r/2, no admissible term count
+// within 64 segments, or more serial terms than the Taylor series): Taylor
+// series in segments of norm <= 4 after the shift by the interval midpoint.
 //
 // GB300 issues float64 at 1/64 of the float32 rate, so a serial float64 chain
 // costs ~70 cycles per operation: the recurrences (Bessel values, Chebyshev
@@ -323,27 +328,27 @@ __global__ void __launch_bounds__(THREADS) k_arn2(ArnArgs a, size_t n) {
 // tolerances the result serves) and every loop over rows or terms is spread
 // over the block.
 constexpr int CHEB_MAX = 600;
+constexpr int SEG_MAX = 64;  // Chebyshev segments
 constexpr int SX = 128;  // threads
 
 __device__ __forceinline__ df dfd(double v) { return df_from_double(v); }
 __device__ __forceinline__ double dd(df v) { return (double)v.hi + (double)v.lo; }
 
-// block reductions over SX threads (sh: 4 doubles of scratch, reused after a barrier)
-__device__ double blk_min(double v, double* sh, int tid) {
-  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
-  if ((tid & 31) == 0) sh[tid >> 5] = v;
-  __syncthreads();
-  const double r = fmin(fmin(sh[0], sh[1]), fmin(sh[2], sh[3]));
-  __syncthreads();
-  return r;
-}
-__device__ double blk_max(double v, double* sh, int tid) { return -blk_min(-v, sh, tid); }
+// block reductions over SX threads (sh: 4 entries of scratch, reused after a barrier)
 __device__ df blk_dfsum(df v, df* sh, int tid) {
   for (int o = 16; o > 0; o >>= 1)
     v = df_add(v, df_make(__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)));
   if ((tid & 31) == 0) sh[tid >> 5] = v;
   __syncthreads();
   const df r = df_add(df_add(sh[0], sh[1]), df_add(sh[2], sh[3]));
+  __syncthreads();
+  return r;
+}
+__device__ float blk_maxf(float v, float* sh, int tid) {
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_down_sync(0xffffffffu, v, o));
+  if ((tid & 31) == 0) sh[tid >> 5] = v;
+  __syncthreads();
+  const float r = fmaxf(fmaxf(sh[0], sh[1]), fmaxf(sh[2], sh[3]));
   __syncthreads();
   return r;
 }
@@ -356,317 +361,405 @@ __device__ int blk_imin(int v, int* sh, int tid) {
   return r;
 }
 
-// number of eigenvalues < x of the symmetric tridiagonal (diag a, squared off-diagonal b2)
+// number of eigenvalues < x of the symmetric tridiagonal (diag a, squared off-diagonal b2);
+// the division is the fast reciprocal form (the bounds carry a 1e-5 relative margin)
 __device__ int sturm_count(int n, const float* a, const float* b2, float x) {
   int cnt = 0;
   float q = a[0] - x;
   cnt += q < 0.f;
   for (int i = 1; i < n; ++i) {
     if (q == 0.f) q = 1e-30f;
-    q = (a[i] - x) - b2[i - 1] / q;
+    q = (a[i] - x) - __fdividef(b2[i - 1], q);
     cnt += q < 0.f;
   }
   return cnt;
 }
 
 struct SmallExpWork {
-  double x[KIOPS_MMAX + 2];  // result (float64)
-  df xv[KIOPS_MMAX + 2], t0[KIOPS_MMAX + 2], t1[KIOPS_MMAX + 2], t2[KIOPS_MMAX + 2];
-  df ca[KIOPS_MMAX + 2], cu[KIOPS_MMAX + 2], cl[KIOPS_MMAX + 2];  // scaled matrix of the recurrence
+  double x[KIOPS_MMAX + 2];           // result (float64)
+  float2 nb[2][KIOPS_MMAX + 4];       // recurrence rows for the neighbours (ping-pong; row i at i + 1,
+                                      // zero pads at 0 and n + 1)
   df bes[CHEB_MAX + 2];
   df invk[32];
   float fa[KIOPS_MMAX + 2], fs2[KIOPS_MMAX + 2], fk2[KIOPS_MMAX + 2], fz[KIOPS_MMAX + 2];
   int cnt[SX];
-  double br[4];
-  double sh[4];
+  float pts[SX];
+  float br[4];
+  float shf[4];
   df shd[4];
   int shi[4];
   int mode, S, K;
-  double shift, c, r, lead, glo, ghi, kb, rho, l2rho;
+  double lead;
 };
 
-// Sturm multisection of [lo, hi] with `np` points per round on threads
-// [t0, t0 + np), `rounds` rounds; returns the outer bound of the largest
-// (want_max) or smallest eigenvalue.  All SX threads call it (barriers).
-// (Used for the imaginary extent; the two real bounds share their rounds.)
-__device__ double multisect(int n, const float* a, const float* b2, double lo, double hi, bool want_max, int t0,
-                            int np, int rounds, SmallExpWork& w, int slot, int tid) {
-  for (int round = 0; round < rounds; ++round) {
-    const bool mine = tid >= t0 && tid < t0 + np;
-    if (mine) {
-      const int t = tid - t0;
-      const double x = lo + (hi - lo) * (double)(t + 1) / (double)(np + 1);
-      w.cnt[tid] = sturm_count(n, a, b2, (float)x);
-    }
-    __syncthreads();
-    if (tid == t0) {
-      double nlo = lo, nhi = hi;
-      const double step = (hi - lo) / (double)(np + 1);
-      if (want_max) {  // smallest point with all eigenvalues below it
-        int t = 0;
-        while (t < np && w.cnt[t0 + t] < n) ++t;
-        nhi = (t < np) ? lo + step * (t + 1) : hi;
-        nlo = (t > 0) ? lo + step * t : lo;
-      } else {  // largest point with no eigenvalue below it
-        int t = np - 1;
-        while (t >= 0 && w.cnt[t0 + t] > 0) --t;
-        nlo = (t >= 0) ? lo + step * (t + 1) : lo;
-        nhi = (t < np - 1) ? lo + step * (t + 2) : hi;
-      }
-      w.br[2 * slot] = nlo;
-      w.br[2 * slot + 1] = nhi;
-    }
-    __syncthreads();
-    lo = w.br[2 * slot];
-    hi = w.br[2 * slot + 1];
-    __syncthreads();
+// One round of Sturm multisection of the brackets [lo[g], hi[g]] (g = 0: the
+// largest eigenvalue, threads 0..np-1; g = 1: the smallest, threads np..2np-1;
+// ng groups): each thread counts at one of np interior points, the first
+// thread of each group narrows its bracket to one cell.  All SX threads call
+// it (barriers).  The points are kept in shared memory so the bracket update
+// uses exactly the values that were counted.
+__device__ void msect_round(int n, const float* a, const float* b2, float (&lo)[2], float (&hi)[2], int ng,
+                            int np, SmallExpWork& w, int tid) {
+  const int g = tid / np, t = tid - g * np;
+  if (g < ng) {
+    const float x = __fmaf_rn(hi[g] - lo[g], (float)(t + 1) / (float)(np + 1), lo[g]);
+    w.pts[tid] = x;
+    w.cnt[tid] = sturm_count(n, a, b2, x);
   }
-  const double margin = 1e-5 * (fabs(lo) + fabs(hi)) + 1e-300;
-  return want_max ? hi + margin : lo - margin;
+  __syncthreads();
+  if (g < ng && t == 0) {
+    const int o = g * np;
+    float nlo = lo[g], nhi = hi[g];
+    if (g == 0) {  // smallest point with all eigenvalues below it
+      int s = 0;
+      while (s < np && w.cnt[o + s] < n) ++s;
+      nhi = (s < np) ? w.pts[o + s] : hi[g];
+      nlo = (s > 0) ? w.pts[o + s - 1] : lo[g];
+    } else {  // largest point with no eigenvalue below it
+      int s = np - 1;
+      while (s >= 0 && w.cnt[o + s] > 0) --s;
+      nlo = (s >= 0) ? w.pts[o + s] : lo[g];
+      nhi = (s < np - 1) ? w.pts[o + s + 1] : hi[g];
+    }
+    w.br[2 * g] = nlo;
+    w.br[2 * g + 1] = nhi;
+  }
+  __syncthreads();
+  for (int q = 0; q < ng; ++q) {
+    lo[q] = w.br[2 * q];
+    hi[q] = w.br[2 * q + 1];
+  }
+  __syncthreads();
 }
 
-// The largest (threads 0..63) and the smallest (threads 64..127) eigenvalue
-// of the symmetric tridiagonal at once: 4 rounds of 64-point multisection
-// each; outer bounds with the 1e-5 relative margin.
-__device__ void multisect2(int n, const float* a, const float* b2, double glo, double ghi, SmallExpWork& w,
-                           int tid, double& lam_hi, double& lam_lo) {
-  double lo[2] = {glo, glo}, hi[2] = {ghi, ghi};
-  const int g = tid >> 6, t = tid & 63;  // group 0: largest, group 1: smallest
-  for (int round = 0; round < 4; ++round) {
-    const double x = lo[g] + (hi[g] - lo[g]) * (double)(t + 1) / 65.0;
-    w.cnt[tid] = sturm_count(n, a, b2, (float)x);
+// Chebyshev segments: x <- I~_0 x + 2 sum_{k=1}^{K-1} I~_k T_k(Y) x, S times,
+// with M = 2Y in (ma, mu, ml); x renormalised by a power of two before every
+// segment but the first (lead collects the exponents).  R rows per thread.
+template <int R>
+__device__ void cheb_segments(int n, int S, int K, const df (&ma)[R], const df (&mu)[R], const df (&ml)[R],
+                              df (&xr)[R], double& lead, SmallExpWork& w, int tid) {
+  const df b0 = w.bes[0], b1 = df_scale2(w.bes[1], 2.f);
+  for (int seg = 0; seg < S; ++seg) {
+    if (seg > 0) {
+      float mx = 0.f;
+#pragma unroll
+      for (int q = 0; q < R; ++q) mx = fmaxf(mx, fabsf(xr[q].hi));
+      mx = blk_maxf(mx, w.shf, tid);
+      int e = 0;
+      if (mx > 0.f) (void)frexpf(mx, &e);
+      const float f = ldexpf(1.f, -e);
+#pragma unroll
+      for (int q = 0; q < R; ++q) xr[q] = df_scale2(xr[q], f);
+      lead += e * 0.69314718055994530942;
+    }
+    df tm[R], tc[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const int i = tid + q * SX;
+      if (i < n) w.nb[0][i + 1] = make_float2(xr[q].hi, xr[q].lo);
+    }
     __syncthreads();
-    if (t == 0) {
-      const double step = (hi[g] - lo[g]) / 65.0;
-      double nlo = lo[g], nhi = hi[g];
-      if (g == 0) {  // smallest point with all eigenvalues below it
-        int s = 0;
-        while (s < 64 && w.cnt[s] < n) ++s;
-        nhi = (s < 64) ? lo[g] + step * (s + 1) : hi[g];
-        nlo = (s > 0) ? lo[g] + step * s : lo[g];
-      } else {  // largest point with no eigenvalue below it
-        int s = 63;
-        while (s >= 0 && w.cnt[64 + s] > 0) --s;
-        nlo = (s >= 0) ? lo[g] + step * (s + 1) : lo[g];
-        nhi = (s < 63) ? lo[g] + step * (s + 2) : hi[g];
+    // T_1 = Y x (half the row of M); x <- I~_0 x + 2 I~_1 T_1
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const int i = tid + q * SX;
+      tm[q] = xr[q];
+      tc[q] = df_make(0.f, 0.f);
+      if (i < n) {
+        float p[3], e[3];
+        df_prod(ma[q], xr[q], p[0], e[0]);
+        df_prod(mu[q], cv(w.nb[0][i + 2]), p[1], e[1]);
+        df_prod(ml[q], cv(w.nb[0][i]), p[2], e[2]);
+        const df v = df_scale2(df_sum_pairs<3>(p, e), 0.5f);
+        w.nb[1][i + 1] = make_float2(v.hi, v.lo);
+        xr[q] = df_fma(b1, v, df_mul(b0, xr[q]));
+        tc[q] = v;
       }
-      w.br[2 * g] = nlo;
-      w.br[2 * g + 1] = nhi;
     }
     __syncthreads();
-    for (int q = 0; q < 2; ++q) {
-      lo[q] = w.br[2 * q];
-      hi[q] = w.br[2 * q + 1];
+    // T_k = M T_{k-1} - T_{k-2}; term k reads nb[(k - 1) & 1], writes nb[k & 1]
+    df bk = df_scale2(w.bes[2], 2.f);
+    for (int k = 2; k < K; ++k) {
+      const float2* src = w.nb[(k - 1) & 1];
+      float2* dst = w.nb[k & 1];
+      const df bnext = df_scale2(w.bes[k + 1], 2.f);
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        const int i = tid + q * SX;
+        if (i < n) {
+          float p[4], e[4];
+          df_prod(ma[q], tc[q], p[0], e[0]);
+          df_prod(mu[q], cv(src[i + 2]), p[1], e[1]);
+          df_prod(ml[q], cv(src[i]), p[2], e[2]);
+          p[3] = -tm[q].hi;
+          e[3] = -tm[q].lo;
+          const df v = df_sum_pairs<4>(p, e);
+          dst[i + 1] = make_float2(v.hi, v.lo);
+          xr[q] = df_fma(bk, v, xr[q]);
+          tm[q] = tc[q];
+          tc[q] = v;
+        }
+      }
+      bk = bnext;
+      __syncthreads();
     }
-    __syncthreads();
   }
-  lam_hi = hi[0] + (1e-5 * (fabs(lo[0]) + fabs(hi[0])) + 1e-300);
-  lam_lo = lo[1] - (1e-5 * (fabs(lo[1]) + fabs(hi[1])) + 1e-300);
+}
+
+// Taylor segments: x <- sum_{k=0}^{30} M^k x / k!, S times, M = (T - cI)/S in
+// (ma, mu, ml); renormalised like the Chebyshev segments.
+template <int R>
+__device__ void taylor_segments(int n, int S, const df (&ma)[R], const df (&mu)[R], const df (&ml)[R],
+                                df (&xr)[R], double& lead, SmallExpWork& w, int tid) {
+  for (int seg = 0; seg < S; ++seg) {
+    if (seg > 0) {
+      float mx = 0.f;
+#pragma unroll
+      for (int q = 0; q < R; ++q) mx = fmaxf(mx, fabsf(xr[q].hi));
+      mx = blk_maxf(mx, w.shf, tid);
+      int e = 0;
+      if (mx > 0.f) (void)frexpf(mx, &e);
+      const float f = ldexpf(1.f, -e);
+#pragma unroll
+      for (int q = 0; q < R; ++q) xr[q] = df_scale2(xr[q], f);
+      lead += e * 0.69314718055994530942;
+    }
+    df tc[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const int i = tid + q * SX;
+      tc[q] = xr[q];
+      if (i < n) w.nb[0][i + 1] = make_float2(xr[q].hi, xr[q].lo);
+    }
+    __syncthreads();
+    for (int k = 1; k <= 30; ++k) {
+      const float2* src = w.nb[(k - 1) & 1];
+      float2* dst = w.nb[k & 1];
+      const df ik = w.invk[k];
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        const int i = tid + q * SX;
+        if (i < n) {
+          float p[3], e[3];
+          df_prod(ma[q], tc[q], p[0], e[0]);
+          df_prod(mu[q], cv(src[i + 2]), p[1], e[1]);
+          df_prod(ml[q], cv(src[i]), p[2], e[2]);
+          const df v = df_mul(df_sum_pairs<3>(p, e), ik);
+          dst[i + 1] = make_float2(v.hi, v.lo);
+          xr[q] = df_add(xr[q], v);
+          tc[q] = v;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// The recurrence matrix rows of this thread (M = (T - cI) cscale), the
+// starting vector e_1, and the chosen recurrence; x returned in w.x.
+template <int R>
+__device__ void run_recurrence(int n, const double* dg, const double* up, const double* lo, double c,
+                               double cscale, int mode, int S, int K, double& lead, SmallExpWork& w, int tid) {
+  df ma[R], mu[R], ml[R], xr[R];
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    const int i = tid + q * SX;
+    const bool in = i < n;
+    ma[q] = dfd(in ? (dg[i] - c) * cscale : 0.0);
+    mu[q] = dfd((in && i + 1 < n) ? up[i] * cscale : 0.0);
+    ml[q] = dfd((in && i >= 1) ? lo[i - 1] * cscale : 0.0);
+    xr[q] = df_make((i == 0) ? 1.f : 0.f, 0.f);
+  }
+  if (mode == 0)
+    cheb_segments<R>(n, S, K, ma, mu, ml, xr, lead, w, tid);
+  else
+    taylor_segments<R>(n, S, ma, mu, ml, xr, lead, w, tid);
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    const int i = tid + q * SX;
+    if (i < n) w.x[i] = dd(xr[q]);
+  }
 }
 
 // x = exp(T) e_1 for the n x n tridiagonal T = tridiag(lo, dg, up) (already
 // scaled by tau); lead: on return x holds exp(T) e_1 / e^{lead}.  Block-wide
-// (SX threads); work arrays in shared memory.
+// (SX threads); work arrays in shared memory.  The set-up (bounds, counts)
+// runs in float32 and a few float64 scalars: float64 issues at 1/64 rate.
 __device__ void small_exp_e1(int n, const double* dg, const double* up, const double* lo, SmallExpWork& w,
                              int tid) {
   // symmetric / skew parts in float32, Gershgorin box of each (one row per thread)
-  double glo = 1e300, ghi = -1e300, kb = 0.0;
+  float glo = 3e38f, ghi = -3e38f, kb = 0.f;
   for (int i = tid; i < n; i += SX) {
-    const double s = (i + 1 < n) ? 0.5 * (up[i] + lo[i]) : 0.0;
-    const double k = (i + 1 < n) ? 0.5 * (up[i] - lo[i]) : 0.0;
-    w.fa[i] = (float)dg[i];
-    w.fs2[i] = (float)(s * s);
-    w.fk2[i] = (float)(k * k);
+    const float ui = (i + 1 < n) ? (float)up[i] : 0.f, li = (i + 1 < n) ? (float)lo[i] : 0.f;
+    const float s = 0.5f * (ui + li), k = 0.5f * (ui - li);
+    const float di = (float)dg[i];
+    w.fa[i] = di;
+    w.fs2[i] = s * s;
+    w.fk2[i] = k * k;
     w.fz[i] = 0.f;
-    double rs = fabs(s), rk = fabs(k);
+    float rs = fabsf(s), rk = fabsf(k);
     if (i >= 1) {
-      rs += 0.5 * fabs(up[i - 1] + lo[i - 1]);
-      rk += 0.5 * fabs(up[i - 1] - lo[i - 1]);
+      const float um = (float)up[i - 1], lm = (float)lo[i - 1];
+      rs += 0.5f * fabsf(um + lm);
+      rk += 0.5f * fabsf(um - lm);
     }
-    glo = fmin(glo, dg[i] - rs);
-    ghi = fmax(ghi, dg[i] + rs);
-    kb = fmax(kb, rk);
+    glo = fminf(glo, di - rs);
+    ghi = fmaxf(ghi, di + rs);
+    kb = fmaxf(kb, rk);
   }
-  glo = blk_min(glo, w.sh, tid);
-  ghi = blk_max(ghi, w.sh, tid);
-  kb = blk_max(kb, w.sh, tid);
-  glo -= 1e-6 * (fabs(glo) + 1.0);
-  ghi += 1e-6 * (fabs(ghi) + 1.0);
-  kb = kb * (1.0 + 1e-6) + 1e-300;
-  // both real-part bounds in the same rounds (64 points each, 4 rounds: 65^-4 of the box), then iota
-  double lam_hi = 0.0, lam_lo = 0.0;
-  multisect2(n, w.fa, w.fs2, glo, ghi, w, tid, lam_hi, lam_lo);
-  const double iota = (n > 1) ? multisect(n, w.fz, w.fk2, 0.0, kb, true, 0, SX, 3, w, 0, tid) : 0.0;
+  glo = -blk_maxf(-glo, w.shf, tid);
+  ghi = blk_maxf(ghi, w.shf, tid);
+  kb = blk_maxf(kb, w.shf, tid);
+  // float32 rounding of the entries and sums: 1e-5 relative outward
+  glo -= 1e-5f * (fabsf(glo) + 1.f);
+  ghi += 1e-5f * (fabsf(ghi) + 1.f);
+  kb = kb * (1.f + 1e-5f) + 1e-30f;
+  // both real-part bounds in the same rounds (64 points each, 2 rounds: 65^-2 of
+  // the box), then iota (128 points, 1 round: 1/129 of its Gershgorin bound);
+  // looser bounds only widen the box and the ellipse
+  float lo2[2] = {glo, glo}, hi2[2] = {ghi, ghi};
+  for (int round = 0; round < 2; ++round) msect_round(n, w.fa, w.fs2, lo2, hi2, 2, 64, w, tid);
+  const double lam_hi = (double)hi2[0] + (1e-5 * (fabs((double)lo2[0]) + fabs((double)hi2[0])) + 1e-300);
+  const double lam_lo = (double)lo2[1] - (1e-5 * (fabs((double)lo2[1]) + fabs((double)hi2[1])) + 1e-300);
+  double iota = 0.0;
+  if (n > 1) {
+    float lo1[2] = {0.f, 0.f}, hi1[2] = {kb, kb};
+    msect_round(n, w.fz, w.fk2, lo1, hi1, 1, SX, w, tid);
+    iota = (double)hi1[0] * (1.0 + 1e-5) + 1e-300;
+  }
   const double r = 0.5 * (lam_hi - lam_lo), c = 0.5 * (lam_hi + lam_lo);
+  // Taylor segment count (norm <= 4 each) about the centre of the box:
+  // ||T - cI||_2 <= 2 sqrt(r^2 + iota^2) (numerical radius), or the 1-norm if smaller
+  const float cf = (float)c;
+  float cs = 0.f;
+  for (int i = tid; i < n; i += SX) {
+    float v = fabsf((float)dg[i] - cf);
+    if (i >= 1) v += fabsf((float)up[i - 1]);
+    if (i + 1 < n) v += fabsf((float)lo[i]);
+    cs = fmaxf(cs, v);
+  }
+  const float nrm1 = blk_maxf(cs, w.shf, tid) * (1.f + 1e-5f);
+  const float rf = (float)r, iof = (float)iota;
+  const float tnrm = fminf(nrm1, 2.f * sqrtf(rf * rf + iof * iof) * (1.f + 1e-5f));
+  const int S_taylor = tnrm > 4.f ? (int)ceilf(tnrm / 4.f) : 1;
   int mode = (!(r >= 1e-3) || iota > 0.5 * r) ? 1 : 0;
-  int K = -1;
+  int K = -1, S = 1;
   if (mode == 0) {
-    const double y0 = iota / r;
-    const double b2 = 0.5 * (y0 * y0 + sqrt(y0 * y0 * y0 * y0 + 4.0 * y0 * y0));
-    const double rho = sqrt(1.0 + b2) + sqrt(b2);
-    int kmax = (int)(r + 12.0 * sqrt(r) + 60.0);
-    if (kmax > CHEB_MAX) kmax = CHEB_MAX;
-    if (tid == 0) {
-      // Miller's backward recurrence I_{k-1} = (2k/r) I_k + I_{k+1} in double-float,
-      // rescaled by powers of two
-      const int kstart = kmax + 40 + (int)sqrt(r);
-      const df ir2 = dfd(2.0 / r);
-      df ip1 = df_make(0.f, 0.f), ik = df_make(1e-30f, 0.f);
-      for (int k = kstart; k >= 0; --k) {
-        if (k <= kmax) w.bes[k] = ik;
-        const df im1 = df_add(df_mul(df_mul(df_make((float)k, 0.f), ir2), ik), ip1);
-        ip1 = ik;
-        ik = im1;
-        if (fabsf(ik.hi) > 1e30f) {
-          ik = df_scale2(ik, 0x1p-100f);
-          ip1 = df_scale2(ip1, 0x1p-100f);
-          for (int q = k; q <= kmax; ++q) w.bes[q] = df_scale2(w.bes[q], 0x1p-100f);
+    // Bernstein ellipse holding the box [-1, 1] x [-iota/r, iota/r] (the same for
+    // every segment: exp(X) = exp(X/S)^S scales the box, not its aspect)
+    const float y0 = iof / rf;
+    const float b2 = 0.5f * (y0 * y0 + sqrtf(y0 * y0 * y0 * y0 + 4.f * y0 * y0));
+    const float lnrho = logf(sqrtf(1.f + b2) + sqrtf(b2)) * (1.f + 1e-5f);
+    // first segment count: the scaled Bessel values are close to
+    // e^{-k^2/(2 rs)} / sqrt(2 pi rs), so max_k 2 I~_k(rs) rho^k is close to
+    // 2 e^{rs ln(rho)^2 / 2} / sqrt(2 pi rs); take the smallest S whose estimate
+    // is <= 2^6 (the exact amplification test below decides)
+    while (S < SEG_MAX) {
+      const float rs = rf / (float)S;
+      const float est = 0.5f * rs * lnrho * lnrho * 1.44269504f + 1.f - 0.5f * log2f(6.28318531f * rs);
+      if (est <= 6.f) break;
+      ++S;
+    }
+    for (int attempt = 0; attempt < 4; ++attempt) {
+      const double rs = r / S;
+      const float rsf = (float)rs;
+      // kmax: an upper bound of the term count from
+      //   I~_k(x) <= (x/2)^k / k! e^{x^2/(4(k+1)) - x}
+      // (the series of I_k term by term against that of the exponential) and
+      // Robbins' ln k! >= k ln k - k + ln(2 pi k)/2: the first k > 2 where that
+      // bound of 2 I~_k rho^k and of its predecessor is <= 1e-16 (every thread
+      // tests some k, one block minimum)
+      const float lstep = lnrho + logf(0.5f * rsf);
+      auto lbound = [&](int k) -> float {
+        const float kf = (float)k;
+        const float lfact = kf * logf(kf) - kf + 0.5f * logf(6.28318531f * kf);
+        return 0.69314718f + kf * lstep - lfact - rsf + rsf * rsf / (4.f * (kf + 1.f));
+      };
+      int kb_min = CHEB_MAX;
+      for (int k = 3 + tid; k <= CHEB_MAX - 2; k += SX)
+        if (lbound(k) <= -36.8413615f && lbound(k - 1) <= -36.8413615f) kb_min = min(kb_min, k + 2);  // ln(1e-16)
+      const int kmax = blk_imin(kb_min, w.shi, tid);
+      if (tid == 0) {
+        // Miller's backward recurrence I_{k-1} = (2k/rs) I_k + I_{k+1} in double-float,
+        // rescaled by powers of two; started 24 indices beyond both kmax and 2 rs, where
+        // each step down shrinks the start error by a factor >= 2
+        const int kstart = max(kmax, 2 * (int)rs) + 24;
+        const df ir2 = dfd(2.0 / rs);
+        df ip1 = df_make(0.f, 0.f), ik = df_make(1e-30f, 0.f);
+        for (int k = kstart; k >= 0; --k) {
+          if (k <= kmax) w.bes[k] = ik;
+          const df im1 = df_fma(df_mul(df_make((float)k, 0.f), ir2), ik, ip1);
+          ip1 = ik;
+          ik = im1;
+          if (fabsf(ik.hi) > 1e30f) {
+            ik = df_scale2(ik, 0x1p-100f);
+            ip1 = df_scale2(ip1, 0x1p-100f);
+            for (int q = k; q <= kmax; ++q) w.bes[q] = df_scale2(w.bes[q], 0x1p-100f);
+          }
         }
       }
-      w.rho = rho;
-      w.l2rho = log2(rho);
+      __syncthreads();
+      // normalise: I~_0 + 2 sum_{k >= 1} I~_k = 1
+      df part = df_make(0.f, 0.f);
+      for (int k = tid; k <= kmax; k += SX) part = df_add(part, k == 0 ? w.bes[0] : df_scale2(w.bes[k], 2.f));
+      const df sum = blk_dfsum(part, w.shd, tid);
+      const df isum = dfd(1.0 / dd(sum));
+      for (int k = tid; k <= kmax; k += SX) w.bes[k] = df_mul(w.bes[k], isum);
+      // one more entry, zero, for the look-ahead of the recurrence
+      if (tid == 0) w.bes[kmax + 1] = df_make(0.f, 0.f);
+      __syncthreads();
+      // term count: the first k > 2 with 2 I~_k rho^k and 2 I~_{k-1} rho^{k-1} <= 1e-16
+      // (log2 in float32: a threshold test); no count before rho^k > 2^96 (T_k(Y) x
+      // must stay inside the double-float range)
+      const float l2r = lnrho * 1.44269504f;
+      const float lim = -53.15f;  // log2(1e-16)
+      auto lv = [&](int k) -> float {
+        const float b = 2.f * w.bes[k].hi;
+        return (b > 0.f ? log2f(b) : -1e30f) + (float)k * l2r;
+      };
+      int kc = 1 << 30;
+      for (int k = 3 + tid; k <= kmax; k += SX)
+        if (lv(k) <= lim && lv(k - 1) <= lim && (float)k * l2r <= 96.f) kc = min(kc, k);
+      kc = blk_imin(kc, w.shi, tid);
+      if (kc < (1 << 30)) {
+        // amplification of rounding errors: max_{k < K} 2 I~_k rho^k
+        float amp = -1e30f;
+        for (int k = tid; k < kc; k += SX) amp = fmaxf(amp, lv(k));
+        amp = blk_maxf(amp, w.shf, tid);
+        if (amp <= 6.644f) K = kc;  // log2(100)
+      }
+      if (K >= 0 || S >= SEG_MAX) break;
+      ++S;
     }
-    __syncthreads();
-    // normalise: I~_0 + 2 sum_{k >= 1} I~_k = 1
-    df part = df_make(0.f, 0.f);
-    for (int k = tid; k <= kmax; k += SX) part = df_add(part, k == 0 ? w.bes[0] : df_scale2(w.bes[k], 2.f));
-    const df sum = blk_dfsum(part, w.shd, tid);
-    const df isum = dfd(1.0 / dd(sum));
-    for (int k = tid; k <= kmax; k += SX) w.bes[k] = df_mul(w.bes[k], isum);
-    __syncthreads();
-    // term count: the first k > 2 with 2 I~_k rho^k and 2 I~_{k-1} rho^{k-1} <= 1e-16
-    // (log2 in float32: a threshold test); no count before rho^k > 2^96 (T_k(Y) e1 must
-    // stay inside the double-float range) -> Taylor
-    const float l2r = (float)w.l2rho;
-    const float lim = -53.15f;  // log2(1e-16)
-    auto lv = [&](int k) -> float {
-      const float b = 2.f * w.bes[k].hi;
-      return (b > 0.f ? log2f(b) : -1e30f) + (float)k * l2r;
-    };
-    int kc = 1 << 30;
-    for (int k = 3 + tid; k <= kmax; k += SX)
-      if (lv(k) <= lim && lv(k - 1) <= lim && (float)k * l2r <= 96.f) kc = min(kc, k);
-    kc = blk_imin(kc, w.shi, tid);
-    if (kc < (1 << 30)) {
-      // amplification of rounding errors: max_{k < K} 2 I~_k rho^k
-      double amp = -1e300;
-      for (int k = tid; k < kc; k += SX) amp = fmax(amp, (double)lv(k));
-      amp = blk_max(amp, w.sh, tid);
-      if (amp <= 6.644) K = kc;  // log2(100)
-    }
-    if (K < 0) mode = 1;
+    // Chebyshev only while it needs fewer serial terms than the Taylor fallback
+    if (K < 0 || (long)S * K > 30L * S_taylor) mode = 1;
   }
-  // the recurrence in double-float
-  df* x = w.xv;
-  if (mode == 1) {
-    // Taylor, S segments of norm <= 4, 30 terms each (4^31/31! < 6e-16), about
-    // the centre of the field-of-values box; ||T - cI||_2 <= 2 sqrt(r^2 + iota^2)
-    // (numerical radius), or the 1-norm if smaller
-    double cs = 0.0;
-    for (int i = tid; i < n; i += SX) {
-      double v = fabs(dg[i] - c);
-      if (i >= 1) v += fabs(up[i - 1]);
-      if (i + 1 < n) v += fabs(lo[i]);
-      cs = fmax(cs, v);
-    }
-    const double nrm1 = blk_max(cs, w.sh, tid);
-    const double nrm = fmin(nrm1, 2.0 * sqrt(r * r + iota * iota));
-    const int S = nrm > 4.0 ? (int)ceil(nrm / 4.0) : 1;
-    const double sc = 1.0 / S;
-    for (int i = tid; i < n; i += SX) {
-      w.ca[i] = dfd((dg[i] - c) * sc);
-      w.cu[i] = dfd(up[i] * sc);
-      w.cl[i] = dfd(lo[i] * sc);
-      x[i] = df_make(i == 0 ? 1.f : 0.f, 0.f);
-    }
-    if (tid < 32) w.invk[tid] = dfd(tid > 0 ? 1.0 / tid : 0.0);
-    __syncthreads();
-    double lead = c;
-    for (int seg = 0; seg < S; ++seg) {
-      // keep x near 1 by a power of two (each segment multiplies it by at most e^4)
-      double mx = 0.0;
-      for (int i = tid; i < n; i += SX) mx = fmax(mx, fabs((double)x[i].hi));
-      mx = blk_max(mx, w.sh, tid);
-      int e = 0;
-      if (mx > 0.0) (void)frexp(mx, &e);
-      if (e != 0) {
-        const float f = ldexpf(1.f, -e);
-        for (int i = tid; i < n; i += SX) w.t0[i] = df_scale2(x[i], f);
-        lead += e * 0.69314718055994530942;
-      } else {
-        for (int i = tid; i < n; i += SX) w.t0[i] = x[i];
-      }
-      __syncthreads();
-      for (int i = tid; i < n; i += SX) x[i] = w.t0[i];
-      __syncthreads();
-      df* cur = w.t0;
-      df* nxt = w.t1;
-      for (int k = 1; k <= 30; ++k) {
-        for (int i = tid; i < n; i += SX) {
-          df v = df_mul(w.ca[i], cur[i]);
-          if (i + 1 < n) v = df_add(v, df_mul(w.cu[i], cur[i + 1]));
-          if (i >= 1) v = df_add(v, df_mul(w.cl[i - 1], cur[i - 1]));
-          v = df_mul(v, w.invk[k]);
-          nxt[i] = v;
-          x[i] = df_add(x[i], v);
-        }
-        __syncthreads();
-        df* tsw = cur;
-        cur = nxt;
-        nxt = tsw;
-      }
-    }
-    if (tid == 0) {
-      w.mode = 1;
-      w.lead = lead;
-      w.S = S;
-    }
-  } else {
-    // x = I~_0 e1 + 2 sum_{k>=1} I~_k T_k(Y) e1,  Y = (T - cI)/r
-    const double ir = 1.0 / r;
-    for (int i = tid; i < n; i += SX) {
-      w.ca[i] = dfd((dg[i] - c) * ir);
-      w.cu[i] = dfd(up[i] * ir);
-      w.cl[i] = dfd(lo[i] * ir);
-    }
-    __syncthreads();
-    df* tm = w.t0;
-    df* tc = w.t1;
-    df* tn = w.t2;
-    for (int i = tid; i < n; i += SX) {
-      tm[i] = df_make(i == 0 ? 1.f : 0.f, 0.f);
-      // T_1 e1 = Y e1: column 0 of Y
-      tc[i] = i == 0 ? w.ca[0] : (i == 1 ? w.cl[0] : df_make(0.f, 0.f));
-      x[i] = df_make(0.f, 0.f);
-      if (i == 0) x[i] = w.bes[0];
-      x[i] = df_add(x[i], df_mul(df_scale2(w.bes[1], 2.f), tc[i]));
-    }
-    __syncthreads();
-    for (int k = 2; k < K; ++k) {
-      const df bk = df_scale2(w.bes[k], 2.f);
-      for (int i = tid; i < n; i += SX) {
-        // T_{k} = 2 Y T_{k-1} - T_{k-2}
-        df v = df_mul(w.ca[i], tc[i]);
-        if (i + 1 < n) v = df_add(v, df_mul(w.cu[i], tc[i + 1]));
-        if (i >= 1) v = df_add(v, df_mul(w.cl[i - 1], tc[i - 1]));
-        v = df_sub(df_scale2(v, 2.f), tm[i]);
-        tn[i] = v;
-        x[i] = df_add(x[i], df_mul(bk, v));
-      }
-      __syncthreads();
-      df* tsw = tm;
-      tm = tc;
-      tc = tn;
-      tn = tsw;
-    }
-    if (tid == 0) {
-      w.mode = 0;
-      w.lead = lam_hi;  // e^{c + r}
-      w.K = K;
-    }
+  if (mode == 1) S = S_taylor;
+
+  // The recurrence in double-float.  Each thread keeps its rows (i = tid + q SX)
+  // of the matrix, of the last two terms and of the sum in registers; the rows
+  // its neighbours need pass through a ping-pong buffer (term k writes nb[k & 1]
+  // and reads nb[(k - 1) & 1]), one barrier per term.  The new row is one sum of
+  // product pairs with a single renormalisation.
+  // Matrix of the recurrence: Chebyshev 2Y = 2(T - cI)/r, Taylor (T - cI)/S.
+  for (int i = tid; i < KIOPS_MMAX + 4; i += SX) {
+    w.nb[0][i] = make_float2(0.f, 0.f);
+    w.nb[1][i] = make_float2(0.f, 0.f);
   }
-  __syncthreads();
-  for (int i = tid; i < n; i += SX) w.x[i] = dd(x[i]);
+  if (tid < 32) w.invk[tid] = dfd(tid > 0 ? 1.0 / tid : 0.0);
+  __syncthreads();  // pads and invk before the first rows are written
+  double lead = (mode == 0) ? lam_hi : c;  // Chebyshev: S (c + r)/S; Taylor: the shift
+  const double cscale = (mode == 0) ? 2.0 / r : 1.0 / S;
+  if (n <= SX)
+    run_recurrence<1>(n, dg, up, lo, c, cscale, mode, S, K, lead, w, tid);
+  else
+    run_recurrence<2>(n, dg, up, lo, c, cscale, mode, S, K, lead, w, tid);
+  if (tid == 0) {
+    w.mode = mode;
+    w.lead = lead;
+    w.K = K;
+    w.S = S;
+  }
   __syncthreads();
 }
 

@@ -62,3 +62,35 @@ def test_small_expm_scalar_and_zero(px):
     z = dev(np.zeros(4))
     phix.phix_small_expm(ctx, z, dev(np.zeros(3)), dev(np.zeros(3)), 1.0, F)
     assert F.cpu().numpy().tolist() == [1.0, 0.0, 0.0, 0.0]
+
+
+def _krylov_like(n, r, skew, seed):
+    """Tridiagonal with the shape of a window-2 Hessenberg matrix of a
+    diffusion-dominated Jacobian: diagonal spread over [-2r, 0], positive
+    symmetric off-diagonals of size ~r/4, a skew part `skew` times that."""
+    rng = np.random.default_rng(seed)
+    d = -r * (1 + np.cos(np.linspace(0, np.pi, n))) * rng.uniform(0.9, 1.0, n)
+    s = r / 2 * rng.uniform(0.3, 0.6, n - 1)
+    k = skew * s * rng.uniform(-1, 1, n - 1)
+    return d, s + k, s - k
+
+
+@pytest.mark.parametrize("n,r,skew", [(41, 50, 1.0), (65, 100, 0.5), (65, 100, 1.0), (97, 200, 1.0),
+                                      (129, 400, 1.0), (129, 400, 0.2)])
+def test_small_expm_wide_spectrum_takes_chebyshev_segments(px, n, r, skew):
+    """Field-of-values half-widths r ~ 70..550 with iota/r ~ 0.05..0.3 (the
+    range of the Krylov method's tau Hbar on stiff diffusion-reaction
+    problems): one Chebyshev expansion would amplify rounding by up to 2^16
+    or more, so the expansion runs in segments exp(X/S)^S; the result stays
+    within the normwise 1e-12 of scipy's dense expm."""
+    phix, ctx = px
+    d, u, l = _krylov_like(n, r, skew, n + int(r))
+    T = np.diag(d) + np.diag(u, 1) + np.diag(l, -1)
+    E = scipy.linalg.expm(T)
+    dev = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda")
+    F = torch.empty(n, dtype=torch.float64, device="cuda")
+    mode = phix.phix_small_expm(ctx, dev(d), dev(u), dev(l), 1.0, F)
+    got = F.cpu().numpy()
+    err = np.linalg.norm(got - E[:, 0]) / np.linalg.norm(E, 2)
+    assert mode == 0, "expected the Chebyshev path"
+    assert err <= 1e-12, err
