@@ -207,8 +207,8 @@ __device__ bool block_partials_and_last(A (&acc)[NV], double* partials, unsigned
       for (int w = 0; w < THREADS / 32; ++w) s += sred[w][tid];
       partials[(size_t)blockIdx.x * (KMAX + 1) + tid] = s;
     }
+    __threadfence();  // the writers' partials visible before the arrival count
   }
-  __threadfence();
   __syncthreads();
   if (tid == 0) {
     unsigned int t = atomicAdd(count, 1u);

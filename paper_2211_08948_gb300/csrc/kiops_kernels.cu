@@ -14,6 +14,7 @@
 //   pass 2: z <- z - h_jj V_j - h_{j-1,j} V_{j-1} in place, partial ||z||^2;
 // the last block of each pass adds the tail terms, forms h_jj, h_{j-1,j},
 // h_{j+1,j}, s_{j+1} and writes the coefficients of the next launch.
+#include <algorithm>
 #include "iter_common.cuh"
 
 namespace phix {
@@ -23,6 +24,24 @@ namespace {
 // dot products: float64, or double-float accumulation
 __device__ __forceinline__ void acc_dot(double& a, double x, double y) { a = fma(x, y, a); }
 __device__ __forceinline__ void acc_dot(df& a, df x, df y) { a = df_fma(x, y, a); }
+
+// accumulator of <z, z> in pass 1: float64 in the float64 path, float32 otherwise
+template <typename A>
+struct AccSq {
+  using F = float;
+};
+template <>
+struct AccSq<double> {
+  using F = double;
+};
+__device__ __forceinline__ double acc_sq_f(double a, double z) { return fma(z, z, a); }
+__device__ __forceinline__ float acc_sq_f(float a, df z) { return fmaf(z.hi, z.hi, a); }
+template <typename A>
+__device__ __forceinline__ A acc_from_f(typename AccSq<A>::F v);
+template <>
+__device__ __forceinline__ double acc_from_f<double>(double v) { return v; }
+template <>
+__device__ __forceinline__ df acc_from_f<df>(float v) { return df_make(v, 0.f); }
 
 template <int P>
 struct KTr;
@@ -101,6 +120,8 @@ __global__ void __launch_bounds__(THREADS) k_arn1(ArnArgs a) {
     bw[b] = b < a.nb ? coef<C>(__ldcg(&kc->bd[a.bslot[b]]), __ldcg(&kc->bf[a.bslot[b]])) : C{};
 
   Acc acc[3] = {acc_zero<Acc>(), acc_zero<Acc>(), acc_zero<Acc>()};
+  // <z, z> only sets the happy-breakdown threshold: float32 in the double-float path
+  typename AccSq<Acc>::F zz = 0;
   const T* __restrict__ zj = static_cast<const T*>(a.zj);
   const T* __restrict__ zm = static_cast<const T*>(a.zjm1);
   T* __restrict__ zo = static_cast<T*>(a.zout);
@@ -108,7 +129,11 @@ __global__ void __launch_bounds__(THREADS) k_arn1(ArnArgs a) {
   const int nx = a.nx, ny = a.ny;
   const size_t plane = (size_t)nx * ny;
 
-  for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+  // a contiguous, balanced range of tiles per block (neighbouring tiles share
+  // their halo rows in L1/L2; blocks differ by at most one tile)
+  const int t_begin = (int)(((long long)blockIdx.x * a.ntiles) / gridDim.x);
+  const int t_end = (int)(((long long)(blockIdx.x + 1) * a.ntiles) / gridDim.x);
+  for (int tile = t_begin; tile < t_end; ++tile) {
     const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
     const int iy = ty * TILE_Y + threadIdx.y;
     const int ix = (tx * 32 + threadIdx.x) * V;
@@ -133,6 +158,38 @@ __global__ void __launch_bounds__(THREADS) k_arn1(ArnArgs a) {
       }
       we[q] = ldr1(b + row + ixm);
       ea[q] = ldr1(b + row + ixp);
+    }
+    // every load of the tile issued before its arithmetic: z_{j-1} for the
+    // second dot and the augmented columns B t (sum_b bw_b b-copy_b)
+    C cm[NC][V], zb[NC][V];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      const size_t i0 = q * plane + row + ix;
+      if (zm) {
+        if constexpr (V == 2)
+          ldr2(zm + i0, cm[q][0], cm[q][1]);
+        else
+          cm[q][0] = ldr1(zm + i0);
+      } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v) cm[q][v] = C{};
+      }
+#pragma unroll
+      for (int v = 0; v < V; ++v) zb[q][v] = C{};
+#pragma unroll
+      for (int bq = 0; bq < KIOPS_PMAX; ++bq) {
+        if (bq < a.nb) {
+          const T* bb = static_cast<const T*>(a.bz[bq]) + i0;
+          if constexpr (V == 2) {
+            C b0, b1;
+            ldr2(bb, b0, b1);
+            zb[q][0] = zb[q][0] + bw[bq] * b0;
+            zb[q][1] = zb[q][1] + bw[bq] * b1;
+          } else {
+            zb[q][0] = zb[q][0] + bw[bq] * ldr1(bb);
+          }
+        }
+      }
     }
 #pragma unroll
     for (int v = 0; v < V; ++v) {
@@ -166,16 +223,16 @@ __global__ void __launch_bounds__(THREADS) k_arn1(ArnArgs a) {
 #pragma unroll
       for (int q = 0; q < NC; ++q) {
         const size_t idx = q * plane + row + ix + v;
-        C z = J[q];
-        for (int b = 0; b < a.nb; ++b) z = z + bw[b] * ldr1(static_cast<const T*>(a.bz[b]) + idx);
+        const C z = J[q] + zb[q][v];
         st1(zo + idx, z);
         acc_dot(acc[0], c[q][v], z);
-        if (zm) acc_dot(acc[1], ldr1(zm + idx), z);
-        acc_dot(acc[2], z, z);
+        acc_dot(acc[1], cm[q][v], z);
+        zz = acc_sq_f(zz, z);
       }
     }
   }
 
+  acc[2] = acc_from_f<Acc>(zz);
   if (block_partials_and_last<Acc, 3>(acc, a.partials, &kc->count)) {
     double tot[3];
     reduce_partials<Acc, 3>(a.partials, tot);
@@ -1005,11 +1062,26 @@ CombArgs make_comb(const KiopsSpec& s, int n, double* out, double scale) {
   return c;
 }
 
+// resident blocks per SM of a THREADS-thread kernel (at least 1)
+int blocks_per_sm(const void* fn) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, THREADS, 0) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 4;
+  }
+  return nb < 1 ? 1 : nb;
+}
+
+// Both passes run as one wave of resident blocks (SMs x occupancy): a grid
+// beyond that leaves a partial second wave on a third of the SMs.
 template <int P, int OP>
 cudaError_t arn_t(const KiopsSpec& s, int j, cudaStream_t st) {
+  static const int occ1v2 = blocks_per_sm(reinterpret_cast<const void*>(k_arn1<P, OP, 2>));
+  static const int occ1v1 = blocks_per_sm(reinterpret_cast<const void*>(k_arn1<P, OP, 1>));
+  static const int occ2 = blocks_per_sm(reinterpret_cast<const void*>(k_arn2<P>));
   const int V = (s.nx % 2 == 0) ? 2 : 1;
   ArnArgs a = make_arn(s, j, V);
-  const int g1 = s.grid < a.ntiles ? s.grid : a.ntiles;
+  const int g1 = std::min(s.nsm * (V == 2 ? occ1v2 : occ1v1), a.ntiles);
   if (V == 2)
     k_arn1<P, OP, 2><<<g1, dim3(32, TILE_Y), 0, st>>>(a);
   else
@@ -1017,7 +1089,7 @@ cudaError_t arn_t(const KiopsSpec& s, int j, cudaStream_t st) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const size_t N = (size_t)s.nx * s.ny * (OP == PHIX_OP_GRAYSCOTT ? 2 : 1);
-  k_arn2<P><<<s.grid, dim3(32, TILE_Y), 0, st>>>(a, N);
+  k_arn2<P><<<s.nsm * occ2, dim3(32, TILE_Y), 0, st>>>(a, N);
   return cudaGetLastError();
 }
 

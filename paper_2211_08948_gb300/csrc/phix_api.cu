@@ -750,6 +750,7 @@ void kiops_run(phix_ctx* ctx, const OpState& os, int prec, double h, const doubl
   for (int i = 0; i < 8; ++i) ks.kJ[i] = os.kJ[i];
   ks.nscaled = n_scaled(os.d.kind);
   ks.grid = ctx->grid_iter;
+  ks.nsm = ctx->nsm;
   // b_j (j >= 1) copies in the iteration precision and their 1-norms -> eta
   int nb = 0;
   for (int j = 1; j <= p; ++j)

@@ -180,7 +180,8 @@ struct KiopsSpec {
   double h;                     // A = h J
   double kJ[8];                 // unscaled uniform J coefficients
   int nscaled;
-  int grid;
+  int grid;                     // streaming kernels (combine, start)
+  int nsm;                      // SMs (the Arnoldi kernels size their grids by occupancy)
 };
 // w_0 = c [b_0; e_p / eta] (c a power of two): Zhat_0 = c b_0 (or 0), tail_0 = c e_p / eta,
 // s_0 = 1/||w_0||, next pass-1 coefficients.
