@@ -37,7 +37,7 @@ WORKLOAD = "Gray-Scott 1024x1024x2, EXPRB43 steps, h=100x explicit limit, Leja, 
 # DRAM bytes (read + write) of one launch of the dominant kernel, from an ncu --set full capture
 # of this configuration (k_iter, a K = 2 launch, cold caches); null for configurations without a
 # capture of the current kernel.
-TRAFFIC = {("leja", 1024, "DF64"): 67.15e6 + 8.72e6}
+TRAFFIC = {}
 
 
 def parse():

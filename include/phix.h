@@ -119,6 +119,10 @@ typedef struct {
                           and PHIX_KERNEL_TMA force one (TMA needs rows of a multiple of
                           16 bytes, i.e. nx even, nx % 4 == 0 for 4-byte state, and
                           falls back to the single-step kernel otherwise)             */
+  int kiops_fused;     /* KIOPS: 1 (default) runs each Arnoldi step as one pass (the
+                          orthogonalisation of step j staged in shared memory and pass 1
+                          of step j + 1 read from it) when nx % 64 == 0 and ny % 8 == 0;
+                          0, or other grids: two passes per step                      */
 } phix_opts;
 
 typedef enum { PHIX_KERNEL_AUTO = 0, PHIX_KERNEL_SINGLE = 1, PHIX_KERNEL_TMA = 2 } phix_kernel;

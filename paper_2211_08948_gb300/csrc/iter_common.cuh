@@ -218,36 +218,64 @@ __device__ bool block_partials_and_last(A (&acc)[NV], double* partials, unsigned
   return last;
 }
 
-// Last block: totals[j] = sum over blocks of the partials (fixed order: strided
-// per thread, then a halving tree).  The totals are valid in thread 0 only.
-template <typename A, int NV>
-__device__ void reduce_partials(const double* partials, double (&tot)[NV]) {
+// Last block: totals[j] = sum over blocks of the partials (fixed order: up to
+// four strided partials per thread loaded at once, then a tree).  The totals
+// are valid in thread 0 only.  Double-float partials: the tree runs on warp
+// shuffles (float32 lanes) with one barrier between the warp and block levels;
+// the last block's reduction is on the critical path of every launch.
+struct NoHook {
+  __device__ void operator()() const {}
+};
+// `hook` runs in every thread just before the block barrier (work that the
+// caller wants overlapped with the partials' latency and published by it).
+template <typename A, int NV, typename H = NoHook>
+__device__ void reduce_partials(const double* partials, double (&tot)[NV], H hook = H{}) {
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   if constexpr (PartialsDF<A>::value) {
-    __shared__ float2 sfin[THREADS][KMAX + 1];
+    constexpr int NW = THREADS / 32;
+    __shared__ float2 swarp[NW][KMAX + 1];
+    const int lane = tid & 31, warp = tid >> 5;
     df s[NV];
 #pragma unroll
     for (int j = 0; j < NV; ++j) s[j] = df_make(0.f, 0.f);
-    for (int b = tid; b < (int)gridDim.x; b += THREADS) {
+    const float2* pf = reinterpret_cast<const float2*>(partials);
+    for (int b0 = tid; b0 < (int)gridDim.x; b0 += 4 * THREADS) {
+      float2 v[4][NV];
 #pragma unroll
-      for (int j = 0; j < NV; ++j)
-        s[j] = df_add(s[j], cv(__ldcg(reinterpret_cast<const float2*>(partials + (size_t)b * (KMAX + 1) + j))));
-    }
+      for (int q = 0; q < 4; ++q) {
+        const int b = b0 + q * THREADS;
 #pragma unroll
-    for (int j = 0; j < NV; ++j) sfin[tid][j] = make_float2(s[j].hi, s[j].lo);
-    __syncthreads();
-    for (int w = THREADS / 2; w > 0; w >>= 1) {
-      if (tid < w) {
-#pragma unroll
-        for (int j = 0; j < NV; ++j) {
-          const df t = df_add(cv(sfin[tid][j]), cv(sfin[tid + w][j]));
-          sfin[tid][j] = make_float2(t.hi, t.lo);
-        }
+        for (int j = 0; j < NV; ++j)
+          v[q][j] = b < (int)gridDim.x ? __ldcg(pf + (size_t)b * (KMAX + 1) + j) : make_float2(0.f, 0.f);
       }
-      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int j = 0; j < NV; ++j) s[j] = df_add(s[j], cv(v[q][j]));
     }
 #pragma unroll
-    for (int j = 0; j < NV; ++j) tot[j] = tid == 0 ? (double)sfin[0][j].x + (double)sfin[0][j].y : 0.0;
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int j = 0; j < NV; ++j) s[j] = df_add(s[j], shfl_down(s[j], o));
+    if (lane == 0)
+#pragma unroll
+      for (int j = 0; j < NV; ++j) swarp[warp][j] = make_float2(s[j].hi, s[j].lo);
+    hook();
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < NV; ++j) tot[j] = 0.0;
+    if (warp == 0) {
+#pragma unroll
+      for (int j = 0; j < NV; ++j) s[j] = lane < NW ? cv(swarp[lane][j]) : df_make(0.f, 0.f);
+#pragma unroll
+      for (int o = NW / 2; o > 0; o >>= 1)
+#pragma unroll
+        for (int j = 0; j < NV; ++j) s[j] = df_add(s[j], shfl_down(s[j], o));
+      // float64 work in one thread only (a warp's float64 instruction holds the pipe ~64 cycles)
+      if (lane == 0)
+#pragma unroll
+        for (int j = 0; j < NV; ++j) tot[j] = (double)s[j].hi + (double)s[j].lo;
+    }
   } else {
     __shared__ double sfin[THREADS][KMAX + 1];
     double s[NV];
@@ -259,6 +287,7 @@ __device__ void reduce_partials(const double* partials, double (&tot)[NV]) {
     }
 #pragma unroll
     for (int j = 0; j < NV; ++j) sfin[tid][j] = s[j];
+    hook();
     __syncthreads();
     for (int w = THREADS / 2; w > 0; w >>= 1) {
       if (tid < w) {

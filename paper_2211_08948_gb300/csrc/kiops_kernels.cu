@@ -43,6 +43,39 @@ __device__ __forceinline__ double acc_from_f<double>(double v) { return v; }
 template <>
 __device__ __forceinline__ df acc_from_f<df>(float v) { return df_make(v, 0.f); }
 
+// ws w - c1 z - c0 y: float64, or one sum of double-float product pairs with a
+// single renormalisation
+__device__ __forceinline__ double orth3(double ws, double w, double c1, double z, double c0, double y) {
+  return ws * w - c1 * z - c0 * y;
+}
+__device__ __forceinline__ df orth3(df ws, df w, df c1, df z, df c0, df y) {
+  float p[3], e[3];
+  df_prod(ws, w, p[0], e[0]);
+  df_prod(df_neg(c1), z, p[1], e[1]);
+  df_prod(df_neg(c0), y, p[2], e[2]);
+  return df_sum_pairs<3>(p, e);
+}
+
+// r = 1/sqrt(x), s = sqrt(x): a float32 seed and two Newton steps
+// y <- y (3/2 - x y^2 / 2) in float64 inside the float32 range, a float64
+// square root and division outside it (and for 0, inf, NaN)
+__device__ __forceinline__ void rsqrt_and_sqrt(double x, double& r, double& s) {
+  if (x > 1e-30 && x < 1e30) {
+    double y = (double)rsqrtf((float)x);
+    y = y * fma(-0.5 * x * y, y, 1.5);
+    y = y * fma(-0.5 * x * y, y, 1.5);
+    r = y;
+    s = x * y;
+  } else {
+    s = sqrt(x);
+    r = 1.0 / s;
+  }
+}
+
+// a value in its storage form (float64, or the two float32 parts)
+__device__ __forceinline__ double stv(double v) { return v; }
+__device__ __forceinline__ float2 stv(df v) { return make_float2(v.hi, v.lo); }
+
 template <int P>
 struct KTr;
 template <>
@@ -63,7 +96,10 @@ struct KTr<P_DF64> {
 struct ArnArgs {
   const void* zj;
   const void* zjm1;  // NULL for j = 0
-  void* zout;        // slot j + 1
+  void* zout;        // slot j + 1 (fused first pass: the scratch vector W0)
+  const void* win;   // fused step: W (pass-1 result of step j, scaled by ws)
+  void* wout;        // fused step: u (pass-1 result of step j + 1, unscaled)
+  int fused;         // pass 1 of step 0 feeding fused steps
   const void* bz[KIOPS_PMAX];
   int bslot[KIOPS_PMAX];
   int nb;
@@ -99,6 +135,32 @@ __device__ void prepare_pass1(KiopsCtl* kc, int j, int p, double h, const double
 __device__ __forceinline__ float2 split2d(double v) {
   float hi = (float)v;
   return make_float2(hi, (float)(v - (double)hi));
+}
+
+// After pass 1 of step j (tail[j + 1] = tail of A~ z_j, c1/c0 set): the
+// orthogonalised tail of Zhat_{j+1}, the scale ws of the scratch vector W, and
+// the coefficients of u = A~ [Zhat_{j+1}; tail_{j+1}] without the s_{j+1}
+// factor (k h, ga = h, b-column weights eta tail_{j+1}).  Single thread.
+__device__ void fused_prepare(KiopsCtl* kc, int j, int p, double ws, double h, const double* kJ, int nscaled) {
+  double* t1 = kc->tail + (j + 1) * KIOPS_PMAX;
+  const double* t0 = kc->tail + j * KIOPS_PMAX;
+  for (int t = 0; t < p; ++t) {
+    double v = t1[t] - kc->c1d * t0[t];
+    if (j >= 1) v -= kc->c0d * kc->tail[(j - 1) * KIOPS_PMAX + t];
+    t1[t] = v;
+    const double b = kc->eta * v;
+    kc->bud[t] = b;
+    kc->buf[t] = split2d(b);
+  }
+  kc->wsd = ws;
+  kc->wsf = split2d(ws);
+  for (int i = 0; i < 8; ++i) {
+    const double v = i < nscaled ? kJ[i] * h : kJ[i];
+    kc->kud[i] = v;
+    kc->kuf[i] = split2d(v);
+  }
+  kc->gud = h;
+  kc->guf = split2d(h);
 }
 
 template <int P, int OP, int V>
@@ -259,12 +321,301 @@ __global__ void __launch_bounds__(THREADS) k_arn1(ArnArgs a) {
       kc->c0d = c0;
       kc->c1f = split2d(c1);
       kc->c0f = split2d(c0);
+      if (a.fused) fused_prepare(kc, j, p, 1.0, a.h, a.kJ, a.nscaled);
       if (!isfinite(hjj) || !isfinite(hjm) || !isfinite(zz)) {
         kc->status = PHIX_ENAN;
         kc->stop = 1;
       }
       kc->count = 0;
       __threadfence();
+    }
+  }
+}
+
+// Fused Arnoldi step j (grids of whole tiles: nx % 64 == 0, ny % TILE_Y == 0).
+// Completes step j: Zhat_{j+1} = ws W - c1 Zhat_j - c0 Zhat_{j-1} (written to
+// slot j + 1 and, with a one-point halo ring recomputed from W, Zhat_j,
+// Zhat_{j-1}, staged in shared memory), and runs pass 1 of step j + 1 from
+// the staged tile: u = A~ [Zhat_{j+1}; tail_{j+1}] without the factor s_{j+1}
+// (written to the other scratch vector), with <Zhat_{j+1}, Zhat_{j+1}>,
+// <Zhat_{j+1}, u>, <Zhat_j, u> and <u, u>.  Five vectors move per step instead
+// of seven (two-pass); the recompute is the ring, 9/32 of the tile.
+template <int P, int OP>
+__global__ void __launch_bounds__(THREADS) k_arnf(ArnArgs a) {
+  using T = typename KTr<P>::T;
+  using C = typename KTr<P>::C;
+  using S = typename KTr<P>::S;
+  using Acc = typename KTr<P>::Acc;
+  constexpr int V = 2;
+  constexpr int NC = (OP == PHIX_OP_GRAYSCOTT) ? 2 : 1;
+  constexpr int TW = 32 * V, SW = TW + 2, NRING = 2 * TW + 2 * TILE_Y;
+  static_assert(NRING <= THREADS, "one ring point per thread");
+  __shared__ T sm[NC][TILE_Y + 2][SW];
+  KiopsCtl* kc = a.kc;
+  if (__ldcg(&kc->stop)) return;
+  const C ws = coef<C>(__ldcg(&kc->wsd), __ldcg(&kc->wsf));
+  const C c1 = coef<C>(__ldcg(&kc->c1d), __ldcg(&kc->c1f));
+  const C c0 = coef<C>(__ldcg(&kc->c0d), __ldcg(&kc->c0f));
+  C kk[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) kk[i] = coef<C>(__ldcg(&kc->kud[i]), __ldcg(&kc->kuf[i]));
+  const C ga = coef<C>(__ldcg(&kc->gud), __ldcg(&kc->guf));
+  C bw[KIOPS_PMAX];
+#pragma unroll
+  for (int b = 0; b < KIOPS_PMAX; ++b)
+    bw[b] = b < a.nb ? coef<C>(__ldcg(&kc->bud[a.bslot[b]]), __ldcg(&kc->buf[a.bslot[b]])) : C{};
+
+  Acc acc[4] = {acc_zero<Acc>(), acc_zero<Acc>(), acc_zero<Acc>(), acc_zero<Acc>()};
+  typename AccSq<Acc>::F uu = 0;
+  const T* __restrict__ W = static_cast<const T*>(a.win);
+  const T* __restrict__ zj = static_cast<const T*>(a.zj);
+  const T* __restrict__ zm = static_cast<const T*>(a.zjm1);
+  T* __restrict__ zo = static_cast<T*>(a.zout);
+  T* __restrict__ uo = static_cast<T*>(a.wout);
+  const S* __restrict__ st = static_cast<const S*>(a.st);
+  const int nx = a.nx, ny = a.ny;
+  const size_t plane = (size_t)nx * ny;
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  auto orth = [&](C w, C z, C y) -> C { return orth3(ws, w, c1, z, c0, y); };
+
+  const int t_begin = (int)(((long long)blockIdx.x * a.ntiles) / gridDim.x);
+  const int t_end = (int)(((long long)(blockIdx.x + 1) * a.ntiles) / gridDim.x);
+  for (int tile = t_begin; tile < t_end; ++tile) {
+    const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+    const int iy0 = ty * TILE_Y, ix0 = tx * TW;
+    const int iy = iy0 + threadIdx.y, ix = ix0 + V * threadIdx.x;
+    const size_t row = (size_t)iy * nx;
+    // own points: W, Zhat_j, Zhat_{j-1}; the ring point; the state and the
+    // augmented columns (every load of the tile issued before its arithmetic)
+    C wv[NC][V], zc[NC][V], mv[NC][V], zb[NC][V];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      const size_t i0 = q * plane + row + ix;
+      ldr2(W + i0, wv[q][0], wv[q][1]);
+      ldr2(zj + i0, zc[q][0], zc[q][1]);
+      if (zm) {
+        ldr2(zm + i0, mv[q][0], mv[q][1]);
+      } else {
+        mv[q][0] = C{};
+        mv[q][1] = C{};
+      }
+      zb[q][0] = C{};
+      zb[q][1] = C{};
+#pragma unroll
+      for (int bq = 0; bq < KIOPS_PMAX; ++bq) {
+        if (bq < a.nb) {
+          C b0, b1;
+          ldr2(static_cast<const T*>(a.bz[bq]) + i0, b0, b1);
+          zb[q][0] = zb[q][0] + bw[bq] * b0;
+          zb[q][1] = zb[q][1] + bw[bq] * b1;
+        }
+      }
+    }
+    int rr = 0, rc = 0;
+    C rv[NC];
+    if (tid < NRING) {
+      if (tid < TW) {  // south row
+        rr = 0;
+        rc = tid + 1;
+      } else if (tid < 2 * TW) {  // north row
+        rr = TILE_Y + 1;
+        rc = tid - TW + 1;
+      } else if (tid < 2 * TW + TILE_Y) {  // west column
+        rr = tid - 2 * TW + 1;
+        rc = 0;
+      } else {  // east column
+        rr = tid - 2 * TW - TILE_Y + 1;
+        rc = TW + 1;
+      }
+      const int gy = (iy0 + rr - 1 + ny) % ny, gx = (ix0 + rc - 1 + nx) % nx;
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        const size_t g = q * plane + (size_t)gy * nx + gx;
+        rv[q] = orth(ldr1(W + g), ldr1(zj + g), zm ? ldr1(zm + g) : C{});
+      }
+    }
+    C g1[V], g2[V];
+    if constexpr (OP == PHIX_OP_GRAYSCOTT) {
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        g1[v] = cv(__ldg(st + row + ix + v));
+        g2[v] = cv(__ldg(st + plane + row + ix + v));
+      }
+    }
+    // Zhat_{j+1} at the own points: to slot j + 1 and the staged tile
+    C zn[NC][V];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        zn[q][v] = orth(wv[q][v], zc[q][v], mv[q][v]);
+        sm[q][threadIdx.y + 1][V * threadIdx.x + 1 + v] = stv(zn[q][v]);
+      }
+      st2(zo + q * plane + row + ix, zn[q][0], zn[q][1]);
+      if (tid < NRING) sm[q][rr][rc] = stv(rv[q]);
+    }
+    __syncthreads();
+    // pass 1 of step j + 1 from the staged tile
+    const int sr = threadIdx.y + 1;
+    C u[NC][V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const int sc = V * threadIdx.x + 1 + v;
+      C J[NC];
+      if constexpr (OP == PHIX_OP_ADVDIFF) {
+        J[0] = stencil_advdiff<C>(kk, cv(sm[0][sr][sc + 1]), cv(sm[0][sr][sc - 1]), cv(sm[0][sr + 1][sc]),
+                                  cv(sm[0][sr - 1][sc]), zn[0][v]);
+      } else if constexpr (OP == PHIX_OP_GRAYSCOTT) {
+        stencil_gs<C>(kk, ga, cv(sm[0][sr][sc + 1]), cv(sm[0][sr][sc - 1]), cv(sm[0][sr + 1][sc]),
+                      cv(sm[0][sr - 1][sc]), zn[0][v], cv(sm[NC - 1][sr][sc + 1]), cv(sm[NC - 1][sr][sc - 1]),
+                      cv(sm[NC - 1][sr + 1][sc]), cv(sm[NC - 1][sr - 1][sc]), zn[NC - 1][v], g1[v], g2[v], J[0],
+                      J[NC - 1]);
+      } else {
+        const int vx = ix + v;
+        const int vxm = vx == 0 ? nx - 1 : vx - 1;
+        const int vxp = vx == nx - 1 ? 0 : vx + 1;
+        const size_t rowp = (size_t)(iy == ny - 1 ? 0 : iy + 1) * nx;
+        const size_t rowm = (size_t)(iy == 0 ? ny - 1 : iy - 1) * nx;
+        C Uc = cv(__ldg(st + row + vx));
+        C Ue = cv(__ldg(st + row + vxp));
+        C Uw = cv(__ldg(st + row + vxm));
+        C Un = cv(__ldg(st + rowp + vx));
+        C Us = cv(__ldg(st + rowm + vx));
+        J[0] = stencil_burgers<C>(kk, ga, cv(sm[0][sr][sc + 1]), cv(sm[0][sr][sc - 1]), cv(sm[0][sr + 1][sc]),
+                                  cv(sm[0][sr - 1][sc]), zn[0][v], Ue, Uw, Un, Us, Uc);
+      }
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        u[q][v] = J[q] + zb[q][v];
+        acc_dot(acc[0], zn[q][v], zn[q][v]);
+        acc_dot(acc[1], zn[q][v], u[q][v]);
+        acc_dot(acc[2], zc[q][v], u[q][v]);
+        uu = acc_sq_f(uu, u[q][v]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NC; ++q) st2(uo + q * plane + row + ix, u[q][0], u[q][1]);
+    __syncthreads();  // the staged tile is overwritten by the next tile
+  }
+
+  acc[3] = acc_from_f<Acc>(uu);
+  if (block_partials_and_last<Acc, 4>(acc, a.partials, &kc->count)) {
+    // Epilogue, a chain of float64 scalars on the critical path of every step
+    // (a float64 instruction holds a pipe ~64 cycles):
+    // - thread 32 reads the control values before the partials and, in the
+    //   reduction's hook, forms the sums that need only the tails;
+    // - thread 0 runs the short chain from the totals;
+    // - one lane per warp splits one result into its float32 pair.
+    constexpr int PM = KIOPS_PMAX;
+    __shared__ double sx[2 * PM + 7];
+    __shared__ double sv[3 + PM];
+    __shared__ int s_go;
+    const int j = a.j, p = a.p;
+    double t1[PM], t0[PM], sj = 0.0, z0j = 0.0, eta = 0.0;
+#pragma unroll
+    for (int t = 0; t < PM; ++t) {
+      t1[t] = (tid == 32 && t < p) ? kc->tail[(j + 1) * PM + t] : 0.0;  // tail_{j+1}, orthogonalised
+      t0[t] = (tid == 32 && t < p) ? kc->tail[j * PM + t] : 0.0;        // tail_j
+    }
+    if (tid == 32) {
+      sj = kc->s[j];
+      z0j = kc->z0[j];
+      eta = kc->eta;
+    }
+    double tot[4];
+    reduce_partials<Acc, 4>(a.partials, tot, [&]() {
+      if (tid == 32) {
+        double T2 = 0.0, A1 = 0.0, A0 = 0.0, A2 = 0.0;
+#pragma unroll
+        for (int t = 0; t < PM; ++t) {
+          T2 = fma(t1[t], t1[t], T2);
+          if (t + 1 < PM) {
+            A1 = fma(t1[t], t1[t + 1], A1);
+            A0 = fma(t0[t], t1[t + 1], A0);
+            A2 = fma(t1[t + 1], t1[t + 1], A2);
+          }
+          sx[7 + t] = t1[t];
+          sx[7 + PM + t] = t0[t];
+        }
+        sx[0] = T2;
+        sx[1] = A1;
+        sx[2] = A0;
+        sx[3] = A2;
+        sx[4] = sj;
+        sx[5] = z0j;
+        sx[6] = eta;
+      }
+    });
+    if (tid == 0) {
+      // A~ z_{j+1} = s_{j+1} [u; K tail_{j+1}] with K the shift: its tail is
+      // s_{j+1} tail_{j+1}[t + 1], so with 1/nz = s_{j+1}^2
+      //   h_{j+1,j+1} = (<Zhat_{j+1}, u> + A1) / nz,   h_{j,j+1} = s_j s_{j+1} (<Zhat_j, u> + A0),
+      //   ||A~ z_{j+1}||^2 = (<u, u> + A2) / nz
+      const double nz = tot[0] + sx[0];
+      double s1, hn;
+      rsqrt_and_sqrt(nz, s1, hn);
+      kc->hl[j] = hn;
+      int go = 0;
+      if (!isfinite(hn)) {
+        kc->status = PHIX_ENAN;
+        kc->stop = 1;
+      } else if (hn <= 1e-12 * sx[5]) {
+        kc->stop = 1;  // happy breakdown: exact invariant subspace of dimension j+1
+        kc->happy_m = j + 1;
+      } else {
+        const double r2 = s1 * s1, sj2 = sx[4];
+        const double h11 = (tot[1] + sx[1]) * r2, h01 = sj2 * s1 * (tot[2] + sx[2]);
+        const double zz = (tot[3] + sx[3]) * r2;
+        const double cc1 = h11 * s1, cc0 = h01 * sj2;
+        kc->s[j + 1] = s1;
+        kc->wsd = s1;
+        kc->hd[j + 1] = h11;
+        kc->hu[j + 1] = h01;
+        kc->c1d = cc1;
+        kc->c0d = cc0;
+        sv[0] = s1;
+        sv[1] = cc1;
+        sv[2] = cc0;
+        // tail_{j+2} = s_{j+1} tail_{j+1}[t + 1] - c1 tail_{j+1} - c0 tail_j (orthogonalised)
+        // and the b-column weights of the next fused step
+        double* t2 = kc->tail + (j + 2) * PM;
+        for (int t = 0; t < p; ++t) {
+          const double tz = (t + 1 < p) ? s1 * sx[7 + t + 1] : 0.0;
+          const double v = tz - cc1 * sx[7 + t] - cc0 * sx[7 + PM + t];
+          t2[t] = v;
+          const double bb = sx[6] * v;
+          kc->bud[t] = bb;
+          sv[3 + t] = bb;
+        }
+        // ||A~ z_{j+1}|| only sets the happy-breakdown threshold: float32 square root in range
+        kc->z0[j + 1] = (zz > 1e-30 && zz < 1e30) ? (double)sqrtf((float)zz) : sqrt(zz);
+        if (!isfinite(h11) || !isfinite(h01) || !isfinite(zz)) {
+          kc->status = PHIX_ENAN;
+          kc->stop = 1;
+        } else {
+          go = 1;
+        }
+      }
+      s_go = go;
+      kc->count = 0;
+    }
+    __syncthreads();
+    // float32 pairs of s_{j+1} (twice), c1, c0 and the b weights: one lane per warp
+    if (s_go && (tid & 31) == 0) {
+      const int k = tid >> 5;
+      if (k < 3 + p) {
+        const float2 f = split2d(sv[k]);
+        if (k == 0) {
+          kc->sf[j + 1] = f;
+          kc->wsf = f;
+        } else if (k == 1) {
+          kc->c1f = f;
+        } else if (k == 2) {
+          kc->c0f = f;
+        } else {
+          kc->buf[k - 3] = f;
+        }
+      }
     }
   }
 }
@@ -1093,6 +1444,40 @@ cudaError_t arn_t(const KiopsSpec& s, int j, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// pass 1 of step 0 into W0, fused steps feeding on it
+template <int P, int OP>
+cudaError_t fused_first_t(const KiopsSpec& s, cudaStream_t st) {
+  static const int occ = blocks_per_sm(reinterpret_cast<const void*>(k_arn1<P, OP, 2>));
+  ArnArgs a = make_arn(s, 0, 2);
+  a.zout = s.W[0];
+  a.fused = 1;
+  k_arn1<P, OP, 2><<<std::min(s.nsm * occ, a.ntiles), dim3(32, TILE_Y), 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int P, int OP>
+cudaError_t fused_step_t(const KiopsSpec& s, int j, cudaStream_t st) {
+  static const int occ = blocks_per_sm(reinterpret_cast<const void*>(k_arnf<P, OP>));
+  ArnArgs a = make_arn(s, j, 2);
+  a.win = s.W[j & 1];
+  a.wout = s.W[(j + 1) & 1];
+  k_arnf<P, OP><<<std::min(s.nsm * occ, a.ntiles), dim3(32, TILE_Y), 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t fused_p(const KiopsSpec& s, int j, bool first, cudaStream_t st) {
+  switch (s.op) {
+    case PHIX_OP_ADVDIFF:
+      return first ? fused_first_t<P, PHIX_OP_ADVDIFF>(s, st) : fused_step_t<P, PHIX_OP_ADVDIFF>(s, j, st);
+    case PHIX_OP_GRAYSCOTT:
+      return first ? fused_first_t<P, PHIX_OP_GRAYSCOTT>(s, st) : fused_step_t<P, PHIX_OP_GRAYSCOTT>(s, j, st);
+    case PHIX_OP_BURGERS:
+      return first ? fused_first_t<P, PHIX_OP_BURGERS>(s, st) : fused_step_t<P, PHIX_OP_BURGERS>(s, j, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
 template <int P>
 cudaError_t arn_p(const KiopsSpec& s, int j, cudaStream_t st) {
   switch (s.op) {
@@ -1110,6 +1495,18 @@ cudaError_t arn_p(const KiopsSpec& s, int j, cudaStream_t st) {
 
 cudaError_t kiops_arnoldi(const KiopsSpec& s, int j, cudaStream_t st) {
   return s.prec == P_FP64 ? arn_p<P_FP64>(s, j, st) : arn_p<P_DF64>(s, j, st);
+}
+
+bool kiops_fused_ok(const KiopsSpec& s) {
+  return s.nx % 64 == 0 && s.ny % TILE_Y == 0 && s.W[0] != nullptr && s.W[1] != nullptr;
+}
+
+cudaError_t kiops_fused_first(const KiopsSpec& s, cudaStream_t st) {
+  return s.prec == P_FP64 ? fused_p<P_FP64>(s, 0, true, st) : fused_p<P_DF64>(s, 0, true, st);
+}
+
+cudaError_t kiops_fused_step(const KiopsSpec& s, int j, cudaStream_t st) {
+  return s.prec == P_FP64 ? fused_p<P_FP64>(s, j, false, st) : fused_p<P_DF64>(s, j, false, st);
 }
 
 cudaError_t small_expm_e1(int n, const double* d, const double* u, const double* l, double tau, double* out,

@@ -237,14 +237,17 @@ __global__ void __launch_bounds__(THREADS) k_iter(IterDev a) {
   }
 
   if (block_partials_and_last<Acc, KMAX + 1>(acc, a.partials, &a.ctl->count)) {
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    // the stop test's coefficients, read before the partials so that their
+    // latency overlaps the reduction
+    double dkd[KMAX];
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) dkd[k] = (MODE == MODE_NEWTON && tid == 0 && k < K) ? dk_d_of(a.ptab, M)[k * M + m] : 0.0;
     double tot[KMAX + 1];
     reduce_partials<Acc, KMAX + 1>(a.partials, tot);
-    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     if (tid == 0) {
       LejaCtl* ctl = a.ctl;
       if (MODE == MODE_NEWTON) {
-        double dkd[KMAX];
-        for (int k = 0; k < K; ++k) dkd[k] = dk_d_of(a.ptab, M)[k * M + m];
         leja_test(ctl, m, K, pp->m_min, pp->m_max, pp->tol, dkd, tot);
       } else {
         // power iteration: y_k = J v_{k-1}, v_{k-1} unit  =>  rho_k = ||y_k||

@@ -149,11 +149,16 @@ __device__ void tma_reduce(const double* partials, double (&tot)[NV], double (*s
     if (lane == 0) sw[warp][j] = v;
   }
   __syncthreads();
+  // the totals in thread 0 only (float64 instructions hold the pipe ~64 cycles per warp)
 #pragma unroll
-  for (int j = 0; j < NV; ++j) {
-    double t = 0.0;
-    for (int w = 0; w < TT / 32; ++w) t += sw[w][j];
-    tot[j] = t;
+  for (int j = 0; j < NV; ++j) tot[j] = 0.0;
+  if (tid == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      double t = 0.0;
+      for (int w = 0; w < TT / 32; ++w) t += sw[w][j];
+      tot[j] = t;
+    }
   }
 }
 
@@ -398,11 +403,13 @@ __global__ void __launch_bounds__(TT, CTAS_PER_SM) k_iter_tma(const __grid_const
   }
 
   if (tma_partials_and_last<Acc, KMAX + 1>(acc, a.partials, &ctl->count, sw)) {
+    // the stop test's coefficients, read before the partials
+    double dkd[KMAX];
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) dkd[k] = (tid == 0 && k < K) ? dk_d_of(a.ptab, M)[k * M + m] : 0.0;
     double tot[KMAX + 1];
     tma_reduce<KMAX + 1>(a.partials, tot, sw);
     if (tid == 0) {
-      double dkd[KMAX];
-      for (int k = 0; k < K; ++k) dkd[k] = dk_d_of(a.ptab, M)[k * M + m];
       leja_test(ctl, m, K, pp->m_min, pp->m_max, pp->tol, dkd, tot);
       ctl->m = m + 1;
       ctl->count = 0;

@@ -25,7 +25,7 @@ enum Slot {
   S_Y0 = 0, S_Y1, S_P0, S_P1, S_P2, S_P3, S_ST,                 // Newton pass
   S_F, S_A, S_B, S_RA, S_RB, S_T0, S_Q, S_T3, S_T4, S_O1, S_O2, S_O3,  // stages
   S_SUB_U, S_SUB_TMP, S_SUB_W0,                                  // substeps (W0..W0+8)
-  S_KBASIS = S_SUB_W0 + 9, S_KB, S_KPTR, S_KCTL, S_KMODE,                       // KIOPS basis, b copies, slot table, control
+  S_KBASIS = S_SUB_W0 + 9, S_KB, S_KPTR, S_KCTL, S_KMODE, S_KW,                 // KIOPS basis, b copies, slot table, control, scratch
   S_ST2,                                                         // Gray-Scott state planes scaled for Newton passes
   S_BPROB, S_BORDER, S_BWS, S_BQ, S_XI,                          // batched problems, order, arena, queue, Leja points
   S_MFEAT, S_MY, S_MG, S_MCNT,                                   // learned interval: features, outputs, gradient
@@ -751,6 +751,12 @@ void kiops_run(phix_ctx* ctx, const OpState& os, int prec, double h, const doubl
   ks.nscaled = n_scaled(os.d.kind);
   ks.grid = ctx->grid_iter;
   ks.nsm = ctx->nsm;
+  ks.W[0] = ks.W[1] = nullptr;
+  if (o.kiops_fused) {
+    ks.W[0] = ws(ctx, S_KW, 2 * N * eb);
+    ks.W[1] = static_cast<unsigned char*>(ks.W[0]) + N * eb;
+  }
+  const bool fused = kiops_fused_ok(ks);
   // b_j (j >= 1) copies in the iteration precision and their 1-norms -> eta
   int nb = 0;
   for (int j = 1; j <= p; ++j)
@@ -789,7 +795,12 @@ void kiops_run(phix_ctx* ctx, const OpState& os, int prec, double h, const doubl
   // the orthogonalisation reads w, z_j, z_{j-1} and writes w back
   const size_t sbytes = os.d.kind == PHIX_OP_GRAYSCOTT ? 2 * os.plane * eb
                        : os.d.kind == PHIX_OP_BURGERS ? os.plane * eb : 0;
-  const double step_bytes = (double)N * eb * (7.0 + nb) + (double)sbytes;
+  // fused steps: read W, Zhat_j, Zhat_{j-1}, the state and the b copies, write
+  // Zhat_{j+1} and u; the pass 1 of step 0 that starts them reads Zhat_0, the
+  // state and the b copies and writes W0
+  const double step_bytes = fused ? (double)N * eb * (5.0 + nb) + (double)sbytes
+                                  : (double)N * eb * (7.0 + nb) + (double)sbytes;
+  const double first_bytes = (double)N * eb * (2.0 + nb) + (double)sbytes;
   KL(kiops_start(ks, b[0], eta, cscale, ctx->stream));
   read_kc(ctx, kc);
   stats.passes += 1;
@@ -816,10 +827,21 @@ void kiops_run(phix_ctx* ctx, const OpState& os, int prec, double h, const doubl
     for (;;) {
       const bool prof = o.profile != 0 && m > built;
       if (prof) CK(cudaEventRecord(ctx->ev[2 * NSLOT], ctx->stream));
+      int launched = 0;
       for (int j = built; j < m; ++j) {
-        ctx->launches += 2;
-        CK(kiops_arnoldi(ks, j, ctx->stream));
+        if (fused) {
+          if (j == 0) {
+            CK(kiops_fused_first(ks, ctx->stream));
+            ++launched;
+          }
+          CK(kiops_fused_step(ks, j, ctx->stream));
+          ++launched;
+        } else {
+          CK(kiops_arnoldi(ks, j, ctx->stream));
+          launched += 2;
+        }
       }
+      ctx->launches += launched;
       if (prof) CK(cudaEventRecord(ctx->ev[2 * NSLOT + 1], ctx->stream));
       KL(kiops_smallexp(kc, m, tau, tau_end, tol, ctx->stream));
       read_kc(ctx, kc);
@@ -832,8 +854,8 @@ void kiops_run(phix_ctx* ctx, const OpState& os, int prec, double h, const doubl
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, ctx->ev[2 * NSLOT], ctx->ev[2 * NSLOT + 1]));
         stats.iter_ms += ms;
-        stats.iter_launches += 2 * steps;
-        stats.iter_bytes += steps * step_bytes;
+        stats.iter_launches += launched;
+        stats.iter_bytes += steps * step_bytes + (fused && built == 0 && steps > 0 ? first_bytes : 0.0);
       }
       if (H.status == PHIX_ENAN || !std::isfinite(H.omega)) fail(ctx, PHIX_ENAN, "KIOPS produced a non-finite value");
       built = m;
@@ -942,6 +964,7 @@ phix_opts resolve_opts(phix_ctx* ctx, const phix_opts* in) {
   if (o.kernel < PHIX_KERNEL_AUTO || o.kernel > PHIX_KERNEL_TMA) fail(ctx, PHIX_EINVAL, "unknown kernel %d", o.kernel);
   if (o.profile < 0 || o.profile > 2) fail(ctx, PHIX_EINVAL, "profile must be 0, 1 or 2");
   if (o.kiops_m_max < 2 || o.kiops_m_max > 128) fail(ctx, PHIX_EINVAL, "kiops_m_max must be in 2..128");
+  if (o.kiops_fused != 0 && o.kiops_fused != 1) fail(ctx, PHIX_EINVAL, "kiops_fused must be 0 or 1");
   return o;
 }
 
@@ -1016,6 +1039,7 @@ void phix_opts_default(phix_opts* o) {
   o->kiops_m_max = 64;
   o->kiops_m_step = 8;
   o->kiops_max_substeps = 10000;
+  o->kiops_fused = 1;
 }
 
 phix_status phix_create(phix_ctx** out, void* stream) {

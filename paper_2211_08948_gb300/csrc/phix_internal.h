@@ -164,6 +164,12 @@ struct KiopsCtl {
   // coefficients of the next pass-2 launch: z' = z - c1 Zhat_j - c0 Zhat_{j-1}
   double c1d, c0d;
   float2 c1f, c0f;
+  // fused steps: Zhat_{j+1} = ws W - c1 Zhat_j - c0 Zhat_{j-1}, then
+  // u = A~ [Zhat_{j+1}; tail_{j+1}] unscaled (k h, ga = h, b-column weights eta tail_{j+1})
+  double wsd;
+  float2 wsf;
+  double kud[8], gud, bud[KIOPS_PMAX];
+  float2 kuf[8], guf, buf[KIOPS_PMAX];
 };
 constexpr size_t KIOPS_HOST_BYTES = 40;  // leading fields the host reads back
 
@@ -182,6 +188,7 @@ struct KiopsSpec {
   int nscaled;
   int grid;                     // streaming kernels (combine, start)
   int nsm;                      // SMs (the Arnoldi kernels size their grids by occupancy)
+  void* W[2];                   // fused steps: scratch vectors (pass-1 results)
 };
 // w_0 = c [b_0; e_p / eta] (c a power of two): Zhat_0 = c b_0 (or 0), tail_0 = c e_p / eta,
 // s_0 = 1/||w_0||, next pass-1 coefficients.
@@ -191,6 +198,13 @@ cudaError_t kiops_convert(int prec, size_t n, const double* b, void* out, double
                           unsigned int* counter, double* norm1, int grid, cudaStream_t st);
 // Arnoldi step j: pass 1 (z = A~ V_j, dots) and pass 2 (orthogonalise, norm).
 cudaError_t kiops_arnoldi(const KiopsSpec& s, int j, cudaStream_t st);
+// Fused Arnoldi steps on tile-aligned grids: kiops_fused_first(s) runs pass 1 of
+// step 0 into the scratch vector W0; kiops_fused_step(s, j) completes step j
+// (Zhat_{j+1} from W, its norm) and runs pass 1 of step j + 1 (u = A~ Zhat_{j+1}
+// into the other scratch vector, its dot products).  W0/W1 alternate.
+bool kiops_fused_ok(const KiopsSpec& s);
+cudaError_t kiops_fused_first(const KiopsSpec& s, cudaStream_t st);
+cudaError_t kiops_fused_step(const KiopsSpec& s, int j, cudaStream_t st);
 // F = exp(tau Hbar) e_1 (n = m+1, or m after a happy breakdown), err, omega.
 cudaError_t kiops_smallexp(KiopsCtl* kc, int m, double tau, double tau_end, double tol, cudaStream_t st);
 // out = exp(tau T) e_1 for a tridiagonal T (device arrays d[n], u[n-1], l[n-1]); mode: 0 Chebyshev, 1 Taylor

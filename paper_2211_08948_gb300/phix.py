@@ -46,7 +46,7 @@ class phix_opts(ctypes.Structure):
                 ("power_rel", ctypes.c_double), ("power_seed", ctypes.c_uint64),
                 ("kiops_m_init", ctypes.c_int), ("kiops_m_max", ctypes.c_int),
                 ("kiops_m_step", ctypes.c_int), ("kiops_max_substeps", ctypes.c_int),
-                ("profile", ctypes.c_int), ("kernel", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("kernel", ctypes.c_int), ("kiops_fused", ctypes.c_int)]
 
 
 class phix_batch_problem(ctypes.Structure):
