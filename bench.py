@@ -37,7 +37,7 @@ WORKLOAD = "Gray-Scott 1024x1024x2, EXPRB43 steps, h=100x explicit limit, Leja, 
 # DRAM bytes (read + write) of one launch of the dominant kernel, from an ncu --set full capture
 # of this configuration (k_iter, a K = 2 launch, cold caches); null for configurations without a
 # capture of the current kernel.
-TRAFFIC = {}
+TRAFFIC = {("leja", 1024, "DF64"): 67.18e6 + 9.53e6}
 
 
 def parse():
@@ -273,7 +273,7 @@ def run_phix(args, world, rank, local):
         "roofline": {
             "bound": "hbm",
             "kernel": ("k_iter (Newton-Leja step; CUDA events around each pass's WHILE loop)" if args.method == "leja"
-                       else "k_arn1 + k_arn2 (Arnoldi step; CUDA events around each run of steps)"),
+                       else "k_arnf (fused Arnoldi step; k_arn1 + k_arn2 on grids of partial tiles; CUDA events around each run of steps)"),
             "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None,
             "traffic": TRAFFIC.get((args.method, n, args.prec)),
