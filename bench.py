@@ -36,8 +36,8 @@ WORKLOAD = "Gray-Scott 1024x1024x2, EXPRB43 steps, h=100x explicit limit, Leja, 
 
 # DRAM bytes (read + write) of one launch of the dominant kernel, from an ncu --set full capture
 # of this configuration (k_iter, a K = 2 launch, cold caches); null for configurations without a
-# capture of the current kernel.
-TRAFFIC = {("leja", 1024, "DF64"): 67.18e6 + 9.53e6}
+# capture of the current kernel.  Keyed by (method, n, precision, Newton kernel).
+TRAFFIC = {("leja", 1024, "DF64", "single"): 67.18e6 + 9.53e6}
 
 
 def parse():
@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--clock-ms", type=int, default=100, help="nvidia-smi sampling period (0 = off)")
     ap.add_argument("--method", default="leja", choices=["leja", "kiops"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "single", "tma"],
+                    help="Newton-step kernel of the Leja path (auto: TMA-staged once an iteration exceeds L2)")
     ap.add_argument("--direct-launch", action="store_true",
                     help="launch every iteration kernel on its own (for ncu, which does not see into "
                          "conditional graphs); not a bench measurement")
@@ -167,7 +169,9 @@ def run_phix(args, world, rank, local):
     N = u0.size
     op = phix.make_jop(phix.PHIX_OP_GRAYSCOTT, n, n, [prm["Du"], prm["Dv"], prm["F"], prm["k"]])
     prec = getattr(phix, "PHIX_" + args.prec)
-    opts = phix.phix_opts_default(prec=prec, profile=2 if args.direct_launch else 1)
+    opts = phix.phix_opts_default(prec=prec, profile=2 if args.direct_launch else 1,
+                                  kernel={"auto": phix.PHIX_KERNEL_AUTO, "single": phix.PHIX_KERNEL_SINGLE,
+                                          "tma": phix.PHIX_KERNEL_TMA}[args.kernel])
     meth = phix.PHIX_KIOPS if args.method == "kiops" else phix.PHIX_LEJA
     tol = 1e-8
     h = prm["h"]
@@ -260,7 +264,8 @@ def run_phix(args, world, rank, local):
         "data": "synthetic (seeded Gray-Scott initial state, seed = rank)",
         "config": {"workload": WORKLOAD if args.method == "leja" else WORKLOAD.replace("Leja", "KIOPS"),
                    "grid": [n, n], "species": 2, "unknowns": N, "h": h, "tol": tol,
-                   "method": args.method, "prec": args.prec, "parallelism": "replicas" if world > 1 else "single",
+                   "method": args.method, "prec": args.prec, "kernel": args.kernel,
+                   "parallelism": "replicas" if world > 1 else "single",
                    "l2": "flushed between steps (256 MB write, inside the timed region)"},
         "time_steps_per_s": args.steps * world / (ms * 1e-3),
         "hbm_gbs_iteration_algorithmic": achieved,
@@ -272,11 +277,14 @@ def run_phix(args, world, rank, local):
         "e2e": e2e,
         "roofline": {
             "bound": "hbm",
-            "kernel": ("k_iter (Newton-Leja step; CUDA events around each pass's WHILE loop)" if args.method == "leja"
+            "kernel": (("k_iter_tma (TMA-staged Newton-Leja step" if sum(s.get("tma_passes", 0) for s in stats) > 0
+                        else "k_iter (Newton-Leja step") + "; CUDA events around each pass's WHILE loop)"
+                       if args.method == "leja"
                        else "k_arnf (fused Arnoldi step; k_arn1 + k_arn2 on grids of partial tiles; CUDA events around each run of steps)"),
             "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None,
-            "traffic": TRAFFIC.get((args.method, n, args.prec)),
+            "traffic": TRAFFIC.get((args.method, n, args.prec, "tma" if sum(s.get("tma_passes", 0) for s in stats) > 0
+                                    else "single")),
             "launches": iter_launches,
             "avg_launch_us": 1e3 * iter_ms / max(1, iter_launches),
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback",
