@@ -228,8 +228,9 @@ struct NoHook {
 };
 // `hook` runs in every thread just before the block barrier (work that the
 // caller wants overlapped with the partials' latency and published by it).
+// `nv` <= NV: only the first nv totals are formed (the others are returned as 0).
 template <typename A, int NV, typename H = NoHook>
-__device__ void reduce_partials(const double* partials, double (&tot)[NV], H hook = H{}) {
+__device__ void reduce_partials(const double* partials, double (&tot)[NV], H hook = H{}, int nv = NV) {
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   if constexpr (PartialsDF<A>::value) {
     constexpr int NW = THREADS / 32;
@@ -246,17 +247,19 @@ __device__ void reduce_partials(const double* partials, double (&tot)[NV], H hoo
         const int b = b0 + q * THREADS;
 #pragma unroll
         for (int j = 0; j < NV; ++j)
-          v[q][j] = b < (int)gridDim.x ? __ldcg(pf + (size_t)b * (KMAX + 1) + j) : make_float2(0.f, 0.f);
+          v[q][j] = (b < (int)gridDim.x && j < nv) ? __ldcg(pf + (size_t)b * (KMAX + 1) + j) : make_float2(0.f, 0.f);
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q)
 #pragma unroll
-        for (int j = 0; j < NV; ++j) s[j] = df_add(s[j], cv(v[q][j]));
+        for (int j = 0; j < NV; ++j)
+          if (j < nv) s[j] = df_add(s[j], cv(v[q][j]));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-      for (int j = 0; j < NV; ++j) s[j] = df_add(s[j], shfl_down(s[j], o));
+      for (int j = 0; j < NV; ++j)
+        if (j < nv) s[j] = df_add(s[j], shfl_down(s[j], o));
     if (lane == 0)
 #pragma unroll
       for (int j = 0; j < NV; ++j) swarp[warp][j] = make_float2(s[j].hi, s[j].lo);
@@ -270,11 +273,13 @@ __device__ void reduce_partials(const double* partials, double (&tot)[NV], H hoo
 #pragma unroll
       for (int o = NW / 2; o > 0; o >>= 1)
 #pragma unroll
-        for (int j = 0; j < NV; ++j) s[j] = df_add(s[j], shfl_down(s[j], o));
+        for (int j = 0; j < NV; ++j)
+          if (j < nv) s[j] = df_add(s[j], shfl_down(s[j], o));
       // float64 work in one thread only (a warp's float64 instruction holds the pipe ~64 cycles)
       if (lane == 0)
 #pragma unroll
-        for (int j = 0; j < NV; ++j) tot[j] = (double)s[j].hi + (double)s[j].lo;
+        for (int j = 0; j < NV; ++j)
+          if (j < nv) tot[j] = (double)s[j].hi + (double)s[j].lo;
     }
   } else {
     __shared__ double sfin[THREADS][KMAX + 1];

@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(THREADS) k_iter(IterDev a) {
 #pragma unroll
     for (int k = 0; k < KMAX; ++k) dkd[k] = (MODE == MODE_NEWTON && tid == 0 && k < K) ? dk_d_of(a.ptab, M)[k * M + m] : 0.0;
     double tot[KMAX + 1];
-    reduce_partials<Acc, KMAX + 1>(a.partials, tot);
+    reduce_partials<Acc, KMAX + 1>(a.partials, tot, NoHook{}, MODE == MODE_NEWTON ? K + 1 : 1);
     if (tid == 0) {
       LejaCtl* ctl = a.ctl;
       if (MODE == MODE_NEWTON) {
@@ -274,8 +274,9 @@ __global__ void __launch_bounds__(THREADS) k_iter(IterDev a) {
       }
       ctl->m = m + 1;
       ctl->count = 0;
+      // no fence: the next launch, the loop condition and the host's copy all
+      // follow the kernel's completion
       if (ctl->done) stop_loop(a);
-      __threadfence();
     }
   }
 }

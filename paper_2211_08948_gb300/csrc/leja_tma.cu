@@ -413,8 +413,9 @@ __global__ void __launch_bounds__(TT, CTAS_PER_SM) k_iter_tma(const __grid_const
       leja_test(ctl, m, K, pp->m_min, pp->m_max, pp->tol, dkd, tot);
       ctl->m = m + 1;
       ctl->count = 0;
+      // no fence: the next launch, the loop condition and the host's copy all
+      // follow the kernel's completion
       if (ctl->done && a.use_cond) cudaGraphSetConditional(a.cond, 0);
-      __threadfence();
     }
   }
 }
