@@ -59,7 +59,9 @@ struct Shared {
   double beta[BM];    // shifts beta_m = -(c/gamma + xi_{m-1})
   float2 betaf[BM];
   double red[NWARP][4];
+  float2 redf[NWARP][4];
   double tot[4];
+  int flag;  // stop decision of the iteration, from thread 0
 };
 
 struct Prob {
@@ -100,25 +102,59 @@ __device__ void dd_block(int l, double a, double b, const double* xi, int M, dou
   __syncthreads();
 }
 
-template <int NV>
-__device__ void block_sum(double (&v)[NV], Shared& sh, int tid) {
+// Block totals of the first nv accumulators, valid in thread 0 (float64).
+// Float and double-float accumulators are reduced as double-float on float32
+// shuffles, float64 ones on float64 shuffles; the float64 totals are formed by
+// one thread only (float64 issues at 1/64 of the float32 rate, so a per-thread
+// float64 tail per iteration outweighs the stencil work of a small problem).
+template <typename Acc>
+__device__ void block_tot(const Acc (&ac)[4], int nv, Shared& sh, int tid, double (&tot)[4]) {
   const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
-  for (int j = 0; j < NV; ++j) {
-    double x = v[j];
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-    if (lane == 0) sh.red[warp][j] = x;
-  }
-  __syncthreads();
-  if (tid < NV) {
-    double s = 0.0;
-    for (int w = 0; w < NWARP; ++w) s += sh.red[w][tid];
-    sh.tot[tid] = s;
-  }
-  __syncthreads();
+  for (int j = 0; j < 4; ++j) tot[j] = 0.0;
+  if constexpr (std::is_same<Acc, double>::value) {
 #pragma unroll
-  for (int j = 0; j < NV; ++j) v[j] = sh.tot[j];
-  __syncthreads();
+    for (int j = 0; j < 4; ++j) {
+      if (j < nv) {
+        double x = ac[j];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) sh.red[warp][j] = x;
+      }
+    }
+    __syncthreads();
+    if (tid == 0)
+      for (int j = 0; j < nv; ++j) {
+        double t = 0.0;
+        for (int w = 0; w < NWARP; ++w) t += sh.red[w][j];
+        tot[j] = t;
+      }
+  } else {
+    df s[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) s[j] = acc_to_df(ac[j]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (j < nv) s[j] = df_add(s[j], shfl_down(s[j], o));
+    if (lane == 0)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) sh.redf[warp][j] = make_float2(s[j].hi, s[j].lo);
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) s[j] = lane < NWARP ? cv(sh.redf[lane][j]) : df_make(0.f, 0.f);
+#pragma unroll
+      for (int o = NWARP / 2; o > 0; o >>= 1)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (j < nv) s[j] = df_add(s[j], shfl_down(s[j], o));
+      if (lane == 0)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (j < nv) tot[j] = (double)s[j].hi + (double)s[j].lo;
+    }
+  }
 }
 
 // J y at (r, c) of the periodic advection-diffusion stencil, coefficients k = {E, W, N, S, C}
@@ -167,8 +203,7 @@ __device__ int block_pass(const BArgs& a, int nx, int ny, const typename Tr<P>::
           acc_sq(ac[1 + k], pv);
         }
       }
-    double t[4] = {acc_to_double(ac[0]), acc_to_double(ac[1]), acc_to_double(ac[2]), acc_to_double(ac[3])};
-    block_sum<4>(t, sh, tid);
+    __syncthreads();  // y_0 and p_k written before the first iteration reads them
   }
   const int m_max = a.m_max;
   for (int m = 1; m <= m_max; ++m) {
@@ -199,20 +234,28 @@ __device__ int block_pass(const BArgs& a, int nx, int ny, const typename Tr<P>::
           acc_sq(ac[1 + k], pv);
         }
       }
-    double t[4] = {acc_to_double(ac[0]), acc_to_double(ac[1]), acc_to_double(ac[2]), acc_to_double(ac[3])};
-    block_sum<4>(t, sh, tid);  // also orders this iteration's writes before the next reads
-    const double ny2 = sqrt(t[0]);
-    bool finite = isfinite(ny2), conv = (m >= a.m_min);
-    for (int k = 0; k < K; ++k) {
-      const double np = sqrt(t[1 + k]);
-      finite = finite && isfinite(np);
-      conv = conv && (fabs(sh.dd[k][m]) * ny2 <= a.tol * np);
+    double t[4];
+    block_tot<Acc>(ac, K + 1, sh, tid, t);  // its barrier orders this iteration's writes before the next reads
+    // stop test (Sec. 2.2) |d_k[m]| ||y_m|| <= tol ||p_k|| on the squares, in thread 0
+    if (tid == 0) {
+      const double ny2 = t[0], tol2 = a.tol * a.tol;
+      bool finite = isfinite(ny2), conv = (m >= a.m_min);
+      for (int k = 0; k < K; ++k) {
+        const double np2 = t[1 + k], d = sh.dd[k][m];
+        finite = finite && isfinite(np2);
+        conv = conv && (d * d * ny2 <= tol2 * np2);
+      }
+      sh.flag = !finite ? 2 : (conv ? 1 : 0);
     }
-    if (!finite) {
+    __syncthreads();  // also: warp 0 has read the shared partials before they are rewritten
+    // every thread reads the flag before the next iteration's reduction barrier,
+    // after which thread 0 rewrites it
+    const int flag = sh.flag;
+    if (flag == 2) {
       *iters = m;
       return PHIX_ENAN;
     }
-    if (conv) {
+    if (flag == 1) {
       *iters = m;
       return PHIX_OK;
     }
