@@ -7,13 +7,17 @@
 //
 // The basis is kept unnormalised, V_i = s_i Zhat_i; the N part of Zhat_i is
 // stored in the iteration precision (float64 or double-float), the p tail
-// entries in float64 inside the control block.  Each Arnoldi step is two
-// grid passes:
+// entries in float64 inside the control block.  An Arnoldi step has two grid
+// passes with a reduction between them (the two inner products per step that
+// incomplete orthogonalisation leaves, Sec. 2.1):
 //   pass 1: z = A~ V_j (5-point stencil + the eta b columns), partial dots
 //           <Zhat_j, z>, <Zhat_{j-1}, z> and ||z||^2;
 //   pass 2: z <- z - h_jj V_j - h_{j-1,j} V_{j-1} in place, partial ||z||^2;
 // the last block of each pass adds the tail terms, forms h_jj, h_{j-1,j},
-// h_{j+1,j}, s_{j+1} and writes the coefficients of the next launch.
+// h_{j+1,j}, s_{j+1} and writes the coefficients of the next launch.  On grids
+// of whole 64 x 8 tiles, pass 2 of step j and pass 1 of step j + 1 run as one
+// launch (k_arnf): the orthogonalised vector is staged in shared memory with a
+// one-point halo ring and the stencil of the next step reads it there.
 #include <algorithm>
 #include "iter_common.cuh"
 
@@ -332,7 +336,8 @@ __global__ void __launch_bounds__(THREADS) k_arn1(ArnArgs a) {
   }
 }
 
-// Fused Arnoldi step j (grids of whole tiles: nx % 64 == 0, ny % TILE_Y == 0).
+// Fused Arnoldi step j of the incomplete orthogonalisation (Sec. 2.1; grids of
+// whole tiles: nx % 64 == 0, ny % TILE_Y == 0).
 // Completes step j: Zhat_{j+1} = ws W - c1 Zhat_j - c0 Zhat_{j-1} (written to
 // slot j + 1 and, with a one-point halo ring recomputed from W, Zhat_j,
 // Zhat_{j-1}, staged in shared memory), and runs pass 1 of step j + 1 from
