@@ -224,14 +224,16 @@ def run_phix(args, world, rank, local):
             dist.barrier()
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
+        # the two pinned buffers alternate: each step's input is the previous
+        # step's result as read back to the host
+        bufs = (hbuf, hout)
         f0.record(stream)
-        for _ in range(args.steps):
+        for k in range(args.steps):
             flush.fill_(1.0)
-            ud.copy_(hbuf, non_blocking=True)
+            ud.copy_(bufs[k & 1], non_blocking=True)
             phix.phix_exprb43_step(ctx, op, ud, h, tol, meth, opts)
-            hout.copy_(ud, non_blocking=True)
-            torch.cuda.current_stream().synchronize()
-            hbuf.copy_(hout)
+            bufs[(k + 1) & 1].copy_(ud, non_blocking=True)
+            torch.cuda.current_stream().synchronize()  # the step's result is on the host
         f1.record(stream)
         torch.cuda.synchronize()
         ems = max_over_ranks(f0.elapsed_time(f1), world, "cuda")

@@ -371,7 +371,11 @@ __global__ void __launch_bounds__(THREADS) k_arnf(ArnArgs a) {
     bw[b] = b < a.nb ? coef<C>(__ldcg(&kc->bud[a.bslot[b]]), __ldcg(&kc->buf[a.bslot[b]])) : C{};
 
   Acc acc[4] = {acc_zero<Acc>(), acc_zero<Acc>(), acc_zero<Acc>(), acc_zero<Acc>()};
-  typename AccSq<Acc>::F uu = 0;
+  // ||Zhat_{j+1}||^2 and <u, u> in float32 on the double-float path: an error d
+  // in ||Zhat_{j+1}|| scales z_{j+1} by 1 + d and h_{j+1,j} by 1/(1 + d), a
+  // diagonal similarity of the Hessenberg matrix that leaves V exp(tau H) e_1
+  // and the error estimate unchanged (and <u, u> only sets a threshold)
+  typename AccSq<Acc>::F zz2 = 0, uu = 0;
   const T* __restrict__ W = static_cast<const T*>(a.win);
   const T* __restrict__ zj = static_cast<const T*>(a.zj);
   const T* __restrict__ zm = static_cast<const T*>(a.zjm1);
@@ -492,7 +496,7 @@ __global__ void __launch_bounds__(THREADS) k_arnf(ArnArgs a) {
 #pragma unroll
       for (int q = 0; q < NC; ++q) {
         u[q][v] = J[q] + zb[q][v];
-        acc_dot(acc[0], zn[q][v], zn[q][v]);
+        zz2 = acc_sq_f(zz2, zn[q][v]);
         acc_dot(acc[1], zn[q][v], u[q][v]);
         acc_dot(acc[2], zc[q][v], u[q][v]);
         uu = acc_sq_f(uu, u[q][v]);
@@ -503,6 +507,7 @@ __global__ void __launch_bounds__(THREADS) k_arnf(ArnArgs a) {
     __syncthreads();  // the staged tile is overwritten by the next tile
   }
 
+  acc[0] = acc_from_f<Acc>(zz2);
   acc[3] = acc_from_f<Acc>(uu);
   if (block_partials_and_last<Acc, 4>(acc, a.partials, &kc->count)) {
     // Epilogue, a chain of float64 scalars on the critical path of every step
@@ -638,6 +643,9 @@ __global__ void __launch_bounds__(THREADS) k_arn2(ArnArgs a, size_t n) {
   const T* __restrict__ zm = static_cast<const T*>(a.zjm1);
   T* __restrict__ zo = static_cast<T*>(a.zout);
   Acc acc[1] = {acc_zero<Acc>()};
+  // ||z||^2 in float32 on the double-float path (the normalisation error is a
+  // diagonal similarity of the Hessenberg matrix: no effect on the result)
+  typename AccSq<Acc>::F zz = 0;
   // element pairs (16-byte accesses; every vector starts 256-byte aligned), two
   // pairs per thread per trip so that six loads are in flight
   const size_t np = n / 2;
@@ -655,14 +663,14 @@ __global__ void __launch_bounds__(THREADS) k_arn2(ArnArgs a, size_t n) {
       z1 = z1 - c0 * b1;
     }
     st2(zo + i, z0, z1);
-    acc_dot(acc[0], z0, z0);
-    acc_dot(acc[0], z1, z1);
+    zz = acc_sq_f(zz, z0);
+    zz = acc_sq_f(zz, z1);
   };
   auto single = [&](size_t i) {
     C z = ldw1(zo + i) - c1 * ldr1(zj + i);
     if (zm) z = z - c0 * ldr1(zm + i);
     st1(zo + i, z);
-    acc_dot(acc[0], z, z);
+    zz = acc_sq_f(zz, z);
   };
   // basis slots lie N elements apart: with N odd every other slot is only
   // 8-byte aligned, and the pairs would be misaligned
@@ -679,6 +687,7 @@ __global__ void __launch_bounds__(THREADS) k_arn2(ArnArgs a, size_t n) {
   } else {
     for (size_t i = t0; i < n; i += stride) single(i);
   }
+  acc[0] = acc_from_f<Acc>(zz);
   if (block_partials_and_last<Acc, 1>(acc, a.partials, &kc->count)) {
     double tot[1];
     reduce_partials<Acc, 1>(a.partials, tot);
