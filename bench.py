@@ -38,7 +38,7 @@ WORKLOAD = "Gray-Scott 1024x1024x2, EXPRB43 steps, h=100x explicit limit, Leja, 
 # of this configuration (k_iter, a K = 2 launch; k_arnf for KIOPS; cold caches); null for configurations without a
 # capture of the current kernel.  Keyed by (method, n, precision, Newton kernel).
 TRAFFIC = {("leja", 1024, "DF64", "single"): 67.18e6 + 9.53e6,
-           ("kiops", 1024, "DF64", "single"): 86.69e6 + 10.23e6}
+           ("kiops", 1024, "DF64", "single"): 86.63e6 + 8.36e6}
 
 
 def parse():

@@ -355,7 +355,9 @@ __global__ void __launch_bounds__(THREADS) k_arnf(ArnArgs a) {
   constexpr int NC = (OP == PHIX_OP_GRAYSCOTT) ? 2 : 1;
   constexpr int TW = 32 * V, SW = TW + 2, NRING = 2 * TW + 2 * TILE_Y;
   static_assert(NRING <= THREADS, "one ring point per thread");
-  __shared__ T sm[NC][TILE_Y + 2][SW];
+  // staged tile, two buffers: one barrier per tile (a buffer is rewritten two
+  // tiles later, after every thread has passed the next tile's barrier)
+  __shared__ T smb[2][NC][TILE_Y + 2][SW];
   KiopsCtl* kc = a.kc;
   if (__ldcg(&kc->stop)) return;
   const C ws = coef<C>(__ldcg(&kc->wsd), __ldcg(&kc->wsf));
@@ -392,6 +394,7 @@ __global__ void __launch_bounds__(THREADS) k_arnf(ArnArgs a) {
   for (int tile = t_begin; tile < t_end; ++tile) {
     const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
     const int iy0 = ty * TILE_Y, ix0 = tx * TW;
+    T (*sm)[TILE_Y + 2][SW] = smb[(tile - t_begin) & 1];
     const int iy = iy0 + threadIdx.y, ix = ix0 + V * threadIdx.x;
     const size_t row = (size_t)iy * nx;
     // own points: W, Zhat_j, Zhat_{j-1}; the ring point; the state and the
@@ -504,7 +507,6 @@ __global__ void __launch_bounds__(THREADS) k_arnf(ArnArgs a) {
     }
 #pragma unroll
     for (int q = 0; q < NC; ++q) st2(uo + q * plane + row + ix, u[q][0], u[q][1]);
-    __syncthreads();  // the staged tile is overwritten by the next tile
   }
 
   acc[0] = acc_from_f<Acc>(zz2);
