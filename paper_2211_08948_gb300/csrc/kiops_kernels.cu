@@ -76,6 +76,31 @@ __device__ __forceinline__ void rsqrt_and_sqrt(double x, double& r, double& s) {
   }
 }
 
+// Asynchronous global -> shared copies (cp.async): 16-byte (L2 only) and
+// 8-byte forms, the commit and the wait for all of this thread's groups.
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// two adjacent values from shared memory as one 16-byte word (p 16-byte aligned)
+__device__ __forceinline__ void lds2(const double* p, double& a, double& b) {
+  const double2 t = *reinterpret_cast<const double2*>(p);
+  a = t.x;
+  b = t.y;
+}
+__device__ __forceinline__ void lds2(const float2* p, df& a, df& b) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  a = df_make(t.x, t.y);
+  b = df_make(t.z, t.w);
+}
+
 // a value in its storage form (float64, or the two float32 parts)
 __device__ __forceinline__ double stv(double v) { return v; }
 __device__ __forceinline__ float2 stv(df v) { return make_float2(v.hi, v.lo); }
@@ -85,6 +110,7 @@ struct KTr;
 template <>
 struct KTr<P_FP64> {
   using T = double;
+  using T2 = double2;
   using C = double;
   using S = double;
   using Acc = double;
@@ -92,6 +118,7 @@ struct KTr<P_FP64> {
 template <>
 struct KTr<P_DF64> {
   using T = float2;
+  using T2 = float4;
   using C = df;
   using S = float2;
   using Acc = df;
@@ -336,6 +363,17 @@ __global__ void __launch_bounds__(THREADS) k_arn1(ArnArgs a) {
   }
 }
 
+// shared-memory layout of the fused step: the two staged-tile buffers, then the
+// per-thread prefetch stage (pairs of W, Zhat_j, Zhat_{j-1}, the state planes
+// and nb b-copies; the ring point's three values)
+constexpr int ARNF_TW = 64, ARNF_SW = ARNF_TW + 2, ARNF_NRING = 2 * ARNF_TW + 2 * TILE_Y;
+__host__ __device__ constexpr int arnf_tile_bytes(int nc, int elem) {
+  return ((2 * nc * (TILE_Y + 2) * ARNF_SW * elem + 15) / 16) * 16;
+}
+__host__ __device__ constexpr int arnf_smem_bytes(int nc, int ng, int nb, int elem) {
+  return arnf_tile_bytes(nc, elem) + (3 * nc + ng + nb * nc) * THREADS * 2 * elem + 3 * nc * ARNF_NRING * elem;
+}
+
 // Fused Arnoldi step j of the incomplete orthogonalisation (Sec. 2.1; grids of
 // whole tiles: nx % 64 == 0, ny % TILE_Y == 0).
 // Completes step j: Zhat_{j+1} = ws W - c1 Zhat_j - c0 Zhat_{j-1} (written to
@@ -355,9 +393,22 @@ __global__ void __launch_bounds__(THREADS) k_arnf(ArnArgs a) {
   constexpr int NC = (OP == PHIX_OP_GRAYSCOTT) ? 2 : 1;
   constexpr int TW = 32 * V, SW = TW + 2, NRING = 2 * TW + 2 * TILE_Y;
   static_assert(NRING <= THREADS, "one ring point per thread");
-  // staged tile, two buffers: one barrier per tile (a buffer is rewritten two
-  // tiles later, after every thread has passed the next tile's barrier)
-  __shared__ T smb[2][NC][TILE_Y + 2][SW];
+  static_assert(TW == ARNF_TW && SW == ARNF_SW && NRING == ARNF_NRING, "layout of arnf_smem_bytes");
+  // Dynamic shared memory: the staged tile (two buffers, one barrier per tile:
+  // a buffer is rewritten two tiles later, after every thread has passed the
+  // next tile's barrier), then each thread's prefetch stage (see below).
+  extern __shared__ __align__(16) unsigned char dsm[];
+  using T2 = typename KTr<P>::T2;  // a pair of values, 16 bytes
+  constexpr int NG = (OP == PHIX_OP_GRAYSCOTT) ? 2 : 0;  // state planes staged per point pair
+  T (*smb)[NC][TILE_Y + 2][SW] = reinterpret_cast<T (*)[NC][TILE_Y + 2][SW]>(dsm);
+  T2* stW = reinterpret_cast<T2*>(dsm + arnf_tile_bytes(NC, (int)sizeof(T)));
+  T2* stZ = stW + NC * THREADS;
+  T2* stM = stZ + NC * THREADS;
+  T2* stG = stM + NC * THREADS;
+  T2* stB = stG + NG * THREADS;
+  T* rgW = reinterpret_cast<T*>(stB + a.nb * NC * THREADS);
+  T* rgZ = rgW + NC * NRING;
+  T* rgM = rgZ + NC * NRING;
   KiopsCtl* kc = a.kc;
   if (__ldcg(&kc->stop)) return;
   const C ws = coef<C>(__ldcg(&kc->wsd), __ldcg(&kc->wsf));
@@ -391,22 +442,70 @@ __global__ void __launch_bounds__(THREADS) k_arnf(ArnArgs a) {
 
   const int t_begin = (int)(((long long)blockIdx.x * a.ntiles) / gridDim.x);
   const int t_end = (int)(((long long)(blockIdx.x + 1) * a.ntiles) / gridDim.x);
+  // the ring point of this thread (tid < NRING): its staged-tile row and column
+  int rr = 0, rc = 0;
+  if (tid < TW) {  // south row
+    rr = 0;
+    rc = tid + 1;
+  } else if (tid < 2 * TW) {  // north row
+    rr = TILE_Y + 1;
+    rc = tid - TW + 1;
+  } else if (tid < 2 * TW + TILE_Y) {  // west column
+    rr = tid - 2 * TW + 1;
+    rc = 0;
+  } else if (tid < NRING) {  // east column
+    rr = tid - 2 * TW - TILE_Y + 1;
+    rc = TW + 1;
+  }
+  // Prefetch stage: every thread copies (cp.async) exactly the values it will
+  // read itself — its point pairs of W, Zhat_j, Zhat_{j-1}, the state planes
+  // and the b-copies, and its ring point — so the stage needs no barrier; the
+  // copies of tile k+1 are requested once tile k's staged values are consumed
+  // and arrive while tile k is computed.
+  auto prefetch = [&](int tile) {
+    const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+    const int iy0 = ty * TILE_Y, ix0 = tx * TW;
+    const size_t row = (size_t)(iy0 + threadIdx.y) * nx;
+    const int ix = ix0 + V * threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      const size_t i0 = q * plane + row + ix;
+      cp_async16(stW + q * THREADS + tid, W + i0);
+      cp_async16(stZ + q * THREADS + tid, zj + i0);
+      if (zm) cp_async16(stM + q * THREADS + tid, zm + i0);
+#pragma unroll
+      for (int bq = 0; bq < KIOPS_PMAX; ++bq)
+        if (bq < a.nb) cp_async16(stB + (bq * NC + q) * THREADS + tid, static_cast<const T*>(a.bz[bq]) + i0);
+    }
+#pragma unroll
+    for (int g = 0; g < NG; ++g) cp_async16(stG + g * THREADS + tid, st + g * plane + row + ix);
+    if (tid < NRING) {
+      const int gy = (iy0 + rr - 1 + ny) % ny, gx = (ix0 + rc - 1 + nx) % nx;
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        const size_t gq = q * plane + (size_t)gy * nx + gx;
+        cp_async8(rgW + q * NRING + tid, W + gq);
+        cp_async8(rgZ + q * NRING + tid, zj + gq);
+        if (zm) cp_async8(rgM + q * NRING + tid, zm + gq);
+      }
+    }
+    cp_async_commit();
+  };
+  if (t_begin < t_end) prefetch(t_begin);
   for (int tile = t_begin; tile < t_end; ++tile) {
     const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
     const int iy0 = ty * TILE_Y, ix0 = tx * TW;
     T (*sm)[TILE_Y + 2][SW] = smb[(tile - t_begin) & 1];
     const int iy = iy0 + threadIdx.y, ix = ix0 + V * threadIdx.x;
     const size_t row = (size_t)iy * nx;
-    // own points: W, Zhat_j, Zhat_{j-1}; the ring point; the state and the
-    // augmented columns (every load of the tile issued before its arithmetic)
+    cp_async_wait_all();  // this thread's copies of the tile have landed
     C wv[NC][V], zc[NC][V], mv[NC][V], zb[NC][V];
 #pragma unroll
     for (int q = 0; q < NC; ++q) {
-      const size_t i0 = q * plane + row + ix;
-      ldr2(W + i0, wv[q][0], wv[q][1]);
-      ldr2(zj + i0, zc[q][0], zc[q][1]);
+      lds2(reinterpret_cast<const T*>(stW + q * THREADS + tid), wv[q][0], wv[q][1]);
+      lds2(reinterpret_cast<const T*>(stZ + q * THREADS + tid), zc[q][0], zc[q][1]);
       if (zm) {
-        ldr2(zm + i0, mv[q][0], mv[q][1]);
+        lds2(reinterpret_cast<const T*>(stM + q * THREADS + tid), mv[q][0], mv[q][1]);
       } else {
         mv[q][0] = C{};
         mv[q][1] = C{};
@@ -417,41 +516,29 @@ __global__ void __launch_bounds__(THREADS) k_arnf(ArnArgs a) {
       for (int bq = 0; bq < KIOPS_PMAX; ++bq) {
         if (bq < a.nb) {
           C b0, b1;
-          ldr2(static_cast<const T*>(a.bz[bq]) + i0, b0, b1);
+          lds2(reinterpret_cast<const T*>(stB + (bq * NC + q) * THREADS + tid), b0, b1);
           zb[q][0] = zb[q][0] + bw[bq] * b0;
           zb[q][1] = zb[q][1] + bw[bq] * b1;
         }
       }
     }
-    int rr = 0, rc = 0;
     C rv[NC];
     if (tid < NRING) {
-      if (tid < TW) {  // south row
-        rr = 0;
-        rc = tid + 1;
-      } else if (tid < 2 * TW) {  // north row
-        rr = TILE_Y + 1;
-        rc = tid - TW + 1;
-      } else if (tid < 2 * TW + TILE_Y) {  // west column
-        rr = tid - 2 * TW + 1;
-        rc = 0;
-      } else {  // east column
-        rr = tid - 2 * TW - TILE_Y + 1;
-        rc = TW + 1;
-      }
-      const int gy = (iy0 + rr - 1 + ny) % ny, gx = (ix0 + rc - 1 + nx) % nx;
 #pragma unroll
-      for (int q = 0; q < NC; ++q) {
-        const size_t g = q * plane + (size_t)gy * nx + gx;
-        rv[q] = orth(ldr1(W + g), ldr1(zj + g), zm ? ldr1(zm + g) : C{});
-      }
+      for (int q = 0; q < NC; ++q)
+        rv[q] = orth(cv(rgW[q * NRING + tid]), cv(rgZ[q * NRING + tid]), zm ? cv(rgM[q * NRING + tid]) : C{});
     }
-    C g1[V], g2[V];
+    // Gray-Scott state terms ga V^2, ga 2UV, formed now so that every staged
+    // value is consumed before the next request overwrites the stage
+    C a1[V], a2[V];
     if constexpr (OP == PHIX_OP_GRAYSCOTT) {
+      C g1[V], g2[V];
+      lds2(reinterpret_cast<const T*>(stG + tid), g1[0], g1[1]);
+      lds2(reinterpret_cast<const T*>(stG + THREADS + tid), g2[0], g2[1]);
 #pragma unroll
       for (int v = 0; v < V; ++v) {
-        g1[v] = cv(__ldg(st + row + ix + v));
-        g2[v] = cv(__ldg(st + plane + row + ix + v));
+        a1[v] = ga * g1[v];
+        a2[v] = ga * g2[v];
       }
     }
     // Zhat_{j+1} at the own points: to slot j + 1 and the staged tile
@@ -466,6 +553,9 @@ __global__ void __launch_bounds__(THREADS) k_arnf(ArnArgs a) {
       st2(zo + q * plane + row + ix, zn[q][0], zn[q][1]);
       if (tid < NRING) sm[q][rr][rc] = stv(rv[q]);
     }
+    // every staged value is consumed (zn, zb, rv, a1, a2 depend on them): request
+    // the next tile into the stage while this one is computed
+    if (tile + 1 < t_end) prefetch(tile + 1);
     __syncthreads();
     // pass 1 of step j + 1 from the staged tile
     const int sr = threadIdx.y + 1;
@@ -478,10 +568,10 @@ __global__ void __launch_bounds__(THREADS) k_arnf(ArnArgs a) {
         J[0] = stencil_advdiff<C>(kk, cv(sm[0][sr][sc + 1]), cv(sm[0][sr][sc - 1]), cv(sm[0][sr + 1][sc]),
                                   cv(sm[0][sr - 1][sc]), zn[0][v]);
       } else if constexpr (OP == PHIX_OP_GRAYSCOTT) {
-        stencil_gs<C>(kk, ga, cv(sm[0][sr][sc + 1]), cv(sm[0][sr][sc - 1]), cv(sm[0][sr + 1][sc]),
-                      cv(sm[0][sr - 1][sc]), zn[0][v], cv(sm[NC - 1][sr][sc + 1]), cv(sm[NC - 1][sr][sc - 1]),
-                      cv(sm[NC - 1][sr + 1][sc]), cv(sm[NC - 1][sr - 1][sc]), zn[NC - 1][v], g1[v], g2[v], J[0],
-                      J[NC - 1]);
+        stencil_gs_a<C>(kk, cv(sm[0][sr][sc + 1]), cv(sm[0][sr][sc - 1]), cv(sm[0][sr + 1][sc]),
+                        cv(sm[0][sr - 1][sc]), zn[0][v], cv(sm[NC - 1][sr][sc + 1]), cv(sm[NC - 1][sr][sc - 1]),
+                        cv(sm[NC - 1][sr + 1][sc]), cv(sm[NC - 1][sr - 1][sc]), zn[NC - 1][v], a1[v], a2[v], J[0],
+                        J[NC - 1]);
       } else {
         const int vx = ix + v;
         const int vxm = vx == 0 ? nx - 1 : vx - 1;
@@ -1430,9 +1520,9 @@ CombArgs make_comb(const KiopsSpec& s, int n, double* out, double scale) {
 }
 
 // resident blocks per SM of a THREADS-thread kernel (at least 1)
-int blocks_per_sm(const void* fn) {
+int blocks_per_sm(const void* fn, size_t dsmem = 0) {
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, THREADS, 0) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, THREADS, dsmem) != cudaSuccess) {
     (void)cudaGetLastError();
     return 4;
   }
@@ -1471,13 +1561,34 @@ cudaError_t fused_first_t(const KiopsSpec& s, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// dynamic shared memory of a fused launch with nb b-columns
+template <int P, int OP>
+int arnf_smem(int nb) {
+  constexpr int nc = (OP == PHIX_OP_GRAYSCOTT) ? 2 : 1, ng = (OP == PHIX_OP_GRAYSCOTT) ? 2 : 0;
+  return arnf_smem_bytes(nc, ng, nb, (int)sizeof(typename KTr<P>::T));
+}
+
+// the kernel's dynamic shared-memory limit raised to its largest layout (once),
+// and its occupancy at that layout
+template <int P, int OP>
+int arnf_setup() {
+  const void* fn = reinterpret_cast<const void*>(k_arnf<P, OP>);
+  const int smax = arnf_smem<P, OP>(KIOPS_PMAX);
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smax) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  return blocks_per_sm(fn, (size_t)smax);
+}
+
 template <int P, int OP>
 cudaError_t fused_step_t(const KiopsSpec& s, int j, cudaStream_t st) {
-  static const int occ = blocks_per_sm(reinterpret_cast<const void*>(k_arnf<P, OP>));
+  static const int occ = arnf_setup<P, OP>();
+  if (occ < 1) return cudaErrorInvalidConfiguration;
   ArnArgs a = make_arn(s, j, 2);
   a.win = s.W[j & 1];
   a.wout = s.W[(j + 1) & 1];
-  k_arnf<P, OP><<<std::min(s.nsm * occ, a.ntiles), dim3(32, TILE_Y), 0, st>>>(a);
+  k_arnf<P, OP><<<std::min(s.nsm * occ, a.ntiles), dim3(32, TILE_Y), arnf_smem<P, OP>(s.nb), st>>>(a);
   return cudaGetLastError();
 }
 
