@@ -306,6 +306,61 @@ __device__ void reduce_partials(const double* partials, double (&tot)[NV], H hoo
   }
 }
 
+// As reduce_partials for double-float partials, the totals returned as
+// double-float pairs (valid in thread 0): no float64 instruction at all.
+template <typename A, int NV>
+__device__ void reduce_partials_df(const double* partials, df (&tot)[NV], int nv = NV) {
+  static_assert(PartialsDF<A>::value, "double-float partials only");
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  constexpr int NW = THREADS / 32;
+  __shared__ float2 swarp[NW][KMAX + 1];
+  const int lane = tid & 31, warp = tid >> 5;
+  df s[NV];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) s[j] = df_make(0.f, 0.f);
+  const float2* pf = reinterpret_cast<const float2*>(partials);
+  for (int b0 = tid; b0 < (int)gridDim.x; b0 += 4 * THREADS) {
+    float2 v[4][NV];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int b = b0 + q * THREADS;
+#pragma unroll
+      for (int j = 0; j < NV; ++j)
+        v[q][j] = (b < (int)gridDim.x && j < nv) ? __ldcg(pf + (size_t)b * (KMAX + 1) + j) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int j = 0; j < NV; ++j)
+        if (j < nv) s[j] = df_add(s[j], cv(v[q][j]));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int j = 0; j < NV; ++j)
+      if (j < nv) s[j] = df_add(s[j], shfl_down(s[j], o));
+  if (lane == 0)
+#pragma unroll
+    for (int j = 0; j < NV; ++j) swarp[warp][j] = make_float2(s[j].hi, s[j].lo);
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < NV; ++j) tot[j] = df_make(0.f, 0.f);
+  if (warp == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) s[j] = lane < NW ? cv(swarp[lane][j]) : df_make(0.f, 0.f);
+#pragma unroll
+    for (int o = NW / 2; o > 0; o >>= 1)
+#pragma unroll
+      for (int j = 0; j < NV; ++j)
+        if (j < nv) s[j] = df_add(s[j], shfl_down(s[j], o));
+#pragma unroll
+    for (int j = 0; j < NV; ++j) tot[j] = s[j];
+  }
+}
+
+// a <= b for normalised double-float values (|lo| <= ulp(hi)/2)
+__device__ __forceinline__ bool df_le(df a, df b) { return a.hi < b.hi || (a.hi == b.hi && a.lo <= b.lo); }
+
 // Stop test of the Newton-Leja chain at iteration m (Sec. 2.2):
 // |d_k[m]| ||y_m|| <= tol ||p_m^(k)|| for every k, compared as squares (no
 // square root on the critical path between launches); tot holds the squared
@@ -323,6 +378,34 @@ __device__ inline void leja_test(LejaCtl* ctl, int m, int K, int m_min, int m_ma
     conv = conv && (dkd[k] * dkd[k] * ny2 <= tol2 * np2);
   }
   ctl->ysq = ny2;
+  if (!finite) {
+    ctl->status = PHIX_ENAN;
+    ctl->iters = m;
+    ctl->done = 1;
+  } else if (conv) {
+    ctl->status = PHIX_OK;
+    ctl->iters = m;
+    ctl->done = 1;
+  } else if (m >= m_max) {
+    ctl->status = PHIX_ENOTCONV;
+    ctl->iters = m;
+    ctl->done = 1;
+  }
+}
+
+// The same test on double-float totals: ||y_m||^2 q_k <= ||p_m^(k)||^2 with
+// q_k = (d_k[m] / tol)^2 from the parameter block (float32 instructions only;
+// a decision differs from the float64 form only at a relative tie ~2^-47).
+__device__ inline void leja_test_df(LejaCtl* ctl, int m, int K, int m_min, int m_max, const float2* qk,
+                                    const df* tot) {
+  const df ny2 = tot[0];
+  bool finite = isfinite(ny2.hi);
+  bool conv = (m >= m_min);
+  for (int k = 0; k < K; ++k) {
+    const df np2 = tot[1 + k];
+    finite = finite && isfinite(np2.hi);
+    conv = conv && df_le(df_mul(ny2, cv(qk[k])), np2);
+  }
   if (!finite) {
     ctl->status = PHIX_ENAN;
     ctl->iters = m;
@@ -400,7 +483,8 @@ __device__ __forceinline__ CJ stencil_burgers(const CJ (&k)[8], CJ ga, CJ e, CJ 
 
 
 // ---------------------------------------------------------------------------
-// Chain parameter block: PassParams | beta_d[M] | beta_f[M] | dk_d[KMAX][M] | dk_f[KMAX][M]
+// Chain parameter block: PassParams | beta_d[M] | beta_f[M] | dk_d[KMAX][M] | dk_f[KMAX][M] | q_f[KMAX][M]
+// (q = (d_k[m] / tol)^2 in double-float: the stop test without float64)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ const PassParams* pp_of(const unsigned char* t) {
   return reinterpret_cast<const PassParams*>(t);
@@ -416,6 +500,9 @@ __device__ __forceinline__ const double* dk_d_of(const unsigned char* t, int M) 
 }
 __device__ __forceinline__ const float2* dk_f_of(const unsigned char* t, int M) {
   return reinterpret_cast<const float2*>(t + sizeof(PassParams) + 16 * (size_t)M + 8 * (size_t)KMAX * M);
+}
+__device__ __forceinline__ const float2* q_f_of(const unsigned char* t, int M) {
+  return reinterpret_cast<const float2*>(t + sizeof(PassParams) + 16 * (size_t)M + 16 * (size_t)KMAX * M);
 }
 
 // centre-coefficient indices that the Newton shift beta is folded into

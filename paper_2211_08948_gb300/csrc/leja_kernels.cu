@@ -15,6 +15,7 @@
 // Layout: planar float64-sized elements (double, or a float2 hi/lo pair),
 // 2D periodic grid, 32 x 8 thread tiles, V = 2 consecutive x points per
 // thread (16-byte loads) when nx is even, grid-stride over tiles.
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <type_traits>
@@ -238,6 +239,24 @@ __global__ void __launch_bounds__(THREADS) k_iter(IterDev a) {
 
   if (block_partials_and_last<Acc, KMAX + 1>(acc, a.partials, &a.ctl->count)) {
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    if constexpr (MODE == MODE_NEWTON && PartialsDF<Acc>::value) {
+      // the test's factors (d_k[m]/tol)^2, read before the partials so that their
+      // latency overlaps the reduction; totals and test in double-float
+      float2 qk[KMAX];
+#pragma unroll
+      for (int k = 0; k < KMAX; ++k)
+        qk[k] = (tid == 0 && k < K) ? q_f_of(a.ptab, M)[k * M + m] : make_float2(0.f, 0.f);
+      df tot[KMAX + 1];
+      reduce_partials_df<Acc, KMAX + 1>(a.partials, tot, K + 1);
+      if (tid == 0) {
+        LejaCtl* ctl = a.ctl;
+        leja_test_df(ctl, m, K, pp->m_min, pp->m_max, qk, tot);
+        ctl->m = m + 1;
+        ctl->count = 0;
+        if (ctl->done) stop_loop(a);
+      }
+      return;
+    }
     // the stop test's coefficients, read before the partials so that their
     // latency overlaps the reduction
     double dkd[KMAX];
@@ -476,7 +495,7 @@ __global__ void __launch_bounds__(THREADS)
 // ---------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------
-size_t ptab_bytes(int M) { return sizeof(PassParams) + 16 * (size_t)M + 16 * (size_t)KMAX * M; }
+size_t ptab_bytes(int M) { return sizeof(PassParams) + 16 * (size_t)M + 24 * (size_t)KMAX * M; }
 
 static float2 split2(double x) {
   float hi = (float)x;
@@ -511,11 +530,15 @@ void ptab_fill(void* host, int K, int m_min, int m_max, double tol, double rel, 
       bd[m] = beta[m];
       bf[m] = split2(beta[m]);
     }
+  float2* qf = reinterpret_cast<float2*>(b + sizeof(PassParams) + 16 * (size_t)M + 16 * (size_t)KMAX * M);
   if (dk)
     for (int k = 0; k < K; ++k)
       for (int m = 0; m < M; ++m) {
         dd[k * M + m] = dk[k][m];
         df2[k * M + m] = split2(dk[k][m]);
+        const double r = tol > 0 ? dk[k][m] / tol : 0.0;
+        // beyond the float32 range: +inf (the test never passes there)
+        qf[k * M + m] = r * r > 3.0e38 ? make_float2(INFINITY, 0.f) : split2(r * r);
       }
 }
 
