@@ -37,7 +37,8 @@ WORKLOAD = "Gray-Scott 1024x1024x2, EXPRB43 steps, h=100x explicit limit, Leja, 
 # DRAM bytes (read + write) of one launch of the dominant kernel, from an ncu --set full capture
 # of this configuration (k_iter, a K = 2 launch; k_arnf for KIOPS; cold caches); null for configurations without a
 # capture of the current kernel.  Keyed by (method, n, precision, Newton kernel).
-TRAFFIC = {("kiops", 1024, "DF64", "single"): 86.58e6 + 8.34e6}
+TRAFFIC = {("leja", 1024, "DF64", "single"): 67.17e6 + 8.82e6,
+           ("kiops", 1024, "DF64", "single"): 86.58e6 + 8.34e6}
 
 
 def parse():
