@@ -110,24 +110,76 @@ template <typename A, int NV>
 __device__ bool tma_partials_and_last(A (&acc)[NV], double* partials, unsigned int* count, double (*sw)[KMAX + 1]) {
   __shared__ bool last;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // float and double-float accumulators: double-float partials (float2 in the
+  // double slots), no float64 instruction; float64 accumulators: float64
+  constexpr bool DFP = !std::is_same<A, double>::value;
 #pragma unroll
   for (int j = 0; j < NV; ++j) {
     A v = acc[j];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = acc_add(v, shfl_down(v, o));
-    if (lane == 0) sw[warp][j] = acc_to_double(v);
+    if (lane == 0) {
+      if constexpr (DFP) {
+        const df d = acc_to_df(v);
+        reinterpret_cast<float2*>(&sw[warp][j])[0] = make_float2(d.hi, d.lo);
+      } else {
+        sw[warp][j] = v;
+      }
+    }
   }
   __syncthreads();
   if (tid < NV) {
-    double s = 0.0;
-    for (int w = 0; w < TT / 32; ++w) s += sw[w][tid];
-    partials[(size_t)blockIdx.x * (KMAX + 1) + tid] = s;
+    if constexpr (DFP) {
+      df s = df_make(0.f, 0.f);
+      for (int w = 0; w < TT / 32; ++w) s = df_add(s, cv(reinterpret_cast<const float2*>(&sw[w][tid])[0]));
+      reinterpret_cast<float2*>(partials + (size_t)blockIdx.x * (KMAX + 1) + tid)[0] = make_float2(s.hi, s.lo);
+    } else {
+      double s = 0.0;
+      for (int w = 0; w < TT / 32; ++w) s += sw[w][tid];
+      partials[(size_t)blockIdx.x * (KMAX + 1) + tid] = s;
+    }
+    __threadfence();  // the writers' partials visible before the arrival count
   }
-  __threadfence();
   __syncthreads();
   if (tid == 0) last = (atomicAdd(count, 1u) == gridDim.x - 1);
   __syncthreads();
   return last;
+}
+
+// Last block, double-float partials: totals as double-float pairs in thread 0
+// (strided per thread, then float32-lane shuffles; no float64 instruction).
+template <int NV>
+__device__ void tma_reduce_df(const double* partials, df (&tot)[NV], int nv, double (*sw)[KMAX + 1]) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = TT / 32;
+  df s[NV];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) s[j] = df_make(0.f, 0.f);
+  const float2* pf = reinterpret_cast<const float2*>(partials);
+  for (int b = tid; b < (int)gridDim.x; b += TT) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j)
+      if (j < nv) s[j] = df_add(s[j], cv(__ldcg(pf + (size_t)b * (KMAX + 1) + j)));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int j = 0; j < NV; ++j)
+      if (j < nv) s[j] = df_add(s[j], shfl_down(s[j], o));
+  __syncthreads();  // sw is reused
+  if (lane == 0)
+#pragma unroll
+    for (int j = 0; j < NV; ++j) reinterpret_cast<float2*>(&sw[warp][j])[0] = make_float2(s[j].hi, s[j].lo);
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < NV; ++j) tot[j] = df_make(0.f, 0.f);
+  if (tid == 0)
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      df t = df_make(0.f, 0.f);
+      for (int w = 0; w < NW; ++w) t = df_add(t, cv(reinterpret_cast<const float2*>(&sw[w][j])[0]));
+      tot[j] = t;
+    }
 }
 
 template <int NV>
@@ -403,6 +455,22 @@ __global__ void __launch_bounds__(TT, CTAS_PER_SM) k_iter_tma(const __grid_const
   }
 
   if (tma_partials_and_last<Acc, KMAX + 1>(acc, a.partials, &ctl->count, sw)) {
+    if constexpr (!std::is_same<Acc, double>::value) {
+      // double-float totals and stop test, (d_k[m]/tol)^2 read before the partials
+      float2 qk[KMAX];
+#pragma unroll
+      for (int k = 0; k < KMAX; ++k)
+        qk[k] = (tid == 0 && k < K) ? q_f_of(a.ptab, M)[k * M + m] : make_float2(0.f, 0.f);
+      df tot[KMAX + 1];
+      tma_reduce_df<KMAX + 1>(a.partials, tot, K + 1, sw);
+      if (tid == 0) {
+        leja_test_df(ctl, m, K, pp->m_min, pp->m_max, qk, tot);
+        ctl->m = m + 1;
+        ctl->count = 0;
+        if (ctl->done && a.use_cond) cudaGraphSetConditional(a.cond, 0);
+      }
+      return;
+    }
     // the stop test's coefficients, read before the partials
     double dkd[KMAX];
 #pragma unroll
