@@ -255,47 +255,47 @@ __global__ void __launch_bounds__(THREADS) k_iter(IterDev a) {
         ctl->count = 0;
         if (ctl->done) stop_loop(a);
       }
-      return;
-    }
-    // the stop test's coefficients, read before the partials so that their
-    // latency overlaps the reduction
-    double dkd[KMAX];
+    } else {
+      // the stop test's coefficients, read before the partials so that their
+      // latency overlaps the reduction
+      double dkd[KMAX];
 #pragma unroll
-    for (int k = 0; k < KMAX; ++k) dkd[k] = (MODE == MODE_NEWTON && tid == 0 && k < K) ? dk_d_of(a.ptab, M)[k * M + m] : 0.0;
-    double tot[KMAX + 1];
-    reduce_partials<Acc, KMAX + 1>(a.partials, tot, NoHook{}, MODE == MODE_NEWTON ? K + 1 : 1);
-    if (tid == 0) {
-      LejaCtl* ctl = a.ctl;
-      if (MODE == MODE_NEWTON) {
-        leja_test(ctl, m, K, pp->m_min, pp->m_max, pp->tol, dkd, tot);
-      } else {
-        // power iteration: y_k = J v_{k-1}, v_{k-1} unit  =>  rho_k = ||y_k||
-        double rho = sqrt(tot[0]);
-        double prev = ctl->rho;
-        ctl->rho_prev = prev;
-        ctl->rho = rho;
-        ctl->iters = m;
-        if (!isfinite(rho)) {
-          ctl->status = PHIX_ENAN;
-          ctl->done = 1;
-        } else if (rho == 0.0) {
-          ctl->status = PHIX_OK;
-          ctl->done = 1;
-        } else if ((m >= 2 && fabs(rho - prev) <= pp->rel * rho) || m >= pp->m_max) {
-          ctl->status = PHIX_OK;
-          ctl->done = 1;
+      for (int k = 0; k < KMAX; ++k) dkd[k] = (MODE == MODE_NEWTON && tid == 0 && k < K) ? dk_d_of(a.ptab, M)[k * M + m] : 0.0;
+      double tot[KMAX + 1];
+      reduce_partials<Acc, KMAX + 1>(a.partials, tot, NoHook{}, MODE == MODE_NEWTON ? K + 1 : 1);
+      if (tid == 0) {
+        LejaCtl* ctl = a.ctl;
+        if (MODE == MODE_NEWTON) {
+          leja_test(ctl, m, K, pp->m_min, pp->m_max, pp->tol, dkd, tot);
+        } else {
+          // power iteration: y_k = J v_{k-1}, v_{k-1} unit  =>  rho_k = ||y_k||
+          double rho = sqrt(tot[0]);
+          double prev = ctl->rho;
+          ctl->rho_prev = prev;
+          ctl->rho = rho;
+          ctl->iters = m;
+          if (!isfinite(rho)) {
+            ctl->status = PHIX_ENAN;
+            ctl->done = 1;
+          } else if (rho == 0.0) {
+            ctl->status = PHIX_OK;
+            ctl->done = 1;
+          } else if ((m >= 2 && fabs(rho - prev) <= pp->rel * rho) || m >= pp->m_max) {
+            ctl->status = PHIX_OK;
+            ctl->done = 1;
+          }
+          double al = 1.0 / rho;
+          ctl->alpha = al;
+          float ah = (float)al;
+          ctl->alpha_hi = ah;
+          ctl->alpha_lo = (float)(al - (double)ah);
         }
-        double al = 1.0 / rho;
-        ctl->alpha = al;
-        float ah = (float)al;
-        ctl->alpha_hi = ah;
-        ctl->alpha_lo = (float)(al - (double)ah);
+        ctl->m = m + 1;
+        ctl->count = 0;
+        // no fence: the next launch, the loop condition and the host's copy all
+        // follow the kernel's completion
+        if (ctl->done) stop_loop(a);
       }
-      ctl->m = m + 1;
-      ctl->count = 0;
-      // no fence: the next launch, the loop condition and the host's copy all
-      // follow the kernel's completion
-      if (ctl->done) stop_loop(a);
     }
   }
 }
