@@ -43,6 +43,11 @@ def test_version_and_opts_defaults():
     o = phix.phix_opts_default()
     assert o.prec == phix.PHIX_DF64 and o.m_max == 500 and o.m_min == 3
     assert o.safety == 1.2 and o.rho_re < 0 and o.gamma_cap == 200.0
+    assert (o.kiops_m_init, o.kiops_m_max, o.kiops_m_step, o.kiops_max_substeps) == (16, 64, 8, 10000)
+    assert o.profile == 0 and o.kernel == phix.PHIX_KERNEL_AUTO
+    # the last field: its default read back through the ctypes mirror checks the
+    # mirror's layout against the C struct that phix_opts_default fills
+    assert o.kiops_fused == 1
     assert ctypes.sizeof(phix.phix_jop) == 4 * 3 + 4 + 8 * 8 + 8
 
 
