@@ -42,7 +42,9 @@
 extern "C" {
 #endif
 
-#define PHIX_VERSION 100
+/* Rises whenever the layout of a public struct changes: callers must be built
+ * against the header of the library they load (101: phix_opts.kiops_fused). */
+#define PHIX_VERSION 101
 
 typedef struct phix_ctx phix_ctx;
 

@@ -39,7 +39,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_version_and_opts_defaults():
     phix, lib = _lib()
-    assert phix.phix_version() == 100
+    assert phix.phix_version() == 101
     o = phix.phix_opts_default()
     assert o.prec == phix.PHIX_DF64 and o.m_max == 500 and o.m_min == 3
     assert o.safety == 1.2 and o.rho_re < 0 and o.gamma_cap == 200.0
