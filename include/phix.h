@@ -301,12 +301,19 @@ phix_status phix_small_expm(phix_ctx* ctx, int n, const double* d, const double*
  * block, reduction partials, Newton basis, accumulators, Jacobian state
  * arrays) is one fixed array of PHIX_NOALLOC_SCRATCH_BYTES in device memory,
  * held by every GPU that loads the library until the process exits.
- *   - Limits: N * e * (2 + nout) + state planes + 80 KiB <= 32 MiB, with
- *     e = 8 bytes (PHIX_FP64, PHIX_DF64, PHIX_FP32_JV) or 4 (PHIX_FP32); e.g.
- *     Gray-Scott up to 512 x 512 with nout = 4 in double-float.  Larger
- *     problems return PHIX_ETOOBIG.  opts->m_max <= PHIX_NOALLOC_MMAX.  Only
- *     one vertical pass: an action that would need substeps (gamma_cap,
- *     iota_cap) returns PHIX_EINVAL.
+ *   - Limits: PHIX_NOALLOC_OVERHEAD_BYTES (control block, reduction
+ *     partials, parameter block: 190 KiB) + (2 + nout) vectors of N * e bytes
+ *     + the state planes (Gray-Scott 2, Burgers 1, of nx * ny * s bytes), each
+ *     rounded up to 256 bytes, must fit in PHIX_NOALLOC_SCRATCH_BYTES, with
+ *     e = 8 bytes (PHIX_FP64, PHIX_DF64, PHIX_FP32_JV) or 4 (PHIX_FP32) and
+ *     s = 8 (PHIX_FP64, PHIX_DF64) or 4; e.g. Gray-Scott up to 512 x 512 with
+ *     nout = 4 in double-float.  Larger problems return PHIX_ETOOBIG.
+ *     opts->m_max and opts->power_max_it <= PHIX_NOALLOC_MMAX.  Only one
+ *     vertical pass: an action that would need substeps (gamma_cap,
+ *     iota_cap) returns PHIX_EINVAL.  A zero spectral interval (e.g. a zero
+ *     operator) gives phi_l(0) v = v / l!, as phix_phi_action does.
+ *   - Host staging (parameter block, coefficient tables, ~180 KB) is static
+ *     per host thread, not on the caller's stack.
  *   - The first call on a device sets that device up (looks up the scratch's
  *     device address); make that first call before any stream capture.
  *   - Every call, on any stream, shares the one scratch array, which keeps
@@ -318,6 +325,7 @@ phix_status phix_small_expm(phix_ctx* ctx, int n, const double* d, const double*
  *     return value (also stats->status) is the error.                       */
 #define PHIX_NOALLOC_SCRATCH_BYTES (32u << 20)
 #define PHIX_NOALLOC_MMAX 1000
+#define PHIX_NOALLOC_OVERHEAD_BYTES 194560u
 phix_status phix_phi_action_noalloc(const phix_jop* op, double h, const double* v, int nout,
                                     const int* l, const double* scale, double* const* out,
                                     double tol, const phix_opts* opts, void* cuda_stream,

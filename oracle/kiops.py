@@ -7,7 +7,7 @@ incomplete orthogonalisation ("as few as two" inner products per
 iteration), the step is split into substeps, and the substep length and
 the Krylov dimension are adapted from an error estimate.  The KIOPS paper
 itself is not reproduced; the concrete rules below are this project's
-reading (each listed in the design doc):
+reading, followed alike by this module and by the CUDA library:
 
 * B and the tail are balanced by eta = 2^-ceil(log2 max_j ||b_j||_1):
   A~ uses eta*B, the start vector is [b_0; e_p / eta].

@@ -3,7 +3,8 @@ test, spectrum by power iteration, divided differences) and Sec. 4 (the
 "vertical" form: one Newton basis shared by several phi-functions /
 scales).
 
-Readings of the paper (each listed in the design doc):
+Readings of the paper where it is silent or ambiguous (this module follows
+them, and the CUDA library follows the same readings):
 * spectrum: alpha <= Re sigma(J) <= beta <= 0; c = (alpha+beta)/2 and
   gamma = (beta-alpha)/4 map [alpha, beta] onto the Leja domain [-2, 2];
   the interpolated function is phi_l(s h (c + gamma xi)) where s is the

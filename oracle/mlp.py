@@ -110,7 +110,14 @@ def features(kind, nx, ny, params, h, state):
     5 max|s1|, 6 max|s2|, 7 mean|s1|, 8 max g, 9 mean g  (g = (|dE-W| + |dN-S|)/2 of s1),
     10 GS: max V^2 | Burgers: max|U_x+U_y| / rho_diff, 11 GS: max(0, max 2UV) | Burgers: 0,
     12 Burgers: max|U|(nx+ny)/rho_diff | GS: 0, 13 F, 14 k, 15 1.
-    rho_diff = 8 Dmax (nx^2 + ny^2)/2 = 4 Dmax (nx^2 + ny^2)."""
+    rho_diff = 8 Dmax (nx^2 + ny^2)/2 = 4 Dmax (nx^2 + ny^2).
+    These features are this project's own choice (the paper defines no
+    learned interval).  Feature 11 is the largest positive value of the
+    reaction coefficient 2UV, the term of the Gray-Scott Jacobian that can
+    push eigenvalues to the right; it is clamped at 0 (a non-positive 2UV
+    cannot widen the interval), and 0 is also the identity element both
+    implementations start that maximum from.  On the Gray-Scott states of
+    the workloads (U, V >= 0) the clamp is never active."""
     f = np.zeros(NFEAT)
     N = nx * ny
     s1 = state[:N].reshape(ny, nx)

@@ -495,8 +495,6 @@ __global__ void __launch_bounds__(THREADS)
 // ---------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------
-size_t ptab_bytes(int M) { return sizeof(PassParams) + 16 * (size_t)M + 24 * (size_t)KMAX * M; }
-
 static float2 split2(double x) {
   float hi = (float)x;
   return make_float2(hi, (float)(x - (double)hi));

@@ -61,7 +61,11 @@ struct PassParams {
   double kd[8], gad;
   float2 kf[8], gaf;
 };
-size_t ptab_bytes(int M);
+// Bytes of a parameter block with tables of M entries (the layout above plus
+// the stop-test table q_k[m] = (d_k[m]/tol)^2 as double-float pairs).
+constexpr size_t ptab_bytes(int M) {
+  return sizeof(PassParams) + 16 * (size_t)M + 24 * (size_t)KMAX * (size_t)M;
+}
 // Fill a host copy of a parameter block.  beta and dk may be NULL (power iteration).
 void ptab_fill(void* host, int K, int m_min, int m_max, double tol, double rel, const double* k8,
                double ga, const double* beta, const double* const* dk, int prescaled = 0);

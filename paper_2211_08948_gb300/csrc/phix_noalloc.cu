@@ -38,7 +38,23 @@ struct DeviceSetup {
 DeviceSetup g_setup[MAX_DEVICES];
 std::mutex g_mu;
 
-size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+constexpr size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+constexpr size_t PTAB_MAX = ptab_bytes(PHIX_NOALLOC_MMAX + 1);  // parameter block of the longest chain
+
+// The fixed part of the scratch (control block, partials, parameter block),
+// as the header states it.
+static_assert(CTL_BYTES + align256(PARTIAL_BYTES) + align256(PTAB_MAX) == PHIX_NOALLOC_OVERHEAD_BYTES,
+              "PHIX_NOALLOC_OVERHEAD_BYTES must match the scratch layout");
+
+// Host staging of one call: the parameter block and the coefficient tables.
+// Thread-local (one per host thread, in static storage rather than on the
+// stack), so calls from several host threads do not share it.
+struct HostStage {
+  alignas(16) unsigned char ptab[PTAB_MAX];
+  double d[KMAX][PHIX_NOALLOC_MMAX + 1];
+  double beta[PHIX_NOALLOC_MMAX + 1];
+};
+thread_local HostStage g_stage;
 
 // Once per device, with that device current: the scratch's device address.
 phix_status setup_device(int dev, DeviceSetup** out) {
@@ -112,7 +128,7 @@ extern "C" phix_status phix_phi_action_noalloc(const phix_jop* op, double h, con
   const size_t st_planes = op->kind == PHIX_OP_GRAYSCOTT ? 2 : (op->kind == PHIX_OP_BURGERS ? 1 : 0);
   // scratch layout: control block | partials | parameter block | y0 | y1 | p_0..p_{K-1} | state planes
   const size_t vec = align256(N * eb);
-  const size_t ptb = align256(ptab_bytes(PHIX_NOALLOC_MMAX + 1));
+  const size_t ptb = align256(PTAB_MAX);
   const size_t need = CTL_BYTES + align256(PARTIAL_BYTES) + ptb + (2 + (size_t)nout) * vec +
                       align256(st_planes * plane * sb);
   if (need > (size_t)PHIX_NOALLOC_SCRATCH_BYTES) return finish(PHIX_ETOOBIG);
@@ -178,10 +194,10 @@ extern "C" phix_status phix_phi_action_noalloc(const phix_jop* op, double h, con
     beta_i = o.rho_hi;
     st.rho = o.rho_re;
   } else {
-    // parameter block on the host stack, copied synchronously into the scratch
-    static_assert(PHIX_NOALLOC_MMAX <= 1000, "stack parameter block sized for m_max <= 1000");
-    alignas(16) unsigned char hp[sizeof(PassParams) + 16 * 1001 + 16 * KMAX * 1001];
+    // parameter block staged in this thread's static buffer (sized for
+    // PHIX_NOALLOC_MMAX + 1 entries), copied into the scratch
     if (o.power_max_it > PHIX_NOALLOC_MMAX) return finish(PHIX_EINVAL);
+    unsigned char* hp = g_stage.ptab;
     ptab_fill(hp, 0, 0, o.power_max_it, 0.0, o.power_rel, kJ, 1.0, nullptr, nullptr);
     if (cudaMemcpyAsync(ptab, hp, ptab_bytes(o.power_max_it + 1), cudaMemcpyHostToDevice, c.st) != cudaSuccess)
       return finish(PHIX_ECUDA);
@@ -219,7 +235,18 @@ extern "C" phix_status phix_phi_action_noalloc(const phix_jop* op, double h, con
   // interval anchored at its right end beta
   const double gamma = std::max(0.25 * (beta_i - alpha_i), 2.0 * std::max(0.0, o.rho_im));
   const double cc = beta_i - 2.0 * gamma;
-  if (gamma == 0.0) return finish(PHIX_EINVAL);
+  if (gamma == 0.0) {
+    // zero spectrum (e.g. a zero operator): phi_l(0) v = v / l!, as phix_phi_action gives
+    for (int k = 0; k < nout; ++k) {
+      double f = 1.0;
+      for (int i = 2; i <= l[k]; ++i) f *= i;
+      const double c1 = 1.0 / f;
+      const double* x1 = v;
+      if (!ok(launch_lincomb(N, 1, &c1, &x1, out[k], grid_stream, c.st))) return finish(PHIX_ECUDA);
+    }
+    if (cudaStreamSynchronize(c.st) != cudaSuccess) return finish(PHIX_ECUDA);
+    return finish(PHIX_OK);
+  }
   // one vertical pass only: a substepped action needs more vectors than the scratch holds
   for (int k = 0; k < nout; ++k) {
     double s_re = o.gamma_cap > 0 ? scale[k] * h * gamma / o.gamma_cap : 0.0;
@@ -227,10 +254,10 @@ extern "C" phix_status phix_phi_action_noalloc(const phix_jop* op, double h, con
     if (s_re > 1.0 + 1e-12 || s_im > 1.0 + 1e-12) return finish(PHIX_EINVAL);
   }
 
-  // ---- divided differences (host, on the stack) ---------------------------
+  // ---- divided differences (host, in this thread's static buffer) ---------
   const int M = o.m_max + 1;
   const double* xi = leja_table(M);
-  double d[KMAX][PHIX_NOALLOC_MMAX + 1];
+  double (*d)[PHIX_NOALLOC_MMAX + 1] = g_stage.d;
   for (int k = 0; k < nout; ++k) {
     const double a0 = scale[k] * h * cc, b0 = scale[k] * h * gamma;
     for (int i = 0; i < M; ++i) d[k][i] = phi_host(l[k], a0 + b0 * xi[i]);
@@ -239,8 +266,8 @@ extern "C" phix_status phix_phi_action_noalloc(const phix_jop* op, double h, con
 
   // ---- Newton-Leja pass ----------------------------------------------------
   {
-    alignas(16) unsigned char hp[sizeof(PassParams) + 16 * 1001 + 16 * KMAX * 1001];
-    double beta[PHIX_NOALLOC_MMAX + 1];
+    unsigned char* hp = g_stage.ptab;
+    double* beta = g_stage.beta;
     beta[0] = 0.0;
     for (int m = 1; m < M; ++m) beta[m] = -(cc / gamma + xi[m - 1]);
     const double* dk[KMAX] = {};

@@ -17,6 +17,7 @@ STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOTCONV", 3: "ENAN", 4: "ETIMEOUT", 5
                 7: "ETOOBIG"}
 PHIX_NOALLOC_SCRATCH_BYTES = 32 << 20
 PHIX_NOALLOC_MMAX = 1000
+PHIX_NOALLOC_OVERHEAD_BYTES = 194560
 PHIX_MLP_NPARAM = 5443
 PHIX_MLP_NFEAT = 16
 PHIX_LEJA, PHIX_KIOPS = 0, 1
