@@ -1,6 +1,7 @@
-"""The oracle's EXPRB43 and EPIRK4s3 steps against the stage coefficients the
-paper prints (Eq. exprb43, Sec. 5.4; Eq. epirk4s3, Sec. 5.1), stored in
-tests/golden/.  With f(x) = d^2 + d^3 + c elementwise (d = x - u0) and the
+"""The oracle's integrator steps against the stage coefficients the paper
+prints (Eq. exprb43, Sec. 5.4; Eq. epirk4s3, Sec. 5.1; Eq. epirk4s3a,
+Sec. 5.2; Eq. exprb5s3, Sec. 5.5; Eq. epirk5p1 and its table, Sec. 5.3),
+stored in tests/golden/.  With f(x) = d^2 + d^3 + c elementwise (d = x - u0) and the
 step taken at u0, the Jacobian J(u0) vanishes, every phi_l(s J h) reduces to
 1/l!, and the nonlinear remainder is R(x) = d^2 + d^3: each stage is then an
 explicit polynomial in the printed coefficients, so a wrong coefficient,
@@ -72,10 +73,11 @@ def test_exprb43_matches_printed_coefficients():
     close(u4 - u3, e4 - e3)
 
 
-def test_epirk4s3_matches_printed_coefficients():
+@pytest.mark.parametrize("method", ["kiops", "lekry"])
+def test_epirk4s3_matches_printed_coefficients(method):
     g = read_golden("epirk4s3.txt")
     u0, c, h = _case()
-    u4, u3, st = integrators.epirk4s3_step(Polynomial(u0, c), u0, h, method="kiops", tol=1e-13)
+    u4, u3, st = integrators.epirk4s3_step(Polynomial(u0, c), u0, h, method=method, tol=1e-13)
     R = lambda x: (x - u0) ** 2 + (x - u0) ** 3
     a = u0 + g["c_a"] * c * h
     b = u0 + g["c_b"] * c * h
@@ -84,3 +86,45 @@ def test_epirk4s3_matches_printed_coefficients():
     e4 = e3 + (g["r4a"] * R(a) + g["r4d"] * d) * h / math.factorial(4)
     close(u3 - u0, e3 - u0)
     close(u4 - u3, e4 - e3)
+
+
+@pytest.mark.parametrize("method", ["kiops", "lekry"])
+def test_epirk4s3a_matches_printed_coefficients(method):
+    g = read_golden("epirk4s3a.txt")
+    u0, c, h = _case()
+    u4, u3, st = integrators.epirk4s3a_step(Polynomial(u0, c), u0, h, method=method, tol=1e-13)
+    R = lambda x: (x - u0) ** 2 + (x - u0) ** 3
+    a = u0 + g["c_a"] * c * h
+    b = u0 + g["c_b"] * c * h
+    e3 = u0 + c * h + (g["r3a"] * R(a) + g["r3b"] * R(b)) * h / math.factorial(3)
+    e4 = e3 + (g["r4a"] * R(a) + g["r4b"] * R(b)) * h / math.factorial(4)
+    close(u3 - u0, e3 - u0)
+    close(u4 - u3, e4 - e3)
+
+
+@pytest.mark.parametrize("method", ["kiops", "lekry"])
+def test_exprb53s3_matches_printed_coefficients(method):
+    g = read_golden("exprb53s3.txt")
+    u0, c, h = _case()
+    u5, u3, st = integrators.exprb53s3_step(Polynomial(u0, c), u0, h, method=method, tol=1e-13)
+    R = lambda x: (x - u0) ** 2 + (x - u0) ** 3
+    a = u0 + g["c_a"] * c * h
+    b = u0 + g["c_b"] * c * h + (g["q_a"] + g["q_b"]) * R(a) * h / math.factorial(3)
+    e3 = u0 + c * h + (g["r3a"] * R(a) + g["r3b"] * R(b)) * h / math.factorial(3)
+    e5 = (u0 + c * h + (g["r5a"] * R(a) + g["r5b"] * R(b)) * h / math.factorial(3)
+          + (g["r5c"] * R(a) + g["r5d"] * R(b)) * h / math.factorial(4))
+    close(u3 - u0, e3 - u0)
+    close(u5 - u3, e5 - e3)
+
+
+def test_epirk5p1_matches_printed_coefficients():
+    g = read_golden("epirk5p1.txt")
+    u0, c, h = _case()
+    u5, u4, st = integrators.epirk5p1_step(Polynomial(u0, c), u0, h, method="kiops", tol=1e-13)
+    R = lambda x: (x - u0) ** 2 + (x - u0) ** 3
+    a = u0 + g["a11"] * c * h
+    b = u0 + g["a21"] * c * h + g["a22"] * R(a) * h
+    w = (-2.0 * R(a) + R(b)) * h / math.factorial(3)
+    e4 = u0 + g["b1"] * c * h + g["b2"] * R(a) * h + g["b3"] * w
+    close(u4 - u0, e4 - u0)
+    close(u5 - u0, e4 - u0)   # with J = 0 the hatted and plain scales coincide
