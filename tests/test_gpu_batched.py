@@ -89,8 +89,10 @@ def test_batched_fp32_jv_error(px):
         ref, _ = leja.leja_phi(op.jv, q["v"], q["h"], -q["rho_re"], 0.0, [(1, 1.0)], 1e-10,
                                rho_im=q["rho_im"], iota_cap=4.0)
         worst = max(worst, rel(d["out"][0].cpu().numpy(), ref[0]))
+    # float32 stencil products in every Newton step of every substep (these
+    # advection-heavy problems take up to ~390 substeps); measured 2.1e-6
     print("FP32_JV batched worst rel err", worst)
-    assert worst <= 1e-4
+    assert worst <= 1e-5
 
 
 def test_batched_full_workload_sampled(px):

@@ -174,19 +174,47 @@ def test_substeps_gamma_and_imaginary_caps(px, prec):
 
 
 @pytest.mark.parametrize("prec", ["FP32_JV", "FP32"])
-def test_reduced_precision_errors(px, prec):
+def test_reduced_precision_meets_1e6_on_advdiff_64(px, prec):
+    """Float32 iteration arithmetic on the small advection-diffusion workload
+    (64^2, h = 50x the explicit diffusive step, phi_0..phi_3): every output
+    within the pure-float32 tolerance 1e-6 of the FFT-exact result."""
     phix, ctx = px
     n = 64
     p = synth.advdiff_params(n)
     v = synth.advdiff_gaussian(n)
     rho = 8.0 * p["D"] * n * n
-    outs = [(1, 1.0)]
+    outs = [(0, 1.0), (1, 1.0), (2, 1.0), (3, 1.0)]
     res, st = _run_action(phix, ctx, phix.PHIX_OP_ADVDIFF, n, n, [p["D"], p["ax"], p["ay"]], None, v,
-                          p["h"], outs, 1e-7, prec, rho_re=rho)
-    ex = exact.advdiff_phi_fft(n, p["D"], p["ax"], p["ay"], p["h"], v, 1)
-    err = rel(res[0], ex)
-    print(prec, "rel err vs exact", err, "iters", st.iters)
-    assert err <= 1e-5
+                          p["h"], outs, 1e-8, prec, rho_re=rho)
+    for (l, _), r in zip(outs, res):
+        err = rel(r, exact.advdiff_phi_fft(n, p["D"], p["ax"], p["ay"], p["h"], v, l))
+        print(prec, "phi_%d rel err vs exact" % l, err, "iters", st.iters)
+        assert err <= 1e-6, (l, err)
+
+
+def test_reduced_precision_on_burgers_256(px):
+    """Burgers (256^2, h = 50x explicit, phi_1 of f(u) h, imaginary bound from
+    the state): the double-float form meets the 1e-8 target against the
+    float64 path and both float32 forms the pure-float32 tolerance 1e-6.
+    (On this grid the advection bound splits the action into ~32 substeps of
+    small h gamma, which keeps float32 rounding small; the 2048^2 workload,
+    4 substeps of h gamma ~ 32, carries ~2e-5 and is reported by the bench.)"""
+    phix, ctx = px
+    n = 256
+    prm = synth.burgers_params(n)
+    u = synth.burgers_state(n, seed=2)
+    op = Burgers(n, prm["nu"], state=u)
+    v = op.f(u) * prm["h"]
+    rho_im = 2.0 * n * float(np.max(np.abs(u)))
+    res = {}
+    for prec in ["FP64", "DF64", "FP32_JV", "FP32"]:
+        r, st = _run_action(phix, ctx, phix.PHIX_OP_BURGERS, n, n, [prm["nu"]], u, v, prm["h"], [(1, 1.0)],
+                            1e-8, prec, rho_im=rho_im)
+        res[prec] = r[0]
+    errs = {p_: rel(res[p_], res["FP64"]) for p_ in res}
+    print("errors vs float64", errs)
+    assert errs["DF64"] <= 1e-8
+    assert errs["FP32_JV"] <= 1e-6 and errs["FP32"] <= 1e-6
 
 
 def test_zero_vector_and_zero_step(px):

@@ -135,15 +135,21 @@ def test_learned_interval_end_to_end(px):
         vvec = f64(np.random.default_rng(i).standard_normal(states[i].size))
         out_l = torch.empty_like(vvec)
         out_p = torch.empty_like(vvec)
+        out_r = torch.empty_like(vvec)
         rho_im = 0.0 if spec["kind"] == 1 else float(np.max(np.abs(states[i]))) * 2 * spec["n"]
         o = phix.phix_opts_default(rho_im=rho_im)
-        sl = phix.phix_phi_action_learned(ctx, op, spec["h"], vvec, [1], [1.0], [out_l], 1e-8, params, o)
-        sp = phix.phix_phi_action(ctx, op, spec["h"], vvec, [1], [1.0], [out_p], 1e-8, phix.PHIX_LEJA, o)
+        # two Leja approximants on different intervals each stop within ~tol of
+        # the exact action, so their difference can reach a few tol: the learned
+        # form runs at tol 1e-9 to meet the 1e-8 target against the float64 path
+        sl = phix.phix_phi_action_learned(ctx, op, spec["h"], vvec, [1], [1.0], [out_l], 1e-9, params, o)
+        sp = phix.phix_phi_action(ctx, op, spec["h"], vvec, [1], [1.0], [out_p], 1e-9, phix.PHIX_LEJA, o)
+        o64 = phix.phix_opts_default(rho_im=rho_im, prec=phix.PHIX_FP64)
+        phix.phix_phi_action(ctx, op, spec["h"], vvec, [1], [1.0], [out_r], 1e-9, phix.PHIX_LEJA, o64)
         fallbacks += sl.rejections
         saved += sp.power_mv - sl.power_mv
-        worst = max(worst, float(torch.linalg.norm(out_l - out_p) / torch.linalg.norm(out_p)))
-    print("matvecs saved", saved, "fallbacks", fallbacks, "worst rel diff", worst)
+        worst = max(worst, float(torch.linalg.norm(out_l - out_r) / torch.linalg.norm(out_r)))
+    print("matvecs saved", saved, "fallbacks", fallbacks, "worst rel err vs float64 power path", worst)
     assert np.median(err0) < 0.1
     assert fallbacks <= 6
     assert saved > 0.8 * sum(r[1] for r in rhos[ntr:ntr + 64])
-    assert worst <= 1e-6
+    assert worst <= 1e-8
