@@ -31,7 +31,6 @@ import numpy as np  # noqa: E402
 ACTIONS_PER_STEP = 5
 METRIC = "phi_l(hJ)v actions/s"
 UNIT = "phi-actions/s"
-WORKLOAD = "Gray-Scott 1024x1024x2, EXPRB43 steps, h=100x explicit limit, Leja, tol 1e-8"
 
 
 # DRAM bytes (read + write) of one launch of the dominant kernel, from an ncu --set full capture
@@ -58,9 +57,11 @@ def parse():
     ap.add_argument("--direct-launch", action="store_true",
                     help="launch every iteration kernel on its own (for ncu, which does not see into "
                          "conditional graphs); not a bench measurement")
-    ap.add_argument("--workload", default="grayscott", choices=["grayscott", "burgers", "batched", "learned"],
-                    help="grayscott: EXPRB43 steps (headline); burgers: phi_1(hJ) f h actions on the "
-                         "2048^2 Burgers state (mixed-precision workload)")
+    ap.add_argument("--workload", default="grayscott", choices=["grayscott", "burgers", "batched", "learned",
+                                                                "advdiff"],
+                    help="grayscott: EXPRB43 steps (headline, with every other workload as a leg); the others "
+                         "run one leg on its own")
+    ap.add_argument("--no-legs", action="store_true", help="headline line only (no other workloads)")
     return ap.parse_args()
 
 
@@ -148,11 +149,110 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def roofline(kernel, stats, peak, peak_src, traffic):
+    """Roofline object of the dominant kernel from the library's per-call
+    profile: algorithmic bytes of the iteration launches over their CUDA-event
+    time (events on the context's stream around each loop of iterations)."""
+    it_ms = sum(s["iter_ms"] for s in stats)
+    it_b = sum(s["iter_bytes"] for s in stats)
+    it_l = sum(s["iter_launches"] for s in stats)
+    achieved = it_b / (it_ms * 1e-3) / 1e9 if it_ms > 0 else None
+    return {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": (achieved / peak) if achieved else None, "traffic": traffic, "launches": it_l,
+            "avg_launch_us": 1e3 * it_ms / max(1, it_l), "peak_source": peak_src}
+
+
+class GrayScottRun:
+    """EXPRB43 steps of the Gray-Scott workload on one context: timed runs
+    with the L2 flushed before every step inside the timed region."""
+
+    def __init__(self, torch, phix, synth, ctx, stream, n, seed, flush):
+        self.torch, self.phix, self.ctx, self.stream, self.flush = torch, phix, ctx, stream, flush
+        self.n = n
+        self.prm = synth.grayscott_params(n)
+        self.u0 = synth.grayscott_state(n, seed=seed)
+        self.N = self.u0.size
+        self.op = phix.make_jop(phix.PHIX_OP_GRAYSCOTT, n, n,
+                                [self.prm["Du"], self.prm["Dv"], self.prm["F"], self.prm["k"]])
+
+    def opts(self, prec, profile=1, kernel="auto"):
+        ph = self.phix
+        return ph.phix_opts_default(prec=getattr(ph, "PHIX_" + prec), profile=profile,
+                                    kernel={"auto": ph.PHIX_KERNEL_AUTO, "single": ph.PHIX_KERNEL_SINGLE,
+                                            "tma": ph.PHIX_KERNEL_TMA}[kernel])
+
+    def run(self, steps, warmup, prec="DF64", method="leja", profile=1, kernel="auto", dist=None,
+            sampler=None):
+        """(ms of the timed steps, per-step stats, final state)."""
+        torch, ph = self.torch, self.phix
+        meth = ph.PHIX_KIOPS if method == "kiops" else ph.PHIX_LEJA
+        o = self.opts(prec, profile, kernel)
+        h, tol = self.prm["h"], 1e-8
+        u = torch.tensor(self.u0, dtype=torch.float64, device="cuda")
+        for _ in range(warmup):
+            self.flush.fill_(1.0)
+            ph.phix_exprb43_step(self.ctx, self.op, u, h, tol, meth, o)
+        u.copy_(torch.tensor(self.u0, dtype=torch.float64, device="cuda"))
+        if sampler:
+            sampler.start()
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        stats = []
+        e0.record(self.stream)
+        for _ in range(steps):
+            self.flush.fill_(1.0)  # L2 flush between steps
+            stats.append(ph.phix_exprb43_step(self.ctx, self.op, u, h, tol, meth, o).as_dict())
+        e1.record(self.stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), stats, u.cpu().numpy()
+
+
+def rel_err(a, b, ref0=None):
+    """||a - b|| / ||b|| (or / ||b - ref0||: the error of the increment)."""
+    d = np.linalg.norm(a - b)
+    return float(d / max(np.linalg.norm(b if ref0 is None else b - ref0), 1e-300))
+
+
+def leg_grayscott(run, args, prec, method, kernel="auto", fp64_final=None):
+    """One Gray-Scott EXPRB43 leg: phi-actions/s, ms/step, the roofline of the
+    iteration kernel, and the error against the float64 path's state after
+    the same steps (run here unless given)."""
+    peaks = load_peaks()
+    ms, st, u = run.run(args.steps, args.warmup, prec=prec, method=method, kernel=kernel)
+    if fp64_final is None and prec != "FP64":
+        _, _, fp64_final = run.run(args.steps, 0, prec="FP64", method=method, profile=0)
+    tma = sum(s.get("tma_passes", 0) for s in st) > 0
+    kname = ("k_iter_tma (TMA-staged Newton-Leja step)" if tma else "k_iter (Newton-Leja step)") \
+        if method == "leja" else "k_arnf (fused Arnoldi step)"
+    out = {"workload": "Gray-Scott %dx%dx2, EXPRB43, h=100x explicit, %s, tol 1e-8, %s" % (
+               run.n, run.n, "Leja" if method == "leja" else "KIOPS", prec),
+           "value": ACTIONS_PER_STEP * args.steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / args.steps,
+           "iters_per_step": statistics.mean(s["iters"] for s in st),
+           "roofline": roofline(kname, st, peaks.get("hbm_gbs", 6800.0),
+                                "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback",
+                                TRAFFIC.get((method, run.n, prec, "tma" if tma else "single")))}
+    if fp64_final is not None and prec != "FP64":
+        out["rel_err_vs_fp64"] = rel_err(u, fp64_final)
+        out["rel_err_of_increment_vs_fp64"] = rel_err(u, fp64_final, run.u0)
+    return out, u
+
+
 def run_phix(args, world, rank, local):
     import torch
     import synth
     from paper_2211_08948_gb300 import build, phix
 
+    dist = None
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
@@ -164,94 +264,64 @@ def run_phix(args, world, rank, local):
     phix.load()
     stream = torch.cuda.current_stream()
     ctx = phix.phix_create(stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 129 MB L2
     n = args.n
-    prm = synth.grayscott_params(n)
-    u0 = synth.grayscott_state(n, seed=rank)
-    N = u0.size
-    op = phix.make_jop(phix.PHIX_OP_GRAYSCOTT, n, n, [prm["Du"], prm["Dv"], prm["F"], prm["k"]])
-    prec = getattr(phix, "PHIX_" + args.prec)
-    opts = phix.phix_opts_default(prec=prec, profile=2 if args.direct_launch else 1,
-                                  kernel={"auto": phix.PHIX_KERNEL_AUTO, "single": phix.PHIX_KERNEL_SINGLE,
-                                          "tma": phix.PHIX_KERNEL_TMA}[args.kernel])
+    run = GrayScottRun(torch, phix, synth, ctx, stream, n, rank, flush)
     meth = phix.PHIX_KIOPS if args.method == "kiops" else phix.PHIX_LEJA
-    tol = 1e-8
-    h = prm["h"]
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 135 MB L2
+    profile = 2 if args.direct_launch else 1
 
-    # ---- device-resident run -------------------------------------------------
-    u = torch.tensor(u0, dtype=torch.float64, device="cuda")
-    for _ in range(args.warmup):
-        flush.fill_(1.0)  # the warm-up also loads the flush kernel
-        phix.phix_exprb43_step(ctx, op, u, h, tol, meth, opts)
-    u.copy_(torch.tensor(u0, dtype=torch.float64, device="cuda"))
-    stats = []
+    # ---- device-resident run (the headline) ----------------------------------
     sampler = ClockSampler(local, args.clock_ms)
-    sampler.start()
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        flush.fill_(1.0)  # L2 flush between steps
-        stats.append(phix.phix_exprb43_step(ctx, op, u, h, tol, meth, opts).as_dict())
-    e1.record(stream)
-    torch.cuda.synchronize()
+    ms, stats, u_fast = run.run(args.steps, args.warmup, prec=args.prec, method=args.method, profile=profile,
+                                kernel=args.kernel, dist=dist, sampler=sampler)
     clocks = sampler.stop()
-    ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
+    ms = max_over_ranks(ms, world, "cuda")
     if world > 1:
         dist.barrier()
-    u_fast = u.cpu().numpy()
 
-    # ---- accuracy against the plain float64 path (same steps, untimed) -------
-    uref = torch.tensor(u0, dtype=torch.float64, device="cuda")
-    o64 = phix.phix_opts_default(prec=phix.PHIX_FP64)
-    for _ in range(args.steps):
-        phix.phix_exprb43_step(ctx, op, uref, h, tol, meth, o64)
-    ur = uref.cpu().numpy()
-    rel_err = float(np.linalg.norm(u_fast - ur) / np.linalg.norm(ur))
-    rel_err_incr = float(np.linalg.norm(u_fast - ur) / max(np.linalg.norm(ur - u0), 1e-300))
+    # ---- the plain float64 path: same steps, timed (also the error reference) --
+    ms64, st64, u64 = run.run(args.steps, min(args.warmup, 3), prec="FP64", method=args.method)
+    rel = rel_err(u_fast, u64)
+    rel_incr = rel_err(u_fast, u64, run.u0)
 
-    # ---- end to end: pinned host buffers, H2D + step + D2H every step ---------
+    # ---- end to end through the C-ABI with HOST buffers -------------------------
+    # phix_step_host copies the state in, steps, and copies it back before it
+    # returns: every step moves N doubles each way inside the timed region
     e2e = None
     if not args.no_e2e:
-        hbuf = torch.tensor(u0, dtype=torch.float64).pin_memory()
-        hout = torch.empty_like(hbuf).pin_memory()
-        ud = torch.empty(N, dtype=torch.float64, device="cuda")
+        o = run.opts(args.prec, profile=0, kernel=args.kernel)
+        hbuf = torch.tensor(run.u0, dtype=torch.float64).pin_memory()
+        for _ in range(min(args.warmup, 3)):
+            phix.phix_step_host(ctx, phix.PHIX_EXPRB43, run.op, hbuf, run.prm["h"], 1e-8, meth, o)
+        hbuf.copy_(torch.tensor(run.u0, dtype=torch.float64))
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
-        # the two pinned buffers alternate: each step's input is the previous
-        # step's result as read back to the host
-        bufs = (hbuf, hout)
         f0.record(stream)
-        for k in range(args.steps):
+        for _ in range(args.steps):
             flush.fill_(1.0)
-            ud.copy_(bufs[k & 1], non_blocking=True)
-            phix.phix_exprb43_step(ctx, op, ud, h, tol, meth, opts)
-            bufs[(k + 1) & 1].copy_(ud, non_blocking=True)
-            torch.cuda.current_stream().synchronize()  # the step's result is on the host
+            phix.phix_step_host(ctx, phix.PHIX_EXPRB43, run.op, hbuf, run.prm["h"], 1e-8, meth, o)
         f1.record(stream)
         torch.cuda.synchronize()
         ems = max_over_ranks(f0.elapsed_time(f1), world, "cuda")
         e2e = {"value": whole_job_rate(ACTIONS_PER_STEP * args.steps, ems, world), "unit": UNIT,
-               "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8}
+               "h2d_bytes_per_step": run.N * 8, "d2h_bytes_per_step": run.N * 8,
+               "api": "phix_step_host (host buffer in, host buffer out, per step)",
+               "rel_err_vs_device_run": rel_err(hbuf.numpy(), u_fast)}
 
-    phix.phix_destroy(ctx)
-
-    iter_ms = sum(s["iter_ms"] for s in stats)
-    iter_bytes = sum(s["iter_bytes"] for s in stats)
-    iter_launches = sum(s["iter_launches"] for s in stats)
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        pass
+    peaks = load_peaks()
     peak = peaks.get("hbm_gbs", 6800.0)
-    achieved = iter_bytes / (iter_ms * 1e-3) / 1e9 if iter_ms > 0 else None
+    tma = sum(s.get("tma_passes", 0) for s in stats) > 0
+    kname = (("k_iter_tma (TMA-staged Newton-Leja step" if tma else "k_iter (Newton-Leja step")
+             + "; CUDA events around each pass's chain)") if args.method == "leja" else \
+        "k_arnf (fused Arnoldi step; k_arn1 + k_arn2 on grids of partial tiles; CUDA events around each run of steps)"
+    rf = roofline(kname, stats, peak, "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks
+                  else "fallback", TRAFFIC.get((args.method, n, args.prec, "tma" if tma else "single")))
+    if n <= 1024:
+        rf["note"] = ("one iteration's operands (~117 MB at K = 2) fit in the 126 MB L2: the fraction is "
+                      "algorithmic bandwidth with L2 assistance; legs.grayscott_2048 is the HBM-bound case")
     result = {
         "metric": METRIC,
         "value": whole_job_rate(ACTIONS_PER_STEP * args.steps, ms, world),
@@ -265,111 +335,141 @@ def run_phix(args, world, rank, local):
         "vs_baseline": None,
         "dtype": "f32x2 (double-float)" if args.prec == "DF64" else args.prec.lower(),
         "data": "synthetic (seeded Gray-Scott initial state, seed = rank)",
-        "config": {"workload": WORKLOAD if args.method == "leja" else WORKLOAD.replace("Leja", "KIOPS"),
-                   "grid": [n, n], "species": 2, "unknowns": N, "h": h, "tol": tol,
-                   "method": args.method, "prec": args.prec, "kernel": args.kernel,
-                   "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "flushed between steps (256 MB write, inside the timed region)"},
+        "config": bench_config(args, world),
         "time_steps_per_s": args.steps * world / (ms * 1e-3),
-        "hbm_gbs_iteration_algorithmic": achieved,
-        "rel_err_vs_fp64": rel_err,
-        "rel_err_of_increment_vs_fp64": rel_err_incr,
+        "hbm_gbs_iteration_algorithmic": rf["achieved"],
+        "rel_err_vs_fp64": rel,
+        "rel_err_of_increment_vs_fp64": rel_incr,
+        "fp64_path": {"value": ACTIONS_PER_STEP * args.steps / (ms64 * 1e-3), "unit": UNIT,
+                      "ms_per_step": ms64 / args.steps, "speedup_of_headline": ms64 / ms},
         "newton_iters_per_step": statistics.mean(s["iters"] for s in stats),
         "power_mv_per_step": statistics.mean(s["power_mv"] for s in stats),
         "gpu_launches": int(sum(s["launches"] for s in stats)),
         "e2e": e2e,
-        "roofline": {
-            "bound": "hbm",
-            "kernel": (("k_iter_tma (TMA-staged Newton-Leja step" if sum(s.get("tma_passes", 0) for s in stats) > 0
-                        else "k_iter (Newton-Leja step") + "; CUDA events around each pass's WHILE loop)"
-                       if args.method == "leja"
-                       else "k_arnf (fused Arnoldi step; k_arn1 + k_arn2 on grids of partial tiles; CUDA events around each run of steps)"),
-            "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": (achieved / peak) if achieved else None,
-            "traffic": TRAFFIC.get((args.method, n, args.prec, "tma" if sum(s.get("tma_passes", 0) for s in stats) > 0
-                                    else "single")),
-            "launches": iter_launches,
-            "avg_launch_us": 1e3 * iter_ms / max(1, iter_launches),
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback",
-        },
+        "roofline": rf,
         "clocks": clocks,
     }
+    if world == 1 and not args.no_legs:
+        legs = {}
+        t0 = time.perf_counter()
+        legs["kiops"], _ = leg_grayscott(run, args, args.prec, "kiops")
+        run2 = GrayScottRun(torch, phix, synth, ctx, stream, 2048, rank, flush)
+        legs["grayscott_2048"], _ = leg_grayscott(run2, args, args.prec, "leja")
+        del run2
+        legs["advdiff_64"] = leg_advdiff(torch, phix, synth, ctx, stream, args)
+        legs["burgers_2048"] = leg_burgers(torch, phix, synth, ctx, stream, args)
+        legs["batched_4096"] = leg_batched(torch, phix, synth, ctx, stream, args)
+        legs["learned"] = leg_learned(torch, phix, synth, ctx, stream, args)
+        legs["wall_s"] = time.perf_counter() - t0
+        result["legs"] = legs
+    phix.phix_destroy(ctx)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        result["cpu_baseline"] = cpu_baseline(n, u0, prm, tol)
+        result["cpu_baseline"] = cpu_baseline(n, run.u0, run.prm, 1e-8)
     if world > 1:
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(result), flush=True)
 
 
-def run_burgers(args, world, rank, local):
-    """phi_1(h J) f(u) h on the Burgers 2048^2 state: one action per step, with
-    the interval from power iteration; every precision's result is compared
-    with the float64 path's."""
-    import torch
-    import synth
-    from paper_2211_08948_gb300 import build, phix
-    torch.cuda.set_device(local)
-    build.build()
-    stream = torch.cuda.current_stream()
-    ctx = phix.phix_create(stream)
-    n = 2048 if args.n == 1024 else args.n
+def bench_config(args, world):
+    """The workload the line is quoted on (shared by both arms)."""
+    n = args.n
+    return {"workload": workload_name(n, args.method, args.prec),
+            "grid": [n, n], "species": 2, "unknowns": 2 * n * n, "h": 100.0 / (4.0 * 2e-5 * n * n), "tol": 1e-8,
+            "method": args.method, "prec": args.prec, "kernel": args.kernel,
+            "parallelism": "replicas" if world > 1 else "single",
+            "l2": "flushed between steps (256 MB write, inside the timed region)"}
+
+
+def workload_name(n, method, prec):
+    return "Gray-Scott %dx%dx2, EXPRB43 steps, h=100x explicit limit, %s, tol 1e-8" % (
+        n, n, "Leja" if method == "leja" else "KIOPS")
+
+
+def timed(torch, stream, fn, reps, warmup):
+    """CUDA-event ms of `reps` calls of fn() after `warmup` untimed calls; fn's results."""
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    res = []
+    e0.record(stream)
+    for _ in range(reps):
+        res.append(fn())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), res
+
+
+def leg_advdiff(torch, phix, synth, ctx, stream, args):
+    """Advection-diffusion 64^2 (u_t = lap u + 10 (u_x + u_y)), phi_0..phi_3 of the
+    Gaussian v at h = 50x the explicit diffusive step, tol 1e-10, Leja (vertical,
+    one basis) and KIOPS, float64 and double-float.  1 call = 4 phi-actions."""
+    n = 64
+    p = synth.advdiff_params(n)
+    v = torch.tensor(synth.advdiff_gaussian(n), dtype=torch.float64, device="cuda")
+    op = phix.make_jop(phix.PHIX_OP_ADVDIFF, n, n, [p["D"], p["ax"], p["ay"]])
+    rho = 8.0 * p["D"] * n * n
+    outs = {}
+    res = {}
+    reps = max(args.steps, 20)
+    for meth in ["leja", "kiops"]:
+        for prec in ["FP64", "DF64"]:
+            o = phix.phix_opts_default(prec=getattr(phix, "PHIX_" + prec), rho_re=rho)
+            out = [torch.empty_like(v) for _ in range(4)]
+            mid = phix.PHIX_LEJA if meth == "leja" else phix.PHIX_KIOPS
+            ms, st = timed(torch, stream, lambda: phix.phix_phi_action(ctx, op, p["h"], v, [0, 1, 2, 3], [1.0] * 4,
+                                                                      out, 1e-10, mid, o), reps, args.warmup)
+            outs[(meth, prec)] = [t.clone() for t in out]
+            res["%s_%s" % (meth, prec)] = {"value": 4 * reps / (ms * 1e-3), "unit": UNIT,
+                                          "us_per_call": 1e3 * ms / reps, "iters": st[-1].iters}
+    for meth in ["leja", "kiops"]:
+        ref = outs[(meth, "FP64")]
+        res["%s_DF64" % meth]["rel_err_vs_fp64"] = max(
+            float(torch.linalg.norm(a - b) / torch.linalg.norm(b)) for a, b in zip(outs[(meth, "DF64")], ref))
+    res["max_rel_diff_leja_vs_kiops_fp64"] = max(
+        float(torch.linalg.norm(a - b) / torch.linalg.norm(b)) for a, b in zip(outs[("leja", "FP64")],
+                                                                                outs[("kiops", "FP64")]))
+    res["workload"] = "advection-diffusion 64x64, phi_0..phi_3, h=50x explicit, tol 1e-10"
+    return res
+
+
+def leg_burgers(torch, phix, synth, ctx, stream, args, n=2048):
+    """phi_1(h J) f(u) h on the Burgers state (nu = 1e-3, h = 50x explicit), one
+    action per call, interval by power iteration, imaginary bound from the
+    state; every precision's result against the float64 path's."""
     prm = synth.burgers_params(n)
-    u0 = torch.tensor(synth.burgers_state(n, seed=rank), dtype=torch.float64, device="cuda")
+    u0 = torch.tensor(synth.burgers_state(n, seed=0), dtype=torch.float64, device="cuda")
     op = phix.make_jop(phix.PHIX_OP_BURGERS, n, n, [prm["nu"]], u0)
     h = prm["h"]
-    # v = f(u0) h (the expensive term of the step), by the library's RHS kernel
     v = torch.empty_like(u0)
     phix.phix_rhs(ctx, op, u0, v)
     v.mul_(h)
-    meth = phix.PHIX_KIOPS if args.method == "kiops" else phix.PHIX_LEJA
-    tol = 1e-8
-    res = {}
-    outs = {}
+    rho_im = 2.0 * n * float(torch.max(torch.abs(u0)))
+    peaks = load_peaks()
+    res, outs = {}, {}
     for pr in ["FP64", "DF64", "FP32_JV", "FP32"]:
-        o = phix.phix_opts_default(prec=getattr(phix, "PHIX_" + pr), profile=1)
+        o = phix.phix_opts_default(prec=getattr(phix, "PHIX_" + pr), profile=1, rho_im=rho_im)
         out = torch.empty_like(v)
-        for _ in range(args.warmup):
-            phix.phix_phi_action(ctx, op, h, v, [1], [1.0], [out], tol, meth, o)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        st = []
-        e0.record(stream)
-        for _ in range(args.steps):
-            st.append(phix.phix_phi_action(ctx, op, h, v, [1], [1.0], [out], tol, meth, o).as_dict())
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
+        ms, st = timed(torch, stream, lambda: phix.phix_phi_action(ctx, op, h, v, [1], [1.0], [out], 1e-8,
+                                                                  phix.PHIX_LEJA, o).as_dict(),
+                       args.steps, args.warmup)
         outs[pr] = out.clone()
-        it_ms = sum(s["iter_ms"] for s in st)
-        it_b = sum(s["iter_bytes"] for s in st)
-        res[pr] = {"actions_per_s": args.steps / (ms * 1e-3), "ms_per_action": ms / args.steps,
-                   "newton_iters": st[-1]["iters"], "power_mv": st[-1]["power_mv"],
-                   "iter_gbs": it_b / (it_ms * 1e-3) / 1e9 if it_ms > 0 else None}
-    ref = outs["FP64"]
+        res[pr] = {"value": args.steps / (ms * 1e-3), "unit": UNIT, "ms_per_action": ms / args.steps,
+                   "newton_iters": st[-1]["iters"], "substeps": st[-1]["substeps"], "power_mv": st[-1]["power_mv"],
+                   "roofline": roofline("k_iter / k_iter_tma", st, peaks.get("hbm_gbs", 6800.0),
+                                        "MEASURED_PEAKS.json hbm_gbs (of measured)", None)}
     for pr in res:
-        res[pr]["rel_err_vs_fp64"] = float(torch.linalg.norm(outs[pr] - ref) / torch.linalg.norm(ref))
-    phix.phix_destroy(ctx)
-    print(json.dumps({"metric": METRIC, "workload": "Burgers %dx%d, nu=1e-3, phi_1(hJ) f h, h=50x explicit, "
-                      "tol 1e-8, %s" % (n, n, args.method), "unit": UNIT, "steps": args.steps,
-                      "warmup": args.warmup, "by_precision": res}), flush=True)
+        res[pr]["rel_err_vs_fp64"] = float(torch.linalg.norm(outs[pr] - outs["FP64"]) / torch.linalg.norm(outs["FP64"]))
+        res[pr]["speedup_vs_fp64"] = res[pr]["value"] / res["FP64"]["value"]
+    res["workload"] = "Burgers %dx%d, nu=1e-3, phi_1(hJ) f h, h=50x explicit, tol 1e-8, Leja" % (n, n)
+    return res
 
 
-def run_batched(args, world, rank, local):
-    """4096 independent periodic advection-diffusion problems (sides log-uniform
-    32..512, D ~ U(0.1, 1), a ~ U(0, 50)^2, h = 10..200x explicit, Gaussian v),
-    phi_0, phi_1, phi_2 of each, tol 1e-8, in one persistent launch per step."""
-    import torch
-    import synth
-    from paper_2211_08948_gb300 import build, phix
-    torch.cuda.set_device(local)
-    build.build()
-    stream = torch.cuda.current_stream()
-    ctx = phix.phix_create(stream)
-    spec = synth.batched_problems(4096, seed=rank)
-    probs = []
-    unknowns = 0
+def batched_setup(torch, synth, count, seed):
+    spec = synth.batched_problems(count, seed=seed)
+    probs, unknowns = [], 0
     for q in spec:
         n = q["n"]
         v = torch.tensor(synth.random_vector(n * n, q["seed_v"]), dtype=torch.float64, device="cuda")
@@ -377,123 +477,121 @@ def run_batched(args, world, rank, local):
                           rho_re=8.0 * q["D"] * n * n, rho_im=(abs(q["ax"]) + abs(q["ay"])) * n, v=v,
                           out=[torch.empty_like(v) for _ in range(3)]))
         unknowns += n * n
-    res = {}
-    outs = {}
+    return probs, unknowns
+
+
+def leg_batched(torch, phix, synth, ctx, stream, args, count=4096):
+    """4096 independent periodic advection-diffusion problems (sides log-uniform
+    32..512, D ~ U(0.1, 1), a ~ U(0, 50)^2, h = 10..200x explicit, Gaussian v),
+    phi_0, phi_1, phi_2 of each, tol 1e-8, one persistent launch per batch."""
+    probs, unknowns = batched_setup(torch, synth, count, 0)
+    res, outs = {}, {}
+    reps = max(1, min(args.steps, 3))
     for pr in ["FP64", "DF64", "FP32_JV"]:
         o = phix.phix_opts_default(prec=getattr(phix, "PHIX_" + pr), profile=1)
-        for _ in range(args.warmup):
-            st, _ = phix.phix_phi_action_batched(ctx, probs, [0, 1, 2], 1e-8, o)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        launch_ms = 0.0
-        for _ in range(args.steps):
-            st, per = phix.phix_phi_action_batched(ctx, probs, [0, 1, 2], 1e-8, o)
-            launch_ms += st.iter_ms
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
+        ms, rr = timed(torch, stream, lambda: phix.phix_phi_action_batched(ctx, probs, [0, 1, 2], 1e-8, o),
+                       reps, 1)
+        st, per = rr[-1]
         outs[pr] = [[t.clone() for t in q["out"]] for q in probs[:256]]
-        res[pr] = {"actions_per_s": 3 * len(probs) * args.steps / (ms * 1e-3), "ms_per_batch": ms / args.steps,
-                   "launch_ms": launch_ms / args.steps, "ctas_per_sm": st.substeps,
-                   "newton_iters": st.iters, "failed": int(sum(1 for s in per if s != 0))}
+        res[pr] = {"value": 3 * len(probs) * reps / (ms * 1e-3), "unit": UNIT, "ms_per_batch": ms / reps,
+                   "launch_ms": st.iter_ms, "ctas_per_sm": st.substeps, "newton_iters": st.iters,
+                   "failed": int(sum(1 for s in per if s != 0))}
     for pr in res:
         num = sum(float(torch.linalg.norm(a - b) ** 2) for x, y in zip(outs[pr], outs["FP64"]) for a, b in zip(x, y))
         den = sum(float(torch.linalg.norm(b) ** 2) for y in outs["FP64"] for b in y)
         res[pr]["rel_err_vs_fp64_first256"] = (num / den) ** 0.5
-    phix.phix_destroy(ctx)
-    print(json.dumps({"metric": METRIC, "workload": "batched: 4096 periodic advection-diffusion problems, "
-                      "sides 32..512, phi_0..phi_2, tol 1e-8, one persistent launch", "unit": UNIT,
-                      "unknowns": unknowns, "steps": args.steps, "warmup": args.warmup, "by_precision": res}),
-          flush=True)
+        res[pr]["speedup_vs_fp64"] = res[pr]["value"] / res["FP64"]["value"]
+    res["workload"] = ("batched: %d periodic advection-diffusion problems (%d unknowns), sides 32..512, "
+                       "phi_0..phi_2, tol 1e-8, one persistent launch per batch, %d batches timed" % (
+                           count, unknowns, reps))
+    return res
 
 
-def run_learned(args, world, rank, local):
-    """Learned spectral interval: label 1024 Gray-Scott / Burgers states (sides
+def leg_learned(torch, phix, synth, ctx, stream, args, nlabel=1024, nact=200):
+    """Learned spectral interval: label Gray-Scott / Burgers states (sides
     32..128) with the method's power iteration, train the MLP on the GPU, then
-    run phi_1 actions on 256 held-out states (cycled, fresh v each time) with
-    the learned interval and with power iteration; report actions/s, matvecs
-    saved, fallbacks and the largest difference between the two results."""
-    import torch
-    import synth
-    from paper_2211_08948_gb300 import build, phix, learned
-    torch.cuda.set_device(local)
-    build.build()
-    stream = torch.cuda.current_stream()
-    ctx = phix.phix_create(stream)
-    specs = synth.learned_state_specs(1280, seed=rank)
+    phi_1 actions on held-out states with the learned interval and with power
+    iteration; matvecs saved and the error against the float64 power-iteration
+    path."""
+    from paper_2211_08948_gb300 import learned
+    specs = synth.learned_state_specs(nlabel + 256, seed=0)
     probs = []
     for sp in specs:
         st = torch.tensor(synth.learned_state(sp), dtype=torch.float64, device="cuda")
         kind = phix.PHIX_OP_GRAYSCOTT if sp["kind"] == 1 else phix.PHIX_OP_BURGERS
         probs.append((phix.make_jop(kind, sp["n"], sp["n"], sp["params"], st), sp["h"], st))
     t0 = time.perf_counter()
-    X, T, mv_labels = learned.make_dataset(ctx, probs[:1024], torch)
+    X, T, mv_labels = learned.make_dataset(ctx, probs[:nlabel], torch)
     t1 = time.perf_counter()
     params, loss = learned.train(ctx, X, T, torch)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
-    nact = max(1, args.steps)
-    evalp = probs[1024:]
-    res = {}
-    outs = {}
+    evalp = probs[nlabel:]
     # two Leja approximants at tolerance tau (different intervals, different stopping
     # points) differ by a few tau: tol 1e-9 keeps both within 1e-8 of the float64 result
     tol = 1e-9
-
-    def act(mode, a):
-        op, h, st = evalp[a % len(evalp)]
+    vs = []
+    for a in range(min(nact, len(evalp))):
         gen = torch.Generator(device="cuda").manual_seed(a)
-        v = torch.randn(st.numel(), dtype=torch.float64, device="cuda", generator=gen)
-        out = torch.empty_like(v)
-        rho_im = 0.0 if op.kind == phix.PHIX_OP_GRAYSCOTT else float(torch.max(torch.abs(st))) * 2 * op.nx
+        vs.append(torch.randn(evalp[a][2].numel(), dtype=torch.float64, device="cuda", generator=gen))
+
+    def act(mode, a, out):
+        op, h, st = evalp[a % len(evalp)]
+        v = vs[a % len(vs)]
+        rho_im = 0.0 if op.kind == phix.PHIX_OP_GRAYSCOTT else float(op._keepalive.abs().max()) * 2 * op.nx
         o = phix.phix_opts_default(rho_im=rho_im)
         if mode == "fp64":
             o.prec = phix.PHIX_FP64
         if mode == "learned":
-            s = phix.phix_phi_action_learned(ctx, op, h, v, [1], [1.0], [out], tol, params, o)
-        else:
-            s = phix.phix_phi_action(ctx, op, h, v, [1], [1.0], [out], tol, phix.PHIX_LEJA, o)
-        return out, s
+            return phix.phix_phi_action_learned(ctx, op, h, v, [1], [1.0], [out], tol, params, o)
+        return phix.phix_phi_action(ctx, op, h, v, [1], [1.0], [out], tol, phix.PHIX_LEJA, o)
 
-    # warm-up: both arms see every timed problem once (tables, graphs, workspace)
+    outs = {m: [torch.empty_like(vs[a % len(vs)]) for a in range(nact)] for m in ["learned", "power", "fp64"]}
+    res = {}
     for mode in ["learned", "power"]:
-        for a in range(min(nact, len(evalp))):
-            act(mode, a)
-    for mode in ["learned", "power"]:
-        mv, fb, worst = 0, 0, 0.0
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for a in range(nact):
-            out, s = act(mode, a)
-            if mode == "learned":
-                fb += s.rejections
-            mv += s.power_mv
-            if a < 256:
-                outs.setdefault(mode, []).append(out)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        res[mode] = {"actions_per_s": nact / (ms * 1e-3), "power_matvecs": mv, "fallbacks": fb}
-    worst = max(float(torch.linalg.norm(a - b) / torch.linalg.norm(b)) for a, b in zip(outs["learned"], outs["power"]))
-    # the plain float64 path (power iteration, float64 arithmetic), untimed, on the first 64 problems
-    nref = min(64, len(outs["learned"]))
-    err = {"learned": 0.0, "power": 0.0}
-    for a in range(nref):
-        ref, _ = act("fp64", a)
-        for mode in err:
-            err[mode] = max(err[mode], float(torch.linalg.norm(outs[mode][a] - ref) / torch.linalg.norm(ref)))
+        for a in range(nact):  # warm-up: tables, graphs, workspace
+            act(mode, a, outs[mode][a])
+        cnt = {"mv": 0, "fb": 0}
+
+        def one_pass():
+            for a in range(nact):
+                s = act(mode, a, outs[mode][a])
+                cnt["mv"] += s.power_mv
+                cnt["fb"] += s.rejections
+        ms, _ = timed(torch, stream, one_pass, 1, 0)
+        res[mode] = {"value": nact / (ms * 1e-3), "unit": UNIT, "power_matvecs": cnt["mv"], "fallbacks": cnt["fb"]}
+    for a in range(nact):
+        act("fp64", a, outs["fp64"][a])
+    err = {m: max(float(torch.linalg.norm(x - r) / torch.linalg.norm(r)) for x, r in zip(outs[m], outs["fp64"]))
+           for m in ["learned", "power"]}
+    return {"workload": "learned spectral interval: phi_1(hJ)v on %d held-out Gray-Scott/Burgers states "
+                        "(sides 32..128), tol 1e-9; labels from %d states" % (nact, nlabel),
+            "by_interval": res, "speedup_vs_power": res["learned"]["value"] / res["power"]["value"],
+            "matvecs_saved": res["power"]["power_matvecs"] - res["learned"]["power_matvecs"],
+            "rel_err_vs_fp64_power_path": err, "label_power_matvecs": mv_labels, "label_s": t1 - t0,
+            "train_s": t2 - t1, "train_loss": loss}
+
+
+def run_leg(args, world, rank, local):
+    """One leg on its own (--workload), printed as its own JSON object."""
+    import torch
+    import synth
+    from paper_2211_08948_gb300 import build, phix
+    torch.cuda.set_device(local)
+    build.build()
+    stream = torch.cuda.current_stream()
+    ctx = phix.phix_create(stream)
+    if args.workload == "burgers":
+        out = leg_burgers(torch, phix, synth, ctx, stream, args, n=2048 if args.n == 1024 else args.n)
+    elif args.workload == "batched":
+        out = leg_batched(torch, phix, synth, ctx, stream, args)
+    elif args.workload == "advdiff":
+        out = leg_advdiff(torch, phix, synth, ctx, stream, args)
+    else:
+        out = leg_learned(torch, phix, synth, ctx, stream, args)
     phix.phix_destroy(ctx)
-    print(json.dumps({"metric": METRIC, "workload": "learned spectral interval: phi_1(hJ)v on 256 held-out Gray-Scott/"
-                      "Burgers states (sides 32..128), tol 1e-9", "unit": UNIT, "actions": nact,
-                      "rel_err_vs_fp64_power": err, "fp64_reference_problems": nref,
-                      "label_states": 1024, "label_power_matvecs": mv_labels, "label_s": t1 - t0, "train_s": t2 - t1,
-                      "train_loss": loss, "by_interval": res,
-                      "matvecs_saved": res["power"]["power_matvecs"] - res["learned"]["power_matvecs"],
-                      "max_rel_diff_learned_vs_power": worst}), flush=True)
+    out.update({"metric": METRIC, "steps": args.steps, "warmup": args.warmup})
+    print(json.dumps(out), flush=True)
 
 
 def cpu_baseline(n, u0, prm, tol):
@@ -543,7 +641,7 @@ def run_reference(args, world, rank):
         "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "grid": [n, n]},
+        "data": "synthetic", "config": bench_config(args, world),
         "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -554,12 +652,8 @@ def main():
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
-    elif args.workload == "burgers":
-        run_burgers(args, world, rank, local)
-    elif args.workload == "batched":
-        run_batched(args, world, rank, local)
-    elif args.workload == "learned":
-        run_learned(args, world, rank, local)
+    elif args.workload != "grayscott":
+        run_leg(args, world, rank, local)
     else:
         run_phix(args, world, rank, local)
 

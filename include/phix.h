@@ -10,8 +10,11 @@
  *   Krylov / augmented ... Sec. 2.1 (Theorem: exp of [[A, B], [0, K]])
  *   Leja interpolation ... Sec. 2.2 (Newton form at Leja points, stop test)
  *   vertical form ........ Sec. 4
- *   EPIRK4s3 ............. Sec. 5.1, Eq. (epirk4s3)
+ *   EPIRK4s3 ............. Sec. 5.1, Eq. (epirk4s3)   LeKry ... Sec. 5.1
+ *   EPIRK4s3A ............ Sec. 5.2, Eq. (epirk4s3a)
+ *   EPIRK5P1 ............. Sec. 5.3, Eq. (epirk5p1)
  *   EXPRB43 .............. Sec. 5.4, Eq. (exprb43)
+ *   EXPRB53s3 ............ Sec. 5.5, Eq. (exprb5s3)
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -60,7 +63,20 @@ typedef enum {
                          fixed scratch (PHIX_NOALLOC_SCRATCH_BYTES)           */
 } phix_status;
 
-typedef enum { PHIX_LEJA = 0, PHIX_KIOPS = 1 } phix_method;
+/* How the phi-functions are evaluated.  PHIX_LEKRY (Sec. 5.1) is a policy of
+ * the step functions: internal stages by Leja, the solution combinations by
+ * KIOPS; the phi-action entry points take PHIX_LEJA or PHIX_KIOPS only.     */
+typedef enum { PHIX_LEJA = 0, PHIX_KIOPS = 1, PHIX_LEKRY = 2 } phix_method;
+
+/* Exponential integrators of Sec. 5 (each embedded with a lower-order
+ * solution whose difference is the error estimate).                       */
+typedef enum {
+  PHIX_EXPRB43 = 0,   /* Eq. (exprb43),  Sec. 5.4: order 4, estimate order 3        */
+  PHIX_EPIRK4S3 = 1,  /* Eq. (epirk4s3), Sec. 5.1: order 4, estimate order 3        */
+  PHIX_EPIRK4S3A = 2, /* Eq. (epirk4s3a), Sec. 5.2: order 4, estimate order 3       */
+  PHIX_EXPRB53S3 = 3, /* Eq. (exprb5s3), Sec. 5.5: order 5, estimate order 3        */
+  PHIX_EPIRK5P1 = 4   /* Eq. (epirk5p1) and its table, Sec. 5.3: order 5, est. 4    */
+} phix_scheme;
 
 /* Arithmetic of the iteration (Newton-Leja step / Arnoldi).  Inputs and
  * outputs are always float64; divided differences, Leja points, the small
@@ -206,11 +222,42 @@ phix_status phix_exprb43_step(phix_ctx* ctx, const phix_jop* op, double* u_inout
                               double tol, phix_method method, const phix_opts* opts,
                               double* err_est, phix_stats* stats);
 
-/* One EPIRK4s3 step, Eq. (epirk4s3): phi_1 at scales 1/8, 1/9, 1 on f h
- * vertically, then phi_3 and phi_4 on the remainder combinations.         */
+/* One EPIRK4s3 step, Eq. (epirk4s3) (= phix_step with PHIX_EPIRK4S3).
+ * Leja: phi_1 at scales 1/8, 1/9, 1 on f h vertically, then phi_3 and phi_4
+ * on the remainder combinations.  KIOPS: output times 1/8, 1/9 of one run,
+ * u_3 as one horizontal combination, phi_4 individually.                   */
 phix_status phix_epirk4s3_step(phix_ctx* ctx, const phix_jop* op, double* u_inout, double h,
                                double tol, phix_method method, const phix_opts* opts,
                                double* err_est, phix_stats* stats);
+
+/* One step of any scheme of Sec. 5: u_inout <- the higher-order solution;
+ * J and f at u_inout; *err_est = ||u_high - u_low||_2.  Grouping of the
+ * phi-functions (Sec. 5):
+ *   PHIX_LEJA   the terms on f(u) h in one vertical Newton pass (EXPRB43:
+ *               scales 1/2, 1; EPIRK4s3: 1/8, 1/9, 1; EPIRK4s3A: 1/2, 2/3, 1;
+ *               EXPRB53s3: 1/2, 9/10, 1, then phi_3 at 1/2, 9/10 on R(a) h;
+ *               EPIRK5P1: three passes of three / three / two outputs), every
+ *               phi-function of a remainder combination individually;
+ *   PHIX_KIOPS  internal stages as output times of one Krylov run; the
+ *               solutions of EPIRK4s3, EPIRK4s3A and EXPRB53s3 as one
+ *               horizontal combination sum_j phi_j(hJ) b_j each; EXPRB43 and
+ *               EPIRK5P1 as for Leja;
+ *   PHIX_LEKRY  EPIRK4s3, EPIRK4s3A, EXPRB53s3 only (else PHIX_EINVAL):
+ *               internal stages by Leja, solution combinations by KIOPS, the
+ *               phi_4 error term of the EPIRK4 family by Leja; opts->prec must
+ *               be PHIX_FP64 or PHIX_DF64.
+ * u_inout is a DEVICE vector of length N.                                  */
+phix_status phix_step(phix_ctx* ctx, phix_scheme scheme, const phix_jop* op, double* u_inout, double h,
+                      double tol, phix_method method, const phix_opts* opts, double* err_est,
+                      phix_stats* stats);
+
+/* As phix_step with the state in HOST memory (N doubles; page-locked memory
+ * gives full copy bandwidth, pageable memory works): the call copies it to
+ * the device, takes the step and, on success, copies the new state back
+ * before it returns.  On failure u_host_inout is unchanged.                 */
+phix_status phix_step_host(phix_ctx* ctx, phix_scheme scheme, const phix_jop* op, double* u_host_inout,
+                           double h, double tol, phix_method method, const phix_opts* opts,
+                           double* err_est, phix_stats* stats);
 
 /* One problem of a batch: a periodic advection-diffusion operator
  * J = D lap + ax d/dx + ay d/dy on an nx x ny grid, a step h, its spectral

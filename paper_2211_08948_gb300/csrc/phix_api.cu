@@ -29,6 +29,7 @@ enum Slot {
   S_ST2,                                                         // Gray-Scott state planes scaled for Newton passes
   S_BPROB, S_BORDER, S_BWS, S_BQ, S_XI,                          // batched problems, order, arena, queue, Leja points
   S_MFEAT, S_MY, S_MG, S_MCNT,                                   // learned interval: features, outputs, gradient
+  S_FH, S_O4, S_O5, S_O6, S_UH,                                  // stages: f h, more outputs, device copy of a host state
   S_NSLOT
 };
 
@@ -1482,21 +1483,44 @@ phix_status phix_phi_combination(phix_ctx* ctx, const phix_jop* op, double h, co
   });
 }
 
-// EXPRB43 and EPIRK4s3 share this driver; `scheme` selects the coefficients.
-static phix_status exp_step(phix_ctx* ctx, const phix_jop* op, double* u, double h, double tol,
-                            phix_method method, const phix_opts* opts, double* err_est,
-                            phix_stats* stats, int scheme) {
+// One step of an exponential integrator of Sec. 5 (the driver of every
+// scheme; `scheme` selects the stage program).  The phi-functions are grouped
+// as Sec. 5 describes per scheme and method: Leja evaluates the terms acting
+// on f(u) h in one vertical pass and the rest individually; KIOPS evaluates
+// the internal stages vertically (output times of one run) and the solution
+// stages of EPIRK4s3, EPIRK4s3A and EXPRB53s3 as one horizontal combination
+// (Theorem of Sec. 2.1); LeKry takes the internal stages (and the error term
+// of the EPIRK4 family) by Leja and the combinations by KIOPS.
+// uh != NULL: the state is in HOST memory: it is copied in, stepped, and
+// copied back (on success) before the call returns.
+static phix_status exp_step(phix_ctx* ctx, int scheme, const phix_jop* op, double* u_in, double* uh, double h,
+                            double tol, phix_method method, const phix_opts* opts, double* err_est,
+                            phix_stats* stats) {
   return guarded(ctx, stats, [&](phix_stats& st) -> phix_status {
     check_op(ctx, op, false);
-    if (!u) fail(ctx, PHIX_EINVAL, "u_inout is NULL");
+    if (!u_in && !uh) fail(ctx, PHIX_EINVAL, "u_inout is NULL");
     if (!(h > 0) || !std::isfinite(h)) fail(ctx, PHIX_EINVAL, "h must be finite and > 0");
     if (!(tol > 0)) fail(ctx, PHIX_EINVAL, "tol must be > 0");
+    if (scheme < PHIX_EXPRB43 || scheme > PHIX_EPIRK5P1) fail(ctx, PHIX_EINVAL, "unknown scheme %d", scheme);
     phix_opts o = resolve_opts(ctx, opts);
-    if (method != PHIX_LEJA && method != PHIX_KIOPS) fail(ctx, PHIX_EINVAL, "unknown method %d", (int)method);
+    if (method != PHIX_LEJA && method != PHIX_KIOPS && method != PHIX_LEKRY)
+      fail(ctx, PHIX_EINVAL, "unknown method %d", (int)method);
+    if (method == PHIX_LEKRY && (scheme == PHIX_EXPRB43 || scheme == PHIX_EPIRK5P1))
+      fail(ctx, PHIX_EINVAL, "scheme %d has no LeKry form (no linear combination of phi-functions)", scheme);
+    if (method == PHIX_LEKRY && o.prec != PHIX_FP64 && o.prec != PHIX_DF64)
+      fail(ctx, PHIX_EINVAL, "LeKry needs prec PHIX_FP64 or PHIX_DF64 (one state format for both methods)");
+    // iteration arithmetic: KIOPS runs float64 or double-float
     const int prec = method == PHIX_KIOPS ? kiops_prec(o.prec) : (int)o.prec;
+    const phix_method inner = method == PHIX_KIOPS ? PHIX_KIOPS : PHIX_LEJA;  // internal stages
+    const size_t N = (size_t)op->nx * op->ny * ncomp_of(op->kind);
+    double* u = u_in;
+    if (uh) {
+      u = wsd(ctx, S_UH, N);
+      CK(cudaMemcpyAsync(u, uh, N * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    }
     OpState os = make_opstate(ctx, op, u, prec);
-    const size_t N = os.N;
     double* F = wsd(ctx, S_F, N);
+    double* FH = wsd(ctx, S_FH, N);
     double* A = wsd(ctx, S_A, N);
     double* B = wsd(ctx, S_B, N);
     double* RA = wsd(ctx, S_RA, N);
@@ -1508,62 +1532,148 @@ static phix_status exp_step(phix_ctx* ctx, const phix_jop* op, double* u, double
     double* P1 = wsd(ctx, S_O1, N);
     double* P2 = wsd(ctx, S_O2, N);
     double* P3 = wsd(ctx, S_O3, N);
+    double* O4 = wsd(ctx, S_O4, N);
+    double* O5 = wsd(ctx, S_O5, N);
+    double* O6 = wsd(ctx, S_O6, N);
     KL(launch_rhs(os.d, u, F, ctx->grid_stream, ctx->stream));
     Interval ivv{};
-    if (method == PHIX_LEJA) ivv = interval_for(ctx, os, prec, o, st);
-    const Interval* iv = method == PHIX_LEJA ? &ivv : nullptr;
-    lincomb(ctx, N, {h}, {F}, T0);
-    if (scheme == 0) {
-      // EXPRB43, Eq. (exprb43)
-      int l2[2] = {1, 1};
-      double s2[2] = {0.5, 1.0};
-      double* o2[2] = {P1, P2};
-      phi_actions(ctx, os, method, prec, h, T0, 2, l2, s2, o2, tol, o, iv, st);
+    if (method != PHIX_KIOPS) ivv = interval_for(ctx, os, prec, o, st);
+    const Interval* iv = method != PHIX_KIOPS ? &ivv : nullptr;
+    lincomb(ctx, N, {h}, {F}, FH);
+    // phi_{l_k}(s_k h J) x for up to four outputs, by `how` (Leja vertical or KIOPS output times)
+    auto vert = [&](phix_method how, const double* x, std::vector<int> l, std::vector<double> s,
+                    std::vector<double*> out) {
+      phi_actions(ctx, os, how, prec, h, x, (int)l.size(), l.data(), s.data(), out.data(), tol, o,
+                  how == PHIX_LEJA ? iv : nullptr, st);
+    };
+    // sum_j phi_j(hJ) b_j by one KIOPS run (Theorem of Sec. 2.1)
+    auto horiz = [&](std::vector<const double*> b, double* out) {
+      std::vector<std::vector<KOut>> outs(1, std::vector<KOut>(1, KOut{out, 1.0}));
+      kiops_run(ctx, os, prec, h, b.data(), (int)b.size() - 1, std::vector<double>(1, 1.0), outs, tol, o, st);
+    };
+    auto remainder = [&](const double* x, double* R) {
+      KL(launch_remainder(os.d, u, x, R, ctx->grid_stream, ctx->stream));
+    };
+    // the step: u_new = u + sum_i cn[i] xn[i]; error estimate ||sum_i ce[i] xe[i]||
+    std::vector<double> cn, ce;
+    std::vector<const double*> xn, xe;
+    if (scheme == PHIX_EXPRB43) {
+      // Eq. (exprb43)
+      vert(method, FH, {1, 1}, {0.5, 1.0}, {P1, P2});
       lincomb(ctx, N, {1.0, 0.5}, {u, P1}, A);                 // a = u + 1/2 phi_1(h/2 J) f h
-      KL(launch_remainder(os.d, u, A, RA, ctx->grid_stream, ctx->stream));
+      remainder(A, RA);
       lincomb(ctx, N, {h}, {RA}, T0);
-      int l1 = 1;
-      double s1 = 1.0;
-      double* oq[1] = {Q};
-      phi_actions(ctx, os, method, prec, h, T0, 1, &l1, &s1, oq, tol, o, iv, st);
+      vert(method, T0, {1}, {1.0}, {Q});
       lincomb(ctx, N, {1.0, 1.0, 1.0}, {u, P2, Q}, B);         // b = u + phi_1 f h + phi_1 R(a) h
-      KL(launch_remainder(os.d, u, B, RB, ctx->grid_stream, ctx->stream));
+      remainder(B, RB);
       lincomb(ctx, N, {16.0 * h, -2.0 * h}, {RA, RB}, T0);
-      int l3 = 3;
-      double* o3[1] = {T3};
-      phi_actions(ctx, os, method, prec, h, T0, 1, &l3, &s1, o3, tol, o, iv, st);
+      vert(method, T0, {3}, {1.0}, {T3});
       lincomb(ctx, N, {-48.0 * h, 12.0 * h}, {RA, RB}, T0);
-      int l4 = 4;
-      double* o4[1] = {T4};
-      phi_actions(ctx, os, method, prec, h, T0, 1, &l4, &s1, o4, tol, o, iv, st);
+      vert(method, T0, {4}, {1.0}, {T4});
+      cn = {1.0, 1.0, 1.0};
+      xn = {P2, T3, T4};                                        // u4 = u + phi_1 f h + T3 + T4
+      ce = {1.0};
+      xe = {T4};                                                // u4 - u3
+    } else if (scheme == PHIX_EPIRK4S3 || scheme == PHIX_EPIRK4S3A) {
+      // Eq. (epirk4s3) / Eq. (epirk4s3a): one structure, their coefficients
+      const bool a4 = scheme == PHIX_EPIRK4S3A;
+      const double ca = a4 ? 0.5 : 1.0 / 8.0, cb = a4 ? 2.0 / 3.0 : 1.0 / 9.0;
+      // w3 = 1892 Ra + 1458 (Rb - 2 Ra) | 32 Ra - 27/2 Rb ;  w4 = -42336 Ra - 34992 (Rb - 2 Ra) | -144 Ra + 81 Rb
+      const double w3a = a4 ? 32.0 : 1892.0 - 2.0 * 1458.0, w3b = a4 ? -13.5 : 1458.0;
+      const double w4a = a4 ? -144.0 : -42336.0 + 2.0 * 34992.0, w4b = a4 ? 81.0 : -34992.0;
+      if (method == PHIX_LEJA)
+        vert(PHIX_LEJA, FH, {1, 1, 1}, {ca, cb, 1.0}, {P1, P3, P2});
+      else
+        vert(inner, FH, {1, 1}, {ca, cb}, {P1, P3});
+      lincomb(ctx, N, {1.0, ca}, {u, P1}, A);
+      lincomb(ctx, N, {1.0, cb}, {u, P3}, B);
+      remainder(A, RA);
+      remainder(B, RB);
+      lincomb(ctx, N, {w3a * h, w3b * h}, {RA, RB}, T0);
+      if (method == PHIX_LEJA) {
+        vert(PHIX_LEJA, T0, {3}, {1.0}, {T3});
+        cn = {1.0, 1.0, 1.0};
+        xn = {P2, T3, T4};
+      } else {
+        horiz({nullptr, FH, nullptr, T0}, T3);                  // u3 - u = phi_1 f h + phi_3 w3 h
+        cn = {1.0, 1.0};
+        xn = {T3, T4};
+      }
+      lincomb(ctx, N, {w4a * h, w4b * h}, {RA, RB}, T0);
+      vert(method == PHIX_KIOPS ? PHIX_KIOPS : PHIX_LEJA, T0, {4}, {1.0}, {T4});
+      ce = {1.0};
+      xe = {T4};
+    } else if (scheme == PHIX_EXPRB53S3) {
+      // Eq. (exprb5s3)
+      if (method == PHIX_LEJA)
+        vert(PHIX_LEJA, FH, {1, 1, 1}, {0.5, 0.9, 1.0}, {P1, P3, P2});
+      else
+        vert(inner, FH, {1, 1}, {0.5, 0.9}, {P1, P3});
+      lincomb(ctx, N, {1.0, 0.5}, {u, P1}, A);                 // a = u + 1/2 phi_1(h/2 J) f h
+      remainder(A, RA);
+      lincomb(ctx, N, {h}, {RA}, T0);
+      vert(inner, T0, {3, 3}, {0.5, 0.9}, {Q, O4});
+      // b = u + 9/10 phi_1(9h/10 J) f h + (27/25 phi_3(h/2 J) + 729/125 phi_3(9h/10 J)) R(a) h
+      lincomb(ctx, N, {1.0, 0.9, 27.0 / 25.0, 729.0 / 125.0}, {u, P3, Q, O4}, B);
+      remainder(B, RB);
+      if (method == PHIX_LEJA) {
+        lincomb(ctx, N, {2.0 * h, (150.0 / 81.0) * h}, {RA, RB}, T0);
+        vert(PHIX_LEJA, T0, {3}, {1.0}, {T3});
+        lincomb(ctx, N, {18.0 * h, (-250.0 / 81.0) * h}, {RA, RB}, T0);
+        vert(PHIX_LEJA, T0, {3}, {1.0}, {T4});
+        lincomb(ctx, N, {-60.0 * h, (500.0 / 27.0) * h}, {RA, RB}, T0);
+        vert(PHIX_LEJA, T0, {4}, {1.0}, {O5});
+        cn = {1.0, 1.0, 1.0};
+        xn = {P2, T4, O5};                                      // u5 = u + phi_1 f h + T4 + O5
+        ce = {1.0, 1.0, -1.0};
+        xe = {T4, O5, T3};                                      // u5 - u3
+      } else {
+        lincomb(ctx, N, {2.0 * h, (150.0 / 81.0) * h}, {RA, RB}, T0);
+        horiz({nullptr, FH, nullptr, T0}, T3);                  // u3 - u
+        lincomb(ctx, N, {18.0 * h, (-250.0 / 81.0) * h}, {RA, RB}, T0);
+        lincomb(ctx, N, {-60.0 * h, (500.0 / 27.0) * h}, {RA, RB}, O6);
+        horiz({nullptr, FH, nullptr, T0, O6}, T4);              // u5 - u
+        cn = {1.0};
+        xn = {T4};
+        ce = {1.0, -1.0};
+        xe = {T4, T3};
+      }
     } else {
-      // EPIRK4s3, Eq. (epirk4s3)
-      int l3v[3] = {1, 1, 1};
-      double s3[3] = {1.0 / 8.0, 1.0 / 9.0, 1.0};
-      double* o3v[3] = {P1, P3, P2};
-      phi_actions(ctx, os, method, prec, h, T0, 3, l3v, s3, o3v, tol, o, iv, st);
-      lincomb(ctx, N, {1.0, 1.0 / 8.0}, {u, P1}, A);
-      lincomb(ctx, N, {1.0, 1.0 / 9.0}, {u, P3}, B);
-      KL(launch_remainder(os.d, u, A, RA, ctx->grid_stream, ctx->stream));
-      KL(launch_remainder(os.d, u, B, RB, ctx->grid_stream, ctx->stream));
-      // 1892 Ra + 1458 (Rb - 2 Ra) = -1024 Ra + 1458 Rb
-      lincomb(ctx, N, {(1892.0 - 2.0 * 1458.0) * h, 1458.0 * h}, {RA, RB}, T0);
-      int l3 = 3;
-      double s1 = 1.0;
-      double* o3[1] = {T3};
-      phi_actions(ctx, os, method, prec, h, T0, 1, &l3, &s1, o3, tol, o, iv, st);
-      // -42336 Ra - 34992 (Rb - 2 Ra) = 27648 Ra - 34992 Rb
-      lincomb(ctx, N, {(-42336.0 + 2.0 * 34992.0) * h, -34992.0 * h}, {RA, RB}, T0);
-      int l4 = 4;
-      double* o4[1] = {T4};
-      phi_actions(ctx, os, method, prec, h, T0, 1, &l4, &s1, o4, tol, o, iv, st);
+      // EPIRK5P1, Eq. (epirk5p1) and its coefficient table: three vertical passes
+      const double a11 = 0.35129592695058193092, a21 = 0.84405472011657126298, a22 = 1.6905891609568963624;
+      const double b1 = 1.0, b2 = 1.2727127317356892397, b3 = 2.2714599265422622275;
+      const double g11 = 0.35129592695058193092, g21 = 0.84405472011657126298, g22 = 0.5, g31 = 1.0;
+      const double g32 = 0.71111095364366870359, g32h = 0.5, g33 = 0.62378111953371494809, g33h = 1.0;
+      vert(method, FH, {1, 1, 1}, {g11, g21, g31}, {P1, P3, P2});
+      lincomb(ctx, N, {1.0, a11}, {u, P1}, A);
+      remainder(A, RA);
+      lincomb(ctx, N, {h}, {RA}, T0);
+      vert(method, T0, {1, 1, 1}, {g22, g32h, g32}, {Q, O4, O5});
+      lincomb(ctx, N, {1.0, a21, a22}, {u, P3, Q}, B);
+      remainder(B, RB);
+      lincomb(ctx, N, {-2.0 * h, h}, {RA, RB}, T0);
+      vert(method, T0, {3, 3}, {g33, g33h}, {T3, T4});
+      cn = {b1, b2, b3};
+      xn = {P2, O5, T3};                                        // u5
+      ce = {b2, b3, -b2, -b3};
+      xe = {O5, T3, O4, T4};                                    // u5 - u4
     }
-    // err = ||u4 - u3|| = ||T4||;  u4 = u + phi_1(hJ) f h + T3 + T4
-    KL(launch_norm2(N, T4, nullptr, ctx->partials, ctx->counter, ctx->scal, ctx->grid_stream, ctx->stream));
+    // err = ||u_high - u_low||
+    const double* ev = xe[0];
+    if (xe.size() > 1 || ce[0] != 1.0) {
+      lincomb(ctx, N, ce, xe, O6);
+      ev = O6;
+    }
+    KL(launch_norm2(N, ev, nullptr, ctx->partials, ctx->counter, ctx->scal, ctx->grid_stream, ctx->stream));
     CK(cudaMemcpyAsync(ctx->scal_h, ctx->scal, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     flush(ctx);  // u changes only when every pass succeeded
     if (ctx->ran_out) throw Rerun{};
-    if (st.status == PHIX_OK) lincomb(ctx, N, {1.0, 1.0, 1.0, 1.0}, {u, P2, T3, T4}, u);
+    if (st.status == PHIX_OK) {
+      cn.insert(cn.begin(), 1.0);
+      xn.insert(xn.begin(), u);
+      lincomb(ctx, N, cn, xn, u);
+      if (uh) CK(cudaMemcpyAsync(uh, u, N * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    }
     CK(cudaStreamSynchronize(ctx->stream));
     st.err_est = std::sqrt(ctx->scal_h[0]);
     if (err_est) *err_est = st.err_est;
@@ -1574,13 +1684,24 @@ static phix_status exp_step(phix_ctx* ctx, const phix_jop* op, double* u, double
 phix_status phix_exprb43_step(phix_ctx* ctx, const phix_jop* op, double* u_inout, double h, double tol,
                               phix_method method, const phix_opts* opts, double* err_est,
                               phix_stats* stats) {
-  return exp_step(ctx, op, u_inout, h, tol, method, opts, err_est, stats, 0);
+  return exp_step(ctx, PHIX_EXPRB43, op, u_inout, nullptr, h, tol, method, opts, err_est, stats);
 }
 
 phix_status phix_epirk4s3_step(phix_ctx* ctx, const phix_jop* op, double* u_inout, double h, double tol,
                                phix_method method, const phix_opts* opts, double* err_est,
                                phix_stats* stats) {
-  return exp_step(ctx, op, u_inout, h, tol, method, opts, err_est, stats, 1);
+  return exp_step(ctx, PHIX_EPIRK4S3, op, u_inout, nullptr, h, tol, method, opts, err_est, stats);
+}
+
+phix_status phix_step(phix_ctx* ctx, phix_scheme scheme, const phix_jop* op, double* u_inout, double h, double tol,
+                      phix_method method, const phix_opts* opts, double* err_est, phix_stats* stats) {
+  return exp_step(ctx, (int)scheme, op, u_inout, nullptr, h, tol, method, opts, err_est, stats);
+}
+
+phix_status phix_step_host(phix_ctx* ctx, phix_scheme scheme, const phix_jop* op, double* u_host_inout, double h,
+                           double tol, phix_method method, const phix_opts* opts, double* err_est,
+                           phix_stats* stats) {
+  return exp_step(ctx, (int)scheme, op, nullptr, u_host_inout, h, tol, method, opts, err_est, stats);
 }
 
 }  // extern "C"

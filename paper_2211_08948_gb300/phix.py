@@ -20,7 +20,8 @@ PHIX_NOALLOC_MMAX = 1000
 PHIX_NOALLOC_OVERHEAD_BYTES = 194560
 PHIX_MLP_NPARAM = 5443
 PHIX_MLP_NFEAT = 16
-PHIX_LEJA, PHIX_KIOPS = 0, 1
+PHIX_LEJA, PHIX_KIOPS, PHIX_LEKRY = 0, 1, 2
+PHIX_EXPRB43, PHIX_EPIRK4S3, PHIX_EPIRK4S3A, PHIX_EXPRB53S3, PHIX_EPIRK5P1 = range(5)
 PHIX_KERNEL_AUTO, PHIX_KERNEL_SINGLE, PHIX_KERNEL_TMA = 0, 1, 2
 PHIX_FP64, PHIX_DF64, PHIX_FP32_JV, PHIX_FP32 = 0, 1, 2, 3
 PHIX_OP_ADVDIFF, PHIX_OP_GRAYSCOTT, PHIX_OP_BURGERS = 0, 1, 2
@@ -31,6 +32,7 @@ EXPORTS = [
     "phix_phi_action", "phix_phi_combination", "phix_spectrum", "phix_exprb43_step",
     "phix_epirk4s3_step", "phix_rhs", "phix_small_expm", "phix_phi_action_batched", "phix_features",
     "phix_mlp_forward", "phix_mlp_grad", "phix_mlp_train", "phix_phi_action_learned", "phix_leja_points", "phix_divided_differences", "phix_phi_action_noalloc",
+    "phix_step", "phix_step_host",
 ]
 
 
@@ -115,6 +117,9 @@ def load(path=None):
     lib.phix_small_expm.argtypes = [P, I, P, P, P, D, P, ctypes.POINTER(I)]
     lib.phix_spectrum.argtypes = [P, ctypes.POINTER(phix_jop), ctypes.POINTER(phix_opts),
                                   ctypes.POINTER(D), ctypes.POINTER(phix_stats)]
+    for f in (lib.phix_step, lib.phix_step_host):
+        f.argtypes = [P, I, ctypes.POINTER(phix_jop), P, D, D, I, ctypes.POINTER(phix_opts),
+                      ctypes.POINTER(D), ctypes.POINTER(phix_stats)]
     for f in (lib.phix_exprb43_step, lib.phix_epirk4s3_step):
         f.argtypes = [P, ctypes.POINTER(phix_jop), P, D, D, I, ctypes.POINTER(phix_opts),
                       ctypes.POINTER(D), ctypes.POINTER(phix_stats)]
@@ -139,6 +144,20 @@ def _ptr(x):
     if not (x.is_cuda and x.dtype.is_floating_point and x.element_size() == 8 and x.is_contiguous()):
         raise ValueError("expected a contiguous float64 CUDA tensor")
     return x.data_ptr()
+
+
+def _hptr(x):
+    """Address of a contiguous float64 CPU tensor (or a raw host address)."""
+    if isinstance(x, int):
+        return x
+    if x.is_cuda or x.dtype != _torch_f64(x) or not x.is_contiguous():
+        raise ValueError("expected a contiguous float64 CPU tensor")
+    return x.data_ptr()
+
+
+def _torch_f64(x):
+    import torch
+    return torch.float64
 
 
 def _fptr(x):
@@ -324,10 +343,10 @@ def phix_spectrum(ctx, op, opts=None):
     return rho.value, st
 
 
-def _step(fn, ctx, op, u, h, tol, method, opts, check):
+def _step(fn, ctx, op, u, h, tol, method, opts, check, ptr=_ptr):
     err = ctypes.c_double()
     st = phix_stats()
-    rc = fn(ctx, ctypes.byref(op), _ptr(u), h, tol, method,
+    rc = fn(ctx, ctypes.byref(op), ptr(u), h, tol, method,
             ctypes.byref(opts) if opts is not None else None, ctypes.byref(err), ctypes.byref(st))
     if check:
         _check(ctx, rc)
@@ -341,6 +360,21 @@ def phix_exprb43_step(ctx, op, u, h, tol, method=PHIX_LEJA, opts=None, check=Tru
 
 def phix_epirk4s3_step(ctx, op, u, h, tol, method=PHIX_LEJA, opts=None, check=True):
     return _step(load().phix_epirk4s3_step, ctx, op, u, h, tol, method, opts, check)
+
+
+def phix_step(ctx, scheme, op, u, h, tol, method=PHIX_LEJA, opts=None, check=True):
+    """u <- one step of `scheme` (PHIX_EXPRB43 .. PHIX_EPIRK5P1), in place on the
+    device vector u; returns phix_stats (err_est = ||u_high - u_low||)."""
+    fn = load().phix_step
+    return _step(lambda c, o, x, *a: fn(c, scheme, o, x, *a), ctx, op, u, h, tol, method, opts, check)
+
+
+def phix_step_host(ctx, scheme, op, u_host, h, tol, method=PHIX_LEJA, opts=None, check=True):
+    """As phix_step with the state in host memory: u_host is a CPU float64
+    tensor (page-locked for full copy bandwidth) or a raw host address."""
+    fn = load().phix_step_host
+    return _step(lambda c, o, x, *a: fn(c, scheme, o, x, *a), ctx, op, u_host, h, tol, method, opts, check,
+                 ptr=_hptr)
 
 
 def phix_leja_points(m):
