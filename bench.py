@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--method", default="leja", choices=["leja", "kiops"])
     ap.add_argument("--kernel", default="auto", choices=["auto", "single", "tma"],
                     help="Newton-step kernel of the Leja path (auto: TMA-staged once an iteration exceeds L2)")
+    ap.add_argument("--chain", default="auto", choices=["auto", "persistent", "graph"],
+                    help="Newton passes as one cooperative launch (auto, persistent) or one launch per "
+                         "iteration in a conditional graph")
     ap.add_argument("--direct-launch", action="store_true",
                     help="launch every iteration kernel on its own (for ncu, which does not see into "
                          "conditional graphs); not a bench measurement")
@@ -176,6 +179,7 @@ class GrayScottRun:
     def __init__(self, torch, phix, synth, ctx, stream, n, seed, flush):
         self.torch, self.phix, self.ctx, self.stream, self.flush = torch, phix, ctx, stream, flush
         self.n = n
+        self.chain = "auto"
         self.prm = synth.grayscott_params(n)
         self.u0 = synth.grayscott_state(n, seed=seed)
         self.N = self.u0.size
@@ -186,7 +190,9 @@ class GrayScottRun:
         ph = self.phix
         return ph.phix_opts_default(prec=getattr(ph, "PHIX_" + prec), profile=profile,
                                     kernel={"auto": ph.PHIX_KERNEL_AUTO, "single": ph.PHIX_KERNEL_SINGLE,
-                                            "tma": ph.PHIX_KERNEL_TMA}[kernel])
+                                            "tma": ph.PHIX_KERNEL_TMA}[kernel],
+                                    chain={"auto": ph.PHIX_CHAIN_AUTO, "persistent": ph.PHIX_CHAIN_PERSISTENT,
+                                           "graph": ph.PHIX_CHAIN_GRAPH}[self.chain])
 
     def run(self, steps, warmup, prec="DF64", method="leja", profile=1, kernel="auto", dist=None,
             sampler=None):
@@ -267,6 +273,7 @@ def run_phix(args, world, rank, local):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 129 MB L2
     n = args.n
     run = GrayScottRun(torch, phix, synth, ctx, stream, n, rank, flush)
+    run.chain = args.chain
     meth = phix.PHIX_KIOPS if args.method == "kiops" else phix.PHIX_LEJA
     profile = 2 if args.direct_launch else 1
 
@@ -376,7 +383,7 @@ def bench_config(args, world):
     n = args.n
     return {"workload": workload_name(n, args.method, args.prec),
             "grid": [n, n], "species": 2, "unknowns": 2 * n * n, "h": 100.0 / (4.0 * 2e-5 * n * n), "tol": 1e-8,
-            "method": args.method, "prec": args.prec, "kernel": args.kernel,
+            "method": args.method, "prec": args.prec, "kernel": args.kernel, "chain": args.chain,
             "parallelism": "replicas" if world > 1 else "single",
             "l2": "flushed between steps (256 MB write, inside the timed region)"}
 

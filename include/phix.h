@@ -46,8 +46,9 @@ extern "C" {
 #endif
 
 /* Rises whenever the layout of a public struct changes: callers must be built
- * against the header of the library they load (101: phix_opts.kiops_fused). */
-#define PHIX_VERSION 101
+ * against the header of the library they load (101: phix_opts.kiops_fused;
+ * 102: phix_opts.chain). */
+#define PHIX_VERSION 102
 
 typedef struct phix_ctx phix_ctx;
 
@@ -141,7 +142,17 @@ typedef struct {
                           orthogonalisation of step j staged in shared memory and pass 1
                           of step j + 1 read from it) when nx % 64 == 0 and ny % 8 == 0;
                           0, or other grids: two passes per step                      */
+  int chain;           /* Leja Newton pass with the single-step kernel:
+                          PHIX_CHAIN_AUTO (default) and PHIX_CHAIN_PERSISTENT run the
+                          whole pass in ONE cooperative launch (every block resident,
+                          one grid-wide barrier per iteration, the stop test taken by
+                          every block on the same totals; a barrier wait that exceeds
+                          2 s ends the pass with PHIX_ETIMEOUT); PHIX_CHAIN_GRAPH runs
+                          one launch per iteration inside a conditional CUDA graph.
+                          The TMA-staged kernel always runs one launch per iteration. */
 } phix_opts;
+
+typedef enum { PHIX_CHAIN_AUTO = 0, PHIX_CHAIN_PERSISTENT = 1, PHIX_CHAIN_GRAPH = 2 } phix_chain;
 
 typedef enum { PHIX_KERNEL_AUTO = 0, PHIX_KERNEL_SINGLE = 1, PHIX_KERNEL_TMA = 2 } phix_kernel;
 
@@ -170,6 +181,10 @@ typedef struct {
 
 void phix_opts_default(phix_opts* opts);
 int phix_version(void);
+/* sizeof(phix_opts) and sizeof(phix_stats) as the library was built: a caller's
+ * mirror of the structs (e.g. a foreign-function binding) checks its layout. */
+size_t phix_opts_size(void);
+size_t phix_stats_size(void);
 
 /* Create a context bound to a CUDA stream (cudaStream_t passed as void*,
  * NULL = legacy default stream) on the current device.  Returns PHIX_EINVAL
@@ -258,6 +273,43 @@ phix_status phix_step(phix_ctx* ctx, phix_scheme scheme, const phix_jop* op, dou
 phix_status phix_step_host(phix_ctx* ctx, phix_scheme scheme, const phix_jop* op, double* u_host_inout,
                            double h, double tol, phix_method method, const phix_opts* opts,
                            double* err_est, phix_stats* stats);
+
+/* ---- Automatic step-size control (Sec. 2.3) -------------------------------
+ * phix_integrate advances u' = f(u) from t = 0 to t_end with phix_step and a
+ * step-size controller:
+ *   traditional: dt_{n+1} = dt_n (tol / e_n)^(1/(p+1));
+ *   cost:        dt_{n+1} = min(dt_traditional, dt_n * F) with the cost
+ *                controller's factor F of Sec. 2.3 (alpha 0.65241444, beta
+ *                0.26862269, lambda 1.37412002, delta 0.64446017) applied to the
+ *                cost per unit time c_n = (Jacobian products of step n) / dt_n;
+ * e_n = ||u_high - u_low||_2 / sqrt(N); a step with e_n > tol (or whose
+ * phi-actions fail to converge) is rejected and retried (with the
+ * traditional step, or half the step after a failure); p is the order of
+ * the scheme's embedded estimate (3; EPIRK5P1: 4); the last step lands on
+ * t_end.  The cost controller starts from the third step (it needs two
+ * accepted steps).                                                          */
+typedef enum { PHIX_CONTROL_TRADITIONAL = 0, PHIX_CONTROL_COST = 1 } phix_controller;
+typedef struct {
+  double t_end;     /* > 0                                                         */
+  double dt0;       /* first trial step, > 0                                       */
+  double tol;       /* accept e_n <= tol                                           */
+  double iter_tol;  /* tolerance of the phi-actions (<= 0: tol)                   */
+  double dt_max;    /* > 0: largest step (bounds the step on linear problems, where
+                       e_n = 0); <= 0: none                                        */
+  int controller;   /* phix_controller                                             */
+  int max_steps;    /* accepted + rejected attempts; then PHIX_ENOTCONV            */
+} phix_adapt;
+typedef struct {
+  int status, accepted, rejected;
+  double t;             /* time reached (t_end on success)                         */
+  double dt_next;       /* the step the controller proposes after the last one      */
+  long long matvecs;    /* Jacobian-vector products of every attempt               */
+} phix_adapt_stats;
+/* u_inout: DEVICE state (length N), advanced in place.  dts (HOST, may be
+ * NULL): the accepted step sizes, at most max_steps entries.               */
+phix_status phix_integrate(phix_ctx* ctx, phix_scheme scheme, const phix_jop* op, double* u_inout,
+                           const phix_adapt* ad, phix_method method, const phix_opts* opts, double* dts,
+                           phix_adapt_stats* stats);
 
 /* One problem of a batch: a periodic advection-diffusion operator
  * J = D lap + ax d/dx + ay d/dy on an nx x ny grid, a step h, its spectral
@@ -377,6 +429,58 @@ phix_status phix_phi_action_noalloc(const phix_jop* op, double h, const double* 
                                     const int* l, const double* scale, double* const* out,
                                     double tol, const phix_opts* opts, void* cuda_stream,
                                     phix_stats* stats);
+
+/* ---- Domain decomposition (multi-GPU Leja) -------------------------------
+ * The Newton-Leja pass needs, per iteration, one stencil product and one
+ * reduction of squared norms (Sec. 2.2; the paper's low-communication case
+ * for Leja, Sec. 1 and Sec. 2.1), so it splits into rectangular blocks of the
+ * global periodic grid: each block is stored with a one-cell halo ring that
+ * the caller fills between iterations (a 4-face exchange), and the per-block
+ * norms are summed over all blocks by the caller (an allreduce).  These calls
+ * are the per-block kernels; the Python driver domain.py does the exchange,
+ * the (optionally lagged) allreduce and the stop test.  All float64, all
+ * asynchronous on the context's stream.
+ *
+ * Block layout: per species a padded (bx + 2) x (by + 2) plane, row-major,
+ * interior at rows 1..by and columns 1..bx (species planes back to back);
+ * accumulators p_k are unpadded bx x by planes per species.                 */
+typedef struct {
+  int kind;            /* phix_op_kind                                              */
+  int gnx, gny;        /* the global grid (dx = 1/gnx, dy = 1/gny, periodic)        */
+  int x0, y0;          /* first column / row of this block in the global grid       */
+  int bx, by;          /* block interior size, >= 1, inside the global grid         */
+  double param[8];     /* as phix_jop                                                */
+  const double* state; /* DEVICE, padded like y with filled halos: GRAYSCOTT (u, v),
+                          BURGERS (U); may be NULL for ADVDIFF                         */
+} phix_block;
+
+/* One Newton-Leja (or power) iteration on a block:
+ *   y_out == NULL:  p_k = dk[k] * y_in (interior), the pass's first term;
+ *   else:           y_out = a * J y_in + b * y_in on the interior of y_out
+ *                   (Newton: a = 1/gamma, b = -(c/gamma + xi_m); power: a =
+ *                   1/||y_in||, b = 0), p_k += dk[k] * y_out.
+ * y_in must have its halo filled.  norms (DEVICE, K + 1 doubles) receives
+ * ||y||^2 (y = y_in when initialising, else y_out) and ||p_k||^2 over the
+ * block interior.  0 <= K <= 4; p: HOST array of K device planes; dk: HOST
+ * array of K coefficients d_k[m].                                           */
+phix_status phix_block_newton(phix_ctx* ctx, const phix_block* blk, const double* y_in, double* y_out, int K,
+                              double* const* p, const double* dk, double a, double b, double* norms);
+
+/* Faces of a padded block: dir = 0 packs the interior faces of y_pad into
+ * faces, dir = 1 writes faces into the halo ring of y_pad.  faces (DEVICE):
+ * [S | N | W | E], each face all species back to back: ncomp*bx values for S
+ * and N (rows y = 1 and y = by; halos y = 0 and y = by + 1), ncomp*by for W
+ * and E (columns 1 and bx; halos 0 and bx + 1).                              */
+phix_status phix_block_faces(phix_ctx* ctx, const phix_block* blk, int dir, double* y_pad, double* faces);
+
+/* Interior of y_pad <- the power iteration's SplitMix64 start vector at this
+ * block's GLOBAL indices (species, row, column of the gnx x gny grid).      */
+phix_status phix_block_start(phix_ctx* ctx, const phix_block* blk, uint64_t seed, double* y_pad);
+
+/* Host utility: the stop test of Sec. 2.2 on global squared norms:
+ * 1 if m >= m_min and |dkm[k]| sqrt(ysq) <= tol sqrt(psq[k]) for every
+ * k < K; 0 if not; -1 if a norm is not finite.  HOST arrays.                */
+int phix_leja_stop(int K, int m, int m_min, const double* dkm, double tol, double ysq, const double* psq);
 
 /* Host utility: the first m real Leja points on [-2, 2] (xi_0 = 2,
  * xi_1 = -2, xi_2 = 0, then greedy max-product), Sec. 2.2.  xi is a HOST

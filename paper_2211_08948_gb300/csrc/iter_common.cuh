@@ -98,6 +98,40 @@ __device__ __forceinline__ void ldr2(const float* p, float& a, float& b) {
   a = t.x;
   b = t.y;
 }
+// loads of the Newton basis y: through the non-coherent path (COH = 0) when
+// every launch is one iteration, through L2 (COH = 1) in a persistent chain,
+// where other blocks rewrite the same addresses between iterations
+template <int COH>
+__device__ __forceinline__ double ldy1(const double* p) {
+  if constexpr (COH) return __ldcg(p); else return __ldg(p);
+}
+template <int COH>
+__device__ __forceinline__ df ldy1(const float2* p) {
+  if constexpr (COH) return cv(__ldcg(p)); else return cv(__ldg(p));
+}
+template <int COH>
+__device__ __forceinline__ float ldy1(const float* p) {
+  if constexpr (COH) return __ldcg(p); else return __ldg(p);
+}
+template <int COH>
+__device__ __forceinline__ void ldy2(const double* p, double& a, double& b) {
+  double2 t = COH ? __ldcg(reinterpret_cast<const double2*>(p)) : __ldg(reinterpret_cast<const double2*>(p));
+  a = t.x;
+  b = t.y;
+}
+template <int COH>
+__device__ __forceinline__ void ldy2(const float2* p, df& a, df& b) {
+  float4 t = COH ? __ldcg(reinterpret_cast<const float4*>(p)) : __ldg(reinterpret_cast<const float4*>(p));
+  a = df_make(t.x, t.y);
+  b = df_make(t.z, t.w);
+}
+template <int COH>
+__device__ __forceinline__ void ldy2(const float* p, float& a, float& b) {
+  float2 t = COH ? __ldcg(reinterpret_cast<const float2*>(p)) : __ldg(reinterpret_cast<const float2*>(p));
+  a = t.x;
+  b = t.y;
+}
+
 // read-write loads (accumulators)
 __device__ __forceinline__ double ldw1(const double* p) { return *p; }
 __device__ __forceinline__ df ldw1(const float2* p) { return cv(*p); }
@@ -216,6 +250,84 @@ __device__ bool block_partials_and_last(A (&acc)[NV], double* partials, unsigned
   }
   __syncthreads();
   return last;
+}
+
+// Persistent chains: the block's sums into partials[blockIdx.x * (KMAX+1) + j]
+// (the same block-level reduction as above, no arrival count).
+template <typename A, int NV>
+__device__ void block_partials_only(A (&acc)[NV], double* partials) {
+  __shared__ double sred[THREADS / 32][KMAX + 1];
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    A v = acc[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = acc_add(v, shfl_down(v, o));
+    if (lane == 0) {
+      if constexpr (PartialsDF<A>::value) {
+        const df d = acc_to_df(v);
+        reinterpret_cast<float2*>(&sred[warp][j])[0] = make_float2(d.hi, d.lo);
+      } else {
+        sred[warp][j] = v;
+      }
+    }
+  }
+  __syncthreads();
+  if (tid < NV) {
+    if constexpr (PartialsDF<A>::value) {
+      df s = df_make(0.f, 0.f);
+      for (int w = 0; w < THREADS / 32; ++w) s = df_add(s, cv(reinterpret_cast<const float2*>(&sred[w][tid])[0]));
+      reinterpret_cast<float2*>(partials + (size_t)blockIdx.x * (KMAX + 1) + tid)[0] = make_float2(s.hi, s.lo);
+    } else {
+      double s = 0.0;
+      for (int w = 0; w < THREADS / 32; ++w) s += sred[w][tid];
+      partials[(size_t)blockIdx.x * (KMAX + 1) + tid] = s;
+    }
+  }
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid-wide barrier of a cooperative launch (every block resident): arrival
+// count and generation in device memory, both zero at the chain's start.
+// The wait is bounded (2 s of %globaltimer): on expiry the barrier returns
+// false in every thread of the block, which must then leave the kernel.
+__device__ __forceinline__ bool grid_barrier(unsigned int* count, unsigned int* gen) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    int ok = 1;
+    const unsigned int g = ld_acquire(gen);  // the generation before this block arrives
+    __threadfence();                         // the block's writes visible before its arrival
+    if (atomicAdd(count, 1u) == gridDim.x - 1) {
+      atomicExch(count, 0u);
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      const unsigned long long t0 = globaltimer_ns();
+      while (ld_acquire(gen) == g) {
+        if (globaltimer_ns() - t0 > 2000000000ull) {
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
 }
 
 // Last block: totals[j] = sum over blocks of the partials (fixed order: up to
@@ -530,5 +642,16 @@ template <>
 __device__ __forceinline__ df coef<df>(double, float2 f) { return df_make(f.x, f.y); }
 template <>
 __device__ __forceinline__ float coef<float>(double, float2 f) { return f.x; }
+
+// SplitMix64 (Steele, Lea & Flood 2014): x_i = seed + (i+1)*golden; 64-bit
+// finaliser; the top 53 bits mapped to [-0.5, 0.5).  The power iteration's
+// start vector, element i of the stream `seed`.
+__device__ __forceinline__ double splitmix_uniform(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z = z ^ (z >> 31);
+  return (double)(z >> 11) * 0x1.0p-53 - 0.5;
+}
 
 }  // namespace phix

@@ -48,8 +48,8 @@ __device__ __forceinline__ void stop_loop(const IterDev& a) {
 // ---------------------------------------------------------------------------
 // The iteration kernel.
 // ---------------------------------------------------------------------------
-template <int P, int OP, int V, int MODE>
-__global__ void __launch_bounds__(THREADS) k_iter(IterDev a) {
+template <int P, int OP, int V, int MODE, int PERSIST>
+__global__ void __launch_bounds__(THREADS, 2) k_iter(IterDev a) {
   using T = typename Tr<P>::T;
   using C = typename Tr<P>::C;
   using CJ = typename Tr<P>::CJ;
@@ -64,16 +64,18 @@ __global__ void __launch_bounds__(THREADS) k_iter(IterDev a) {
     if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) stop_loop(a);
     return;
   }
-  const int m = __ldcg(&a.ctl->m);
+  int m = __ldcg(&a.ctl->m);
   const PassParams* pp = pp_of(a.ptab);
   const int M = pp->M;
   const int K = (MODE == MODE_NEWTON) ? pp->K : 0;
-
+  const CJ ga = coef<CJ>(pp->gad, pp->gaf);
+  const bool prescaled = MODE == MODE_NEWTON && pp->prescaled;
+  // PERSIST: every iteration of the chain in this one (cooperative) launch,
+  // one grid barrier per iteration; otherwise one iteration per launch
+  for (;;) {
   CJ kk[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) kk[j] = coef<CJ>(pp->kd[j], pp->kf[j]);
-  const CJ ga = coef<CJ>(pp->gad, pp->gaf);
-  const bool prescaled = MODE == MODE_NEWTON && pp->prescaled;
   C beta{};
   C dk[KMAX];
   C alpha_pw{};
@@ -123,16 +125,16 @@ __global__ void __launch_bounds__(THREADS) k_iter(IterDev a) {
     for (int q = 0; q < NC; ++q) {
       const T* b = yin + q * plane;
       if constexpr (V == 2) {
-        ldr2(b + row + ix, c[q][0], c[q][1]);
-        ldr2(b + rowp + ix, nn[q][0], nn[q][1]);
-        ldr2(b + rowm + ix, ss[q][0], ss[q][1]);
+        ldy2<PERSIST>(b + row + ix, c[q][0], c[q][1]);
+        ldy2<PERSIST>(b + rowp + ix, nn[q][0], nn[q][1]);
+        ldy2<PERSIST>(b + rowm + ix, ss[q][0], ss[q][1]);
       } else {
-        c[q][0] = ldr1(b + row + ix);
-        nn[q][0] = ldr1(b + rowp + ix);
-        ss[q][0] = ldr1(b + rowm + ix);
+        c[q][0] = ldy1<PERSIST>(b + row + ix);
+        nn[q][0] = ldy1<PERSIST>(b + rowp + ix);
+        ss[q][0] = ldy1<PERSIST>(b + rowm + ix);
       }
-      we[q] = ldr1(b + row + ixm);
-      ea[q] = ldr1(b + row + ixp);
+      we[q] = ldy1<PERSIST>(b + row + ixm);
+      ea[q] = ldy1<PERSIST>(b + row + ixp);
     }
 
     // accumulators p_k, loaded before any store of this tile so that all
@@ -237,6 +239,61 @@ __global__ void __launch_bounds__(THREADS) k_iter(IterDev a) {
     }
   }
 
+  if constexpr (PERSIST) {
+    // block partials into this iteration's half of the partials buffer (the
+    // halves alternate, so a block can write iteration m + 1's sums while a
+    // slower one still reads iteration m's), the grid barrier, then every
+    // block forms the same totals in the same order and takes the same stop
+    // decision; block 0 records it in the control block
+    static_assert(MODE == MODE_NEWTON, "persistent chains run Newton-Leja passes");
+    double* part = a.partials + (size_t)(m & 1) * gridDim.x * (KMAX + 1);
+    block_partials_only<Acc, KMAX + 1>(acc, part);
+    if (!grid_barrier(&a.ctl->bar_count, &a.ctl->bar_gen)) {
+      if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
+        a.ctl->status = PHIX_ETIMEOUT;
+        a.ctl->iters = m;
+        a.ctl->done = 1;
+      }
+      return;
+    }
+    __shared__ int s_done;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    LejaCtl local{};
+    if constexpr (PartialsDF<Acc>::value) {
+      float2 qk[KMAX];
+#pragma unroll
+      for (int k = 0; k < KMAX; ++k)
+        qk[k] = (tid == 0 && k < K) ? q_f_of(a.ptab, M)[k * M + m] : make_float2(0.f, 0.f);
+      df tot[KMAX + 1];
+      reduce_partials_df<Acc, KMAX + 1>(part, tot, K + 1);
+      if (tid == 0) leja_test_df(&local, m, K, pp->m_min, pp->m_max, qk, tot);
+    } else {
+      double dkd[KMAX];
+#pragma unroll
+      for (int k = 0; k < KMAX; ++k) dkd[k] = (tid == 0 && k < K) ? dk_d_of(a.ptab, M)[k * M + m] : 0.0;
+      double tot[KMAX + 1];
+      reduce_partials<Acc, KMAX + 1>(part, tot, NoHook{}, K + 1);
+      if (tid == 0) leja_test(&local, m, K, pp->m_min, pp->m_max, pp->tol, dkd, tot);
+    }
+    if (tid == 0) {
+      s_done = local.done;
+      if (blockIdx.x == 0) {
+        LejaCtl* ctl = a.ctl;
+        if (local.done) {
+          ctl->status = local.status;
+          ctl->iters = local.iters;
+          ctl->ysq = local.ysq;
+          for (int k = 0; k < KMAX; ++k) ctl->psq[k] = local.psq[k];
+          ctl->done = 1;
+        }
+        ctl->m = m + 1;
+      }
+    }
+    __syncthreads();
+    if (s_done) return;
+    ++m;
+    continue;
+  }
   if (block_partials_and_last<Acc, KMAX + 1>(acc, a.partials, &a.ctl->count)) {
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     if constexpr (MODE == MODE_NEWTON && PartialsDF<Acc>::value) {
@@ -298,6 +355,8 @@ __global__ void __launch_bounds__(THREADS) k_iter(IterDev a) {
       }
     }
   }
+  return;
+  }  // for (;;)
 }
 
 // ---------------------------------------------------------------------------
@@ -409,15 +468,6 @@ __global__ void __launch_bounds__(THREADS) k_finalize(size_t n, int K, PtrPack p
       o[i] = s * d;
     }
   }
-}
-
-// SplitMix64 (Steele, Lea & Flood 2014): x_i = seed + (i+1)*golden; 64-bit finaliser.
-__device__ __forceinline__ double splitmix_uniform(uint64_t seed, uint64_t i) {
-  uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  z = z ^ (z >> 31);
-  return (double)(z >> 11) * 0x1.0p-53 - 0.5;
 }
 
 template <int P>
@@ -561,7 +611,37 @@ static IterDev make_dev(const ChainSpec& s, int V) {
 // the kernel function of a spec
 template <int P, int OP, int MODE>
 static void* kfn_t(int V) {
-  return V == 2 ? (void*)k_iter<P, OP, 2, MODE> : (void*)k_iter<P, OP, 1, MODE>;
+  return V == 2 ? (void*)k_iter<P, OP, 2, MODE, 0> : (void*)k_iter<P, OP, 1, MODE, 0>;
+}
+template <int P, int OP>
+static void* kfn_chain_op(int V) {
+  return V == 2 ? (void*)k_iter<P, OP, 2, MODE_NEWTON, 1> : (void*)k_iter<P, OP, 1, MODE_NEWTON, 1>;
+}
+template <int P>
+static void* kfn_chain_p(int op, int V) {
+  switch (op) {
+    case PHIX_OP_ADVDIFF:
+      return kfn_chain_op<P, PHIX_OP_ADVDIFF>(V);
+    case PHIX_OP_GRAYSCOTT:
+      return kfn_chain_op<P, PHIX_OP_GRAYSCOTT>(V);
+    case PHIX_OP_BURGERS:
+      return kfn_chain_op<P, PHIX_OP_BURGERS>(V);
+  }
+  return nullptr;
+}
+// the persistent (whole-chain) Newton kernel of a spec
+static void* kfn_chain(const ChainSpec& s, int V) {
+  switch (s.prec) {
+    case P_FP64:
+      return kfn_chain_p<P_FP64>(s.op, V);
+    case P_DF64:
+      return kfn_chain_p<P_DF64>(s.op, V);
+    case P_FP32JV:
+      return kfn_chain_p<P_FP32JV>(s.op, V);
+    case P_FP32:
+      return kfn_chain_p<P_FP32>(s.op, V);
+  }
+  return nullptr;
 }
 template <int P, int MODE>
 static void* kfn_op(int op, int V) {
@@ -622,6 +702,27 @@ cudaError_t launch_iter(const ChainSpec& s, cudaStream_t st) {
   void* args[1] = {&a};
   dim3 grid(s.grid < a.ntiles ? s.grid : a.ntiles);
   return cudaLaunchKernel(fn, grid, dim3(32, TILE_Y), args, 0, st);
+}
+
+int chain_grid(const ChainSpec& s, int nsm) {
+  const int V = (s.nx % 2 == 0) ? 2 : 1;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kfn_chain(s, V), THREADS, 0) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  const int ntiles = make_dev(s, V).ntiles;
+  const int g = nb * nsm;
+  return g < ntiles ? g : ntiles;
+}
+
+cudaError_t launch_chain(const ChainSpec& s, cudaStream_t st) {
+  const int V = (s.nx % 2 == 0) ? 2 : 1;
+  IterDev a = make_dev(s, V);
+  void* fn = kfn_chain(s, V);
+  if (!fn || s.grid < 1) return cudaErrorInvalidValue;
+  void* args[1] = {&a};
+  return cudaLaunchCooperativeKernel(fn, dim3(s.grid), dim3(32, TILE_Y), args, 0, st);
 }
 
 int iter_tiles(const ChainSpec& s) {

@@ -81,64 +81,159 @@ __global__ void __launch_bounds__(128) k_mlp_fwd(const float* __restrict__ p, co
   for (int j = 0; j < NO; ++j) Y[(size_t)s * NO + j] = y[j];
 }
 
-// Gradient of the batch-mean loss over samples [0, n) of (X, T): one CTA,
-// per-sample backward, shared-memory float atomics for the parameter sums.
-__global__ void __launch_bounds__(256) k_mlp_grad(const float* __restrict__ p, const float* __restrict__ X,
-                                                  const float* __restrict__ T, int n, float* __restrict__ G,
-                                                  float* loss_out) {
-  __shared__ Net net;
-  __shared__ float g[NP];
-  __shared__ float lsum;
-  const int tid = threadIdx.x;
-  load_net(p, net, tid, blockDim.x);
-  for (int i = tid; i < NP; i += blockDim.x) g[i] = 0.f;
-  if (tid == 0) lsum = 0.f;
-  __syncthreads();
+// Gradient of the batch-mean loss over samples [0, n) of (X, T): one CTA of
+// 256 threads, the batch in chunks of GC samples held in shared memory as
+// row-major activation tiles (rows padded to 65 floats: a warp reading 32
+// consecutive samples of one unit hits 32 banks).  Each layer is a small
+// dense product done with warp-broadcast weights; each thread owns a fixed
+// set of weight-gradient entries and accumulates them in registers over the
+// whole batch (no atomics), so the sums run in one fixed order.
+constexpr int GC = 64;            // samples per chunk
+constexpr int LD = 65;            // padded row length of the activation tiles
+constexpr int GT = 256;           // threads
+struct GradSmem {
+  float w1[H1 * NI];              // bf16-rounded weights as float32, natural layout W[j][i]
+  float w2[H2 * H1];
+  float w3[NO * H2];
+  float b[NB];
+  float x[GC * NI];
+  float z1[GC * LD], a1[GC * LD], z2[GC * LD], a2[GC * LD];
+  float dy[GC * 4];
+  float red[GT / 32][NO + 1];
+};
+
+__device__ __forceinline__ float bf(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+
+__global__ void __launch_bounds__(GT) k_mlp_grad(const float* __restrict__ p, const float* __restrict__ X,
+                                                 const float* __restrict__ T, int n, float* __restrict__ G,
+                                                 float* loss_out) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  GradSmem& S = *reinterpret_cast<GradSmem*>(smraw);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int i = tid; i < H1 * NI; i += GT) S.w1[i] = bf(p[OW1 + i]);
+  for (int i = tid; i < H2 * H1; i += GT) S.w2[i] = bf(p[OW2 + i]);
+  for (int i = tid; i < NO * H2; i += GT) S.w3[i] = bf(p[OW3 + i]);
+  for (int i = tid; i < H1; i += GT) S.b[i] = p[OB1 + i];
+  for (int i = tid; i < H2; i += GT) S.b[H1 + i] = p[OB2 + i];
+  if (tid < NO) S.b[H1 + H2 + tid] = p[OB3 + tid];
+  // register accumulators: W2 entries e = tid + 256 q (16), W1 entries tid + 256 q (4),
+  // W3 entry tid (tid < 192), b1 / b2 entry in gb (tid < 64 / 64 <= tid < 128), b3 in gb3 (tid < 3)
+  float gw2[16], gw1[4], gw3 = 0.f, gb = 0.f, gb3 = 0.f, lacc = 0.f;
+#pragma unroll
+  for (int q = 0; q < 16; ++q) gw2[q] = 0.f;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) gw1[q] = 0.f;
   const float inv_n = 1.f / n;
-  for (int s = tid; s < n; s += blockDim.x) {
-    float x[NI], z1[H1], a1[H1], z2[H2], a2[H2], y[NO];
-    for (int i = 0; i < NI; ++i) x[i] = X[(size_t)s * NI + i];
-    mlp_sample(net, x, z1, a1, z2, a2, y);
-    float dy[NO], l = 0.f;
-    for (int j = 0; j < NO; ++j) {
-      const float t = T[(size_t)s * NO + j];
-      const float d = y[j] - t;
-      const float w = (j == 0 && y[0] < t) ? 4.f : 1.f;
-      l += w * d * d;
-      dy[j] = 2.f * w * d * inv_n;
-    }
-    atomicAdd(&lsum, l * inv_n);
-    // layer 3
-    float da2[H2];
-    for (int i = 0; i < H2; ++i) da2[i] = 0.f;
-    for (int j = 0; j < NO; ++j) {
-      atomicAdd(&g[OB3 + j], dy[j]);
-      for (int i = 0; i < H2; ++i) {
-        atomicAdd(&g[OW3 + j * H2 + i], dy[j] * a2[i]);
-        da2[i] = fmaf(dy[j], wv(net, OW3 + j * H2 + i), da2[i]);
-      }
-    }
-    // layer 2
-    float da1[H1];
-    for (int i = 0; i < H1; ++i) da1[i] = 0.f;
-    for (int j = 0; j < H2; ++j) {
-      const float dz = da2[j] * gelu_d(z2[j]);
-      atomicAdd(&g[OB2 + j], dz);
-      for (int i = 0; i < H1; ++i) {
-        atomicAdd(&g[OW2 + j * H1 + i], dz * a1[i]);
-        da1[i] = fmaf(dz, wv(net, OW2 + j * H1 + i), da1[i]);
-      }
-    }
-    // layer 1
-    for (int j = 0; j < H1; ++j) {
-      const float dz = da1[j] * gelu_d(z1[j]);
-      atomicAdd(&g[OB1 + j], dz);
-      for (int i = 0; i < NI; ++i) atomicAdd(&g[OW1 + j * NI + i], dz * x[i]);
-    }
-  }
   __syncthreads();
-  for (int i = tid; i < NP; i += blockDim.x) G[i] = g[i];
-  if (tid == 0 && loss_out) *loss_out = lsum;
+  for (int c0 = 0; c0 < n; c0 += GC) {
+    const int cn = min(GC, n - c0);
+    for (int i = tid; i < GC * NI; i += GT) S.x[i] = (i / NI) < cn ? X[(size_t)c0 * NI + i] : 0.f;
+    __syncthreads();
+    // layer 1: thread -> sample s = lane + 32 (warp & 1), units j = (warp >> 1) + 4 r
+    const int s = lane + 32 * (warp & 1);
+    for (int r = 0; r < H1 / 4; ++r) {
+      const int j = (warp >> 1) + 4 * r;
+      float z = S.b[j];
+#pragma unroll
+      for (int i = 0; i < NI; ++i) z = fmaf(S.w1[j * NI + i], S.x[s * NI + i], z);
+      S.z1[s * LD + j] = z;
+      S.a1[s * LD + j] = gelu(z);
+    }
+    __syncthreads();
+    for (int r = 0; r < H2 / 4; ++r) {
+      const int j = (warp >> 1) + 4 * r;
+      float z = S.b[H1 + j];
+#pragma unroll 16
+      for (int i = 0; i < H1; ++i) z = fmaf(S.w2[j * H1 + i], S.a1[s * LD + i], z);
+      S.z2[s * LD + j] = z;
+      S.a2[s * LD + j] = gelu(z);
+    }
+    __syncthreads();
+    // outputs, loss and dL/dy (threads 0..GC-1, one sample each)
+    if (tid < GC) {
+      float l = 0.f;
+#pragma unroll
+      for (int j = 0; j < NO; ++j) {
+        float y = S.b[H1 + H2 + j];
+        for (int i = 0; i < H2; ++i) y = fmaf(S.w3[j * H2 + i], S.a2[tid * LD + i], y);
+        float d = 0.f;
+        if (tid < cn) {
+          const float t = T[(size_t)(c0 + tid) * NO + j];
+          const float e = y - t;
+          const float w = (j == 0 && y < t) ? 4.f : 1.f;
+          l += w * e * e;
+          d = 2.f * w * e * inv_n;
+        }
+        S.dy[tid * 4 + j] = d;
+      }
+      lacc += l * inv_n;
+    }
+    __syncthreads();
+    // dW3, db3
+    if (tid < NO * H2) {
+      const int j = tid / H2, i = tid % H2;
+      for (int q = 0; q < GC; ++q) gw3 = fmaf(S.dy[q * 4 + j], S.a2[q * LD + i], gw3);
+    }
+    if (tid < NO)
+      for (int q = 0; q < GC; ++q) gb3 += S.dy[q * 4 + tid];
+    // dZ2 = (dY W3) * gelu'(Z2), in place of Z2
+    for (int r = 0; r < H2 / 4; ++r) {
+      const int j = (warp >> 1) + 4 * r;
+      float d = 0.f;
+#pragma unroll
+      for (int o = 0; o < NO; ++o) d = fmaf(S.dy[s * 4 + o], S.w3[o * H2 + j], d);
+      S.z2[s * LD + j] = d * gelu_d(S.z2[s * LD + j]);
+    }
+    __syncthreads();
+    // dW2[j][i] += sum_s dZ2[s][j] A1[s][i]  (entries e = tid + 256 q: j = e / 64, i = e % 64)
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int e = tid + GT * q, j = e / H1, i = e % H1;
+      float acc = gw2[q];
+      for (int t = 0; t < GC; ++t) acc = fmaf(S.z2[t * LD + j], S.a1[t * LD + i], acc);
+      gw2[q] = acc;
+    }
+    if (tid >= H1 && tid < H1 + H2)
+      for (int t = 0; t < GC; ++t) gb += S.z2[t * LD + tid - H1];
+    __syncthreads();
+    // dZ1 = (dZ2 W2) * gelu'(Z1), into the A1 tile (A1 is no longer needed)
+    for (int r = 0; r < H1 / 4; ++r) {
+      const int i = (warp >> 1) + 4 * r;
+      float d = 0.f;
+#pragma unroll 16
+      for (int j = 0; j < H2; ++j) d = fmaf(S.z2[s * LD + j], S.w2[j * H1 + i], d);
+      S.a1[s * LD + i] = d * gelu_d(S.z1[s * LD + i]);
+    }
+    __syncthreads();
+    // dW1[j][i] += sum_s dZ1[s][j] X[s][i] (entries e = tid + 256 q: j = e / 16, i = e % 16), db1
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid + GT * q, j = e / NI, i = e % NI;
+      float acc = gw1[q];
+      for (int t = 0; t < GC; ++t) acc = fmaf(S.a1[t * LD + j], S.x[t * NI + i], acc);
+      gw1[q] = acc;
+    }
+    if (tid < H1)
+      for (int t = 0; t < GC; ++t) gb += S.a1[t * LD + tid];
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 16; ++q) G[OW2 + tid + GT * q] = gw2[q];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) G[OW1 + tid + GT * q] = gw1[q];
+  if (tid < NO * H2) G[OW3 + tid] = gw3;
+  if (tid < H1) G[OB1 + tid] = gb;
+  if (tid >= H1 && tid < H1 + H2) G[OB2 + tid - H1] = gb;
+  if (tid < NO) G[OB3 + tid] = gb3;
+  // batch loss: threads 0..GC-1 hold their samples' terms
+  for (int o = 16; o > 0; o >>= 1) lacc += __shfl_down_sync(0xffffffffu, lacc, o);
+  if (lane == 0) S.red[warp][0] = lacc;
+  __syncthreads();
+  if (tid == 0 && loss_out) {
+    float l = 0.f;
+    for (int w = 0; w < GT / 32; ++w) l += S.red[w][0];
+    *loss_out = l;
+  }
 }
 
 // Adam (Kingma & Ba 2015) on the float32 master weights; step counts from 1
@@ -274,7 +369,9 @@ cudaError_t launch_mlp_forward(const float* p, const float* X, int n, float* Y, 
 
 cudaError_t launch_mlp_grad(const float* p, const float* X, const float* T, int n, float* G, float* loss,
                             cudaStream_t st) {
-  k_mlp_grad<<<1, 256, 0, st>>>(p, X, T, n, G, loss);
+  cudaError_t e = cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(GradSmem));
+  if (e != cudaSuccess) return e;
+  k_mlp_grad<<<1, GT, sizeof(GradSmem), st>>>(p, X, T, n, G, loss);
   return cudaGetLastError();
 }
 

@@ -29,7 +29,7 @@ enum Slot {
   S_ST2,                                                         // Gray-Scott state planes scaled for Newton passes
   S_BPROB, S_BORDER, S_BWS, S_BQ, S_XI,                          // batched problems, order, arena, queue, Leja points
   S_MFEAT, S_MY, S_MG, S_MCNT,                                   // learned interval: features, outputs, gradient
-  S_FH, S_O4, S_O5, S_O6, S_UH,                                  // stages: f h, more outputs, device copy of a host state
+  S_FH, S_O4, S_O5, S_O6, S_UH, S_UB,                            // stages: f h, more outputs, host-state copy, step backup
   S_NSLOT
 };
 
@@ -65,6 +65,7 @@ struct phix_ctx {
     double bytes_per_launch;
     int m_table;          // last iteration the pass's table covers
     int m_limit;          // the caller's m_max
+    bool persistent;      // one cooperative launch ran the whole chain
   };
   std::vector<Pending> pend;     // queued passes since the last flush
   int nslot = 0;                 // slots in use
@@ -178,6 +179,33 @@ void check_op(phix_ctx* ctx, const phix_jop* op, bool need_state) {
     fail(ctx, PHIX_EINVAL, "operator kind %d needs a state vector", op->kind);
 }
 
+// Uniform coefficients of the Jacobian's stencil on an nx x ny periodic grid
+// of the unit square (dx = 1/nx, dy = 1/ny), Sec. 3 centred differences.
+void uniform_coeffs(int kind, int nx, int ny, const double* p, double (&k)[8]) {
+  const double idx2 = (double)nx * nx, idy2 = (double)ny * ny;
+  for (double& x : k) x = 0.0;
+  if (kind == PHIX_OP_ADVDIFF) {
+    k[0] = p[0] * idx2 + 0.5 * p[1] * nx;  // E
+    k[1] = p[0] * idx2 - 0.5 * p[1] * nx;  // W
+    k[2] = p[0] * idy2 + 0.5 * p[2] * ny;  // N (y + 1)
+    k[3] = p[0] * idy2 - 0.5 * p[2] * ny;  // S
+    k[4] = -2.0 * p[0] * (idx2 + idy2);    // C
+  } else if (kind == PHIX_OP_GRAYSCOTT) {
+    k[0] = p[0] * idx2;
+    k[1] = p[0] * idy2;
+    k[2] = -2.0 * p[0] * (idx2 + idy2) - p[2];
+    k[3] = p[1] * idx2;
+    k[4] = p[1] * idy2;
+    k[5] = -2.0 * p[1] * (idx2 + idy2) - (p[2] + p[3]);
+  } else {
+    k[0] = p[0] * idx2;
+    k[1] = p[0] * idy2;
+    k[2] = -2.0 * p[0] * (idx2 + idy2);
+    k[3] = 0.5 * nx;
+    k[4] = 0.5 * ny;
+  }
+}
+
 OpState make_opstate(phix_ctx* ctx, const phix_jop* op, const double* state, int prec) {
   OpState s{};
   s.d.kind = op->kind;
@@ -188,29 +216,7 @@ OpState make_opstate(phix_ctx* ctx, const phix_jop* op, const double* state, int
   s.plane = (size_t)op->nx * op->ny;
   s.N = s.plane * s.ncomp;
   s.state = state;
-  const double idx2 = (double)op->nx * op->nx, idy2 = (double)op->ny * op->ny;
-  const double* p = op->param;
-  for (double& k : s.kJ) k = 0.0;
-  if (op->kind == PHIX_OP_ADVDIFF) {
-    s.kJ[0] = p[0] * idx2 + 0.5 * p[1] * op->nx;  // E
-    s.kJ[1] = p[0] * idx2 - 0.5 * p[1] * op->nx;  // W
-    s.kJ[2] = p[0] * idy2 + 0.5 * p[2] * op->ny;  // N (y + 1)
-    s.kJ[3] = p[0] * idy2 - 0.5 * p[2] * op->ny;  // S
-    s.kJ[4] = -2.0 * p[0] * (idx2 + idy2);        // C
-  } else if (op->kind == PHIX_OP_GRAYSCOTT) {
-    s.kJ[0] = p[0] * idx2;
-    s.kJ[1] = p[0] * idy2;
-    s.kJ[2] = -2.0 * p[0] * (idx2 + idy2) - p[2];
-    s.kJ[3] = p[1] * idx2;
-    s.kJ[4] = p[1] * idy2;
-    s.kJ[5] = -2.0 * p[1] * (idx2 + idy2) - (p[2] + p[3]);
-  } else {
-    s.kJ[0] = p[0] * idx2;
-    s.kJ[1] = p[0] * idy2;
-    s.kJ[2] = -2.0 * p[0] * (idx2 + idy2);
-    s.kJ[3] = 0.5 * op->nx;
-    s.kJ[4] = 0.5 * op->ny;
-  }
+  uniform_coeffs(op->kind, op->nx, op->ny, op->param, s.kJ);
   s.st = nullptr;
   if (op->kind != PHIX_OP_ADVDIFF) {
     size_t nplanes = op->kind == PHIX_OP_GRAYSCOTT ? 2 : 1;
@@ -243,8 +249,9 @@ void flush(phix_ctx* ctx) {
   for (const phix_ctx::Pending& q : ctx->pend) {
     const LejaCtl& c = ctx->ctl_h[q.slot];
     // the WHILE loop ran until the body holding iteration `iters` (one body
-    // when the chain stopped before its first iteration)
-    ctx->launches += (long)GRAPH_ITERS * std::max(1, (c.iters + GRAPH_ITERS - 1) / GRAPH_ITERS);
+    // when the chain stopped before its first iteration); a persistent chain
+    // is one launch
+    ctx->launches += q.persistent ? 1 : (long)GRAPH_ITERS * std::max(1, (c.iters + GRAPH_ITERS - 1) / GRAPH_ITERS);
     if (!q.stats) continue;
     const int status = c.done ? c.status : PHIX_ENOTCONV;
     if (status == PHIX_ENOTCONV && c.iters == q.m_table && q.m_table < q.m_limit) {
@@ -447,16 +454,32 @@ void leja_pass(phix_ctx* ctx, const OpState& os, int prec, const double* v, int 
     const bool want = o.kernel == PHIX_KERNEL_TMA || (o.kernel == PHIX_KERNEL_AUTO && work > ctx->l2_bytes);
     cs.tma = want && tma_eligible(cs) ? 1 : 0;
   }
+  bool persistent = false;
   if (cs.tma) {
     cs.grid = tma_grid(cs, ctx->nsm);
   } else {
-    const int gmax = ctx->nsm * std::min(8, iter_blocks_per_sm(cs));
-    const int ntiles = iter_tiles(cs);
-    const int per = (ntiles + gmax - 1) / gmax;  // tiles per block, balanced
-    cs.grid = (ntiles + per - 1) / per;
+    if (o.chain != PHIX_CHAIN_GRAPH) {
+      // the whole pass in one cooperative launch: every block resident, its
+      // partials double-buffered (2 x grid x (KMAX + 1) doubles)
+      const int g = chain_grid(cs, ctx->nsm);
+      persistent = g >= 1 && 2 * g <= ctx->grid_iter;
+      if (persistent) cs.grid = g;
+    }
+    if (!persistent) {
+      const int gmax = ctx->nsm * std::min(8, iter_blocks_per_sm(cs));
+      const int ntiles = iter_tiles(cs);
+      const int per = (ntiles + gmax - 1) / gmax;  // tiles per block, balanced
+      cs.grid = (ntiles + per - 1) / per;
+    }
   }
   const bool profile = o.profile != 0;
-  queue_chain(ctx, s, cs, profile, o.profile == 2, m_max);
+  if (persistent) {
+    if (profile) CK(cudaEventRecord(ctx->ev[2 * s], ctx->stream));
+    CK(launch_chain(cs, ctx->stream));
+    if (profile) CK(cudaEventRecord(ctx->ev[2 * s + 1], ctx->stream));
+  } else {
+    queue_chain(ctx, s, cs, profile, o.profile == 2, m_max);
+  }
   stats.tma_passes += cs.tma;
   KL(launch_finalize(prec, os.N, K, p, out, ctl, ctx->grid_stream, ctx->stream));
   phix_ctx::Pending q{};
@@ -465,6 +488,7 @@ void leja_pass(phix_ctx* ctx, const OpState& os, int prec, const double* v, int 
   q.profile = profile;
   q.m_table = m_max;
   q.m_limit = o.m_max;
+  q.persistent = persistent;
   if (profile) {
     // algorithmic bytes of one iteration launch: read y, write the new
     // iterate, read and write each p_k, read the state planes
@@ -966,6 +990,7 @@ phix_opts resolve_opts(phix_ctx* ctx, const phix_opts* in) {
   if (o.profile < 0 || o.profile > 2) fail(ctx, PHIX_EINVAL, "profile must be 0, 1 or 2");
   if (o.kiops_m_max < 2 || o.kiops_m_max > 128) fail(ctx, PHIX_EINVAL, "kiops_m_max must be in 2..128");
   if (o.kiops_fused != 0 && o.kiops_fused != 1) fail(ctx, PHIX_EINVAL, "kiops_fused must be 0 or 1");
+  if (o.chain < PHIX_CHAIN_AUTO || o.chain > PHIX_CHAIN_GRAPH) fail(ctx, PHIX_EINVAL, "unknown chain mode %d", o.chain);
   return o;
 }
 
@@ -1020,6 +1045,8 @@ phix_status guarded(phix_ctx* ctx, phix_stats* stats, F&& body) {
 extern "C" {
 
 int phix_version(void) { return PHIX_VERSION; }
+size_t phix_opts_size(void) { return sizeof(phix_opts); }
+size_t phix_stats_size(void) { return sizeof(phix_stats); }
 
 void phix_opts_default(phix_opts* o) {
   if (!o) return;
@@ -1041,6 +1068,7 @@ void phix_opts_default(phix_opts* o) {
   o->kiops_m_step = 8;
   o->kiops_max_substeps = 10000;
   o->kiops_fused = 1;
+  o->chain = PHIX_CHAIN_AUTO;
 }
 
 phix_status phix_create(phix_ctx** out, void* stream) {
@@ -1702,6 +1730,156 @@ phix_status phix_step_host(phix_ctx* ctx, phix_scheme scheme, const phix_jop* op
                            double tol, phix_method method, const phix_opts* opts, double* err_est,
                            phix_stats* stats) {
   return exp_step(ctx, (int)scheme, op, nullptr, u_host_inout, h, tol, method, opts, err_est, stats);
+}
+
+// ---- automatic step-size control (Sec. 2.3) --------------------------------
+static double cost_factor(double c_n, double c_prev, double dt_n, double dt_prev) {
+  const double alpha = 0.65241444, beta = 0.26862269, lambda = 1.37412002, delta = 0.64446017;
+  const double den = std::log(dt_n) - std::log(dt_prev);
+  const double D = std::fabs(den) < 1e-14 ? 0.0 : (std::log(c_n) - std::log(c_prev)) / den;
+  const double sf = std::exp(-alpha * std::tanh(beta * D));
+  if (sf >= 1.0 && sf < lambda) return lambda;
+  if (sf >= delta && sf < 1.0) return delta;
+  return sf;
+}
+
+phix_status phix_integrate(phix_ctx* ctx, phix_scheme scheme, const phix_jop* op, double* u, const phix_adapt* ad,
+                           phix_method method, const phix_opts* opts, double* dts, phix_adapt_stats* stats) {
+  phix_adapt_stats as{};
+  auto finish = [&](phix_status rc) {
+    as.status = rc;
+    if (stats) *stats = as;
+    return rc;
+  };
+  if (!ctx) return finish(PHIX_EINVAL);
+  double* backup = nullptr;
+  size_t N = 0;
+  phix_status rc = guarded(ctx, nullptr, [&](phix_stats&) -> phix_status {
+    check_op(ctx, op, false);
+    if (!u || !ad) fail(ctx, PHIX_EINVAL, "u_inout or adapt is NULL");
+    if (!(ad->t_end > 0) || !(ad->dt0 > 0) || !(ad->tol > 0) || ad->max_steps < 1 ||
+        (ad->controller != PHIX_CONTROL_TRADITIONAL && ad->controller != PHIX_CONTROL_COST))
+      fail(ctx, PHIX_EINVAL, "bad phix_adapt (t_end, dt0, tol > 0; max_steps >= 1; controller)");
+    if (scheme < PHIX_EXPRB43 || scheme > PHIX_EPIRK5P1) fail(ctx, PHIX_EINVAL, "unknown scheme %d", (int)scheme);
+    N = (size_t)op->nx * op->ny * ncomp_of(op->kind);
+    backup = wsd(ctx, S_UB, N);
+    return PHIX_OK;
+  });
+  if (rc != PHIX_OK) return finish(rc);
+  const int order = scheme == PHIX_EPIRK5P1 ? 4 : 3;  // of the embedded estimate
+  const double itol = ad->iter_tol > 0 ? ad->iter_tol : ad->tol;
+  double t = 0.0, dt = ad->dt0;
+  double hist_c[2] = {0, 0}, hist_dt[2] = {0, 0};
+  long long spent = 0;
+  int nhist = 0;
+  while (t < ad->t_end * (1 - 1e-14)) {
+    if (as.accepted + as.rejected >= ad->max_steps) {
+      as.t = t;
+      set_err(ctx, "max_steps reached at t = %g", t);
+      return finish(PHIX_ENOTCONV);
+    }
+    dt = std::min(dt, ad->t_end - t);
+    if (ad->dt_max > 0) dt = std::min(dt, ad->dt_max);
+    if (cudaMemcpyAsync(backup, u, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess) {
+      set_err(ctx, "step backup copy failed");
+      return finish(PHIX_ECUDA);
+    }
+    double en = 0.0;
+    phix_stats st{};
+    rc = exp_step(ctx, (int)scheme, op, u, nullptr, dt, itol, method, opts, &en, &st);
+    spent += st.jv + st.power_mv;
+    as.matvecs += st.jv + st.power_mv;
+    if (rc != PHIX_OK && rc != PHIX_ENOTCONV) return finish(rc);
+    const double err = en / std::sqrt((double)N);
+    const double dt_trad = err == 0.0 ? HUGE_VAL : dt * std::pow(ad->tol / err, 1.0 / (order + 1));
+    if (rc != PHIX_OK || err > ad->tol) {
+      // rejected: the step changed u only if its phi-actions succeeded
+      if (rc == PHIX_OK &&
+          cudaMemcpyAsync(u, backup, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess) {
+        set_err(ctx, "step restore copy failed");
+        return finish(PHIX_ECUDA);
+      }
+      as.rejected += 1;
+      dt = rc == PHIX_OK ? dt_trad : 0.5 * dt;
+      continue;
+    }
+    t += dt;
+    if (dts) dts[as.accepted] = dt;
+    as.accepted += 1;
+    hist_c[0] = hist_c[1];
+    hist_dt[0] = hist_dt[1];
+    hist_c[1] = (double)spent / dt;
+    hist_dt[1] = dt;
+    ++nhist;
+    spent = 0;
+    double nxt = dt_trad;
+    if (ad->controller == PHIX_CONTROL_COST && nhist >= 2)
+      nxt = std::min(nxt, dt * cost_factor(hist_c[1], hist_c[0], hist_dt[1], hist_dt[0]));
+    else if (std::isinf(nxt))
+      nxt = dt;
+    dt = nxt;
+  }
+  as.t = t;
+  as.dt_next = dt;
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return finish(PHIX_ECUDA);
+  return finish(PHIX_OK);
+}
+
+// ---- domain-decomposed Newton-Leja pass: the per-block kernels -------------
+static phix_status block_check(phix_ctx* ctx, const phix_block* b) {
+  if (!b) fail(ctx, PHIX_EINVAL, "block is NULL");
+  if (b->kind < 0 || b->kind > 2) fail(ctx, PHIX_EINVAL, "unknown operator kind %d", b->kind);
+  if (b->gnx < 3 || b->gny < 3 || b->bx < 1 || b->by < 1 || b->x0 < 0 || b->y0 < 0 ||
+      b->x0 + b->bx > b->gnx || b->y0 + b->by > b->gny)
+    fail(ctx, PHIX_EINVAL, "block %dx%d at (%d, %d) does not fit the %dx%d grid", b->bx, b->by, b->x0, b->y0, b->gnx,
+         b->gny);
+  return PHIX_OK;
+}
+
+phix_status phix_block_newton(phix_ctx* ctx, const phix_block* blk, const double* y_in, double* y_out, int K,
+                              double* const* p, const double* dk, double a, double b, double* norms) {
+  return guarded(ctx, nullptr, [&](phix_stats&) -> phix_status {
+    block_check(ctx, blk);
+    if (!y_in || !norms || K < 0 || K > KMAX || (K > 0 && (!p || !dk)))
+      fail(ctx, PHIX_EINVAL, "bad arguments (y_in, norms, K in 0..%d, p and dk for K > 0)", KMAX);
+    for (int k = 0; k < K; ++k)
+      if (!p[k]) fail(ctx, PHIX_EINVAL, "p[%d] is NULL", k);
+    if (blk->kind != PHIX_OP_ADVDIFF && !blk->state) fail(ctx, PHIX_EINVAL, "operator kind %d needs a state", blk->kind);
+    double k8[8];
+    uniform_coeffs(blk->kind, blk->gnx, blk->gny, blk->param, k8);
+    KL(launch_block_newton(blk->kind, blk->bx, blk->by, ncomp_of(blk->kind), K, y_in, y_out, p, blk->state, k8, dk, a,
+                           b, ctx->partials, ctx->counter, norms, ctx->grid_stream, ctx->stream));
+    return PHIX_OK;
+  });
+}
+
+phix_status phix_block_faces(phix_ctx* ctx, const phix_block* blk, int dir, double* y_pad, double* faces) {
+  return guarded(ctx, nullptr, [&](phix_stats&) -> phix_status {
+    block_check(ctx, blk);
+    if (!y_pad || !faces || (dir != 0 && dir != 1)) fail(ctx, PHIX_EINVAL, "bad arguments");
+    KL(launch_block_faces(blk->bx, blk->by, ncomp_of(blk->kind), dir, y_pad, faces, ctx->stream));
+    return PHIX_OK;
+  });
+}
+
+phix_status phix_block_start(phix_ctx* ctx, const phix_block* blk, uint64_t seed, double* y_pad) {
+  return guarded(ctx, nullptr, [&](phix_stats&) -> phix_status {
+    block_check(ctx, blk);
+    if (!y_pad) fail(ctx, PHIX_EINVAL, "y_pad is NULL");
+    KL(launch_block_splitmix(blk->bx, blk->by, ncomp_of(blk->kind), blk->gnx, blk->gny, blk->x0, blk->y0, seed, y_pad,
+                             ctx->grid_stream, ctx->stream));
+    return PHIX_OK;
+  });
+}
+
+int phix_leja_stop(int K, int m, int m_min, const double* dkm, double tol, double ysq, const double* psq) {
+  if (!std::isfinite(ysq)) return -1;
+  bool ok = m >= m_min;
+  for (int k = 0; k < K; ++k) {
+    if (!std::isfinite(psq[k])) return -1;
+    ok = ok && std::fabs(dkm[k]) * std::sqrt(ysq) <= tol * std::sqrt(psq[k]);
+  }
+  return ok ? 1 : 0;
 }
 
 }  // extern "C"

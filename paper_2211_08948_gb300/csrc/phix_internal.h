@@ -39,6 +39,7 @@ struct LejaCtl {
   double rho_prev;
   double alpha;        // power iteration: 1/||y_k|| for the next launch
   float alpha_hi, alpha_lo;
+  unsigned int bar_count, bar_gen;  // grid barrier of a persistent chain (zero at its start)
 };
 
 // Parameters of one chain of iteration launches, in device memory, written by
@@ -99,6 +100,11 @@ int tma_grid(const ChainSpec& s, int nsm);
 cudaError_t tma_node_params(const ChainSpec& s, cudaKernelNodeParams* np, void* arg_storage, size_t arg_bytes);
 size_t tma_arg_bytes();
 int iter_tiles(const ChainSpec& s);  // tiles of one launch (work units of the grid loop)
+// Persistent chain (MODE_NEWTON, single-step kernel): every iteration of the
+// pass in one cooperative launch of chain_grid() blocks (all resident), one
+// grid barrier per iteration; s.partials must hold 2 * grid * (KMAX + 1).
+int chain_grid(const ChainSpec& s, int nsm);  // 0 if the kernel cannot be resident
+cudaError_t launch_chain(const ChainSpec& s, cudaStream_t st);
 
 // y0 = v / sigma (stored in the precision's format), p_k = d_k[0] y0, norms, ctl->m = 1.
 struct InitLaunch {
@@ -255,6 +261,20 @@ cudaError_t launch_lincomb(size_t n, int nterms, const double* c, const double* 
 // result[0] = ||x - y||_2^2 (y may be NULL) -> device double via last-block reduction
 cudaError_t launch_norm2(size_t n, const double* x, const double* y, double* partials,
                          unsigned int* counter, double* result, int grid, cudaStream_t s);
+
+// ---- domain-decomposed Newton-Leja pass (block_kernels.cu) ----------------
+// padded block (bx + 2) x (by + 2) per species; yout == NULL: p_k = dk[k] yin
+// (interior) and norms of yin; else yout = a J yin + b yin, p_k += dk[k] yout.
+// norms[0..K] = ||y||^2, ||p_k||^2 over the block interior (device).
+cudaError_t launch_block_newton(int kind, int bx, int by, int ncomp, int K, const double* yin, double* yout,
+                                double* const* p, const double* st, const double* k8, const double* dk,
+                                double a, double b, double* partials, unsigned int* counter, double* norms,
+                                int grid, cudaStream_t s);
+// dir 0: interior faces -> buf; dir 1: buf -> halo faces ([S | N | W | E], species contiguous per face)
+cudaError_t launch_block_faces(int bx, int by, int ncomp, int dir, double* ypad, double* buf, cudaStream_t s);
+// interior of a padded block <- SplitMix64 stream by global index
+cudaError_t launch_block_splitmix(int bx, int by, int ncomp, int gnx, int gny, int x0, int y0, uint64_t seed,
+                                  double* ypad, int grid, cudaStream_t s);
 
 // ---- host math (host_math.cpp) --------------------------------------------
 double phi_host(int l, double z);

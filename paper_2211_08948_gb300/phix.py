@@ -23,6 +23,8 @@ PHIX_MLP_NFEAT = 16
 PHIX_LEJA, PHIX_KIOPS, PHIX_LEKRY = 0, 1, 2
 PHIX_EXPRB43, PHIX_EPIRK4S3, PHIX_EPIRK4S3A, PHIX_EXPRB53S3, PHIX_EPIRK5P1 = range(5)
 PHIX_KERNEL_AUTO, PHIX_KERNEL_SINGLE, PHIX_KERNEL_TMA = 0, 1, 2
+PHIX_CHAIN_AUTO, PHIX_CHAIN_PERSISTENT, PHIX_CHAIN_GRAPH = 0, 1, 2
+PHIX_CONTROL_TRADITIONAL, PHIX_CONTROL_COST = 0, 1
 PHIX_FP64, PHIX_DF64, PHIX_FP32_JV, PHIX_FP32 = 0, 1, 2, 3
 PHIX_OP_ADVDIFF, PHIX_OP_GRAYSCOTT, PHIX_OP_BURGERS = 0, 1, 2
 
@@ -32,7 +34,8 @@ EXPORTS = [
     "phix_phi_action", "phix_phi_combination", "phix_spectrum", "phix_exprb43_step",
     "phix_epirk4s3_step", "phix_rhs", "phix_small_expm", "phix_phi_action_batched", "phix_features",
     "phix_mlp_forward", "phix_mlp_grad", "phix_mlp_train", "phix_phi_action_learned", "phix_leja_points", "phix_divided_differences", "phix_phi_action_noalloc",
-    "phix_step", "phix_step_host",
+    "phix_step", "phix_step_host", "phix_block_newton", "phix_block_faces", "phix_block_start",
+    "phix_leja_stop", "phix_opts_size", "phix_stats_size", "phix_integrate",
 ]
 
 
@@ -49,7 +52,8 @@ class phix_opts(ctypes.Structure):
                 ("power_rel", ctypes.c_double), ("power_seed", ctypes.c_uint64),
                 ("kiops_m_init", ctypes.c_int), ("kiops_m_max", ctypes.c_int),
                 ("kiops_m_step", ctypes.c_int), ("kiops_max_substeps", ctypes.c_int),
-                ("profile", ctypes.c_int), ("kernel", ctypes.c_int), ("kiops_fused", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("kernel", ctypes.c_int), ("kiops_fused", ctypes.c_int),
+                ("chain", ctypes.c_int)]
 
 
 class phix_batch_problem(ctypes.Structure):
@@ -57,6 +61,23 @@ class phix_batch_problem(ctypes.Structure):
                 ("ay", ctypes.c_double), ("h", ctypes.c_double), ("rho_re", ctypes.c_double),
                 ("rho_hi", ctypes.c_double), ("rho_im", ctypes.c_double), ("v", ctypes.c_void_p),
                 ("out", ctypes.c_void_p * 3)]
+
+
+class phix_block(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("gnx", ctypes.c_int), ("gny", ctypes.c_int), ("x0", ctypes.c_int),
+                ("y0", ctypes.c_int), ("bx", ctypes.c_int), ("by", ctypes.c_int),
+                ("param", ctypes.c_double * 8), ("state", ctypes.c_void_p)]
+
+
+class phix_adapt(ctypes.Structure):
+    _fields_ = [("t_end", ctypes.c_double), ("dt0", ctypes.c_double), ("tol", ctypes.c_double),
+                ("iter_tol", ctypes.c_double), ("dt_max", ctypes.c_double), ("controller", ctypes.c_int),
+                ("max_steps", ctypes.c_int)]
+
+
+class phix_adapt_stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("accepted", ctypes.c_int), ("rejected", ctypes.c_int),
+                ("t", ctypes.c_double), ("dt_next", ctypes.c_double), ("matvecs", ctypes.c_longlong)]
 
 
 class phix_stats(ctypes.Structure):
@@ -94,6 +115,8 @@ def load(path=None):
     lib.phix_opts_default.argtypes = [ctypes.POINTER(phix_opts)]
     lib.phix_opts_default.restype = None
     lib.phix_version.restype = I
+    lib.phix_opts_size.restype = ctypes.c_size_t
+    lib.phix_stats_size.restype = ctypes.c_size_t
     lib.phix_create.argtypes = [ctypes.POINTER(P), P]
     lib.phix_destroy.argtypes = [P]
     lib.phix_last_error.argtypes = [P]
@@ -117,6 +140,14 @@ def load(path=None):
     lib.phix_small_expm.argtypes = [P, I, P, P, P, D, P, ctypes.POINTER(I)]
     lib.phix_spectrum.argtypes = [P, ctypes.POINTER(phix_jop), ctypes.POINTER(phix_opts),
                                   ctypes.POINTER(D), ctypes.POINTER(phix_stats)]
+    lib.phix_block_newton.argtypes = [P, ctypes.POINTER(phix_block), P, P, I, ctypes.POINTER(P),
+                                      ctypes.POINTER(D), D, D, P]
+    lib.phix_block_faces.argtypes = [P, ctypes.POINTER(phix_block), I, P, P]
+    lib.phix_block_start.argtypes = [P, ctypes.POINTER(phix_block), ctypes.c_uint64, P]
+    lib.phix_leja_stop.argtypes = [I, I, I, ctypes.POINTER(D), D, D, ctypes.POINTER(D)]
+    lib.phix_leja_stop.restype = I
+    lib.phix_integrate.argtypes = [P, I, ctypes.POINTER(phix_jop), P, ctypes.POINTER(phix_adapt), I,
+                                   ctypes.POINTER(phix_opts), ctypes.POINTER(D), ctypes.POINTER(phix_adapt_stats)]
     for f in (lib.phix_step, lib.phix_step_host):
         f.argtypes = [P, I, ctypes.POINTER(phix_jop), P, D, D, I, ctypes.POINTER(phix_opts),
                       ctypes.POINTER(D), ctypes.POINTER(phix_stats)]
@@ -375,6 +406,55 @@ def phix_step_host(ctx, scheme, op, u_host, h, tol, method=PHIX_LEJA, opts=None,
     fn = load().phix_step_host
     return _step(lambda c, o, x, *a: fn(c, scheme, o, x, *a), ctx, op, u_host, h, tol, method, opts, check,
                  ptr=_hptr)
+
+
+def phix_integrate(ctx, scheme, op, u, t_end, dt0, tol, method=PHIX_LEJA, controller=PHIX_CONTROL_COST,
+                   iter_tol=0.0, dt_max=0.0, max_steps=10000, opts=None, check=True):
+    """Advance the device state u from 0 to t_end with step-size control (Sec. 2.3).
+    Returns (phix_adapt_stats, list of accepted step sizes)."""
+    ad = phix_adapt(t_end=t_end, dt0=dt0, tol=tol, iter_tol=iter_tol, dt_max=dt_max, controller=controller,
+                    max_steps=max_steps)
+    dts = (ctypes.c_double * max_steps)()
+    st = phix_adapt_stats()
+    rc = load().phix_integrate(ctx, scheme, ctypes.byref(op), _ptr(u), ctypes.byref(ad), method,
+                               ctypes.byref(opts) if opts is not None else None, dts, ctypes.byref(st))
+    if check:
+        _check(ctx, rc)
+    return st, list(dts[:st.accepted])
+
+
+def make_block(kind, gnx, gny, x0, y0, bx, by, params, state=None):
+    """phix_block for one block of the gnx x gny grid; `state` (padded device
+    tensor) is kept alive by the returned object."""
+    b = phix_block()
+    b.kind, b.gnx, b.gny, b.x0, b.y0, b.bx, b.by = kind, gnx, gny, x0, y0, bx, by
+    for i, p in enumerate(params):
+        b.param[i] = p
+    b.state = _ptr(state)
+    b._keepalive = state
+    return b
+
+
+def phix_block_newton(ctx, blk, y_in, y_out, p, dk, a, b, norms):
+    """One block iteration (y_out None: initialise p_k = dk[k] y_in)."""
+    K = len(p)
+    P = (ctypes.c_void_p * max(1, K))(*[_ptr(t) for t in p])
+    Dk = (ctypes.c_double * max(1, K))(*dk)
+    _check(ctx, load().phix_block_newton(ctx, ctypes.byref(blk), _ptr(y_in), _ptr(y_out), K, P, Dk, a, b,
+                                         _ptr(norms)))
+
+
+def phix_block_faces(ctx, blk, direction, y_pad, faces):
+    _check(ctx, load().phix_block_faces(ctx, ctypes.byref(blk), direction, _ptr(y_pad), _ptr(faces)))
+
+
+def phix_block_start(ctx, blk, seed, y_pad):
+    _check(ctx, load().phix_block_start(ctx, ctypes.byref(blk), seed, _ptr(y_pad)))
+
+
+def phix_leja_stop(K, m, m_min, dkm, tol, ysq, psq):
+    D = ctypes.c_double * max(1, K)
+    return load().phix_leja_stop(K, m, m_min, D(*dkm), tol, ysq, D(*psq))
 
 
 def phix_leja_points(m):

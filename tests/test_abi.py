@@ -39,7 +39,9 @@ def test_library_exports_every_declared_symbol():
 
 def test_version_and_opts_defaults():
     phix, lib = _lib()
-    assert phix.phix_version() == 101
+    assert phix.phix_version() == 102
+    assert lib.phix_opts_size() == ctypes.sizeof(phix.phix_opts)
+    assert lib.phix_stats_size() == ctypes.sizeof(phix.phix_stats)
     o = phix.phix_opts_default()
     assert o.prec == phix.PHIX_DF64 and o.m_max == 500 and o.m_min == 3
     assert o.safety == 1.2 and o.rho_re < 0 and o.gamma_cap == 200.0
@@ -47,7 +49,7 @@ def test_version_and_opts_defaults():
     assert o.profile == 0 and o.kernel == phix.PHIX_KERNEL_AUTO
     # the last field: its default read back through the ctypes mirror checks the
     # mirror's layout against the C struct that phix_opts_default fills
-    assert o.kiops_fused == 1
+    assert o.kiops_fused == 1 and o.chain == phix.PHIX_CHAIN_AUTO
     assert ctypes.sizeof(phix.phix_jop) == 4 * 3 + 4 + 8 * 8 + 8
 
 

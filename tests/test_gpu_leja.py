@@ -280,3 +280,44 @@ def test_chain_past_its_truncated_table_reruns_with_full_table(px, prec):
     assert st.iters == info["iters"] == m_min
     for r, o in zip(res, ref):
         assert rel(r, o) <= 1e-10
+
+
+@pytest.mark.parametrize("kind", ["advdiff", "grayscott", "burgers"])
+@pytest.mark.parametrize("prec", ["FP64", "DF64", "FP32_JV", "FP32"])
+def test_persistent_chain_equals_graph_chain(px, kind, prec):
+    """The whole Newton pass in one cooperative launch (grid barrier per
+    iteration, every block taking the stop decision) against one launch per
+    iteration in a conditional graph: the pointwise Newton updates are the
+    same code, so with the same iteration count the outputs are identical."""
+    phix, ctx = px
+    n = 96
+    if kind == "advdiff":
+        p = synth.advdiff_params(n)
+        op = phix.make_jop(phix.PHIX_OP_ADVDIFF, n, n, [p["D"], p["ax"], p["ay"]])
+        v = dev(synth.advdiff_gaussian(n))
+        h, kw = p["h"], dict(rho_re=8.0 * p["D"] * n * n)
+    elif kind == "grayscott":
+        prm = synth.grayscott_params(n, Du=2e-3, Dv=1e-3, mult=30.0)
+        st = dev(synth.grayscott_state(n, seed=6, patch=24))
+        op = phix.make_jop(phix.PHIX_OP_GRAYSCOTT, n, n, [prm["Du"], prm["Dv"], prm["F"], prm["k"]], st)
+        v = dev(np.random.default_rng(3).standard_normal(2 * n * n))
+        h, kw = prm["h"], {}
+    else:
+        prm = synth.burgers_params(n, mult=10.0)
+        u = synth.burgers_state(n, seed=6)
+        op = phix.make_jop(phix.PHIX_OP_BURGERS, n, n, [prm["nu"]], dev(u))
+        v = dev(np.random.default_rng(3).standard_normal(n * n))
+        h, kw = prm["h"], dict(rho_im=2.0 * n * float(np.abs(u).max()))
+    ls, ss = [0, 1, 1], [1.0, 0.5, 1.0]
+    res = {}
+    for chain in (phix.PHIX_CHAIN_PERSISTENT, phix.PHIX_CHAIN_GRAPH):
+        out = [torch.empty_like(v) for _ in ls]
+        o = phix.phix_opts_default(prec=_prec(phix, prec), chain=chain, **kw)
+        st = phix.phix_phi_action(ctx, op, h, v, ls, ss, out, 1e-10, phix.PHIX_LEJA, o)
+        res[chain] = (out, st)
+    (a, sa), (b, sb) = res[phix.PHIX_CHAIN_PERSISTENT], res[phix.PHIX_CHAIN_GRAPH]
+    assert sa.iters == sb.iters and sa.substeps == sb.substeps
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+    # a persistent pass is one launch; the graph's passes launch once per iteration
+    assert sa.launches < sb.launches
