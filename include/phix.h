@@ -283,7 +283,7 @@ phix_status phix_step_host(phix_ctx* ctx, phix_scheme scheme, const phix_jop* op
  *                0.26862269, lambda 1.37412002, delta 0.64446017) applied to the
  *                cost per unit time c_n = (Jacobian products of step n) / dt_n;
  * e_n = ||u_high - u_low||_2 / sqrt(N); a step with e_n > tol (or whose
- * phi-actions fail to converge) is rejected and retried (with the
+ * phi-actions fail to converge) is rejected and retried (with 0.9 times the
  * traditional step, or half the step after a failure); p is the order of
  * the scheme's embedded estimate (3; EPIRK5P1: 4); the last step lands on
  * t_end.  The cost controller starts from the third step (it needs two

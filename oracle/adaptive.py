@@ -15,7 +15,11 @@ What the paper fixes (Sec. 2.3):
 Readings where the paper is silent (the CUDA library follows the same):
 * e_n = ||u_high - u_low||_2 / sqrt(N), the root-mean-square difference of
   the two embedded solutions, compared with tol; a step with e_n > tol is
-  rejected and retried with the traditional step computed from it.
+  rejected and retried with 0.9 times the traditional step computed from it
+  (the paper gives no rule for rejected steps; without the factor the retry
+  aims exactly at tol and is rejected again whenever rounding puts e_n a
+  hair above it, repeatedly).  A step whose phi-actions fail to converge is
+  retried with half the step.
 * p + 1 is the power of dt in e_n: p is the order of the lower-order
   (embedded) solution, the error estimator's order (3 for EXPRB43, EPIRK4s3,
   EPIRK4s3A and EXPRB53s3, 4 for EPIRK5P1).
@@ -38,6 +42,7 @@ import numpy as np
 from . import integrators
 
 ALPHA, BETA, LAM, DELTA = 0.65241444, 0.26862269, 1.37412002, 0.64446017
+RETRY = 0.9  # factor on the traditional step after a rejection
 
 
 def traditional(dt, err, tol, order):
@@ -87,7 +92,7 @@ def integrate(op, u0, t_end, dt0, tol, scheme="exprb43", method="leja", controll
         dt_trad = traditional(dt, err, tol, order)
         if err > tol or st["status"] != 0:
             info["rejected"] += 1
-            dt = dt_trad if st["status"] == 0 else 0.5 * dt
+            dt = RETRY * dt_trad if st["status"] == 0 else 0.5 * dt
             continue
         u = uh
         t += dt

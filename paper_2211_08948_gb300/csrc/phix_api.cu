@@ -1800,7 +1800,7 @@ phix_status phix_integrate(phix_ctx* ctx, phix_scheme scheme, const phix_jop* op
         return finish(PHIX_ECUDA);
       }
       as.rejected += 1;
-      dt = rc == PHIX_OK ? dt_trad : 0.5 * dt;
+      dt = rc == PHIX_OK ? 0.9 * dt_trad : 0.5 * dt;  // the retry aims below tol
       continue;
     }
     t += dt;

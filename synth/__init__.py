@@ -53,6 +53,15 @@ def grayscott_state(n=1024, seed=0, patch=64, amp=0.1):
     return np.concatenate([u.reshape(-1), v.reshape(-1)])
 
 
+def grayscott_gaussian(n=64):
+    """The paper's smooth Gray-Scott initial state (Sec. 3): u = 1 - exp(-150 r_u),
+    v = exp(-150 r_v), r_u = (x-1/2)^2 + (y-1/2)^2, r_v = (x-1/2)^2 + 2 (y-1/2)^2."""
+    X, Y = grid_xy(n)
+    u = 1.0 - np.exp(-150.0 * ((X - 0.5) ** 2 + (Y - 0.5) ** 2))
+    v = np.exp(-150.0 * ((X - 0.5) ** 2 + 2.0 * (Y - 0.5) ** 2))
+    return np.concatenate([u.reshape(-1), v.reshape(-1)])
+
+
 def grayscott_params(n=1024, Du=2e-5, Dv=1e-5, F=0.04, k=0.06, mult=100.0):
     dx = 1.0 / n
     h = mult * dx * dx / (4.0 * max(Du, Dv))

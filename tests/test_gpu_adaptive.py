@@ -35,7 +35,7 @@ def test_integrate_vs_oracle(px, scheme, method, controller):
     phix, ctx = px
     n = 32
     prm = synth.grayscott_params(n, Du=2e-3, Dv=1e-3, mult=5.0)
-    u0 = synth.grayscott_state(n, seed=7, patch=12, amp=0.3)
+    u0 = synth.grayscott_gaussian(n)
     T = 40.0 * prm["h"]
     tol = 1e-6
     op = phix.make_jop(phix.PHIX_OP_GRAYSCOTT, n, n, [prm["Du"], prm["Dv"], prm["F"], prm["k"]])
