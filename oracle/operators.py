@@ -104,6 +104,9 @@ class Burgers:
 
 def with_state(op, state):
     """Copy of a nonlinear operator linearised at `state` (J(u^n), Sec. 1)."""
+    from . import problems
+    if isinstance(op, (problems.ADR, problems.AllenCahn, problems.Brusselator)):
+        return problems.with_state(op, state)
     if isinstance(op, GrayScott):
         return GrayScott(op.n, op.Du, op.Dv, op.F, op.k, state, ny=op.ny)
     if isinstance(op, Burgers):

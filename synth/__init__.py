@@ -62,6 +62,30 @@ def grayscott_gaussian(n=64):
     return np.concatenate([u.reshape(-1), v.reshape(-1)])
 
 
+def cell_xy(n, x0=0.0, L=1.0):
+    """Cell-centre coordinates (X, Y), shape (n, n), of [x0, x0 + L]^2 (X along axis 1)."""
+    x = x0 + (np.arange(n, dtype=np.float64) + 0.5) * (L / n)
+    return np.meshgrid(x, x, indexing="xy")
+
+
+def adr_state(n=64):
+    """The paper's ADR initial state (Sec. 3): 256 (x y (1 - x)(1 - y))^2 + 0.3 on [0, 1]^2."""
+    X, Y = cell_xy(n)
+    return (256.0 * (X * Y * (1 - X) * (1 - Y)) ** 2 + 0.3).reshape(-1)
+
+
+def allen_cahn_state(n=64):
+    """The paper's Allen-Cahn initial state (Sec. 3): 0.1 + 0.1 cos(2 pi x) cos(2 pi y) on [-1, 1]^2."""
+    X, Y = cell_xy(n, -1.0, 2.0)
+    return (0.1 + 0.1 * np.cos(2 * np.pi * X) * np.cos(2 * np.pi * Y)).reshape(-1)
+
+
+def brusselator_state(n=64):
+    """The paper's Brusselator initial state (Sec. 3): u = 2 + 0.25 y, v = 1 + 0.8 x on [0, 1]^2."""
+    X, Y = cell_xy(n)
+    return np.concatenate([(2.0 + 0.25 * Y).reshape(-1), (1.0 + 0.8 * X).reshape(-1)])
+
+
 def grayscott_params(n=1024, Du=2e-5, Dv=1e-5, F=0.04, k=0.06, mult=100.0):
     dx = 1.0 / n
     h = mult * dx * dx / (4.0 * max(Du, Dv))
