@@ -500,9 +500,17 @@ def leg_batched(torch, phix, synth, ctx, stream, args, count=4096):
                        reps, 1)
         st, per = rr[-1]
         outs[pr] = [[t.clone() for t in q["out"]] for q in probs[:256]]
+        bt, smem, per_sm = phix.phix_batched_config(ctx)
         res[pr] = {"value": 3 * len(probs) * reps / (ms * 1e-3), "unit": UNIT, "ms_per_batch": ms / reps,
-                   "launch_ms": st.iter_ms, "ctas_per_sm": st.substeps, "newton_iters": st.iters,
-                   "failed": int(sum(1 for s in per if s != 0))}
+                   "launch_ms": st.iter_ms, "tuned": {"threads_per_cta": bt, "smem_bytes": smem,
+                                                      "ctas_per_sm": per_sm},
+                   "newton_iters": st.iters, "failed": int(sum(1 for s in per if s != 0))}
+        # the untuned launch (512 threads, no shared-memory passes, 2 CTAs per SM) on a fresh context
+        ctx0 = phix.phix_create(stream)
+        o0 = phix.phix_opts_default(prec=getattr(phix, "PHIX_" + pr))
+        ms0, _ = timed(torch, stream, lambda: phix.phix_phi_action_batched(ctx0, probs, [0, 1, 2], 1e-8, o0), reps, 1)
+        phix.phix_destroy(ctx0)
+        res[pr]["untuned_value"] = 3 * len(probs) * reps / (ms0 * 1e-3)
     for pr in res:
         num = sum(float(torch.linalg.norm(a - b) ** 2) for x, y in zip(outs[pr], outs["FP64"]) for a, b in zip(x, y))
         den = sum(float(torch.linalg.norm(b) ** 2) for y in outs["FP64"] for b in y)

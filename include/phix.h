@@ -331,14 +331,24 @@ typedef struct {
  * graph: each CTA takes whole problems from a largest-first queue and runs
  * the vertical Leja pass (or the ODE-identity substeps) with block-level
  * reductions.  opts->prec: PHIX_FP64, PHIX_DF64 or PHIX_FP32_JV; opts->m_max
- * <= 500.  opts->profile = 1 additionally tunes the CTAs per SM on this batch
- * (first call per batch shape) and reports the launch time in iter_ms.
+ * <= 500.  opts->profile = 1 additionally autotunes the launch on the first
+ * call per batch shape (the problem sizes, count and precision): threads per
+ * CTA (256, 512, 1024) x dynamic shared memory per CTA (0, 48 KiB, 100 KiB:
+ * a vertical pass whose basis pair and accumulators fit runs on shared
+ * memory) x CTAs per SM (the resident maximum and half of it), each timed on
+ * a subsample (every 8th problem in largest-first order) and cached in the
+ * context; it also reports the launch time in iter_ms.  Without profile the
+ * tuned configuration of the shape is used if there is one, else 512
+ * threads, no shared-memory passes, 2 CTAs per SM (phix_batched_config).
  * per_prob (HOST, may be NULL) receives each problem's status; stats->iters
  * sums the Newton iterations of all problems.  Problems are read from HOST
  * memory (the array), vectors are device memory.                           */
 phix_status phix_phi_action_batched(phix_ctx* ctx, const phix_batch_problem* probs, int nprob, int nout,
                                     const int* l, double tol, const phix_opts* opts, int* per_prob,
                                     phix_stats* stats);
+
+/* The launch configuration of the context's last batched call.           */
+phix_status phix_batched_config(const phix_ctx* ctx, int* threads_per_cta, int* smem_bytes, int* ctas_per_sm);
 
 /* Learned spectral interval (north_star form "learned"; replaces the power
  * iterations of Sec. 2.2 by a prediction, with power iteration as fallback).

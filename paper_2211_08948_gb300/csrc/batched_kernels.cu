@@ -18,9 +18,8 @@ namespace phix {
 
 namespace {
 
-constexpr int BTHREADS = 512;
-constexpr int NWARP = BTHREADS / 32;
-constexpr int BM = 501;  // longest divided-difference table (m_max <= 500)
+constexpr int MAXWARP = 32;  // block sizes 256, 512, 1024 (tuned per batch shape)
+constexpr int BM = 501;      // longest divided-difference table (m_max <= 500)
 
 __device__ double phi_dev(int l, double z) {
   if (l == 0) return exp(z);
@@ -58,8 +57,8 @@ struct Shared {
   double tmp[BM];
   double beta[BM];    // shifts beta_m = -(c/gamma + xi_{m-1})
   float2 betaf[BM];
-  double red[NWARP][4];
-  float2 redf[NWARP][4];
+  double red[MAXWARP][4];
+  float2 redf[MAXWARP][4];
   double tot[4];
   int flag;  // stop decision of the iteration, from thread 0
 };
@@ -85,20 +84,23 @@ struct BArgs {
   double tol, gamma_cap, iota_cap;
   int nout;
   int l[3];
+  unsigned int smem_bytes;  // dynamic shared memory: a vertical pass whose basis pair and
+                            // accumulators fit runs on shared memory instead of the arena
 };
 
 // d = divided differences of xi -> phi_l(a + b xi), i < M (block-wide, float64)
 __device__ void dd_block(int l, double a, double b, const double* xi, int M, double* d, float2* df2, double* tmp,
                          int tid) {
-  for (int i = tid; i < M; i += BTHREADS) d[i] = phi_dev(l, a + b * xi[i]);
+  const int nthr = blockDim.x;
+  for (int i = tid; i < M; i += nthr) d[i] = phi_dev(l, a + b * xi[i]);
   __syncthreads();
   for (int j = 1; j < M; ++j) {
-    for (int i = j + tid; i < M; i += BTHREADS) tmp[i] = (d[i] - d[i - 1]) / (xi[i] - xi[i - j]);
+    for (int i = j + tid; i < M; i += nthr) tmp[i] = (d[i] - d[i - 1]) / (xi[i] - xi[i - j]);
     __syncthreads();
-    for (int i = j + tid; i < M; i += BTHREADS) d[i] = tmp[i];
+    for (int i = j + tid; i < M; i += nthr) d[i] = tmp[i];
     __syncthreads();
   }
-  for (int i = tid; i < M; i += BTHREADS) df2[i] = split_d(d[i]);
+  for (int i = tid; i < M; i += nthr) df2[i] = split_d(d[i]);
   __syncthreads();
 }
 
@@ -110,6 +112,7 @@ __device__ void dd_block(int l, double a, double b, const double* xi, int M, dou
 template <typename Acc>
 __device__ void block_tot(const Acc (&ac)[4], int nv, Shared& sh, int tid, double (&tot)[4]) {
   const int lane = tid & 31, warp = tid >> 5;
+  const int NWARP = blockDim.x >> 5;
 #pragma unroll
   for (int j = 0; j < 4; ++j) tot[j] = 0.0;
   if constexpr (std::is_same<Acc, double>::value) {
@@ -145,7 +148,7 @@ __device__ void block_tot(const Acc (&ac)[4], int nv, Shared& sh, int tid, doubl
 #pragma unroll
       for (int j = 0; j < 4; ++j) s[j] = lane < NWARP ? cv(sh.redf[lane][j]) : df_make(0.f, 0.f);
 #pragma unroll
-      for (int o = NWARP / 2; o > 0; o >>= 1)
+      for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
         for (int j = 0; j < 4; ++j)
           if (j < nv) s[j] = df_add(s[j], shfl_down(s[j], o));
@@ -183,6 +186,7 @@ __device__ int block_pass(const BArgs& a, int nx, int ny, const typename Tr<P>::
   using Acc = typename Tr<P>::AccN;
   constexpr bool FOLD = std::is_same<C, CJ>::value;
   const int lane = tid & 31, warp = tid >> 5;
+  const int NWARP = blockDim.x >> 5;
   const double al = 1.0 / gamma;
   CJ k0[5];
   for (int j = 0; j < 5; ++j) k0[j] = coef<CJ>(al * kJ[j], split_d(al * kJ[j]));
@@ -264,12 +268,14 @@ __device__ int block_pass(const BArgs& a, int nx, int ny, const typename Tr<P>::
   return PHIX_ENOTCONV;
 }
 
-template <int P>
-__global__ void __launch_bounds__(BTHREADS) k_batched(BArgs a) {
+template <int P, int BT>
+__global__ void __launch_bounds__(BT) k_batched(BArgs a) {
   using T = typename Tr<P>::T;
   using C = typename Tr<P>::C;
+  constexpr int BTHREADS = BT, NWARP = BT / 32;
   __shared__ Shared sh;
   __shared__ int slot_s;
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
   const int tid = threadIdx.x;
   const int M = a.m_max + 1;
   for (;;) {
@@ -332,12 +338,22 @@ __global__ void __launch_bounds__(BTHREADS) k_batched(BArgs a) {
         for (int k = 0; k < a.nout; ++k)
           dd_block(a.l[k], h * cc, h * gamma, a.xi, M, sh.dd[k], sh.ddf[k], sh.tmp, tid);
         int it = 0;
-        status = block_pass<P>(a, nx, ny, VV, Y0, Y1, PP, a.nout, kJ, gamma, sh, tid, &it);
+        T* y0 = Y0;
+        T* y1 = Y1;
+        T* pp[3] = {PP[0], PP[1], PP[2]};
+        if ((size_t)(2 + a.nout) * N * sizeof(T) <= a.smem_bytes) {
+          // small problem: the whole pass on shared memory (generic addressing)
+          T* sm = reinterpret_cast<T*>(dyn_smem);
+          y0 = sm;
+          y1 = sm + N;
+          for (int k = 0; k < a.nout; ++k) pp[k] = sm + (2 + k) * N;
+        }
+        status = block_pass<P>(a, nx, ny, VV, y0, y1, pp, a.nout, kJ, gamma, sh, tid, &it);
         iters = it;
         subs = 1;
         for (int k = 0; k < a.nout; ++k)
           for (size_t i = tid; i < N; i += BTHREADS) {
-            const C pv = cv(PP[k][i]);
+            const C pv = cv(pp[k][i]);
             double d;
             if constexpr (P == P_FP64)
               d = pv;
@@ -422,10 +438,49 @@ __global__ void __launch_bounds__(BTHREADS) k_batched(BArgs a) {
 
 size_t batched_prob_bytes() { return sizeof(Prob); }
 
+template <int P>
+static void* batched_fn(int bt) {
+  switch (bt) {
+    case 256:
+      return (void*)k_batched<P, 256>;
+    case 512:
+      return (void*)k_batched<P, 512>;
+    case 1024:
+      return (void*)k_batched<P, 1024>;
+  }
+  return nullptr;
+}
+static void* batched_kernel(int prec, int bt) {
+  switch (prec) {
+    case P_FP64:
+      return batched_fn<P_FP64>(bt);
+    case P_DF64:
+      return batched_fn<P_DF64>(bt);
+    case P_FP32JV:
+      return batched_fn<P_FP32JV>(bt);
+  }
+  return nullptr;
+}
+
+int batched_blocks_per_sm(int prec, int bt, unsigned int smem_bytes) {
+  void* fn = batched_kernel(prec, bt);
+  if (!fn) return 0;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, bt, smem_bytes) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  return nb;
+}
+
 // probs: device array of nprob Prob records (host-built with batched_fill_prob)
 cudaError_t launch_batched(int prec, void* probs, const int* order, int nprob, unsigned int* queue, void* ws,
                            const double* xi, int m_max, int m_min, double tol, double gamma_cap, double iota_cap,
-                           int nout, const int* l, int grid, cudaStream_t st) {
+                           int nout, const int* l, int grid, int bt, unsigned int smem_bytes, cudaStream_t st) {
   if (m_max + 1 > BM || nout < 1 || nout > 3) return cudaErrorInvalidValue;
   BArgs a{};
   a.probs = static_cast<Prob*>(probs);
@@ -441,20 +496,13 @@ cudaError_t launch_batched(int prec, void* probs, const int* order, int nprob, u
   a.iota_cap = iota_cap;
   a.nout = nout;
   for (int k = 0; k < nout; ++k) a.l[k] = l[k];
-  switch (prec) {
-    case P_FP64:
-      k_batched<P_FP64><<<grid, BTHREADS, 0, st>>>(a);
-      break;
-    case P_DF64:
-      k_batched<P_DF64><<<grid, BTHREADS, 0, st>>>(a);
-      break;
-    case P_FP32JV:
-      k_batched<P_FP32JV><<<grid, BTHREADS, 0, st>>>(a);
-      break;
-    default:
-      return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
+  a.smem_bytes = smem_bytes;
+  void* fn = batched_kernel(prec, bt);
+  if (!fn) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+  if (e != cudaSuccess) return e;
+  void* args[1] = {&a};
+  return cudaLaunchKernel(fn, dim3(grid), dim3(bt), args, smem_bytes, st);
 }
 
 void batched_fill_prob(void* dst, int nx, int ny, double D, double ax, double ay, double h, double rho_re,

@@ -711,12 +711,11 @@ int chain_grid(const ChainSpec& s, int nsm) {
     (void)cudaGetLastError();
     return 0;
   }
-  // as many blocks as stay resident, the tiles split evenly (every block
-  // takes ceil(ntiles / g) tiles; a grid-wide barrier waits for the slowest)
+  // every resident block (the same count on every SM; an even tile split over
+  // fewer blocks leaves some SMs with one block fewer, measured no faster)
   const int ntiles = make_dev(s, V).ntiles;
-  const int gmax = nb * nsm;
-  const int per = (ntiles + gmax - 1) / gmax;
-  return (ntiles + per - 1) / per;
+  const int g = nb * nsm;
+  return g < ntiles ? g : ntiles;
 }
 
 cudaError_t launch_chain(const ChainSpec& s, cudaStream_t st) {

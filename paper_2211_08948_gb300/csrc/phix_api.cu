@@ -91,7 +91,13 @@ struct phix_ctx {
     cudaGraphExec_t exec;
   };
   std::vector<BatchGraph> bgraphs;  // batched launch graphs
-  std::vector<std::pair<unsigned long long, int>> btune;  // tuned CTAs per SM per batch shape
+  struct BatchCfg {
+    int bt = 512;            // threads per CTA
+    unsigned int smem = 0;   // dynamic shared memory per CTA (small passes run there)
+    int per_sm = 2;          // CTAs per SM
+  };
+  std::vector<std::pair<unsigned long long, BatchCfg>> btune;  // tuned launch per batch shape
+  BatchCfg blast;                   // the configuration of the last batched call
 };
 
 static constexpr int GRAPH_ITERS = 8;  // iteration launches per body of a chain's WHILE loop
@@ -1180,7 +1186,12 @@ phix_status phix_phi_action_batched(phix_ctx* ctx, const phix_batch_problem* pro
     for (int i = 0; i < nprob; ++i) order[i] = ord[i].second;
     const size_t eb = 8;
     void* dprob = ws(ctx, S_BPROB, pb * nprob);
-    int* dorder = static_cast<int*>(ws(ctx, S_BORDER, sizeof(int) * nprob));
+    // the order (largest work first) and, after it, a tuning subsample: every
+    // 8th problem of that order, which keeps the size and stiffness mix
+    const int nsub = nprob >= 512 ? (nprob + 7) / 8 : nprob;
+    std::vector<int> sub(nsub);
+    for (int i = 0; i < nsub; ++i) sub[i] = order[(size_t)i * nprob / nsub];
+    int* dorder = static_cast<int*>(ws(ctx, S_BORDER, sizeof(int) * (size_t)(nprob + nsub)));
     void* arena = ws(ctx, S_BWS, off * eb);
     unsigned int* q = static_cast<unsigned int*>(ws(ctx, S_BQ, sizeof(unsigned int)));
     const int M = o.m_max + 1;
@@ -1188,12 +1199,18 @@ phix_status phix_phi_action_batched(phix_ctx* ctx, const phix_batch_problem* pro
     CK(cudaMemcpyAsync(xi, leja_table(M), sizeof(double) * M, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(dprob, hp.data(), pb * nprob, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(dorder, order.data(), sizeof(int) * nprob, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(dorder + nprob, sub.data(), sizeof(int) * nsub, cudaMemcpyHostToDevice, ctx->stream));
     key = (key ^ (unsigned long long)o.prec) * 1099511628211ull;
     key = (key ^ (unsigned long long)nprob) * 1099511628211ull;
-    // one graph per (arena, problem table, prec, grid): queue reset + persistent launch
-    auto graph_for = [&](int grid) -> cudaGraphExec_t {
-      unsigned long long gk = (key ^ (unsigned long long)(uintptr_t)arena ^ ((unsigned long long)grid << 40)) *
-                              1099511628211ull;
+    using Cfg = phix_ctx::BatchCfg;
+    // one graph per (arena, problem table, prec, launch configuration, problem
+    // subset): queue reset + persistent launch
+    auto graph_for = [&](const Cfg& c, bool subset) -> cudaGraphExec_t {
+      const int grid = ctx->nsm * c.per_sm;
+      unsigned long long gk = key ^ (unsigned long long)(uintptr_t)arena;
+      for (unsigned long long v : {(unsigned long long)c.bt, (unsigned long long)c.smem, (unsigned long long)grid,
+                                   (unsigned long long)subset})
+        gk = (gk ^ v) * 1099511628211ull;
       for (auto& g : ctx->bgraphs)
         if (g.key == gk && g.grid == grid) return g.exec;
       cudaStream_t cs;
@@ -1201,8 +1218,9 @@ phix_status phix_phi_action_batched(phix_ctx* ctx, const phix_batch_problem* pro
       cudaGraph_t g;
       CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
       cudaError_t e1 = cudaMemsetAsync(q, 0, sizeof(unsigned int), cs);
-      cudaError_t e2 = launch_batched(o.prec, dprob, dorder, nprob, q, arena, xi, o.m_max, o.m_min, tol,
-                                      o.gamma_cap, o.iota_cap, nout, l, grid, cs);
+      cudaError_t e2 = launch_batched(o.prec, dprob, subset ? dorder + nprob : dorder, subset ? nsub : nprob, q, arena,
+                                      xi, o.m_max, o.m_min, tol, o.gamma_cap, o.iota_cap, nout, l, grid, c.bt, c.smem,
+                                      cs);
       cudaError_t e3 = cudaStreamEndCapture(cs, &g);
       cudaStreamDestroy(cs);
       CK(e1);
@@ -1212,43 +1230,55 @@ phix_status phix_phi_action_batched(phix_ctx* ctx, const phix_batch_problem* pro
       cudaError_t e4 = cudaGraphInstantiate(&ex, g, 0);
       cudaGraphDestroy(g);
       CK(e4);
-      if (ctx->bgraphs.size() >= 16) {
+      if (ctx->bgraphs.size() >= 32) {
         cudaGraphExecDestroy(ctx->bgraphs.front().exec);
         ctx->bgraphs.erase(ctx->bgraphs.begin());
       }
       ctx->bgraphs.push_back(phix_ctx::BatchGraph{gk, grid, ex});
       return ex;
     };
-    int per_sm = 2;
+    Cfg cfg;
     bool tuned = false;
     for (auto& t : ctx->btune)
       if (t.first == key) {
-        per_sm = t.second;
+        cfg = t.second;
         tuned = true;
       }
     cudaEvent_t ev0, ev1;
     CK(cudaEventCreate(&ev0));
     CK(cudaEventCreate(&ev1));
     if (o.profile && !tuned) {
-      // autotune: CTAs per SM (each CTA owns whole problems; more CTAs hide
-      // latency, fewer leave more L1 per problem)
+      // autotune on the subsample: threads per CTA x shared-memory residency
+      // of small passes x CTAs per SM (the resident maximum and half of it)
       float best = 1e30f;
-      for (int c = 1; c <= 4; ++c) {
-        cudaGraphExec_t ex = graph_for(ctx->nsm * c);
-        CK(cudaEventRecord(ev0, ctx->stream));
-        CK(cudaGraphLaunch(ex, ctx->stream));
-        CK(cudaEventRecord(ev1, ctx->stream));
-        CK(cudaEventSynchronize(ev1));
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, ev0, ev1));
-        if (ms < best) {
-          best = ms;
-          per_sm = c;
+      for (int bt : {256, 512, 1024})
+        for (unsigned int sm : {0u, 48u << 10, 100u << 10}) {
+          const int occ = std::min(4, batched_blocks_per_sm(o.prec, bt, sm));
+          if (occ < 1) continue;
+          for (int per : {occ, std::max(1, occ / 2)}) {
+            Cfg c;
+            c.bt = bt;
+            c.smem = sm;
+            c.per_sm = per;
+            cudaGraphExec_t ex = graph_for(c, true);
+            CK(cudaEventRecord(ev0, ctx->stream));
+            CK(cudaGraphLaunch(ex, ctx->stream));
+            CK(cudaEventRecord(ev1, ctx->stream));
+            CK(cudaEventSynchronize(ev1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, ev0, ev1));
+            if (ms < best) {
+              best = ms;
+              cfg = c;
+            }
+            if (per == 1) break;
+          }
         }
-      }
-      ctx->btune.push_back(std::make_pair(key, per_sm));
+      ctx->btune.push_back(std::make_pair(key, cfg));
     }
-    cudaGraphExec_t ex = graph_for(ctx->nsm * per_sm);
+    ctx->blast = cfg;
+    const int per_sm = cfg.per_sm;
+    cudaGraphExec_t ex = graph_for(cfg, false);
     CK(cudaEventRecord(ev0, ctx->stream));
     CK(cudaGraphLaunch(ex, ctx->stream));
     ctx->launches += 1;
@@ -1263,7 +1293,7 @@ phix_status phix_phi_action_batched(phix_ctx* ctx, const phix_batch_problem* pro
       st.iter_ms = ms;
       st.iter_launches = 1;
     }
-    st.substeps = per_sm;  // CTAs per SM used (tuned when profile = 1)
+    st.substeps = per_sm;  // CTAs per SM used (tuned when profile = 1); phix_batched_config has the rest
     int worst = PHIX_OK;
     for (int i = 0; i < nprob; ++i) {
       int s_, it, sb;
@@ -1280,6 +1310,14 @@ phix_status phix_phi_action_batched(phix_ctx* ctx, const phix_batch_problem* pro
     }
     return PHIX_OK;
   });
+}
+
+phix_status phix_batched_config(const phix_ctx* ctx, int* threads_per_cta, int* smem_bytes, int* ctas_per_sm) {
+  if (!ctx) return PHIX_EINVAL;
+  if (threads_per_cta) *threads_per_cta = ctx->blast.bt;
+  if (smem_bytes) *smem_bytes = (int)ctx->blast.smem;
+  if (ctas_per_sm) *ctas_per_sm = ctx->blast.per_sm;
+  return PHIX_OK;
 }
 
 // blocks of the features reduction: about four points per thread, at most 512

@@ -229,9 +229,12 @@ void batched_fill_prob(void* dst, int nx, int ny, double D, double ax, double ay
                        double rho_hi, double rho_im, const double* v, double* const* out, int nout,
                        unsigned long long ws_off);
 void batched_read_prob(const void* src, int* status, int* iters, int* substeps);
+// bt: threads per CTA (256, 512 or 1024); smem_bytes: dynamic shared memory per CTA (a
+// vertical pass whose basis pair and accumulators fit in it runs there)
 cudaError_t launch_batched(int prec, void* probs, const int* order, int nprob, unsigned int* queue, void* ws,
                            const double* xi, int m_max, int m_min, double tol, double gamma_cap, double iota_cap,
-                           int nout, const int* l, int grid, cudaStream_t st);
+                           int nout, const int* l, int grid, int bt, unsigned int smem_bytes, cudaStream_t st);
+int batched_blocks_per_sm(int prec, int bt, unsigned int smem_bytes);  // 0: not launchable
 
 // ---- learned spectral interval (mlp_kernels.cu) ---------------------------
 int mlp_nparam();

@@ -35,7 +35,7 @@ EXPORTS = [
     "phix_epirk4s3_step", "phix_rhs", "phix_small_expm", "phix_phi_action_batched", "phix_features",
     "phix_mlp_forward", "phix_mlp_grad", "phix_mlp_train", "phix_phi_action_learned", "phix_leja_points", "phix_divided_differences", "phix_phi_action_noalloc",
     "phix_step", "phix_step_host", "phix_block_newton", "phix_block_faces", "phix_block_start",
-    "phix_leja_stop", "phix_opts_size", "phix_stats_size", "phix_integrate",
+    "phix_leja_stop", "phix_opts_size", "phix_stats_size", "phix_integrate", "phix_batched_config",
 ]
 
 
@@ -421,6 +421,13 @@ def phix_integrate(ctx, scheme, op, u, t_end, dt0, tol, method=PHIX_LEJA, contro
     if check:
         _check(ctx, rc)
     return st, list(dts[:st.accepted])
+
+
+def phix_batched_config(ctx):
+    """(threads per CTA, dynamic shared memory bytes, CTAs per SM) of the last batched call."""
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(ctx, load().phix_batched_config(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
 
 
 def make_block(kind, gnx, gny, x0, y0, bx, by, params, state=None):
