@@ -47,8 +47,8 @@ extern "C" {
 
 /* Rises whenever the layout of a public struct changes: callers must be built
  * against the header of the library they load (101: phix_opts.kiops_fused;
- * 102: phix_opts.chain). */
-#define PHIX_VERSION 102
+ * 102: phix_opts.chain; 103: phix_opts.jv, phix_opts.leja_augmented). */
+#define PHIX_VERSION 103
 
 typedef struct phix_ctx phix_ctx;
 
@@ -95,7 +95,15 @@ typedef enum {
   PHIX_OP_ADVDIFF = 0,   /* f(u) = D lap u + ax u_x + ay u_y (linear), 1 species        */
   PHIX_OP_GRAYSCOTT = 1, /* Sec. 3: f_u = Du lap u - u v^2 + F(1-u),
                                     f_v = Dv lap v + u v^2 - (F+k) v, 2 species     */
-  PHIX_OP_BURGERS = 2    /* f(u) = nu lap u - u (u_x + u_y), 1 species                  */
+  PHIX_OP_BURGERS = 2,   /* f(u) = nu lap u - u (u_x + u_y), 1 species                  */
+  /* The paper's no-flow problems (Sec. 3): cell-centred grids with homogeneous
+   * Neumann boundaries (ghost cell = boundary cell), dx = L/nx, dy = L/ny.
+   * Leja path only, in float64 whatever opts->prec (KIOPS: PHIX_EINVAL).    */
+  PHIX_OP_ADR = 3,        /* f(u) = a lap u + b (u_x + u_y) + g u (1-u)(u-1/2) on [0,1]^2;
+                             param: a, b, g                                              */
+  PHIX_OP_ALLEN_CAHN = 4, /* f(u) = a lap u + u - u^3 on [-1,1]^2 (L = 2); param: a       */
+  PHIX_OP_BRUSSELATOR = 5 /* f_u = a lap u + 1 + u^2 v - 4u, f_v = a lap v + 3u - u^2 v
+                             on [0,1]^2, 2 species; param: a                             */
 } phix_op_kind;
 
 /* A Jacobian operator J = J(state) of one of the right-hand sides above.  */
@@ -114,7 +122,9 @@ typedef struct {
   double safety;       /* spectral interval [-safety*rho, 0] from power iteration (1.2) */
   double rho_re;       /* > 0: |Re lambda|max of J supplied by the caller: the interval
                           is [-rho_re, rho_hi] and no power iteration runs (default -1) */
-  double rho_hi;       /* upper end of the real interval when rho_re > 0 (default 0)   */
+  double rho_hi;       /* upper end of the real interval, with rho_re or with the power
+                          iteration's [-safety*rho, rho_hi] (default 0; > 0 for spectra
+                          reaching into the right half-plane, e.g. Allen-Cahn)         */
   double rho_im;       /* >= 0: bound on |Im lambda(J)|, used for substep counts (0)   */
   double gamma_cap;    /* Leja: max s*h*gamma per substep (default 200)                */
   double iota_cap;     /* Leja: max s*h*rho_im per substep, 0 = off (default 4)        */
@@ -142,6 +152,13 @@ typedef struct {
                           orthogonalisation of step j staged in shared memory and pass 1
                           of step j + 1 read from it) when nx % 64 == 0 and ny % 8 == 0;
                           0, or other grids: two passes per step                      */
+  int jv;              /* Leja: PHIX_JV_ANALYTIC (default) or PHIX_JV_FD, the "numerical"
+                          Jacobian of Sec. 4: J w ~ (f(u + eps w) - f(u)) / eps with
+                          eps = sqrt(2^-52) (1 + ||u||) / ||w||, in float64 (a comparison
+                          variant: one right-hand-side stencil per Newton iteration)     */
+  int leja_augmented;  /* phix_phi_combination with PHIX_LEJA: 0 (default) sums the
+                          individual phi_j actions; 1 interpolates exp of the augmented
+                          matrix of the Theorem of Sec. 2.1 (Appendix A), float64        */
   int chain;           /* Leja Newton pass with the single-step kernel:
                           PHIX_CHAIN_AUTO (default) and PHIX_CHAIN_PERSISTENT run the
                           whole pass in ONE cooperative launch (every block resident,
@@ -153,6 +170,7 @@ typedef struct {
 } phix_opts;
 
 typedef enum { PHIX_CHAIN_AUTO = 0, PHIX_CHAIN_PERSISTENT = 1, PHIX_CHAIN_GRAPH = 2 } phix_chain;
+typedef enum { PHIX_JV_ANALYTIC = 0, PHIX_JV_FD = 1 } phix_jv;
 
 typedef enum { PHIX_KERNEL_AUTO = 0, PHIX_KERNEL_SINGLE = 1, PHIX_KERNEL_TMA = 2 } phix_kernel;
 

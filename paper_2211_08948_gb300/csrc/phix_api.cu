@@ -30,6 +30,7 @@ enum Slot {
   S_BPROB, S_BORDER, S_BWS, S_BQ, S_XI,                          // batched problems, order, arena, queue, Leja points
   S_MFEAT, S_MY, S_MG, S_MCNT,                                   // learned interval: features, outputs, gradient
   S_FH, S_O4, S_O5, S_O6, S_UH, S_UB,                            // stages: f h, more outputs, host-state copy, step backup
+  S_GTAB, S_GCTL, S_GFU, S_GZ,                                   // general pass: table, control, f(u), zero state
   S_NSLOT
 };
 
@@ -162,7 +163,9 @@ void* ws(phix_ctx* ctx, int slot, size_t bytes) {
 }
 double* wsd(phix_ctx* ctx, int slot, size_t n) { return static_cast<double*>(ws(ctx, slot, n * sizeof(double))); }
 
-int ncomp_of(int kind) { return kind == PHIX_OP_GRAYSCOTT ? 2 : 1; }
+int ncomp_of(int kind) { return (kind == PHIX_OP_GRAYSCOTT || kind == PHIX_OP_BRUSSELATOR) ? 2 : 1; }
+// operators served by the general float64 kernel only (the no-flow problems)
+bool general_kind(int kind) { return kind >= PHIX_OP_ADR; }
 
 size_t elem_bytes(int prec) { return prec == P_FP32 ? 4 : 8; }
 
@@ -178,7 +181,7 @@ struct OpState {
 
 void check_op(phix_ctx* ctx, const phix_jop* op, bool need_state) {
   if (!op) fail(ctx, PHIX_EINVAL, "op is NULL");
-  if (op->kind < 0 || op->kind > 2) fail(ctx, PHIX_EINVAL, "unknown operator kind %d", op->kind);
+  if (op->kind < 0 || op->kind > PHIX_OP_BRUSSELATOR) fail(ctx, PHIX_EINVAL, "unknown operator kind %d", op->kind);
   if (op->nx < 3 || op->ny < 3) fail(ctx, PHIX_EINVAL, "grid %dx%d too small (>= 3 required)", op->nx, op->ny);
   if ((size_t)op->nx * op->ny > ((size_t)1 << 31)) fail(ctx, PHIX_EINVAL, "grid too large");
   if (need_state && op->kind != PHIX_OP_ADVDIFF && !op->state)
@@ -224,7 +227,7 @@ OpState make_opstate(phix_ctx* ctx, const phix_jop* op, const double* state, int
   s.state = state;
   uniform_coeffs(op->kind, op->nx, op->ny, op->param, s.kJ);
   s.st = nullptr;
-  if (op->kind != PHIX_OP_ADVDIFF) {
+  if (op->kind != PHIX_OP_ADVDIFF && !general_kind(op->kind)) {
     size_t nplanes = op->kind == PHIX_OP_GRAYSCOTT ? 2 : 1;
     size_t sb = prec == P_FP64 || prec == P_DF64 ? 8 : 4;
     void* st = ws(ctx, S_ST, nplanes * s.plane * sb);
@@ -396,12 +399,168 @@ void queue_chain(phix_ctx* ctx, int s, const ChainSpec& spec, bool profile, bool
   if (profile) CK(cudaEventRecord(ctx->ev[2 * s + 1], ctx->stream));
 }
 
+// ---------------------------------------------------------------------------
+// The general float64 path (general_kernels.cu): the no-flow problems, the
+// finite-difference Jacobian and the augmented-matrix form.  One launch per
+// iteration, GRAPH_ITERS at a time, the host reading the control block in
+// between (the device stops the chain itself; at most m_max + GRAPH_ITERS
+// launches).
+// ---------------------------------------------------------------------------
+struct GenAug {                 // augmented-matrix form (Appendix A)
+  std::vector<const double*> src;  // b_j, j = 1..p (index j - 1; NULL = zero)
+  double hgamma = 1.0;             // h gamma of the interval (source weights 1 / (h gamma))
+  double hc = 0.0;
+};
+
+struct GenOp {                  // operator data of the general kernel
+  const double* st = nullptr;   // state (nonlinear operators)
+  const double* fu = nullptr;   // f(state) (finite differences)
+  double fd_scale = 0.0;
+  int fd = 0;
+};
+
+GenOp general_op(phix_ctx* ctx, const OpState& os, const phix_opts& o) {
+  GenOp g;
+  g.fd = o.jv == PHIX_JV_FD;
+  g.st = os.state;
+  if (g.fd) {
+    if (!g.st) {  // a linear operator has no state: linearise at zero
+      double* z = wsd(ctx, S_GZ, os.N);
+      CK(cudaMemsetAsync(z, 0, os.N * sizeof(double), ctx->stream));
+      g.st = z;
+    }
+    double* fu = wsd(ctx, S_GFU, os.N);
+    KL(launch_rhs(os.d, g.st, fu, ctx->grid_stream, ctx->stream));
+    KL(launch_norm2(os.N, g.st, nullptr, ctx->partials, ctx->counter, ctx->scal, ctx->grid_stream, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->scal_h, ctx->scal, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    g.fu = fu;
+    g.fd_scale = std::sqrt(std::ldexp(1.0, -52)) * (1.0 + std::sqrt(ctx->scal_h[0]));
+  }
+  return g;
+}
+
+// Run a general chain (init or power start already queued) to its end; returns the control block.
+LejaCtl general_chain(phix_ctx* ctx, int mode, const OpState& os, int K, double* const* y, double* const* p,
+                      const GenOp& go, const GenAug* aug, LejaCtl* ctl, const double* tab, int m_max) {
+  std::vector<const double*> src;
+  if (aug) src = aug->src;
+  LejaCtl c{};
+  for (int launched = 0; launched <= m_max;) {
+    for (int i = 0; i < GRAPH_ITERS; ++i, ++launched)
+      KL(launch_general(mode, os.d.kind, os.d.nx, os.d.ny, K, nullptr, y, p, go.st, go.fu, go.fd_scale, go.fd, os.d.p,
+                        src.data(), (int)src.size(), ctl, ctx->partials, tab, ctx->grid_stream, ctx->stream));
+    CK(cudaMemcpyAsync(&c, ctl, sizeof c, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (c.done) break;
+  }
+  return c;
+}
+
+// One vertical Newton-Leja pass on the general kernel: out[k] = sum_m d_k[m] y_m
+// (the outputs accumulate in place, float64, no input scaling).
+void general_pass(phix_ctx* ctx, const OpState& os, const double* v, int K,
+                  const std::vector<const std::vector<double>*>& d, double c, double gamma, double tol,
+                  const phix_opts& o, double* const* out, phix_stats& stats, const GenAug* aug = nullptr) {
+  flush(ctx);
+  const int M = (int)d[0]->size();
+  const int m_max = M - 1;
+  const double* xi = leja_table(M);
+  std::vector<double> tab(gen_table_doubles(M), 0.0);
+  const int nsrc = aug ? (int)aug->src.size() : 0;
+  tab[0] = K;
+  tab[1] = o.m_min;
+  tab[2] = m_max;
+  tab[3] = M;
+  tab[4] = tol;
+  tab[5] = 0.0;
+  tab[6] = 1.0 / gamma;
+  tab[7] = nsrc;
+  double* beta = &tab[8];
+  double* dk = beta + M;
+  double* w = dk + (size_t)KMAX * M;
+  double* yt = w + (size_t)KIOPS_PMAX * M;
+  double* pt = yt + M;
+  for (int m = 1; m < M; ++m) beta[m] = -(c / gamma + xi[m - 1]);
+  for (int k = 0; k < K; ++k)
+    for (int m = 0; m < M; ++m) dk[(size_t)k * M + m] = (*d[k])[m];
+  if (aug && nsrc > 0) {
+    // the tail y_T of the augmented vector [b_0; e_p] evolves alone:
+    // y_T,m+1 = ((K - hc)/(h gamma) - xi_m) y_T,m (K: the upward shift); its
+    // source weights B y_T / (h gamma) and its share of the norms are known here
+    const int pn = nsrc;
+    std::vector<double> yT(pn, 0.0), pT(pn, 0.0), nxt(pn);
+    yT[pn - 1] = 1.0;
+    for (int m = 0; m < M; ++m) {
+      double y2 = 0.0, p2 = 0.0;
+      for (int i = 0; i < pn; ++i) {
+        pT[i] += (*d[0])[m] * yT[i];
+        y2 += yT[i] * yT[i];
+        p2 += pT[i] * pT[i];
+      }
+      yt[m] = y2;
+      pt[m] = p2;  // K == 1 in the augmented form
+      for (int j = 1; j <= pn; ++j) w[(size_t)m * KIOPS_PMAX + (j - 1)] = yT[pn - j] / aug->hgamma;
+      for (int i = 0; i < pn; ++i) {
+        const double ky = i + 1 < pn ? yT[i + 1] : 0.0;
+        nxt[i] = (ky - aug->hc * yT[i]) / aug->hgamma - (m < M - 1 ? xi[m] : 0.0) * yT[i];
+      }
+      yT = nxt;
+    }
+  }
+  double* dtab = wsd(ctx, S_GTAB, tab.size());
+  CK(cudaMemcpyAsync(dtab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  LejaCtl* ctl = static_cast<LejaCtl*>(ws(ctx, S_GCTL, sizeof(LejaCtl)));
+  CK(cudaMemsetAsync(ctl, 0, sizeof(LejaCtl), ctx->stream));
+  double* y[2] = {wsd(ctx, S_Y0, os.N), wsd(ctx, S_Y1, os.N)};
+  const GenOp go = general_op(ctx, os, o);
+  std::vector<const double*> src;
+  if (aug) src = aug->src;
+  KL(launch_general(2, os.d.kind, os.d.nx, os.d.ny, K, v, y, out, go.st, go.fu, go.fd_scale, go.fd, os.d.p,
+                    src.data(), nsrc, ctl, ctx->partials, dtab, ctx->grid_stream, ctx->stream));
+  const LejaCtl cb = general_chain(ctx, 0, os, K, y, out, go, aug, ctl, dtab, m_max);
+  const int status = cb.done ? cb.status : PHIX_ENOTCONV;
+  if (status == PHIX_ENOTCONV && cb.iters == m_max && m_max < o.m_max) {
+    ctx->ran_out = true;  // the table was too short: the call runs again with full tables
+    throw Rerun{};
+  }
+  stats.iters += cb.iters;
+  stats.jv += cb.iters;
+  stats.passes += 1;
+  if (status != PHIX_OK) stats.status = status;
+}
+
+// Power iteration on the general kernel (the no-flow problems, or the
+// finite-difference Jacobian).
+double general_power(phix_ctx* ctx, const OpState& os, const phix_opts& o, int* mv) {
+  flush(ctx);
+  std::vector<double> tab(gen_table_doubles(1), 0.0);
+  tab[2] = o.power_max_it;
+  tab[3] = 1;
+  tab[5] = o.power_rel;
+  double* dtab = wsd(ctx, S_GTAB, tab.size());
+  CK(cudaMemcpyAsync(dtab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  LejaCtl* ctl = static_cast<LejaCtl*>(ws(ctx, S_GCTL, sizeof(LejaCtl)));
+  CK(cudaMemsetAsync(ctl, 0, sizeof(LejaCtl), ctx->stream));
+  double* y[2] = {wsd(ctx, S_Y0, os.N), wsd(ctx, S_Y1, os.N)};
+  const GenOp go = general_op(ctx, os, o);
+  KL(launch_power_start(P_FP64, os.N, o.power_seed, y[0], ctl, ctx->partials, ctx->grid_iter, ctx->stream));
+  const LejaCtl c = general_chain(ctx, 1, os, 0, y, nullptr, go, nullptr, ctl, dtab, o.power_max_it);
+  if (c.status == PHIX_ENAN) fail(ctx, PHIX_ENAN, "power iteration produced a non-finite norm");
+  *mv = c.iters;
+  return c.rho;
+}
+
 // One Newton-Leja pass (Sec. 2.2): queued; its outcome reaches `stats` at the
 // next flush.
 void leja_pass(phix_ctx* ctx, const OpState& os, int prec, const double* v, int K,
                const std::vector<const std::vector<double>*>& d, double c, double gamma, double tol,
                const phix_opts& o, double* const* out, phix_stats& stats, const void* st_newton,
                int prescaled) {
+  if (general_kind(os.d.kind) || o.jv == PHIX_JV_FD) {
+    general_pass(ctx, os, v, K, d, c, gamma, tol, o, out, stats);
+    return;
+  }
   const int M = (int)d[0]->size();  // table length: at most o.m_max + 1
   const int m_max = M - 1;
   const double* xi = leja_table(M);
@@ -560,6 +719,7 @@ std::vector<std::vector<double>> pass_tables(phix_ctx* ctx, int K, const int* l,
 
 // Power iteration (Sec. 2.2) on the device; flushes to read the estimate.
 double power_iteration(phix_ctx* ctx, const OpState& os, int prec, const phix_opts& o, int* mv) {
+  if (general_kind(os.d.kind) || o.jv == PHIX_JV_FD) return general_power(ctx, os, o, mv);
   const size_t eb = elem_bytes(prec);
   void* y[2] = {ws(ctx, S_Y0, os.N * eb), ws(ctx, S_Y1, os.N * eb)};
   const int s = acquire_slot(ctx, ptab_bytes(o.power_max_it + 1));
@@ -646,7 +806,7 @@ void leja_phi(phix_ctx* ctx, const OpState& os, int prec, double h, const double
   // per state and factor, shared by every pass of the call)
   const void* st_n = os.st;
   int pre = 0;
-  if (os.d.kind == PHIX_OP_GRAYSCOTT) {
+  if (os.d.kind == PHIX_OP_GRAYSCOTT && o.jv != PHIX_JV_FD) {
     const double alpha = 1.0 / ivc.gamma;
     const size_t sb = prec == P_FP64 || prec == P_DF64 ? 8 : 4;
     void* st2 = ws(ctx, S_ST2, 2 * os.plane * sb);
@@ -960,7 +1120,7 @@ Interval interval_for(phix_ctx* ctx, const OpState& os, int prec, const phix_opt
     stats.power_mv += mv;
     iv.rho = rho;
     alpha = -o.safety * rho;
-    beta = 0.0;
+    beta = o.rho_hi;
   }
   iv.c = 0.5 * (alpha + beta);
   iv.gamma = 0.25 * (beta - alpha);
@@ -972,6 +1132,8 @@ void phi_actions(phix_ctx* ctx, const OpState& os, phix_method method, int prec,
                  int nout, const int* l, const double* sc, double* const* out, double tol, const phix_opts& o,
                  const Interval* iv, phix_stats& stats) {
   if (method == PHIX_KIOPS) {
+    if (general_kind(os.d.kind) || o.jv == PHIX_JV_FD)
+      fail(ctx, PHIX_EINVAL, "KIOPS covers the periodic operators with analytic Jacobians only");
     kiops_phi(ctx, os, prec, h, v, nout, l, sc, out, tol, o, stats);
     return;
   }
@@ -997,6 +1159,8 @@ phix_opts resolve_opts(phix_ctx* ctx, const phix_opts* in) {
   if (o.kiops_m_max < 2 || o.kiops_m_max > 128) fail(ctx, PHIX_EINVAL, "kiops_m_max must be in 2..128");
   if (o.kiops_fused != 0 && o.kiops_fused != 1) fail(ctx, PHIX_EINVAL, "kiops_fused must be 0 or 1");
   if (o.chain < PHIX_CHAIN_AUTO || o.chain > PHIX_CHAIN_GRAPH) fail(ctx, PHIX_EINVAL, "unknown chain mode %d", o.chain);
+  if (o.jv != PHIX_JV_ANALYTIC && o.jv != PHIX_JV_FD) fail(ctx, PHIX_EINVAL, "unknown jv mode %d", o.jv);
+  if (o.leja_augmented != 0 && o.leja_augmented != 1) fail(ctx, PHIX_EINVAL, "leja_augmented must be 0 or 1");
   return o;
 }
 
@@ -1075,6 +1239,8 @@ void phix_opts_default(phix_opts* o) {
   o->kiops_max_substeps = 10000;
   o->kiops_fused = 1;
   o->chain = PHIX_CHAIN_AUTO;
+  o->jv = PHIX_JV_ANALYTIC;
+  o->leja_augmented = 0;
 }
 
 phix_status phix_create(phix_ctx** out, void* stream) {
@@ -1532,6 +1698,36 @@ phix_status phix_phi_combination(phix_ctx* ctx, const phix_jop* op, double h, co
       return PHIX_OK;
     }
     OpState os = make_opstate(ctx, op, op->state, o.prec);
+    if (o.leja_augmented) {
+      // exp of the augmented matrix of the Theorem of Sec. 2.1 by one Leja
+      // pass (Appendix A): start vector [b_0; e_p], interval h [alpha, 0]
+      Interval iv = interval_for(ctx, os, o.prec, o, st);
+      GenAug aug;
+      aug.hgamma = h * iv.gamma;
+      aug.hc = h * iv.c;
+      double* zero = wsd(ctx, S_GZ, os.N);
+      CK(cudaMemsetAsync(zero, 0, os.N * sizeof(double), ctx->stream));
+      bool any = false;
+      for (int j = 1; j <= p; ++j) {
+        aug.src.push_back(b[j] ? b[j] : zero);  // a NULL b_j is a zero column
+        any = any || b[j];
+      }
+      if (!any) aug.src.clear();
+      const double* b0 = b[0] ? b[0] : zero;
+      if (aug.src.empty() && p > 0) {  // only b_0: a plain phi_0 pass
+        p = 0;
+      }
+      int l0 = 0;
+      const double a0 = h * iv.c, g0 = h * iv.gamma;
+      const std::vector<std::vector<double>> d = pass_tables(ctx, 1, &l0, &a0, &g0, tol, o);
+      std::vector<const std::vector<double>*> dp(1, &d[0]);
+      double* outs[1] = {out};
+      phix_opts og = o;
+      og.jv = o.jv;
+      general_pass(ctx, os, b0, 1, dp, iv.c, iv.gamma, tol, og, outs, st, p > 0 ? &aug : nullptr);
+      CK(cudaStreamSynchronize(ctx->stream));
+      return PHIX_OK;
+    }
     CK(cudaMemsetAsync(out, 0, os.N * sizeof(double), ctx->stream));
     Interval iv = interval_for(ctx, os, o.prec, o, st);
     double* tmp = wsd(ctx, S_O3, os.N);

@@ -279,6 +279,14 @@ cudaError_t launch_block_faces(int bx, int by, int ncomp, int dir, double* ypad,
 cudaError_t launch_block_splitmix(int bx, int by, int ncomp, int gnx, int gny, int x0, int y0, uint64_t seed,
                                   double* ypad, int grid, cudaStream_t s);
 
+// ---- general float64 Newton / power step (general_kernels.cu) -------------
+// mode 0 Newton, 1 power, 2 init; tab: gen_table_doubles(M) doubles (device)
+size_t gen_table_doubles(int M);
+cudaError_t launch_general(int mode, int kind, int nx, int ny, int K, const double* v, double* const* y,
+                           double* const* p, const double* st, const double* fu, double fd_scale, int fd,
+                           const double* prm, const double* const* src, int nsrc, LejaCtl* ctl, double* partials,
+                           const double* tab, int grid, cudaStream_t s);
+
 // ---- host math (host_math.cpp) --------------------------------------------
 double phi_host(int l, double z);
 int leja_points_host(double* xi, int m);                 // 0 on success

@@ -229,7 +229,7 @@ extern "C" phix_status phix_phi_action_noalloc(const phix_jop* op, double h, con
     st.power_mv = c.h.iters;
     st.rho = c.h.rho;
     alpha_i = -o.safety * c.h.rho;
-    beta_i = 0.0;
+    beta_i = o.rho_hi;
   }
   // half-width covering twice the imaginary extent (complex spectra), the
   // interval anchored at its right end beta

@@ -3,99 +3,22 @@
 // actions with an axpy (ODE-identity substeps), linear combinations and
 // norms.  They run a handful of times per time step, against hundreds of
 // Newton-Leja iterations, so they stay in plain float64.
-#include "phix_internal.h"
+#include "op_points.cuh"
 
 namespace phix {
 
 namespace {
 
-struct Nbr {
-  double c, e, w, n, s;
-};
-
-__device__ __forceinline__ Nbr load_nbr(const double* __restrict__ x, int nx, int ny, int ix, int iy) {
-  const int ixm = ix == 0 ? nx - 1 : ix - 1, ixp = ix == nx - 1 ? 0 : ix + 1;
-  const int iym = iy == 0 ? ny - 1 : iy - 1, iyp = iy == ny - 1 ? 0 : iy + 1;
-  Nbr r;
-  r.c = x[(size_t)iy * nx + ix];
-  r.e = x[(size_t)iy * nx + ixp];
-  r.w = x[(size_t)iy * nx + ixm];
-  r.n = x[(size_t)iyp * nx + ix];
-  r.s = x[(size_t)iym * nx + ix];
-  return r;
-}
-
-__device__ __forceinline__ double lap(const Nbr& a, double idx2, double idy2) {
-  return (a.e + a.w - 2.0 * a.c) * idx2 + (a.n + a.s - 2.0 * a.c) * idy2;
-}
-__device__ __forceinline__ double ddx(const Nbr& a, double i2dx) { return (a.e - a.w) * i2dx; }
-__device__ __forceinline__ double ddy(const Nbr& a, double i2dy) { return (a.n - a.s) * i2dy; }
-
-struct Geo {
-  int nx, ny;
-  double idx2, idy2, i2dx, i2dy;
-};
-__device__ __forceinline__ Geo geo(const OpDesc& op) {
-  Geo g;
-  g.nx = op.nx;
-  g.ny = op.ny;
-  double dx = 1.0 / op.nx, dy = 1.0 / op.ny;
-  g.idx2 = 1.0 / (dx * dx);
-  g.idy2 = 1.0 / (dy * dy);
-  g.i2dx = 0.5 / dx;
-  g.i2dy = 0.5 / dy;
-  return g;
-}
-
-// f(u) at one grid point; writes 1 or 2 species values
-__device__ __forceinline__ void rhs_point(const OpDesc& op, const Geo& g, const double* u, int ix,
-                                          int iy, double* out) {
-  const size_t plane = (size_t)g.nx * g.ny;
-  if (op.kind == PHIX_OP_ADVDIFF) {
-    Nbr a = load_nbr(u, g.nx, g.ny, ix, iy);
-    out[0] = op.p[0] * lap(a, g.idx2, g.idy2) + op.p[1] * ddx(a, g.i2dx) + op.p[2] * ddy(a, g.i2dy);
-  } else if (op.kind == PHIX_OP_GRAYSCOTT) {
-    Nbr a = load_nbr(u, g.nx, g.ny, ix, iy);
-    Nbr b = load_nbr(u + plane, g.nx, g.ny, ix, iy);
-    double uvv = a.c * b.c * b.c;
-    out[0] = op.p[0] * lap(a, g.idx2, g.idy2) - uvv + op.p[2] * (1.0 - a.c);
-    out[1] = op.p[1] * lap(b, g.idx2, g.idy2) + uvv - (op.p[2] + op.p[3]) * b.c;
-  } else {
-    Nbr a = load_nbr(u, g.nx, g.ny, ix, iy);
-    out[0] = op.p[0] * lap(a, g.idx2, g.idy2) - a.c * (ddx(a, g.i2dx) + ddy(a, g.i2dy));
-  }
-}
-
-// J(state) x at one grid point
-__device__ __forceinline__ void jv_point(const OpDesc& op, const Geo& g, const double* st,
-                                         const double* x, int ix, int iy, double* out) {
-  const size_t plane = (size_t)g.nx * g.ny;
-  const size_t i = (size_t)iy * g.nx + ix;
-  if (op.kind == PHIX_OP_ADVDIFF) {
-    Nbr a = load_nbr(x, g.nx, g.ny, ix, iy);
-    out[0] = op.p[0] * lap(a, g.idx2, g.idy2) + op.p[1] * ddx(a, g.i2dx) + op.p[2] * ddy(a, g.i2dy);
-  } else if (op.kind == PHIX_OP_GRAYSCOTT) {
-    Nbr a = load_nbr(x, g.nx, g.ny, ix, iy);
-    Nbr b = load_nbr(x + plane, g.nx, g.ny, ix, iy);
-    double U = st[i], V = st[plane + i];
-    out[0] = op.p[0] * lap(a, g.idx2, g.idy2) - (V * V + op.p[2]) * a.c - 2.0 * U * V * b.c;
-    out[1] = op.p[1] * lap(b, g.idx2, g.idy2) + V * V * a.c + (2.0 * U * V - (op.p[2] + op.p[3])) * b.c;
-  } else {
-    Nbr a = load_nbr(x, g.nx, g.ny, ix, iy);
-    Nbr U = load_nbr(st, g.nx, g.ny, ix, iy);
-    double divU = ddx(U, g.i2dx) + ddy(U, g.i2dy);
-    out[0] = op.p[0] * lap(a, g.idx2, g.idy2) - divU * a.c - U.c * (ddx(a, g.i2dx) + ddy(a, g.i2dy));
-  }
-}
-
 __global__ void k_rhs(OpDesc op, const double* __restrict__ u, double* __restrict__ f) {
-  Geo g = geo(op);
+  const Geo g = make_geo(op.kind, op.nx, op.ny);
   const size_t plane = (size_t)g.nx * g.ny;
-  const int nc = op.kind == PHIX_OP_GRAYSCOTT ? 2 : 1;
+  const int nc = op_ncomp(op.kind);
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < plane; i += (size_t)gridDim.x * blockDim.x) {
     const int ix = (int)((unsigned)i % (unsigned)g.nx), iy = (int)((unsigned)i / (unsigned)g.nx);  // i < 2^31
+    const Nbr a = load_nbr(u, g, ix, iy);
+    const Nbr b = nc == 2 ? load_nbr(u + plane, g, ix, iy) : a;
     double o[2];
-    rhs_point(op, g, u, ix, iy, o);
+    rhs_nbr(op.kind, op.p, g, a, b, o);
     for (int q = 0; q < nc; ++q) f[q * plane + i] = o[q];
   }
 }
@@ -122,26 +45,52 @@ __global__ void k_remainder_gs(size_t plane, const double* __restrict__ u, const
 
 __global__ void k_remainder_burgers(OpDesc op, const double* __restrict__ u, const double* __restrict__ a,
                                     double* __restrict__ R) {
-  Geo g = geo(op);
+  const Geo g = make_geo(op.kind, op.nx, op.ny);
   const unsigned plane = (unsigned)g.nx * (unsigned)g.ny;  // <= 2^31 points
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < plane; i += gridDim.x * blockDim.x) {
     const int ix = (int)(i % (unsigned)g.nx), iy = (int)(i / (unsigned)g.nx);
-    Nbr A = load_nbr(a, g.nx, g.ny, ix, iy), U = load_nbr(u, g.nx, g.ny, ix, iy);
+    Nbr A = load_nbr(a, g, ix, iy), U = load_nbr(u, g, ix, iy);
     Nbr d{A.c - U.c, A.e - U.e, A.w - U.w, A.n - U.n, A.s - U.s};
-    R[i] = -d.c * (ddx(d, g.i2dx) + ddy(d, g.i2dy));
+    R[i] = -d.c * grad_sum(d, g);
+  }
+}
+
+// The no-flow problems' remainders, pointwise in d = a - u (their linear parts
+// cancel):  ADR  g (n(a) - n(u) - n'(u) d) with n(u) = u (1-u)(u-1/2):  g d^2 (3/2 - a - 2u);
+// Allen-Cahn  -(a^3 - u^3 - 3u^2 d) = -d^2 (a + 2u);
+// Brusselator  a_u^2 a_v - u^2 v - 2uv d_u - u^2 d_v = d_u (2u d_v + v d_u + d_u d_v) = R_u, R_v = -R_u.
+__global__ void k_remainder_point(int kind, double gcoef, size_t plane, const double* __restrict__ u,
+                                  const double* __restrict__ a, double* __restrict__ R) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < plane; i += (size_t)gridDim.x * blockDim.x) {
+    const double uc = u[i], ac = a[i], d = ac - uc;
+    if (kind == PHIX_OP_ADR) {
+      R[i] = gcoef * d * d * (1.5 - ac - 2.0 * uc);
+    } else if (kind == PHIX_OP_ALLEN_CAHN) {
+      R[i] = -d * d * (ac + 2.0 * uc);
+    } else {
+      const double v = u[plane + i], dv = a[plane + i] - v;
+      const double r = d * (2.0 * uc * dv + v * d + d * dv);
+      R[i] = r;
+      R[plane + i] = -r;
+    }
   }
 }
 
 __global__ void k_jv_axpy(OpDesc op, const double* __restrict__ st, const double* __restrict__ x,
                           double alpha, const double* __restrict__ v, double beta,
                           double* __restrict__ out) {
-  Geo g = geo(op);
+  const Geo g = make_geo(op.kind, op.nx, op.ny);
   const size_t plane = (size_t)g.nx * g.ny;
-  const int nc = op.kind == PHIX_OP_GRAYSCOTT ? 2 : 1;
+  const int nc = op_ncomp(op.kind);
+  const Nbr zero{0, 0, 0, 0, 0};
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < plane; i += (size_t)gridDim.x * blockDim.x) {
     const int ix = (int)((unsigned)i % (unsigned)g.nx), iy = (int)((unsigned)i / (unsigned)g.nx);  // i < 2^31
+    const Nbr xa = load_nbr(x, g, ix, iy);
+    const Nbr xb = nc == 2 ? load_nbr(x + plane, g, ix, iy) : xa;
+    const Nbr sa = st ? load_nbr(st, g, ix, iy) : zero;
+    const Nbr sb = (st && nc == 2) ? load_nbr(st + plane, g, ix, iy) : sa;
     double o[2];
-    jv_point(op, g, st, x, ix, iy, o);
+    jv_nbr(op.kind, op.p, g, xa, xb, sa, sb, o);
     for (int q = 0; q < nc; ++q) {
       double r = alpha * o[q];
       if (v) r += beta * v[q * plane + i];
@@ -222,6 +171,8 @@ cudaError_t launch_remainder(const OpDesc& op, const double* u, const double* a,
     k_remainder_gs<<<clamp_grid(plane, grid), 256, 0, s>>>(plane, u, a, R);
   } else if (op.kind == PHIX_OP_BURGERS) {
     k_remainder_burgers<<<clamp_grid(plane, grid), 256, 0, s>>>(op, u, a, R);
+  } else if (op.kind >= PHIX_OP_ADR) {
+    k_remainder_point<<<clamp_grid(plane, grid), 256, 0, s>>>(op.kind, op.p[2], plane, u, a, R);
   } else {
     return cudaMemsetAsync(R, 0, plane * sizeof(double), s);
   }

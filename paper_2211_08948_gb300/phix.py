@@ -27,6 +27,8 @@ PHIX_CHAIN_AUTO, PHIX_CHAIN_PERSISTENT, PHIX_CHAIN_GRAPH = 0, 1, 2
 PHIX_CONTROL_TRADITIONAL, PHIX_CONTROL_COST = 0, 1
 PHIX_FP64, PHIX_DF64, PHIX_FP32_JV, PHIX_FP32 = 0, 1, 2, 3
 PHIX_OP_ADVDIFF, PHIX_OP_GRAYSCOTT, PHIX_OP_BURGERS = 0, 1, 2
+PHIX_OP_ADR, PHIX_OP_ALLEN_CAHN, PHIX_OP_BRUSSELATOR = 3, 4, 5
+PHIX_JV_ANALYTIC, PHIX_JV_FD = 0, 1
 
 # every symbol include/phix.h declares
 EXPORTS = [
@@ -53,7 +55,7 @@ class phix_opts(ctypes.Structure):
                 ("kiops_m_init", ctypes.c_int), ("kiops_m_max", ctypes.c_int),
                 ("kiops_m_step", ctypes.c_int), ("kiops_max_substeps", ctypes.c_int),
                 ("profile", ctypes.c_int), ("kernel", ctypes.c_int), ("kiops_fused", ctypes.c_int),
-                ("chain", ctypes.c_int)]
+                ("jv", ctypes.c_int), ("leja_augmented", ctypes.c_int), ("chain", ctypes.c_int)]
 
 
 class phix_batch_problem(ctypes.Structure):

@@ -39,7 +39,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_version_and_opts_defaults():
     phix, lib = _lib()
-    assert phix.phix_version() == 102
+    assert phix.phix_version() == 103
     assert lib.phix_opts_size() == ctypes.sizeof(phix.phix_opts)
     assert lib.phix_stats_size() == ctypes.sizeof(phix.phix_stats)
     o = phix.phix_opts_default()
@@ -49,7 +49,7 @@ def test_version_and_opts_defaults():
     assert o.profile == 0 and o.kernel == phix.PHIX_KERNEL_AUTO
     # the last field: its default read back through the ctypes mirror checks the
     # mirror's layout against the C struct that phix_opts_default fills
-    assert o.kiops_fused == 1 and o.chain == phix.PHIX_CHAIN_AUTO
+    assert o.kiops_fused == 1 and o.chain == phix.PHIX_CHAIN_AUTO and o.jv == 0 and o.leja_augmented == 0
     assert ctypes.sizeof(phix.phix_jop) == 4 * 3 + 4 + 8 * 8 + 8
 
 
