@@ -98,7 +98,7 @@ typedef enum {
   PHIX_OP_BURGERS = 2,   /* f(u) = nu lap u - u (u_x + u_y), 1 species                  */
   /* The paper's no-flow problems (Sec. 3): cell-centred grids with homogeneous
    * Neumann boundaries (ghost cell = boundary cell), dx = L/nx, dy = L/ny.
-   * Leja path only, in float64 whatever opts->prec (KIOPS: PHIX_EINVAL).    */
+   * Leja and KIOPS iterate in float64 for these whatever opts->prec.         */
   PHIX_OP_ADR = 3,        /* f(u) = a lap u + b (u_x + u_y) + g u (1-u)(u-1/2) on [0,1]^2;
                              param: a, b, g                                              */
   PHIX_OP_ALLEN_CAHN = 4, /* f(u) = a lap u + u - u^3 on [-1,1]^2 (L = 2); param: a       */

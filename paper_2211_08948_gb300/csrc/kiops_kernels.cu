@@ -20,6 +20,7 @@
 // one-point halo ring and the stencil of the next step reads it there.
 #include <algorithm>
 #include "iter_common.cuh"
+#include "op_points.cuh"
 
 namespace phix {
 
@@ -140,6 +141,8 @@ struct ArnArgs {
   int j, p, nx, ny, ntiles, tiles_x, nscaled;
   double h;
   double kJ[8];
+  int gkind;         // general operator (the no-flow problems): its kind, parameters;
+  double gprm[8];    // st is then the raw float64 state
 };
 
 // next pass-1 coefficients from s[j] (single thread)
@@ -193,6 +196,8 @@ __device__ void fused_prepare(KiopsCtl* kc, int j, int p, double ws, double h, c
   kc->gud = h;
   kc->guf = split2d(h);
 }
+
+__device__ void arn1_finish(const ArnArgs& a, KiopsCtl* kc, const double (&tot)[3]);
 
 template <int P, int OP, int V>
 __global__ void __launch_bounds__(THREADS) k_arn1(ArnArgs a) {
@@ -329,7 +334,60 @@ __global__ void __launch_bounds__(THREADS) k_arn1(ArnArgs a) {
   if (block_partials_and_last<Acc, 3>(acc, a.partials, &kc->count)) {
     double tot[3];
     reduce_partials<Acc, 3>(a.partials, tot);
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
+    if (threadIdx.x == 0 && threadIdx.y == 0) arn1_finish(a, kc, tot);
+  }
+}
+
+// Pass 1 of Arnoldi step j for a general operator (the no-flow problems),
+// float64, one point per thread: z = A~ V_j = (h s_j) J Zhat_j + B t (the
+// augmented columns), with <Zhat_j, z>, <Zhat_{j-1}, z>, ||z||^2.
+__global__ void __launch_bounds__(THREADS) k_arn1g(ArnArgs a) {
+  KiopsCtl* kc = a.kc;
+  if (__ldcg(&kc->stop)) return;
+  const double g = __ldcg(&kc->gad);  // h s_j
+  double bw[KIOPS_PMAX];
+  for (int b = 0; b < KIOPS_PMAX; ++b) bw[b] = b < a.nb ? __ldcg(&kc->bd[a.bslot[b]]) : 0.0;
+  const Geo geo = make_geo(a.gkind, a.nx, a.ny);
+  const int nc = op_ncomp(a.gkind);
+  const size_t plane = (size_t)a.nx * a.ny;
+  const double* zj = static_cast<const double*>(a.zj);
+  const double* zm = static_cast<const double*>(a.zjm1);
+  double* zo = static_cast<double*>(a.zout);
+  const double* st = static_cast<const double*>(a.st);
+  const Nbr zero{0, 0, 0, 0, 0};
+  double acc[3] = {0.0, 0.0, 0.0};
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  for (size_t i = (size_t)blockIdx.x * THREADS + tid; i < plane; i += (size_t)gridDim.x * THREADS) {
+    const int ix = (int)(i % (size_t)a.nx), iy = (int)(i / (size_t)a.nx);
+    const Nbr xa = load_nbr(zj, geo, ix, iy);
+    const Nbr xb = nc == 2 ? load_nbr(zj + plane, geo, ix, iy) : xa;
+    const Nbr sa = st ? load_nbr(st, geo, ix, iy) : zero;
+    const Nbr sb = (st && nc == 2) ? load_nbr(st + plane, geo, ix, iy) : sa;
+    double J[2];
+    jv_nbr(a.gkind, a.gprm, geo, xa, xb, sa, sb, J);
+    const double xc[2] = {xa.c, xb.c};
+    for (int q = 0; q < nc; ++q) {
+      const size_t idx = q * plane + i;
+      double z = g * J[q];
+      for (int b = 0; b < a.nb; ++b) z += bw[b] * static_cast<const double*>(a.bz[b])[idx];
+      zo[idx] = z;
+      acc[0] += xc[q] * z;
+      if (zm) acc[1] += zm[idx] * z;
+      acc[2] += z * z;
+    }
+  }
+  if (block_partials_and_last<double, 3>(acc, a.partials, &kc->count)) {
+    double tot[3];
+    reduce_partials<double, 3>(a.partials, tot);
+    if (threadIdx.x == 0 && threadIdx.y == 0) arn1_finish(a, kc, tot);
+  }
+}
+
+// The epilogue of pass 1 (single thread): h_{j,j}, h_{j-1,j}, ||A~ V_j||, the
+// tail of A~ V_j, the pass-2 coefficients.
+__device__ void arn1_finish(const ArnArgs& a, KiopsCtl* kc, const double (&tot)[3]) {
+  {
+    {
       const int j = a.j, p = a.p;
       const double sj = kc->s[j];
       const double* tj = kc->tail + j * KIOPS_PMAX;
@@ -1501,6 +1559,8 @@ ArnArgs make_arn(const KiopsSpec& s, int j, int V) {
   a.nscaled = s.nscaled;
   a.h = s.h;
   for (int i = 0; i < 8; ++i) a.kJ[i] = s.kJ[i];
+  a.gkind = s.op;
+  for (int i = 0; i < 8; ++i) a.gprm[i] = s.prm[i];
   return a;
 }
 
@@ -1545,7 +1605,7 @@ cudaError_t arn_t(const KiopsSpec& s, int j, cudaStream_t st) {
     k_arn1<P, OP, 1><<<g1, dim3(32, TILE_Y), 0, st>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const size_t N = (size_t)s.nx * s.ny * (OP == PHIX_OP_GRAYSCOTT ? 2 : 1);
+  const size_t N = (size_t)s.nx * s.ny * op_ncomp(OP);
   k_arn2<P><<<s.nsm * occ2, dim3(32, TILE_Y), 0, st>>>(a, N);
   return cudaGetLastError();
 }
@@ -1605,6 +1665,20 @@ cudaError_t fused_p(const KiopsSpec& s, int j, bool first, cudaStream_t st) {
   return cudaErrorInvalidValue;
 }
 
+// general operators: float64 pass 1 on k_arn1g, then the common pass 2
+cudaError_t arn_general(const KiopsSpec& s, int j, cudaStream_t st) {
+  static const int occ1 = blocks_per_sm(reinterpret_cast<const void*>(k_arn1g));
+  static const int occ2 = blocks_per_sm(reinterpret_cast<const void*>(k_arn2<P_FP64>));
+  ArnArgs a = make_arn(s, j, 1);
+  const size_t plane = (size_t)s.nx * s.ny;
+  const int g1 = (int)std::min<size_t>((size_t)s.nsm * occ1, (plane + THREADS - 1) / THREADS);
+  k_arn1g<<<g1, dim3(32, TILE_Y), 0, st>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_arn2<P_FP64><<<s.nsm * occ2, dim3(32, TILE_Y), 0, st>>>(a, plane * op_ncomp(s.op));
+  return cudaGetLastError();
+}
+
 template <int P>
 cudaError_t arn_p(const KiopsSpec& s, int j, cudaStream_t st) {
   switch (s.op) {
@@ -1615,6 +1689,7 @@ cudaError_t arn_p(const KiopsSpec& s, int j, cudaStream_t st) {
     case PHIX_OP_BURGERS:
       return arn_t<P, PHIX_OP_BURGERS>(s, j, st);
   }
+  if (P == P_FP64 && s.op >= PHIX_OP_ADR) return arn_general(s, j, st);
   return cudaErrorInvalidValue;
 }
 
@@ -1625,7 +1700,8 @@ cudaError_t kiops_arnoldi(const KiopsSpec& s, int j, cudaStream_t st) {
 }
 
 bool kiops_fused_ok(const KiopsSpec& s) {
-  return s.nx % 64 == 0 && s.ny % TILE_Y == 0 && s.W[0] != nullptr && s.W[1] != nullptr;
+  return s.op <= PHIX_OP_BURGERS && s.nx % 64 == 0 && s.ny % TILE_Y == 0 && s.W[0] != nullptr &&
+         s.W[1] != nullptr;
 }
 
 cudaError_t kiops_fused_first(const KiopsSpec& s, cudaStream_t st) {
@@ -1649,7 +1725,7 @@ cudaError_t kiops_smallexp(KiopsCtl* kc, int m, double tau, double tau_end, doub
 }
 
 cudaError_t kiops_combine(const KiopsSpec& s, int n, double* out, double scale, cudaStream_t st) {
-  const size_t N = (size_t)s.nx * s.ny * (s.op == PHIX_OP_GRAYSCOTT ? 2 : 1);
+  const size_t N = (size_t)s.nx * s.ny * op_ncomp(s.op);
   CombArgs c = make_comb(s, n, out, scale);
   if (s.prec == P_FP64)
     k_kcomb<P_FP64><<<s.grid, dim3(32, TILE_Y), 0, st>>>(c, N);
@@ -1659,7 +1735,7 @@ cudaError_t kiops_combine(const KiopsSpec& s, int n, double* out, double scale, 
 }
 
 cudaError_t kiops_start(const KiopsSpec& s, const double* b0, double eta, double cscale, cudaStream_t st) {
-  const size_t N = (size_t)s.nx * s.ny * (s.op == PHIX_OP_GRAYSCOTT ? 2 : 1);
+  const size_t N = (size_t)s.nx * s.ny * op_ncomp(s.op);
   CombArgs c = make_comb(s, 1, nullptr, 0.0);
   if (s.prec == P_FP64)
     k_kstart<P_FP64><<<s.grid, dim3(32, TILE_Y), 0, st>>>(b0, static_cast<double*>(s.Zh[0]), N, c, eta, cscale);

@@ -917,7 +917,8 @@ void read_kc(phix_ctx* ctx, KiopsCtl* kc) {
 void kiops_run(phix_ctx* ctx, const OpState& os, int prec, double h, const double* const* b, int p,
                const std::vector<double>& times, const std::vector<std::vector<KOut>>& outs, double tol,
                const phix_opts& o, phix_stats& stats) {
-  const int kp = kiops_prec(prec);
+  const bool general = general_kind(os.d.kind);  // the no-flow problems: float64 general pass 1
+  const int kp = general ? P_FP64 : kiops_prec(prec);
   const size_t N = os.N, eb = 8;
   const int mmax = o.kiops_m_max;
   if (p > KIOPS_PMAX) fail(ctx, PHIX_EINVAL, "KIOPS supports p <= %d", KIOPS_PMAX);
@@ -932,7 +933,8 @@ void kiops_run(phix_ctx* ctx, const OpState& os, int prec, double h, const doubl
   void** Zd = static_cast<void**>(ws(ctx, S_KPTR, sizeof(void*) * (mmax + 2)));
   CK(cudaMemcpyAsync(Zd, ks.Zh, sizeof(void*) * (mmax + 2), cudaMemcpyHostToDevice, ctx->stream));
   ks.Z = Zd;
-  ks.st = os.st;
+  ks.st = general ? static_cast<const void*>(os.state) : os.st;
+  for (int i = 0; i < 8; ++i) ks.prm[i] = os.d.p[i];
   KiopsCtl* kc = static_cast<KiopsCtl*>(ws(ctx, S_KCTL, sizeof(KiopsCtl)));
   CK(cudaMemsetAsync(kc, 0, sizeof(KiopsCtl), ctx->stream));
   ks.kc = kc;
@@ -1132,8 +1134,7 @@ void phi_actions(phix_ctx* ctx, const OpState& os, phix_method method, int prec,
                  int nout, const int* l, const double* sc, double* const* out, double tol, const phix_opts& o,
                  const Interval* iv, phix_stats& stats) {
   if (method == PHIX_KIOPS) {
-    if (general_kind(os.d.kind) || o.jv == PHIX_JV_FD)
-      fail(ctx, PHIX_EINVAL, "KIOPS covers the periodic operators with analytic Jacobians only");
+    if (o.jv == PHIX_JV_FD) fail(ctx, PHIX_EINVAL, "KIOPS takes the analytic Jacobian only");
     kiops_phi(ctx, os, prec, h, v, nout, l, sc, out, tol, o, stats);
     return;
   }

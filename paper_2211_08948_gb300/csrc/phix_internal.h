@@ -195,6 +195,8 @@ struct KiopsSpec {
   double* partials;
   double h;                     // A = h J
   double kJ[8];                 // unscaled uniform J coefficients
+  double prm[8];                // operator parameters (general operators: the no-flow problems,
+                                // float64 only, st = the raw state)
   int nscaled;
   int grid;                     // streaming kernels (combine, start)
   int nsm;                      // SMs (the Arnoldi kernels size their grids by occupancy)

@@ -119,14 +119,47 @@ def test_no_flow_exprb43_step_vs_oracle(px, kind):
     assert st.err_est == pytest.approx(np.linalg.norm(u4 - u3), rel=1e-6)
 
 
-def test_no_flow_rejects_kiops(px):
+@pytest.mark.parametrize("kind", ["adr", "allen_cahn", "brusselator"])
+def test_no_flow_kiops_vs_oracle(px, kind):
+    """KIOPS on the no-flow problems (float64 general Arnoldi pass): phi_0 and
+    phi_1 at output times 1/2, 1 against the oracle's KIOPS-style method."""
     phix, ctx = px
-    n = 16
-    k, prm, op, u, h = problem(phix, "allen_cahn", n)
-    out = torch.empty(u.size, dtype=torch.float64, device="cuda")
-    st = phix.phix_phi_action(ctx, phix.make_jop(k, n, n, prm, dev(u)), h, dev(u), [1], [1.0], [out], 1e-8,
-                              phix.PHIX_KIOPS, None, check=False)
-    assert st.status == phix.PHIX_EINVAL
+    n = 32
+    k, prm, op, u, h = problem(phix, kind, n)
+    v = np.random.default_rng(9).standard_normal(u.size)
+    outs = [(0, 1.0), (1, 0.5), (1, 1.0)]
+    jop = phix.make_jop(k, n, n, prm, dev(u))
+    od = [torch.empty(u.size, dtype=torch.float64, device="cuda") for _ in outs]
+    kw = dict(m_init=16, m_max=64, m_step=8)
+    st = phix.phix_phi_action(ctx, jop, h, dev(v), [l for l, _ in outs], [s for _, s in outs], od, 1e-10,
+                              phix.PHIX_KIOPS, phix.phix_opts_default())
+    ref, infos = kiops.kiops_phi(lambda x: h * op.jv(x), v, outs, 1e-10, **kw)
+    assert st.iters == sum(i["matvecs"] for i in infos)
+    for o, r in zip(od, ref):
+        assert rel(o.cpu().numpy(), r) <= 1e-10
+
+
+@pytest.mark.parametrize("kind,scheme,method", [("adr", "epirk4s3", "lekry"), ("brusselator", "exprb53s3", "kiops"),
+                                                ("allen_cahn", "epirk5p1", "kiops")])
+def test_no_flow_krylov_steps_vs_oracle(px, kind, scheme, method):
+    phix, ctx = px
+    n = 32
+    k, prm, op, u, h = problem(phix, kind, n)
+    base = problems.ADR(n, *prm) if kind == "adr" else (problems.AllenCahn(n, *prm) if kind == "allen_cahn"
+                                                          else problems.Brusselator(n, *prm))
+    kw, okw = {}, {}
+    if kind == "adr" and method == "lekry":
+        kw["rho_im"] = 2.0 * abs(prm[1]) * n
+        okw = dict(leja_kw=dict(rho_im=kw["rho_im"], iota_cap=4.0))
+    ud = dev(u)
+    sch = {"epirk4s3": phix.PHIX_EPIRK4S3, "exprb53s3": phix.PHIX_EXPRB53S3, "epirk5p1": phix.PHIX_EPIRK5P1}[scheme]
+    meth = phix.PHIX_LEKRY if method == "lekry" else phix.PHIX_KIOPS
+    st = phix.phix_step(ctx, sch, phix.make_jop(k, n, n, prm), ud, h, 1e-10, meth,
+                        phix.phix_opts_default(prec=phix.PHIX_FP64, **kw))
+    uh, ul, ost = integrators.STEPS[scheme](base, u, h, method=method, tol=1e-10,
+                                            kiops_kw=dict(m_init=16, m_max=64, m_step=8), **okw)
+    assert rel(ud.cpu().numpy() - u, uh - u) <= 1e-9
+    assert st.err_est == pytest.approx(np.linalg.norm(uh - ul), rel=1e-6)
 
 
 @pytest.mark.parametrize("kind", ["grayscott", "brusselator"])
