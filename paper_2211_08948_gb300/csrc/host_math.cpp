@@ -112,31 +112,36 @@ void divided_differences_host(const double* x, double* f, int n) {
 }
 
 void DDTable::grow(int n) {
-  if ((int)d.size() >= n) return;
+  const int n0 = (int)d.size();
+  if (n0 >= n) return;
   const double* x = leja_table(n);
-  d.reserve(n);
-  diag.reserve(n);
-  for (int i = (int)d.size(); i < n; ++i) {
-    // new diagonal: nd[0] = f(x_i), nd[k] = (nd[k-1] - diag[k-1]) / (x_i - x_{i-k})
-    double nv = phi_host(l, a + b * x[i]);
-    if (i == 0) {
-      diag.push_back(nv);
-      d.push_back(nv);
-      continue;
+  // The new points i = n0 .. n-1 column by column: column j holds
+  // f[x_{i-j}, ..., x_i] = (f[x_{i-j+1}..x_i] - f[x_{i-j}..x_{i-1}]) / (x_i - x_{i-j}),
+  // the entry at i = n0 taking its left neighbour from the stored diagonal of
+  // point n0 - 1.  The same operations as point-by-point growth, in an order
+  // whose inner loop has independent divisions.
+  const int C = n - n0;
+  std::vector<double> col(C), nxt(C), ndiag(n);
+  for (int c = 0; c < C; ++c) col[c] = phi_host(l, a + b * x[n0 + c]);
+  d.resize(n);
+  if (n0 == 0) d[0] = col[0];
+  ndiag[0] = col[C - 1];
+  for (int j = 1; j < n; ++j) {
+    const int c0 = std::max(0, j - n0);
+    const double* __restrict__ cv = col.data();
+    double* __restrict__ nv = nxt.data();
+    const double* __restrict__ xi = x + n0;
+    int c = c0;
+    if (c == 0) {
+      nv[0] = (cv[0] - diag[j - 1]) / (xi[0] - xi[-j]);
+      c = 1;
     }
-    double ov = diag[0];
-    diag[0] = nv;
-    for (int k = 1; k <= i; ++k) {
-      const double next_ov = k < i ? diag[k] : 0.0;
-      nv = (nv - ov) / (x[i] - x[i - k]);
-      ov = next_ov;
-      if (k < i)
-        diag[k] = nv;
-      else
-        diag.push_back(nv);
-    }
-    d.push_back(nv);
+    for (; c < C; ++c) nv[c] = (cv[c] - cv[c - 1]) / (xi[c] - xi[c - j]);
+    col.swap(nxt);
+    if (j >= n0) d[j] = col[j - n0];
+    ndiag[j] = col[C - 1];
   }
+  diag.swap(ndiag);
 }
 
 }  // namespace phix
