@@ -160,12 +160,13 @@ typedef struct {
                           individual phi_j actions; 1 interpolates exp of the augmented
                           matrix of the Theorem of Sec. 2.1 (Appendix A), float64        */
   int chain;           /* Leja Newton pass with the single-step kernel:
-                          PHIX_CHAIN_AUTO (default) and PHIX_CHAIN_PERSISTENT run the
-                          whole pass in ONE cooperative launch (every block resident,
-                          one grid-wide barrier per iteration, the stop test taken by
-                          every block on the same totals; a barrier wait that exceeds
-                          2 s ends the pass with PHIX_ETIMEOUT); PHIX_CHAIN_GRAPH runs
-                          one launch per iteration inside a conditional CUDA graph.
+                          PHIX_CHAIN_PERSISTENT runs the whole pass in ONE cooperative
+                          launch (every block resident, one grid-wide barrier per
+                          iteration, the stop test taken by every block on the same
+                          totals; a barrier wait that exceeds 2 s ends the pass with
+                          PHIX_ETIMEOUT); PHIX_CHAIN_AUTO (default) and
+                          PHIX_CHAIN_GRAPH run one launch per iteration inside a
+                          conditional CUDA graph (measured faster on GB300).
                           The TMA-staged kernel always runs one launch per iteration. */
 } phix_opts;
 

@@ -102,8 +102,11 @@ __global__ void __launch_bounds__(THREADS, 2) k_iter(IterDev a) {
 #pragma unroll
   for (int j = 0; j <= KMAX; ++j) acc[j] = acc_zero<Acc>();
 
-  const T* __restrict__ yin = static_cast<const T*>(a.y[(m - 1) & 1]);
-  T* __restrict__ yout = static_cast<T*>(const_cast<void*>(a.y[m & 1]));
+  // (selects, not a runtime index into the argument block, which would copy
+  // the block to local memory)
+  const bool odd = m & 1;
+  const T* __restrict__ yin = static_cast<const T*>(odd ? a.y[0] : a.y[1]);
+  T* __restrict__ yout = static_cast<T*>(const_cast<void*>(odd ? a.y[1] : a.y[0]));
   const S* __restrict__ st = static_cast<const S*>(a.st);
   const int nx = a.nx, ny = a.ny;
   const size_t plane = (size_t)nx * ny;

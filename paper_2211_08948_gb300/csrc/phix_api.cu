@@ -623,7 +623,7 @@ void leja_pass(phix_ctx* ctx, const OpState& os, int prec, const double* v, int 
   if (cs.tma) {
     cs.grid = tma_grid(cs, ctx->nsm);
   } else {
-    if (o.chain != PHIX_CHAIN_GRAPH) {
+    if (o.chain == PHIX_CHAIN_PERSISTENT) {
       // the whole pass in one cooperative launch: every block resident, its
       // partials double-buffered (2 x grid x (KMAX + 1) doubles)
       const int g = chain_grid(cs, ctx->nsm);
