@@ -52,8 +52,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--clock-ms", type=int, default=100, help="nvidia-smi sampling period (0 = off)")
     ap.add_argument("--method", default="leja", choices=["leja", "kiops"])
-    ap.add_argument("--kernel", default="auto", choices=["auto", "single", "tma"],
-                    help="Newton-step kernel of the Leja path (auto: TMA-staged once an iteration exceeds L2)")
+    ap.add_argument("--kernel", default="auto", choices=["auto", "single", "tma", "fused2"],
+                    help="Newton-step kernel of the Leja path (auto: TMA-staged once an iteration exceeds L2; "
+                         "fused2: two iterations per launch)")
     ap.add_argument("--chain", default="auto", choices=["auto", "persistent", "graph"],
                     help="Newton passes as one cooperative launch (auto, persistent) or one launch per "
                          "iteration in a conditional graph")
@@ -190,7 +191,7 @@ class GrayScottRun:
         ph = self.phix
         return ph.phix_opts_default(prec=getattr(ph, "PHIX_" + prec), profile=profile,
                                     kernel={"auto": ph.PHIX_KERNEL_AUTO, "single": ph.PHIX_KERNEL_SINGLE,
-                                            "tma": ph.PHIX_KERNEL_TMA}[kernel],
+                                            "tma": ph.PHIX_KERNEL_TMA, "fused2": ph.PHIX_KERNEL_FUSED2}[kernel],
                                     chain={"auto": ph.PHIX_CHAIN_AUTO, "persistent": ph.PHIX_CHAIN_PERSISTENT,
                                            "graph": ph.PHIX_CHAIN_GRAPH}[self.chain])
 

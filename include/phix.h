@@ -144,10 +144,16 @@ typedef struct {
                           the host polls the chain) (default 0)                         */
   int kernel;          /* Leja Newton-step kernel: PHIX_KERNEL_AUTO (default) takes the
                           TMA-staged kernel when one iteration's operands exceed the L2
-                          cache and the single-step kernel otherwise; PHIX_KERNEL_SINGLE
-                          and PHIX_KERNEL_TMA force one (TMA needs rows of a multiple of
-                          16 bytes, i.e. nx even, nx % 4 == 0 for 4-byte state, and
-                          falls back to the single-step kernel otherwise)             */
+                          cache and the single-step kernel otherwise; PHIX_KERNEL_SINGLE,
+                          PHIX_KERNEL_TMA and PHIX_KERNEL_FUSED2 force one (TMA needs
+                          rows of a multiple of 16 bytes, i.e. nx even, nx % 4 == 0 for
+                          4-byte state; FUSED2 nx % 64 == 0 and ny % 16 == 0; each falls
+                          back to the single-step kernel otherwise).  The two-iteration
+                          kernel computes iterations m and m + 1 in one launch from y_{m-1}
+                          staged with a two-point ring, storing y_{m+1} and p_m: half the
+                          memory traffic per iteration, the same results bit for bit as
+                          one iteration per launch for the same stop iteration (on
+                          GB300 no faster: the double-float arithmetic binds).          */
   int kiops_fused;     /* KIOPS: 1 (default) runs each Arnoldi step as one pass (the
                           orthogonalisation of step j staged in shared memory and pass 1
                           of step j + 1 read from it) when nx % 64 == 0 and ny % 8 == 0;
@@ -173,7 +179,7 @@ typedef struct {
 typedef enum { PHIX_CHAIN_AUTO = 0, PHIX_CHAIN_PERSISTENT = 1, PHIX_CHAIN_GRAPH = 2 } phix_chain;
 typedef enum { PHIX_JV_ANALYTIC = 0, PHIX_JV_FD = 1 } phix_jv;
 
-typedef enum { PHIX_KERNEL_AUTO = 0, PHIX_KERNEL_SINGLE = 1, PHIX_KERNEL_TMA = 2 } phix_kernel;
+typedef enum { PHIX_KERNEL_AUTO = 0, PHIX_KERNEL_SINGLE = 1, PHIX_KERNEL_TMA = 2, PHIX_KERNEL_FUSED2 = 3 } phix_kernel;
 
 /* Per-call statistics (host struct, filled on return).                    */
 typedef struct {

@@ -18,7 +18,7 @@ LIB = os.path.join(HERE, "libphix.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
          "-I" + INCLUDE, "-I" + CSRC]
-SOURCES = ["leja_kernels.cu", "leja_tma.cu", "kiops_kernels.cu", "batched_kernels.cu", "mlp_kernels.cu", "stage_kernels.cu", "phix_api.cu", "host_math.cpp", "phix_noalloc.cu", "block_kernels.cu", "general_kernels.cu"]
+SOURCES = ["leja_kernels.cu", "leja_tma.cu", "kiops_kernels.cu", "batched_kernels.cu", "mlp_kernels.cu", "stage_kernels.cu", "phix_api.cu", "host_math.cpp", "phix_noalloc.cu", "block_kernels.cu", "general_kernels.cu", "leja_fused.cu"]
 
 
 def _nvcc():

@@ -451,22 +451,32 @@ __global__ void __launch_bounds__(THREADS)
 }
 
 template <int P>
-__global__ void __launch_bounds__(THREADS) k_finalize(size_t n, int K, PtrPack pk, const LejaCtl* ctl) {
+__global__ void __launch_bounds__(THREADS) k_finalize(size_t n, int K, PtrPack pk, const LejaCtl* ctl, FusedOut fo) {
   using T = typename Tr<P>::T;
+  using C = typename Tr<P>::C;
   const double s = __ldcg(&ctl->sigma);
+  // a two-iteration chain that stopped at an even m >= 2: p_m = p_{m-1} + d_k[m] y_m
+  const int it = __ldcg(&ctl->iters);
+  const bool def = fo.ptab != nullptr && it >= 2 && !(it & 1);
+  const T* yd = def ? static_cast<const T*>(((it >> 1) & 1) ? fo.y[1] : fo.y[0]) : nullptr;
+  const unsigned char* tab = static_cast<const unsigned char*>(fo.ptab);
   const size_t stride = (size_t)gridDim.x * THREADS;
   for (int k = 0; k < K; ++k) {
     const T* p = static_cast<const T*>(pk.p[k]);
     double* o = pk.o[k];
+    C dk{};
+    if (def) {
+      const int M = pp_of(tab)->M;
+      dk = coef<C>(dk_d_of(tab, M)[k * M + it], dk_f_of(tab, M)[k * M + it]);
+    }
     for (size_t i = (size_t)blockIdx.x * THREADS + threadIdx.y * 32 + threadIdx.x; i < n; i += stride) {
-      T x = p[i];
+      C x = cv(p[i]);
+      if (def) x = mad(dk, cv(yd[i]), x);
       double d;
-      if constexpr (P == P_FP64) {
-        d = x;
-      } else if constexpr (P == P_FP32) {
+      if constexpr (P == P_FP64 || P == P_FP32) {
         d = (double)x;
       } else {
-        d = (double)x.x + (double)x.y;
+        d = (double)x.hi + (double)x.lo;
       }
       o[i] = s * d;
     }
@@ -679,6 +689,7 @@ static void* kfn(const ChainSpec& s, int V) {
 cudaError_t iter_node_params(const ChainSpec& s, cudaKernelNodeParams* np, void* arg_storage,
                              size_t arg_bytes) {
   if (s.tma) return tma_node_params(s, np, arg_storage, arg_bytes);
+  if (s.fused2) return fused2_node_params(s, np, arg_storage, arg_bytes);
   if (arg_bytes < sizeof(IterDev)) return cudaErrorInvalidValue;
   const int V = (s.nx % 2 == 0) ? 2 : 1;
   IterDev a = make_dev(s, V);
@@ -698,6 +709,13 @@ cudaError_t iter_node_params(const ChainSpec& s, cudaKernelNodeParams* np, void*
 }
 
 cudaError_t launch_iter(const ChainSpec& s, cudaStream_t st) {
+  if (s.fused2 || s.tma) {
+    alignas(64) unsigned char argbuf[2048];
+    cudaKernelNodeParams np;
+    const cudaError_t e = iter_node_params(s, &np, argbuf, sizeof argbuf);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchKernel(np.func, np.gridDim, np.blockDim, np.kernelParams, np.sharedMemBytes, st);
+  }
   const int V = (s.nx % 2 == 0) ? 2 : 1;
   IterDev a = make_dev(s, V);
   void* fn = kfn(s, V);
@@ -731,6 +749,7 @@ cudaError_t launch_chain(const ChainSpec& s, cudaStream_t st) {
 }
 
 int iter_tiles(const ChainSpec& s) {
+  if (s.fused2) return fused2_tiles(s);
   const int V = (s.nx % 2 == 0) ? 2 : 1;
   return make_dev(s, V).ntiles;
 }
@@ -781,22 +800,23 @@ cudaError_t launch_scale(const double* v, size_t n, LejaCtl* ctl, double* partia
 }
 
 cudaError_t launch_finalize(int prec, size_t n, int K, void* const* p, double* const* out,
-                            const LejaCtl* ctl, int grid, cudaStream_t s) {
+                            const LejaCtl* ctl, int grid, cudaStream_t s, const FusedOut* fo) {
   PtrPack pk{};
   for (int k = 0; k < K && k < KMAX; ++k) {
     pk.p[k] = p[k];
     pk.o[k] = out[k];
   }
+  const FusedOut f = fo ? *fo : FusedOut{};
   switch (prec) {
     case P_FP64:
-      k_finalize<P_FP64><<<grid, dim3(32, TILE_Y), 0, s>>>(n, K, pk, ctl);
+      k_finalize<P_FP64><<<grid, dim3(32, TILE_Y), 0, s>>>(n, K, pk, ctl, f);
       break;
     case P_DF64:
     case P_FP32JV:
-      k_finalize<P_DF64><<<grid, dim3(32, TILE_Y), 0, s>>>(n, K, pk, ctl);
+      k_finalize<P_DF64><<<grid, dim3(32, TILE_Y), 0, s>>>(n, K, pk, ctl, f);
       break;
     case P_FP32:
-      k_finalize<P_FP32><<<grid, dim3(32, TILE_Y), 0, s>>>(n, K, pk, ctl);
+      k_finalize<P_FP32><<<grid, dim3(32, TILE_Y), 0, s>>>(n, K, pk, ctl, f);
       break;
     default:
       return cudaErrorInvalidValue;

@@ -67,6 +67,7 @@ struct phix_ctx {
     int m_table;          // last iteration the pass's table covers
     int m_limit;          // the caller's m_max
     bool persistent;      // one cooperative launch ran the whole chain
+    bool fused2;          // two iterations per launch
   };
   std::vector<Pending> pend;     // queued passes since the last flush
   int nslot = 0;                 // slots in use
@@ -260,7 +261,8 @@ void flush(phix_ctx* ctx) {
     // the WHILE loop ran until the body holding iteration `iters` (one body
     // when the chain stopped before its first iteration); a persistent chain
     // is one launch
-    ctx->launches += q.persistent ? 1 : (long)GRAPH_ITERS * std::max(1, (c.iters + GRAPH_ITERS - 1) / GRAPH_ITERS);
+    const int work_launches = q.fused2 ? (c.iters + 1) / 2 : c.iters;
+    ctx->launches += q.persistent ? 1 : (long)GRAPH_ITERS * std::max(1, (work_launches + GRAPH_ITERS - 1) / GRAPH_ITERS);
     if (!q.stats) continue;
     const int status = c.done ? c.status : PHIX_ENOTCONV;
     if (status == PHIX_ENOTCONV && c.iters == q.m_table && q.m_table < q.m_limit) {
@@ -392,7 +394,8 @@ void queue_chain(phix_ctx* ctx, int s, const ChainSpec& spec, bool profile, bool
       CK(cudaStreamSynchronize(ctx->stream));
       if (c.done) break;
     }
-    ctx->launches -= (long)GRAPH_ITERS * std::max(1, (c.iters + GRAPH_ITERS - 1) / GRAPH_ITERS);  // counted at the flush
+    const int wl = key.fused2 ? (c.iters + 1) / 2 : c.iters;
+    ctx->launches -= (long)GRAPH_ITERS * std::max(1, (wl + GRAPH_ITERS - 1) / GRAPH_ITERS);  // counted at the flush
   } else {
     CK(cudaGraphLaunch(chain_graph(ctx, key), ctx->stream));  // its kernel launches are counted at the flush
   }
@@ -610,18 +613,29 @@ void leja_pass(phix_ctx* ctx, const OpState& os, int prec, const double* v, int 
   cs.partials = ctx->partials;
   cs.ptab = ptab;
   cs.K = K;
+  const double st_b = os.d.kind == PHIX_OP_GRAYSCOTT ? 2.0 * os.plane * eb
+                     : os.d.kind == PHIX_OP_BURGERS ? 1.0 * os.plane * eb : 0.0;
   {
     // TMA staging pays once an iteration's operands no longer stay in L2
-    // (read y, write y', read and write each p_k, read the state)
-    const double st_b = os.d.kind == PHIX_OP_GRAYSCOTT ? 2.0 * os.plane * eb
-                       : os.d.kind == PHIX_OP_BURGERS ? 1.0 * os.plane * eb : 0.0;
+    // (read y, write y', read and write each p_k, read the state).  Two
+    // iterations per launch on request only: measured on GB300 it is no faster
+    // (1024^2 Gray-Scott double-float 21.5-22.4 us per iteration against 18.6-18.7
+    // single-step; 2048^2 69.9-72.2 against 73.0-73.3 TMA-staged; Burgers 2048^2
+    // float64 179 against 163, float32 26.2 against 24.5)
     const double work = (double)os.N * eb * (2.0 + 2.0 * K) + st_b;
+    cs.fused2 = o.kernel == PHIX_KERNEL_FUSED2 && o.chain != PHIX_CHAIN_PERSISTENT && fused2_eligible(cs) ? 1 : 0;
     const bool want = o.kernel == PHIX_KERNEL_TMA || (o.kernel == PHIX_KERNEL_AUTO && work > ctx->l2_bytes);
-    cs.tma = want && tma_eligible(cs) ? 1 : 0;
+    cs.tma = !cs.fused2 && want && tma_eligible(cs) ? 1 : 0;
   }
   bool persistent = false;
   if (cs.tma) {
     cs.grid = tma_grid(cs, ctx->nsm);
+  } else if (cs.fused2) {
+    // the partials hold two halves of grid x (KMAX + 1)
+    const int gmax = std::min(ctx->grid_iter / 2, ctx->nsm * std::min(8, fused2_blocks_per_sm(cs)));
+    const int ntiles = fused2_tiles(cs);
+    const int per = (ntiles + gmax - 1) / gmax;  // tiles per block, balanced
+    cs.grid = (ntiles + per - 1) / per;
   } else {
     if (o.chain == PHIX_CHAIN_PERSISTENT) {
       // the whole pass in one cooperative launch: every block resident, its
@@ -646,7 +660,11 @@ void leja_pass(phix_ctx* ctx, const OpState& os, int prec, const double* v, int 
     queue_chain(ctx, s, cs, profile, o.profile == 2, m_max);
   }
   stats.tma_passes += cs.tma;
-  KL(launch_finalize(prec, os.N, K, p, out, ctl, ctx->grid_stream, ctx->stream));
+  FusedOut fo{};
+  fo.y[0] = y[0];
+  fo.y[1] = y[1];
+  fo.ptab = ptab;
+  KL(launch_finalize(prec, os.N, K, p, out, ctl, ctx->grid_stream, ctx->stream, cs.fused2 ? &fo : nullptr));
   phix_ctx::Pending q{};
   q.slot = s;
   q.stats = &stats;
@@ -654,13 +672,15 @@ void leja_pass(phix_ctx* ctx, const OpState& os, int prec, const double* v, int 
   q.m_table = m_max;
   q.m_limit = o.m_max;
   q.persistent = persistent;
+  q.fused2 = cs.fused2 != 0;
   if (profile) {
-    // algorithmic bytes of one iteration launch: read y, write the new
-    // iterate, read and write each p_k, read the state planes
+    // algorithmic bytes of one iteration: read y, write the new iterate, read
+    // and write each p_k, read the state planes; a two-iteration launch moves
+    // that once for two iterations
     const size_t sb = (prec == P_FP64 || prec == P_DF64) ? 8 : 4;
     const double st_bytes = os.d.kind == PHIX_OP_GRAYSCOTT ? 2.0 * os.plane * sb
                            : os.d.kind == PHIX_OP_BURGERS ? 1.0 * os.plane * sb : 0.0;
-    q.bytes_per_launch = (double)os.N * eb * (2.0 + 2.0 * K) + st_bytes;
+    q.bytes_per_launch = ((double)os.N * eb * (2.0 + 2.0 * K) + st_bytes) / (cs.fused2 ? 2.0 : 1.0);
   }
   ctx->pend.push_back(q);
 }
@@ -1155,7 +1175,7 @@ phix_opts resolve_opts(phix_ctx* ctx, const phix_opts* in) {
   if (o.m_min < 0) fail(ctx, PHIX_EINVAL, "m_min must be >= 0");
   if (!(o.safety > 0)) fail(ctx, PHIX_EINVAL, "safety must be > 0");
   if (o.power_max_it < 1 || o.power_max_it > 4000) fail(ctx, PHIX_EINVAL, "power_max_it must be in 1..4000");
-  if (o.kernel < PHIX_KERNEL_AUTO || o.kernel > PHIX_KERNEL_TMA) fail(ctx, PHIX_EINVAL, "unknown kernel %d", o.kernel);
+  if (o.kernel < PHIX_KERNEL_AUTO || o.kernel > PHIX_KERNEL_FUSED2) fail(ctx, PHIX_EINVAL, "unknown kernel %d", o.kernel);
   if (o.profile < 0 || o.profile > 2) fail(ctx, PHIX_EINVAL, "profile must be 0, 1 or 2");
   if (o.kiops_m_max < 2 || o.kiops_m_max > 128) fail(ctx, PHIX_EINVAL, "kiops_m_max must be in 2..128");
   if (o.kiops_fused != 0 && o.kiops_fused != 1) fail(ctx, PHIX_EINVAL, "kiops_fused must be 0 or 1");

@@ -83,6 +83,7 @@ struct ChainSpec {
   int grid;           // blocks (<= partials capacity)
   int K;              // MODE_NEWTON: accumulators
   int tma;            // MODE_NEWTON: 1 = the TMA-staged kernel (leja_tma.cu)
+  int fused2;         // MODE_NEWTON: 1 = two iterations per launch (leja_fused.cu)
   int use_cond;       // launched as the body of a conditional WHILE graph node:
   unsigned long long cond;  // its handle; the kernel clears it once the chain stopped
 };
@@ -100,6 +101,15 @@ int tma_grid(const ChainSpec& s, int nsm);
 cudaError_t tma_node_params(const ChainSpec& s, cudaKernelNodeParams* np, void* arg_storage, size_t arg_bytes);
 size_t tma_arg_bytes();
 int iter_tiles(const ChainSpec& s);  // tiles of one launch (work units of the grid loop)
+// Two Newton iterations per launch (leja_fused.cu): grids whose sides are
+// multiples of 64 x 16; the launch starting at iteration m stores y_{m+1}
+// and p_m and leaves d_k[m+1] y_{m+1} to the next launch or to the output
+// conversion (launch_finalize with a FusedOut); partials: two halves of
+// grid * (KMAX + 1).
+bool fused2_eligible(const ChainSpec& s);
+int fused2_tiles(const ChainSpec& s);
+int fused2_blocks_per_sm(const ChainSpec& s);
+cudaError_t fused2_node_params(const ChainSpec& s, cudaKernelNodeParams* np, void* arg_storage, size_t arg_bytes);
 // Persistent chain (MODE_NEWTON, single-step kernel): every iteration of the
 // pass in one cooperative launch of chain_grid() blocks (all resident), one
 // grid barrier per iteration; s.partials must hold 2 * grid * (KMAX + 1).
@@ -127,9 +137,17 @@ struct PtrPack {
   const void* p[KMAX];
   double* o[KMAX];
 };
-// out_k = sigma * p_k (float64); p and out are HOST arrays of K device pointers
+// A chain of two-iteration launches that stopped at an even iteration m >= 2
+// left d_k[m] y_m out of the accumulators: y_m is in y[(m/2) & 1], d_k[m] in
+// the pass's parameter block.
+struct FusedOut {
+  const void* y[2];
+  const void* ptab;
+};
+// out_k = sigma * p_k (float64); p and out are HOST arrays of K device
+// pointers; fo (NULL: none) adds the term a two-iteration chain deferred
 cudaError_t launch_finalize(int prec, size_t n, int K, void* const* p, double* const* out,
-                            const LejaCtl* ctl, int grid, cudaStream_t s);
+                            const LejaCtl* ctl, int grid, cudaStream_t s, const FusedOut* fo = nullptr);
 
 // power iteration start: y0[i] = splitmix64_uniform(seed, i) in the precision's format,
 // ctl->alpha = 1/||y0||, ctl->m = 1.

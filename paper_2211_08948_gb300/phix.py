@@ -22,7 +22,7 @@ PHIX_MLP_NPARAM = 5443
 PHIX_MLP_NFEAT = 16
 PHIX_LEJA, PHIX_KIOPS, PHIX_LEKRY = 0, 1, 2
 PHIX_EXPRB43, PHIX_EPIRK4S3, PHIX_EPIRK4S3A, PHIX_EXPRB53S3, PHIX_EPIRK5P1 = range(5)
-PHIX_KERNEL_AUTO, PHIX_KERNEL_SINGLE, PHIX_KERNEL_TMA = 0, 1, 2
+PHIX_KERNEL_AUTO, PHIX_KERNEL_SINGLE, PHIX_KERNEL_TMA, PHIX_KERNEL_FUSED2 = 0, 1, 2, 3
 PHIX_CHAIN_AUTO, PHIX_CHAIN_PERSISTENT, PHIX_CHAIN_GRAPH = 0, 1, 2
 PHIX_CONTROL_TRADITIONAL, PHIX_CONTROL_COST = 0, 1
 PHIX_FP64, PHIX_DF64, PHIX_FP32_JV, PHIX_FP32 = 0, 1, 2, 3
