@@ -67,6 +67,12 @@ def parse():
                     help="grayscott: EXPRB43 steps (headline, with every other workload as a leg); the others "
                          "run one leg on its own")
     ap.add_argument("--no-legs", action="store_true", help="headline line only (no other workloads)")
+    ap.add_argument("--full", action="store_true",
+                    help="--workload learned at its stated scale: 200k labelled states of sides 128..1024 "
+                         "(drawn on the GPU), 10k phi_1 actions on held-out states")
+    ap.add_argument("--labels", type=int, default=200000, help="--full: labelled states")
+    ap.add_argument("--actions", type=int, default=10000, help="--full: timed phi_1 actions per interval")
+    ap.add_argument("--ckpt", default=None, help="--full: directory of the label checkpoint shards (resumable)")
     return ap.parse_args()
 
 
@@ -589,6 +595,103 @@ def leg_learned(torch, phix, synth, ctx, stream, args, nlabel=1024, nact=200):
             "train_s": t2 - t1, "train_loss": loss}
 
 
+def leg_learned_full(torch, phix, synth, ctx, stream, args):
+    """The learned spectral interval at its stated scale: args.labels
+    Gray-Scott / Burgers states of sides log-uniform 128..1024 drawn on the
+    GPU, each labelled by the library's power iteration and label targets
+    (checkpointed in shards under args.ckpt: a stopped run resumes), the MLP
+    trained on the GPU, then args.actions phi_1 actions (tol 1e-9) on
+    held-out states with the learned interval and with power iteration; every
+    action timed by CUDA events on the stream, states drawn outside the timed
+    calls; errors against the float64 power-iteration path on every 20th
+    state.  States are visited in order of size (the chain graphs are cached
+    per grid shape); the first action of each size runs once untimed in both
+    modes."""
+    from paper_2211_08948_gb300 import learned
+    nl, na = args.labels, args.actions
+    specs = synth.learned_state_specs(nl + na, seed=5, n_lo=128, n_hi=1024)
+    lab = sorted(range(nl), key=lambda i: (specs[i]["n"], i))
+    ev = sorted(range(nl, nl + na), key=lambda i: (specs[i]["n"], i))
+
+    def problem(j):
+        sp = specs[lab[j]]
+        st = synth.learned_state_torch(sp, torch)
+        kind = phix.PHIX_OP_GRAYSCOTT if sp["kind"] == 1 else phix.PHIX_OP_BURGERS
+        return phix.make_jop(kind, sp["n"], sp["n"], sp["params"], st), sp["h"], st
+
+    t0 = time.perf_counter()
+    X, T, mv_labels = learned.make_dataset(ctx, problem, torch, n=nl, ckpt_dir=args.ckpt,
+                                           tag="learned_state_specs(seed=5, 128..1024)[:%d] by side" % nl)
+    t1 = time.perf_counter()
+    perm = np.random.default_rng(0).permutation(nl)  # batches mixing sizes and kinds
+    params, loss = learned.train(ctx, X[perm], T[perm], torch)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    tol = 1e-9
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    modes = ("learned", "power")
+    tot, mv, fb, err = ({m: 0 for m in modes} for _ in range(4))
+    iters, subs = {m: 0 for m in modes}, {m: 0 for m in modes}
+    nerr, last_n, sizes, ratio = 0, None, [], []
+
+    def act(mode, op, h, v, out, rho_im):
+        o = phix.phix_opts_default(rho_im=rho_im, prec=phix.PHIX_FP64 if mode == "fp64" else phix.PHIX_DF64)
+        if mode == "learned":
+            return phix.phix_phi_action_learned(ctx, op, h, v, [1], [1.0], [out], tol, params, o)
+        return phix.phix_phi_action(ctx, op, h, v, [1], [1.0], [out], tol, phix.PHIX_LEJA, o)
+
+    for a, i in enumerate(ev):
+        sp = specs[i]
+        st = synth.learned_state_torch(sp, torch)
+        kind = phix.PHIX_OP_GRAYSCOTT if sp["kind"] == 1 else phix.PHIX_OP_BURGERS
+        op = phix.make_jop(kind, sp["n"], sp["n"], sp["params"], st)
+        gen = torch.Generator(device="cuda").manual_seed(i)
+        v = torch.randn(st.numel(), dtype=torch.float64, device="cuda", generator=gen)
+        rho_im = 0.0 if kind == phix.PHIX_OP_GRAYSCOTT else float(st.abs().max()) * 2 * sp["n"]
+        outs = {m: torch.empty_like(v) for m in modes}
+        if sp["n"] != last_n:  # graphs and tables of a new size, untimed
+            for m in modes:
+                act(m, op, sp["h"], v, outs[m], rho_im)
+            last_n = sp["n"]
+        sizes.append(sp["n"])
+        rho = {}
+        for m in modes:
+            torch.cuda.synchronize()
+            e0.record(stream)
+            s = act(m, op, sp["h"], v, outs[m], rho_im)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot[m] += e0.elapsed_time(e1)
+            mv[m] += s.power_mv
+            fb[m] += s.rejections
+            iters[m] += s.iters
+            subs[m] += s.substeps
+            rho[m] = s.rho
+        ratio.append(rho["learned"] / rho["power"])
+        if a % 20 == 0:
+            ref = torch.empty_like(v)
+            act("fp64", op, sp["h"], v, ref, rho_im)
+            nr = float(torch.linalg.norm(ref))
+            for m in modes:
+                err[m] = max(err[m], float(torch.linalg.norm(outs[m] - ref)) / nr)
+            nerr += 1
+    res = {m: {"value": na / (tot[m] * 1e-3), "unit": UNIT, "ms": tot[m], "power_matvecs": mv[m],
+               "fallbacks": fb[m]} for m in modes}
+    return {"workload": "learned spectral interval at scale: %d labelled Gray-Scott/Burgers states (sides "
+                        "128..1024, drawn on the GPU), phi_1(hJ)v on %d held-out states, tol 1e-9, double-float"
+                        % (nl, na),
+            "by_interval": res, "speedup_vs_power": res["learned"]["value"] / res["power"]["value"],
+            "matvecs_saved": mv["power"] - mv["learned"],
+            "rel_err_vs_fp64_power_path": {"max": err, "states": nerr},
+            "label_power_matvecs": mv_labels, "label_s": t1 - t0, "train_s": t2 - t1, "train_loss": loss,
+            "eval_sides": {"min": min(sizes), "median": int(np.median(sizes)), "max": max(sizes)},
+            "newton_iters_per_action": {m: iters[m] / na for m in modes},
+            "substeps_per_action": {m: subs[m] / na for m in modes},
+            "rho_learned_over_power": {q: float(np.quantile(ratio, x)) for q, x in
+                                       (("min", 0.0), ("p01", 0.01), ("median", 0.5), ("p99", 0.99), ("max", 1.0))}}
+
+
 def run_leg(args, world, rank, local):
     """One leg on its own (--workload), printed as its own JSON object."""
     import torch
@@ -604,6 +707,8 @@ def run_leg(args, world, rank, local):
         out = leg_batched(torch, phix, synth, ctx, stream, args)
     elif args.workload == "advdiff":
         out = leg_advdiff(torch, phix, synth, ctx, stream, args)
+    elif args.full:
+        out = leg_learned_full(torch, phix, synth, ctx, stream, args)
     else:
         out = leg_learned(torch, phix, synth, ctx, stream, args)
     phix.phix_destroy(ctx)

@@ -8,6 +8,9 @@
 // under-estimated spectral radius is the dangerous side), batch mean.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+#include <cmath>
+
 #include "iter_common.cuh"
 
 namespace phix {
@@ -46,6 +49,7 @@ __device__ void load_net(const float* __restrict__ p, Net& n, int tid, int nthr)
 }
 
 __device__ __forceinline__ float wv(const Net& n, int i) { return __bfloat162float(n.w[i]); }
+__device__ __forceinline__ float bf16r(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 
 // one sample: x[16] -> y[3]; activations kept for the backward pass
 __device__ void mlp_sample(const Net& n, const float* x, float* z1, float* a1, float* z2, float* a2, float* y) {
@@ -79,6 +83,36 @@ __global__ void __launch_bounds__(128) k_mlp_fwd(const float* __restrict__ p, co
   for (int i = 0; i < NI; ++i) x[i] = X[(size_t)s * NI + i];
   mlp_sample(net, x, z1, a1, z2, a2, y);
   for (int j = 0; j < NO; ++j) Y[(size_t)s * NO + j] = y[j];
+}
+
+// Inference of a few samples (the learned phi-action evaluates one): one CTA
+// of 64 threads per sample, thread j owning hidden unit j of each layer and
+// the activations in shared memory; weights read from global memory and
+// rounded to bfloat16 as they are used.  Every unit's sum is the same fmaf
+// chain as in mlp_sample (inputs in ascending order), so the outputs equal
+// k_mlp_fwd's bit for bit.
+__global__ void __launch_bounds__(64) k_mlp_fwd_unit(const float* __restrict__ p, const float* __restrict__ X,
+                                                     float* __restrict__ Y) {
+  __shared__ float x[NI], a1[H1], a2[H2];
+  const int j = threadIdx.x, s = blockIdx.x;
+  if (j < NI) x[j] = X[(size_t)s * NI + j];
+  __syncthreads();
+  float z = p[OB1 + j];
+#pragma unroll
+  for (int i = 0; i < NI; ++i) z = fmaf(bf16r(p[OW1 + j * NI + i]), x[i], z);
+  a1[j] = gelu(z);
+  __syncthreads();
+  z = p[OB2 + j];
+#pragma unroll 16
+  for (int i = 0; i < H1; ++i) z = fmaf(bf16r(p[OW2 + j * H1 + i]), a1[i], z);
+  a2[j] = gelu(z);
+  __syncthreads();
+  if (j < NO) {
+    z = p[OB3 + j];
+#pragma unroll 16
+    for (int i = 0; i < H2; ++i) z = fmaf(bf16r(p[OW3 + j * H2 + i]), a2[i], z);
+    Y[(size_t)s * NO + j] = z;
+  }
 }
 
 // Gradient of the batch-mean loss over samples [0, n) of (X, T): one CTA of
@@ -251,7 +285,7 @@ __global__ void k_adam(float* __restrict__ p, float* __restrict__ m, float* __re
   }
 }
 
-// ---- state features (grid reduction, float64) ----------------------------
+// ---- state features (grid reduction) --------------------------------------
 // partial slots: 0 max|s1| 1 max|s2| 2 sum|s1| 3 max g 4 sum g 5 max V^2 6 max 2UV
 //                7 max|div U| (Burgers)
 constexpr int NF = 8;
@@ -278,36 +312,55 @@ __device__ void feat_block_reduce(const double* a, double (*sr)[NF]) {
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(256) k_features(int kind, int nx, int ny, double p0, double p1, double p2,
-                                                  double p3, double h, const double* __restrict__ st,
-                                                  double* partials, unsigned int* counter, float* feats) {
+// the operator and step features, computed on the host in float64
+struct FConst {
+  float f[16];
+};
+
+__global__ void __launch_bounds__(256) k_features(int kind, int nx, int ny, float rho_diff, FConst fconst,
+                                                  const double* __restrict__ st, double* partials,
+                                                  unsigned int* counter, float* feats) {
   __shared__ double sr[8][NF];
   __shared__ bool last;
   const int tid = threadIdx.x;
   const size_t N = (size_t)nx * ny;
-  double a[NF];
-  for (int j = 0; j < NF; ++j) a[j] = 0.0;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + tid; i < N; i += (size_t)gridDim.x * blockDim.x) {
-    const int r = (int)(i / nx), c = (int)(i % nx);
-    const int cm = c == 0 ? nx - 1 : c - 1, cp = c == nx - 1 ? 0 : c + 1;
-    const int rm = r == 0 ? ny - 1 : r - 1, rp = r == ny - 1 ? 0 : r + 1;
-    const double s1 = st[i];
-    const double dx = st[(size_t)r * nx + cp] - st[(size_t)r * nx + cm];
-    const double dy = st[(size_t)rp * nx + c] - st[(size_t)rm * nx + c];
-    const double g = 0.5 * (fabs(dx) + fabs(dy));
-    a[0] = fmax(a[0], fabs(s1));
-    a[2] += fabs(s1);
-    a[3] = fmax(a[3], g);
-    a[4] += g;
-    if (kind == PHIX_OP_GRAYSCOTT) {
-      const double s2 = st[N + i];
-      a[1] = fmax(a[1], fabs(s2));
-      a[5] = fmax(a[5], s2 * s2);
-      a[6] = fmax(a[6], 2.0 * s1 * s2);
-    } else {
-      a[7] = fmax(a[7], fabs(0.5 * (dx * nx + dy * ny)));
+  // per point: the centred differences in float64 (differences of close
+  // values), then float32 (the features are float32; rounding is monotone,
+  // so the maximum of the rounded values is the rounded maximum); the sums
+  // of the two means in float32 per thread (a few points each), float64
+  // across threads and blocks
+  float mx[NF];
+  float sm2 = 0.f, sm4 = 0.f;
+  for (int j = 0; j < NF; ++j) mx[j] = 0.f;
+  for (int r = blockIdx.x; r < ny; r += gridDim.x) {
+    const size_t row = (size_t)r * nx;
+    const size_t rowm = (size_t)(r == 0 ? ny - 1 : r - 1) * nx, rowp = (size_t)(r == ny - 1 ? 0 : r + 1) * nx;
+    for (int c = tid; c < nx; c += blockDim.x) {
+      const int cm = c == 0 ? nx - 1 : c - 1, cp = c == nx - 1 ? 0 : c + 1;
+      const double s1 = st[row + c];
+      const double dx = st[row + cp] - st[row + cm];
+      const double dy = st[rowp + c] - st[rowm + c];
+      const float as1 = fabsf((float)s1);
+      const float g = 0.5f * (fabsf((float)dx) + fabsf((float)dy));
+      mx[0] = fmaxf(mx[0], as1);
+      sm2 += as1;
+      mx[3] = fmaxf(mx[3], g);
+      sm4 += g;
+      if (kind == PHIX_OP_GRAYSCOTT) {
+        const float s2 = (float)st[N + row + c];
+        const float s1f = (float)s1;
+        mx[1] = fmaxf(mx[1], fabsf(s2));
+        mx[5] = fmaxf(mx[5], s2 * s2);
+        mx[6] = fmaxf(mx[6], 2.f * s1f * s2);
+      } else {
+        mx[7] = fmaxf(mx[7], fabsf((float)(0.5 * (dx * nx + dy * ny))));
+      }
     }
   }
+  double a[NF];
+  for (int j = 0; j < NF; ++j) a[j] = mx[j];
+  a[2] = sm2;
+  a[4] = sm4;
   // block reduction: max slots by max, slots 2 and 4 by sum
   feat_block_reduce(a, sr);
   if (tid < NF) partials[(size_t)blockIdx.x * NF + tid] = sr[0][tid];
@@ -325,36 +378,42 @@ __global__ void __launch_bounds__(256) k_features(int kind, int nx, int ny, doub
     }
   __syncthreads();
   feat_block_reduce(a, sr);
-  if (tid == 0) {
-    double t[NF];
-    for (int j = 0; j < NF; ++j) t[j] = sr[0][j];
-    const double Dmax = kind == PHIX_OP_GRAYSCOTT ? fmax(p0, p1) : p0;
-    const double rho_diff = 4.0 * Dmax * ((double)nx * nx + (double)ny * ny);
-    double f[16];
-    for (int j = 0; j < 16; ++j) f[j] = 0.0;
-    f[0] = kind == PHIX_OP_GRAYSCOTT ? 1.0 : 0.0;
-    f[1] = log((double)N) / 10.0;
-    f[2] = log(Dmax) / 10.0;
-    f[3] = log(h) / 10.0;
-    f[4] = log(h * rho_diff) / 5.0;
-    f[5] = t[0];
-    f[6] = t[1];
-    f[7] = t[2] / (double)N;
-    f[8] = t[3];
-    f[9] = t[4] / (double)N;
-    if (kind == PHIX_OP_GRAYSCOTT) {
-      f[10] = t[5];
-      f[11] = t[6];
-      f[13] = p2;
-      f[14] = p3;
-    } else {
-      f[10] = t[7] / rho_diff;
-      f[12] = t[0] * (nx + ny) / rho_diff;
+  if (tid < 16) {
+    // the operator and step features (host-computed) and the state's
+    float f = fconst.f[tid];
+    const double* t = sr[0];
+    switch (tid) {
+      case 5: f = (float)t[0]; break;
+      case 6: f = (float)t[1]; break;
+      case 7: f = (float)(t[2] / (double)N); break;
+      case 8: f = (float)t[3]; break;
+      case 9: f = (float)(t[4] / (double)N); break;
+      case 10: f = kind == PHIX_OP_GRAYSCOTT ? (float)t[5] : (float)t[7] / rho_diff; break;
+      case 11: f = kind == PHIX_OP_GRAYSCOTT ? (float)t[6] : 0.f; break;
+      case 12: f = kind == PHIX_OP_GRAYSCOTT ? 0.f : (float)t[0] * (float)(nx + ny) / rho_diff; break;
+      default: break;
     }
-    f[15] = 1.0;
-    for (int j = 0; j < 16; ++j) feats[j] = (float)f[j];
+    feats[tid] = f;
+  }
+  if (tid == 0) {
     *counter = 0;
     __threadfence();
+  }
+}
+
+// *out = max_i |x_i| (out zeroed by the caller): block maxima, then one
+// atomicMax per block on the bit patterns (non-negative doubles order as
+// their unsigned 64-bit patterns), independent of the block order.
+__global__ void __launch_bounds__(256) k_maxabs(const double* __restrict__ x, size_t n, unsigned long long* out) {
+  double m = 0.0;
+  for (size_t i = (size_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (size_t)gridDim.x * 256) m = fmax(m, fabs(x[i]));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+  __shared__ double sw[8];
+  if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < 8; ++w) m = fmax(m, sw[w]);
+    atomicMax(out, (unsigned long long)__double_as_longlong(m));
   }
 }
 
@@ -363,7 +422,10 @@ __global__ void __launch_bounds__(256) k_features(int kind, int nx, int ny, doub
 int mlp_nparam() { return NP; }
 
 cudaError_t launch_mlp_forward(const float* p, const float* X, int n, float* Y, cudaStream_t st) {
-  k_mlp_fwd<<<(n + 127) / 128, 128, 0, st>>>(p, X, n, Y);
+  if (n <= 256)
+    k_mlp_fwd_unit<<<n, H1, 0, st>>>(p, X, Y);
+  else
+    k_mlp_fwd<<<(n + 127) / 128, 128, 0, st>>>(p, X, n, Y);
   return cudaGetLastError();
 }
 
@@ -380,9 +442,29 @@ cudaError_t launch_adam(float* p, float* m, float* v, const float* g, int step, 
   return cudaGetLastError();
 }
 
+cudaError_t launch_maxabs(const double* x, size_t n, double* out, int grid, cudaStream_t st) {
+  k_maxabs<<<grid, 256, 0, st>>>(x, n, reinterpret_cast<unsigned long long*>(out));
+  return cudaGetLastError();
+}
+
 cudaError_t launch_features(int kind, int nx, int ny, const double* prm, double h, const double* state,
                             double* partials, unsigned int* counter, float* feats, int grid, cudaStream_t st) {
-  k_features<<<grid, 256, 0, st>>>(kind, nx, ny, prm[0], prm[1], prm[2], prm[3], h, state, partials, counter, feats);
+  // features that depend on the operator and the step only, computed here in
+  // float64 and passed in the kernel's argument block
+  FConst fc{};
+  const double Dmax = kind == PHIX_OP_GRAYSCOTT ? std::max(prm[0], prm[1]) : prm[0];
+  const double rho_diff = 4.0 * Dmax * ((double)nx * nx + (double)ny * ny);
+  fc.f[0] = kind == PHIX_OP_GRAYSCOTT ? 1.f : 0.f;
+  fc.f[1] = (float)(std::log((double)nx * ny) / 10.0);
+  fc.f[2] = (float)(std::log(Dmax) / 10.0);
+  fc.f[3] = (float)(std::log(h) / 10.0);
+  fc.f[4] = (float)(std::log(h * rho_diff) / 5.0);
+  if (kind == PHIX_OP_GRAYSCOTT) {
+    fc.f[13] = (float)prm[2];
+    fc.f[14] = (float)prm[3];
+  }
+  fc.f[15] = 1.f;
+  k_features<<<grid, 256, 0, st>>>(kind, nx, ny, (float)rho_diff, fc, state, partials, counter, feats);
   return cudaGetLastError();
 }
 

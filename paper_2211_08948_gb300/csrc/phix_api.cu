@@ -1527,6 +1527,36 @@ phix_status phix_features(phix_ctx* ctx, const phix_jop* op, double h, float* fe
   });
 }
 
+phix_status phix_learned_targets(phix_ctx* ctx, const phix_jop* op, double h, double rho, const phix_opts* opts,
+                                 float* t) {
+  return guarded(ctx, nullptr, [&](phix_stats&) -> phix_status {
+    check_op(ctx, op, true);
+    if (op->kind != PHIX_OP_GRAYSCOTT && op->kind != PHIX_OP_BURGERS)
+      fail(ctx, PHIX_EINVAL, "targets are defined for Gray-Scott and Burgers");
+    if (!t || !(h > 0) || !(rho > 0) || !std::isfinite(rho)) fail(ctx, PHIX_EINVAL, "bad targets arguments");
+    const phix_opts o = resolve_opts(ctx, opts);
+    const double Dmax = op->kind == PHIX_OP_GRAYSCOTT ? std::max(op->param[0], op->param[1]) : op->param[0];
+    const double rho_diff = 4.0 * Dmax * ((double)op->nx * op->nx + (double)op->ny * op->ny);
+    double rho_im = 0.0;
+    if (op->kind == PHIX_OP_BURGERS) {
+      // Bendixson bound of the skew part of J: max|U| (nx + ny)
+      CK(cudaMemsetAsync(ctx->scal, 0, sizeof(double), ctx->stream));
+      KL(launch_maxabs(op->state, (size_t)op->nx * op->ny, ctx->scal, ctx->grid_stream, ctx->stream));
+      CK(cudaMemcpyAsync(ctx->scal_h, ctx->scal, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      rho_im = ctx->scal_h[0] * (double)(op->nx + op->ny);
+    }
+    // the substep count of a phi_1 action of step h on the interval the Leja
+    // path takes from this estimate (the complex-spectrum half-width rule)
+    const double gamma = std::max(0.25 * o.safety * rho, 2.0 * rho_im);
+    const int s = substeps_for(h, 1.0, gamma, rho_im, o);
+    t[0] = (float)std::log(rho / rho_diff);
+    t[1] = (float)std::log1p(rho_im / rho_diff);
+    t[2] = (float)std::log((double)s);
+    return PHIX_OK;
+  });
+}
+
 phix_status phix_mlp_forward(phix_ctx* ctx, const float* params, const float* X, int n, float* Y) {
   return guarded(ctx, nullptr, [&](phix_stats&) -> phix_status {
     if (!params || !X || !Y || n < 1) fail(ctx, PHIX_EINVAL, "bad mlp_forward arguments");
@@ -1600,7 +1630,7 @@ phix_status phix_phi_action_learned(phix_ctx* ctx, const phix_jop* op, double h,
     const double rho_im = std::max(0.0, rho_diff * std::expm1((double)yh[1]));
     if (!std::isfinite(rho) || !(rho > 0)) fail(ctx, PHIX_ENAN, "network produced a non-finite interval");
     phix_opts ol = o;
-    ol.rho_re = o.safety * 1.05 * rho;
+    ol.rho_re = o.safety * rho;
     ol.rho_hi = 0.0;
     ol.rho_im = rho_im;
     Interval iv;

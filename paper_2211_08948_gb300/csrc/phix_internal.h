@@ -262,6 +262,8 @@ cudaError_t launch_mlp_forward(const float* p, const float* X, int n, float* Y, 
 cudaError_t launch_mlp_grad(const float* p, const float* X, const float* T, int n, float* G, float* loss,
                             cudaStream_t st);
 cudaError_t launch_adam(float* p, float* m, float* v, const float* g, int step, float lr, cudaStream_t st);
+// *out = max |x_i| (*out zeroed by the caller; device pointers)
+cudaError_t launch_maxabs(const double* x, size_t n, double* out, int grid, cudaStream_t st);
 cudaError_t launch_features(int kind, int nx, int ny, const double* prm, double h, const double* state,
                             double* partials, unsigned int* counter, float* feats, int grid, cudaStream_t st);
 

@@ -38,6 +38,7 @@ EXPORTS = [
     "phix_mlp_forward", "phix_mlp_grad", "phix_mlp_train", "phix_phi_action_learned", "phix_leja_points", "phix_divided_differences", "phix_phi_action_noalloc",
     "phix_step", "phix_step_host", "phix_block_newton", "phix_block_faces", "phix_block_start",
     "phix_leja_stop", "phix_opts_size", "phix_stats_size", "phix_integrate", "phix_batched_config",
+    "phix_learned_targets",
 ]
 
 
@@ -131,6 +132,8 @@ def load(path=None):
     lib.phix_rhs.argtypes = [P, ctypes.POINTER(phix_jop), P, P]
     F = ctypes.c_float
     lib.phix_features.argtypes = [P, ctypes.POINTER(phix_jop), D, P]
+    lib.phix_learned_targets.argtypes = [P, ctypes.POINTER(phix_jop), D, D, ctypes.POINTER(phix_opts),
+                                         ctypes.POINTER(F)]
     lib.phix_mlp_forward.argtypes = [P, P, P, I, P]
     lib.phix_mlp_grad.argtypes = [P, P, P, P, I, P, ctypes.POINTER(F)]
     lib.phix_mlp_train.argtypes = [P, P, P, P, ctypes.POINTER(I), P, P, I, I, I, F, ctypes.POINTER(F)]
@@ -321,6 +324,14 @@ def phix_phi_action_batched(ctx, problems, l, tol, opts=None, check=True):
 def phix_features(ctx, op, h, feats):
     """feats (float32[16]) <- features of op at op.state with step h."""
     _check(ctx, load().phix_features(ctx, ctypes.byref(op), h, _fptr(feats)))
+
+
+def phix_learned_targets(ctx, op, h, rho, opts=None):
+    """The network's three training targets for op at op.state (a list)."""
+    t = (ctypes.c_float * 3)()
+    _check(ctx, load().phix_learned_targets(ctx, ctypes.byref(op), h, rho,
+                                            ctypes.byref(opts) if opts is not None else None, t))
+    return list(t)
 
 
 def phix_mlp_forward(ctx, params, X, Y):

@@ -14,6 +14,12 @@ Workload recipes:
   smoothed by 3 Jacobi sweeps, h = 50 * dx^2/(4 nu)
 * batched advection-diffusion problems: side round(exp(U(ln 32, ln 512))),
   D ~ U(0.1,1), a ~ U(0,50)^2, h = U_log(10,200) * dx^2/(4D), v ~ N(0,1)
+* learned spectral interval: Gray-Scott and Burgers states alternately, side
+  log-uniform (even), diffusion log-uniform, h = U_log(10,100) x the
+  explicit step, Gray-Scott u=1, v=0 plus U(0, amp) on a random central
+  patch, Burgers amp (sin sin + 0.1 N(0,1)) smoothed by 3 Jacobi sweeps; at
+  the full scale (sides 128..1024, 200k states) drawn on the GPU by torch's
+  seeded generator (`learned_state_torch`), the same recipe
 
 Vectors are float64, C-contiguous, planar: species-major, then row (y),
 then column (x); grid nodes x_j = j/n on the periodic unit square.
@@ -159,3 +165,29 @@ def learned_state(spec):
     if spec["kind"] == 1:
         return grayscott_state(spec["n"], seed=spec["seed"], patch=spec["patch"], amp=spec["amp"])
     return spec["amp"] * burgers_state(spec["n"], seed=spec["seed"])
+
+
+def learned_state_torch(spec, torch, device="cuda"):
+    """The learned_state recipe drawn on the device with torch's generator
+    seeded by spec["seed"] (other values than learned_state's numpy draws,
+    the same distribution): float64, planar."""
+    n = spec["n"]
+    g = torch.Generator(device=device).manual_seed(spec["seed"])
+    if spec["kind"] == 1:
+        u = torch.ones((n, n), dtype=torch.float64, device=device)
+        v = torch.zeros((n, n), dtype=torch.float64, device=device)
+        pa = spec["patch"]
+        lo = n // 2 - pa // 2
+        if pa > 0:
+            u[lo:lo + pa, lo:lo + pa] += spec["amp"] * torch.rand((pa, pa), dtype=torch.float64, device=device,
+                                                                  generator=g)
+            v[lo:lo + pa, lo:lo + pa] += spec["amp"] * torch.rand((pa, pa), dtype=torch.float64, device=device,
+                                                                  generator=g)
+        return torch.cat([u.reshape(-1), v.reshape(-1)])
+    x = torch.arange(n, dtype=torch.float64, device=device) / n
+    Y, X = torch.meshgrid(x, x, indexing="ij")
+    u = torch.sin(2 * np.pi * X) * torch.sin(2 * np.pi * Y) + 0.1 * torch.randn((n, n), dtype=torch.float64,
+                                                                             device=device, generator=g)
+    for _ in range(3):
+        u = 0.25 * (torch.roll(u, 1, 0) + torch.roll(u, -1, 0) + torch.roll(u, 1, 1) + torch.roll(u, -1, 1))
+    return (spec["amp"] * u).reshape(-1).contiguous()

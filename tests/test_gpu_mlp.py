@@ -59,6 +59,20 @@ def test_features_vs_oracle(px):
         assert np.allclose(feats.cpu().numpy(), ref, rtol=1e-6, atol=1e-6), (spec["kind"], feats, ref)
 
 
+def test_learned_targets_vs_oracle(px):
+    """The library's label targets (interval and substep rule of its own Leja
+    path) against the oracle's labels, at the library's own power-iteration
+    estimate."""
+    phix, ctx = px
+    for spec in synth.learned_state_specs(12, seed=4):
+        s = synth.learned_state(spec)
+        op = _op(phix, spec, f64(s))
+        rho, _ = phix.phix_spectrum(ctx, op, phix.phix_opts_default())
+        t = phix.phix_learned_targets(ctx, op, spec["h"], rho)
+        ref = mlp.labels(spec["kind"], spec["n"], spec["n"], spec["params"], spec["h"], s, rho)
+        assert np.allclose(t, ref, rtol=1e-6, atol=1e-6), (spec, t, ref)
+
+
 def test_forward_and_grad_vs_oracle(px):
     phix, ctx = px
     rng = np.random.default_rng(1)
