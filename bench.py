@@ -36,7 +36,7 @@ UNIT = "phi-actions/s"
 # DRAM bytes (read + write) of one launch of the dominant kernel, from an ncu --set full capture
 # of this configuration (k_iter, a K = 2 launch; k_arnf for KIOPS; cold caches); null for configurations without a
 # capture of the current kernel.  Keyed by (method, n, precision, Newton kernel).
-TRAFFIC = {("leja", 1024, "DF64", "single"): 67.17e6 + 8.82e6,
+TRAFFIC = {("leja", 1024, "DF64", "single"): 67.16e6 + 3.71e6,
            ("leja", 2048, "DF64", "tma"): 270.30e6 + 146.65e6,
            ("kiops", 1024, "DF64", "single"): 86.58e6 + 8.34e6}
 
