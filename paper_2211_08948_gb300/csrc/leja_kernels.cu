@@ -60,16 +60,20 @@ __global__ void __launch_bounds__(THREADS, 2) k_iter(IterDev a) {
   // FP32_JV keeps the stencil in float32 and the shift in double-float: no folding
   constexpr bool FOLD = (MODE == MODE_NEWTON) && std::is_same<C, CJ>::value;
 
-  if (__ldcg(&a.ctl->done)) {  // the chain already stopped
-    if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) stop_loop(a);
-    return;
-  }
+  // the control word, the iteration index and the parameter header are
+  // independent loads: issued together, one round trip before the
+  // coefficient and tile loads (the stop flag is tested after them)
+  const int done0 = __ldcg(&a.ctl->done);
   int m = __ldcg(&a.ctl->m);
   const PassParams* pp = pp_of(a.ptab);
   const int M = pp->M;
   const int K = (MODE == MODE_NEWTON) ? pp->K : 0;
   const CJ ga = coef<CJ>(pp->gad, pp->gaf);
   const bool prescaled = MODE == MODE_NEWTON && pp->prescaled;
+  if (done0) {  // the chain already stopped
+    if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) stop_loop(a);
+    return;
+  }
   // PERSIST: every iteration of the chain in this one (cooperative) launch,
   // one grid barrier per iteration; otherwise one iteration per launch
   for (;;) {
