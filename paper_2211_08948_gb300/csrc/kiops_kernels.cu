@@ -468,7 +468,9 @@ __global__ void __launch_bounds__(THREADS) k_arnf(ArnArgs a) {
   T* rgZ = rgW + NC * NRING;
   T* rgM = rgZ + NC * NRING;
   KiopsCtl* kc = a.kc;
-  if (__ldcg(&kc->stop)) return;
+  // the stop flag and the step's coefficients: independent loads, issued
+  // together (the flag is tested after them)
+  const int stop0 = __ldcg(&kc->stop);
   const C ws = coef<C>(__ldcg(&kc->wsd), __ldcg(&kc->wsf));
   const C c1 = coef<C>(__ldcg(&kc->c1d), __ldcg(&kc->c1f));
   const C c0 = coef<C>(__ldcg(&kc->c0d), __ldcg(&kc->c0f));
@@ -480,6 +482,7 @@ __global__ void __launch_bounds__(THREADS) k_arnf(ArnArgs a) {
 #pragma unroll
   for (int b = 0; b < KIOPS_PMAX; ++b)
     bw[b] = b < a.nb ? coef<C>(__ldcg(&kc->bud[a.bslot[b]]), __ldcg(&kc->buf[a.bslot[b]])) : C{};
+  if (stop0) return;
 
   Acc acc[4] = {acc_zero<Acc>(), acc_zero<Acc>(), acc_zero<Acc>(), acc_zero<Acc>()};
   // ||Zhat_{j+1}||^2 and <u, u> in float32 on the double-float path: an error d

@@ -233,13 +233,16 @@ __global__ void __launch_bounds__(TT, CTAS_PER_SM) k_iter_tma(const __grid_const
   __shared__ int s_abort;
 
   LejaCtl* ctl = a.ctl;
-  if (__ldcg(&ctl->done)) {
-    if (blockIdx.x == 0 && threadIdx.x == 0 && a.use_cond) cudaGraphSetConditional(a.cond, 0);
-    return;
-  }
+  // the stop flag, the iteration index and the table length: independent
+  // loads, issued together (the flag is tested after them)
+  const int done0 = __ldcg(&ctl->done);
   const int m = __ldcg(&ctl->m);
   const PassParams* pp = pp_of(a.ptab);
   const int M = pp->M;
+  if (done0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a.use_cond) cudaGraphSetConditional(a.cond, 0);
+    return;
+  }
   const int K = a.K;
   const int tid = threadIdx.x;
 
@@ -261,8 +264,10 @@ __global__ void __launch_bounds__(TT, CTAS_PER_SM) k_iter_tma(const __grid_const
   const int nx = a.nx, ny = a.ny;
   const size_t plane = (size_t)nx * ny;
   const int pin = (m - 1) & 1;
-  const T* __restrict__ yin = static_cast<const T*>(a.y[pin]);
-  T* __restrict__ yout = static_cast<T*>(a.y[m & 1]);
+  // selects, not a runtime index into the argument block (which would copy
+  // the block to local memory)
+  const T* __restrict__ yin = static_cast<const T*>(pin ? a.y[1] : a.y[0]);
+  T* __restrict__ yout = static_cast<T*>(pin ? a.y[0] : a.y[1]);
   const S* __restrict__ stg = static_cast<const S*>(a.st);
   const int nst = a.stages;
   const int nt = (a.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;  // tiles of this CTA
