@@ -23,7 +23,7 @@ namespace {
 // The scratch itself.  In host code `noalloc_scratch` names a host-side
 // stand-in, not device memory: kernels must be given the device address
 // obtained from cudaGetSymbolAddress (below), never the symbol itself.
-__device__ __align__(256) unsigned char noalloc_scratch[PHIX_NOALLOC_SCRATCH_BYTES];
+static __device__ __align__(256) unsigned char noalloc_scratch[PHIX_NOALLOC_SCRATCH_BYTES];
 
 constexpr int MAX_DEVICES = 64;
 constexpr int MAX_GRID = 2048;
