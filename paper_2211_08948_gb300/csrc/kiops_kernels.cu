@@ -1338,7 +1338,8 @@ __device__ void small_exp_e1(int n, const double* dg, const double* up, const do
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(SX) k_kexp(KiopsCtl* kc, int m, double tau, double tau_end, double tol) {
+__global__ void __launch_bounds__(SX) k_kexp(KiopsCtl* kc, int m, double tau, double tau_end, double tol,
+                                              KiopsMailbox* mbox, unsigned int seq) {
   __shared__ double dg[KIOPS_MMAX + 2], up[KIOPS_MMAX + 2], lo[KIOPS_MMAX + 2];
   __shared__ SmallExpWork w;
   __shared__ int n_s;
@@ -1376,6 +1377,14 @@ __global__ void __launch_bounds__(SX) k_kexp(KiopsCtl* kc, int m, double tau, do
     kc->omega = omega;
     if (!isfinite(omega)) kc->status = PHIX_ENAN;
     __threadfence();
+    if (mbox) {
+      // the decision's inputs to the host: the header, then its sequence number
+      const unsigned int* src = reinterpret_cast<const unsigned int*>(kc);
+      unsigned int* dst = reinterpret_cast<unsigned int*>(mbox->header);
+      for (int i = 0; i < (int)(KIOPS_HOST_BYTES / 4); ++i) dst[i] = __ldcg(src + i);
+      __threadfence_system();
+      mbox->seq = seq;
+    }
   }
 }
 
@@ -1722,8 +1731,9 @@ cudaError_t small_expm_e1(int n, const double* d, const double* u, const double*
   return cudaGetLastError();
 }
 
-cudaError_t kiops_smallexp(KiopsCtl* kc, int m, double tau, double tau_end, double tol, cudaStream_t st) {
-  k_kexp<<<1, 128, 0, st>>>(kc, m, tau, tau_end, tol);
+cudaError_t kiops_smallexp(KiopsCtl* kc, int m, double tau, double tau_end, double tol, KiopsMailbox* mbox,
+                           unsigned int seq, cudaStream_t st) {
+  k_kexp<<<1, 128, 0, st>>>(kc, m, tau, tau_end, tol, mbox, seq);
   return cudaGetLastError();
 }
 

@@ -7,6 +7,8 @@
 // chains' control blocks once per call) -> outputs scaled back to float64.  EXPRB43 / EPIRK4s3 steps chain these actions with
 // float64 stage kernels.
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -87,6 +89,9 @@ struct phix_ctx {
   };
   std::vector<Graph> graphs;     // cached chain graphs (WHILE loops of iteration launches)
   KiopsCtl* kc_h = nullptr;      // pinned mirror of the KIOPS control header
+  KiopsMailbox* kmb_h = nullptr; // host-mapped decision mailbox (host address)
+  KiopsMailbox* kmb_d = nullptr; // its device address
+  unsigned int kmb_seq = 0;
   struct BatchGraph {
     unsigned long long key;
     int grid;
@@ -934,6 +939,25 @@ void read_kc(phix_ctx* ctx, KiopsCtl* kc) {
   CK(cudaStreamSynchronize(ctx->stream));
 }
 
+// The small exponential with its decision read from the mailbox: poll the
+// sequence number (a few microseconds after the kernel's write, against the
+// wake-up of a stream synchronisation); after 0.5 s without it, synchronise
+// the stream, which reports a failed kernel, and read the mailbox then.
+void smallexp_decision(phix_ctx* ctx, KiopsCtl* kc, int m, double tau, double tau_end, double tol) {
+  const unsigned int seq = ++ctx->kmb_seq;
+  KL(kiops_smallexp(kc, m, tau, tau_end, tol, ctx->kmb_d, seq, ctx->stream));
+  const auto t0 = std::chrono::steady_clock::now();
+  for (long spin = 0; ctx->kmb_h->seq != seq; ++spin) {
+    if ((spin & 1023) == 1023 && std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(500)) {
+      CK(cudaStreamSynchronize(ctx->stream));
+      if (ctx->kmb_h->seq != seq) fail(ctx, PHIX_ECUDA, "KIOPS decision mailbox not written");
+      break;
+    }
+  }
+  std::atomic_thread_fence(std::memory_order_acquire);
+  std::memcpy(ctx->kc_h, const_cast<const unsigned char*>(ctx->kmb_h->header), KIOPS_HOST_BYTES);
+}
+
 void kiops_run(phix_ctx* ctx, const OpState& os, int prec, double h, const double* const* b, int p,
                const std::vector<double>& times, const std::vector<std::vector<KOut>>& outs, double tol,
                const phix_opts& o, phix_stats& stats) {
@@ -1056,8 +1080,7 @@ void kiops_run(phix_ctx* ctx, const OpState& os, int prec, double h, const doubl
       }
       ctx->launches += launched;
       if (prof) CK(cudaEventRecord(ctx->ev[2 * NSLOT + 1], ctx->stream));
-      KL(kiops_smallexp(kc, m, tau, tau_end, tol, ctx->stream));
-      read_kc(ctx, kc);
+      smallexp_decision(ctx, kc, m, tau, tau_end, tol);
       const KiopsCtl& H = *ctx->kc_h;
       const int happy = H.happy_m;
       const int steps = (happy > 0 ? std::min(happy, m) : m) - built;
@@ -1289,6 +1312,15 @@ phix_status phix_create(phix_ctx** out, void* stream) {
     CK(cudaMallocHost(&ctx->scal_h, sizeof(double) * 16));
     CK(cudaMalloc(&ctx->counter, sizeof(unsigned int)));
     CK(cudaMallocHost(&ctx->kc_h, sizeof(KiopsCtl)));
+    {
+      void* mb = nullptr;
+      CK(cudaHostAlloc(&mb, sizeof(KiopsMailbox), cudaHostAllocMapped));
+      ctx->kmb_h = static_cast<KiopsMailbox*>(mb);
+      std::memset(mb, 0, sizeof(KiopsMailbox));
+      void* md = nullptr;
+      CK(cudaHostGetDevicePointer(&md, mb, 0));
+      ctx->kmb_d = static_cast<KiopsMailbox*>(md);
+    }
     CK(cudaMemset(ctx->counter, 0, sizeof(unsigned int)));
     CK(cudaMemset(ctx->ctl, 0, sizeof(LejaCtl) * NSLOT));
     CK(cudaDeviceSynchronize());
@@ -1317,6 +1349,7 @@ phix_status phix_destroy(phix_ctx* ctx) {
   if (ctx->ptab_h) cudaFreeHost(ctx->ptab_h);
   if (ctx->ptab_d) cudaFree(ctx->ptab_d);
   if (ctx->kc_h) cudaFreeHost(ctx->kc_h);
+  if (ctx->kmb_h) cudaFreeHost(ctx->kmb_h);
   delete ctx;
   return PHIX_OK;
 }

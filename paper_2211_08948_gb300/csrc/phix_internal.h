@@ -200,6 +200,14 @@ struct KiopsCtl {
   float2 kuf[8], guf, buf[KIOPS_PMAX];
 };
 constexpr size_t KIOPS_HOST_BYTES = 40;  // leading fields the host reads back
+// Host-mapped (zero-copy) mailbox of the substep decision: the small
+// exponential's kernel copies the header fields there, then publishes `seq`
+// (system-scope fence in between); the host polls `seq` instead of a copy
+// and a stream synchronisation.
+struct KiopsMailbox {
+  unsigned char header[KIOPS_HOST_BYTES];
+  volatile unsigned int seq;
+};
 
 struct KiopsSpec {
   int prec, op, nx, ny, p;
@@ -236,7 +244,10 @@ bool kiops_fused_ok(const KiopsSpec& s);
 cudaError_t kiops_fused_first(const KiopsSpec& s, cudaStream_t st);
 cudaError_t kiops_fused_step(const KiopsSpec& s, int j, cudaStream_t st);
 // F = exp(tau Hbar) e_1 (n = m+1, or m after a happy breakdown), err, omega.
-cudaError_t kiops_smallexp(KiopsCtl* kc, int m, double tau, double tau_end, double tol, cudaStream_t st);
+// mbox (device address of a host-mapped KiopsMailbox, or NULL): receives the
+// header and then seq
+cudaError_t kiops_smallexp(KiopsCtl* kc, int m, double tau, double tau_end, double tol, KiopsMailbox* mbox,
+                           unsigned int seq, cudaStream_t st);
 // out = exp(tau T) e_1 for a tridiagonal T (device arrays d[n], u[n-1], l[n-1]); mode: 0 Chebyshev, 1 Taylor
 cudaError_t small_expm_e1(int n, const double* d, const double* u, const double* l, double tau, double* out,
                           int* mode, cudaStream_t st);
