@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(BT) k_batched(BArgs a) {
       else if constexpr (P == P_FP32)
         x = (float)pr.v[i];
       else
-        x = df_from_double(pr.v[i]);
+        x = df_split_pow2(pr.v[i], 0);
       st1(VV + i, x);
     }
     __syncthreads();
@@ -360,7 +360,7 @@ __global__ void __launch_bounds__(BT) k_batched(BArgs a) {
             else if constexpr (P == P_FP32)
               d = (double)pv;
             else
-              d = (double)pv.hi + (double)pv.lo;
+              d = df_to_double_pow2(pv, 0);
             pr.out[k][i] = d;
           }
       } else {
@@ -418,7 +418,7 @@ __global__ void __launch_bounds__(BT) k_batched(BArgs a) {
             else if constexpr (P == P_FP32)
               d = (double)uv;
             else
-              d = (double)uv.hi + (double)uv.lo;
+              d = df_to_double_pow2(uv, 0);
             pr.out[k][i] = d;
           }
           __syncthreads();

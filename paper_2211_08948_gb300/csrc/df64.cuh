@@ -106,6 +106,57 @@ __device__ __forceinline__ df df_scale2(df a, float p2) {
   return df_make(__fmul_rn(a.hi, p2), __fmul_rn(a.lo, p2));
 }
 
+// Conversions between float64 and double-float by integer operations.  The
+// float64 conversions (two roundings to float32 and a float64 subtraction,
+// or two widenings and a float64 addition) run on GB300's float64 pipe,
+// which makes the vector set-up and output kernels conversion-bound; these
+// forms give the same values, bit for bit, from the bit patterns.
+//
+// df_split_pow2(x, e2) = df_from_double(x * 2^e2): hi = x rounded to float32
+// (nearest, ties to even, on the 29 dropped fraction bits: the carry into
+// the exponent field is the rounding overflow), lo = the remainder, an
+// integer of at most 29 bits times a power of two, rounded to float32 by the
+// integer conversion and scaled exactly.  For |x 2^e2| in [2^-60, 2^60); zero
+// and every other value take the float64 conversions.
+__device__ __forceinline__ df df_split_pow2(double x, int e2) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((u >> 52) & 0x7FF) + e2;
+  const unsigned int sg = (unsigned int)(u >> 32) & 0x80000000u;
+  if (e < 1023 - 60 || e >= 1023 + 60) {
+    if ((u << 1) == 0ull) return df_make(__uint_as_float(sg), 0.f);  // signed zero; its remainder +0
+    const double y = e2 == 0 ? x : ldexp(x, e2);
+    const float hi = __double2float_rn(y);
+    return df_make(hi, __double2float_rn(y - (double)hi));
+  }
+  const unsigned long long f = u & 0xFFFFFFFFFFFFFull;       // 52 fraction bits
+  const unsigned int top = (unsigned int)(f >> 29);          // the 23 kept
+  const unsigned int low = (unsigned int)f & 0x1FFFFFFFu;    // the 29 dropped
+  const unsigned int up = (low > 0x10000000u) | ((low == 0x10000000u) & (top & 1u));
+  const unsigned int hb = (((unsigned int)(e - 1023 + 127)) << 23) + top + up;
+  const int r = (int)low - (int)(up << 29);                  // x - hi in units of 2^(e - 1075)
+  const float lo = __int2float_rn(r) * __uint_as_float((unsigned int)(e - 1075 + 127) << 23);
+  return df_make(__uint_as_float(hb | sg), (sg && r != 0) ? -lo : lo);  // an exact remainder is +0
+}
+
+// float32 -> float64 times 2^e2 from the bit pattern (normal floats and zero;
+// subnormal, infinite and NaN values by the float64 conversion)
+__device__ __forceinline__ double f_to_double_pow2(float v, int e2) {
+  const unsigned int b = __float_as_uint(v);
+  const unsigned int E = (b >> 23) & 0xFFu;
+  if ((b & 0x7FFFFFFFu) == 0u) return __longlong_as_double((long long)((unsigned long long)(b >> 31) << 63));
+  const int de = (int)E - 127 + 1023 + e2;  // the float64 exponent field
+  if (E == 0u || E == 255u || de < 1 || de > 2046) return ldexp((double)v, e2);
+  const unsigned long long d = ((unsigned long long)(b >> 31) << 63) | ((unsigned long long)de << 52) |
+                               ((unsigned long long)(b & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)d);
+}
+
+// df_to_double(a) * 2^e2: both parts widened exactly, one float64 addition
+// (exact: the parts of a normalised pair span at most 48 bits)
+__device__ __forceinline__ double df_to_double_pow2(df a, int e2) {
+  return f_to_double_pow2(a.hi, e2) + f_to_double_pow2(a.lo, e2);
+}
+
 __device__ __forceinline__ df operator+(df a, df b) { return df_add(a, b); }
 __device__ __forceinline__ df operator-(df a, df b) { return df_sub(a, b); }
 __device__ __forceinline__ df operator*(df a, df b) { return df_mul(a, b); }

@@ -1444,7 +1444,7 @@ __global__ void __launch_bounds__(THREADS) k_kcomb(CombArgs a, size_t N) {
       if constexpr (P == P_FP64)
         d = w;
       else
-        d = (double)w.hi + (double)w.lo;
+        d = df_to_double_pow2(w, 0);
       a.out[i] = a.scale * d;
     }
     acc_dot(acc[0], w, w);
@@ -1492,7 +1492,7 @@ __global__ void __launch_bounds__(THREADS)
     if constexpr (P == P_FP64)
       w = x;
     else
-      w = df_from_double(x);
+      w = df_split_pow2(x, 0);
     st1(z0 + i, w);
     acc_dot(acc[0], w, w);
   }
@@ -1534,7 +1534,7 @@ __global__ void __launch_bounds__(THREADS)
     if constexpr (P == P_FP64)
       out[i] = x;
     else {
-      df w = df_from_double(x);
+      df w = df_split_pow2(x, 0);
       out[i] = make_float2(w.hi, w.lo);
     }
   }

@@ -385,18 +385,19 @@ __global__ void __launch_bounds__(THREADS)
 #pragma unroll
   for (int j = 0; j <= KMAX; ++j) acc[j] = acc_zero<Acc>();
   const double is = __ldcg(&a.ctl->inv_sigma);
+  const int se = __ldcg(&a.ctl->sigma_e);
   const size_t stride = (size_t)gridDim.x * THREADS;
   for (size_t i = (size_t)blockIdx.x * THREADS + threadIdx.y * 32 + threadIdx.x; i < n; i += stride) {
-    double x = v[i] * is;
     C y;
     if constexpr (P == P_FP64) {
+      const double x = v[i] * is;
       y = x;
       y0[i] = x;
     } else if constexpr (P == P_FP32) {
-      y = (float)x;
+      y = (float)(v[i] * is);
       y0[i] = y;
     } else {
-      y = df_from_double(x);
+      y = df_split_pow2(v[i], -se);  // v / sigma, sigma a power of two
       y0[i] = make_float2(y.hi, y.lo);
     }
     acc_sq(acc[0], y);
@@ -447,6 +448,7 @@ __global__ void __launch_bounds__(THREADS)
         sig = ldexp(1.0, e);
       }
       ctl->sigma = sig;
+      ctl->sigma_e = (int)ilogb(sig);
       ctl->inv_sigma = 1.0 / sig;
       ctl->count = 0;
       __threadfence();
@@ -459,6 +461,7 @@ __global__ void __launch_bounds__(THREADS) k_finalize(size_t n, int K, PtrPack p
   using T = typename Tr<P>::T;
   using C = typename Tr<P>::C;
   const double s = __ldcg(&ctl->sigma);
+  const int se = __ldcg(&ctl->sigma_e);
   // a two-iteration chain that stopped at an even m >= 2: p_m = p_{m-1} + d_k[m] y_m
   const int it = __ldcg(&ctl->iters);
   const bool def = fo.ptab != nullptr && it >= 2 && !(it & 1);
@@ -476,13 +479,11 @@ __global__ void __launch_bounds__(THREADS) k_finalize(size_t n, int K, PtrPack p
     for (size_t i = (size_t)blockIdx.x * THREADS + threadIdx.y * 32 + threadIdx.x; i < n; i += stride) {
       C x = cv(p[i]);
       if (def) x = mad(dk, cv(yd[i]), x);
-      double d;
       if constexpr (P == P_FP64 || P == P_FP32) {
-        d = (double)x;
+        o[i] = s * (double)x;
       } else {
-        d = (double)x.hi + (double)x.lo;
+        o[i] = df_to_double_pow2(x, se);  // sigma (hi + lo), sigma a power of two
       }
-      o[i] = s * d;
     }
   }
 }
@@ -504,7 +505,7 @@ __global__ void __launch_bounds__(THREADS)
       y = (float)x;
       y0[i] = y;
     } else {
-      y = df_from_double(x);
+      y = df_split_pow2(x, 0);
       y0[i] = make_float2(y.hi, y.lo);
     }
     acc_sq(acc[0], y);
@@ -549,7 +550,7 @@ __global__ void __launch_bounds__(THREADS)
       if constexpr (P == P_FP64) {
         s = g[j];
       } else if constexpr (P == P_DF64) {
-        df d = df_from_double(g[j]);
+        df d = df_split_pow2(g[j], 0);
         s = make_float2(d.hi, d.lo);
       } else {
         s = (float)g[j];

@@ -30,7 +30,7 @@ struct LejaCtl {
   int iters;           // iteration index m at which the chain stopped
   int status;          // phix_status
   int m;               // index of the next iteration of the chain (advanced by the last block)
-  int pad;
+  int sigma_e;         // sigma = 2^sigma_e
   double ysq;          // ||y_m||^2 (scaled units) of the last completed launch
   double psq[KMAX];    // ||p_m^(k)||^2
   double sigma;        // input scale, a power of two
