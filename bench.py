@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--clock-ms", type=int, default=100, help="nvidia-smi sampling period (0 = off)")
+    ap.add_argument("--clock-ms", type=int, default=20, help="nvidia-smi sampling period (0 = off)")
     ap.add_argument("--method", default="leja", choices=["leja", "kiops"])
     ap.add_argument("--kernel", default="auto", choices=["auto", "single", "tma", "fused2"],
                     help="Newton-step kernel of the Leja path (auto: TMA-staged once an iteration exceeds L2; "
