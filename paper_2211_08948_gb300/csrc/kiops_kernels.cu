@@ -19,6 +19,7 @@
 // launch (k_arnf): the orthogonalised vector is staged in shared memory with a
 // one-point halo ring and the stencil of the next step reads it there.
 #include <algorithm>
+#include <cstdint>
 #include "iter_common.cuh"
 #include "op_points.cuh"
 
@@ -1130,6 +1131,133 @@ __device__ void taylor_segments(int n, int S, const df (&ma)[R], const df (&mu)[
   }
 }
 
+// The same recurrences on one warp (n <= 32 R): lane l keeps rows
+// l R .. l R + R - 1, so a term's neighbour rows are the lane's own except at
+// its two ends, which come from the adjacent lanes by shuffles — no barrier
+// per term.  Rows >= n stay zero, as do the missing neighbours of rows 0 and
+// n - 1; each row's arithmetic is that of the block form above, term by term.
+template <int R>
+__device__ __forceinline__ void warp_nbrs(const df (&t)[R], df (&up)[R], df (&dn)[R], int lane) {
+  const float uh = __shfl_down_sync(0xffffffffu, t[0].hi, 1), ul = __shfl_down_sync(0xffffffffu, t[0].lo, 1);
+  const float dh = __shfl_up_sync(0xffffffffu, t[R - 1].hi, 1), dl = __shfl_up_sync(0xffffffffu, t[R - 1].lo, 1);
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    up[q] = (q + 1 < R) ? t[q + 1] : (lane < 31 ? df_make(uh, ul) : df_make(0.f, 0.f));
+    dn[q] = (q > 0) ? t[q - 1] : (lane > 0 ? df_make(dh, dl) : df_make(0.f, 0.f));
+  }
+}
+
+template <int R>
+__device__ __forceinline__ void warp_renorm(df (&xr)[R], double& lead) {
+  float mx = 0.f;
+#pragma unroll
+  for (int q = 0; q < R; ++q) mx = fmaxf(mx, fabsf(xr[q].hi));
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  int e = 0;
+  if (mx > 0.f) (void)frexpf(mx, &e);
+  const float f = ldexpf(1.f, -e);
+#pragma unroll
+  for (int q = 0; q < R; ++q) xr[q] = df_scale2(xr[q], f);
+  lead += e * 0.69314718055994530942;
+}
+
+template <int R>
+__device__ void warp_cheb_segments(int n, int S, int K, const df (&ma)[R], const df (&mu)[R], const df (&ml)[R],
+                                   df (&xr)[R], double& lead, const SmallExpWork& w, int lane) {
+  const df b0 = w.bes[0], b1 = df_scale2(w.bes[1], 2.f);
+  for (int seg = 0; seg < S; ++seg) {
+    if (seg > 0) warp_renorm<R>(xr, lead);
+    df tm[R], tc[R], up[R], dn[R];
+    warp_nbrs<R>(xr, up, dn, lane);
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      tm[q] = xr[q];
+      tc[q] = df_make(0.f, 0.f);
+      if (lane * R + q < n) {
+        float p[3], e[3];
+        df_prod(ma[q], xr[q], p[0], e[0]);
+        df_prod(mu[q], up[q], p[1], e[1]);
+        df_prod(ml[q], dn[q], p[2], e[2]);
+        const df v = df_scale2(df_sum_pairs<3>(p, e), 0.5f);
+        xr[q] = df_fma(b1, v, df_mul(b0, xr[q]));
+        tc[q] = v;
+      }
+    }
+    df bk = df_scale2(w.bes[2], 2.f);
+    for (int k = 2; k < K; ++k) {
+      const df bnext = df_scale2(w.bes[k + 1], 2.f);
+      warp_nbrs<R>(tc, up, dn, lane);
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        if (lane * R + q < n) {
+          float p[4], e[4];
+          df_prod(ma[q], tc[q], p[0], e[0]);
+          df_prod(mu[q], up[q], p[1], e[1]);
+          df_prod(ml[q], dn[q], p[2], e[2]);
+          p[3] = -tm[q].hi;
+          e[3] = -tm[q].lo;
+          const df v = df_sum_pairs<4>(p, e);
+          xr[q] = df_fma(bk, v, xr[q]);
+          tm[q] = tc[q];
+          tc[q] = v;
+        }
+      }
+      bk = bnext;
+    }
+  }
+}
+
+template <int R>
+__device__ void warp_taylor_segments(int n, int S, const df (&ma)[R], const df (&mu)[R], const df (&ml)[R],
+                                     df (&xr)[R], double& lead, const SmallExpWork& w, int lane) {
+  for (int seg = 0; seg < S; ++seg) {
+    if (seg > 0) warp_renorm<R>(xr, lead);
+    df tc[R], up[R], dn[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) tc[q] = xr[q];
+    for (int k = 1; k <= 30; ++k) {
+      const df ik = w.invk[k];
+      warp_nbrs<R>(tc, up, dn, lane);
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        if (lane * R + q < n) {
+          float p[3], e[3];
+          df_prod(ma[q], tc[q], p[0], e[0]);
+          df_prod(mu[q], up[q], p[1], e[1]);
+          df_prod(ml[q], dn[q], p[2], e[2]);
+          const df v = df_mul(df_sum_pairs<3>(p, e), ik);
+          xr[q] = df_add(xr[q], v);
+          tc[q] = v;
+        }
+      }
+    }
+  }
+}
+
+template <int R>
+__device__ void run_recurrence_warp(int n, const double* dg, const double* up, const double* lo, double c,
+                                    double cscale, int mode, int S, int K, double& lead, SmallExpWork& w, int lane) {
+  df ma[R], mu[R], ml[R], xr[R];
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    const int i = lane * R + q;
+    const bool in = i < n;
+    ma[q] = dfd(in ? (dg[i] - c) * cscale : 0.0);
+    mu[q] = dfd((in && i + 1 < n) ? up[i] * cscale : 0.0);
+    ml[q] = dfd((in && i >= 1) ? lo[i - 1] * cscale : 0.0);
+    xr[q] = df_make((i == 0) ? 1.f : 0.f, 0.f);
+  }
+  if (mode == 0)
+    warp_cheb_segments<R>(n, S, K, ma, mu, ml, xr, lead, w, lane);
+  else
+    warp_taylor_segments<R>(n, S, ma, mu, ml, xr, lead, w, lane);
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    const int i = lane * R + q;
+    if (i < n) w.x[i] = dd(xr[q]);
+  }
+}
+
 // The recurrence matrix rows of this thread (M = (T - cI) cscale), the
 // starting vector e_1, and the chosen recurrence; x returned in w.x.
 template <int R>
@@ -1325,10 +1453,19 @@ __device__ void small_exp_e1(int n, const double* dg, const double* up, const do
   __syncthreads();  // pads and invk before the first rows are written
   double lead = (mode == 0) ? lam_hi : c;  // Chebyshev: S (c + r)/S; Taylor: the shift
   const double cscale = (mode == 0) ? 2.0 / r : 1.0 / S;
-  if (n <= SX)
+  // up to 64 rows on one warp (no barrier per term), larger matrices on the block
+  if (n <= 64) {
+    if (tid < 32) {
+      if (n <= 32)
+        run_recurrence_warp<1>(n, dg, up, lo, c, cscale, mode, S, K, lead, w, tid);
+      else
+        run_recurrence_warp<2>(n, dg, up, lo, c, cscale, mode, S, K, lead, w, tid);
+    }
+  } else if (n <= SX) {
     run_recurrence<1>(n, dg, up, lo, c, cscale, mode, S, K, lead, w, tid);
-  else
+  } else {
     run_recurrence<2>(n, dg, up, lo, c, cscale, mode, S, K, lead, w, tid);
+  }
   if (tid == 0) {
     w.mode = mode;
     w.lead = lead;
@@ -1342,21 +1479,17 @@ __global__ void __launch_bounds__(SX) k_kexp(KiopsCtl* kc, int m, double tau, do
                                               KiopsMailbox* mbox, unsigned int seq) {
   __shared__ double dg[KIOPS_MMAX + 2], up[KIOPS_MMAX + 2], lo[KIOPS_MMAX + 2];
   __shared__ SmallExpWork w;
-  __shared__ int n_s;
   const int tid = threadIdx.x;
-  if (tid == 0) {
-    const int hm = kc->happy_m;
-    const int mm = hm > 0 ? hm : m;
-    n_s = hm > 0 ? hm : m + 1;
-    const int n = n_s;
-    for (int i = 0; i < n; ++i) {
-      dg[i] = tau * (i < mm ? kc->hd[i] : 0.0);          // row m of Hbar has no diagonal
-      up[i] = tau * ((i + 1 < mm) ? kc->hu[i + 1] : 0.0);  // (i, i+1); column m is zero
-      lo[i] = tau * ((i + 1 < n) ? kc->hl[i] : 0.0);       // (i+1, i)
-    }
+  // one row of the matrix per thread (independent loads, not a serial chain)
+  const int hm = __ldcg(&kc->happy_m);
+  const int mm = hm > 0 ? hm : m;
+  const int n = hm > 0 ? hm : m + 1;
+  for (int i = tid; i < n; i += 128) {
+    dg[i] = tau * (i < mm ? __ldcg(&kc->hd[i]) : 0.0);          // row m of Hbar has no diagonal
+    up[i] = tau * ((i + 1 < mm) ? __ldcg(&kc->hu[i + 1]) : 0.0);  // (i, i+1); column m is zero
+    lo[i] = tau * ((i + 1 < n) ? __ldcg(&kc->hl[i]) : 0.0);       // (i+1, i)
   }
   __syncthreads();
-  const int n = n_s;
   small_exp_e1(n, dg, up, lo, w, tid);
   const double e = exp(w.lead);
   for (int i = tid; i < n; i += 128) {
@@ -1414,12 +1547,13 @@ struct CombArgs {
   double* out;
   double scale;
   int p, nscaled;
+  int pairs;  // N even, slots and out 16-byte aligned: 16-byte loads of element pairs
   double h;
   double kJ[8];
 };
 
 template <int P>
-__global__ void __launch_bounds__(THREADS) k_kcomb(CombArgs a, size_t N) {
+__global__ void __launch_bounds__(THREADS, 4) k_kcomb(CombArgs a, size_t N) {
   using T = typename KTr<P>::T;
   using C = typename KTr<P>::C;
   using Acc = typename KTr<P>::Acc;
@@ -1435,7 +1569,54 @@ __global__ void __launch_bounds__(THREADS) k_kcomb(CombArgs a, size_t N) {
   T* z0 = const_cast<T*>(zp[0]);
   Acc acc[1] = {acc_zero<Acc>()};
   const size_t stride = (size_t)gridDim.x * THREADS;
-  for (size_t i = (size_t)blockIdx.x * THREADS + tid; i < N; i += stride) {
+  // Pairs of elements, one 16-byte load per basis vector (a.pairs: N even,
+  // every slot and the output 16-byte aligned).  The loads of KC basis vectors
+  // are issued before their products are summed, so a thread waits for memory
+  // once per KC terms instead of once per term; the sum runs in the basis
+  // order, the same arithmetic as the element loop below.
+  size_t i0 = 0;
+  if (a.pairs) {
+    constexpr int KC = 8;
+    const size_t np = N / 2;
+    for (size_t v = (size_t)blockIdx.x * THREADS + tid; v < np; v += stride) {
+      C w0{}, w1{};
+      for (int k0 = 0; k0 < a.n; k0 += KC) {
+        C x0[KC], x1[KC];
+#pragma unroll
+        for (int q = 0; q < KC; ++q)
+          if (k0 + q < a.n) ldr2(zp[k0 + q] + 2 * v, x0[q], x1[q]);
+#pragma unroll
+        for (int q = 0; q < KC; ++q) {
+          if (k0 + q < a.n) {
+            const C c = cf[k0 + q];
+            if (k0 + q == 0) {
+              w0 = c * x0[q];
+              w1 = c * x1[q];
+            } else {
+              w0 = w0 + c * x0[q];
+              w1 = w1 + c * x1[q];
+            }
+          }
+        }
+      }
+      st2(z0 + 2 * v, w0, w1);
+      if (a.out) {
+        double d0, d1;
+        if constexpr (P == P_FP64) {
+          d0 = w0;
+          d1 = w1;
+        } else {
+          d0 = df_to_double_pow2(w0, 0);
+          d1 = df_to_double_pow2(w1, 0);
+        }
+        *reinterpret_cast<double2*>(a.out + 2 * v) = make_double2(a.scale * d0, a.scale * d1);
+      }
+      acc_dot(acc[0], w0, w0);
+      acc_dot(acc[0], w1, w1);
+    }
+    i0 = 2 * np;
+  }
+  for (size_t i = i0 + (size_t)blockIdx.x * THREADS + tid; i < N; i += stride) {
     C w = cf[0] * ldr1(zp[0] + i);
     for (int k = 1; k < a.n; ++k) w = w + cf[k] * ldr1(zp[k] + i);
     st1(z0 + i, w);
@@ -1740,6 +1921,9 @@ cudaError_t kiops_smallexp(KiopsCtl* kc, int m, double tau, double tau_end, doub
 cudaError_t kiops_combine(const KiopsSpec& s, int n, double* out, double scale, cudaStream_t st) {
   const size_t N = (size_t)s.nx * s.ny * op_ncomp(s.op);
   CombArgs c = make_comb(s, n, out, scale);
+  bool al = N % 2 == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0;
+  for (int k = 0; k < n; ++k) al = al && (reinterpret_cast<uintptr_t>(s.Zh[k]) & 15) == 0;
+  c.pairs = al ? 1 : 0;
   if (s.prec == P_FP64)
     k_kcomb<P_FP64><<<s.grid, dim3(32, TILE_Y), 0, st>>>(c, N);
   else

@@ -218,3 +218,46 @@ def test_kiops_scales_with_its_input(px, prec, c):
     for a, b in zip(res[c], res[1.0]):
         assert np.all(np.isfinite(a))
         assert np.linalg.norm(a - b) <= 1e-12 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("prec", ["FP64", "DF64"])
+@pytest.mark.parametrize("case", ["odd_grid", "offset_output"])
+def test_kiops_combination_element_and_pair_paths(px, prec, case):
+    """The basis combination reads element pairs with 16-byte loads when the
+    unknown count is even and the slots and the output are 16-byte aligned,
+    and single elements otherwise: an odd grid (45 x 37) and an output view
+    one float64 past an aligned address take the element path.  Both against
+    the oracle's KIOPS-style method; the offset output also against the same
+    action into aligned outputs (pair path), equal to rounding."""
+    phix, ctx = px
+    nx, ny = (45, 37) if case == "odd_grid" else (48, 40)
+    D, ax, ay = 0.5, 1.5, -2.0
+    h = 40.0 / (4 * D * (nx * nx + ny * ny))
+    v = np.random.default_rng(21).standard_normal(nx * ny)
+    outs = [(1, 0.5), (2, 1.0)]
+    tol = 1e-9
+    kw = dict(m_init=8, m_max=24, m_step=4)
+    op = phix.make_jop(phix.PHIX_OP_ADVDIFF, nx, ny, [D, ax, ay])
+    vd = dev(v)
+    if case == "offset_output":
+        bufs = [torch.empty(nx * ny + 1, dtype=torch.float64, device="cuda") for _ in outs]
+        od = [b[1:] for b in bufs]
+        assert all(o.data_ptr() % 16 == 8 for o in od)
+    else:
+        od = [torch.empty_like(vd) for _ in outs]
+    st = phix.phix_phi_action(ctx, op, h, vd, [l for l, _ in outs], [s for _, s in outs], od, tol,
+                              phix.PHIX_KIOPS, _opts(phix, prec, **kw))
+    assert st.status == 0
+    aop = AdvDiff(nx, D, ax, ay, ny=ny)
+    ref, _ = kiops.kiops_phi(lambda x: h * aop.jv(x), v, outs, tol, **kw)
+    for (l, s), r, o in zip(outs, od, ref):
+        bs = [None] * (l + 1)
+        bs[l] = v
+        assert kiops_parity(host(r), o, bs, tol)
+    if case == "offset_output":
+        od2 = [torch.empty_like(vd) for _ in outs]
+        st2 = phix.phix_phi_action(ctx, op, h, vd, [l for l, _ in outs], [s for _, s in outs], od2, tol,
+                                   phix.PHIX_KIOPS, _opts(phix, prec, **kw))
+        assert st2.iters == st.iters and st2.substeps == st.substeps
+        for a, b in zip(od, od2):
+            assert rel(host(a), host(b)) <= 1e-13
