@@ -955,7 +955,10 @@ struct SmallExpWork {
   double x[KIOPS_MMAX + 2];           // result (float64)
   float2 nb[2][KIOPS_MMAX + 4];       // recurrence rows for the neighbours (ping-pong; row i at i + 1,
                                       // zero pads at 0 and n + 1)
+  float2 n2[2][2][KIOPS_MMAX + 6];  // Chebyshev pairs (T_{k-1}, T_k), ping-pong; row i at i + 2, zero pads
   df bes[CHEB_MAX + 2];
+  short bres[CHEB_MAX + 2];           // rescalings of the Miller recurrence before bes[k] was stored
+  int nres;                           // and in all
   df invk[32];
   float fa[KIOPS_MMAX + 2], fs2[KIOPS_MMAX + 2], fk2[KIOPS_MMAX + 2], fz[KIOPS_MMAX + 2];
   int cnt[SX];
@@ -1011,9 +1014,14 @@ __device__ void msect_round(int n, const float* a, const float* b2, float (&lo)[
 // Chebyshev segments: x <- I~_0 x + 2 sum_{k=1}^{K-1} I~_k T_k(Y) x, S times,
 // with M = 2Y in (ma, mu, ml); x renormalised by a power of two before every
 // segment but the first (lead collects the exponents).  R rows per thread.
+// Terms advance two at a time from (T_{k-1}, T_k):
+//   T_{k+1} = M T_k - T_{k-1},   T_{k+2} = (M^2 - I) T_k - M T_{k-1},
+// the pentadiagonal M^2 - I in pc (columns i-2 .. i+2 of row i): both new
+// terms depend only on the pair before, so the serial chain and the
+// exchanges through shared memory (one barrier per pair) are halved.
 template <int R>
 __device__ void cheb_segments(int n, int S, int K, const df (&ma)[R], const df (&mu)[R], const df (&ml)[R],
-                              df (&xr)[R], double& lead, SmallExpWork& w, int tid) {
+                              const df (&pc)[R][5], df (&xr)[R], double& lead, SmallExpWork& w, int tid) {
   const df b0 = w.bes[0], b1 = df_scale2(w.bes[1], 2.f);
   for (int seg = 0; seg < S; ++seg) {
     if (seg > 0) {
@@ -1028,11 +1036,12 @@ __device__ void cheb_segments(int n, int S, int K, const df (&ma)[R], const df (
       for (int q = 0; q < R; ++q) xr[q] = df_scale2(xr[q], f);
       lead += e * 0.69314718055994530942;
     }
+    // rows of the exchanged terms: row i at index i + 2, zero pads around
     df tm[R], tc[R];
 #pragma unroll
     for (int q = 0; q < R; ++q) {
       const int i = tid + q * SX;
-      if (i < n) w.nb[0][i + 1] = make_float2(xr[q].hi, xr[q].lo);
+      if (i < n) w.n2[0][0][i + 2] = make_float2(xr[q].hi, xr[q].lo);
     }
     __syncthreads();
     // T_1 = Y x (half the row of M); x <- I~_0 x + 2 I~_1 T_1
@@ -1044,41 +1053,75 @@ __device__ void cheb_segments(int n, int S, int K, const df (&ma)[R], const df (
       if (i < n) {
         float p[3], e[3];
         df_prod(ma[q], xr[q], p[0], e[0]);
-        df_prod(mu[q], cv(w.nb[0][i + 2]), p[1], e[1]);
-        df_prod(ml[q], cv(w.nb[0][i]), p[2], e[2]);
+        df_prod(mu[q], cv(w.n2[0][0][i + 3]), p[1], e[1]);
+        df_prod(ml[q], cv(w.n2[0][0][i + 1]), p[2], e[2]);
         const df v = df_scale2(df_sum_pairs<3>(p, e), 0.5f);
-        w.nb[1][i + 1] = make_float2(v.hi, v.lo);
+        w.n2[0][1][i + 2] = make_float2(v.hi, v.lo);
         xr[q] = df_fma(b1, v, df_mul(b0, xr[q]));
         tc[q] = v;
       }
     }
     __syncthreads();
-    // T_k = M T_{k-1} - T_{k-2}; term k reads nb[(k - 1) & 1], writes nb[k & 1]
-    df bk = df_scale2(w.bes[2], 2.f);
-    for (int k = 2; k < K; ++k) {
-      const float2* src = w.nb[(k - 1) & 1];
-      float2* dst = w.nb[k & 1];
-      const df bnext = df_scale2(w.bes[k + 1], 2.f);
+    // pairs: tm = T_{k-1}, tc = T_k, also in n2[par][0], n2[par][1]
+    int k = 1, par = 0;
+    for (; k + 2 < K; k += 2) {
+      const float2* om = w.n2[par][0];
+      const float2* oc = w.n2[par][1];
+      float2* nm = w.n2[par ^ 1][0];
+      float2* nc = w.n2[par ^ 1][1];
+      const df c1 = df_scale2(w.bes[k + 1], 2.f), c2 = df_scale2(w.bes[k + 2], 2.f);
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        const int i = tid + q * SX;
+        if (i < n) {
+          const df cw2 = cv(oc[i]), cw1 = cv(oc[i + 1]), ce1 = cv(oc[i + 3]), ce2 = cv(oc[i + 4]);
+          const df mw1 = cv(om[i + 1]), me1 = cv(om[i + 3]);
+          float p[4], e[4];
+          df_prod(ma[q], tc[q], p[0], e[0]);
+          df_prod(mu[q], ce1, p[1], e[1]);
+          df_prod(ml[q], cw1, p[2], e[2]);
+          p[3] = -tm[q].hi;
+          e[3] = -tm[q].lo;
+          const df v1 = df_sum_pairs<4>(p, e);
+          float P[8], E[8];
+          df_prod(pc[q][0], cw2, P[0], E[0]);
+          df_prod(pc[q][1], cw1, P[1], E[1]);
+          df_prod(pc[q][2], tc[q], P[2], E[2]);
+          df_prod(pc[q][3], ce1, P[3], E[3]);
+          df_prod(pc[q][4], ce2, P[4], E[4]);
+          df_prod(df_neg(ma[q]), tm[q], P[5], E[5]);
+          df_prod(df_neg(mu[q]), me1, P[6], E[6]);
+          df_prod(df_neg(ml[q]), mw1, P[7], E[7]);
+          const df v2 = df_sum_pairs<8>(P, E);
+          nm[i + 2] = make_float2(v1.hi, v1.lo);
+          nc[i + 2] = make_float2(v2.hi, v2.lo);
+          xr[q] = df_fma(c2, v2, df_fma(c1, v1, xr[q]));
+          tm[q] = v1;
+          tc[q] = v2;
+        }
+      }
+      par ^= 1;
+      __syncthreads();
+    }
+    // one last term when K - 2 is odd
+    if (k + 1 < K) {
+      const float2* oc = w.n2[par][1];
+      const df c1 = df_scale2(w.bes[k + 1], 2.f);
 #pragma unroll
       for (int q = 0; q < R; ++q) {
         const int i = tid + q * SX;
         if (i < n) {
           float p[4], e[4];
           df_prod(ma[q], tc[q], p[0], e[0]);
-          df_prod(mu[q], cv(src[i + 2]), p[1], e[1]);
-          df_prod(ml[q], cv(src[i]), p[2], e[2]);
+          df_prod(mu[q], cv(oc[i + 3]), p[1], e[1]);
+          df_prod(ml[q], cv(oc[i + 1]), p[2], e[2]);
           p[3] = -tm[q].hi;
           e[3] = -tm[q].lo;
-          const df v = df_sum_pairs<4>(p, e);
-          dst[i + 1] = make_float2(v.hi, v.lo);
-          xr[q] = df_fma(bk, v, xr[q]);
-          tm[q] = tc[q];
-          tc[q] = v;
+          xr[q] = df_fma(c1, df_sum_pairs<4>(p, e), xr[q]);
         }
       }
-      bk = bnext;
-      __syncthreads();
     }
+    __syncthreads();  // every read of n2 done before the next segment writes it
   }
 }
 
@@ -1131,133 +1174,6 @@ __device__ void taylor_segments(int n, int S, const df (&ma)[R], const df (&mu)[
   }
 }
 
-// The same recurrences on one warp (n <= 32 R): lane l keeps rows
-// l R .. l R + R - 1, so a term's neighbour rows are the lane's own except at
-// its two ends, which come from the adjacent lanes by shuffles — no barrier
-// per term.  Rows >= n stay zero, as do the missing neighbours of rows 0 and
-// n - 1; each row's arithmetic is that of the block form above, term by term.
-template <int R>
-__device__ __forceinline__ void warp_nbrs(const df (&t)[R], df (&up)[R], df (&dn)[R], int lane) {
-  const float uh = __shfl_down_sync(0xffffffffu, t[0].hi, 1), ul = __shfl_down_sync(0xffffffffu, t[0].lo, 1);
-  const float dh = __shfl_up_sync(0xffffffffu, t[R - 1].hi, 1), dl = __shfl_up_sync(0xffffffffu, t[R - 1].lo, 1);
-#pragma unroll
-  for (int q = 0; q < R; ++q) {
-    up[q] = (q + 1 < R) ? t[q + 1] : (lane < 31 ? df_make(uh, ul) : df_make(0.f, 0.f));
-    dn[q] = (q > 0) ? t[q - 1] : (lane > 0 ? df_make(dh, dl) : df_make(0.f, 0.f));
-  }
-}
-
-template <int R>
-__device__ __forceinline__ void warp_renorm(df (&xr)[R], double& lead) {
-  float mx = 0.f;
-#pragma unroll
-  for (int q = 0; q < R; ++q) mx = fmaxf(mx, fabsf(xr[q].hi));
-  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  int e = 0;
-  if (mx > 0.f) (void)frexpf(mx, &e);
-  const float f = ldexpf(1.f, -e);
-#pragma unroll
-  for (int q = 0; q < R; ++q) xr[q] = df_scale2(xr[q], f);
-  lead += e * 0.69314718055994530942;
-}
-
-template <int R>
-__device__ void warp_cheb_segments(int n, int S, int K, const df (&ma)[R], const df (&mu)[R], const df (&ml)[R],
-                                   df (&xr)[R], double& lead, const SmallExpWork& w, int lane) {
-  const df b0 = w.bes[0], b1 = df_scale2(w.bes[1], 2.f);
-  for (int seg = 0; seg < S; ++seg) {
-    if (seg > 0) warp_renorm<R>(xr, lead);
-    df tm[R], tc[R], up[R], dn[R];
-    warp_nbrs<R>(xr, up, dn, lane);
-#pragma unroll
-    for (int q = 0; q < R; ++q) {
-      tm[q] = xr[q];
-      tc[q] = df_make(0.f, 0.f);
-      if (lane * R + q < n) {
-        float p[3], e[3];
-        df_prod(ma[q], xr[q], p[0], e[0]);
-        df_prod(mu[q], up[q], p[1], e[1]);
-        df_prod(ml[q], dn[q], p[2], e[2]);
-        const df v = df_scale2(df_sum_pairs<3>(p, e), 0.5f);
-        xr[q] = df_fma(b1, v, df_mul(b0, xr[q]));
-        tc[q] = v;
-      }
-    }
-    df bk = df_scale2(w.bes[2], 2.f);
-    for (int k = 2; k < K; ++k) {
-      const df bnext = df_scale2(w.bes[k + 1], 2.f);
-      warp_nbrs<R>(tc, up, dn, lane);
-#pragma unroll
-      for (int q = 0; q < R; ++q) {
-        if (lane * R + q < n) {
-          float p[4], e[4];
-          df_prod(ma[q], tc[q], p[0], e[0]);
-          df_prod(mu[q], up[q], p[1], e[1]);
-          df_prod(ml[q], dn[q], p[2], e[2]);
-          p[3] = -tm[q].hi;
-          e[3] = -tm[q].lo;
-          const df v = df_sum_pairs<4>(p, e);
-          xr[q] = df_fma(bk, v, xr[q]);
-          tm[q] = tc[q];
-          tc[q] = v;
-        }
-      }
-      bk = bnext;
-    }
-  }
-}
-
-template <int R>
-__device__ void warp_taylor_segments(int n, int S, const df (&ma)[R], const df (&mu)[R], const df (&ml)[R],
-                                     df (&xr)[R], double& lead, const SmallExpWork& w, int lane) {
-  for (int seg = 0; seg < S; ++seg) {
-    if (seg > 0) warp_renorm<R>(xr, lead);
-    df tc[R], up[R], dn[R];
-#pragma unroll
-    for (int q = 0; q < R; ++q) tc[q] = xr[q];
-    for (int k = 1; k <= 30; ++k) {
-      const df ik = w.invk[k];
-      warp_nbrs<R>(tc, up, dn, lane);
-#pragma unroll
-      for (int q = 0; q < R; ++q) {
-        if (lane * R + q < n) {
-          float p[3], e[3];
-          df_prod(ma[q], tc[q], p[0], e[0]);
-          df_prod(mu[q], up[q], p[1], e[1]);
-          df_prod(ml[q], dn[q], p[2], e[2]);
-          const df v = df_mul(df_sum_pairs<3>(p, e), ik);
-          xr[q] = df_add(xr[q], v);
-          tc[q] = v;
-        }
-      }
-    }
-  }
-}
-
-template <int R>
-__device__ void run_recurrence_warp(int n, const double* dg, const double* up, const double* lo, double c,
-                                    double cscale, int mode, int S, int K, double& lead, SmallExpWork& w, int lane) {
-  df ma[R], mu[R], ml[R], xr[R];
-#pragma unroll
-  for (int q = 0; q < R; ++q) {
-    const int i = lane * R + q;
-    const bool in = i < n;
-    ma[q] = dfd(in ? (dg[i] - c) * cscale : 0.0);
-    mu[q] = dfd((in && i + 1 < n) ? up[i] * cscale : 0.0);
-    ml[q] = dfd((in && i >= 1) ? lo[i - 1] * cscale : 0.0);
-    xr[q] = df_make((i == 0) ? 1.f : 0.f, 0.f);
-  }
-  if (mode == 0)
-    warp_cheb_segments<R>(n, S, K, ma, mu, ml, xr, lead, w, lane);
-  else
-    warp_taylor_segments<R>(n, S, ma, mu, ml, xr, lead, w, lane);
-#pragma unroll
-  for (int q = 0; q < R; ++q) {
-    const int i = lane * R + q;
-    if (i < n) w.x[i] = dd(xr[q]);
-  }
-}
-
 // The recurrence matrix rows of this thread (M = (T - cI) cscale), the
 // starting vector e_1, and the chosen recurrence; x returned in w.x.
 template <int R>
@@ -1273,9 +1189,26 @@ __device__ void run_recurrence(int n, const double* dg, const double* up, const 
     ml[q] = dfd((in && i >= 1) ? lo[i - 1] * cscale : 0.0);
     xr[q] = df_make((i == 0) ? 1.f : 0.f, 0.f);
   }
-  if (mode == 0)
-    cheb_segments<R>(n, S, K, ma, mu, ml, xr, lead, w, tid);
-  else
+  if (mode == 0) {
+    // row i of M^2 - I (float64 from the float64 entries of M: a diagonal,
+    // u super-, l sub-diagonal; entries outside the matrix are zero)
+    df pc[R][5];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const int i = tid + q * SX;
+      const bool in = i < n;
+      auto a_ = [&](int j) { return (j >= 0 && j < n) ? (dg[j] - c) * cscale : 0.0; };
+      auto u_ = [&](int j) { return (j >= 0 && j + 1 < n) ? up[j] * cscale : 0.0; };
+      auto l_ = [&](int j) { return (j >= 1 && j < n) ? lo[j - 1] * cscale : 0.0; };
+      const double ai = a_(i), ui = u_(i), li = l_(i);
+      pc[q][0] = dfd(in ? li * l_(i - 1) : 0.0);
+      pc[q][1] = dfd(in ? li * (ai + a_(i - 1)) : 0.0);
+      pc[q][2] = dfd(in ? ai * ai + ui * l_(i + 1) + li * u_(i - 1) - 1.0 : 0.0);
+      pc[q][3] = dfd(in ? ui * (ai + a_(i + 1)) : 0.0);
+      pc[q][4] = dfd(in ? ui * u_(i + 1) : 0.0);
+    }
+    cheb_segments<R>(n, S, K, ma, mu, ml, pc, xr, lead, w, tid);
+  } else
     taylor_segments<R>(n, S, ma, mu, ml, xr, lead, w, tid);
 #pragma unroll
   for (int q = 0; q < R; ++q) {
@@ -1388,21 +1321,36 @@ __device__ void small_exp_e1(int n, const double* dg, const double* up, const do
         // each step down shrinks the start error by a factor >= 2
         const int kstart = max(kmax, 2 * (int)rs) + 24;
         const df ir2 = dfd(2.0 / rs);
+        // The values already stored are rescaled with the recurrence; a stored
+        // value only records how many rescalings preceded it (bres), and the
+        // ones that follow are applied below, in parallel, off this serial chain.
         df ip1 = df_make(0.f, 0.f), ik = df_make(1e-30f, 0.f);
+        int nres = 0;
         for (int k = kstart; k >= 0; --k) {
-          if (k <= kmax) w.bes[k] = ik;
+          if (k <= kmax) {
+            w.bes[k] = ik;
+            w.bres[k] = (short)nres;
+          }
           const df im1 = df_fma(df_mul(df_make((float)k, 0.f), ir2), ik, ip1);
           ip1 = ik;
           ik = im1;
           if (fabsf(ik.hi) > 1e30f) {
             ik = df_scale2(ik, 0x1p-100f);
             ip1 = df_scale2(ip1, 0x1p-100f);
-            for (int q = k; q <= kmax; ++q) w.bes[q] = df_scale2(w.bes[q], 0x1p-100f);
+            ++nres;
           }
         }
+        w.nres = nres;
       }
       __syncthreads();
-      // normalise: I~_0 + 2 sum_{k >= 1} I~_k = 1
+      // each stored value times 2^-100 once per later rescaling, in sequence (the
+      // same products as rescaling every stored value at each event)
+      for (int k = tid; k <= kmax; k += SX) {
+        df bv = w.bes[k];
+        for (int q = w.bres[k]; q < w.nres; ++q) bv = df_scale2(bv, 0x1p-100f);
+        w.bes[k] = bv;
+      }
+      // normalise: I~_0 + 2 sum_{k >= 1} I~_k = 1 (each thread sums the entries it rescaled)
       df part = df_make(0.f, 0.f);
       for (int k = tid; k <= kmax; k += SX) part = df_add(part, k == 0 ? w.bes[0] : df_scale2(w.bes[k], 2.f));
       const df sum = blk_dfsum(part, w.shd, tid);
@@ -1449,23 +1397,16 @@ __device__ void small_exp_e1(int n, const double* dg, const double* up, const do
     w.nb[0][i] = make_float2(0.f, 0.f);
     w.nb[1][i] = make_float2(0.f, 0.f);
   }
+  for (int i = tid; i < KIOPS_MMAX + 6; i += SX)
+    for (int a = 0; a < 4; ++a) w.n2[a >> 1][a & 1][i] = make_float2(0.f, 0.f);
   if (tid < 32) w.invk[tid] = dfd(tid > 0 ? 1.0 / tid : 0.0);
   __syncthreads();  // pads and invk before the first rows are written
   double lead = (mode == 0) ? lam_hi : c;  // Chebyshev: S (c + r)/S; Taylor: the shift
   const double cscale = (mode == 0) ? 2.0 / r : 1.0 / S;
-  // up to 64 rows on one warp (no barrier per term), larger matrices on the block
-  if (n <= 64) {
-    if (tid < 32) {
-      if (n <= 32)
-        run_recurrence_warp<1>(n, dg, up, lo, c, cscale, mode, S, K, lead, w, tid);
-      else
-        run_recurrence_warp<2>(n, dg, up, lo, c, cscale, mode, S, K, lead, w, tid);
-    }
-  } else if (n <= SX) {
+  if (n <= SX)
     run_recurrence<1>(n, dg, up, lo, c, cscale, mode, S, K, lead, w, tid);
-  } else {
+  else
     run_recurrence<2>(n, dg, up, lo, c, cscale, mode, S, K, lead, w, tid);
-  }
   if (tid == 0) {
     w.mode = mode;
     w.lead = lead;
@@ -1569,13 +1510,15 @@ __global__ void __launch_bounds__(THREADS, 4) k_kcomb(CombArgs a, size_t N) {
   T* z0 = const_cast<T*>(zp[0]);
   Acc acc[1] = {acc_zero<Acc>()};
   const size_t stride = (size_t)gridDim.x * THREADS;
-  // Pairs of elements, one 16-byte load per basis vector (a.pairs: N even,
-  // every slot and the output 16-byte aligned).  The loads of KC basis vectors
-  // are issued before their products are summed, so a thread waits for memory
-  // once per KC terms instead of once per term; the sum runs in the basis
-  // order, the same arithmetic as the element loop below.
+  // Double-float path: pairs of elements, one 16-byte load per basis vector
+  // (a.pairs: N even, every slot and the output 16-byte aligned).  The loads
+  // of KC basis vectors are issued before their products are summed, so a
+  // thread waits for memory once per KC terms instead of once per term; the
+  // sum runs in the basis order, the same arithmetic as the element loop
+  // below.  (The float64 path is bound by GB300's float64 rate, not by these
+  // latencies: it keeps the element loop.)
   size_t i0 = 0;
-  if (a.pairs) {
+  if (P == P_DF64 && a.pairs) {
     constexpr int KC = 8;
     const size_t np = N / 2;
     for (size_t v = (size_t)blockIdx.x * THREADS + tid; v < np; v += stride) {
