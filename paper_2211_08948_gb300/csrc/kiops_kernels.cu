@@ -1610,8 +1610,7 @@ __global__ void __launch_bounds__(THREADS)
   Acc acc[1] = {acc_zero<Acc>()};
   const size_t stride = (size_t)gridDim.x * THREADS;
   const int tid = threadIdx.y * 32 + threadIdx.x;
-  for (size_t i = (size_t)blockIdx.x * THREADS + tid; i < N; i += stride) {
-    double x = b0 ? c * b0[i] : 0.0;  // c: a power of two, exact
+  auto body = [&](size_t i, double x) {
     C w;
     if constexpr (P == P_FP64)
       w = x;
@@ -1619,7 +1618,16 @@ __global__ void __launch_bounds__(THREADS)
       w = df_split_pow2(x, 0);
     st1(z0 + i, w);
     acc_dot(acc[0], w, w);
+  };
+  size_t i = (size_t)blockIdx.x * THREADS + tid;
+  for (; i + (UNR - 1) * stride < N; i += UNR * stride) {
+    double x[UNR];
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) x[u] = b0 ? c * __ldg(b0 + i + u * stride) : 0.0;  // c: a power of two, exact
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) body(i + u * stride, x[u]);
   }
+  for (; i < N; i += stride) body(i, b0 ? c * __ldg(b0 + i) : 0.0);
   if (block_partials_and_last<Acc, 1>(acc, a.partials, &kc->count)) {
     double tot[1];
     reduce_partials<Acc, 1>(a.partials, tot);
@@ -1651,17 +1659,26 @@ __global__ void __launch_bounds__(THREADS)
                unsigned int* counter, double* norm1) {
   double acc[1] = {0.0};
   const size_t stride = (size_t)gridDim.x * THREADS;
-  for (size_t i = (size_t)blockIdx.x * THREADS + threadIdx.y * 32 + threadIdx.x; i < n; i += stride) {
-    double x = b[i];
+  auto body = [&](size_t i, double x) {
     acc[0] += fabs(x);
-    if (!out) continue;  // norm only
+    if (!out) return;  // norm only
     if constexpr (P == P_FP64)
       out[i] = x;
     else {
       df w = df_split_pow2(x, 0);
       out[i] = make_float2(w.hi, w.lo);
     }
+  };
+  // the thread's elements in grid-stride order, their loads issued UNR at a time
+  size_t i = (size_t)blockIdx.x * THREADS + threadIdx.y * 32 + threadIdx.x;
+  for (; i + (UNR - 1) * stride < n; i += UNR * stride) {
+    double x[UNR];
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) x[u] = __ldg(b + i + u * stride);
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) body(i + u * stride, x[u]);
   }
+  for (; i < n; i += stride) body(i, __ldg(b + i));
   if (block_partials_and_last<double, 1>(acc, partials, counter)) {
     double tot[1];
     reduce_partials<double, 1>(partials, tot);

@@ -387,17 +387,17 @@ __global__ void __launch_bounds__(THREADS)
   const double is = __ldcg(&a.ctl->inv_sigma);
   const int se = __ldcg(&a.ctl->sigma_e);
   const size_t stride = (size_t)gridDim.x * THREADS;
-  for (size_t i = (size_t)blockIdx.x * THREADS + threadIdx.y * 32 + threadIdx.x; i < n; i += stride) {
+  auto body = [&](size_t i, double vi) {
     C y;
     if constexpr (P == P_FP64) {
-      const double x = v[i] * is;
+      const double x = vi * is;
       y = x;
       y0[i] = x;
     } else if constexpr (P == P_FP32) {
-      y = (float)(v[i] * is);
+      y = (float)(vi * is);
       y0[i] = y;
     } else {
-      y = df_split_pow2(v[i], -se);  // v / sigma, sigma a power of two
+      y = df_split_pow2(vi, -se);  // v / sigma, sigma a power of two
       y0[i] = make_float2(y.hi, y.lo);
     }
     acc_sq(acc[0], y);
@@ -409,7 +409,17 @@ __global__ void __launch_bounds__(THREADS)
         acc_sq(acc[1 + k], p);
       }
     }
+  };
+  // the thread's elements in grid-stride order, their loads issued UNR at a time
+  size_t i = (size_t)blockIdx.x * THREADS + threadIdx.y * 32 + threadIdx.x;
+  for (; i + (UNR - 1) * stride < n; i += UNR * stride) {
+    double x[UNR];
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) x[u] = __ldg(v + i + u * stride);
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) body(i + u * stride, x[u]);
   }
+  for (; i < n; i += stride) body(i, __ldg(v + i));
   if (block_partials_and_last<Acc, KMAX + 1>(acc, a.partials, &a.ctl->count)) {
     double tot[KMAX + 1];
     reduce_partials<Acc, KMAX + 1>(a.partials, tot);
@@ -429,8 +439,16 @@ __global__ void __launch_bounds__(THREADS)
     k_scale(const double* __restrict__ v, size_t n, LejaCtl* ctl, double* partials) {
   double acc[1] = {0.0};
   const size_t stride = (size_t)gridDim.x * THREADS;
-  for (size_t i = (size_t)blockIdx.x * THREADS + threadIdx.y * 32 + threadIdx.x; i < n; i += stride) {
-    double x = v[i];
+  size_t i = (size_t)blockIdx.x * THREADS + threadIdx.y * 32 + threadIdx.x;
+  for (; i + (UNR - 1) * stride < n; i += UNR * stride) {
+    double x[UNR];
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) x[u] = __ldg(v + i + u * stride);
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) acc[0] = fma(x[u], x[u], acc[0]);
+  }
+  for (; i < n; i += stride) {
+    const double x = __ldg(v + i);
     acc[0] = fma(x, x, acc[0]);
   }
   if (block_partials_and_last<double, 1>(acc, partials, &ctl->count)) {
@@ -476,15 +494,26 @@ __global__ void __launch_bounds__(THREADS) k_finalize(size_t n, int K, PtrPack p
       const int M = pp_of(tab)->M;
       dk = coef<C>(dk_d_of(tab, M)[k * M + it], dk_f_of(tab, M)[k * M + it]);
     }
-    for (size_t i = (size_t)blockIdx.x * THREADS + threadIdx.y * 32 + threadIdx.x; i < n; i += stride) {
-      C x = cv(p[i]);
-      if (def) x = mad(dk, cv(yd[i]), x);
+    auto body = [&](size_t i, C x, C yv) {
+      if (def) x = mad(dk, yv, x);
       if constexpr (P == P_FP64 || P == P_FP32) {
         o[i] = s * (double)x;
       } else {
         o[i] = df_to_double_pow2(x, se);  // sigma (hi + lo), sigma a power of two
       }
+    };
+    size_t i = (size_t)blockIdx.x * THREADS + threadIdx.y * 32 + threadIdx.x;
+    for (; i + (UNR - 1) * stride < n; i += UNR * stride) {
+      C x[UNR], yv[UNR];
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) {
+        x[u] = cv(p[i + u * stride]);
+        yv[u] = def ? cv(yd[i + u * stride]) : C{};
+      }
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) body(i + u * stride, x[u], yv[u]);
     }
+    for (; i < n; i += stride) body(i, cv(p[i]), def ? cv(yd[i]) : C{});
   }
 }
 
@@ -534,16 +563,16 @@ __global__ void __launch_bounds__(THREADS)
                  double scale) {
   using S = typename Tr<P>::S;
   const size_t stride = (size_t)gridDim.x * THREADS;
-  for (size_t i = (size_t)blockIdx.x * THREADS + threadIdx.y * 32 + threadIdx.x; i < plane; i += stride) {
+  const bool gs = op == PHIX_OP_GRAYSCOTT;
+  auto body = [&](size_t i, double U, double Vv) {
     double g[2];
     int ng = 1;
-    if (op == PHIX_OP_GRAYSCOTT) {
-      double U = state[i], Vv = state[plane + i];
+    if (gs) {
       g[0] = scale * (Vv * Vv);
       g[1] = scale * (2.0 * U * Vv);
       ng = 2;
     } else {
-      g[0] = scale * state[i];
+      g[0] = scale * U;
     }
     for (int j = 0; j < ng; ++j) {
       S s;
@@ -557,7 +586,19 @@ __global__ void __launch_bounds__(THREADS)
       }
       st[j * plane + i] = s;
     }
+  };
+  size_t i = (size_t)blockIdx.x * THREADS + threadIdx.y * 32 + threadIdx.x;
+  for (; i + (UNR - 1) * stride < plane; i += UNR * stride) {
+    double U[UNR], Vv[UNR];
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+      U[u] = __ldg(state + i + u * stride);
+      Vv[u] = gs ? __ldg(state + plane + i + u * stride) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) body(i + u * stride, U[u], Vv[u]);
   }
+  for (; i < plane; i += stride) body(i, __ldg(state + i), gs ? __ldg(state + plane + i) : 0.0);
 }
 
 // ---------------------------------------------------------------------------

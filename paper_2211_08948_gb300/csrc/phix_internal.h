@@ -15,6 +15,7 @@ namespace phix {
 constexpr int KMAX = 4;       // accumulators of one vertical Newton pass
 constexpr int TILE_Y = 8;     // rows per tile (one warp per row)
 constexpr int THREADS = 256;  // 32 x 8
+constexpr int UNR = 4;        // elements per thread whose loads a streaming kernel issues together
 
 enum Prec { P_FP64 = 0, P_DF64 = 1, P_FP32JV = 2, P_FP32 = 3 };
 enum Mode { MODE_NEWTON = 0, MODE_POWER = 1 };

@@ -33,14 +33,29 @@ __global__ void k_rhs(OpDesc op, const double* __restrict__ u, double* __restric
 // (f(a) and f(u) carry the O(n^2) Laplacian terms; R is O(|d|^2)).
 __global__ void k_remainder_gs(size_t plane, const double* __restrict__ u, const double* __restrict__ a,
                                double* __restrict__ R) {
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < plane; i += (size_t)gridDim.x * blockDim.x) {
-    const double v = u[plane + i];
-    const double au = a[i], av = a[plane + i];
-    const double du = au - u[i], dv = av - v;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  auto body = [&](size_t i, double uu, double v, double au, double av) {
+    const double du = au - uu, dv = av - v;
     const double r = dv * (au * dv + 2.0 * v * du);
     R[i] = -r;
     R[plane + i] = r;
+  };
+  // the thread's points in grid-stride order, their loads issued UNR at a time
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + (UNR - 1) * stride < plane; i += UNR * stride) {
+    double uu[UNR], v[UNR], au[UNR], av[UNR];
+#pragma unroll
+    for (int q = 0; q < UNR; ++q) {
+      const size_t j = i + q * stride;
+      uu[q] = u[j];
+      v[q] = u[plane + j];
+      au[q] = a[j];
+      av[q] = a[plane + j];
+    }
+#pragma unroll
+    for (int q = 0; q < UNR; ++q) body(i + q * stride, uu[q], v[q], au[q], av[q]);
   }
+  for (; i < plane; i += stride) body(i, u[i], u[plane + i], a[i], a[plane + i]);
 }
 
 __global__ void k_remainder_burgers(OpDesc op, const double* __restrict__ u, const double* __restrict__ a,
@@ -105,7 +120,25 @@ struct Comb {
 };
 
 __global__ void k_lincomb(size_t n, int nt, Comb cb, double* out) {
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // UNR elements per pass: each term's loads of them issued together; every
+  // element's sum runs over the terms in order, as in the element loop below
+  for (; i + (UNR - 1) * stride < n; i += UNR * stride) {
+    double r[UNR];
+#pragma unroll
+    for (int q = 0; q < UNR; ++q) r[q] = 0.0;
+    for (int t = 0; t < nt; ++t) {
+      double x[UNR];
+#pragma unroll
+      for (int q = 0; q < UNR; ++q) x[q] = cb.x[t][i + q * stride];
+#pragma unroll
+      for (int q = 0; q < UNR; ++q) r[q] += cb.c[t] * x[q];
+    }
+#pragma unroll
+    for (int q = 0; q < UNR; ++q) out[i + q * stride] = r[q];
+  }
+  for (; i < n; i += stride) {
     double r = 0.0;
     for (int t = 0; t < nt; ++t) r += cb.c[t] * cb.x[t][i];
     out[i] = r;
@@ -117,7 +150,16 @@ __global__ void k_norm2(size_t n, const double* __restrict__ x, const double* __
   __shared__ double sw[32];
   __shared__ bool last;
   double s = 0.0;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + (UNR - 1) * stride < n; i += UNR * stride) {
+    double d[UNR];
+#pragma unroll
+    for (int q = 0; q < UNR; ++q) d[q] = y ? x[i + q * stride] - y[i + q * stride] : x[i + q * stride];
+#pragma unroll
+    for (int q = 0; q < UNR; ++q) s = fma(d[q], d[q], s);
+  }
+  for (; i < n; i += stride) {
     double d = y ? x[i] - y[i] : x[i];
     s = fma(d, d, s);
   }
