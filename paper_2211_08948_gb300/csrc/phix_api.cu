@@ -70,6 +70,7 @@ struct phix_ctx {
     int m_limit;          // the caller's m_max
     bool persistent;      // one cooperative launch ran the whole chain
     bool fused2;          // two iterations per launch
+    int prefix;           // graph chain: launches ahead of its WHILE node
   };
   std::vector<Pending> pend;     // queued passes since the last flush
   int nslot = 0;                 // slots in use
@@ -263,11 +264,14 @@ void flush(phix_ctx* ctx) {
   CK(cudaStreamSynchronize(ctx->stream));
   for (const phix_ctx::Pending& q : ctx->pend) {
     const LejaCtl& c = ctx->ctl_h[q.slot];
-    // the WHILE loop ran until the body holding iteration `iters` (one body
-    // when the chain stopped before its first iteration); a persistent chain
-    // is one launch
+    // the prefix launches, then the WHILE loop until the body holding the
+    // launch that stopped the chain (none when it stopped inside the prefix;
+    // one body when a chain without prefix stopped before its first
+    // iteration); a persistent chain is one launch
     const int work_launches = q.fused2 ? (c.iters + 1) / 2 : c.iters;
-    ctx->launches += q.persistent ? 1 : (long)GRAPH_ITERS * std::max(1, (work_launches + GRAPH_ITERS - 1) / GRAPH_ITERS);
+    const int rest = work_launches - q.prefix;
+    const long bodies = rest > 0 ? (rest + GRAPH_ITERS - 1) / GRAPH_ITERS : (q.prefix == 0 ? 1 : 0);
+    ctx->launches += q.persistent ? 1 : q.prefix + (long)GRAPH_ITERS * bodies;
     if (!q.stats) continue;
     const int status = c.done ? c.status : PHIX_ENOTCONV;
     if (status == PHIX_ENOTCONV && c.iters == q.m_table && q.m_table < q.m_limit) {
@@ -342,18 +346,30 @@ cudaGraphExec_t chain_graph(phix_ctx* ctx, const ChainSpec& key) {
     cudaGraphConditionalHandle h;
     e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
     if (e != cudaSuccess) break;
+    ChainSpec spec = key;
+    spec.use_cond = 1;
+    spec.cond = h;
+    alignas(64) unsigned char argbuf[2048];  // kernel arguments (tensor maps are 64-byte aligned)
+    // the prefix: launches in sequence ahead of the loop, clearing the same
+    // condition when the chain has stopped
+    cudaGraphNode_t last = nullptr;
+    for (int i = 0; i < key.prefix && e == cudaSuccess; ++i) {
+      cudaKernelNodeParams np;
+      e = iter_node_params(spec, &np, argbuf, sizeof argbuf);
+      if (e != cudaSuccess) break;
+      cudaGraphNode_t node;
+      e = cudaGraphAddKernelNode(&node, g, last ? &last : nullptr, last ? 1 : 0, &np);
+      last = node;
+    }
+    if (e != cudaSuccess) break;
     cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};  // the rest zero
     cp.conditional.handle = h;
     cp.conditional.type = cudaGraphCondTypeWhile;
     cp.conditional.size = 1;
     cudaGraphNode_t cn;
-    e = cudaGraphAddNode(&cn, g, nullptr, nullptr, 0, &cp);
+    e = cudaGraphAddNode(&cn, g, last ? &last : nullptr, nullptr, last ? 1 : 0, &cp);
     if (e != cudaSuccess) break;
     cudaGraph_t body = cp.conditional.phGraph_out[0];
-    ChainSpec spec = key;
-    spec.use_cond = 1;
-    spec.cond = h;
-    alignas(64) unsigned char argbuf[2048];  // kernel arguments (tensor maps are 64-byte aligned)
     cudaGraphNode_t prev = nullptr;
     for (int i = 0; i < GRAPH_ITERS && e == cudaSuccess; ++i) {
       cudaKernelNodeParams np;
@@ -657,6 +673,14 @@ void leja_pass(phix_ctx* ctx, const OpState& os, int prec, const double* v, int 
     }
   }
   const bool profile = o.profile != 0;
+  // graph chains: the predicted chain length (the table was truncated to
+  // twice the prediction plus 24; chains measured 1.2-1.9x the prediction),
+  // in whole bodies, runs ahead of the WHILE node without condition evaluations
+  if (!persistent && o.profile != 2 && m_max < o.m_max) {
+    const int m_pred = (M - 24) / 2;
+    const int pl = cs.fused2 ? m_pred / 2 : m_pred;
+    cs.prefix = std::max(0, pl / GRAPH_ITERS * GRAPH_ITERS);
+  }
   if (persistent) {
     if (profile) CK(cudaEventRecord(ctx->ev[2 * s], ctx->stream));
     CK(launch_chain(cs, ctx->stream));
@@ -678,6 +702,7 @@ void leja_pass(phix_ctx* ctx, const OpState& os, int prec, const double* v, int 
   q.m_limit = o.m_max;
   q.persistent = persistent;
   q.fused2 = cs.fused2 != 0;
+  q.prefix = cs.prefix;
   if (profile) {
     // algorithmic bytes of one iteration: read y, write the new iterate, read
     // and write each p_k, read the state planes; a two-iteration launch moves

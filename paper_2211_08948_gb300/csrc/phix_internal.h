@@ -87,6 +87,8 @@ struct ChainSpec {
   int fused2;         // MODE_NEWTON: 1 = two iterations per launch (leja_fused.cu)
   int use_cond;       // launched as the body of a conditional WHILE graph node:
   unsigned long long cond;  // its handle; the kernel clears it once the chain stopped
+  int prefix;         // graph chains: launches queued ahead of the WHILE node (no condition
+                      // evaluations; a launch after the stop returns at once and clears the condition)
 };
 // One iteration launch.
 cudaError_t launch_iter(const ChainSpec& s, cudaStream_t st);
