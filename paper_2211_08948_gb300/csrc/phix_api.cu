@@ -767,9 +767,8 @@ std::vector<std::vector<double>> pass_tables(phix_ctx* ctx, int K, const int* l,
   return d;
 }
 
-// Power iteration (Sec. 2.2) on the device; flushes to read the estimate.
-double power_iteration(phix_ctx* ctx, const OpState& os, int prec, const phix_opts& o, int* mv) {
-  if (general_kind(os.d.kind) || o.jv == PHIX_JV_FD) return general_power(ctx, os, o, mv);
+// Power iteration (Sec. 2.2) on the device, queued: returns its slot.
+int power_iteration_queue(phix_ctx* ctx, const OpState& os, int prec, const phix_opts& o) {
   const size_t eb = elem_bytes(prec);
   void* y[2] = {ws(ctx, S_Y0, os.N * eb), ws(ctx, S_Y1, os.N * eb)};
   const int s = acquire_slot(ctx, ptab_bytes(o.power_max_it + 1));
@@ -793,11 +792,37 @@ double power_iteration(phix_ctx* ctx, const OpState& os, int prec, const phix_op
   phix_ctx::Pending q{};
   q.slot = s;
   ctx->pend.push_back(q);
-  flush(ctx);
+  return s;
+}
+
+double power_result(phix_ctx* ctx, int s, int* mv) {
   const LejaCtl& c = ctx->ctl_h[s];
   if (c.status == PHIX_ENAN) fail(ctx, PHIX_ENAN, "power iteration produced a non-finite norm");
   *mv = c.iters;
   return c.rho;
+}
+
+// The estimate, flushing every queued pass.
+double power_iteration(phix_ctx* ctx, const OpState& os, int prec, const phix_opts& o, int* mv) {
+  if (general_kind(os.d.kind) || o.jv == PHIX_JV_FD) return general_power(ctx, os, o, mv);
+  const int s = power_iteration_queue(ctx, os, prec, o);
+  flush(ctx);
+  return power_result(ctx, s, mv);
+}
+
+// Queued with a read-back of its control block behind it (and an event after
+// that): the host queues work that does not need the estimate, then waits
+// for the read-back alone (power_iteration_collect) while that work runs.
+int power_iteration_split(phix_ctx* ctx, const OpState& os, int prec, const phix_opts& o) {
+  const int s = power_iteration_queue(ctx, os, prec, o);
+  CK(cudaMemcpyAsync(ctx->ctl_h + s, ctx->ctl + s, sizeof(LejaCtl), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaEventRecord(ctx->ev[2 * NSLOT + 2], ctx->stream));
+  return s;
+}
+
+double power_iteration_collect(phix_ctx* ctx, int s, int* mv) {
+  CK(cudaEventSynchronize(ctx->ev[2 * NSLOT + 2]));
+  return power_result(ctx, s, mv);
 }
 
 double factorial(int n) {
@@ -1177,25 +1202,31 @@ void kiops_phi(phix_ctx* ctx, const OpState& os, int prec, double h, const doubl
   }
 }
 
-Interval interval_for(phix_ctx* ctx, const OpState& os, int prec, const phix_opts& o, phix_stats& stats) {
+// The interval [-safety rho, rho_hi] from a power-iteration estimate.
+Interval interval_from_estimate(double rho, int mv, const phix_opts& o, phix_stats& stats) {
   Interval iv{};
-  double alpha, beta;
-  if (o.rho_re > 0) {
-    alpha = -o.rho_re;
-    beta = o.rho_hi;
-    iv.rho = o.rho_re;
-  } else {
-    int mv = 0;
-    double rho = power_iteration(ctx, os, prec, o, &mv);
-    stats.power_mv += mv;
-    iv.rho = rho;
-    alpha = -o.safety * rho;
-    beta = o.rho_hi;
-  }
+  stats.power_mv += mv;
+  iv.rho = rho;
+  const double alpha = -o.safety * rho, beta = o.rho_hi;
   iv.c = 0.5 * (alpha + beta);
   iv.gamma = 0.25 * (beta - alpha);
   stats.rho = iv.rho;
   return iv;
+}
+
+Interval interval_for(phix_ctx* ctx, const OpState& os, int prec, const phix_opts& o, phix_stats& stats) {
+  if (o.rho_re > 0) {
+    Interval iv{};
+    const double alpha = -o.rho_re, beta = o.rho_hi;
+    iv.rho = o.rho_re;
+    iv.c = 0.5 * (alpha + beta);
+    iv.gamma = 0.25 * (beta - alpha);
+    stats.rho = iv.rho;
+    return iv;
+  }
+  int mv = 0;
+  const double rho = power_iteration(ctx, os, prec, o, &mv);
+  return interval_from_estimate(rho, mv, o, stats);
 }
 
 void phi_actions(phix_ctx* ctx, const OpState& os, phix_method method, int prec, double h, const double* v,
@@ -1327,7 +1358,7 @@ phix_status phix_create(phix_ctx** out, void* stream) {
     ctx->grid_stream = ctx->nsm * 8;
     CK(cudaMalloc(&ctx->ctl, sizeof(LejaCtl) * NSLOT));
     CK(cudaMallocHost(&ctx->ctl_h, sizeof(LejaCtl) * NSLOT));
-    for (int i = 0; i < 2 * NSLOT + 2; ++i) {  // + one pair for KIOPS
+    for (int i = 0; i < 2 * NSLOT + 3; ++i) {  // + one pair for KIOPS, one for the power-iteration read-back
       cudaEvent_t e;
       CK(cudaEventCreate(&e));
       ctx->ev.push_back(e);
@@ -1906,11 +1937,22 @@ static phix_status exp_step(phix_ctx* ctx, int scheme, const phix_jop* op, doubl
     double* O4 = wsd(ctx, S_O4, N);
     double* O5 = wsd(ctx, S_O5, N);
     double* O6 = wsd(ctx, S_O6, N);
-    KL(launch_rhs(os.d, u, F, ctx->grid_stream, ctx->stream));
+    // the power iteration first, then f(u) and h f(u) (which do not need the
+    // estimate) run on the device while the host reads the estimate and
+    // builds the first pass's coefficient tables
     Interval ivv{};
-    if (method != PHIX_KIOPS) ivv = interval_for(ctx, os, prec, o, st);
-    const Interval* iv = method != PHIX_KIOPS ? &ivv : nullptr;
+    const bool split = method != PHIX_KIOPS && !(o.rho_re > 0) && !general_kind(os.d.kind) && o.jv != PHIX_JV_FD;
+    const int pslot = split ? power_iteration_split(ctx, os, prec, o) : -1;
+    KL(launch_rhs(os.d, u, F, ctx->grid_stream, ctx->stream));
     lincomb(ctx, N, {h}, {F}, FH);
+    if (split) {
+      int mv = 0;
+      const double rho = power_iteration_collect(ctx, pslot, &mv);
+      ivv = interval_from_estimate(rho, mv, o, st);
+    } else if (method != PHIX_KIOPS) {
+      ivv = interval_for(ctx, os, prec, o, st);
+    }
+    const Interval* iv = method != PHIX_KIOPS ? &ivv : nullptr;
     // phi_{l_k}(s_k h J) x for up to four outputs, by `how` (Leja vertical or KIOPS output times)
     auto vert = [&](phix_method how, const double* x, std::vector<int> l, std::vector<double> s,
                     std::vector<double*> out) {
