@@ -172,7 +172,10 @@ typedef struct {
                           totals; a barrier wait that exceeds 2 s ends the pass with
                           PHIX_ETIMEOUT); PHIX_CHAIN_AUTO (default) and
                           PHIX_CHAIN_GRAPH run one launch per iteration inside a
-                          conditional CUDA graph (measured faster on GB300).
+                          CUDA graph: the chain length predicted from the divided
+                          differences as plain launches, then a conditional WHILE
+                          node of 8 launches per evaluation (measured faster on
+                          GB300; a launch after the stop returns at once).
                           The TMA-staged kernel always runs one launch per iteration. */
 } phix_opts;
 
