@@ -353,7 +353,7 @@ typedef struct {
   double* out[3];      /* device, nx*ny each, out[k] for l[k], k < nout             */
 } phix_batch_problem;
 
-/* Batched actions (north_star form "batching"; Sec. 2.2 per problem): for
+/* Batched actions (many small independent problems; Sec. 2.2 per problem): for
  * every problem i < nprob, out[k] = phi_{l[k]}(h_i J_i) v_i, k < nout <= 3,
  * l[k] in 0..2, all in ONE persistent kernel launch replayed from a CUDA
  * graph: each CTA takes whole problems from a largest-first queue and runs
@@ -378,7 +378,7 @@ phix_status phix_phi_action_batched(phix_ctx* ctx, const phix_batch_problem* pro
 /* The launch configuration of the context's last batched call.           */
 phix_status phix_batched_config(const phix_ctx* ctx, int* threads_per_cta, int* smem_bytes, int* ctas_per_sm);
 
-/* Learned spectral interval (north_star form "learned"; replaces the power
+/* Learned spectral interval (a trained predictor of the interval; replaces the power
  * iterations of Sec. 2.2 by a prediction, with power iteration as fallback).
  * MLP 16 -> 64 -> 64 -> 3, GELU, bfloat16 weights / float32 accumulation;
  * params: PHIX_MLP_NPARAM float32 values W1[64x16] b1[64] W2[64x64] b2[64]
