@@ -20,7 +20,14 @@ leja         Leja points, divided differences, power iteration, Newton
 kiops        KIOPS-style Krylov action on the augmented matrix (Sec. 2.1)
 exact        exact references: FFT diagonalisation, dense expm of the
              augmented matrix (Theorem of Sec. 2.1)
-integrators  EXPRB43 (Eq. exprb43) and EPIRK4s3 (Eq. epirk4s3) steps
+integrators  the steps of Sec. 5: EXPRB43 (Eq. exprb43), EPIRK4s3 (Eq. epirk4s3),
+             EPIRK4s3A (Eq. epirk4s3a), EXPRB53s3 (Eq. exprb5s3), EPIRK5P1 (its
+             coefficient table), with Leja, KIOPS or LeKry (Sec. 5.1) and the
+             vertical / horizontal grouping of Sec. 4
+adaptive     traditional and cost step-size controllers (Sec. 2.3)
+problems     the no-flow test problems of Sec. 3 (ADR, Allen-Cahn, Brusselator)
+variants     finite-difference Jacobian actions (Sec. 4), augmented-matrix Leja
+             (Appendix A)
 mlp          MLP forward/backward/Adam for the learned spectral interval
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test in
