@@ -1017,8 +1017,9 @@ __device__ void msect_round(int n, const float* a, const float* b2, float (&lo)[
 // Terms advance two at a time from (T_{k-1}, T_k):
 //   T_{k+1} = M T_k - T_{k-1},   T_{k+2} = (M^2 - I) T_k - M T_{k-1},
 // the pentadiagonal M^2 - I in pc (columns i-2 .. i+2 of row i): both new
-// terms depend only on the pair before, so the serial chain and the
-// exchanges through shared memory (one barrier per pair) are halved.
+// terms depend only on the pair before, so a pair of terms takes one exchange
+// through shared memory and one barrier (the arithmetic per term is not
+// reduced: the step is bound by each row's dependent double-float operations).
 template <int R>
 __device__ void cheb_segments(int n, int S, int K, const df (&ma)[R], const df (&mu)[R], const df (&ml)[R],
                               const df (&pc)[R][5], df (&xr)[R], double& lead, SmallExpWork& w, int tid) {
